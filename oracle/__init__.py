@@ -1,0 +1,495 @@
+"""FP64 CPU oracle of the voxel deformation-aware neural intersection function.
+
+TEST INFRASTRUCTURE ONLY: only `tests/`, `__graft_entry__.smoke()` and the
+CPU-baseline leg of `bench.py` may import this package. It shares no code with
+the CUDA library (`paper_2604_24666_gb300/csrc`) and never imports it.
+
+The oracle follows the paper step by step, in float64:
+
+* geometry (C, `nif_oracle.c`): deformation and inverse (Sec. 2), voxelization
+  (Sec. 2), ray / deformed-voxel segments (Sec. 2.1-2.2), linearized-segment
+  labels (Sec. 2), exact deformed-space hits;
+* the hybrid encoding psi = phi o gamma (Eq. 1, Sec. 2.3), its backward;
+* the MLP (Sec. 2, Fig. 2d) forward and backward;
+* the task losses and the uncertainty weighting (Sec. 2.4);
+* Adam;
+* the segmented-ray distance and hit reconstruction (Sec. 2.2).
+
+Where the paper is silent the oracle takes the readings that the library
+states in its header (`include/nif.h`); every such reading is listed with the
+design notes of the repository.
+
+Integer decisions made from floating point (hash-grid cell indices) are taken
+in float32, the precision the kernels use: the oracle rounds the grid
+coordinate u to float32 and forms the float32 product u*N_l before the floor.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+K_BEND = 0.75          # bend curvature per unit bend parameter
+EPS_DIST = 1e-2        # epsilon of the log-space distance loss (voxel units)
+TASKS = ("distance", "normal", "albedo", "material", "occlusion")
+
+
+def build(force: bool = False) -> str:
+    """Compile the C part of the oracle with gcc (FP64, no FMA contraction)."""
+    src = os.path.join(_HERE, "nif_oracle.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-o", tmp, src, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            dp, fp, ip, lp = (np.ctypeslib.ndpointer(np.float64, flags="C"),
+                              np.ctypeslib.ndpointer(np.float32, flags="C"),
+                              np.ctypeslib.ndpointer(np.int32, flags="C"),
+                              np.ctypeslib.ndpointer(np.int64, flags="C"))
+            u8 = np.ctypeslib.ndpointer(np.uint8, flags="C")
+            L.or_deform.argtypes = [dp, dp, dp, ctypes.c_long]
+            L.or_inverse.argtypes = [dp, dp, dp, ctypes.c_long]
+            L.or_jacobians.argtypes = [dp, dp, dp, dp, ctypes.c_long]
+            L.or_voxelize.argtypes = [ctypes.c_int, fp, ip, ctypes.c_int, u8, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_long]
+            L.or_voxelize.restype = ctypes.c_long
+            L.or_segments.argtypes = [ctypes.c_int, u8, dp, fp, ctypes.c_long, ctypes.c_int, ip, ip,
+                                      dp, dp, dp]
+            L.or_segments.restype = ctypes.c_long
+            L.or_labels.argtypes = [lp, ip, fp, ip, fp, u8, ctypes.c_long, ip, dp, dp, u8, dp, dp, dp,
+                                    u8, dp]
+            L.or_exact_hits.argtypes = [dp, ip, ctypes.c_int, fp, ctypes.c_long, dp, ip]
+            L.or_num_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+# ---------------------------------------------------------------------------
+# Deformation (Sec. 2; family and parameterisation are our reading)
+# ---------------------------------------------------------------------------
+
+def _pose(pose) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(pose, np.float64).reshape(3))
+
+
+def deform(pose, x) -> np.ndarray:
+    """D(x): rest -> deformed, D = Bend o Twist o Taper about the cube centre."""
+    x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, 3))
+    y = np.empty_like(x)
+    lib().or_deform(_pose(pose), x, y, len(x))
+    return y
+
+
+def inverse(pose, y) -> np.ndarray:
+    """D^-1(y): deformed -> rest (closed form)."""
+    y = np.ascontiguousarray(np.asarray(y, np.float64).reshape(-1, 3))
+    x = np.empty_like(y)
+    lib().or_inverse(_pose(pose), y, x, len(y))
+    return x
+
+
+def jacobians(pose, x):
+    """(J, Jp): dD/dx [n,3,3] and dD/d(bend,twist,taper) [n,3,3] at rest points x."""
+    x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, 3))
+    J = np.empty((len(x), 9))
+    Jp = np.empty((len(x), 9))
+    lib().or_jacobians(_pose(pose), x, J, Jp, len(x))
+    return J.reshape(-1, 3, 3), Jp.reshape(-1, 3, 3)
+
+
+# ---------------------------------------------------------------------------
+# Voxelization (Sec. 2)
+# ---------------------------------------------------------------------------
+
+def voxelize(N: int, mesh):
+    """(occ [N^3] uint8 x-fastest, tri_ptr [N^3+1] int64, tri_idx int32)."""
+    verts = np.ascontiguousarray(mesh.verts, np.float32)
+    tris = np.ascontiguousarray(mesh.tris, np.int32)
+    occ = np.zeros(N ** 3, np.uint8)
+    total = lib().or_voxelize(N, verts, tris, len(tris), occ, None, None, 0)
+    ptr = np.zeros(N ** 3 + 1, np.int64)
+    idx = np.zeros(max(total, 1), np.int32)
+    lib().or_voxelize(N, verts, tris, len(tris), occ, ptr.ctypes.data, idx.ctypes.data, total)
+    return occ, ptr, idx[:total]
+
+
+# ---------------------------------------------------------------------------
+# Segments (Sec. 2.1, Sec. 2.2)
+# ---------------------------------------------------------------------------
+
+class Segments:
+    """Ragged segment lists: ray r owns rows [off[r], off[r+1])."""
+
+    def __init__(self, count, vox, t0, t1, margin):
+        self.count = count
+        self.off = np.concatenate([[0], np.cumsum(count)]).astype(np.int64)
+        self.vox = vox
+        self.t0 = t0
+        self.t1 = t1
+        self.margin = margin
+        self.ray = np.repeat(np.arange(len(count)), count)
+
+    def __len__(self):
+        return int(self.off[-1])
+
+
+def segments(N: int, occ, pose, rays, max_per_ray: int = 512) -> Segments:
+    rays = np.ascontiguousarray(rays, np.float32)
+    n = len(rays)
+    cnt = np.zeros(n, np.int32)
+    vox = np.zeros(n * max_per_ray, np.int32)
+    t0 = np.zeros(n * max_per_ray)
+    t1 = np.zeros(n * max_per_ray)
+    mar = np.zeros(n)
+    ov = lib().or_segments(N, np.ascontiguousarray(occ, np.uint8), _pose(pose), rays, n,
+                           max_per_ray, cnt, vox, t0, t1, mar)
+    if ov:
+        raise RuntimeError(f"{ov} rays exceed {max_per_ray} segments")
+    sel = (np.arange(max_per_ray)[None, :] < cnt[:, None]).reshape(-1)
+    return Segments(cnt, vox[sel], t0[sel], t1[sel], mar)
+
+
+def linearize(pose, rays, seg: Segments):
+    """Rest-space straight segment of every (ray, voxel) segment (Sec. 2).
+
+    x0 = o + t0 d, x1 = o + t1 d in deformed space; p0 = D^-1(x0), p1 = D^-1(x1).
+    Returns p0, p1 [S,3], l_def = |x1 - x0|, l_rest = |p1 - p0|.
+    """
+    rays = np.asarray(rays, np.float64)
+    o = rays[seg.ray, 0:3]
+    d = rays[seg.ray, 3:6]
+    x0 = o + seg.t0[:, None] * d
+    x1 = o + seg.t1[:, None] * d
+    p0 = inverse(pose, x0)
+    p1 = inverse(pose, x1)
+    return p0, p1, np.linalg.norm(x1 - x0, axis=1), np.linalg.norm(p1 - p0, axis=1)
+
+
+def labels(mesh, tri_ptr, tri_idx, vox, p0, p1):
+    """Ground truth of the linearized rest segments: dict of arrays (Sec. 2)."""
+    n = len(vox)
+    out = dict(occ=np.zeros(n, np.uint8), tpar=np.zeros(n), normal=np.zeros((n, 3)),
+               albedo=np.zeros((n, 3)), material=np.zeros(n, np.uint8), margin=np.zeros(n))
+    lib().or_labels(np.ascontiguousarray(tri_ptr, np.int64), np.ascontiguousarray(tri_idx, np.int32),
+                    np.ascontiguousarray(mesh.verts, np.float32), np.ascontiguousarray(mesh.tris, np.int32),
+                    np.ascontiguousarray(mesh.albedo, np.float32), np.ascontiguousarray(mesh.material, np.uint8),
+                    n, np.ascontiguousarray(vox, np.int32), np.ascontiguousarray(p0, np.float64),
+                    np.ascontiguousarray(p1, np.float64), out["occ"], out["tpar"], out["normal"],
+                    out["albedo"], out["material"], out["margin"])
+    return out
+
+
+def exact_hits(mesh, pose, rays):
+    """First hit of each ray with the deformed mesh (vertices mapped by D)."""
+    dv = np.ascontiguousarray(deform(pose, mesh.verts.astype(np.float64)))
+    rays = np.ascontiguousarray(rays, np.float32)
+    t = np.zeros(len(rays))
+    tri = np.zeros(len(rays), np.int32)
+    lib().or_exact_hits(dv, np.ascontiguousarray(mesh.tris, np.int32), len(mesh.tris), rays,
+                        len(rays), t, tri)
+    return t, tri
+
+
+# ---------------------------------------------------------------------------
+# Hybrid encoding psi = phi o gamma (Eq. 1)
+# ---------------------------------------------------------------------------
+
+def level_res(cfg):
+    """N_l = floor(N_min * b^l), l = 0..L-1."""
+    return [int(np.floor(cfg.base_res * cfg.growth ** l)) for l in range(cfg.levels)]
+
+
+def level_dense(cfg):
+    T = 1 << cfg.log2_table
+    return [(n + 1) ** 3 <= T for n in level_res(cfg)]
+
+
+def gamma(cfg, p):
+    """gamma(x) = [x, sin(2^k x), cos(2^k x)]_{k<F} as P = 1+2F 3-vectors [n, P, 3]
+    and their grid coordinates u in [0,1]^3 (x as is, (g+1)/2 for sin/cos)."""
+    p = np.clip(np.asarray(p, np.float64), 0.0, 1.0)
+    g = [p]
+    for k in range(cfg.pe_bands):
+        g.append(np.sin((2.0 ** k) * p))
+        g.append(np.cos((2.0 ** k) * p))
+    g = np.stack(g, 1)
+    u = g.copy()
+    u[:, 1:] = 0.5 * (g[:, 1:] + 1.0)
+    return g, u
+
+
+def grid_index(cfg, l, corner):
+    """Table row of integer grid vertex corner [.., 3] (uint32 arithmetic)."""
+    Nl = level_res(cfg)[l]
+    T = 1 << cfg.log2_table
+    c = corner.astype(np.uint64)
+    if (Nl + 1) ** 3 <= T:
+        return (c[..., 0] + c[..., 1] * (Nl + 1) + c[..., 2] * (Nl + 1) ** 2).astype(np.int64)
+    h = (c[..., 0] * np.uint64(1)) ^ ((c[..., 1] * np.uint64(2654435761)) & np.uint64(0xFFFFFFFF)) \
+        ^ ((c[..., 2] * np.uint64(805459861)) & np.uint64(0xFFFFFFFF))
+    return (h & np.uint64(T - 1)).astype(np.int64)
+
+
+def _cell(cfg, l, u):
+    """Cell of u at level l: float32 decision q = fl32(fl32(u) * N_l), i0, w."""
+    Nl = level_res(cfg)[l]
+    uf = np.asarray(u, np.float32).astype(np.float64)
+    q = (uf * Nl).astype(np.float32).astype(np.float64)
+    i0 = np.minimum(np.floor(q), Nl - 1).astype(np.int64)
+    w = q - i0
+    return i0, w
+
+
+_CORNERS = np.array([[(c >> 0) & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)], np.int64)
+
+
+def grid_encode(cfg, tables, u):
+    """phi(u) for points u [n, 3]: [n, L, F_d], trilinear per level (Eq. 1)."""
+    tables = np.asarray(tables, np.float64)
+    out = np.zeros((len(u), cfg.levels, cfg.feats))
+    for l in range(cfg.levels):
+        i0, w = _cell(cfg, l, u)
+        for c in _CORNERS:
+            idx = grid_index(cfg, l, i0 + c)
+            wt = np.prod(np.where(c == 1, w, 1.0 - w), axis=1)
+            out[:, l, :] += wt[:, None] * tables[l][idx]
+    return out
+
+
+def encode_points(cfg, tables, p):
+    """psi(p) = phi(gamma(p)) for rest points p [n,3]: [n, P*L*F_d],
+    ordered [term][level][feature]."""
+    _, u = gamma(cfg, p)
+    n, P = u.shape[0], u.shape[1]
+    feats = np.stack([grid_encode(cfg, tables, u[:, t]) for t in range(P)], 1)
+    return feats.reshape(n, -1)
+
+
+def encode_segments(cfg, tables, p0, p1):
+    """MLP input of a segment: psi(p0) (+) psi(p1) [S, 2*P*L*F_d]."""
+    return np.concatenate([encode_points(cfg, tables, p0), encode_points(cfg, tables, p1)], 1)
+
+
+def encode_points_backward(cfg, tables, p, dfeat):
+    """Gradients of sum(dfeat * psi(p)): (dtables [L,T,F_d], dp [n,3])."""
+    tables = np.asarray(tables, np.float64)
+    res = level_res(cfg)
+    pc = np.asarray(p, np.float64)
+    inside = (pc >= 0.0) & (pc <= 1.0)
+    pcl = np.clip(pc, 0.0, 1.0)
+    g, u = gamma(cfg, pc)
+    n, P = u.shape[0], u.shape[1]
+    dfeat = np.asarray(dfeat, np.float64).reshape(n, P, cfg.levels, cfg.feats)
+    dtab = np.zeros_like(tables)
+    du = np.zeros((n, P, 3))
+    for t in range(P):
+        for l in range(cfg.levels):
+            i0, w = _cell(cfg, l, u[:, t])
+            gl = dfeat[:, t, l, :]
+            for c in _CORNERS:
+                idx = grid_index(cfg, l, i0 + c)
+                f = np.where(c == 1, w, 1.0 - w)
+                wt = np.prod(f, axis=1)
+                np.add.at(dtab[l], idx, wt[:, None] * gl)
+                val = (tables[l][idx] * gl).sum(1)
+                for a in range(3):
+                    others = np.prod(np.delete(f, a, axis=1), axis=1)
+                    sgn = 1.0 if c[a] == 1 else -1.0
+                    du[:, t, a] += sgn * others * res[l] * val
+    # chain through u(gamma(p)): x-term du/dp = 1; sin term 0.5*2^k cos(2^k p); cos term -0.5*2^k sin(2^k p)
+    dp = du[:, 0, :].copy()
+    for k in range(cfg.pe_bands):
+        f = 2.0 ** k
+        dp += du[:, 1 + 2 * k, :] * 0.5 * f * np.cos(f * pcl)
+        dp += du[:, 2 + 2 * k, :] * (-0.5) * f * np.sin(f * pcl)
+    dp = np.where(inside, dp, 0.0)
+    return dtab, dp
+
+
+# ---------------------------------------------------------------------------
+# MLP (Sec. 2, Fig. 2d): ReLU hidden layers, no bias, linear output
+# ---------------------------------------------------------------------------
+
+def mlp_forward(ws, x):
+    """Returns (out [S, O], acts) with acts[i] the input of layer i."""
+    acts = [np.asarray(x, np.float64)]
+    h = acts[0]
+    for i, w in enumerate(ws):
+        z = h @ np.asarray(w, np.float64).T
+        if i < len(ws) - 1:
+            h = np.maximum(z, 0.0)
+            acts.append(h)
+        else:
+            h = z
+    return h, acts
+
+
+def mlp_backward(ws, acts, dout):
+    """(dws, dx) for dL/dout."""
+    g = np.asarray(dout, np.float64)
+    dws = [None] * len(ws)
+    for i in range(len(ws) - 1, -1, -1):
+        w = np.asarray(ws[i], np.float64)
+        dws[i] = g.T @ acts[i]
+        g = g @ w
+        if i > 0:
+            g = g * (acts[i] > 0)
+    return dws, g
+
+
+# ---------------------------------------------------------------------------
+# Losses (Sec. 2.4)
+# ---------------------------------------------------------------------------
+
+def _sigmoid(z):
+    return 0.5 * (1.0 + np.tanh(0.5 * z))
+
+
+def _softplus(z):
+    return np.maximum(z, 0.0) + np.log1p(np.exp(-np.abs(z)))
+
+
+def loss(cfg, out, lab, s, l_rest):
+    """Uncertainty-weighted multi-task loss and its gradients.
+
+    out   [S, O] network outputs: 0 occupancy logit, 1 distance (ReLU),
+          2:5 normal, 5:8 albedo logits (sigmoid), 8:8+M material logits.
+    lab   dict of occ, tpar, normal, albedo, material (from `labels`).
+    s     [5] log-variances (distance, normal, albedo, material, occlusion).
+    l_rest [S] rest-segment lengths; the distance target is the rest hit
+          distance in voxel units, tpar * l_rest * N.
+    Returns (total, parts [5], dout [S, O], ds [5]).
+    """
+    out = np.asarray(out, np.float64)
+    s = np.asarray(s, np.float64)
+    S = out.shape[0]
+    M = cfg.n_materials
+    hit = lab["occ"].astype(bool)
+    nh = int(hit.sum())
+    dout = np.zeros_like(out)
+    parts = np.zeros(5)
+    es = np.exp(-s)
+    if nh > 0:
+        zh = out[hit]
+        # distance: ReLU head, MSE of logs
+        dh = np.maximum(zh[:, 1], 0.0)
+        y = lab["tpar"][hit] * np.asarray(l_rest)[hit] * cfg.voxel_res
+        e = np.log(dh + EPS_DIST) - np.log(y + EPS_DIST)
+        parts[0] = (e * e).sum() / nh
+        gd = 0.5 * es[0] * 2.0 * e / (dh + EPS_DIST) / nh * (zh[:, 1] > 0)
+        # normal: 1 - cosine
+        nhat = zh[:, 2:5]
+        n = lab["normal"][hit]
+        nn = np.maximum(np.linalg.norm(nhat, axis=1), 1e-8)
+        dot = (nhat * n).sum(1)
+        parts[1] = (1.0 - dot / nn).sum() / nh
+        gn = -(n / nn[:, None] - (dot / nn ** 3)[:, None] * nhat) * (0.5 * es[1] / nh)
+        # albedo: sigmoid + L1
+        ah = _sigmoid(zh[:, 5:8])
+        diff = ah - lab["albedo"][hit]
+        parts[2] = np.abs(diff).sum() / (3 * nh)
+        ga = np.sign(diff) * ah * (1 - ah) * (0.5 * es[2] / (3 * nh))
+        # material: cross entropy
+        zm = zh[:, 8:8 + M]
+        mx = zm.max(1, keepdims=True)
+        lse = mx[:, 0] + np.log(np.exp(zm - mx).sum(1))
+        m = lab["material"][hit].astype(np.int64)
+        parts[3] = (lse - zm[np.arange(nh), m]).sum() / nh
+        sm = np.exp(zm - lse[:, None])
+        sm[np.arange(nh), m] -= 1.0
+        gm = sm * (es[3] / nh)
+        g = np.zeros((nh, out.shape[1]))
+        g[:, 1] = gd
+        g[:, 2:5] = gn
+        g[:, 5:8] = ga
+        g[:, 8:8 + M] = gm
+        dout[hit] = g
+    # occlusion: BCE with logits over all segments
+    z0 = out[:, 0]
+    occ = lab["occ"].astype(np.float64)
+    parts[4] = (_softplus(z0) - occ * z0).sum() / S
+    dout[:, 0] = (_sigmoid(z0) - occ) * (es[4] / S)
+    wreg = np.array([0.5, 0.5, 0.5, 1.0, 1.0])
+    total = float((wreg * es * parts + 0.5 * s).sum())
+    ds = -wreg * es * parts + 0.5
+    return total, parts, dout, ds
+
+
+# ---------------------------------------------------------------------------
+# Adam
+# ---------------------------------------------------------------------------
+
+def adam(theta, m, v, g, step, lr, b1=0.9, b2=0.99, eps=1e-15):
+    """One Adam step (1-based step); returns new (theta, m, v)."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** step)
+    vh = v / (1 - b2 ** step)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ---------------------------------------------------------------------------
+# Reconstruction along the segmented ray (Sec. 2.2)
+# ---------------------------------------------------------------------------
+
+def reconstruct(cfg, pose, rays, seg: Segments, out, p0, p1, l_def, l_rest):
+    """Per ray: first segment k (in list order) with sigmoid(occ) > 0.5;
+    D = sum_{j<k} (delta_j + l_j) + delta_k + t_k with t_k the predicted rest
+    distance mapped to deformed length, t_k = (dist/N) * l_def/l_rest, clamped
+    to [0, l_def]. The normal is J_D^{-T} n_rest normalised, evaluated at the
+    predicted rest hit point. Returns dict hit, D, normal, albedo, material, k.
+    """
+    rays = np.asarray(rays, np.float64)
+    n = len(rays)
+    res = dict(hit=np.zeros(n, np.uint8), D=np.full(n, np.inf), normal=np.zeros((n, 3)),
+               albedo=np.zeros((n, 3)), material=np.zeros(n, np.uint8), k=np.full(n, -1))
+    for r in range(n):
+        a, b = seg.off[r], seg.off[r + 1]
+        prev = rays[r, 0:3]
+        acc = 0.0
+        for j in range(a, b):
+            x0 = rays[r, 0:3] + seg.t0[j] * rays[r, 3:6]
+            x1 = rays[r, 0:3] + seg.t1[j] * rays[r, 3:6]
+            delta = np.linalg.norm(x0 - prev)
+            if out[j, 0] > 0.0:
+                trest = max(out[j, 1], 0.0) / cfg.voxel_res
+                tk = trest * l_def[j] / l_rest[j] if l_rest[j] > 0 else 0.0
+                tk = min(max(tk, 0.0), l_def[j])
+                res["hit"][r] = 1
+                res["k"][r] = j - a
+                res["D"][r] = acc + delta + tk
+                frac = trest / l_rest[j] if l_rest[j] > 0 else 0.0
+                ph = p0[j] + frac * (p1[j] - p0[j])
+                J, _ = jacobians(pose, ph[None])
+                nd = np.linalg.solve(J[0].T, out[j, 2:5])
+                res["normal"][r] = nd / max(np.linalg.norm(nd), 1e-30)
+                res["albedo"][r] = _sigmoid(out[j, 5:8])
+                res["material"][r] = int(np.argmax(out[j, 8:8 + cfg.n_materials]))
+                break
+            acc += delta + np.linalg.norm(x1 - x0)
+            prev = x1
+    return res
