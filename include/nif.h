@@ -1,0 +1,312 @@
+/*
+ * nif.h -- C ABI of the GB300 (sm_103a) implementation of the voxel
+ * deformation-aware neural intersection function (Kao, Makowski, Fujieda,
+ * Harada, "Voxel Deformation-Aware Neural Intersection Function", 2026).
+ *
+ * The method (Sec. 2): geometry is voxelized in a rest space; a
+ * parameterized deformation moves the voxels into a deformed space where rays
+ * are traced as straight lines (Sec. 2.1). Each ray / occupied-voxel segment
+ * is mapped back to rest space by the inverse deformation and approximated by
+ * a straight rest segment (local linearization, Sec. 2); its end points are
+ * encoded by psi = phi o gamma (positional encoding followed by a
+ * multiresolution hash grid, Eq. 1) and an MLP predicts occlusion, distance,
+ * normal, albedo and material. Distances are reconstructed along the
+ * segmented ray (Sec. 2.2). Training uses task losses combined by learned
+ * uncertainty weights (Sec. 2.4).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns nif_status; no C++ exception crosses this ABI.
+ *  - "_dev" pointers are CUDA device pointers owned by the caller; "_host"
+ *    pointers are host memory owned by the caller. The library owns only the
+ *    memory behind a nif_handle (mesh copy, voxels, parameters, optimizer
+ *    state, scratch), allocated in nif_create or grown on demand by a call
+ *    that needs more scratch, and freed by nif_destroy.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *    enqueued on it; a call blocks the host only where its description says
+ *    so (it returns a count or a value to host memory).
+ *  - A handle is not thread-safe: use one handle per host thread / stream.
+ *  - Errors found on the device (segment capacity exceeded, non-finite
+ *    loss) are latched in a status word that the next synchronising call
+ *    returns; nif_last_error() gives a message for the last failure.
+ *  - All floating-point work of the library is FP32 unless stated; the
+ *    mixed-precision query path stores hash features in FP16 and runs the
+ *    MLP with BF16 or FP16 operands and FP32 accumulation on tensor cores.
+ */
+#ifndef NIF_H
+#define NIF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nif_handle nif_handle;
+
+typedef enum {
+    NIF_OK = 0,
+    NIF_ERR_ARG = -1,       /* invalid argument (null, size, unsupported config) */
+    NIF_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+    NIF_ERR_OOM = -3,       /* device allocation failed */
+    NIF_ERR_CAPACITY = -4,  /* a device-side list overflowed its capacity */
+    NIF_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+    NIF_ERR_NAN = -6,       /* non-finite loss or gradient */
+    NIF_ERR_STATE = -7      /* call not valid in the handle's state */
+} nif_status;
+
+typedef enum { NIF_FP32 = 0, NIF_BF16 = 1, NIF_FP16 = 2 } nif_precision;
+
+/* Sizes of the method. Symbols follow the paper: F frequency bands of the
+ * positional encoding, L hash-grid levels (Eq. 1). */
+typedef struct {
+    int voxel_res;          /* N: rest-space voxel grid N^3 over [0,1]^3; power of two, 2..512 */
+    int pe_bands;           /* F: gamma(x) = [x, sin(2^k x), cos(2^k x)]_{k<F} (Eq. 1); 0..8 */
+    int levels;             /* L: hash-grid levels (Eq. 1); 1..32 */
+    int feats;              /* F_d: features per level; must be 2 */
+    int log2_table;         /* T = 2^log2_table entries per level; 4..24 */
+    int base_res;           /* N_min: coarsest grid resolution */
+    float growth;           /* b: level l has N_l = floor(N_min * b^l) cells per axis */
+    int mlp_depth;          /* H hidden ReLU layers; 1..8 */
+    int mlp_width;          /* W: hidden width; 16, 32, 64 or 128 */
+    int n_materials;        /* M material classes; 1..8 */
+    int precision;          /* nif_precision of nif_query's encoding + MLP */
+    unsigned flags;         /* reserved, 0 */
+    unsigned long long seed;/* parameter initialisation and training-sample seed */
+} nif_config;
+
+/* Rest-space triangle mesh inside [0,1]^3 (host memory, copied by nif_create). */
+typedef struct {
+    const float* verts;                 /* [n_verts * 3] */
+    int n_verts;
+    const int* tris;                    /* [n_tris * 3], outward winding */
+    int n_tris;
+    const float* tri_albedo;            /* [n_tris * 3] in [0,1], or NULL (0.5) */
+    const unsigned char* tri_material;  /* [n_tris] < n_materials, or NULL (0) */
+} nif_mesh;
+
+/* Deformation parameters (our reading; the paper names no family):
+ * D(x) = c + Bend(Twist(Taper(x - c))), c = (0.5, 0.5, 0.5);
+ * Taper s = 1 + taper*z scales (x, y); Twist turns (x, y) by twist*z radians;
+ * Bend (Barr 1984) bends the x-z plane with curvature 0.75*bend. */
+typedef struct { float bend, twist, taper; } nif_pose;
+
+/* Ray in the deformed space of its instance; d of unit length. 32 bytes. */
+typedef struct { float o[3], d[3], tmin, tmax; } nif_ray;
+
+/* Query result of one ray. 32 bytes. hit = 0 means no hit, D = +inf. */
+typedef struct {
+    float D;              /* distance along the ray to the predicted hit (Sec. 2.2) */
+    float n[3];           /* deformed-space unit normal */
+    float albedo[3];
+    unsigned char hit, material, pad[2];
+} nif_hit;
+
+/* One ray / occupied deformed voxel segment (Sec. 2.2). 16 bytes.
+ * voxel = i + N*(j + N*k) of the rest voxel; [t0, t1] along the ray. */
+typedef struct { uint32_t ray, voxel; float t0, t1; } nif_segment;
+
+/* Linearized rest segment of a nif_segment (Sec. 2). 32 bytes.
+ * p0 = D^-1(o + t0 d), p1 = D^-1(o + t1 d); l_def = |x1 - x0|, l_rest = |p1 - p0|. */
+typedef struct { float p0[3], p1[3], l_def, l_rest; } nif_linseg;
+
+/* Ground-truth attributes of a linearized segment (Sec. 2). 32 bytes.
+ * tpar in [0,1] is the hit parameter along p0 -> p1; normal is the unit
+ * geometric normal of the hit triangle in rest space. */
+typedef struct {
+    float tpar, normal[3], albedo[3];
+    unsigned char occ, material, pad[2];
+} nif_label;
+
+/* Parameter groups for nif_get_params / nif_set_params (FP32, host memory). */
+enum {
+    NIF_PARAM_TABLES = 0,   /* [L][T][F_d] hash-grid tables */
+    NIF_PARAM_LOGVAR = 1,   /* [5] s_i = log sigma_i^2: distance, normal, albedo, material, occlusion */
+    NIF_PARAM_LAYER0 = 16   /* + i: weight of layer i, [out][in] row-major, i = 0..H;
+                               layer H is the output layer with 16 rows: 0 occupancy logit,
+                               1 distance, 2-4 normal, 5-7 albedo logits, 8.. material logits */
+};
+
+/* ------------------------------------------------------------------------ */
+/* Lifetime                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Validates cfg, copies the mesh to the device, voxelizes it in rest space
+ * (Sec. 2; triangle/box overlap of voxels dilated by 1e-7) and builds the
+ * fixed-topology octree over the occupied voxels used by the per-pose
+ * "simple BVH" (Sec. 2.1). Parameters are initialised from cfg->seed
+ * (tables U[-1e-4, 1e-4], Kaiming-uniform weights, s = 0). Blocks the host.
+ * On failure *out is NULL and nif_last_error(NULL) explains. */
+nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, nif_handle** out);
+
+/* Frees everything the handle owns. NULL is a no-op. Synchronises the device. */
+void nif_destroy(nif_handle* h);
+
+/* Message of the last failure on this handle (or of the calling thread's
+ * last nif_create when h is NULL). Never NULL; valid until the next call. */
+const char* nif_last_error(const nif_handle* h);
+
+/* Size in bytes of a parameter group (see the enum above). */
+nif_status nif_param_bytes(const nif_handle* h, int group, size_t* bytes);
+/* Copy a parameter group to/from host memory (FP32). Blocks the host.
+ * nif_set_params also refreshes the FP16 table copy and resets nothing else. */
+nif_status nif_get_params(nif_handle* h, int group, void* dst_host, size_t bytes);
+nif_status nif_set_params(nif_handle* h, int group, const void* src_host, size_t bytes);
+/* Reset the Adam moments and step counter of the handle. */
+nif_status nif_reset_optimizer(nif_handle* h);
+
+/* Rest-space voxelization (Sec. 2): occ_host [N^3] (x fastest) gets 1 for
+ * occupied voxels. If tri_ptr_host is not NULL it receives [N^3 + 1] offsets
+ * and tri_idx_host (capacity `cap`) the ascending triangle ids overlapping
+ * each voxel. *n_pairs_host (nullable) gets the total number of pairs.
+ * Blocks the host. */
+nif_status nif_get_voxels(nif_handle* h, unsigned char* occ_host, int64_t* tri_ptr_host,
+                          int32_t* tri_idx_host, int64_t cap, int64_t* n_pairs_host);
+
+/* ------------------------------------------------------------------------ */
+/* Stages of the hot path (device buffers, enqueued on `stream`)             */
+/* ------------------------------------------------------------------------ */
+
+/* Ray / deformed-voxel segments (Sec. 2.1, Sec. 2.2). Instance i (pose
+ * poses_host[i]) owns rays[inst_offsets[i] .. inst_offsets[i+1]);
+ * inst_offsets_dev may be NULL when n_inst == 1. For every ray, every
+ * occupied voxel whose deformed hull (the hexahedron of its 8 deformed
+ * lattice corners, each face split into two triangles along the diagonal
+ * from its lowest lattice corner) is hit at least twice gives the segment
+ * [max(t_min_hit, tmin), min(t_max_hit, tmax)] when that is non-empty;
+ * a ray's segments are sorted by (t0, voxel). Candidates come from a
+ * per-pose refit of the octree's boxes.
+ * Output: ray_offsets_dev [n_rays + 1] (exclusive scan of the per-ray
+ * counts) and segs_dev (capacity seg_cap). *n_segs_host (nullable) receives
+ * the total. Blocks the host. segs_dev == NULL only counts. Returns
+ * NIF_ERR_CAPACITY (and writes nothing past seg_cap) when the total exceeds
+ * seg_cap. */
+nif_status nif_segments(nif_handle* h, const nif_pose* poses_host, int n_inst,
+                        const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
+                        uint32_t* ray_offsets_dev, nif_segment* segs_dev, int64_t seg_cap,
+                        int64_t* n_segs_host, void* stream);
+
+/* Local linearization (Sec. 2): lin_dev[s] from segs_dev[s] for s < n_segs. */
+nif_status nif_linearize(nif_handle* h, const nif_pose* poses_host, int n_inst,
+                         const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
+                         const nif_segment* segs_dev, int64_t n_segs, nif_linseg* lin_dev,
+                         void* stream);
+
+/* Hybrid encoding psi(p) = phi(gamma(p)) of rest points (Eq. 1). p is clamped
+ * to [0,1]^3; each of the P = 1 + 2F terms of gamma goes through the same
+ * hash grid at u = term (x term) or u = (term + 1)/2 (sin, cos terms);
+ * level l uses q = fl32(u * N_l), cell i0 = min(floor(q), N_l - 1), the
+ * dense index i + j(N_l+1) + k(N_l+1)^2 when (N_l+1)^3 <= T, otherwise the
+ * hash (i * 1 ^ j * 2654435761 ^ k * 805459861) mod T, and trilinear weights.
+ * feats_dev: [n][P][L][F_d], FP32 (out_dtype NIF_FP32) or BF16/FP16.
+ * rows_dev (nullable): [n][P][L] int32 table row of each cell's (0,0,0) corner. */
+nif_status nif_encode_points(nif_handle* h, const float* pts_dev, int64_t n, void* feats_dev,
+                             int out_dtype, int32_t* rows_dev, void* stream);
+
+/* Encoding of segments: feats_dev [n][2][P][L][F_d] = psi(p0) (+) psi(p1).
+ * `table_dtype` NIF_FP32 reads the FP32 tables, NIF_FP16 the FP16 copy. */
+nif_status nif_encode_segments(nif_handle* h, const nif_linseg* lin_dev, int64_t n,
+                               void* feats_dev, int out_dtype, int table_dtype, void* stream);
+
+/* Backward of nif_encode_points: adds d(sum dfeats * psi)/d(table) into
+ * dtables_dev [L][T][F_d] (FP32 atomics) and, if dpts_dev is not NULL,
+ * writes d/dp [n][3] (zero where p was clamped). */
+nif_status nif_encode_points_backward(nif_handle* h, const float* pts_dev, int64_t n,
+                                      const float* dfeats_dev, float* dtables_dev,
+                                      float* dpts_dev, void* stream);
+
+/* MLP forward (Sec. 2, Fig. 2d): H ReLU layers without bias and a linear
+ * output layer; out_dev [n][16] FP32. x_dev [n][in_dim] of x_dtype.
+ * precision NIF_FP32 runs FP32 FFMA; NIF_BF16 / NIF_FP16 run tcgen05 tensor
+ * cores with FP32 accumulation (x_dtype must then equal precision).
+ * acts_dev (nullable, FP32 only): [H][n][W] post-ReLU hidden activations. */
+nif_status nif_mlp_forward(nif_handle* h, const void* x_dev, int x_dtype, int64_t n,
+                           float* out_dev, int precision, float* acts_dev, void* stream);
+
+/* MLP backward (FP32): given x_dev [n][in_dim], acts_dev from nif_mlp_forward
+ * and dout_dev [n][16], adds dL/dW into the handle's gradient buffer and
+ * writes dx_dev [n][in_dim] (nullable). */
+nif_status nif_mlp_backward(nif_handle* h, const float* x_dev, int64_t n, const float* acts_dev,
+                            const float* dout_dev, float* dx_dev, void* stream);
+
+/* Ground-truth labels (Sec. 2): the straight rest segment p0 -> p1 of lin[s]
+ * against the triangles overlapping voxel segs[s].voxel; first hit in
+ * [0,1], ties to the smaller triangle id. */
+nif_status nif_labels(nif_handle* h, const nif_segment* segs_dev, const nif_linseg* lin_dev,
+                      int64_t n, nif_label* labels_dev, void* stream);
+
+/* Task losses and uncertainty weighting (Sec. 2.4) for n segments:
+ * distance: ReLU head, mean over hit segments of (log(d+eps) - log(y+eps))^2
+ *   with y = tpar * l_rest * N and eps = 1e-2 (voxel units);
+ * normal: mean over hits of 1 - cos; albedo: sigmoid, mean L1 over hits and
+ * channels; material: cross-entropy over hits; occlusion: BCE with logits
+ * over all segments; total = sum_reg (0.5 e^-s L + 0.5 s) + sum_cls
+ * (e^-s L + 0.5 s). Writes dout_dev [n][16] (nullable) and adds dL/ds into
+ * the gradient buffer; parts_host (nullable, blocks) gets
+ * [total, L_dist, L_normal, L_albedo, L_material, L_occ]. */
+nif_status nif_loss(nif_handle* h, const float* out_dev, const nif_label* labels_dev,
+                    const nif_linseg* lin_dev, int64_t n, float* dout_dev, double* parts_host,
+                    void* stream);
+
+/* Gradient buffer (same layout as the parameters) and Adam (beta1 0.9,
+ * beta2 0.99, eps 1e-15; learning rate lr_grid for tables and s, lr_mlp
+ * for the weights). nif_zero_grad clears it; nif_get_grad / nif_set_grad
+ * copy a group out / in (blocking). nif_adam_step clears the gradient. */
+nif_status nif_zero_grad(nif_handle* h, void* stream);
+nif_status nif_get_grad(nif_handle* h, int group, void* dst_host, size_t bytes);
+nif_status nif_set_grad(nif_handle* h, int group, const void* src_host, size_t bytes);
+nif_status nif_adam_step(nif_handle* h, float lr_grid, float lr_mlp, void* stream);
+
+/* Per-ray reconstruction (Sec. 2.2): the first segment (in list order) with
+ * sigmoid(occupancy) > 0.5 gives D = t0 |d| + t_k, t_k = (dist / N) *
+ * l_def / l_rest clamped to [0, l_def]; the normal is J_D^-T n_rest at the
+ * predicted rest hit point; albedo = sigmoid, material = argmax.
+ * flags & NIF_SHADOW_ONLY fills only hit. */
+#define NIF_SHADOW_ONLY 1u
+nif_status nif_reconstruct(nif_handle* h, const nif_pose* poses_host, int n_inst,
+                           const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
+                           const uint32_t* ray_offsets_dev, const nif_segment* segs_dev,
+                           const nif_linseg* lin_dev, const float* out_dev, nif_hit* hits_dev,
+                           unsigned flags, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Whole paths                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Query (the inference hot path): segments -> linearization -> encoding ->
+ * MLP (cfg.precision) -> reconstruction, for n_inst deformed instances of
+ * the handle's shape. Rays and hits are device buffers of n_rays entries.
+ * Does not block the host; scratch grows on demand (growing synchronises). */
+nif_status nif_query(nif_handle* h, const nif_pose* poses_host, int n_inst,
+                     const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
+                     nif_hit* hits_dev, unsigned flags, void* stream);
+
+/* One training step (FP32) on caller-given rays: segments of the rays are
+ * generated and the first n_segments (in ray order) are labelled, encoded,
+ * passed through the MLP, the losses are back-propagated into tables,
+ * weights and s, and Adam updates them. loss_host (nullable) receives
+ * [total, L_dist, L_normal, L_albedo, L_material, L_occ] and blocks. */
+nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses_host, int n_inst,
+                               const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
+                               int64_t n_segments, float lr_grid, float lr_mlp, double* loss_host,
+                               void* stream);
+
+/* One training step with samples drawn on the device from step_seed:
+ * n_poses poses with every parameter U[-1,1] and, per pose, rays whose
+ * origins are uniform on the radius-2 sphere about the cube centre aimed at
+ * points uniform in [0,1]^3 (counter-based splitmix64 stream), enough rays
+ * for n_segments segments. poses_out_host (nullable) receives the poses. */
+nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses,
+                          unsigned long long step_seed, float lr_grid, float lr_mlp,
+                          nif_pose* poses_out_host, double* loss_host, void* stream);
+
+/* Draws the training rays of nif_train_step: rays_dev [n] for stream id
+ * `stream_id` of step_seed (uniforms are the top 24 bits of splitmix64 of
+ * (step_seed, stream_id, index)). */
+nif_status nif_sample_rays(nif_handle* h, unsigned long long step_seed, int stream_id, int n,
+                           nif_ray* rays_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NIF_H */

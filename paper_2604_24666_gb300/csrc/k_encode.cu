@@ -1,0 +1,320 @@
+// k_encode.cu -- hybrid encoding psi = phi o gamma (Eq. 1) forward and
+// backward.
+//
+// gamma(x) = [x, sin(2^k x), cos(2^k x)]_{k<F} gives P = 1 + 2F 3-vectors;
+// each goes through the same multiresolution grid phi (Sec. 2.3: "each ...
+// frequency-modulated sample is independently processed by the multi-level
+// hash grid encoder") at u = x (x term) or u = (g + 1)/2 (sin and cos terms).
+// Level l has N_l cells per axis: q = fl32(u * N_l), i0 = min(floor(q), N_l-1),
+// w = q - i0; the row of grid vertex (i,j,k) is the dense index
+// i + j(N_l+1) + k(N_l+1)^2 when (N_l+1)^3 <= T and otherwise the spatial hash
+// (i * 1 ^ j * 2654435761 ^ k * 805459861) mod T of Mueller et al. (2022).
+//
+// One thread owns one (point, term) pair: it evaluates the term's sines once
+// and loops over the L levels, issuing the 8 corner loads of a level
+// back-to-back (float2 = both features of an FP32 row, half2 of an FP16 row).
+#include "nif_internal.cuh"
+
+namespace {
+
+struct Cell {
+    int ix, iy, iz;
+    float wx, wy, wz;
+};
+
+__device__ __forceinline__ Cell cell_of(float3 u, int Nl) {
+    float fn = (float)Nl;
+    float qx = __fmul_rn(u.x, fn), qy = __fmul_rn(u.y, fn), qz = __fmul_rn(u.z, fn);
+    Cell c;
+    c.ix = min((int)floorf(qx), Nl - 1);
+    c.iy = min((int)floorf(qy), Nl - 1);
+    c.iz = min((int)floorf(qz), Nl - 1);
+    c.wx = qx - (float)c.ix;
+    c.wy = qy - (float)c.iy;
+    c.wz = qz - (float)c.iz;
+    return c;
+}
+
+__device__ __forceinline__ uint32_t grid_row(uint32_t i, uint32_t j, uint32_t k, int Nl, bool dense,
+                                             uint32_t T) {
+    if (dense) {
+        uint32_t s = (uint32_t)Nl + 1u;
+        return i + j * s + k * s * s;
+    }
+    return (i ^ (j * 2654435761u) ^ (k * 805459861u)) & (T - 1u);
+}
+
+// u of term t of gamma(p); p already clamped to [0,1]
+__device__ __forceinline__ float3 term_u(float3 p, int t) {
+    if (t == 0) return p;
+    int k = (t - 1) >> 1;
+    float f = (float)(1 << k);
+    float sx, cx, sy, cy, sz, cz;
+    sincosf(f * p.x, &sx, &cx);
+    sincosf(f * p.y, &sy, &cy);
+    sincosf(f * p.z, &sz, &cz);
+    if ((t - 1) & 1) return make_float3((cx + 1.0f) * 0.5f, (cy + 1.0f) * 0.5f, (cz + 1.0f) * 0.5f);
+    return make_float3((sx + 1.0f) * 0.5f, (sy + 1.0f) * 0.5f, (sz + 1.0f) * 0.5f);
+}
+
+// du/dp of term t (diagonal), zero where p was clamped
+__device__ __forceinline__ float3 term_dudp(float3 p, int t) {
+    if (t == 0) return make_float3(1.f, 1.f, 1.f);
+    int k = (t - 1) >> 1;
+    float f = (float)(1 << k);
+    float sx, cx, sy, cy, sz, cz;
+    sincosf(f * p.x, &sx, &cx);
+    sincosf(f * p.y, &sy, &cy);
+    sincosf(f * p.z, &sz, &cz);
+    if ((t - 1) & 1) return make_float3(-0.5f * f * sx, -0.5f * f * sy, -0.5f * f * sz);
+    return make_float3(0.5f * f * cx, 0.5f * f * cy, 0.5f * f * cz);
+}
+
+__device__ __forceinline__ float3 clamp01(float3 p) {
+    return make_float3(fminf(fmaxf(p.x, 0.f), 1.f), fminf(fmaxf(p.y, 0.f), 1.f), fminf(fmaxf(p.z, 0.f), 1.f));
+}
+
+template <typename TT>
+__device__ __forceinline__ float2 load_row(const TT* tab, uint32_t row);
+template <>
+__device__ __forceinline__ float2 load_row<float>(const float* tab, uint32_t row) {
+    return __ldg(reinterpret_cast<const float2*>(tab) + row);
+}
+template <>
+__device__ __forceinline__ float2 load_row<__half>(const __half* tab, uint32_t row) {
+    __half2 v = __ldg(reinterpret_cast<const __half2*>(tab) + row);
+    return __half22float2(v);
+}
+
+template <typename OT>
+__device__ __forceinline__ void store2(OT* out, int64_t i, float2 v);
+template <>
+__device__ __forceinline__ void store2<float>(float* out, int64_t i, float2 v) {
+    *reinterpret_cast<float2*>(out + i) = v;
+}
+template <>
+__device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* out, int64_t i, float2 v) {
+    *reinterpret_cast<__nv_bfloat162*>(out + i) = __floats2bfloat162_rn(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ void store2<__half>(__half* out, int64_t i, float2 v) {
+    *reinterpret_cast<__half2*>(out + i) = __floats2half2_rn(v.x, v.y);
+}
+
+// phi at u for all levels: writes L float2 starting at out[o]
+template <typename TT, typename OT>
+__device__ __forceinline__ void grid_all_levels(const GridInfo& g, const TT* __restrict__ tab, float3 u,
+                                                OT* __restrict__ out, int64_t o, int32_t* rows,
+                                                int64_t ro) {
+    for (int l = 0; l < g.L; l++) {
+        int Nl = g.res[l];
+        bool dense = (g.dense_mask >> l) & 1u;
+        Cell c = cell_of(u, Nl);
+        const TT* tl = tab + (int64_t)l * g.T * 2;
+        float2 acc = make_float2(0.f, 0.f);
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            v[q] = load_row<TT>(tl, grid_row(c.ix + (q & 1), c.iy + ((q >> 1) & 1), c.iz + ((q >> 2) & 1), Nl,
+                                             dense, g.T));
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) * ((q & 4) ? c.wz : 1.f - c.wz);
+            acc.x += w * v[q].x;
+            acc.y += w * v[q].y;
+        }
+        store2<OT>(out, o + 2 * l, acc);
+        if (rows) rows[ro + l] = (int32_t)grid_row(c.ix, c.iy, c.iz, Nl, dense, g.T);
+    }
+}
+
+template <typename TT, typename OT>
+__global__ void __launch_bounds__(256) k_encode_points(GridInfo g, const TT* __restrict__ tab,
+                                                       const float* __restrict__ pts, int64_t n,
+                                                       OT* __restrict__ out, int32_t* __restrict__ rows) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= n * g.P) return;
+    int64_t i = gid / g.P;
+    int t = (int)(gid - i * g.P);
+    float3 p = clamp01(make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]));
+    float3 u = term_u(p, t);
+    grid_all_levels<TT, OT>(g, tab, u, out, gid * g.L * 2, rows, gid * g.L);
+}
+
+template <typename TT, typename OT>
+__global__ void __launch_bounds__(256) k_encode_segments(GridInfo g, const TT* __restrict__ tab,
+                                                         const nif_linseg* __restrict__ lin,
+                                                         const uint32_t* __restrict__ n_dev, int64_t n_max,
+                                                         OT* __restrict__ out) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    int per = 2 * g.P;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n * per;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = gid / per;
+        int r = (int)(gid - s * per);
+        int e = r >= g.P;
+        int t = r - e * g.P;
+        const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+        float3 p = clamp01(make_float3(L[0], L[1], L[2]));
+        float3 u = term_u(p, t);
+        grid_all_levels<TT, OT>(g, tab, u, out, gid * g.L * 2, nullptr, 0);
+    }
+}
+
+// backward: scatter w * dfeat into the FP32 table gradient; optional d/dp
+__device__ __forceinline__ void grid_backward(const GridInfo& g, const float* __restrict__ tab, float3 u,
+                                              const float* __restrict__ df, float* __restrict__ dtab,
+                                              float3* du) {
+    float3 acc = make_float3(0.f, 0.f, 0.f);
+    for (int l = 0; l < g.L; l++) {
+        int Nl = g.res[l];
+        bool dense = (g.dense_mask >> l) & 1u;
+        Cell c = cell_of(u, Nl);
+        float2 gr = *reinterpret_cast<const float2*>(df + 2 * l);
+        float* dl = dtab + (int64_t)l * g.T * 2;
+        const float* tl = tab + (int64_t)l * g.T * 2;
+        float3 dl_du = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            uint32_t row = grid_row(c.ix + (q & 1), c.iy + ((q >> 1) & 1), c.iz + ((q >> 2) & 1), Nl, dense, g.T);
+            float fx = (q & 1) ? c.wx : 1.f - c.wx;
+            float fy = (q & 2) ? c.wy : 1.f - c.wy;
+            float fz = (q & 4) ? c.wz : 1.f - c.wz;
+            float w = fx * fy * fz;
+            atomicAdd(reinterpret_cast<float2*>(dl) + row, make_float2(w * gr.x, w * gr.y));
+            if (du) {
+                float2 v = __ldg(reinterpret_cast<const float2*>(tl) + row);
+                float val = v.x * gr.x + v.y * gr.y;
+                dl_du.x += ((q & 1) ? 1.f : -1.f) * fy * fz * val;
+                dl_du.y += ((q & 2) ? 1.f : -1.f) * fx * fz * val;
+                dl_du.z += ((q & 4) ? 1.f : -1.f) * fx * fy * val;
+            }
+        }
+        float fn = (float)Nl;
+        acc.x += fn * dl_du.x;
+        acc.y += fn * dl_du.y;
+        acc.z += fn * dl_du.z;
+    }
+    if (du) *du = acc;
+}
+
+__global__ void __launch_bounds__(256) k_encode_points_bwd(GridInfo g, const float* __restrict__ tab,
+                                                           const float* __restrict__ pts, int64_t n,
+                                                           const float* __restrict__ dfeats,
+                                                           float* __restrict__ dtab, float* __restrict__ dpts) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= n * g.P) return;
+    int64_t i = gid / g.P;
+    int t = (int)(gid - i * g.P);
+    float3 raw = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+    float3 p = clamp01(raw);
+    float3 u = term_u(p, t);
+    float3 du;
+    grid_backward(g, tab, u, dfeats + gid * g.L * 2, dtab, dpts ? &du : nullptr);
+    if (dpts) {
+        float3 j = term_dudp(p, t);
+        if (raw.x < 0.f || raw.x > 1.f) j.x = 0.f;
+        if (raw.y < 0.f || raw.y > 1.f) j.y = 0.f;
+        if (raw.z < 0.f || raw.z > 1.f) j.z = 0.f;
+        atomicAdd(dpts + 3 * i, du.x * j.x);
+        atomicAdd(dpts + 3 * i + 1, du.y * j.y);
+        atomicAdd(dpts + 3 * i + 2, du.z * j.z);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_encode_segments_bwd(GridInfo g, const float* __restrict__ tab,
+                                                             const nif_linseg* __restrict__ lin,
+                                                             const uint32_t* __restrict__ n_dev, int64_t n_max,
+                                                             const float* __restrict__ dfeats,
+                                                             float* __restrict__ dtab) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    int per = 2 * g.P;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n * per;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = gid / per;
+        int r = (int)(gid - s * per);
+        int e = r >= g.P;
+        int t = r - e * g.P;
+        const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+        float3 p = clamp01(make_float3(L[0], L[1], L[2]));
+        float3 u = term_u(p, t);
+        grid_backward(g, tab, u, dfeats + gid * g.L * 2, dtab, nullptr);
+    }
+}
+
+template <typename TT, typename OT>
+void launch_points(nif_handle* h, const TT* tab, const float* pts, int64_t n, void* feats, int32_t* rows,
+                   cudaStream_t s) {
+    k_encode_points<TT, OT><<<nif_blocks(n * h->P, 256), 256, 0, s>>>(h->grid, tab, pts, n, (OT*)feats, rows);
+}
+
+template <typename TT, typename OT>
+void launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
+                     void* feats, cudaStream_t s) {
+    unsigned g = nif_blocks(n_max * 2 * h->P, 256);
+    unsigned cap = (unsigned)h->num_sms * 16;
+    if (g > cap) g = cap;
+    k_encode_segments<TT, OT><<<g, 256, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
+}
+
+}  // namespace
+
+nif_status nif_encode_points_run(nif_handle* h, const float* pts, int64_t n, void* feats, int out_dtype,
+                                 int32_t* rows, cudaStream_t s) {
+    if (n <= 0) return NIF_OK;
+    const float* tab = h->d_params + h->off_tables;
+    if (out_dtype == NIF_FP32) launch_points<float, float>(h, tab, pts, n, feats, rows, s);
+    else if (out_dtype == NIF_BF16) launch_points<float, __nv_bfloat16>(h, tab, pts, n, feats, rows, s);
+    else if (out_dtype == NIF_FP16) launch_points<float, __half>(h, tab, pts, n, feats, rows, s);
+    else return nif_fail(h, NIF_ERR_ARG, "out_dtype");
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
+                                   void* feats, int out_dtype, int table_dtype, cudaStream_t s) {
+    if (n_max <= 0) return NIF_OK;
+    if (table_dtype == NIF_FP16) {
+        nif_status st = nif_refresh_lowp(h, s);
+        if (st != NIF_OK) return st;
+        const __half* tab = h->d_tables_h;
+        if (out_dtype == NIF_FP32) launch_segments<__half, float>(h, tab, lin, n_dev, n_max, feats, s);
+        else if (out_dtype == NIF_BF16) launch_segments<__half, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s);
+        else if (out_dtype == NIF_FP16) launch_segments<__half, __half>(h, tab, lin, n_dev, n_max, feats, s);
+        else return nif_fail(h, NIF_ERR_ARG, "out_dtype");
+    } else if (table_dtype == NIF_FP32) {
+        const float* tab = h->d_params + h->off_tables;
+        if (out_dtype == NIF_FP32) launch_segments<float, float>(h, tab, lin, n_dev, n_max, feats, s);
+        else if (out_dtype == NIF_BF16) launch_segments<float, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s);
+        else if (out_dtype == NIF_FP16) launch_segments<float, __half>(h, tab, lin, n_dev, n_max, feats, s);
+        else return nif_fail(h, NIF_ERR_ARG, "out_dtype");
+    } else {
+        return nif_fail(h, NIF_ERR_ARG, "table_dtype");
+    }
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n, const float* dfeats,
+                                     float* dtables, float* dpts, cudaStream_t s) {
+    if (n <= 0) return NIF_OK;
+    if (dpts) NIF_CK(h, cudaMemsetAsync(dpts, 0, sizeof(float) * 3 * n, s));
+    k_encode_points_bwd<<<nif_blocks(n * h->P, 256), 256, 0, s>>>(h->grid, h->d_params + h->off_tables, pts, n,
+                                                                 dfeats, dtables, dpts);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
+                                       const float* dfeats, float* dtables, cudaStream_t s) {
+    if (n_max <= 0) return NIF_OK;
+    unsigned g = nif_blocks(n_max * 2 * h->P, 256);
+    unsigned cap = (unsigned)h->num_sms * 16;
+    if (g > cap) g = cap;
+    k_encode_segments_bwd<<<g, 256, 0, s>>>(h->grid, h->d_params + h->off_tables, lin, n_dev, n_max, dfeats,
+                                            dtables);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}

@@ -1,0 +1,455 @@
+// k_segment.cu -- per-pose refit of the deformed-voxel octree, ray / deformed
+// voxel segment generation (Sec. 2.1, Sec. 2.2), exclusive scan, and the local
+// linearization of each segment into rest space (Sec. 2).
+//
+// Segment definition (shared with the header): every occupied voxel whose
+// deformed hull is hit at least twice gives [max(t_lo, tmin), min(t_hi, tmax)]
+// when non-empty; the hull is the hexahedron of the voxel's 8 deformed lattice
+// corners with each face split along the diagonal from its lowest lattice
+// corner. Hull hits use the watertight ray/triangle test of Woop, Benthin and
+// Wald (JCGT 2013): every edge function is evaluated once per canonical
+// (low-id, high-id) corner pair with explicitly rounded FP32 operations, so a
+// face shared by two voxels gives bit-identical decisions and hit distances in
+// both.
+//
+// The paper starts the traversal with a BVH over the deformed voxels and then
+// walks exit faces; here the per-pose BVH (an octree over the occupied voxels
+// in Morton order whose boxes are refitted per pose) enumerates every occupied
+// hull the ray can meet, which yields the same segment set by definition and
+// needs no walk through empty voxels.
+#include "nif_internal.cuh"
+
+namespace {
+
+constexpr float kBoxPad = 4e-6f;   // absolute dilation of refitted boxes
+
+// ---------------------------------------------------------------------------
+// Refit
+// ---------------------------------------------------------------------------
+__global__ void k_refit_leaves(int N, int n_leaves, int n_nodes, int n_inst,
+                               const uint32_t* __restrict__ leaf_lat,
+                               const float4* __restrict__ poses, float* __restrict__ corners,
+                               float4* __restrict__ aabb) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)n_leaves * n_inst) return;
+    int inst = (int)(gid / n_leaves);
+    int leaf = (int)(gid - (int64_t)inst * n_leaves);
+    uint32_t lat = leaf_lat[leaf];
+    int i = lat & 1023, j = (lat >> 10) & 1023, k = (lat >> 20) & 1023;
+    float4 pose = poses[inst];
+    float invN = 1.0f / (float)N;   // exact: N is a power of two
+    float* C = corners + ((int64_t)inst * n_leaves + leaf) * 24;
+    float3 lo = make_float3(1e30f, 1e30f, 1e30f), hi = make_float3(-1e30f, -1e30f, -1e30f);
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        float3 x = make_float3((float)(i + (c & 1)) * invN, (float)(j + ((c >> 1) & 1)) * invN,
+                               (float)(k + ((c >> 2) & 1)) * invN);
+        float3 y = nif_deform(x, pose);
+        C[3 * c + 0] = y.x;
+        C[3 * c + 1] = y.y;
+        C[3 * c + 2] = y.z;
+        lo = make_float3(fminf(lo.x, y.x), fminf(lo.y, y.y), fminf(lo.z, y.z));
+        hi = make_float3(fmaxf(hi.x, y.x), fmaxf(hi.y, y.y), fmaxf(hi.z, y.z));
+    }
+    float4* B = aabb + ((int64_t)inst * n_nodes + leaf) * 2;
+    B[0] = make_float4(lo.x - kBoxPad, lo.y - kBoxPad, lo.z - kBoxPad, 0.f);
+    B[1] = make_float4(hi.x + kBoxPad, hi.y + kBoxPad, hi.z + kBoxPad, 0.f);
+}
+
+__global__ void k_refit_level(int level_begin, int level_count, int n_leaves, int n_nodes,
+                              int n_inst, const int2* __restrict__ child, float4* __restrict__ aabb) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)level_count * n_inst) return;
+    int inst = (int)(gid / level_count);
+    int node = level_begin + (int)(gid - (int64_t)inst * level_count);
+    int2 ch = child[node - n_leaves];
+    float4* A = aabb + (int64_t)inst * n_nodes * 2;
+    float4 lo = make_float4(1e30f, 1e30f, 1e30f, 0.f), hi = make_float4(-1e30f, -1e30f, -1e30f, 0.f);
+    for (int c = ch.x; c < ch.x + ch.y; c++) {
+        float4 a = A[2 * c], b = A[2 * c + 1];
+        lo.x = fminf(lo.x, a.x); lo.y = fminf(lo.y, a.y); lo.z = fminf(lo.z, a.z);
+        hi.x = fmaxf(hi.x, b.x); hi.y = fmaxf(hi.y, b.y); hi.z = fmaxf(hi.z, b.z);
+    }
+    A[2 * node] = lo;
+    A[2 * node + 1] = hi;
+}
+
+// ---------------------------------------------------------------------------
+// Traversal
+// ---------------------------------------------------------------------------
+struct RayPre {
+    float ox, oy, oz, dx, dy, dz, tmin, tmax;
+    float ix, iy, iz;              // 1/d for the slab test
+    int kx, ky, kz;                // Woop's axis permutation
+    float Sx, Sy, Sz;              // shear constants
+};
+
+__device__ __forceinline__ RayPre ray_pre(const nif_ray* rays, int r) {
+    const float4* R = reinterpret_cast<const float4*>(rays + r);
+    float4 a = R[0], b = R[1];
+    RayPre p;
+    p.ox = a.x; p.oy = a.y; p.oz = a.z; p.dx = a.w; p.dy = b.x; p.dz = b.y; p.tmin = b.z; p.tmax = b.w;
+    p.ix = 1.0f / p.dx; p.iy = 1.0f / p.dy; p.iz = 1.0f / p.dz;
+    float ad[3] = {fabsf(p.dx), fabsf(p.dy), fabsf(p.dz)};
+    int kz = ad[0] > ad[1] ? (ad[0] > ad[2] ? 0 : 2) : (ad[1] > ad[2] ? 1 : 2);
+    int kx = kz + 1 == 3 ? 0 : kz + 1;
+    int ky = kx + 1 == 3 ? 0 : kx + 1;
+    float d[3] = {p.dx, p.dy, p.dz};
+    if (d[kz] < 0.0f) { int t = kx; kx = ky; ky = t; }
+    p.kx = kx; p.ky = ky; p.kz = kz;
+    p.Sx = __fdiv_rn(d[kx], d[kz]);
+    p.Sy = __fdiv_rn(d[ky], d[kz]);
+    p.Sz = __fdiv_rn(1.0f, d[kz]);
+    return p;
+}
+
+__device__ __forceinline__ bool slab(const RayPre& r, float4 lo, float4 hi) {
+    float t0x = (lo.x - r.ox) * r.ix, t1x = (hi.x - r.ox) * r.ix;
+    float t0y = (lo.y - r.oy) * r.iy, t1y = (hi.y - r.oy) * r.iy;
+    float t0z = (lo.z - r.oz) * r.iz, t1z = (hi.z - r.oz) * r.iz;
+    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), r.tmin));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), r.tmax));
+    return tn <= tf;
+}
+
+__device__ __forceinline__ float edge_fn(const float* X, const float* Y, int a, int b) {
+    // 2D cross product of the sheared corners a < b (canonical direction)
+    return __fsub_rn(__fmul_rn(X[a], Y[b]), __fmul_rn(Y[a], X[b]));
+}
+
+// One canonical triangle (A < B < C by lattice order); updates hit count and range.
+__device__ __forceinline__ void tri_hit(const float* X, const float* Y, const float* Zs, int A, int B,
+                                        int C, int& hits, float& tlo, float& thi) {
+    float U = -edge_fn(X, Y, B, C);
+    float V = edge_fn(X, Y, A, C);
+    float W = -edge_fn(X, Y, A, B);
+    bool neg = (U < 0.f) || (V < 0.f) || (W < 0.f);
+    bool pos = (U > 0.f) || (V > 0.f) || (W > 0.f);
+    if (neg && pos) return;
+    float det = __fadd_rn(__fadd_rn(U, V), W);
+    if (det == 0.f) return;
+    float T = __fadd_rn(__fadd_rn(__fmul_rn(U, Zs[A]), __fmul_rn(V, Zs[B])), __fmul_rn(W, Zs[C]));
+    float t = __fdiv_rn(T, det);
+    hits++;
+    tlo = fminf(tlo, t);
+    thi = fmaxf(thi, t);
+}
+
+// Hull of one voxel: returns true and [t0, t1] when it forms a segment.
+__device__ __forceinline__ bool hull_segment(const RayPre& r, const float* __restrict__ C, float& t0,
+                                             float& t1) {
+    float X[8], Y[8], Zs[8];
+    const float4* C4 = reinterpret_cast<const float4*>(C);
+    float c[24];
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        float4 v = __ldg(C4 + q);
+        c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+    }
+    float o[3] = {r.ox, r.oy, r.oz};
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        float A[3] = {__fsub_rn(c[3 * k], o[0]), __fsub_rn(c[3 * k + 1], o[1]), __fsub_rn(c[3 * k + 2], o[2])};
+        float ax = r.kx == 0 ? A[0] : (r.kx == 1 ? A[1] : A[2]);
+        float ay = r.ky == 0 ? A[0] : (r.ky == 1 ? A[1] : A[2]);
+        float az = r.kz == 0 ? A[0] : (r.kz == 1 ? A[1] : A[2]);
+        X[k] = __fsub_rn(ax, __fmul_rn(r.Sx, az));
+        Y[k] = __fsub_rn(ay, __fmul_rn(r.Sy, az));
+        Zs[k] = __fmul_rn(r.Sz, az);
+    }
+    int hits = 0;
+    float tlo = 3.0e38f, thi = -3.0e38f;
+    // faces {lo, s1, s2, hi}: triangles (lo, s1, hi), (lo, s2, hi)
+    tri_hit(X, Y, Zs, 0, 2, 6, hits, tlo, thi); tri_hit(X, Y, Zs, 0, 4, 6, hits, tlo, thi);  // x = 0
+    tri_hit(X, Y, Zs, 1, 3, 7, hits, tlo, thi); tri_hit(X, Y, Zs, 1, 5, 7, hits, tlo, thi);  // x = 1
+    tri_hit(X, Y, Zs, 0, 1, 5, hits, tlo, thi); tri_hit(X, Y, Zs, 0, 4, 5, hits, tlo, thi);  // y = 0
+    tri_hit(X, Y, Zs, 2, 3, 7, hits, tlo, thi); tri_hit(X, Y, Zs, 2, 6, 7, hits, tlo, thi);  // y = 1
+    tri_hit(X, Y, Zs, 0, 1, 3, hits, tlo, thi); tri_hit(X, Y, Zs, 0, 2, 3, hits, tlo, thi);  // z = 0
+    tri_hit(X, Y, Zs, 4, 5, 7, hits, tlo, thi); tri_hit(X, Y, Zs, 4, 6, 7, hits, tlo, thi);  // z = 1
+    if (hits < 2) return false;
+    t0 = fmaxf(tlo, r.tmin);
+    t1 = fminf(thi, r.tmax);
+    return t1 > t0;
+}
+
+__device__ __forceinline__ int find_inst(const int* inst_off, int n_inst, int r) {
+    if (!inst_off || n_inst <= 1) return 0;
+    int lo = 0, hi = n_inst - 1;     // largest i with inst_off[i] <= r
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(inst_off + mid) <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int kStack = 96;
+
+template <bool EMIT>
+__global__ void __launch_bounds__(128) k_seg_traverse(
+    const nif_ray* __restrict__ rays, const int* __restrict__ inst_off, int n_inst, int n_rays,
+    TreeView tree, const float* __restrict__ corners, const float4* __restrict__ aabb,
+    uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets, nif_segment* __restrict__ segs,
+    int64_t cap, int* status) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    int inst = find_inst(inst_off, n_inst, r);
+    RayPre ray = ray_pre(rays, r);
+    const float4* A = aabb + (int64_t)inst * tree.n_nodes * 2;
+    const float* Cbase = corners + (int64_t)inst * tree.n_leaves * 24;
+    int64_t base = EMIT ? (int64_t)offsets[r] : 0;
+    int64_t end = EMIT ? (int64_t)offsets[r + 1] : 0;
+    uint32_t n = 0;
+    int stack[kStack];
+    int sp = 0;
+    for (int q = tree.top_begin + tree.top_count - 1; q >= tree.top_begin; q--) stack[sp++] = q;
+    while (sp > 0) {
+        int node = stack[--sp];
+        if (node < tree.n_leaves) {
+            if (!slab(ray, __ldg(A + 2 * node), __ldg(A + 2 * node + 1))) continue;
+            float t0, t1;
+            if (hull_segment(ray, Cbase + (int64_t)node * 24, t0, t1)) {
+                if (EMIT) {
+                    int64_t pos = base + n;
+                    if (pos < end && pos < cap) {
+                        nif_segment sg;
+                        sg.ray = (uint32_t)r;
+                        sg.voxel = __ldg(tree.leaf_vox + node);
+                        sg.t0 = t0;
+                        sg.t1 = t1;
+                        segs[pos] = sg;
+                    }
+                }
+                n++;
+            }
+            continue;
+        }
+        if (!slab(ray, __ldg(A + 2 * node), __ldg(A + 2 * node + 1))) continue;
+        int2 ch = __ldg(tree.child + (node - tree.n_leaves));
+        if (sp + ch.y > kStack) { nif_set_status(status, NIF_ERR_CAPACITY); break; }
+        for (int c = ch.x + ch.y - 1; c >= ch.x; c--) stack[sp++] = c;
+    }
+    if (!EMIT) {
+        counts[r] = n;
+        return;
+    }
+    // sort this ray's segments by (t0, voxel): short, nearly sorted runs
+    int64_t m = end - base;
+    if (base + m > cap) m = cap - base;
+    for (int64_t a = 1; a < m; a++) {
+        nif_segment key = segs[base + a];
+        int64_t b = a - 1;
+        while (b >= 0) {
+            nif_segment o = segs[base + b];
+            bool gt = o.t0 > key.t0 || (o.t0 == key.t0 && o.voxel > key.voxel);
+            if (!gt) break;
+            segs[base + b + 1] = o;
+            b--;
+        }
+        segs[base + b + 1] = key;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of uint32 (three passes, 1024 elements per block)
+// ---------------------------------------------------------------------------
+constexpr int kScanT = 256, kScanE = 4, kScanB = kScanT * kScanE;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sh, uint32_t& total) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;
+    }
+    __syncthreads();
+    uint32_t warp_pre = wid > 0 ? sh[wid - 1] : 0u;
+    total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_pre + x - v;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_blocks(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                        uint32_t* __restrict__ bsum, int n) {
+    __shared__ uint32_t sh[32];
+    int64_t base = (int64_t)blockIdx.x * kScanB + threadIdx.x * kScanE;
+    uint32_t v[kScanE], s = 0;
+#pragma unroll
+    for (int e = 0; e < kScanE; e++) {
+        v[e] = base + e < n ? in[base + e] : 0u;
+        s += v[e];
+    }
+    uint32_t total;
+    uint32_t pre = block_excl_scan(s, sh, total);
+#pragma unroll
+    for (int e = 0; e < kScanE; e++) {
+        if (base + e < n) out[base + e] = pre;
+        pre += v[e];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_bsum(uint32_t* bsum, int nb, uint32_t* out_total) {
+    __shared__ uint32_t sh[32];
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        int i = b0 + threadIdx.x;
+        uint32_t v = i < nb ? bsum[i] : 0u;
+        uint32_t total;
+        uint32_t pre = block_excl_scan(v, sh, total);
+        if (i < nb) bsum[i] = carry + pre;
+        carry += total;
+    }
+    if (threadIdx.x == 0) *out_total = carry;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_add(uint32_t* __restrict__ out, const uint32_t* __restrict__ bsum,
+                                                     int n) {
+    int64_t base = (int64_t)blockIdx.x * kScanB + threadIdx.x * kScanE;
+    uint32_t add = bsum[blockIdx.x];
+#pragma unroll
+    for (int e = 0; e < kScanE; e++)
+        if (base + e < n) out[base + e] += add;
+}
+
+__global__ void k_clamp_count(const uint32_t* offsets, int n_rays, int64_t cap, uint32_t* n_out,
+                              int* status) {
+    uint32_t tot = offsets[n_rays];
+    if ((int64_t)tot > cap) {
+        nif_set_status(status, NIF_ERR_CAPACITY);
+        tot = (uint32_t)cap;
+    }
+    *n_out = tot;
+}
+
+// ---------------------------------------------------------------------------
+// Linearization
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_linearize(const nif_ray* __restrict__ rays, const int* __restrict__ inst_off,
+                                                   int n_inst, const float4* __restrict__ poses,
+                                                   const nif_segment* __restrict__ segs,
+                                                   const uint32_t* __restrict__ n_dev, int64_t n_max,
+                                                   nif_linseg* __restrict__ lin) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        nif_segment sg = segs[s];
+        const float4* R = reinterpret_cast<const float4*>(rays + sg.ray);
+        float4 a = R[0], b = R[1];
+        int inst = find_inst(inst_off, n_inst, (int)sg.ray);
+        float4 pose = poses[inst];
+        float3 x0 = make_float3(a.x + sg.t0 * a.w, a.y + sg.t0 * b.x, a.z + sg.t0 * b.y);
+        float3 x1 = make_float3(a.x + sg.t1 * a.w, a.y + sg.t1 * b.x, a.z + sg.t1 * b.y);
+        float3 p0 = nif_inverse(x0, pose);
+        float3 p1 = nif_inverse(x1, pose);
+        float dn = sqrtf(a.w * a.w + b.x * b.x + b.y * b.y);
+        float dx = p1.x - p0.x, dy = p1.y - p0.y, dz = p1.z - p0.z;
+        float4* L4 = reinterpret_cast<float4*>(lin + s);
+        L4[0] = make_float4(p0.x, p0.y, p0.z, p1.x);
+        L4[1] = make_float4(p1.y, p1.z, (sg.t1 - sg.t0) * dn, sqrtf(dx * dx + dy * dy + dz * dz));
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+nif_status nif_refit_run(nif_handle* h, int n_inst, cudaStream_t s) {
+    if (h->n_leaves == 0) return NIF_OK;
+    int64_t nl = (int64_t)h->n_leaves * n_inst;
+    k_refit_leaves<<<nif_blocks(nl, 128), 128, 0, s>>>(h->N, h->n_leaves, h->n_nodes, n_inst, h->d_leaf_lat,
+                                                      h->d_pose, h->d_corners, h->d_aabb);
+    NIF_CK_LAUNCH(h);
+    for (size_t l = 0; l < h->level_begin.size(); l++) {
+        int64_t nn = (int64_t)h->level_count[l] * n_inst;
+        k_refit_level<<<nif_blocks(nn, 128), 128, 0, s>>>(h->level_begin[l], h->level_count[l], h->n_leaves,
+                                                         h->n_nodes, n_inst, h->d_child, h->d_aabb);
+        NIF_CK_LAUNCH(h);
+    }
+    return NIF_OK;
+}
+
+static TreeView tree_view(nif_handle* h) {
+    TreeView t;
+    t.n_leaves = h->n_leaves;
+    t.n_nodes = h->n_nodes;
+    t.top_begin = h->top_begin;
+    t.top_count = h->top_count;
+    t.child = h->d_child;
+    t.leaf_vox = h->d_leaf_vox;
+    return t;
+}
+
+nif_status nif_seg_count_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                             uint32_t* counts, cudaStream_t s) {
+    if (n_rays <= 0) return NIF_OK;
+    if (h->n_leaves == 0) {
+        NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n_rays, s));
+        return NIF_OK;
+    }
+    k_seg_traverse<false><<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, tree_view(h),
+                                                                  h->d_corners, h->d_aabb, counts, nullptr,
+                                                                  nullptr, 0, h->d_status);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_seg_emit_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                            const uint32_t* offsets, nif_segment* segs, int64_t cap, cudaStream_t s) {
+    if (n_rays <= 0 || h->n_leaves == 0) return NIF_OK;
+    k_seg_traverse<true><<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, tree_view(h),
+                                                                 h->d_corners, h->d_aabb, nullptr, offsets, segs,
+                                                                 cap, h->d_status);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_scan_run(nif_handle* h, const uint32_t* in, uint32_t* out, int n, cudaStream_t s) {
+    int nb = (int)nif_blocks(n, kScanB);
+    nif_status st = nif_grow(h, h->b_scan, sizeof(uint32_t) * (size_t)(nb + 1));
+    if (st != NIF_OK) return st;
+    uint32_t* bsum = (uint32_t*)h->b_scan.p;
+    if (n > 0) {
+        k_scan_blocks<<<nb, kScanT, 0, s>>>(in, out, bsum, n);
+        NIF_CK_LAUNCH(h);
+    }
+    k_scan_bsum<<<1, 1024, 0, s>>>(bsum, n > 0 ? nb : 0, out + n);
+    NIF_CK_LAUNCH(h);
+    if (n > 0) {
+        k_scan_add<<<nb, kScanT, 0, s>>>(out, bsum, n);
+        NIF_CK_LAUNCH(h);
+    }
+    return NIF_OK;
+}
+
+nif_status nif_clamp_count_run(nif_handle* h, const uint32_t* offsets, int n_rays, int64_t cap, uint32_t* n_out,
+                               cudaStream_t s) {
+    k_clamp_count<<<1, 1, 0, s>>>(offsets, n_rays, cap, n_out, h->d_status);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_linearize_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
+                             const nif_segment* segs, const uint32_t* n_dev, int64_t n_max, nif_linseg* lin,
+                             cudaStream_t s) {
+    if (n_max <= 0) return NIF_OK;
+    unsigned g = nif_blocks(n_max, 256);
+    unsigned cap = (unsigned)h->num_sms * 8;
+    if (g > cap) g = cap;
+    k_linearize<<<g, 256, 0, s>>>(rays, inst_off, n_inst, h->d_pose, segs, n_dev, n_max, lin);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}

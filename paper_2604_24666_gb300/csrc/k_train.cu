@@ -1,0 +1,403 @@
+// k_train.cu -- ground-truth labels of linearized segments (Sec. 2), task
+// losses with uncertainty weighting (Sec. 2.4), Adam, the segmented-ray
+// reconstruction (Sec. 2.2) and the counter-based sampler of training rays.
+#include "nif_internal.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Labels: straight rest segment p0 -> p1 against the voxel's triangles
+// (Moeller-Trumbore, FP32); first hit in [0,1], ties to the smaller id.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_labels(const nif_segment* __restrict__ segs,
+                                                const nif_linseg* __restrict__ lin,
+                                                const uint32_t* __restrict__ n_dev, int64_t n_max,
+                                                const uint32_t* __restrict__ tri_ptr,
+                                                const int32_t* __restrict__ tri_idx,
+                                                const float* __restrict__ verts, const int* __restrict__ tris,
+                                                const float* __restrict__ alb, const uint8_t* __restrict__ mat,
+                                                nif_label* __restrict__ out, int* __restrict__ n_hit,
+                                                uint32_t nvox) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    int local_hits = 0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const float* L = reinterpret_cast<const float*>(lin + s);
+        float ox = L[0], oy = L[1], oz = L[2];
+        float dx = L[3] - ox, dy = L[4] - oy, dz = L[5] - oz;
+        uint32_t v = segs[s].voxel;
+        uint32_t a = 0, b = 0;
+        if (v < nvox) { a = tri_ptr[v]; b = tri_ptr[v + 1]; }    // foreign voxel ids label as empty
+        float best = 2.0f;
+        int bt = -1;
+        for (uint32_t q = a; q < b; q++) {
+            int t = tri_idx[q];
+            int i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
+            float Ax = verts[3 * i0], Ay = verts[3 * i0 + 1], Az = verts[3 * i0 + 2];
+            float e1x = verts[3 * i1] - Ax, e1y = verts[3 * i1 + 1] - Ay, e1z = verts[3 * i1 + 2] - Az;
+            float e2x = verts[3 * i2] - Ax, e2y = verts[3 * i2 + 1] - Ay, e2z = verts[3 * i2 + 2] - Az;
+            float px = dy * e2z - dz * e2y, py = dz * e2x - dx * e2z, pz = dx * e2y - dy * e2x;
+            float det = e1x * px + e1y * py + e1z * pz;
+            if (det == 0.f) continue;
+            float inv = 1.0f / det;
+            float sx = ox - Ax, sy = oy - Ay, sz = oz - Az;
+            float u = (sx * px + sy * py + sz * pz) * inv;
+            if (u < 0.f || u > 1.f) continue;
+            float qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
+            float w = (dx * qx + dy * qy + dz * qz) * inv;
+            if (w < 0.f || u + w > 1.f) continue;
+            float tt = (e2x * qx + e2y * qy + e2z * qz) * inv;
+            if (tt < 0.f || tt > 1.f) continue;
+            if (tt < best) { best = tt; bt = t; }
+        }
+        nif_label lab;
+        if (bt < 0) {
+            lab.tpar = 0.f;
+            lab.normal[0] = lab.normal[1] = lab.normal[2] = 0.f;
+            lab.albedo[0] = lab.albedo[1] = lab.albedo[2] = 0.f;
+            lab.occ = 0;
+            lab.material = 0;
+        } else {
+            int i0 = tris[3 * bt], i1 = tris[3 * bt + 1], i2 = tris[3 * bt + 2];
+            float e1x = verts[3 * i1] - verts[3 * i0], e1y = verts[3 * i1 + 1] - verts[3 * i0 + 1],
+                  e1z = verts[3 * i1 + 2] - verts[3 * i0 + 2];
+            float e2x = verts[3 * i2] - verts[3 * i0], e2y = verts[3 * i2 + 1] - verts[3 * i0 + 1],
+                  e2z = verts[3 * i2 + 2] - verts[3 * i0 + 2];
+            float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+            float il = rsqrtf(nx * nx + ny * ny + nz * nz);
+            lab.tpar = best;
+            lab.normal[0] = nx * il; lab.normal[1] = ny * il; lab.normal[2] = nz * il;
+            lab.albedo[0] = alb[3 * bt]; lab.albedo[1] = alb[3 * bt + 1]; lab.albedo[2] = alb[3 * bt + 2];
+            lab.occ = 1;
+            lab.material = mat[bt];
+            local_hits++;
+        }
+        lab.pad[0] = lab.pad[1] = 0;
+        out[s] = lab;
+    }
+    if (n_hit) {
+        for (int o = 16; o > 0; o >>= 1) local_hits += __shfl_down_sync(0xffffffffu, local_hits, o);
+        if ((threadIdx.x & 31) == 0 && local_hits) atomicAdd(n_hit, local_hits);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Loss (Sec. 2.4). acc[0..4] += sums of the five task losses.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+__device__ __forceinline__ float softplusf_(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
+
+__global__ void __launch_bounds__(256) k_loss(const float* __restrict__ out, const nif_label* __restrict__ labels,
+                                              const nif_linseg* __restrict__ lin, const uint32_t* __restrict__ n_dev,
+                                              int64_t n_max, const int* __restrict__ n_hit,
+                                              const float* __restrict__ s_par, int N, int M,
+                                              float* __restrict__ dout, double* __restrict__ acc) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    int nh = *n_hit;
+    float inv_h = nh > 0 ? 1.0f / (float)nh : 0.f;
+    float inv_n = n > 0 ? 1.0f / (float)n : 0.f;
+    float es[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) es[i] = expf(-s_par[i]);
+    float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const float* z = out + s * NIF_OUT;
+        nif_label lab = labels[s];
+        int mcls = lab.material < M ? lab.material : M - 1;
+        float g[NIF_OUT];
+#pragma unroll
+        for (int i = 0; i < NIF_OUT; i++) g[i] = 0.f;
+        // occlusion: BCE with logits over all segments
+        float occ = lab.occ ? 1.f : 0.f;
+        part[4] += softplusf_(z[0]) - occ * z[0];
+        g[0] = (sigmoidf_(z[0]) - occ) * es[4] * inv_n;
+        if (lab.occ) {
+            // distance: ReLU head, MSE of logs, target in voxel units
+            float dh = fmaxf(z[1], 0.f);
+            float y = lab.tpar * lin[s].l_rest * (float)N;
+            float e = logf(dh + NIF_EPS_DIST) - logf(y + NIF_EPS_DIST);
+            part[0] += e * e;
+            g[1] = z[1] > 0.f ? 0.5f * es[0] * 2.0f * e / (dh + NIF_EPS_DIST) * inv_h : 0.f;
+            // normal: 1 - cos
+            float nx = z[2], ny = z[3], nz = z[4];
+            float nn = fmaxf(sqrtf(nx * nx + ny * ny + nz * nz), 1e-8f);
+            float dot = nx * lab.normal[0] + ny * lab.normal[1] + nz * lab.normal[2];
+            part[1] += 1.0f - dot / nn;
+            float c1 = -0.5f * es[1] * inv_h / nn, c2 = 0.5f * es[1] * inv_h * dot / (nn * nn * nn);
+            g[2] = c1 * lab.normal[0] + c2 * nx;
+            g[3] = c1 * lab.normal[1] + c2 * ny;
+            g[4] = c1 * lab.normal[2] + c2 * nz;
+            // albedo: sigmoid + L1
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                float a = sigmoidf_(z[5 + c]);
+                float d = a - lab.albedo[c];
+                part[2] += fabsf(d) * (1.0f / 3.0f);
+                float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+                g[5 + c] = sg * a * (1.f - a) * 0.5f * es[2] * inv_h * (1.0f / 3.0f);
+            }
+            // material: cross entropy
+            float mx = -3.0e38f;
+            for (int c = 0; c < M; c++) mx = fmaxf(mx, z[8 + c]);
+            float se = 0.f;
+            for (int c = 0; c < M; c++) se += expf(z[8 + c] - mx);
+            float lse = mx + logf(se);
+            part[3] += lse - z[8 + mcls];
+            for (int c = 0; c < M; c++) {
+                float p = expf(z[8 + c] - lse);
+                g[8 + c] = (p - (c == mcls ? 1.f : 0.f)) * es[3] * inv_h;
+            }
+        }
+        if (dout) {
+            float4* D4 = reinterpret_cast<float4*>(dout + s * NIF_OUT);
+#pragma unroll
+            for (int q = 0; q < NIF_OUT / 4; q++) D4[q] = make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+        }
+    }
+    __shared__ float sh[8][5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        float v = part[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w][threadIdx.x];
+        atomicAdd(acc + threadIdx.x, t);
+    }
+}
+
+// parts -> total and dL/ds (added into the gradient buffer)
+__global__ void k_loss_final(double* acc, const uint32_t* __restrict__ n_dev, int64_t n_max,
+                             const int* __restrict__ n_hit, const float* __restrict__ s_par,
+                             float* __restrict__ ds, int* status) {
+    if (threadIdx.x != 0) return;
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    int nh = *n_hit;
+    double L[5];
+    for (int i = 0; i < 4; i++) L[i] = nh > 0 ? acc[i] / nh : 0.0;
+    L[4] = n > 0 ? acc[4] / n : 0.0;
+    const double wreg[5] = {0.5, 0.5, 0.5, 1.0, 1.0};
+    double total = 0;
+    for (int i = 0; i < 5; i++) {
+        double es = exp(-(double)s_par[i]);
+        total += wreg[i] * es * L[i] + 0.5 * s_par[i];
+        if (ds) ds[i] += (float)(-wreg[i] * es * L[i] + 0.5);
+    }
+    acc[8] = total;
+    for (int i = 0; i < 5; i++) acc[9 + i] = L[i];
+    if (!isfinite(total)) nif_set_status(status, NIF_ERR_NAN);
+}
+
+// ---------------------------------------------------------------------------
+// Adam over the whole parameter buffer; zeroes the gradient afterwards.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
+                                              float* __restrict__ v, size_t n, size_t mlp_begin, size_t mlp_end,
+                                              float lr_grid, float lr_mlp, float c1, float c2) {
+    const float b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.f - b1) * gi;
+        float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        float lr = (i >= mlp_begin && i < mlp_end) ? lr_mlp : lr_grid;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        g[i] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction along the segmented ray (Sec. 2.2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_inst_r(const int* inst_off, int n_inst, int r) {
+    if (!inst_off || n_inst <= 1) return 0;
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(inst_off + mid) <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(128) k_reconstruct(const nif_ray* __restrict__ rays, const int* __restrict__ inst_off,
+                                                     int n_inst, int n_rays, const float4* __restrict__ poses,
+                                                     const uint32_t* __restrict__ offsets,
+                                                     const nif_segment* __restrict__ segs,
+                                                     const nif_linseg* __restrict__ lin,
+                                                     const float* __restrict__ out, int64_t seg_cap, int N, int M,
+                                                     nif_hit* __restrict__ hits, unsigned flags) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    int64_t a = offsets[r], b = offsets[r + 1];
+    if (b > seg_cap) b = seg_cap;
+    nif_hit hit;
+    hit.D = __int_as_float(0x7f800000);
+    hit.n[0] = hit.n[1] = hit.n[2] = 0.f;
+    hit.albedo[0] = hit.albedo[1] = hit.albedo[2] = 0.f;
+    hit.hit = 0;
+    hit.material = 0;
+    hit.pad[0] = hit.pad[1] = 0;
+    for (int64_t s = a; s < b; s++) {
+        const float* z = out + s * NIF_OUT;
+        if (!(z[0] > 0.f)) continue;       // sigmoid(occupancy) > 0.5
+        hit.hit = 1;
+        if (flags & NIF_SHADOW_ONLY) break;
+        const float4* R = reinterpret_cast<const float4*>(rays + r);
+        float4 r0 = R[0], r1 = R[1];
+        float dn = sqrtf(r0.w * r0.w + r1.x * r1.x + r1.y * r1.y);
+        nif_linseg L = lin[s];
+        float trest = fmaxf(z[1], 0.f) / (float)N;
+        float tk = L.l_rest > 0.f ? trest * L.l_def / L.l_rest : 0.f;
+        tk = fminf(fmaxf(tk, 0.f), L.l_def);
+        // collinear entry/exit points: sum_{j<k} (delta_j + l_j) + delta_k = t0(k) |d|
+        hit.D = segs[s].t0 * dn + tk;
+        float frac = L.l_rest > 0.f ? trest / L.l_rest : 0.f;
+        float3 ph = make_float3(L.p0[0] + frac * (L.p1[0] - L.p0[0]), L.p0[1] + frac * (L.p1[1] - L.p0[1]),
+                                L.p0[2] + frac * (L.p1[2] - L.p0[2]));
+        int inst = find_inst_r(inst_off, n_inst, r);
+        float3 j0, j1, j2;
+        nif_jacobian_cols(ph, poses[inst], j0, j1, j2);
+        // J^-T n is proportional to n.x (j1 x j2) + n.y (j2 x j0) + n.z (j0 x j1), det J > 0
+        float3 c0 = nif_cross(j1, j2), c1 = nif_cross(j2, j0), c2 = nif_cross(j0, j1);
+        float nx = z[2] * c0.x + z[3] * c1.x + z[4] * c2.x;
+        float ny = z[2] * c0.y + z[3] * c1.y + z[4] * c2.y;
+        float nz = z[2] * c0.z + z[3] * c1.z + z[4] * c2.z;
+        float nl = sqrtf(nx * nx + ny * ny + nz * nz);
+        float il = nl > 1e-30f ? 1.0f / nl : 0.f;
+        hit.n[0] = nx * il; hit.n[1] = ny * il; hit.n[2] = nz * il;
+#pragma unroll
+        for (int c = 0; c < 3; c++) hit.albedo[c] = sigmoidf_(z[5 + c]);
+        int best = 0;
+        for (int c = 1; c < M; c++)
+            if (z[8 + c] > z[8 + best]) best = c;
+        hit.material = (unsigned char)best;
+        break;
+    }
+    hits[r] = hit;
+}
+
+// ---------------------------------------------------------------------------
+// Sampler: splitmix64 stream outputs as uniforms (top 24 bits)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ float uni(uint64_t seed, uint64_t counter) {
+    uint64_t z = mix64(seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull);
+    return (float)(z >> 40) * (1.0f / 16777216.0f);
+}
+
+__global__ void k_sample_rays(uint64_t seed, int stream_id, int n, nif_ray* __restrict__ rays) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t base = (((uint64_t)(uint32_t)stream_id << 32) + (uint64_t)i) * 8ull;
+    float u0 = uni(seed, base), u1 = uni(seed, base + 1), u2 = uni(seed, base + 2), u3 = uni(seed, base + 3),
+          u4 = uni(seed, base + 4);
+    float z = 2.0f * u0 - 1.0f;
+    float a = 6.2831853071795865f * u1;
+    float s = sqrtf(fmaxf(0.f, 1.0f - z * z));
+    float sa, ca;
+    sincosf(a, &sa, &ca);
+    float ox = 0.5f + 2.0f * s * ca, oy = 0.5f + 2.0f * s * sa, oz = 0.5f + 2.0f * z;
+    float dx = u2 - ox, dy = u3 - oy, dz = u4 - oz;
+    float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+    nif_ray r;
+    r.o[0] = ox; r.o[1] = oy; r.o[2] = oz;
+    r.d[0] = dx * il; r.d[1] = dy * il; r.d[2] = dz * il;
+    r.tmin = 0.f;
+    r.tmax = 1e30f;
+    rays[i] = r;
+}
+
+__global__ void k_count_hits(const nif_label* __restrict__ labels, int64_t n, int* __restrict__ n_hit) {
+    int c = 0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        c += labels[s].occ ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(n_hit, c);
+}
+
+}  // namespace
+
+nif_status nif_labels_count_hits(nif_handle* h, const nif_label* labels, int64_t n, cudaStream_t s) {
+    NIF_CK(h, cudaMemsetAsync(h->d_count, 0, sizeof(int), s));
+    if (n > 0) {
+        unsigned g = nif_blocks(n, 256);
+        unsigned cap = (unsigned)h->num_sms * 4;
+        if (g > cap) g = cap;
+        k_count_hits<<<g, 256, 0, s>>>(labels, n, h->d_count);
+        NIF_CK_LAUNCH(h);
+    }
+    return NIF_OK;
+}
+
+nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const uint32_t* n_dev,
+                          int64_t n_max, nif_label* labels, cudaStream_t s) {
+    if (n_max <= 0) return NIF_OK;
+    NIF_CK(h, cudaMemsetAsync(h->d_count, 0, sizeof(int), s));
+    unsigned g = nif_blocks(n_max, 256);
+    unsigned cap = (unsigned)h->num_sms * 8;
+    if (g > cap) g = cap;
+    k_labels<<<g, 256, 0, s>>>(segs, lin, n_dev, n_max, h->d_tri_ptr, h->d_tri_idx, h->d_verts, h->d_tris, h->d_alb,
+                               h->d_mat, labels, h->d_count, (uint32_t)((int64_t)h->N * h->N * h->N));
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels, const nif_linseg* lin,
+                        const uint32_t* n_dev, int64_t n_max, float* dout, cudaStream_t s) {
+    NIF_CK(h, cudaMemsetAsync(h->d_lossacc, 0, sizeof(double) * 16, s));
+    if (n_max > 0) {
+        unsigned g = nif_blocks(n_max, 256);
+        unsigned cap = (unsigned)h->num_sms * 8;
+        if (g > cap) g = cap;
+        k_loss<<<g, 256, 0, s>>>(out, labels, lin, n_dev, n_max, h->d_count, h->d_params + h->off_s, h->N,
+                                 h->cfg.n_materials, dout, h->d_lossacc);
+        NIF_CK_LAUNCH(h);
+    }
+    k_loss_final<<<1, 32, 0, s>>>(h->d_lossacc, n_dev, n_max, h->d_count, h->d_params + h->off_s,
+                                  h->d_grad + h->off_s, h->d_status);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s) {
+    h->adam_step++;
+    double c1 = 1.0 / (1.0 - pow(0.9, (double)h->adam_step));
+    double c2 = 1.0 / (1.0 - pow(0.99, (double)h->adam_step));
+    unsigned g = nif_blocks((int64_t)h->n_params, 256);
+    unsigned cap = (unsigned)h->num_sms * 16;
+    if (g > cap) g = cap;
+    k_adam<<<g, 256, 0, s>>>(h->d_params, h->d_grad, h->d_m, h->d_v, h->n_params, h->off_layer[0], h->off_s,
+                             lr_grid, lr_mlp, (float)c1, (float)c2);
+    NIF_CK_LAUNCH(h);
+    h->lowp_dirty = true;
+    return NIF_OK;
+}
+
+nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                               const uint32_t* offsets, const nif_segment* segs, int64_t seg_cap,
+                               const nif_linseg* lin, const float* out, nif_hit* hits, unsigned flags,
+                               cudaStream_t s) {
+    if (n_rays <= 0) return NIF_OK;
+    k_reconstruct<<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, h->d_pose, offsets, segs,
+                                                          lin, out, seg_cap, h->N, h->cfg.n_materials, hits, flags);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_sample_rays_run(nif_handle* h, unsigned long long seed, int stream_id, int n, nif_ray* rays,
+                               cudaStream_t s) {
+    if (n <= 0) return NIF_OK;
+    k_sample_rays<<<nif_blocks(n, 256), 256, 0, s>>>(seed, stream_id, n, rays);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}

@@ -1,0 +1,766 @@
+// nif_api.cu -- host side of the C ABI declared in include/nif.h: handle
+// lifetime, parameter I/O, the octree topology, and the orchestration of the
+// query and training paths over the kernels of the k_*.cu files.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nif_internal.cuh"
+
+static thread_local std::string g_create_err;
+
+nif_status nif_fail(nif_handle* h, nif_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_err = msg;
+    return st;
+}
+
+nif_status nif_cuda_fail(nif_handle* h, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return nif_fail(h, e == cudaErrorMemoryAllocation ? NIF_ERR_OOM : NIF_ERR_CUDA, m);
+}
+
+nif_status nif_grow(nif_handle* h, nif_handle::Buf& b, size_t bytes) {
+    if (bytes <= b.bytes) return NIF_OK;
+    if (b.p) {
+        NIF_CK(h, cudaDeviceSynchronize());
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return nif_cuda_fail(h, e, "cudaMalloc(scratch)");
+    }
+    b.bytes = want;
+    return NIF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels of the host orchestration
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_to_lowp(const float* __restrict__ src, size_t n, __half* __restrict__ h16,
+                          __nv_bfloat16* __restrict__ b16) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float v = src[i];
+        if (h16) h16[i] = __float2half_rn(v);
+        if (b16) b16[i] = __float2bfloat16_rn(v);
+    }
+}
+
+uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// splitmix64 stream output `counter` of `seed` as a uniform in [0,1) (24 bits)
+float host_uniform(uint64_t seed, uint64_t counter) {
+    uint64_t z = mix64(seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull);
+    return (float)(z >> 40) * (1.0f / 16777216.0f);
+}
+
+uint32_t morton3(uint32_t i, uint32_t j, uint32_t k) {
+    auto spread = [](uint32_t x) {
+        x &= 0x3ff;
+        x = (x | (x << 16)) & 0x030000FF;
+        x = (x | (x << 8)) & 0x0300F00F;
+        x = (x | (x << 4)) & 0x030C30C3;
+        x = (x | (x << 2)) & 0x09249249;
+        return x;
+    };
+    return spread(i) | (spread(j) << 1) | (spread(k) << 2);
+}
+
+}  // namespace
+
+nif_status nif_refresh_lowp(nif_handle* h, cudaStream_t s) {
+    if (!h->lowp_dirty) return NIF_OK;
+    size_t nt = (size_t)h->L * h->T * h->Fd;
+    k_to_lowp<<<std::max(1, std::min(h->num_sms * 8, (int)((nt + 255) / 256))), 256, 0, s>>>(
+        h->d_params + h->off_tables, nt, h->d_tables_h, nullptr);
+    NIF_CK_LAUNCH(h);
+    size_t nw = h->off_s - h->off_layer[0];
+    k_to_lowp<<<std::max(1, std::min(h->num_sms * 8, (int)((nw + 255) / 256))), 256, 0, s>>>(
+        h->d_params + h->off_layer[0], nw, h->d_w_f16, h->d_w_bf16);
+    NIF_CK_LAUNCH(h);
+    h->lowp_dirty = false;
+    return NIF_OK;
+}
+
+nif_status nif_ensure_instances(nif_handle* h, int n_inst) {
+    if (n_inst <= h->inst_cap) return NIF_OK;
+    NIF_CK(h, cudaDeviceSynchronize());
+    cudaFree(h->d_corners);
+    cudaFree(h->d_aabb);
+    cudaFree(h->d_pose);
+    h->d_corners = nullptr;
+    h->d_aabb = nullptr;
+    h->d_pose = nullptr;
+    int cap = std::max(n_inst, 1);
+    NIF_CK(h, cudaMalloc(&h->d_corners, sizeof(float) * 24 * (size_t)std::max(h->n_leaves, 1) * cap));
+    NIF_CK(h, cudaMalloc(&h->d_aabb, sizeof(float4) * 2 * (size_t)std::max(h->n_nodes, 1) * cap));
+    NIF_CK(h, cudaMalloc(&h->d_pose, sizeof(float4) * cap));
+    h->inst_cap = cap;
+    return NIF_OK;
+}
+
+nif_status nif_upload_poses(nif_handle* h, const nif_pose* poses, int n_inst, cudaStream_t s) {
+    nif_status st = nif_ensure_instances(h, n_inst);
+    if (st != NIF_OK) return st;
+    std::vector<float4> p(n_inst);
+    for (int i = 0; i < n_inst; i++) p[i] = make_float4(NIF_KBEND * poses[i].bend, poses[i].twist, poses[i].taper, 0.f);
+    NIF_CK(h, cudaMemcpyAsync(h->d_pose, p.data(), sizeof(float4) * n_inst, cudaMemcpyHostToDevice, s));
+    // the staging vector dies with this scope: make the copy complete first
+    NIF_CK(h, cudaStreamSynchronize(s));
+    return NIF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Lifetime
+// ---------------------------------------------------------------------------
+static nif_status validate(const nif_config* c, const nif_mesh* m) {
+    if (!c || !m) return nif_fail(nullptr, NIF_ERR_ARG, "null config or mesh");
+    if (c->voxel_res < 2 || c->voxel_res > 512 || (c->voxel_res & (c->voxel_res - 1)))
+        return nif_fail(nullptr, NIF_ERR_ARG, "voxel_res must be a power of two in [2, 512]");
+    if (c->pe_bands < 0 || c->pe_bands > 8) return nif_fail(nullptr, NIF_ERR_ARG, "pe_bands in [0, 8]");
+    if (c->levels < 1 || c->levels > NIF_MAX_LEVELS) return nif_fail(nullptr, NIF_ERR_ARG, "levels in [1, 32]");
+    if (c->feats != 2) return nif_fail(nullptr, NIF_ERR_ARG, "feats must be 2");
+    if (c->log2_table < 4 || c->log2_table > 24) return nif_fail(nullptr, NIF_ERR_ARG, "log2_table in [4, 24]");
+    if (c->base_res < 1 || !(c->growth >= 1.0f)) return nif_fail(nullptr, NIF_ERR_ARG, "base_res >= 1, growth >= 1");
+    if (c->mlp_depth < 1 || c->mlp_depth > NIF_MAX_LAYERS - 2) return nif_fail(nullptr, NIF_ERR_ARG, "mlp_depth in [1, 8]");
+    if (c->mlp_width != 16 && c->mlp_width != 32 && c->mlp_width != 64 && c->mlp_width != 128)
+        return nif_fail(nullptr, NIF_ERR_ARG, "mlp_width in {16, 32, 64, 128}");
+    if (c->n_materials < 1 || c->n_materials > 8) return nif_fail(nullptr, NIF_ERR_ARG, "n_materials in [1, 8]");
+    if (c->precision < NIF_FP32 || c->precision > NIF_FP16) return nif_fail(nullptr, NIF_ERR_ARG, "precision");
+    if (m->n_tris < 0 || m->n_verts < 0 || (m->n_tris > 0 && (!m->tris || !m->verts)))
+        return nif_fail(nullptr, NIF_ERR_ARG, "mesh arrays");
+    for (int t = 0; t < m->n_tris * 3; t++)
+        if (m->tris[t] < 0 || m->tris[t] >= m->n_verts) return nif_fail(nullptr, NIF_ERR_ARG, "triangle index out of range");
+    if (m->tri_material)
+        for (int t = 0; t < m->n_tris; t++)
+            if (m->tri_material[t] >= c->n_materials) return nif_fail(nullptr, NIF_ERR_ARG, "material out of range");
+    for (int v = 0; v < m->n_verts * 3; v++)
+        if (!(m->verts[v] >= 0.0f && m->verts[v] <= 1.0f)) return nif_fail(nullptr, NIF_ERR_ARG, "vertices must lie in [0,1]^3");
+    return NIF_OK;
+}
+
+static nif_status build_octree(nif_handle* h) {
+    int N = h->N;
+    int64_t nvox = (int64_t)N * N * N;
+    std::vector<uint8_t> occ(nvox);
+    NIF_CK(h, cudaMemcpy(occ.data(), h->d_occ, nvox, cudaMemcpyDeviceToHost));
+    std::vector<std::pair<uint32_t, uint32_t>> leaves;   // (morton, voxel)
+    for (int64_t v = 0; v < nvox; v++)
+        if (occ[v]) {
+            uint32_t i = v % N, j = (v / N) % N, k = (uint32_t)(v / ((int64_t)N * N));
+            leaves.push_back({morton3(i, j, k), (uint32_t)v});
+        }
+    std::sort(leaves.begin(), leaves.end());
+    int n = (int)leaves.size();
+    h->n_leaves = n;
+    std::vector<uint32_t> vox(n), lat(n);
+    for (int q = 0; q < n; q++) {
+        uint32_t v = leaves[q].second;
+        uint32_t i = v % N, j = (v / N) % N, k = v / (N * N);
+        vox[q] = v;
+        lat[q] = i | (j << 10) | (k << 20);
+    }
+    // internal levels: group nodes sharing the Morton prefix one octree level up
+    std::vector<uint32_t> codes(n);
+    for (int q = 0; q < n; q++) codes[q] = leaves[q].first;
+    std::vector<int2> child;
+    int level_first = 0;      // global index of the current level's first node
+    int level_n = n;
+    int next_global = n;
+    h->level_begin.clear();
+    h->level_count.clear();
+    while (level_n > 8) {
+        std::vector<uint32_t> pcodes;
+        int begin = next_global;
+        for (int q = 0; q < level_n;) {
+            uint32_t pc = codes[q] >> 3;
+            int r = q;
+            while (r < level_n && (codes[r] >> 3) == pc) r++;
+            child.push_back(make_int2(level_first + q, r - q));
+            pcodes.push_back(pc);
+            q = r;
+        }
+        int cnt = (int)pcodes.size();
+        h->level_begin.push_back(begin);
+        h->level_count.push_back(cnt);
+        codes.swap(pcodes);
+        level_first = begin;
+        level_n = cnt;
+        next_global = begin + cnt;
+    }
+    h->n_nodes = next_global;
+    h->top_begin = level_first;
+    h->top_count = level_n;
+    NIF_CK(h, cudaMalloc(&h->d_leaf_vox, sizeof(uint32_t) * std::max(n, 1)));
+    NIF_CK(h, cudaMalloc(&h->d_leaf_lat, sizeof(uint32_t) * std::max(n, 1)));
+    NIF_CK(h, cudaMalloc(&h->d_child, sizeof(int2) * std::max((size_t)1, child.size())));
+    if (n) {
+        NIF_CK(h, cudaMemcpy(h->d_leaf_vox, vox.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+        NIF_CK(h, cudaMemcpy(h->d_leaf_lat, lat.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+    }
+    if (!child.empty())
+        NIF_CK(h, cudaMemcpy(h->d_child, child.data(), sizeof(int2) * child.size(), cudaMemcpyHostToDevice));
+    return NIF_OK;
+}
+
+static nif_status init_params(nif_handle* h) {
+    std::vector<float> p(h->n_params, 0.f);
+    uint64_t seed = h->cfg.seed;
+    uint64_t ctr = 0;
+    size_t nt = (size_t)h->L * h->T * h->Fd;
+    for (size_t i = 0; i < nt; i++) p[h->off_tables + i] = (2.0f * host_uniform(seed, ctr++) - 1.0f) * 1e-4f;
+    for (int l = 0; l < h->n_layers; l++) {
+        float b = std::sqrt(6.0f / (float)h->lay_in[l]);
+        for (int o = 0; o < h->lay_out[l]; o++)
+            for (int i = 0; i < h->lay_in[l]; i++) {
+                float v = (2.0f * host_uniform(seed, ctr++) - 1.0f) * b;
+                bool pad = (l == h->n_layers - 1) && o >= 8 + h->cfg.n_materials;
+                p[h->off_layer[l] + (size_t)o * h->lay_in[l] + i] = pad ? 0.f : v;
+            }
+    }
+    NIF_CK(h, cudaMemcpy(h->d_params, p.data(), sizeof(float) * h->n_params, cudaMemcpyHostToDevice));
+    h->lowp_dirty = true;
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, nif_handle** out) {
+    if (!out) return nif_fail(nullptr, NIF_ERR_ARG, "null out");
+    *out = nullptr;
+    nif_status st = validate(cfg, mesh);
+    if (st != NIF_OK) return st;
+    nif_handle* h = new nif_handle();
+    h->cfg = *cfg;
+    h->N = cfg->voxel_res;
+    h->L = cfg->levels;
+    h->Fd = cfg->feats;
+    h->P = 1 + 2 * cfg->pe_bands;
+    h->T = 1u << cfg->log2_table;
+    h->W = cfg->mlp_width;
+    h->H = cfg->mlp_depth;
+    h->n_layers = h->H + 1;
+    h->in_dim = 2 * h->P * h->L * h->Fd;
+    h->grid.L = h->L;
+    h->grid.Fd = h->Fd;
+    h->grid.P = h->P;
+    h->grid.F = cfg->pe_bands;
+    h->grid.T = h->T;
+    h->grid.dense_mask = 0;
+    for (int l = 0; l < h->L; l++) {
+        double r = std::floor((double)cfg->base_res * std::pow((double)cfg->growth, (double)l));
+        if (r > 1.0e6) { delete h; return nif_fail(nullptr, NIF_ERR_ARG, "level resolution too large"); }
+        h->grid.res[l] = (int)r;
+        double v = (r + 1.0) * (r + 1.0) * (r + 1.0);
+        if (v <= (double)h->T) h->grid.dense_mask |= 1u << l;
+    }
+    int dev = 0;
+    auto fail = [&](nif_status s) {
+        g_create_err = h->err;
+        nif_destroy(h);
+        return s;
+    };
+    if (cudaGetDevice(&dev) != cudaSuccess) { delete h; return nif_fail(nullptr, NIF_ERR_CUDA, "no CUDA device"); }
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (h->num_sms <= 0) h->num_sms = 1;
+
+    // mesh
+    h->n_verts = mesh->n_verts;
+    h->n_tris = mesh->n_tris;
+    {
+        std::vector<float> alb(3 * (size_t)std::max(h->n_tris, 1), 0.5f);
+        std::vector<uint8_t> mat((size_t)std::max(h->n_tris, 1), 0);
+        if (mesh->tri_albedo) std::memcpy(alb.data(), mesh->tri_albedo, sizeof(float) * 3 * h->n_tris);
+        if (mesh->tri_material) std::memcpy(mat.data(), mesh->tri_material, h->n_tris);
+#define CKC(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return fail(nif_cuda_fail(h, e_, #call)); } while (0)
+        CKC(cudaMalloc(&h->d_verts, sizeof(float) * 3 * std::max(h->n_verts, 1)));
+        CKC(cudaMalloc(&h->d_tris, sizeof(int) * 3 * std::max(h->n_tris, 1)));
+        CKC(cudaMalloc(&h->d_alb, sizeof(float) * alb.size()));
+        CKC(cudaMalloc(&h->d_mat, mat.size()));
+        if (h->n_verts) CKC(cudaMemcpy(h->d_verts, mesh->verts, sizeof(float) * 3 * h->n_verts, cudaMemcpyHostToDevice));
+        if (h->n_tris) CKC(cudaMemcpy(h->d_tris, mesh->tris, sizeof(int) * 3 * h->n_tris, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->d_alb, alb.data(), sizeof(float) * alb.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->d_mat, mat.data(), mat.size(), cudaMemcpyHostToDevice));
+    }
+    CKC(cudaMalloc(&h->d_status, sizeof(int) * 4));
+    CKC(cudaMemset(h->d_status, 0, sizeof(int) * 4));
+    CKC(cudaMalloc(&h->d_lossacc, sizeof(double) * 16));
+    CKC(cudaMemset(h->d_lossacc, 0, sizeof(double) * 16));
+    CKC(cudaMalloc(&h->d_count, sizeof(int) * 4));
+    CKC(cudaMemset(h->d_count, 0, sizeof(int) * 4));
+    CKC(cudaMallocHost(&h->h_pinned, sizeof(int) * 16));
+
+    st = nif_voxelize_run(h);
+    if (st != NIF_OK) return fail(st);
+    st = build_octree(h);
+    if (st != NIF_OK) return fail(st);
+
+    // parameter layout
+    size_t off = 0;
+    h->off_tables = 0;
+    off += (size_t)h->L * h->T * h->Fd;
+    for (int l = 0; l < h->n_layers; l++) {
+        h->lay_in[l] = l == 0 ? h->in_dim : h->W;
+        h->lay_out[l] = l == h->n_layers - 1 ? NIF_OUT : h->W;
+        off = (off + 3) & ~(size_t)3;
+        h->off_layer[l] = off;
+        off += (size_t)h->lay_in[l] * h->lay_out[l];
+    }
+    off = (off + 3) & ~(size_t)3;
+    h->off_layer[h->n_layers] = off;
+    h->off_s = off;
+    off += 8;
+    h->n_params = off;
+    CKC(cudaMalloc(&h->d_params, sizeof(float) * off));
+    CKC(cudaMalloc(&h->d_grad, sizeof(float) * off));
+    CKC(cudaMalloc(&h->d_m, sizeof(float) * off));
+    CKC(cudaMalloc(&h->d_v, sizeof(float) * off));
+    CKC(cudaMemset(h->d_grad, 0, sizeof(float) * off));
+    CKC(cudaMemset(h->d_m, 0, sizeof(float) * off));
+    CKC(cudaMemset(h->d_v, 0, sizeof(float) * off));
+    CKC(cudaMalloc(&h->d_tables_h, sizeof(__half) * (size_t)h->L * h->T * h->Fd));
+    CKC(cudaMalloc(&h->d_w_bf16, sizeof(__nv_bfloat16) * (h->off_s - h->off_layer[0])));
+    CKC(cudaMalloc(&h->d_w_f16, sizeof(__half) * (h->off_s - h->off_layer[0])));
+#undef CKC
+    st = init_params(h);
+    if (st != NIF_OK) return fail(st);
+    st = nif_ensure_instances(h, 1);
+    if (st != NIF_OK) return fail(st);
+    *out = h;
+    return NIF_OK;
+}
+
+extern "C" void nif_destroy(nif_handle* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    void* ptrs[] = {h->d_verts, h->d_tris, h->d_alb, h->d_mat, h->d_occ, h->d_tri_ptr, h->d_tri_idx, h->d_child,
+                    h->d_leaf_vox, h->d_leaf_lat, h->d_corners, h->d_aabb, h->d_pose, h->d_params, h->d_grad,
+                    h->d_m, h->d_v, h->d_tables_h, h->d_w_bf16, h->d_w_f16, h->d_status, h->d_lossacc,
+                    h->d_count};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
+                               &h->b_acts, &h->b_dout, &h->b_dx, &h->b_labels, &h->b_scan, &h->b_rays,
+                               &h->b_inst, &h->b_feat2};
+    for (auto* b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    delete h;
+}
+
+extern "C" const char* nif_last_error(const nif_handle* h) {
+    if (!h) return g_create_err.c_str();
+    return h->err.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// Parameters
+// ---------------------------------------------------------------------------
+static bool group_range(const nif_handle* h, int group, size_t* off, size_t* n) {
+    if (group == NIF_PARAM_TABLES) { *off = h->off_tables; *n = (size_t)h->L * h->T * h->Fd; return true; }
+    if (group == NIF_PARAM_LOGVAR) { *off = h->off_s; *n = 5; return true; }
+    int l = group - NIF_PARAM_LAYER0;
+    if (l >= 0 && l < h->n_layers) { *off = h->off_layer[l]; *n = (size_t)h->lay_in[l] * h->lay_out[l]; return true; }
+    return false;
+}
+
+extern "C" nif_status nif_param_bytes(const nif_handle* h, int group, size_t* bytes) {
+    size_t off, n;
+    if (!h || !bytes || !group_range(h, group, &off, &n)) return NIF_ERR_ARG;
+    *bytes = n * sizeof(float);
+    return NIF_OK;
+}
+
+static nif_status copy_group(nif_handle* h, float* base, int group, void* host, size_t bytes, bool to_host) {
+    size_t off, n;
+    if (!h || !host || !group_range(h, group, &off, &n)) return nif_fail(h, NIF_ERR_ARG, "parameter group");
+    if (bytes != n * sizeof(float)) return nif_fail(h, NIF_ERR_ARG, "parameter size mismatch");
+    NIF_CK(h, cudaDeviceSynchronize());
+    if (to_host) NIF_CK(h, cudaMemcpy(host, base + off, bytes, cudaMemcpyDeviceToHost));
+    else NIF_CK(h, cudaMemcpy(base + off, host, bytes, cudaMemcpyHostToDevice));
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_get_params(nif_handle* h, int group, void* dst, size_t bytes) {
+    if (!h) return NIF_ERR_ARG;
+    return copy_group(h, h->d_params, group, dst, bytes, true);
+}
+
+extern "C" nif_status nif_set_params(nif_handle* h, int group, const void* src, size_t bytes) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = copy_group(h, h->d_params, group, const_cast<void*>(src), bytes, false);
+    h->lowp_dirty = true;
+    return st;
+}
+
+extern "C" nif_status nif_get_grad(nif_handle* h, int group, void* dst, size_t bytes) {
+    if (!h) return NIF_ERR_ARG;
+    return copy_group(h, h->d_grad, group, dst, bytes, true);
+}
+
+extern "C" nif_status nif_set_grad(nif_handle* h, int group, const void* src, size_t bytes) {
+    if (!h) return NIF_ERR_ARG;
+    return copy_group(h, h->d_grad, group, const_cast<void*>(src), bytes, false);
+}
+
+extern "C" nif_status nif_zero_grad(nif_handle* h, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    NIF_CK(h, cudaMemsetAsync(h->d_grad, 0, sizeof(float) * h->n_params, (cudaStream_t)stream));
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_reset_optimizer(nif_handle* h) {
+    if (!h) return NIF_ERR_ARG;
+    NIF_CK(h, cudaDeviceSynchronize());
+    NIF_CK(h, cudaMemset(h->d_m, 0, sizeof(float) * h->n_params));
+    NIF_CK(h, cudaMemset(h->d_v, 0, sizeof(float) * h->n_params));
+    h->adam_step = 0;
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_adam_step(nif_handle* h, float lr_grid, float lr_mlp, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    return nif_adam_run(h, lr_grid, lr_mlp, (cudaStream_t)stream);
+}
+
+extern "C" nif_status nif_get_voxels(nif_handle* h, unsigned char* occ, int64_t* tri_ptr, int32_t* tri_idx,
+                                     int64_t cap, int64_t* n_pairs) {
+    if (!h || !occ) return NIF_ERR_ARG;
+    int64_t nvox = (int64_t)h->N * h->N * h->N;
+    NIF_CK(h, cudaDeviceSynchronize());
+    NIF_CK(h, cudaMemcpy(occ, h->d_occ, nvox, cudaMemcpyDeviceToHost));
+    if (n_pairs) *n_pairs = h->n_pairs;
+    if (tri_ptr) {
+        std::vector<uint32_t> p(nvox + 1);
+        NIF_CK(h, cudaMemcpy(p.data(), h->d_tri_ptr, sizeof(uint32_t) * (nvox + 1), cudaMemcpyDeviceToHost));
+        for (int64_t v = 0; v <= nvox; v++) tri_ptr[v] = p[v];
+        if (tri_idx) {
+            int64_t n = std::min(cap, h->n_pairs);
+            if (n > 0) NIF_CK(h, cudaMemcpy(tri_idx, h->d_tri_idx, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        }
+    }
+    return NIF_OK;
+}
+
+static nif_status check_status(nif_handle* h, cudaStream_t s) {
+    NIF_CK(h, cudaStreamSynchronize(s));
+    int st = 0;
+    NIF_CK(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        NIF_CK(h, cudaMemset(h->d_status, 0, sizeof(int)));
+        return nif_fail(h, (nif_status)st, "device-side error latched by a kernel");
+    }
+    return NIF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stages
+// ---------------------------------------------------------------------------
+static nif_status check_inst(nif_handle* h, const nif_pose* poses, int n_inst, const int* inst_off, int n_rays) {
+    if (!poses || n_inst < 1) return nif_fail(h, NIF_ERR_ARG, "poses");
+    if (n_inst > 1 && !inst_off) return nif_fail(h, NIF_ERR_ARG, "inst_offsets required for n_inst > 1");
+    if (n_rays < 0) return nif_fail(h, NIF_ERR_ARG, "n_rays");
+    for (int i = 0; i < n_inst; i++)
+        if (!(std::fabs(poses[i].bend) <= 1.0f && std::fabs(poses[i].twist) <= 4.0f && std::fabs(poses[i].taper) <= 1.0f))
+            return nif_fail(h, NIF_ERR_ARG, "pose outside |bend| <= 1, |twist| <= 4, |taper| <= 1");
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_segments(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                   const int* inst_off, int n_rays, uint32_t* ray_offsets, nif_segment* segs,
+                                   int64_t seg_cap, int64_t* n_segs_host, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    if (!ray_offsets || (n_rays > 0 && !rays)) return nif_fail(h, NIF_ERR_ARG, "buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
+    if ((st = nif_refit_run(h, n_inst, s)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_counts, sizeof(uint32_t) * ((size_t)n_rays + 1))) != NIF_OK) return st;
+    uint32_t* counts = (uint32_t*)h->b_counts.p;
+    if ((st = nif_seg_count_run(h, rays, inst_off, n_inst, n_rays, counts, s)) != NIF_OK) return st;
+    if ((st = nif_scan_run(h, counts, ray_offsets, n_rays, s)) != NIF_OK) return st;
+    if ((st = nif_seg_emit_run(h, rays, inst_off, n_inst, n_rays, ray_offsets, segs, segs ? seg_cap : 0, s)) != NIF_OK)
+        return st;
+    NIF_CK(h, cudaStreamSynchronize(s));
+    uint32_t tot = 0;
+    NIF_CK(h, cudaMemcpy(&tot, ray_offsets + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (n_segs_host) *n_segs_host = tot;
+    st = check_status(h, s);
+    if (st != NIF_OK) return st;
+    if (segs && (int64_t)tot > seg_cap) return nif_fail(h, NIF_ERR_CAPACITY, "segment capacity exceeded");
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_linearize(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                    const int* inst_off, int n_rays, const nif_segment* segs, int64_t n_segs,
+                                    nif_linseg* lin, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
+    return nif_linearize_run(h, rays, inst_off, n_inst, segs, nullptr, n_segs, lin, s);
+}
+
+extern "C" nif_status nif_encode_points(nif_handle* h, const float* pts, int64_t n, void* feats, int out_dtype,
+                                        int32_t* rows, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!pts || !feats))) return NIF_ERR_ARG;
+    return nif_encode_points_run(h, pts, n, feats, out_dtype, rows, (cudaStream_t)stream);
+}
+
+extern "C" nif_status nif_encode_segments(nif_handle* h, const nif_linseg* lin, int64_t n, void* feats,
+                                          int out_dtype, int table_dtype, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!lin || !feats))) return NIF_ERR_ARG;
+    return nif_encode_segments_run(h, lin, nullptr, n, feats, out_dtype, table_dtype, (cudaStream_t)stream);
+}
+
+extern "C" nif_status nif_encode_points_backward(nif_handle* h, const float* pts, int64_t n, const float* dfeats,
+                                                 float* dtables, float* dpts, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!pts || !dfeats || !dtables))) return NIF_ERR_ARG;
+    return nif_encode_points_bwd_run(h, pts, n, dfeats, dtables, dpts, (cudaStream_t)stream);
+}
+
+extern "C" nif_status nif_mlp_forward(nif_handle* h, const void* x, int x_dtype, int64_t n, float* out,
+                                      int precision, float* acts, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!x || !out))) return NIF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == NIF_FP32) {
+        if (x_dtype != NIF_FP32) return nif_fail(h, NIF_ERR_ARG, "FP32 MLP needs FP32 input");
+        nif_status st = NIF_OK;
+        float* a = acts;
+        if (!a) {
+            if ((st = nif_grow(h, h->b_acts, sizeof(float) * (size_t)std::max<int64_t>(n, 1) * h->W * h->H)) != NIF_OK)
+                return st;
+            a = (float*)h->b_acts.p;
+        }
+        return nif_mlp_fwd_fp32_run(h, (const float*)x, nullptr, n, out, a, s);
+    }
+    if (precision != x_dtype) return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP input dtype must equal precision");
+    return nif_mlp_fwd_tc_run(h, x, precision, nullptr, n, out, s);
+}
+
+extern "C" nif_status nif_mlp_backward(nif_handle* h, const float* x, int64_t n, const float* acts, const float* dout,
+                                       float* dx, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!x || !acts || !dout))) return NIF_ERR_ARG;
+    return nif_mlp_bwd_fp32_run(h, x, nullptr, n, acts, dout, dx, (cudaStream_t)stream);
+}
+
+extern "C" nif_status nif_labels(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, int64_t n,
+                                 nif_label* labels, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!segs || !lin || !labels))) return NIF_ERR_ARG;
+    return nif_labels_run(h, segs, lin, nullptr, n, labels, (cudaStream_t)stream);
+}
+
+extern "C" nif_status nif_loss(nif_handle* h, const float* out, const nif_label* labels, const nif_linseg* lin,
+                               int64_t n, float* dout, double* parts_host, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!out || !labels || !lin))) return NIF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    // hit count of these labels (the label stage counted its own batch; recount here)
+    nif_status st = nif_labels_count_hits(h, labels, n, s);
+    if (st != NIF_OK) return st;
+    if ((st = nif_loss_run(h, out, labels, lin, nullptr, n, dout, s)) != NIF_OK) return st;
+    if (parts_host) {
+        double acc[16];
+        NIF_CK(h, cudaStreamSynchronize(s));
+        NIF_CK(h, cudaMemcpy(acc, h->d_lossacc, sizeof(acc), cudaMemcpyDeviceToHost));
+        parts_host[0] = acc[8];
+        for (int i = 0; i < 5; i++) parts_host[1 + i] = acc[9 + i];
+    }
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_reconstruct(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                      const int* inst_off, int n_rays, const uint32_t* ray_offsets,
+                                      const nif_segment* segs, const nif_linseg* lin, const float* out,
+                                      nif_hit* hits, unsigned flags, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
+    return nif_reconstruct_run(h, rays, inst_off, n_inst, n_rays, ray_offsets, segs, INT64_MAX, lin, out, hits, flags,
+                               s);
+}
+
+extern "C" nif_status nif_sample_rays(nif_handle* h, unsigned long long seed, int stream_id, int n, nif_ray* rays,
+                                      void* stream) {
+    if (!h || n < 0 || (n > 0 && !rays)) return NIF_ERR_ARG;
+    return nif_sample_rays_run(h, seed, stream_id, n, rays, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Whole paths
+// ---------------------------------------------------------------------------
+
+// segments of the caller's rays into the handle's scratch; returns the device
+// pointer of the clamped total (<= cap)
+static nif_status segment_into_scratch(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                       const int* inst_off, int n_rays, int64_t cap, bool host_total,
+                                       int64_t* total_host, cudaStream_t s) {
+    nif_status st;
+    if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
+    if ((st = nif_refit_run(h, n_inst, s)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_counts, sizeof(uint32_t) * ((size_t)n_rays + 1))) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_offsets, sizeof(uint32_t) * ((size_t)n_rays + 2))) != NIF_OK) return st;
+    uint32_t* counts = (uint32_t*)h->b_counts.p;
+    uint32_t* offs = (uint32_t*)h->b_offsets.p;
+    if ((st = nif_seg_count_run(h, rays, inst_off, n_inst, n_rays, counts, s)) != NIF_OK) return st;
+    if ((st = nif_scan_run(h, counts, offs, n_rays, s)) != NIF_OK) return st;
+    if (host_total) {
+        uint32_t tot = 0;
+        NIF_CK(h, cudaMemcpyAsync(h->h_pinned, offs + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        NIF_CK(h, cudaStreamSynchronize(s));
+        tot = (uint32_t)h->h_pinned[0];
+        *total_host = tot;
+        if (cap < 0) cap = tot;
+    }
+    if ((st = nif_grow(h, h->b_segs, sizeof(nif_segment) * (size_t)std::max<int64_t>(cap, 1))) != NIF_OK) return st;
+    if ((st = nif_seg_emit_run(h, rays, inst_off, n_inst, n_rays, offs, (nif_segment*)h->b_segs.p, cap, s)) != NIF_OK)
+        return st;
+    // clamped count lives right after the offsets
+    return nif_clamp_count_run(h, offs, n_rays, cap, offs + n_rays + 1, s);
+}
+
+extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                const int* inst_off, int n_rays, nif_hit* hits, unsigned flags, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    if (n_rays == 0) return NIF_OK;
+    if (!rays || !hits) return nif_fail(h, NIF_ERR_ARG, "rays / hits");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t total = 0;
+    if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, -1, true, &total, s)) != NIF_OK)
+        return st;
+    uint32_t* offs = (uint32_t*)h->b_offsets.p;
+    const uint32_t* n_dev = offs + n_rays + 1;
+    int64_t n = std::max<int64_t>(total, 1);
+    if ((st = nif_grow(h, h->b_lin, sizeof(nif_linseg) * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
+    nif_segment* segs = (nif_segment*)h->b_segs.p;
+    nif_linseg* lin = (nif_linseg*)h->b_lin.p;
+    float* out = (float*)h->b_out.p;
+    if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, total, lin, s)) != NIF_OK) return st;
+    int prec = h->cfg.precision;
+    size_t esz = prec == NIF_FP32 ? 4 : 2;
+    if ((st = nif_grow(h, h->b_feat, esz * (size_t)h->in_dim * n)) != NIF_OK) return st;
+    if (prec == NIF_FP32) {
+        if ((st = nif_encode_segments_run(h, lin, n_dev, total, h->b_feat.p, NIF_FP32, NIF_FP32, s)) != NIF_OK)
+            return st;
+        if ((st = nif_grow(h, h->b_acts, sizeof(float) * (size_t)n * h->W * h->H)) != NIF_OK) return st;
+        if ((st = nif_mlp_fwd_fp32_run(h, (const float*)h->b_feat.p, n_dev, total, out, (float*)h->b_acts.p, s)) !=
+            NIF_OK)
+            return st;
+    } else {
+        if ((st = nif_encode_segments_run(h, lin, n_dev, total, h->b_feat.p, prec, NIF_FP16, s)) != NIF_OK) return st;
+        if ((st = nif_mlp_fwd_tc_run(h, h->b_feat.p, prec, n_dev, total, out, s)) != NIF_OK) return st;
+    }
+    return nif_reconstruct_run(h, rays, inst_off, n_inst, n_rays, offs, segs, total, lin, out, hits, flags, s);
+}
+
+extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                          const int* inst_off, int n_rays, int64_t n_segments, float lr_grid,
+                                          float lr_mlp, double* loss_host, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    if (n_segments < 1 || !rays) return nif_fail(h, NIF_ERR_ARG, "n_segments / rays");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, n_segments, false, nullptr, s)) != NIF_OK)
+        return st;
+    // the capacity clamp marks overflow; for training a full batch is the normal case
+    uint32_t* offs = (uint32_t*)h->b_offsets.p;
+    const uint32_t* n_dev = offs + n_rays + 1;
+    int64_t n = n_segments;
+    if ((st = nif_grow(h, h->b_lin, sizeof(nif_linseg) * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_labels, sizeof(nif_label) * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_feat, sizeof(float) * (size_t)h->in_dim * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_dx, sizeof(float) * (size_t)h->in_dim * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_feat2, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_acts, sizeof(float) * (size_t)n * h->W * h->H)) != NIF_OK) return st;
+    nif_segment* segs = (nif_segment*)h->b_segs.p;
+    nif_linseg* lin = (nif_linseg*)h->b_lin.p;
+    nif_label* lab = (nif_label*)h->b_labels.p;
+    float* feat = (float*)h->b_feat.p;
+    float* dx = (float*)h->b_dx.p;
+    float* out = (float*)h->b_out.p;
+    float* dout = (float*)h->b_feat2.p;
+    float* acts = (float*)h->b_acts.p;
+    if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, n, lin, s)) != NIF_OK) return st;
+    if ((st = nif_labels_run(h, segs, lin, n_dev, n, lab, s)) != NIF_OK) return st;
+    if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s)) != NIF_OK) return st;
+    if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
+    if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s)) != NIF_OK) return st;
+    if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s)) != NIF_OK) return st;
+    if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK) return st;
+    if ((st = nif_adam_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
+    if (loss_host) {
+        double acc[16];
+        NIF_CK(h, cudaStreamSynchronize(s));
+        NIF_CK(h, cudaMemcpy(acc, h->d_lossacc, sizeof(acc), cudaMemcpyDeviceToHost));
+        loss_host[0] = acc[8];
+        for (int i = 0; i < 5; i++) loss_host[1 + i] = acc[9 + i];
+        int dst = 0;
+        NIF_CK(h, cudaMemcpy(&dst, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (dst == NIF_ERR_NAN) {
+            cudaMemset(h->d_status, 0, sizeof(int));
+            return nif_fail(h, NIF_ERR_NAN, "non-finite loss");
+        }
+        if (dst == NIF_ERR_CAPACITY) cudaMemset(h->d_status, 0, sizeof(int));   // a full batch
+    }
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses, unsigned long long step_seed,
+                                     float lr_grid, float lr_mlp, nif_pose* poses_out, double* loss_host,
+                                     void* stream) {
+    if (!h || n_segments < 1 || n_poses < 1) return NIF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<nif_pose> poses(n_poses);
+    for (int i = 0; i < n_poses; i++) {
+        uint64_t base = ((0xFFFFull << 32) + (uint64_t)i) * 8ull;
+        poses[i].bend = 2.f * host_uniform(step_seed, base) - 1.f;
+        poses[i].twist = 2.f * host_uniform(step_seed, base + 1) - 1.f;
+        poses[i].taper = 2.f * host_uniform(step_seed, base + 2) - 1.f;
+    }
+    if (poses_out) std::memcpy(poses_out, poses.data(), sizeof(nif_pose) * n_poses);
+    nif_status st;
+    // rays per pose: from the measured segments per ray (probed once)
+    if (h->seg_per_ray <= 0.0) {
+        const int probe = 8192;
+        if ((st = nif_grow(h, h->b_rays, sizeof(nif_ray) * probe)) != NIF_OK) return st;
+        if ((st = nif_sample_rays_run(h, step_seed ^ 0x5bd1e995ull, 0, probe, (nif_ray*)h->b_rays.p, s)) != NIF_OK)
+            return st;
+        int64_t tot = 0;
+        if ((st = segment_into_scratch(h, poses.data(), 1, (nif_ray*)h->b_rays.p, nullptr, probe, -1, true, &tot, s)) !=
+            NIF_OK)
+            return st;
+        h->seg_per_ray = std::max(0.05, (double)tot / probe);
+    }
+    int per = (int)std::ceil((double)n_segments / n_poses / h->seg_per_ray * 1.2) + 1;
+    int n_rays = per * n_poses;
+    if ((st = nif_grow(h, h->b_rays, sizeof(nif_ray) * (size_t)n_rays)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_inst, sizeof(int) * (size_t)(n_poses + 1))) != NIF_OK) return st;
+    nif_ray* rays = (nif_ray*)h->b_rays.p;
+    for (int i = 0; i < n_poses; i++)
+        if ((st = nif_sample_rays_run(h, step_seed, i, per, rays + (size_t)i * per, s)) != NIF_OK) return st;
+    std::vector<int> off(n_poses + 1);
+    for (int i = 0; i <= n_poses; i++) off[i] = i * per;
+    NIF_CK(h, cudaMemcpyAsync(h->b_inst.p, off.data(), sizeof(int) * (n_poses + 1), cudaMemcpyHostToDevice, s));
+    NIF_CK(h, cudaStreamSynchronize(s));
+    return nif_train_step_rays(h, poses.data(), n_poses, rays, (const int*)h->b_inst.p, n_rays, n_segments, lr_grid,
+                               lr_mlp, loss_host, stream);
+}

@@ -1,0 +1,251 @@
+// nif_internal.cuh -- shared internals of the CUDA library (handle, device
+// math of the deformation, launch helpers). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nif.h"
+
+#define NIF_MAX_LEVELS 32
+#define NIF_MAX_LAYERS 10
+#define NIF_OUT 16            // stored output rows (occ, dist, n3, albedo3, M material, pad)
+#define NIF_KBEND 0.75f       // bend curvature per unit bend parameter
+#define NIF_EPS_DIST 1e-2f    // log-distance epsilon (voxel units)
+
+// ---------------------------------------------------------------------------
+// Encoding constants passed by value to kernels.
+// ---------------------------------------------------------------------------
+struct GridInfo {
+    int L, Fd, P, F;          // levels, features, gamma terms (1+2F), bands
+    uint32_t T;               // entries per level (power of two)
+    uint32_t dense_mask;      // bit l set when level l is dense ((N_l+1)^3 <= T)
+    int res[NIF_MAX_LEVELS];  // N_l
+};
+
+// Octree over the occupied voxels (Morton order). Global node numbering:
+// leaves [0, n_leaves), then each internal level in turn; internal node i
+// (global index >= n_leaves) has children [child_begin, child_begin + count).
+struct TreeView {
+    int n_leaves;             // occupied voxels
+    int n_nodes;              // leaves + internal nodes
+    int top_begin, top_count; // nodes the traversal starts from
+    const int2* child;        // [n_nodes - n_leaves]: (begin, count)
+    const uint32_t* leaf_vox; // [n_leaves] rest voxel id of each leaf
+};
+
+struct nif_handle {
+    nif_config cfg{};
+    int N = 0, L = 0, Fd = 2, P = 0, in_dim = 0, W = 0, H = 0, n_layers = 0;
+    uint32_t T = 0;
+    GridInfo grid{};
+
+    // mesh (device copy)
+    float* d_verts = nullptr;
+    int* d_tris = nullptr;
+    float* d_alb = nullptr;
+    uint8_t* d_mat = nullptr;
+    int n_verts = 0, n_tris = 0;
+
+    // voxels
+    uint8_t* d_occ = nullptr;           // [N^3]
+    uint32_t* d_tri_ptr = nullptr;      // [N^3 + 1]
+    int32_t* d_tri_idx = nullptr;       // [n_pairs]
+    int64_t n_pairs = 0;
+
+    // octree topology
+    int n_leaves = 0, n_nodes = 0, top_begin = 0, top_count = 0;
+    std::vector<int> level_begin, level_count;   // internal levels, bottom-up
+    int2* d_child = nullptr;
+    uint32_t* d_leaf_vox = nullptr;             // [n_leaves]
+    uint32_t* d_leaf_lat = nullptr;             // [n_leaves] packed (i,j,k) 10 bits each
+
+    // per-instance geometry (grown on demand)
+    int inst_cap = 0;
+    float* d_corners = nullptr;   // [inst][n_leaves][24]
+    float4* d_aabb = nullptr;     // [inst][n_nodes][2] (lo, hi)
+    float4* d_pose = nullptr;     // [inst] (kappa, twist, taper, 0)
+
+    // parameters: one FP32 buffer [tables | layer 0 .. layer H | s(8)]
+    size_t n_params = 0, off_tables = 0, off_s = 0;
+    size_t off_layer[NIF_MAX_LAYERS + 1] = {0};
+    int lay_out[NIF_MAX_LAYERS] = {0}, lay_in[NIF_MAX_LAYERS] = {0};
+    float* d_params = nullptr;
+    float* d_grad = nullptr;
+    float* d_m = nullptr;
+    float* d_v = nullptr;
+    __half* d_tables_h = nullptr;       // FP16 copy of the tables
+    __nv_bfloat16* d_w_bf16 = nullptr;  // BF16 copy of the weights (layers back to back)
+    __half* d_w_f16 = nullptr;          // FP16 copy of the weights
+    bool lowp_dirty = true;
+    long adam_step = 0;
+
+    // device status word + scratch
+    int* d_status = nullptr;
+    double* d_lossacc = nullptr;        // [16] loss accumulators
+    int* d_count = nullptr;             // [4] counters
+    int* h_pinned = nullptr;            // pinned host word(s)
+
+    // grown scratch buffers (query / train)
+    struct Buf { void* p = nullptr; size_t bytes = 0; };
+    Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
+        b_scan, b_rays, b_inst, b_feat2;
+
+    std::string err;
+    int num_sms = 0;
+    double seg_per_ray = 0.0;           // measured segments per sampled training ray
+};
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+nif_status nif_fail(nif_handle* h, nif_status st, const std::string& msg);
+nif_status nif_cuda_fail(nif_handle* h, cudaError_t e, const char* what);
+nif_status nif_grow(nif_handle* h, nif_handle::Buf& b, size_t bytes);
+nif_status nif_ensure_instances(nif_handle* h, int n_inst);
+nif_status nif_upload_poses(nif_handle* h, const nif_pose* poses, int n_inst, cudaStream_t s);
+nif_status nif_refresh_lowp(nif_handle* h, cudaStream_t s);
+
+#define NIF_CK(h, call)                                                   \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return nif_cuda_fail((h), e_, #call);      \
+    } while (0)
+
+#define NIF_CK_LAUNCH(h)                                                  \
+    do {                                                                  \
+        cudaError_t e_ = cudaGetLastError();                              \
+        if (e_ != cudaSuccess) return nif_cuda_fail((h), e_, "launch");   \
+    } while (0)
+
+static inline unsigned nif_blocks(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the k_*.cu files)
+// ---------------------------------------------------------------------------
+nif_status nif_voxelize_run(nif_handle* h);
+nif_status nif_refit_run(nif_handle* h, int n_inst, cudaStream_t s);
+nif_status nif_seg_count_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
+                             int n_rays, uint32_t* counts, cudaStream_t s);
+nif_status nif_scan_run(nif_handle* h, const uint32_t* in, uint32_t* out, int n, cudaStream_t s);
+nif_status nif_seg_emit_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
+                            int n_rays, const uint32_t* offsets, nif_segment* segs, int64_t cap,
+                            cudaStream_t s);
+nif_status nif_linearize_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
+                             const nif_segment* segs, const uint32_t* n_segs_dev, int64_t n_max,
+                             nif_linseg* lin, cudaStream_t s);
+nif_status nif_encode_points_run(nif_handle* h, const float* pts, int64_t n, void* feats,
+                                 int out_dtype, int32_t* rows, cudaStream_t s);
+nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev,
+                                   int64_t n_max, void* feats, int out_dtype, int table_dtype,
+                                   cudaStream_t s);
+nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n, const float* dfeats,
+                                     float* dtables, float* dpts, cudaStream_t s);
+nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev,
+                                       int64_t n_max, const float* dfeats, float* dtables,
+                                       cudaStream_t s);
+nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
+                                float* out, float* acts, cudaStream_t s);
+nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
+                                const float* acts, const float* dout, float* dx, cudaStream_t s);
+nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev,
+                              int64_t n_max, float* out, cudaStream_t s);
+nif_status nif_labels_count_hits(nif_handle* h, const nif_label* labels, int64_t n, cudaStream_t s);
+nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin,
+                          const uint32_t* n_dev, int64_t n_max, nif_label* labels, cudaStream_t s);
+nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels,
+                        const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max, float* dout,
+                        cudaStream_t s);
+nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s);
+nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
+                               int n_rays, const uint32_t* offsets, const nif_segment* segs,
+                               int64_t seg_cap, const nif_linseg* lin, const float* out,
+                               nif_hit* hits, unsigned flags, cudaStream_t s);
+nif_status nif_sample_rays_run(nif_handle* h, unsigned long long seed, int stream_id, int n,
+                               nif_ray* rays, cudaStream_t s);
+nif_status nif_clamp_count_run(nif_handle* h, const uint32_t* offsets, int n_rays, int64_t cap,
+                               uint32_t* n_out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device math: deformation D = Bend o Twist o Taper about c = (0.5,0.5,0.5)
+// (FP32; kappa = NIF_KBEND * bend). Written without 1/kappa so that kappa -> 0
+// is the identity.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float nif_sinc(float u) {
+    return fabsf(u) < 1e-4f ? 1.0f - u * u * (1.0f / 6.0f) : sinf(u) / u;
+}
+__device__ __forceinline__ float nif_atanc(float u) {
+    return fabsf(u) < 1e-4f ? 1.0f - u * u * (1.0f / 3.0f) : atanf(u) / u;
+}
+
+// pose: (kappa, twist, taper)
+__device__ __forceinline__ float3 nif_deform(float3 x, float4 pose) {
+    float px = x.x - 0.5f, py = x.y - 0.5f, pz = x.z - 0.5f;
+    float s = 1.0f + pose.z * pz;                  // taper
+    float ax = s * px, ay = s * py;
+    float sa, ca;
+    sincosf(pose.y * pz, &sa, &ca);                // twist
+    float bx = ca * ax - sa * ay, by = sa * ax + ca * ay;
+    float be = pose.x * pz;                        // bend
+    float sb, cb;
+    sincosf(be, &sb, &cb);
+    float hb = 0.5f * be;
+    float X = bx * cb + pz * sinf(hb) * nif_sinc(hb);
+    float Z = pz * nif_sinc(be) - bx * sb;
+    return make_float3(X + 0.5f, by + 0.5f, Z + 0.5f);
+}
+
+__device__ __forceinline__ float3 nif_inverse(float3 y, float4 pose) {
+    float X = y.x - 0.5f, Y = y.y - 0.5f, Z = y.z - 0.5f;
+    float k = pose.x;
+    float g = 1.0f - k * X, hz = k * Z;            // inverse bend
+    float r = sqrtf(g * g + hz * hz);
+    float x = (2.0f * X - k * (X * X + Z * Z)) / (1.0f + r);
+    float z = (Z / g) * nif_atanc(hz / g);
+    float sa, ca;                                  // inverse twist
+    sincosf(pose.y * z, &sa, &ca);
+    float tx = ca * x + sa * Y, ty = -sa * x + ca * Y;
+    float s = 1.0f + pose.z * z;                   // inverse taper
+    return make_float3(tx / s + 0.5f, ty / s + 0.5f, z + 0.5f);
+}
+
+// Columns of J = dD/dx at the rest point x.
+__device__ __forceinline__ void nif_jacobian_cols(float3 x, float4 pose, float3& j0, float3& j1,
+                                                  float3& j2) {
+    float px = x.x - 0.5f, py = x.y - 0.5f, pz = x.z - 0.5f;
+    float s = 1.0f + pose.z * pz;
+    float ax = s * px, ay = s * py;
+    float sa, ca;
+    sincosf(pose.y * pz, &sa, &ca);
+    float bx = ca * ax - sa * ay, by = sa * ax + ca * ay;
+    float sb, cb;
+    sincosf(pose.x * pz, &sb, &cb);
+    float m = 1.0f - pose.x * bx;
+    // Jt = [[s,0,ta px],[0,s,ta py],[0,0,1]]
+    // Jw = [[ca,-sa,-th by],[sa,ca,th bx],[0,0,1]]
+    // Jb = [[cb,0,m sb],[0,1,0],[-sb,0,m cb]]
+    float th = pose.y, ta = pose.z;
+    // T = Jw * Jt
+    float T00 = ca * s, T01 = -sa * s, T02 = ca * ta * px - sa * ta * py - th * by;
+    float T10 = sa * s, T11 = ca * s, T12 = sa * ta * px + ca * ta * py + th * bx;
+    // J = Jb * T, with T row 2 = (0, 0, 1)
+    j0 = make_float3(cb * T00, T10, -sb * T00);
+    j1 = make_float3(cb * T01, T11, -sb * T01);
+    j2 = make_float3(cb * T02 + m * sb, T12, -sb * T02 + m * cb);
+}
+
+__device__ __forceinline__ float3 nif_cross(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ void nif_set_status(int* status, int code) {
+    atomicCAS(status, 0, code);
+}

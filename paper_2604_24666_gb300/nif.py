@@ -1,0 +1,384 @@
+"""Python binding of libnif (include/nif.h): argument marshalling only.
+
+Every function named ``nif_*`` here calls the C entry point of the same name;
+torch tensors are used only as device memory (their data pointers are passed
+through) and torch streams as CUDA streams. All computation happens in the
+library's CUDA kernels. If libnif.so is missing the import fails loudly: there
+is no CPU or eager fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnif.so")
+
+NIF_OK, NIF_ERR_ARG, NIF_ERR_CUDA, NIF_ERR_OOM, NIF_ERR_CAPACITY, NIF_ERR_TIMEOUT, NIF_ERR_NAN, NIF_ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+NIF_FP32, NIF_BF16, NIF_FP16 = 0, 1, 2
+NIF_PARAM_TABLES, NIF_PARAM_LOGVAR, NIF_PARAM_LAYER0 = 0, 1, 16
+NIF_SHADOW_ONLY = 1
+
+_STATUS = {0: "NIF_OK", -1: "NIF_ERR_ARG", -2: "NIF_ERR_CUDA", -3: "NIF_ERR_OOM", -4: "NIF_ERR_CAPACITY",
+           -5: "NIF_ERR_TIMEOUT", -6: "NIF_ERR_NAN", -7: "NIF_ERR_STATE"}
+_TORCH_DT = {NIF_FP32: torch.float32, NIF_BF16: torch.bfloat16, NIF_FP16: torch.float16}
+
+
+class NifError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nif_config(ctypes.Structure):
+    _fields_ = [("voxel_res", ctypes.c_int), ("pe_bands", ctypes.c_int), ("levels", ctypes.c_int),
+                ("feats", ctypes.c_int), ("log2_table", ctypes.c_int), ("base_res", ctypes.c_int),
+                ("growth", ctypes.c_float), ("mlp_depth", ctypes.c_int), ("mlp_width", ctypes.c_int),
+                ("n_materials", ctypes.c_int), ("precision", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("seed", ctypes.c_ulonglong)]
+
+
+class nif_mesh(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("n_verts", ctypes.c_int), ("tris", ctypes.c_void_p),
+                ("n_tris", ctypes.c_int), ("tri_albedo", ctypes.c_void_p), ("tri_material", ctypes.c_void_p)]
+
+
+class nif_pose(ctypes.Structure):
+    _fields_ = [("bend", ctypes.c_float), ("twist", ctypes.c_float), ("taper", ctypes.c_float)]
+
+
+# structured views of the 16/32-byte records, for reading results back
+SEGMENT_DTYPE = np.dtype([("ray", np.uint32), ("voxel", np.uint32), ("t0", np.float32), ("t1", np.float32)])
+LINSEG_DTYPE = np.dtype([("p0", np.float32, 3), ("p1", np.float32, 3), ("l_def", np.float32), ("l_rest", np.float32)])
+LABEL_DTYPE = np.dtype([("tpar", np.float32), ("normal", np.float32, 3), ("albedo", np.float32, 3), ("occ", np.uint8),
+                        ("material", np.uint8), ("pad", np.uint8, 2)])
+HIT_DTYPE = np.dtype([("D", np.float32), ("n", np.float32, 3), ("albedo", np.float32, 3), ("hit", np.uint8),
+                      ("material", np.uint8), ("pad", np.uint8, 2)])
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnif.so (built by paper_2604_24666_gb300.build); never falls back."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libnif.so is not built ({LIB_PATH}); run paper_2604_24666_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "nif_create": ([ctypes.POINTER(nif_config), ctypes.POINTER(nif_mesh), ctypes.POINTER(_vp)], ctypes.c_int),
+            "nif_destroy": ([_vp], None),
+            "nif_last_error": ([_vp], ctypes.c_char_p),
+            "nif_param_bytes": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+            "nif_get_params": ([_vp, ctypes.c_int, _vp, ctypes.c_size_t], ctypes.c_int),
+            "nif_set_params": ([_vp, ctypes.c_int, _vp, ctypes.c_size_t], ctypes.c_int),
+            "nif_get_grad": ([_vp, ctypes.c_int, _vp, ctypes.c_size_t], ctypes.c_int),
+            "nif_set_grad": ([_vp, ctypes.c_int, _vp, ctypes.c_size_t], ctypes.c_int),
+            "nif_zero_grad": ([_vp, _vp], ctypes.c_int),
+            "nif_reset_optimizer": ([_vp], ctypes.c_int),
+            "nif_adam_step": ([_vp, ctypes.c_float, ctypes.c_float, _vp], ctypes.c_int),
+            "nif_get_voxels": ([_vp, _vp, _vp, _vp, _i64, ctypes.POINTER(_i64)], ctypes.c_int),
+            "nif_segments": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _i64, ctypes.POINTER(_i64),
+                              _vp], ctypes.c_int),
+            "nif_linearize": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _i64, _vp, _vp], ctypes.c_int),
+            "nif_encode_points": ([_vp, _vp, _i64, _vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+            "nif_encode_segments": ([_vp, _vp, _i64, _vp, ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
+            "nif_encode_points_backward": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+            "nif_mlp_forward": ([_vp, _vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
+            "nif_mlp_backward": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+            "nif_labels": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
+            "nif_loss": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+            "nif_reconstruct": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
+                                 ctypes.c_uint, _vp], ctypes.c_int),
+            "nif_query": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, ctypes.c_uint, _vp], ctypes.c_int),
+            "nif_train_step_rays": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _i64, ctypes.c_float,
+                                     ctypes.c_float, _vp, _vp], ctypes.c_int),
+            "nif_train_step": ([_vp, _i64, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_float, ctypes.c_float, _vp, _vp,
+                                _vp], ctypes.c_int),
+            "nif_sample_rays": ([_vp, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the entry points this binding resolves (all must exist)."""
+    lib()
+    return sorted(n for n in dir(_lib) if n.startswith("nif_"))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return t
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _poses(poses):
+    p = np.ascontiguousarray(np.asarray(poses, np.float32).reshape(-1, 3))
+    arr = (nif_pose * len(p))()
+    for i, (b, t, a) in enumerate(p):
+        arr[i] = nif_pose(float(b), float(t), float(a))
+    return arr, len(p)
+
+
+def _check(h, st):
+    if st != NIF_OK:
+        msg = lib().nif_last_error(h.value if isinstance(h, ctypes.c_void_p) else h)
+        raise NifError(st, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# C-ABI functions (same names)
+# ---------------------------------------------------------------------------
+
+def make_config(net, precision=NIF_FP32, seed=0) -> nif_config:
+    return nif_config(net.voxel_res, net.pe_bands, net.levels, net.feats, net.log2_table, net.base_res,
+                      float(net.growth), net.mlp_depth, net.mlp_width, net.n_materials, int(precision), 0, int(seed))
+
+
+def nif_create(net, mesh, precision=NIF_FP32, seed=0):
+    cfg = make_config(net, precision, seed)
+    v = np.ascontiguousarray(mesh.verts, np.float32)
+    t = np.ascontiguousarray(mesh.tris, np.int32)
+    a = np.ascontiguousarray(mesh.albedo, np.float32)
+    m = np.ascontiguousarray(mesh.material, np.uint8)
+    cm = nif_mesh(v.ctypes.data, len(v), t.ctypes.data, len(t), a.ctypes.data, m.ctypes.data)
+    h = ctypes.c_void_p()
+    st = lib().nif_create(ctypes.byref(cfg), ctypes.byref(cm), ctypes.byref(h))
+    if st != NIF_OK:
+        raise NifError(st, lib().nif_last_error(None).decode())
+    return h
+
+
+def nif_destroy(h):
+    lib().nif_destroy(h)
+
+
+def nif_param_bytes(h, group) -> int:
+    n = ctypes.c_size_t()
+    _check(h, lib().nif_param_bytes(h, group, ctypes.byref(n)))
+    return n.value
+
+
+def nif_get_params(h, group) -> np.ndarray:
+    out = np.zeros(nif_param_bytes(h, group) // 4, np.float32)
+    _check(h, lib().nif_get_params(h, group, _ptr(out), out.nbytes))
+    return out
+
+
+def nif_set_params(h, group, arr):
+    a = np.ascontiguousarray(arr, np.float32).reshape(-1)
+    _check(h, lib().nif_set_params(h, group, _ptr(a), a.nbytes))
+
+
+def nif_get_grad(h, group) -> np.ndarray:
+    out = np.zeros(nif_param_bytes(h, group) // 4, np.float32)
+    _check(h, lib().nif_get_grad(h, group, _ptr(out), out.nbytes))
+    return out
+
+
+def nif_set_grad(h, group, arr):
+    a = np.ascontiguousarray(arr, np.float32).reshape(-1)
+    _check(h, lib().nif_set_grad(h, group, _ptr(a), a.nbytes))
+
+
+def nif_zero_grad(h, stream=None):
+    _check(h, lib().nif_zero_grad(h, _stream(stream)))
+
+
+def nif_reset_optimizer(h):
+    _check(h, lib().nif_reset_optimizer(h))
+
+
+def nif_adam_step(h, lr_grid, lr_mlp, stream=None):
+    _check(h, lib().nif_adam_step(h, lr_grid, lr_mlp, _stream(stream)))
+
+
+def nif_get_voxels(h, N):
+    occ = np.zeros(N ** 3, np.uint8)
+    ptr = np.zeros(N ** 3 + 1, np.int64)
+    n = _i64()
+    _check(h, lib().nif_get_voxels(h, _ptr(occ), _ptr(ptr), None, 0, ctypes.byref(n)))
+    idx = np.zeros(max(n.value, 1), np.int32)
+    _check(h, lib().nif_get_voxels(h, _ptr(occ), _ptr(ptr), _ptr(idx), n.value, None))
+    return occ, ptr, idx[:n.value]
+
+
+def nif_segments(h, poses, rays, inst_offsets=None, seg_cap=None, stream=None):
+    """rays: cuda float32 [n, 8]. Returns (ray_offsets [n+1] int32-as-uint32, segs [S, 4] raw)."""
+    p, n_inst = _poses(poses)
+    n = rays.shape[0]
+    offs = torch.zeros(n + 1, dtype=torch.int32, device=rays.device)
+    if seg_cap is None:      # count-only pass first
+        total = _i64()
+        _check(h, lib().nif_segments(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), n, _ptr(offs), None, 0,
+                                     ctypes.byref(total), _stream(stream)))
+        seg_cap = max(1, total.value)
+    segs = torch.zeros((seg_cap, 4), dtype=torch.int32, device=rays.device)
+    total = _i64()
+    _check(h, lib().nif_segments(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), n, _ptr(offs), _ptr(segs), seg_cap,
+                                 ctypes.byref(total), _stream(stream)))
+    return offs, segs[:total.value]
+
+
+def nif_linearize(h, poses, rays, segs, inst_offsets=None, stream=None):
+    p, n_inst = _poses(poses)
+    lin = torch.zeros((segs.shape[0], 8), dtype=torch.float32, device=rays.device)
+    _check(h, lib().nif_linearize(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0], _ptr(segs),
+                                  segs.shape[0], _ptr(lin), _stream(stream)))
+    return lin
+
+
+def nif_encode_points(h, pts, width, out_dtype=NIF_FP32, rows=False, n_terms=None, levels=None, stream=None):
+    n = pts.shape[0]
+    feats = torch.zeros((n, width), dtype=_TORCH_DT[out_dtype], device=pts.device)
+    r = torch.zeros((n, n_terms * levels), dtype=torch.int32, device=pts.device) if rows else None
+    _check(h, lib().nif_encode_points(h, _ptr(pts), n, _ptr(feats), out_dtype, _ptr(r), _stream(stream)))
+    return feats, r
+
+
+def nif_encode_segments(h, lin, in_dim, out_dtype=NIF_FP32, table_dtype=NIF_FP32, stream=None):
+    feats = torch.zeros((lin.shape[0], in_dim), dtype=_TORCH_DT[out_dtype], device=lin.device)
+    _check(h, lib().nif_encode_segments(h, _ptr(lin), lin.shape[0], _ptr(feats), out_dtype, table_dtype,
+                                        _stream(stream)))
+    return feats
+
+
+def nif_encode_points_backward(h, pts, dfeats, dtables, want_dpts=True, stream=None):
+    dpts = torch.zeros_like(pts) if want_dpts else None
+    _check(h, lib().nif_encode_points_backward(h, _ptr(pts), pts.shape[0], _ptr(dfeats), _ptr(dtables), _ptr(dpts),
+                                               _stream(stream)))
+    return dpts
+
+
+def nif_mlp_forward(h, x, precision=NIF_FP32, acts=None, stream=None):
+    xdt = {torch.float32: NIF_FP32, torch.bfloat16: NIF_BF16, torch.float16: NIF_FP16}[x.dtype]
+    out = torch.zeros((x.shape[0], 16), dtype=torch.float32, device=x.device)
+    _check(h, lib().nif_mlp_forward(h, _ptr(x), xdt, x.shape[0], _ptr(out), precision, _ptr(acts), _stream(stream)))
+    return out
+
+
+def nif_mlp_backward(h, x, acts, dout, want_dx=True, stream=None):
+    dx = torch.zeros_like(x) if want_dx else None
+    _check(h, lib().nif_mlp_backward(h, _ptr(x), x.shape[0], _ptr(acts), _ptr(dout), _ptr(dx), _stream(stream)))
+    return dx
+
+
+def nif_labels(h, segs, lin, stream=None):
+    lab = torch.zeros((segs.shape[0], 8), dtype=torch.float32, device=segs.device)
+    _check(h, lib().nif_labels(h, _ptr(segs), _ptr(lin), segs.shape[0], _ptr(lab), _stream(stream)))
+    return lab
+
+
+def nif_loss(h, out, labels, lin, want_dout=True, stream=None):
+    dout = torch.zeros_like(out) if want_dout else None
+    parts = np.zeros(6, np.float64)
+    _check(h, lib().nif_loss(h, _ptr(out), _ptr(labels), _ptr(lin), out.shape[0], _ptr(dout), _ptr(parts),
+                             _stream(stream)))
+    return parts, dout
+
+
+def nif_reconstruct(h, poses, rays, ray_offsets, segs, lin, out, inst_offsets=None, flags=0, stream=None):
+    p, n_inst = _poses(poses)
+    hits = torch.zeros((rays.shape[0], 8), dtype=torch.float32, device=rays.device)
+    _check(h, lib().nif_reconstruct(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0], _ptr(ray_offsets),
+                                    _ptr(segs), _ptr(lin), _ptr(out), _ptr(hits), flags, _stream(stream)))
+    return hits
+
+
+def nif_query(h, poses, rays, inst_offsets=None, flags=0, hits=None, stream=None):
+    p, n_inst = _poses(poses)
+    if hits is None:
+        hits = torch.zeros((rays.shape[0], 8), dtype=torch.float32, device=rays.device)
+    _check(h, lib().nif_query(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0], _ptr(hits), flags,
+                              _stream(stream)))
+    return hits
+
+
+def nif_train_step_rays(h, poses, rays, n_segments, inst_offsets=None, lr_grid=1e-2, lr_mlp=1e-3, want_loss=True,
+                        stream=None):
+    p, n_inst = _poses(poses)
+    loss = np.zeros(6, np.float64) if want_loss else None
+    _check(h, lib().nif_train_step_rays(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0], n_segments,
+                                        lr_grid, lr_mlp, _ptr(loss), _stream(stream)))
+    return loss
+
+
+def nif_train_step(h, n_segments, n_poses, step_seed, lr_grid=1e-2, lr_mlp=1e-3, want_loss=True, stream=None):
+    loss = np.zeros(6, np.float64) if want_loss else None
+    poses = (nif_pose * n_poses)()
+    _check(h, lib().nif_train_step(h, n_segments, n_poses, step_seed, lr_grid, lr_mlp, poses, _ptr(loss),
+                                   _stream(stream)))
+    return loss, np.array([[q.bend, q.twist, q.taper] for q in poses], np.float32)
+
+
+def nif_sample_rays(h, step_seed, stream_id, n, device="cuda", stream=None):
+    rays = torch.zeros((n, 8), dtype=torch.float32, device=device)
+    _check(h, lib().nif_sample_rays(h, step_seed, stream_id, n, _ptr(rays), _stream(stream)))
+    return rays
+
+
+# ---------------------------------------------------------------------------
+# Convenience owner of a handle
+# ---------------------------------------------------------------------------
+
+class Nif:
+    """Owns a nif_handle for one shape and configuration (see synth.NetConfig)."""
+
+    def __init__(self, net, mesh, precision=NIF_FP32, seed=0):
+        self.net = net
+        self.h = nif_create(net, mesh, precision, seed)
+
+    def close(self):
+        if self.h is not None:
+            nif_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, tables, weights, s=None):
+        nif_set_params(self.h, NIF_PARAM_TABLES, tables)
+        for i, w in enumerate(weights):
+            nif_set_params(self.h, NIF_PARAM_LAYER0 + i, w)
+        if s is not None:
+            nif_set_params(self.h, NIF_PARAM_LOGVAR, s)
+
+    def get_params(self):
+        net = self.net
+        tables = nif_get_params(self.h, NIF_PARAM_TABLES).reshape(net.levels, 1 << net.log2_table, net.feats)
+        ws = [nif_get_params(self.h, NIF_PARAM_LAYER0 + i).reshape(o, i_)
+              for i, (o, i_) in enumerate(net.layer_shapes())]
+        s = nif_get_params(self.h, NIF_PARAM_LOGVAR)
+        return tables, ws, s
+
+    def get_grads(self):
+        net = self.net
+        tables = nif_get_grad(self.h, NIF_PARAM_TABLES).reshape(net.levels, 1 << net.log2_table, net.feats)
+        ws = [nif_get_grad(self.h, NIF_PARAM_LAYER0 + i).reshape(o, i_)
+              for i, (o, i_) in enumerate(net.layer_shapes())]
+        s = nif_get_grad(self.h, NIF_PARAM_LOGVAR)
+        return tables, ws, s

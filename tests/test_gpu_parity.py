@@ -1,0 +1,465 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs come from the seeded generators only; the oracle never sees a value
+produced by the GPU. Integer work (occupancy, triangle lists, voxel id
+sequences, hash rows, labels' hit flags and materials) must match exactly
+wherever the oracle's FP64 decision margin is clear of FP32 rounding; float
+results match within the tolerances stated next to each assertion.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2604_24666_gb300 import synth as S
+from tests.gpu_common import (LABEL_MARGIN, SEG_MARGIN, certain_rays, occupancy_biased_weights,
+                              random_tables)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nif():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_24666_gb300 import nif as N
+    N.lib()
+    return N
+
+
+@pytest.fixture(scope="module")
+def torus():
+    return S.torus_mesh()
+
+
+@pytest.fixture(scope="module")
+def ellipsoids():
+    return S.ellipsoid_union_mesh()
+
+
+def _dev():
+    return torch.device("cuda:0")
+
+
+# ---------------------------------------------------------------------------
+# Voxelization (bit-exact)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,N", [("torus", 16), ("torus", 64), ("ellipsoids", 64)])
+def test_voxelization_bit_exact(nif, torus, ellipsoids, shape, N):
+    mesh = torus if shape == "torus" else ellipsoids
+    net = S.NetConfig(voxel_res=N)
+    h = nif.Nif(net, mesh)
+    occ, ptr, idx = nif.nif_get_voxels(h.h, N)
+    oocc, optr, oidx = O.voxelize(N, mesh)
+    assert np.array_equal(occ, oocc)
+    assert np.array_equal(ptr, optr)
+    assert np.array_equal(idx, oidx)
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Segments (voxel sequences bit-exact on rays decided with margin)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("pose", [(0, 0, 0), (0.4, -0.7, 0.3), (-1.0, 1.0, -1.0), (1.0, -1.5, 1.0)])
+def test_segments_match_oracle(nif, torus, pose):
+    N = 16
+    rays_np = S.sphere_rays(3000, seed=21)
+    h = nif.Nif(S.NetConfig(voxel_res=N), torus)
+    rays = torch.from_numpy(rays_np).to(_dev())
+    offs, segs = nif.nif_segments(h.h, [pose], rays)
+    off = offs.cpu().numpy().astype(np.int64)
+    g = segs.cpu().numpy().view(nif.SEGMENT_DTYPE).reshape(-1)
+    occ, _, _ = O.voxelize(N, torus)
+    seg = O.segments(N, occ, pose, rays_np)
+    certain = seg.margin > SEG_MARGIN
+    assert certain.mean() > 0.97
+    dt = []
+    for r in np.nonzero(certain)[0]:
+        gv = g[off[r]:off[r + 1]]
+        a, b = seg.off[r], seg.off[r + 1]
+        assert np.array_equal(gv["voxel"], seg.vox[a:b]), r
+        assert np.all(gv["ray"] == r)
+        dt.append(np.abs(gv["t0"] - seg.t0[a:b]))
+        dt.append(np.abs(gv["t1"] - seg.t1[a:b]))
+    dt = np.concatenate(dt)
+    # FP32 hull corners (~5e-7) over the incidence cosine; grazing hits dominate the tail
+    assert np.median(dt) < 1e-6 and dt.max() < 1e-3, (np.median(dt), dt.max())
+    # every ray's list is sorted by (t0, voxel)
+    for r in range(len(rays_np)):
+        gv = g[off[r]:off[r + 1]]
+        assert np.all(np.diff(gv["t0"]) >= 0)
+    h.close()
+
+
+def test_segments_multi_instance(nif, torus):
+    N = 16
+    poses = S.poses(5, seed=31)
+    counts = [100, 0, 750, 1, 400]
+    rays_np = S.sphere_rays(sum(counts), seed=32)
+    inst = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    h = nif.Nif(S.NetConfig(voxel_res=N), torus)
+    rays = torch.from_numpy(rays_np).to(_dev())
+    offs, segs = nif.nif_segments(h.h, poses, rays, inst_offsets=torch.from_numpy(inst).to(_dev()))
+    off = offs.cpu().numpy().astype(np.int64)
+    g = segs.cpu().numpy().view(nif.SEGMENT_DTYPE).reshape(-1)
+    occ, _, _ = O.voxelize(N, torus)
+    n_cmp = 0
+    for i in range(5):
+        sub = rays_np[inst[i]:inst[i + 1]]
+        if not len(sub):
+            continue
+        seg = O.segments(N, occ, poses[i], sub)
+        for r in np.nonzero(seg.margin > SEG_MARGIN)[0]:
+            R = inst[i] + r
+            assert np.array_equal(g["voxel"][off[R]:off[R + 1]], seg.vox[seg.off[r]:seg.off[r + 1]])
+            n_cmp += 1
+    assert n_cmp > 1000
+    h.close()
+
+
+def test_segments_ellipsoids64(nif, ellipsoids):
+    N = 64
+    pose = (0.6, 0.9, -0.5)
+    rays_np = S.sphere_rays(600, seed=33)
+    h = nif.Nif(S.NetConfig(voxel_res=N), ellipsoids)
+    offs, segs = nif.nif_segments(h.h, [pose], torch.from_numpy(rays_np).to(_dev()))
+    off = offs.cpu().numpy().astype(np.int64)
+    g = segs.cpu().numpy().view(nif.SEGMENT_DTYPE).reshape(-1)
+    occ, _, _ = O.voxelize(N, ellipsoids)
+    seg = O.segments(N, occ, pose, rays_np)
+    certain = seg.margin > SEG_MARGIN
+    assert certain.mean() > 0.8
+    for r in np.nonzero(certain)[0]:
+        assert np.array_equal(g["voxel"][off[r]:off[r + 1]], seg.vox[seg.off[r]:seg.off[r + 1]]), r
+    h.close()
+
+
+def test_empty_and_missing_rays(nif, torus):
+    h = nif.Nif(S.NetConfig(voxel_res=16), torus)
+    rays = torch.zeros((0, 8), dtype=torch.float32, device=_dev())
+    offs, segs = nif.nif_segments(h.h, [(0, 0, 0)], rays)
+    assert offs.shape[0] == 1 and int(offs[0]) == 0 and segs.shape[0] == 0
+    # rays pointing away from the cube: no segments, no hits
+    r = S.sphere_rays(64, seed=3)
+    r[:, 3:6] *= -1
+    rays = torch.from_numpy(r).to(_dev())
+    offs, segs = nif.nif_segments(h.h, [(0.2, 0.2, 0.2)], rays)
+    assert int(offs[-1]) == 0
+    hits = nif.nif_query(h.h, [(0.2, 0.2, 0.2)], rays).cpu().numpy().view(nif.HIT_DTYPE).reshape(-1)
+    assert not hits["hit"].any() and np.all(np.isinf(hits["D"]))
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Linearization
+# ---------------------------------------------------------------------------
+def test_linearize_matches_oracle(nif, torus):
+    N = 16
+    pose = (0.8, -1.2, 0.6)
+    rays_np = S.sphere_rays(1000, seed=41)
+    keep = certain_rays(N, torus, pose, rays_np)
+    rays_np = rays_np[keep]
+    h = nif.Nif(S.NetConfig(voxel_res=N), torus)
+    rays = torch.from_numpy(rays_np).to(_dev())
+    offs, segs = nif.nif_segments(h.h, [pose], rays)
+    lin = nif.nif_linearize(h.h, [pose], rays, segs).cpu().numpy().view(nif.LINSEG_DTYPE).reshape(-1)
+    occ, _, _ = O.voxelize(N, torus)
+    seg = O.segments(N, occ, pose, rays_np)
+    p0, p1, ld, lr = O.linearize(pose, rays_np, seg)
+    assert len(lin) == len(seg)
+    # t errors (<= ~1e-4 on grazing faces) times |dD^-1/dx| (<= ~2)
+    np.testing.assert_allclose(lin["p0"], p0, atol=5e-4)
+    np.testing.assert_allclose(lin["p1"], p1, atol=5e-4)
+    assert np.median(np.abs(lin["p0"] - p0)) < 2e-6
+    np.testing.assert_allclose(lin["l_def"], ld, atol=5e-4)
+    np.testing.assert_allclose(lin["l_rest"], lr, atol=1e-3)
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Encoding
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("levels,log2T", [(8, 14), (16, 19)])
+def test_encode_points_rows_and_features(nif, torus, levels, log2T):
+    net = S.NetConfig(levels=levels, log2_table=log2T)
+    h = nif.Nif(net, torus)
+    tables = random_tables(net, 51)
+    h.set_params(tables, S.init_params(net)[1])
+    rng = np.random.default_rng(52)
+    pts = rng.uniform(-0.05, 1.05, (3000, 3)).astype(np.float32)
+    pts[:8] = [[0, 0, 0], [1, 1, 1], [0.5, 0.5, 0.5], [1, 0, 1], [0.25, 0.75, 0.125], [0.999999, 0, 0.5],
+               [1e-7, 0.5, 1], [0.5, 1, 0]]
+    width = net.n_terms * levels * 2
+    f, rows = nif.nif_encode_points(h.h, torch.from_numpy(pts).to(_dev()), width, rows=True,
+                                    n_terms=net.n_terms, levels=levels)
+    f = f.cpu().numpy().reshape(len(pts), net.n_terms, levels, 2)
+    rows = rows.cpu().numpy().reshape(len(pts), net.n_terms, levels)
+    ref = O.encode_points(net, tables, pts.astype(np.float64)).reshape(len(pts), net.n_terms, levels, 2)
+    _, u = O.gamma(net, pts.astype(np.float64))
+    res = O.level_res(net)
+    mism = 0
+    for t in range(net.n_terms):
+        for l in range(levels):
+            i0, w = O._cell(net, l, u[:, t])
+            orow = O.grid_index(net, l, i0)
+            if t == 0:
+                # identical float32 u on both sides: bit-exact rows
+                assert np.array_equal(rows[:, t, l], orow), (t, l)
+            else:
+                # u = (sin+1)/2 differs by a few ulps: rows differ only at cell faces
+                bad = rows[:, t, l] != orow
+                q = (u[:, t] * res[l])
+                near = np.abs(q - np.round(q)).min(axis=1) < 2e-6 * res[l] + 1e-6
+                assert np.all(near[bad]), (t, l)
+                mism += bad.sum()
+            du = 0.0 if t == 0 else 4e-7
+            tol = 2e-6 + 8 * res[l] * du * 2
+            np.testing.assert_allclose(f[:, t, l], ref[:, t, l], atol=tol, rtol=0)
+    assert mism < 0.001 * rows.size
+    h.close()
+
+
+def test_encode_points_backward(nif, torus):
+    net = S.NetConfig(levels=8, log2_table=12)
+    h = nif.Nif(net, torus)
+    tables = random_tables(net, 61)
+    h.set_params(tables, S.init_params(net)[1])
+    rng = np.random.default_rng(62)
+    pts = rng.uniform(0.02, 0.98, (2000, 3)).astype(np.float32)
+    width = net.n_terms * net.levels * 2
+    df = rng.normal(size=(len(pts), width)).astype(np.float32)
+    dtab = torch.zeros((net.levels, 1 << net.log2_table, 2), dtype=torch.float32, device=_dev())
+    dp = nif.nif_encode_points_backward(h.h, torch.from_numpy(pts).to(_dev()), torch.from_numpy(df).to(_dev()), dtab)
+    rt, rp = O.encode_points_backward(net, tables, pts.astype(np.float64), df.astype(np.float64))
+    g = dtab.cpu().numpy()
+    err = np.linalg.norm(g - rt) / np.linalg.norm(rt)
+    assert err < 1e-4, err
+    gp = dp.cpu().numpy()
+    errp = np.linalg.norm(gp - rp) / np.linalg.norm(rp)
+    assert errp < 1e-3, errp
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# MLP (FP32)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("depth,width,levels", [(2, 32, 8), (3, 64, 16)])
+def test_mlp_fp32_forward_backward(nif, torus, depth, width, levels):
+    net = S.NetConfig(levels=levels, log2_table=14, mlp_depth=depth, mlp_width=width)
+    h = nif.Nif(net, torus)
+    tables, ws, s = S.init_params(net, seed=71)
+    h.set_params(tables, ws, s)
+    rng = np.random.default_rng(72)
+    n = 1000 + 37                       # several tiles and a ragged tail
+    x = rng.normal(size=(n, net.in_dim)).astype(np.float32)
+    xt = torch.from_numpy(x).to(_dev())
+    acts = torch.zeros((depth, n, width), dtype=torch.float32, device=_dev())
+    out = nif.nif_mlp_forward(h.h, xt, acts=acts).cpu().numpy()
+    ref, racts = O.mlp_forward(ws, x.astype(np.float64))
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(out, ref, atol=2e-5 * scale)
+    dout = rng.normal(size=(n, 16)).astype(np.float32)
+    dout[:, net.out_dim:] = 0
+    nif.nif_zero_grad(h.h)
+    dx = nif.nif_mlp_backward(h.h, xt, acts, torch.from_numpy(dout).to(_dev())).cpu().numpy()
+    torch.cuda.synchronize()
+    rdw, rdx = O.mlp_backward(ws, racts, dout.astype(np.float64))
+    np.testing.assert_allclose(dx, rdx, atol=2e-5 * np.abs(rdx).max())
+    _, gws, _ = h.get_grads()
+    for gw, rw in zip(gws, rdw):
+        np.testing.assert_allclose(gw, rw, atol=2e-5 * np.abs(rw).max() + 1e-7)
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Labels and losses
+# ---------------------------------------------------------------------------
+def _labels_inputs(nif, mesh, N, pose, n_rays, seed):
+    rays_np = S.sphere_rays(n_rays, seed=seed)
+    keep = certain_rays(N, mesh, pose, rays_np, with_labels=True)
+    return rays_np[keep]
+
+
+def test_labels_match_oracle(nif, torus):
+    N = 16
+    pose = (0.5, 1.0, -0.5)
+    rays_np = _labels_inputs(nif, torus, N, pose, 2000, 81)
+    h = nif.Nif(S.NetConfig(voxel_res=N), torus)
+    rays = torch.from_numpy(rays_np).to(_dev())
+    offs, segs = nif.nif_segments(h.h, [pose], rays)
+    lin = nif.nif_linearize(h.h, [pose], rays, segs)
+    lab = nif.nif_labels(h.h, segs, lin).cpu().numpy().view(nif.LABEL_DTYPE).reshape(-1)
+    occ, ptr, idx = O.voxelize(N, torus)
+    seg = O.segments(N, occ, pose, rays_np)
+    p0, p1, ld, lr = O.linearize(pose, rays_np, seg)
+    ref = O.labels(torus, ptr, idx, seg.vox, p0, p1)
+    assert np.array_equal(lab["occ"], ref["occ"])
+    hit = ref["occ"] == 1
+    assert hit.sum() > 200
+    assert np.array_equal(lab["material"][hit], ref["material"][hit])
+    np.testing.assert_allclose(lab["tpar"][hit], ref["tpar"][hit], atol=2e-3)
+    np.testing.assert_allclose(lab["normal"][hit], ref["normal"][hit], atol=1e-5)
+    np.testing.assert_allclose(lab["albedo"][hit], ref["albedo"][hit], atol=0)
+    h.close()
+
+
+def test_loss_matches_oracle(nif, torus):
+    net = S.NetConfig()
+    h = nif.Nif(net, torus)
+    rng = np.random.default_rng(91)
+    n = 3001
+    out = rng.normal(size=(n, 16)).astype(np.float32)
+    out[:, 12:] = 0
+    occ = (rng.random(n) < 0.4).astype(np.uint8)
+    nrm = rng.normal(size=(n, 3)); nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    lab = np.zeros(n, dtype=nif.LABEL_DTYPE)
+    lab["tpar"] = rng.uniform(0, 1, n)
+    lab["normal"] = nrm
+    lab["albedo"] = rng.uniform(0, 1, (n, 3))
+    lab["occ"] = occ
+    lab["material"] = rng.integers(0, 4, n)
+    lin = np.zeros(n, dtype=nif.LINSEG_DTYPE)
+    lin["l_rest"] = rng.uniform(0.2, 1.5, n) / net.voxel_res
+    s = np.array([0.3, -0.2, 0.1, 0.5, -0.4], np.float32)
+    h.set_params(*S.init_params(net)[:2], s)
+    nif.nif_zero_grad(h.h)
+    labt = torch.from_numpy(lab.view(np.float32).reshape(n, 8).copy()).to(_dev())
+    lint = torch.from_numpy(lin.view(np.float32).reshape(n, 8).copy()).to(_dev())
+    parts, dout = nif.nif_loss(h.h, torch.from_numpy(out).to(_dev()), labt, lint)
+    ds = h.get_grads()[2]
+    rl = dict(occ=lab["occ"], tpar=lab["tpar"].astype(np.float64), normal=lab["normal"].astype(np.float64),
+              albedo=lab["albedo"].astype(np.float64), material=lab["material"])
+    tot, rparts, rdout, rds = O.loss(net, out.astype(np.float64), rl, s.astype(np.float64),
+                                     lin["l_rest"].astype(np.float64))
+    np.testing.assert_allclose(parts[1:], rparts, rtol=1e-5)
+    assert abs(parts[0] - tot) < 1e-5 * max(1, abs(tot))
+    np.testing.assert_allclose(dout.cpu().numpy(), rdout, atol=1e-5 * np.abs(rdout).max())
+    np.testing.assert_allclose(ds[:5], rds, atol=1e-5)
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Whole query
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("pose", [(0, 0, 0), (0.6, -1.0, 0.4)])
+def test_query_fp32_matches_oracle(nif, torus, pose):
+    net = S.NetConfig()
+    h = nif.Nif(net, torus)
+    tables = random_tables(net, 101)
+    ws, s = occupancy_biased_weights(net, 102)
+    h.set_params(tables, ws, s)
+    rays_np = S.sphere_rays(1500, seed=103)
+    keep = certain_rays(net.voxel_res, torus, pose, rays_np)
+    rays_np = rays_np[keep]
+    hits = nif.nif_query(h.h, [pose], torch.from_numpy(rays_np).to(_dev())).cpu().numpy()
+    hits = hits.view(nif.HIT_DTYPE).reshape(-1)
+    occ, _, _ = O.voxelize(net.voxel_res, torus)
+    seg = O.segments(net.voxel_res, occ, pose, rays_np)
+    p0, p1, ld, lr = O.linearize(pose, rays_np, seg)
+    out = O.mlp_forward(ws, O.encode_segments(net, tables, p0, p1))[0]
+    res = O.reconstruct(net, pose, rays_np, seg, out, p0, p1, ld, lr)
+    n_cmp = 0
+    for r in range(len(rays_np)):
+        a, b = seg.off[r], seg.off[r + 1]
+        if np.any(np.abs(out[a:b, 0]) < 1e-3):
+            continue                                # occupancy decision too close to call
+        assert hits["hit"][r] == res["hit"][r], r
+        if res["hit"][r]:
+            j = a + res["k"][r]
+            if np.abs(out[j, 8:12] - out[j, 8:12].max()).__lt__(1e-3).sum() == 1:
+                assert hits["material"][r] == res["material"][r]
+            assert abs(hits["D"][r] - res["D"][r]) < 2e-4, (r, hits["D"][r], res["D"][r])
+            np.testing.assert_allclose(hits["albedo"][r], res["albedo"][r], atol=1e-4)
+            assert np.dot(hits["n"][r], res["normal"][r]) > np.cos(np.radians(0.05))
+        n_cmp += 1
+    assert n_cmp > 800
+    assert hits["hit"].sum() > 100
+    h.close()
+
+
+# ---------------------------------------------------------------------------
+# Gradients of a training batch and Adam
+# ---------------------------------------------------------------------------
+def test_train_gradients_match_oracle(nif, torus):
+    net = S.NetConfig()
+    N = net.voxel_res
+    pose = (0.3, -0.6, 0.5)
+    rays_np = _labels_inputs(nif, torus, N, pose, 1500, 111)
+    h = nif.Nif(net, torus)
+    tables = random_tables(net, 112, scale=0.5)
+    tables0, ws, s = S.init_params(net, seed=113)
+    s = np.array([0.1, -0.1, 0.2, 0.0, 0.3], np.float32)
+    h.set_params(tables, ws, s)
+    rays = torch.from_numpy(rays_np).to(_dev())
+    offs, segs = nif.nif_segments(h.h, [pose], rays)
+    lin = nif.nif_linearize(h.h, [pose], rays, segs)
+    lab = nif.nif_labels(h.h, segs, lin)
+    feat = nif.nif_encode_segments(h.h, lin, net.in_dim)
+    n = feat.shape[0]
+    acts = torch.zeros((net.mlp_depth, n, net.mlp_width), dtype=torch.float32, device=_dev())
+    out = nif.nif_mlp_forward(h.h, feat, acts=acts)
+    nif.nif_zero_grad(h.h)
+    parts, dout = nif.nif_loss(h.h, out, lab, lin)
+    dx = nif.nif_mlp_backward(h.h, feat, acts, dout)
+    P = net.n_terms * net.levels * 2
+    linn = lin.view(n, 8)
+    pts = torch.cat([linn[:, 0:3], linn[:, 3:6]], 0).contiguous()
+    dfe = torch.cat([dx[:, :P], dx[:, P:]], 0).contiguous()
+    dtab = torch.zeros((net.levels, 1 << net.log2_table, 2), dtype=torch.float32, device=_dev())
+    nif.nif_encode_points_backward(h.h, pts, dfe, dtab, want_dpts=False)
+    torch.cuda.synchronize()
+    _, gws, gs = h.get_grads()
+
+    occ, ptr, idx = O.voxelize(N, torus)
+    seg = O.segments(N, occ, pose, rays_np)
+    p0, p1, ld, lr = O.linearize(pose, rays_np, seg)
+    rlab = O.labels(torus, ptr, idx, seg.vox, p0, p1)
+    x = O.encode_segments(net, tables, p0, p1)
+    o, racts = O.mlp_forward(ws, x)
+    tot, rparts, rdout, rds = O.loss(net, o, rlab, s, lr)
+    rdw, rdx = O.mlp_backward(ws, racts, rdout)
+    half = P
+    rt0, _ = O.encode_points_backward(net, tables, p0, rdx[:, :half])
+    rt1, _ = O.encode_points_backward(net, tables, p1, rdx[:, half:])
+    rt = rt0 + rt1
+    assert abs(parts[0] - tot) < 1e-4 * max(1.0, abs(tot))
+
+    def rel(a, b):
+        return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+    def cos(a, b):
+        return float(np.dot(a.ravel(), b.ravel()) / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
+
+    for gw, rw in zip(gws, rdw):
+        assert rel(gw, rw) < 1e-3 and cos(gw, rw) > 0.99999, (rel(gw, rw), cos(gw, rw))
+    assert rel(dtab.cpu().numpy(), rt) < 1e-3 and cos(dtab.cpu().numpy(), rt) > 0.99999
+    np.testing.assert_allclose(gs[:5], rds, atol=1e-4)
+    h.close()
+
+
+def test_adam_matches_oracle(nif, torus):
+    net = S.NetConfig(levels=4, log2_table=10)
+    h = nif.Nif(net, torus)
+    tables, ws, s = S.init_params(net, seed=121)
+    s = np.array([0.1, 0.2, -0.3, 0.4, 0.0], np.float32)
+    h.set_params(tables, ws, s)
+    rng = np.random.default_rng(122)
+    groups = [(nif.NIF_PARAM_TABLES, tables, 1e-2), (nif.NIF_PARAM_LOGVAR, s, 1e-2)] + \
+             [(nif.NIF_PARAM_LAYER0 + i, w, 1e-3) for i, w in enumerate(ws)]
+    state = {g: (p.astype(np.float64).ravel(), np.zeros(p.size), np.zeros(p.size)) for g, p, _ in groups}
+    for step in (1, 2, 3):
+        for g, p, lr in groups:
+            gr = (rng.normal(size=p.size) * (rng.random(p.size) < 0.5)).astype(np.float32)
+            if g == nif.NIF_PARAM_LAYER0 + len(ws) - 1:
+                gr.reshape(p.shape)[net.out_dim:] = 0
+            nif.nif_set_grad(h.h, g, gr)
+            th, m, v = state[g]
+            state[g] = O.adam(th, m, v, gr.astype(np.float64), step, lr)
+        nif.nif_adam_step(h.h, 1e-2, 1e-3)
+        torch.cuda.synchronize()
+        for g, p, lr in groups:
+            got = nif.nif_get_params(h.h, g)
+            np.testing.assert_allclose(got, state[g][0], atol=1e-6 + 1e-6 * lr * 100)
+            assert not nif.nif_get_grad(h.h, g).any()     # Adam clears the gradient
+    h.close()
