@@ -1,0 +1,391 @@
+"""Benchmark of the hot path on GB300.
+
+One step = one FP32 training step of the ellipsoid-union workload (64^3
+voxels, 16 hash levels x 2 features, T = 2^19, MLP 576-64-64-64-16):
+16 poses drawn on the device, rays sampled per pose until 2^18 ray/voxel
+segments are filled, then segments -> linearization -> labels -> encoding ->
+MLP -> losses -> backward -> Adam, all in the library's kernels. `value` is
+train samples (segments) per second over all ranks.
+
+Next to it, `query` reports neural intersection queries per second of the
+inference path (torus at 128^3, 2^22 rays, network of the 16^3 torus
+workload) in FP32 and, where built, mixed precision.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs the same per-GPU work (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "neural intersection queries/s and train samples/s on 1 GB300, mixed vs FP32, at stated error"
+TRAIN_WORKLOAD = "ellipsoids64_train"
+QUERY_WORKLOAD = "torus128_query"
+N_SEG = 1 << 18
+N_POSES = 16
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region (clocks and throttle reasons)."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# Oracle timing (the CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_train_sample(n_rays=384, seed=0):
+    """One oracle training step on a bounded sample of the training workload.
+
+    Returns (segments processed, seconds, threads)."""
+    import oracle as O
+    from paper_2604_24666_gb300 import synth as S
+    w = S.WORKLOADS[TRAIN_WORKLOAD]
+    net = w["net"]
+    mesh = S.make_mesh(w["shape"])
+    occ, ptr, idx = O.voxelize(net.voxel_res, mesh)
+    tables, ws, s = S.init_params(net)
+    pose = S.poses(1, seed=100 + seed)[0]
+    rays = S.sphere_rays(n_rays, seed=200 + seed)
+    t0 = time.perf_counter()
+    seg = O.segments(net.voxel_res, occ, pose, rays)
+    p0, p1, ld, lr = O.linearize(pose, rays, seg)
+    lab = O.labels(mesh, ptr, idx, seg.vox, p0, p1)
+    x = O.encode_segments(net, tables, p0, p1)
+    out, acts = O.mlp_forward(ws, x)
+    tot, parts, dout, ds = O.loss(net, out, lab, s, lr)
+    dws, dx = O.mlp_backward(ws, acts, dout)
+    half = net.in_dim // 2
+    dt0, _ = O.encode_points_backward(net, tables, p0, dx[:, :half])
+    dt1, _ = O.encode_points_backward(net, tables, p1, dx[:, half:])
+    z = np.zeros_like(tables, dtype=np.float64)
+    O.adam(tables.astype(np.float64), z, z, dt0 + dt1, 1, 1e-2)
+    for wi, gi in zip(ws, dws):
+        O.adam(wi.astype(np.float64), 0 * gi, 0 * gi, gi, 1, 1e-3)
+    return len(seg), time.perf_counter() - t0, O.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle as O
+    O.build()
+    for i in range(args.warmup):
+        oracle_train_sample(seed=i)
+    segs, secs = 0, 0.0
+    thr = 1
+    for i in range(args.steps):
+        n, t, thr = oracle_train_sample(seed=1000 + i)
+        segs += n
+        secs += t
+    v = segs / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "segments/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": TRAIN_WORKLOAD, "note": "FP64 oracle on the host cores; each step a bounded "
+                       "sample of 384 rays of the workload (one pose)"},
+            "cpu_baseline": {"value": v, "unit": "segments/s", "cores": thr, "kind": "oracle",
+                             "sample": f"{args.steps} steps x 384 rays (~{segs // max(args.steps, 1)} segments/step)"},
+            "e2e": {"value": v, "unit": "segments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def _stage_work(net, stage, n_seg):
+    """Algorithmic bytes or flops of one stage over n_seg segments: (amount, unit, bound)."""
+    P, L = net.n_terms, net.levels
+    gathers = 2 * P * L * 8                       # corner reads per segment
+    if stage == "encode_fwd":
+        return n_seg * (gathers * 8 + 32 + net.in_dim * 4), "bytes", "hbm"
+    if stage == "encode_bwd":
+        return n_seg * (gathers * 8 + 32 + net.in_dim * 4), "bytes", "hbm"
+    mlp = 2 * sum(o * i for (o, i) in net.layer_shapes())
+    if stage == "mlp_fwd_fp32":
+        return n_seg * mlp, "flops", "alu"
+    if stage == "mlp_bwd_fp32":
+        return n_seg * 2 * mlp, "flops", "alu"
+    return None
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_2604_24666_gb300 import build as B
+    B.build()
+    from paper_2604_24666_gb300 import nif, synth as S
+    hbm, bf16, bf16s, peak_src = _peaks()
+    w = S.WORKLOADS[TRAIN_WORKLOAD]
+    net = w["net"]
+    mesh = S.make_mesh(w["shape"])
+    h = nif.Nif(net, mesh, seed=1234 + rank)
+    stream = torch.cuda.current_stream()
+
+    # ---- device-resident training steps -------------------------------
+    seed0 = 77 + 1000003 * rank
+    for i in range(args.warmup):
+        nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + i, want_loss=False)
+    torch.cuda.synchronize()
+    nif.nif_profile(h.h, 1)
+    clk = Clocks(local) if rank == 0 else None
+    launches0 = nif.nif_kernel_launches()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + args.warmup + i, want_loss=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    ms = e0.elapsed_time(e1)
+    launches = nif.nif_kernel_launches() - launches0
+    clocks = clk.stop() if clk else None
+    prof = nif.nif_profile_read(h.h)
+    nif.nif_profile(h.h, 0)
+    ms_max = _max_over_ranks(ms, ws)
+    value = ws * args.steps * N_SEG / (ms_max / 1e3)
+    loss, _ = nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + 99999, want_loss=True)
+
+    # ---- dominant stage and its roofline -------------------------------
+    stages = {k: v for k, v in prof.items()}
+    tot_ms = sum(v[0] for v in stages.values())
+    dom = max(stages, key=lambda k: stages[k][0])
+    roof = None
+    work = _stage_work(net, dom, N_SEG)
+    if work is not None:
+        amount, unit, bound = work
+        avg_ms = stages[dom][0] / max(args.steps, 1)
+        if unit == "bytes":
+            ach = amount / (avg_ms / 1e3) / 1e9
+            roof = {"bound": bound, "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "peak_source": f"{peak_src} hbm_gbs", "traffic": None}
+        else:
+            ach = amount / (avg_ms / 1e3) / 1e12
+            roof = {"bound": bound, "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP32_PEAK_TFLOPS, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                    "traffic": None}
+    kernels = {}
+    for k, (kms, cnt) in sorted(stages.items(), key=lambda kv: -kv[1][0]):
+        ent = {"ms_per_step": kms / max(args.steps, 1), "share": kms / tot_ms if tot_ms else None}
+        wk = _stage_work(net, k, N_SEG)
+        if wk is not None:
+            amount, unit, bound = wk
+            if unit == "bytes":
+                ent["GB/s"] = amount / (ent["ms_per_step"] / 1e3) / 1e9
+                ent["frac_hbm"] = ent["GB/s"] / hbm
+            else:
+                ent["TFLOP/s"] = amount / (ent["ms_per_step"] / 1e3) / 1e12
+                ent["frac_fp32"] = ent["TFLOP/s"] / FP32_PEAK_TFLOPS
+        kernels[k] = ent
+
+    # ---- end to end through the public API, host buffers ----------------
+    n_rays_e2e = int(math.ceil(N_SEG / max(h_seg_per_ray(h, nif), 0.05) * 1.2))
+    rays_host = torch.from_numpy(S.sphere_rays(n_rays_e2e, seed=500 + rank)).pin_memory()
+    poses_e2e = S.poses(1, seed=600 + rank)
+    rays_dev = torch.empty_like(rays_host, device=dev)
+    for i in range(2):
+        rays_dev.copy_(rays_host, non_blocking=True)
+        nif.nif_train_step_rays(h.h, poses_e2e, rays_dev, N_SEG, want_loss=True)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    t0 = time.perf_counter()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for i in range(args.steps):
+        rays_dev.copy_(rays_host, non_blocking=True)
+        nif.nif_train_step_rays(h.h, poses_e2e, rays_dev, N_SEG, want_loss=True)    # loss read back to host
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = _max_over_ranks(f0.elapsed_time(f1), ws)
+    e2e = {"value": ws * args.steps * N_SEG / (e2e_ms / 1e3), "unit": "segments/s",
+           "h2d_bytes_per_step": int(rays_host.numel() * 4), "d2h_bytes_per_step": 48}
+    h.close()
+
+    # ---- inference queries ------------------------------------------------
+    query = run_query(args, nif, S, dev, rank) if not args.no_query else None
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        import oracle as O
+        O.build()
+        n, t, thr = oracle_train_sample(seed=0)
+        segs_s, secs = n, t
+        while secs < 10.0:
+            n, t, thr = oracle_train_sample(seed=int(secs * 100) + 1)
+            segs_s += n
+            secs += t
+        cpu = {"value": segs_s / secs, "unit": "segments/s", "cores": thr, "kind": "oracle",
+               "sample": f"{segs_s} segments of the training workload in {secs:.1f} s (384 rays per sample)"}
+    line = {"metric": METRIC, "value": value, "unit": "segments/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": TRAIN_WORKLOAD, "segments_per_step": N_SEG, "poses_per_step": N_POSES,
+                       "voxels": "64^3", "levels": net.levels, "table": f"2^{net.log2_table}",
+                       "mlp": "-".join(str(x) for x in [net.in_dim] + [net.mlp_width] * net.mlp_depth + [16]),
+                       "l2": "working set larger than L2 (tables, gradients, Adam state 256 MB; features 604 MB)"},
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks, "loss": list(loss) if loss is not None else None, "query": query}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def h_seg_per_ray(h, nif):
+    """Segments per ray of the training ray distribution (count through the C ABI)."""
+    rays = nif.nif_sample_rays(h.h, 4242, 0, 8192)
+    _, segs = nif.nif_segments(h.h, [(0.0, 0.0, 0.0)], rays)
+    return segs.shape[0] / 8192
+
+
+def run_query(args, nif, S, dev, rank):
+    import torch
+    w = S.WORKLOADS[QUERY_WORKLOAD]
+    net = w["net"]
+    mesh = S.make_mesh(w["shape"])
+    n = w["n_rays"]
+    rays = torch.from_numpy(S.sphere_rays(n, seed=900 + rank)).to(dev)
+    pose = S.poses(1, seed=901 + rank)
+    res = {"workload": QUERY_WORKLOAD, "rays_per_step": n}
+    for name, prec in (("fp32", nif.NIF_FP32), ("bf16", nif.NIF_BF16), ("fp16", nif.NIF_FP16)):
+        try:
+            h = nif.Nif(net, mesh, precision=prec, seed=31)
+            ws_, s_ = S.init_params(net, seed=32)[1:]
+            ws_[-1][0, :] *= 4.0
+            h.set_params(S.init_params(net, seed=32)[0], ws_, s_)
+            hits = torch.zeros((n, 8), dtype=torch.float32, device=dev)
+            for i in range(max(args.warmup, 1)):
+                nif.nif_query(h.h, pose, rays, hits=hits)
+            torch.cuda.synchronize()
+            nif.nif_profile(h.h, 1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k = max(2, args.steps // 2)
+            e0.record()
+            for i in range(k):
+                nif.nif_query(h.h, pose, rays, hits=hits)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            prof = nif.nif_profile_read(h.h)
+            nif.nif_profile(h.h, 0)
+            res[name] = {"queries_per_s": n / (ms / 1e3), "ms_per_query_batch": ms,
+                         "stages_ms": {kk: v[0] / k for kk, v in prof.items()},
+                         "hit_rate": float((hits[:, 7].view(torch.int32) & 0xff).ne(0).float().mean().item())}
+            h.close()
+        except nif.NifError as e:
+            res[name] = {"unavailable": str(e)}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--no-query", action="store_true", help="skip the inference-query measurement")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

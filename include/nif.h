@@ -306,6 +306,26 @@ nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses,
 nif_status nif_sample_rays(nif_handle* h, unsigned long long step_seed, int stream_id, int n,
                            nif_ray* rays_dev, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Number of kernels this library has enqueued since it was loaded (all
+ * handles, all threads). */
+unsigned long long nif_kernel_launches(void);
+
+/* Per-stage timing: with profiling on, every stage the handle runs is
+ * bracketed by two CUDA events on its stream (a few microseconds of
+ * overhead per stage). nif_profile(h, 1) clears the record and turns it on,
+ * nif_profile(h, 0) turns it off; both synchronise the device. */
+nif_status nif_profile(nif_handle* h, int enable);
+/* Synchronises, folds the events into per-stage sums and returns entry i:
+ * its name (copied into `name`, capacity name_cap), the summed milliseconds
+ * and the number of timed launches of the stage; *n_names (nullable) gets
+ * the number of stages. i = -1 only reports *n_names. */
+nif_status nif_profile_read(nif_handle* h, int i, char* name, int name_cap, double* ms, long* count,
+                            int* n_names);
+
 #ifdef __cplusplus
 }
 #endif

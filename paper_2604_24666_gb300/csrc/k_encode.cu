@@ -263,6 +263,7 @@ void launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, const 
 
 nif_status nif_encode_points_run(nif_handle* h, const float* pts, int64_t n, void* feats, int out_dtype,
                                  int32_t* rows, cudaStream_t s) {
+    NifProf prof_(h, "encode_points", s);
     if (n <= 0) return NIF_OK;
     const float* tab = h->d_params + h->off_tables;
     if (out_dtype == NIF_FP32) launch_points<float, float>(h, tab, pts, n, feats, rows, s);
@@ -275,6 +276,7 @@ nif_status nif_encode_points_run(nif_handle* h, const float* pts, int64_t n, voi
 
 nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
                                    void* feats, int out_dtype, int table_dtype, cudaStream_t s) {
+    NifProf prof_(h, "encode_fwd", s);
     if (n_max <= 0) return NIF_OK;
     if (table_dtype == NIF_FP16) {
         nif_status st = nif_refresh_lowp(h, s);
@@ -299,6 +301,7 @@ nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const u
 
 nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n, const float* dfeats,
                                      float* dtables, float* dpts, cudaStream_t s) {
+    NifProf prof_(h, "encode_points_bwd", s);
     if (n <= 0) return NIF_OK;
     if (dpts) NIF_CK(h, cudaMemsetAsync(dpts, 0, sizeof(float) * 3 * n, s));
     k_encode_points_bwd<<<nif_blocks(n * h->P, 256), 256, 0, s>>>(h->grid, h->d_params + h->off_tables, pts, n,
@@ -309,6 +312,7 @@ nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n,
 
 nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
                                        const float* dfeats, float* dtables, cudaStream_t s) {
+    NifProf prof_(h, "encode_bwd", s);
     if (n_max <= 0) return NIF_OK;
     unsigned g = nif_blocks(n_max * 2 * h->P, 256);
     unsigned cap = (unsigned)h->num_sms * 16;

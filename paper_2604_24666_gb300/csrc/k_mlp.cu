@@ -107,6 +107,7 @@ nif_status gemm(nif_handle* h, GemmArgs a, cudaStream_t s, int splits = 1) {
 
 nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max, float* out,
                                 float* acts, cudaStream_t s) {
+    NifProf prof_(h, "mlp_fwd_fp32", s);
     if (n_max <= 0) return NIF_OK;
     const float* in = x;
     int64_t in_ld = h->in_dim;
@@ -135,6 +136,7 @@ nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n
 
 nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
                                 const float* acts, const float* dout, float* dx, cudaStream_t s) {
+    NifProf prof_(h, "mlp_bwd_fp32", s);
     if (n_max <= 0) return NIF_OK;
     nif_status st = nif_grow(h, h->b_dout, sizeof(float) * (size_t)n_max * h->W * 2);
     if (st != NIF_OK) return st;

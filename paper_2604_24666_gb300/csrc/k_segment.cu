@@ -368,6 +368,7 @@ __global__ void __launch_bounds__(256) k_linearize(const nif_ray* __restrict__ r
 // Launchers
 // ---------------------------------------------------------------------------
 nif_status nif_refit_run(nif_handle* h, int n_inst, cudaStream_t s) {
+    NifProf prof_(h, "refit", s);
     if (h->n_leaves == 0) return NIF_OK;
     int64_t nl = (int64_t)h->n_leaves * n_inst;
     k_refit_leaves<<<nif_blocks(nl, 128), 128, 0, s>>>(h->N, h->n_leaves, h->n_nodes, n_inst, h->d_leaf_lat,
@@ -395,6 +396,7 @@ static TreeView tree_view(nif_handle* h) {
 
 nif_status nif_seg_count_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
                              uint32_t* counts, cudaStream_t s) {
+    NifProf prof_(h, "seg_count", s);
     if (n_rays <= 0) return NIF_OK;
     if (h->n_leaves == 0) {
         NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n_rays, s));
@@ -409,6 +411,7 @@ nif_status nif_seg_count_run(nif_handle* h, const nif_ray* rays, const int* inst
 
 nif_status nif_seg_emit_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
                             const uint32_t* offsets, nif_segment* segs, int64_t cap, cudaStream_t s) {
+    NifProf prof_(h, "seg_emit", s);
     if (n_rays <= 0 || h->n_leaves == 0) return NIF_OK;
     k_seg_traverse<true><<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, tree_view(h),
                                                                  h->d_corners, h->d_aabb, nullptr, offsets, segs,
@@ -418,6 +421,7 @@ nif_status nif_seg_emit_run(nif_handle* h, const nif_ray* rays, const int* inst_
 }
 
 nif_status nif_scan_run(nif_handle* h, const uint32_t* in, uint32_t* out, int n, cudaStream_t s) {
+    NifProf prof_(h, "scan", s);
     int nb = (int)nif_blocks(n, kScanB);
     nif_status st = nif_grow(h, h->b_scan, sizeof(uint32_t) * (size_t)(nb + 1));
     if (st != NIF_OK) return st;
@@ -445,6 +449,7 @@ nif_status nif_clamp_count_run(nif_handle* h, const uint32_t* offsets, int n_ray
 nif_status nif_linearize_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
                              const nif_segment* segs, const uint32_t* n_dev, int64_t n_max, nif_linseg* lin,
                              cudaStream_t s) {
+    NifProf prof_(h, "linearize", s);
     if (n_max <= 0) return NIF_OK;
     unsigned g = nif_blocks(n_max, 256);
     unsigned cap = (unsigned)h->num_sms * 8;

@@ -341,6 +341,7 @@ nif_status nif_labels_count_hits(nif_handle* h, const nif_label* labels, int64_t
 
 nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const uint32_t* n_dev,
                           int64_t n_max, nif_label* labels, cudaStream_t s) {
+    NifProf prof_(h, "labels", s);
     if (n_max <= 0) return NIF_OK;
     NIF_CK(h, cudaMemsetAsync(h->d_count, 0, sizeof(int), s));
     unsigned g = nif_blocks(n_max, 256);
@@ -354,6 +355,7 @@ nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_lins
 
 nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels, const nif_linseg* lin,
                         const uint32_t* n_dev, int64_t n_max, float* dout, cudaStream_t s) {
+    NifProf prof_(h, "loss", s);
     NIF_CK(h, cudaMemsetAsync(h->d_lossacc, 0, sizeof(double) * 16, s));
     if (n_max > 0) {
         unsigned g = nif_blocks(n_max, 256);
@@ -370,6 +372,7 @@ nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels
 }
 
 nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s) {
+    NifProf prof_(h, "adam", s);
     h->adam_step++;
     double c1 = 1.0 / (1.0 - pow(0.9, (double)h->adam_step));
     double c2 = 1.0 / (1.0 - pow(0.99, (double)h->adam_step));
@@ -387,6 +390,7 @@ nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* in
                                const uint32_t* offsets, const nif_segment* segs, int64_t seg_cap,
                                const nif_linseg* lin, const float* out, nif_hit* hits, unsigned flags,
                                cudaStream_t s) {
+    NifProf prof_(h, "reconstruct", s);
     if (n_rays <= 0) return NIF_OK;
     k_reconstruct<<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, h->d_pose, offsets, segs,
                                                           lin, out, seg_cap, h->N, h->cfg.n_materials, hits, flags);
@@ -396,6 +400,7 @@ nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* in
 
 nif_status nif_sample_rays_run(nif_handle* h, unsigned long long seed, int stream_id, int n, nif_ray* rays,
                                cudaStream_t s) {
+    NifProf prof_(h, "sample_rays", s);
     if (n <= 0) return NIF_OK;
     k_sample_rays<<<nif_blocks(n, 256), 256, 0, s>>>(seed, stream_id, n, rays);
     NIF_CK_LAUNCH(h);

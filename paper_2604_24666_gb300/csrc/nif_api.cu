@@ -9,7 +9,76 @@
 
 #include "nif_internal.cuh"
 
+#include <atomic>
+
 static thread_local std::string g_create_err;
+static std::atomic<unsigned long long> g_launches{0};
+
+void nif_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" unsigned long long nif_kernel_launches(void) { return g_launches.load(); }
+
+NifProf::NifProf(nif_handle* h_, const char* name, cudaStream_t s_) : h(h_), s(s_) {
+    if (!h || !h->prof) return;
+    if (h->prof_used + 2 > h->prof_pool.size()) {
+        for (int i = 0; i < 64; i++) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            h->prof_pool.push_back(e);
+        }
+    }
+    nif_handle::ProfRec r{name, h->prof_pool[h->prof_used], h->prof_pool[h->prof_used + 1]};
+    h->prof_used += 2;
+    cudaEventRecord(r.a, s);
+    rec = h->prof_recs.size();
+    h->prof_recs.push_back(r);
+}
+
+NifProf::~NifProf() {
+    if (rec != (size_t)-1) cudaEventRecord(h->prof_recs[rec].b, s);
+}
+
+extern "C" nif_status nif_profile(nif_handle* h, int enable) {
+    if (!h) return NIF_ERR_ARG;
+    NIF_CK(h, cudaDeviceSynchronize());
+    h->prof = enable != 0;
+    h->prof_recs.clear();
+    h->prof_used = 0;
+    h->prof_sum.clear();
+    return NIF_OK;
+}
+
+// fold the recorded events into per-name sums (synchronises)
+static nif_status prof_fold(nif_handle* h) {
+    NIF_CK(h, cudaDeviceSynchronize());
+    for (auto& r : h->prof_recs) {
+        float ms = 0.f;
+        NIF_CK(h, cudaEventElapsedTime(&ms, r.a, r.b));
+        bool found = false;
+        for (auto& p : h->prof_sum)
+            if (p.first == r.name) { p.second.first += ms; p.second.second += 1; found = true; break; }
+        if (!found) h->prof_sum.push_back({r.name, {(double)ms, 1L}});
+    }
+    h->prof_recs.clear();
+    h->prof_used = 0;
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_profile_read(nif_handle* h, int i, char* name, int name_cap, double* ms, long* count,
+                                       int* n_names) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = prof_fold(h);
+    if (st != NIF_OK) return st;
+    if (n_names) *n_names = (int)h->prof_sum.size();
+    if (i < 0 || i >= (int)h->prof_sum.size()) return i == -1 ? NIF_OK : NIF_ERR_ARG;
+    if (name && name_cap > 0) {
+        std::strncpy(name, h->prof_sum[i].first.c_str(), name_cap - 1);
+        name[name_cap - 1] = 0;
+    }
+    if (ms) *ms = h->prof_sum[i].second.first;
+    if (count) *count = h->prof_sum[i].second.second;
+    return NIF_OK;
+}
 
 nif_status nif_fail(nif_handle* h, nif_status st, const std::string& msg) {
     if (h) h->err = msg;
@@ -356,6 +425,7 @@ extern "C" void nif_destroy(nif_handle* h) {
     for (auto* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    for (auto e : h->prof_pool) cudaEventDestroy(e);
     delete h;
 }
 
@@ -655,17 +725,28 @@ extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst
     if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, total, lin, s)) != NIF_OK) return st;
     int prec = h->cfg.precision;
     size_t esz = prec == NIF_FP32 ? 4 : 2;
-    if ((st = nif_grow(h, h->b_feat, esz * (size_t)h->in_dim * n)) != NIF_OK) return st;
-    if (prec == NIF_FP32) {
-        if ((st = nif_encode_segments_run(h, lin, n_dev, total, h->b_feat.p, NIF_FP32, NIF_FP32, s)) != NIF_OK)
-            return st;
-        if ((st = nif_grow(h, h->b_acts, sizeof(float) * (size_t)n * h->W * h->H)) != NIF_OK) return st;
-        if ((st = nif_mlp_fwd_fp32_run(h, (const float*)h->b_feat.p, n_dev, total, out, (float*)h->b_acts.p, s)) !=
-            NIF_OK)
-            return st;
-    } else {
-        if ((st = nif_encode_segments_run(h, lin, n_dev, total, h->b_feat.p, prec, NIF_FP16, s)) != NIF_OK) return st;
-        if ((st = nif_mlp_fwd_tc_run(h, h->b_feat.p, prec, n_dev, total, out, s)) != NIF_OK) return st;
+    // encode + MLP in chunks whose feature rows stay resident in L2 between
+    // the two kernels (about 48 MB of features per chunk)
+    int64_t chunk = std::max<int64_t>(4096, ((int64_t)48 << 20) / ((int64_t)esz * h->in_dim));
+    chunk = std::min<int64_t>(chunk, n);
+    if ((st = nif_grow(h, h->b_feat, esz * (size_t)h->in_dim * chunk)) != NIF_OK) return st;
+    if (prec == NIF_FP32 &&
+        (st = nif_grow(h, h->b_acts, sizeof(float) * (size_t)chunk * h->W * h->H)) != NIF_OK)
+        return st;
+    for (int64_t c0 = 0; c0 < total; c0 += chunk) {
+        int64_t len = std::min(chunk, total - c0);
+        if (prec == NIF_FP32) {
+            if ((st = nif_encode_segments_run(h, lin + c0, nullptr, len, h->b_feat.p, NIF_FP32, NIF_FP32, s)) != NIF_OK)
+                return st;
+            if ((st = nif_mlp_fwd_fp32_run(h, (const float*)h->b_feat.p, nullptr, len, out + c0 * NIF_OUT,
+                                           (float*)h->b_acts.p, s)) != NIF_OK)
+                return st;
+        } else {
+            if ((st = nif_encode_segments_run(h, lin + c0, nullptr, len, h->b_feat.p, prec, NIF_FP16, s)) != NIF_OK)
+                return st;
+            if ((st = nif_mlp_fwd_tc_run(h, h->b_feat.p, prec, nullptr, len, out + c0 * NIF_OUT, s)) != NIF_OK)
+                return st;
+        }
     }
     return nif_reconstruct_run(h, rays, inst_off, n_inst, n_rays, offs, segs, total, lin, out, hits, flags, s);
 }

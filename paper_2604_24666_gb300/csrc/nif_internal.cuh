@@ -99,6 +99,27 @@ struct nif_handle {
     std::string err;
     int num_sms = 0;
     double seg_per_ray = 0.0;           // measured segments per sampled training ray
+
+    // per-kernel timing (CUDA events on the launching stream), off by default
+    struct ProfRec { const char* name; cudaEvent_t a, b; };
+    bool prof = false;
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    size_t prof_used = 0;
+    std::vector<std::pair<std::string, std::pair<double, long>>> prof_sum;
+};
+
+// Launch counter of every kernel this library enqueues (diagnostics).
+void nif_count_launch();
+
+// Scope that brackets the launches of one named stage with CUDA events when
+// the handle's profiling is on.
+struct NifProf {
+    nif_handle* h;
+    cudaStream_t s;
+    size_t rec = (size_t)-1;
+    NifProf(nif_handle* h_, const char* name, cudaStream_t s_);
+    ~NifProf();
 };
 
 // ---------------------------------------------------------------------------
@@ -119,6 +140,7 @@ nif_status nif_refresh_lowp(nif_handle* h, cudaStream_t s);
 
 #define NIF_CK_LAUNCH(h)                                                  \
     do {                                                                  \
+        nif_count_launch();                                               \
         cudaError_t e_ = cudaGetLastError();                              \
         if (e_ != cudaSuccess) return nif_cuda_fail((h), e_, "launch");   \
     } while (0)

@@ -102,6 +102,10 @@ def lib() -> ctypes.CDLL:
             "nif_train_step": ([_vp, _i64, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_float, ctypes.c_float, _vp, _vp,
                                 _vp], ctypes.c_int),
             "nif_sample_rays": ([_vp, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
+            "nif_kernel_launches": ([], ctypes.c_ulonglong),
+            "nif_profile": ([_vp, ctypes.c_int], ctypes.c_int),
+            "nif_profile_read": ([_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -336,6 +340,28 @@ def nif_sample_rays(h, step_seed, stream_id, n, device="cuda", stream=None):
     rays = torch.zeros((n, 8), dtype=torch.float32, device=device)
     _check(h, lib().nif_sample_rays(h, step_seed, stream_id, n, _ptr(rays), _stream(stream)))
     return rays
+
+
+def nif_kernel_launches() -> int:
+    return int(lib().nif_kernel_launches())
+
+
+def nif_profile(h, enable):
+    _check(h, lib().nif_profile(h, int(enable)))
+
+
+def nif_profile_read(h):
+    """{stage: (total ms, timed launches)} of the handle's profiling record."""
+    n = ctypes.c_int()
+    _check(h, lib().nif_profile_read(h, -1, None, 0, None, None, ctypes.byref(n)))
+    out = {}
+    for i in range(n.value):
+        name = ctypes.create_string_buffer(64)
+        ms = ctypes.c_double()
+        cnt = ctypes.c_long()
+        _check(h, lib().nif_profile_read(h, i, name, 64, ctypes.byref(ms), ctypes.byref(cnt), None))
+        out[name.value.decode()] = (ms.value, cnt.value)
+    return out
 
 
 # ---------------------------------------------------------------------------
