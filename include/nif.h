@@ -215,6 +215,11 @@ nif_status nif_encode_points_backward(nif_handle* h, const float* pts_dev, int64
                                       const float* dfeats_dev, float* dtables_dev,
                                       float* dpts_dev, void* stream);
 
+/* Backward of nif_encode_segments (FP32 tables): adds the table gradient of
+ * sum(dfeats * features) into dtables_dev [L][T][F_d]. */
+nif_status nif_encode_segments_backward(nif_handle* h, const nif_linseg* lin_dev, int64_t n,
+                                        const float* dfeats_dev, float* dtables_dev, void* stream);
+
 /* MLP forward (Sec. 2, Fig. 2d): H ReLU layers without bias and a linear
  * output layer; out_dev [n][16] FP32. x_dev [n][in_dim] of x_dtype.
  * precision NIF_FP32 runs FP32 FFMA; NIF_BF16 / NIF_FP16 run tcgen05 tensor

@@ -244,6 +244,66 @@ __global__ void __launch_bounds__(256) k_encode_segments_bwd(GridInfo g, const f
     }
 }
 
+// Backward with the dense coarse levels 0..Lc-1 accumulated in shared memory
+// by each persistent block and flushed once; finer levels use global float2
+// reductions. soff[l] is the float offset of level l's block in shared memory.
+struct Coarse {
+    int Lc;
+    int soff[NIF_MAX_LEVELS + 1];
+};
+
+__global__ void __launch_bounds__(1024) k_encode_segments_bwd_sm(GridInfo g, Coarse cs,
+                                                                 const nif_linseg* __restrict__ lin,
+                                                                 const uint32_t* __restrict__ n_dev, int64_t n_max,
+                                                                 const float* __restrict__ dfeats,
+                                                                 float* __restrict__ dtab) {
+    extern __shared__ float sacc[];
+    int nsh = cs.soff[cs.Lc];
+    for (int i = threadIdx.x; i < nsh; i += blockDim.x) sacc[i] = 0.f;
+    __syncthreads();
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    int per = 2 * g.P;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n * per;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = gid / per;
+        int r = (int)(gid - s * per);
+        int e = r >= g.P;
+        int t = r - e * g.P;
+        const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+        float3 u = term_u(clamp01(make_float3(L[0], L[1], L[2])), t);
+        const float* df = dfeats + gid * g.L * 2;
+        for (int l = 0; l < g.L; l++) {
+            int Nl = g.res[l];
+            bool dense = (g.dense_mask >> l) & 1u;
+            Cell c = cell_of(u, Nl);
+            float2 gr = *reinterpret_cast<const float2*>(df + 2 * l);
+            bool in_sh = l < cs.Lc;
+            float* dl = in_sh ? sacc + cs.soff[l] : dtab + (int64_t)l * g.T * 2;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                uint32_t row = grid_row(c.ix + (q & 1), c.iy + ((q >> 1) & 1), c.iz + ((q >> 2) & 1), Nl, dense, g.T);
+                float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) * ((q & 4) ? c.wz : 1.f - c.wz);
+                if (in_sh) {
+                    atomicAdd(dl + 2 * row, w * gr.x);
+                    atomicAdd(dl + 2 * row + 1, w * gr.y);
+                } else {
+                    atomicAdd(reinterpret_cast<float2*>(dl) + row, make_float2(w * gr.x, w * gr.y));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int l = 0; l < cs.Lc; l++) {
+        int cnt = cs.soff[l + 1] - cs.soff[l];
+        float* dst = dtab + (int64_t)l * g.T * 2;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            float v = sacc[cs.soff[l] + i];
+            if (v != 0.f) atomicAdd(dst + i, v);
+        }
+    }
+}
+
 template <typename TT, typename OT>
 void launch_points(nif_handle* h, const TT* tab, const float* pts, int64_t n, void* feats, int32_t* rows,
                    cudaStream_t s) {
@@ -314,6 +374,27 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
                                        const float* dfeats, float* dtables, cudaStream_t s) {
     NifProf prof_(h, "encode_bwd", s);
     if (n_max <= 0) return NIF_OK;
+    // dense prefix of levels that fits the shared-memory budget
+    const int budget = 200 * 1024 / 4;
+    Coarse cs{};
+    cs.Lc = 0;
+    cs.soff[0] = 0;
+    for (int l = 0; l < h->L; l++) {
+        if (!((h->grid.dense_mask >> l) & 1u)) break;
+        int64_t r = (int64_t)h->grid.res[l] + 1;
+        int64_t need = r * r * r * 2;
+        if (cs.soff[l] + need > budget) break;
+        cs.soff[l + 1] = cs.soff[l] + (int)need;
+        cs.Lc = l + 1;
+    }
+    size_t smem = sizeof(float) * (size_t)cs.soff[cs.Lc];
+    if (cs.Lc > 0) {
+        NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+        k_encode_segments_bwd_sm<<<h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables);
+        NIF_CK_LAUNCH(h);
+        return NIF_OK;
+    }
     unsigned g = nif_blocks(n_max * 2 * h->P, 256);
     unsigned cap = (unsigned)h->num_sms * 16;
     if (g > cap) g = cap;

@@ -458,3 +458,4 @@ nif_status nif_linearize_run(nif_handle* h, const nif_ray* rays, const int* inst
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
+

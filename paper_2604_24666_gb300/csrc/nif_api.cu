@@ -602,6 +602,12 @@ extern "C" nif_status nif_encode_points_backward(nif_handle* h, const float* pts
     return nif_encode_points_bwd_run(h, pts, n, dfeats, dtables, dpts, (cudaStream_t)stream);
 }
 
+extern "C" nif_status nif_encode_segments_backward(nif_handle* h, const nif_linseg* lin, int64_t n,
+                                                   const float* dfeats, float* dtables, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!lin || !dfeats || !dtables))) return NIF_ERR_ARG;
+    return nif_encode_segments_bwd_run(h, lin, nullptr, n, dfeats, dtables, (cudaStream_t)stream);
+}
+
 extern "C" nif_status nif_mlp_forward(nif_handle* h, const void* x, int x_dtype, int64_t n, float* out,
                                       int precision, float* acts, void* stream) {
     if (!h || n < 0 || (n > 0 && (!x || !out))) return NIF_ERR_ARG;

@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "nif_encode_points": ([_vp, _vp, _i64, _vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
             "nif_encode_segments": ([_vp, _vp, _i64, _vp, ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
             "nif_encode_points_backward": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+            "nif_encode_segments_backward": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
             "nif_mlp_forward": ([_vp, _vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
             "nif_mlp_backward": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
             "nif_labels": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
@@ -273,6 +274,11 @@ def nif_encode_points_backward(h, pts, dfeats, dtables, want_dpts=True, stream=N
     _check(h, lib().nif_encode_points_backward(h, _ptr(pts), pts.shape[0], _ptr(dfeats), _ptr(dtables), _ptr(dpts),
                                                _stream(stream)))
     return dpts
+
+
+def nif_encode_segments_backward(h, lin, dfeats, dtables, stream=None):
+    _check(h, lib().nif_encode_segments_backward(h, _ptr(lin), lin.shape[0], _ptr(dfeats), _ptr(dtables),
+                                                 _stream(stream)))
 
 
 def nif_mlp_forward(h, x, precision=NIF_FP32, acts=None, stream=None):

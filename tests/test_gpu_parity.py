@@ -408,7 +408,12 @@ def test_train_gradients_match_oracle(nif, torus):
     dfe = torch.cat([dx[:, :P], dx[:, P:]], 0).contiguous()
     dtab = torch.zeros((net.levels, 1 << net.log2_table, 2), dtype=torch.float32, device=_dev())
     nif.nif_encode_points_backward(h.h, pts, dfe, dtab, want_dpts=False)
+    # the training path's segment backward (shared-memory coarse levels) gives the same gradient
+    dtab_seg = torch.zeros_like(dtab)
+    nif.nif_encode_segments_backward(h.h, lin, dx, dtab_seg)
     torch.cuda.synchronize()
+    d1, d2 = dtab.cpu().numpy(), dtab_seg.cpu().numpy()
+    assert np.linalg.norm(d1 - d2) <= 1e-5 * np.linalg.norm(d1)
     _, gws, gs = h.get_grads()
 
     occ, ptr, idx = O.voxelize(N, torus)
