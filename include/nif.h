@@ -311,6 +311,29 @@ nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses,
 nif_status nif_sample_rays(nif_handle* h, unsigned long long step_seed, int stream_id, int n,
                            nif_ray* rays_dev, void* stream);
 
+/* Allocation-free variant of nif_segments (the paper has no counterpart:
+ * this is an integration aid). For callers that cannot call cudaMalloc -- a
+ * host application that owns all device memory through its own fixed-budget
+ * allocator, or a latency-critical loop where cudaMalloc's implicit
+ * device-wide synchronisation is not allowed. Same arguments, definition and
+ * outputs as nif_segments; the caller passes every input and output buffer.
+ * Its scratch (per-ray counts and scan block sums) lives in one file-scope
+ * device array of (NIF_NOALLOC_MAX_RAYS + 2048) 32-bit words, about 4 MiB,
+ * that every GPU loading the library holds until the process exits.
+ * Limits: n_rays <= NIF_NOALLOC_MAX_RAYS and n_inst <= the number of
+ * instances the handle already holds buffers for (1 after nif_create, more
+ * after an allocating call with more instances); otherwise NIF_ERR_ARG.
+ * The first call on a device looks the array's device address up (with that
+ * device current); make that first call before any stream capture. Every
+ * call shares the one array: calls that overlap on the GPU (other streams,
+ * other handles, other threads) race and must be serialised by the caller.
+ * Blocks the host like nif_segments. */
+#define NIF_NOALLOC_MAX_RAYS (1 << 20)
+nif_status nif_segments_noalloc(nif_handle* h, const nif_pose* poses_host, int n_inst,
+                                const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
+                                uint32_t* ray_offsets_dev, nif_segment* segs_dev, int64_t seg_cap,
+                                int64_t* n_segs_host, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Diagnostics                                                               */
 /* ------------------------------------------------------------------------ */

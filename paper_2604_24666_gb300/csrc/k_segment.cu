@@ -459,3 +459,20 @@ nif_status nif_linearize_run(nif_handle* h, const nif_ray* rays, const int* inst
     return NIF_OK;
 }
 
+// Exclusive scan with caller-provided block-sum storage (at least
+// ceil(n / 1024) + 1 words); allocates nothing.
+nif_status nif_scan_run_with(nif_handle* h, const uint32_t* in, uint32_t* out, int n, uint32_t* bsum,
+                             cudaStream_t s) {
+    int nb = (int)nif_blocks(n, kScanB);
+    if (n > 0) {
+        k_scan_blocks<<<nb, kScanT, 0, s>>>(in, out, bsum, n);
+        NIF_CK_LAUNCH(h);
+    }
+    k_scan_bsum<<<1, 1024, 0, s>>>(bsum, n > 0 ? nb : 0, out + n);
+    NIF_CK_LAUNCH(h);
+    if (n > 0) {
+        k_scan_add<<<nb, kScanT, 0, s>>>(out, bsum, n);
+        NIF_CK_LAUNCH(h);
+    }
+    return NIF_OK;
+}

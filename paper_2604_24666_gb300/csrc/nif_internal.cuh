@@ -193,6 +193,8 @@ nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* in
                                nif_hit* hits, unsigned flags, cudaStream_t s);
 nif_status nif_sample_rays_run(nif_handle* h, unsigned long long seed, int stream_id, int n,
                                nif_ray* rays, cudaStream_t s);
+nif_status nif_scan_run_with(nif_handle* h, const uint32_t* in, uint32_t* out, int n, uint32_t* bsum,
+                             cudaStream_t s);
 nif_status nif_clamp_count_run(nif_handle* h, const uint32_t* offsets, int n_rays, int64_t cap,
                                uint32_t* n_out, cudaStream_t s);
 

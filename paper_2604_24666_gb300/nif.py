@@ -103,6 +103,8 @@ def lib() -> ctypes.CDLL:
             "nif_train_step": ([_vp, _i64, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_float, ctypes.c_float, _vp, _vp,
                                 _vp], ctypes.c_int),
             "nif_sample_rays": ([_vp, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
+            "nif_segments_noalloc": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _i64,
+                                      ctypes.POINTER(_i64), _vp], ctypes.c_int),
             "nif_kernel_launches": ([], ctypes.c_ulonglong),
             "nif_profile": ([_vp, ctypes.c_int], ctypes.c_int),
             "nif_profile_read": ([_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -244,6 +246,16 @@ def nif_segments(h, poses, rays, inst_offsets=None, seg_cap=None, stream=None):
     _check(h, lib().nif_segments(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), n, _ptr(offs), _ptr(segs), seg_cap,
                                  ctypes.byref(total), _stream(stream)))
     return offs, segs[:total.value]
+
+
+def nif_segments_noalloc(h, poses, rays, ray_offsets, segs, inst_offsets=None, stream=None):
+    """Allocation-free segments into the caller's ray_offsets [n+1] and segs [cap, 4]; returns the total."""
+    p, n_inst = _poses(poses)
+    total = _i64()
+    _check(h, lib().nif_segments_noalloc(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0],
+                                         _ptr(ray_offsets), _ptr(segs), segs.shape[0], ctypes.byref(total),
+                                         _stream(stream)))
+    return total.value
 
 
 def nif_linearize(h, poses, rays, segs, inst_offsets=None, stream=None):
