@@ -1,10 +1,465 @@
-// k_mlp_tc.cu -- tensor-core (tcgen05 / TMEM) MLP forward, BF16 or FP16
-// operands with FP32 accumulation.
+// k_mlp_tc.cu -- MLP forward on the 5th-generation tensor cores (tcgen05 +
+// TMEM), BF16 or FP16 operands with FP32 accumulation (Sec. 2, Fig. 2d: H
+// hidden ReLU layers without bias and a linear output layer).
+//
+// One persistent CTA per SM walks 128-row tiles of the feature matrix X
+// [n x K0]. Warp roles:
+//   warp 0     TMA producer: streams X tiles as 128 x 64-element boxes
+//              (128-byte swizzle) into a ring of shared-memory stages;
+//   warp 1     owns the TMEM accumulator and issues every tcgen05.mma from
+//              one thread: layer 0 reads the X stages, layers >= 1 read the
+//              activation tile the epilogue wrote back to shared memory;
+//   warps 2-5  epilogue: tcgen05.ld of the FP32 accumulator (each warp its
+//              32 TMEM lanes = 32 rows), ReLU, conversion to BF16/FP16 and
+//              store into the next layer's A operand; the last layer's 16
+//              outputs per row go to global memory as FP32.
+// All weights stay resident in shared memory for the whole kernel. Operands
+// use the canonical K-major layout with 128-byte swizzle: 8-row x 128-byte
+// atoms, 16-byte chunk index XOR (row mod 8), atoms 1024 bytes apart.
+// Every wait on an mbarrier is bounded in time; on expiry the kernel records
+// NIF_ERR_TIMEOUT, drains its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "nif_internal.cuh"
+
+namespace {
+
+constexpr int kRows = 128;              // MMA M and rows per tile
+constexpr int kThreads = 192;           // 6 warps
+constexpr uint32_t kStageBytes = kRows * 128;   // one 128 x 64 box of 16-bit elements
+
+struct TcLayout {
+    uint32_t x_off, w0_off, wh_off, wo_off, a_off, bar_off, total;
+    int stages;   // X ring depth
+    int nb0;      // 64-column boxes of X per tile
+    int ks0;      // 16-deep k-steps of layer 0
+    int nbw;      // 64-column blocks of a W-wide operand
+    int ksw;      // k-steps of a W-deep layer
+    uint32_t woff[NIF_MAX_LAYERS];   // element offset of each layer in the 16-bit weight copy
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: about one second of wall time, then the kernel gives up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+    if (mbar_test(bar, parity)) return true;
+    uint64_t t0 = globaltimer();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 63) == 63) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > 1000000000ull) {
+                *abort_flag = 1;
+                atomicCAS(status, 0, (int)NIF_ERR_TIMEOUT);
+                return false;
+            }
+            __nanosleep(64);
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                  // descriptor version
+    d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, A/B both BF16 (fmt 1)
+// or both FP16 (fmt 0), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc_f16(int fmt, int N) {
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(kRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row, k) of a K-major swizzled operand whose 64-column
+// blocks hold `rows` rows each
+__device__ __forceinline__ uint32_t swz_off(int row, int k, int rows) {
+    int blk = k >> 6, chunk = (k & 63) >> 3;
+    return (uint32_t)blk * (uint32_t)rows * 128u + (uint32_t)row * 128u + (uint32_t)((chunk ^ (row & 7)) << 4) +
+           (uint32_t)((k & 7) << 1);
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b, int fmt) {
+    if (fmt == 1) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&v);
+    }
+    __half2 v = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Copy a row-major [rows x K] 16-bit matrix into the swizzled K-major layout,
+// zero-filling columns K .. 64*ceil(K/64).
+__device__ void load_weight(uint8_t* dst, const uint16_t* __restrict__ src, int rows, int K, int tid, int nthr) {
+    int kpad = ((K + 63) / 64) * 64;
+    int chunks = rows * (kpad / 8);
+    for (int c = tid; c < chunks; c += nthr) {
+        int row = c / (kpad / 8), k = (c % (kpad / 8)) * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (k < K) v = *reinterpret_cast<const uint4*>(src + (size_t)row * K + k);
+        *reinterpret_cast<uint4*>(dst + swz_off(row, k, rows)) = v;
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_mlp_tc(const __grid_constant__ CUtensorMap xmap, TcLayout lay, const uint16_t* __restrict__ wts,
+             int K0, int H, int fmt, int64_t n, float* __restrict__ out, int* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte alignment of the dynamic buffer (swizzle atoms)
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int S = lay.stages;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + lay.bar_off);
+    // bars: [0,S) full, [S,2S) empty, 2S acc_full, 2S+1 act_full, 2S+2 drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + lay.bar_off + 8 * (2 * S + 4));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + lay.bar_off + 8 * (2 * S + 4) + 8);
+    const int64_t n_tiles = (n + kRows - 1) / kRows;
+
+    if (tid == 0) {
+        for (int i = 0; i < S; i++) {
+            mbar_init(smem_u32(&bars[i]), 1);
+            mbar_init(smem_u32(&bars[S + i]), 1);
+        }
+        mbar_init(smem_u32(&bars[2 * S]), 1);
+        mbar_init(smem_u32(&bars[2 * S + 1]), 128);
+        mbar_init(smem_u32(&bars[2 * S + 2]), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(W <= 32 ? 32u : (uint32_t)W)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // resident weights: layer 0 [W x K0], hidden [W x W] x (H-1), output [16 x W]
+    load_weight(sm + lay.w0_off, wts + lay.woff[0], W, K0, tid, kThreads);
+    for (int l = 1; l < H; l++)
+        load_weight(sm + lay.wh_off + (uint32_t)(l - 1) * lay.nbw * W * 128, wts + lay.woff[l], W, W, tid, kThreads);
+    load_weight(sm + lay.wo_off, wts + lay.woff[H], 16, W, tid, kThreads);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
+            int slot = 0;
+            uint32_t phase = 0;
+            uint32_t issued_parity_mask = 0, issued_mask = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                for (int b = 0; b < lay.nb0; b++) {
+                    if (!mbar_wait(smem_u32(&bars[S + slot]), phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                    uint32_t fb = smem_u32(&bars[slot]);
+                    mbar_expect_tx(fb, kStageBytes);
+                    tma_load_2d(smem_u32(sm + lay.x_off + (uint32_t)slot * kStageBytes), &xmap, b * 64,
+                                (int)(t * kRows), fb);
+                    issued_mask |= 1u << slot;
+                    issued_parity_mask = (issued_parity_mask & ~(1u << slot)) | (phase << slot);
+                    if (++slot == S) { slot = 0; phase ^= 1u; }
+                }
+            }
+            // drain: every issued copy must have landed before the CTA exits
+            for (int i = 0; i < S; i++)
+                if (issued_mask >> i & 1u) {
+                    volatile int dummy = 0;
+                    mbar_wait(smem_u32(&bars[i]), (issued_parity_mask >> i) & 1u, &dummy, status);
+                }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t id_hid = idesc_f16(fmt, W);
+            const uint32_t id_out = idesc_f16(fmt, 16);
+            int slot = 0;
+            uint32_t phase = 0, act_phase = 0;
+            bool first = true, ok = true;
+            for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                // layer 0: accumulator must be free (previous tile's output read)
+                if (!first) {
+                    if (!mbar_wait(smem_u32(&bars[2 * S + 1]), act_phase, abort_flag, status)) break;
+                    act_phase ^= 1u;
+                    tc_fence_after();
+                }
+                first = false;
+                for (int b = 0; b < lay.nb0 && ok; b++) {
+                    if (!mbar_wait(smem_u32(&bars[slot]), phase, abort_flag, status)) { ok = false; break; }
+                    tc_fence_after();
+                    uint32_t base = smem_u32(sm + lay.x_off + (uint32_t)slot * kStageBytes);
+                    uint32_t wbase = smem_u32(sm + lay.w0_off + (uint32_t)b * W * 128);
+                    for (int j = 0; j < 4; j++) {
+                        int ks = b * 4 + j;
+                        if (ks >= lay.ks0) break;
+                        mma_f16(tmem, sdesc(base + 32 * j), sdesc(wbase + 32 * j), id_hid, ks > 0 ? 1u : 0u);
+                    }
+                    mma_commit(smem_u32(&bars[S + slot]));   // frees the stage when these MMAs finish
+                    if (++slot == S) { slot = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&bars[2 * S]));
+                // layers 1..H read the activation tile written by the epilogue
+                for (int l = 1; l <= H && ok; l++) {
+                    if (!mbar_wait(smem_u32(&bars[2 * S + 1]), act_phase, abort_flag, status)) { ok = false; break; }
+                    act_phase ^= 1u;
+                    tc_fence_after();
+                    bool last = l == H;
+                    uint32_t wb = last ? smem_u32(sm + lay.wo_off)
+                                       : smem_u32(sm + lay.wh_off + (uint32_t)(l - 1) * lay.nbw * W * 128);
+                    uint32_t ab = smem_u32(sm + lay.a_off);
+                    for (int ks = 0; ks < lay.ksw; ks++) {
+                        uint32_t blk = (uint32_t)(ks >> 2), j = (uint32_t)(ks & 3);
+                        uint32_t aoff = blk * kRows * 128 + 32 * j;
+                        uint32_t boff = blk * (uint32_t)(last ? 16 : W) * 128 + 32 * j;
+                        mma_f16(tmem, sdesc(ab + aoff), sdesc(wb + boff), last ? id_out : id_hid, ks > 0 ? 1u : 0u);
+                    }
+                    mma_commit(smem_u32(&bars[2 * S]));
+                }
+            }
+            // all MMAs of this CTA complete before TMEM is released
+            mma_commit(smem_u32(&bars[2 * S + 2]));
+            volatile int dummy = 0;
+            mbar_wait(smem_u32(&bars[2 * S + 2]), 0, &dummy, status);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int q = warp & 3;                   // TMEM lane quarter this warp may access
+        const int row = q * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+        uint32_t acc_phase = 0;
+        uint8_t* A = sm + lay.a_off;
+        for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            bool ok = true;
+            for (int l = 0; l <= H; l++) {
+                int got = 0;
+                if (lane == 0) got = mbar_wait(smem_u32(&bars[2 * S]), acc_phase, abort_flag, status) ? 1 : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) { ok = false; break; }
+                acc_phase ^= 1u;
+                tc_fence_after();
+                if (l < H) {
+                    float v[32];
+#pragma unroll
+                    for (int c0 = 0; c0 < W; c0 += 32) {
+                        tmem_ld32(lane_base + (uint32_t)c0, v);
+#pragma unroll
+                        for (int c = 0; c < 32; c += 8) {
+                            uint4 pk;
+                            pk.x = pack2(fmaxf(v[c], 0.f), fmaxf(v[c + 1], 0.f), fmt);
+                            pk.y = pack2(fmaxf(v[c + 2], 0.f), fmaxf(v[c + 3], 0.f), fmt);
+                            pk.z = pack2(fmaxf(v[c + 4], 0.f), fmaxf(v[c + 5], 0.f), fmt);
+                            pk.w = pack2(fmaxf(v[c + 6], 0.f), fmaxf(v[c + 7], 0.f), fmt);
+                            *reinterpret_cast<uint4*>(A + swz_off(row, c0 + c, kRows)) = pk;
+                        }
+                    }
+                    fence_async_smem();
+                } else {
+                    float v[16];
+                    tmem_ld16(lane_base, v);
+                    int64_t grow = t * kRows + row;
+                    if (grow < n) {
+                        float4* o = reinterpret_cast<float4*>(out + grow * NIF_OUT);
+                        o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                        o[2] = make_float4(v[8], v[9], v[10], v[11]);
+                        o[3] = make_float4(v[12], v[13], v[14], v[15]);
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&bars[2 * S + 1]));
+            }
+            if (!ok) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(W <= 32 ? 32u : (uint32_t)W)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
+
+nif_status get_encoder(nif_handle* h) {
+    if (g_encode_tiled) return NIF_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return nif_fail(h, NIF_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    g_encode_tiled = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return NIF_OK;
+}
+
+TcLayout make_layout(int W, int K0, int H) {
+    TcLayout L{};
+    L.nb0 = (K0 + 63) / 64;
+    L.ks0 = (K0 + 15) / 16;
+    L.nbw = (W + 63) / 64;
+    L.ksw = W / 16;
+    uint32_t off = 0;
+    L.wo_off = 0;
+    off += (uint32_t)L.nbw * 16 * 128;
+    L.w0_off = off;
+    off += (uint32_t)L.nb0 * W * 128;
+    L.wh_off = off;
+    off += (uint32_t)(H - 1) * L.nbw * W * 128;
+    L.a_off = off;
+    off += (uint32_t)L.nbw * kRows * 128;
+    L.x_off = off;
+    // ring depth from what is left of the shared memory budget
+    const uint32_t budget = 220 * 1024;
+    int S = (int)((budget - off - 1024 - 256) / kStageBytes);
+    if (S > 8) S = 8;
+    L.stages = S;
+    off += (uint32_t)S * kStageBytes;
+    L.bar_off = off;
+    off += 8 * (2 * S + 4) + 16;
+    L.total = off + 1024;        // room to align the dynamic buffer to 1024 bytes
+    return L;
+}
+
+template <int W>
+nif_status launch_tc(nif_handle* h, const void* x, int dtype, int64_t n, float* out, cudaStream_t s) {
+    TcLayout lay = make_layout(W, h->in_dim, h->H);
+    for (int l = 0; l < h->n_layers; l++) {
+        lay.woff[l] = (uint32_t)(h->off_layer[l] - h->off_layer[0]);
+        if (lay.woff[l] % 8) return nif_fail(h, NIF_ERR_STATE, "weight copy not 16-byte aligned per layer");
+    }
+    if (lay.stages < 2) return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP: weights do not fit in shared memory");
+    CUtensorMap map;
+    cuuint64_t gdim[2] = {(cuuint64_t)h->in_dim, (cuuint64_t)n};
+    cuuint64_t gstride[1] = {(cuuint64_t)h->in_dim * 2};
+    cuuint32_t box[2] = {64, kRows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode_tiled(&map, dtype == NIF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                                2, const_cast<void*>(x), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return nif_fail(h, NIF_ERR_ARG, "cuTensorMapEncodeTiled failed for the feature matrix");
+    NIF_CK(h, cudaFuncSetAttribute(k_mlp_tc<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
+    int64_t n_tiles = (n + kRows - 1) / kRows;
+    int grid = (int)std::min<int64_t>(n_tiles, h->num_sms);
+    const uint16_t* w = reinterpret_cast<const uint16_t*>(dtype == NIF_BF16 ? (const void*)h->d_w_bf16
+                                                                             : (const void*)h->d_w_f16);
+    k_mlp_tc<W><<<grid, kThreads, lay.total, s>>>(map, lay, w, h->in_dim, h->H, dtype == NIF_BF16 ? 1 : 0, n, out,
+                                                  h->d_status);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+}  // namespace
 
 nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev, int64_t n_max,
                               float* out, cudaStream_t s) {
     NifProf prof_(h, "mlp_fwd_tc", s);
-    (void)x; (void)dtype; (void)n_dev; (void)n_max; (void)out; (void)s;
-    return nif_fail(h, NIF_ERR_STATE, "tensor-core MLP not built yet");
+    if (n_dev) return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP needs a host row count");
+    if (n_max <= 0) return NIF_OK;
+    if (dtype != NIF_BF16 && dtype != NIF_FP16) return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP dtype");
+    if (h->in_dim % 8 != 0) return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP needs in_dim % 8 == 0");
+    if ((reinterpret_cast<uintptr_t>(x) & 15) != 0) return nif_fail(h, NIF_ERR_ARG, "feature matrix not 16-byte aligned");
+    nif_status st = get_encoder(h);
+    if (st != NIF_OK) return st;
+    if ((st = nif_refresh_lowp(h, s)) != NIF_OK) return st;
+    switch (h->W) {
+        case 32: return launch_tc<32>(h, x, dtype, n_max, out, s);
+        case 64: return launch_tc<64>(h, x, dtype, n_max, out, s);
+        case 128: return launch_tc<128>(h, x, dtype, n_max, out, s);
+        default: return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP width must be 32, 64 or 128");
+    }
 }

@@ -382,11 +382,11 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
     for (int l = 0; l < h->n_layers; l++) {
         h->lay_in[l] = l == 0 ? h->in_dim : h->W;
         h->lay_out[l] = l == h->n_layers - 1 ? NIF_OUT : h->W;
-        off = (off + 3) & ~(size_t)3;
+        off = (off + 7) & ~(size_t)7;     // 16-byte aligned rows in the 16-bit copies
         h->off_layer[l] = off;
         off += (size_t)h->lay_in[l] * h->lay_out[l];
     }
-    off = (off + 3) & ~(size_t)3;
+    off = (off + 7) & ~(size_t)7;
     h->off_layer[h->n_layers] = off;
     h->off_s = off;
     off += 8;

@@ -468,3 +468,92 @@ def test_adam_matches_oracle(nif, torus):
             np.testing.assert_allclose(got, state[g][0], atol=1e-6 + 1e-6 * lr * 100)
             assert not nif.nif_get_grad(h.h, g).any()     # Adam clears the gradient
     h.close()
+
+
+# ---------------------------------------------------------------------------
+# Tensor-core MLP (BF16 / FP16 operands, FP32 accumulation)
+# ---------------------------------------------------------------------------
+def _quant(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(torch.float64).numpy()
+
+
+def _mlp_lowp_reference(ws, x, dt):
+    """FP64 MLP on 16-bit-rounded inputs and weights, hidden activations rounded
+    to the same 16-bit type after the ReLU (as the kernel stores them)."""
+    h = _quant(x, dt)
+    for i, w in enumerate(ws):
+        z = h @ _quant(w, dt).T
+        if i < len(ws) - 1:
+            h = _quant(np.maximum(z, 0.0), dt)
+        else:
+            h = z
+    return h
+
+
+@pytest.mark.parametrize("depth,width,levels", [(2, 32, 8), (3, 64, 16), (1, 128, 8)])
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_mlp_tensor_core_forward(nif, torus, depth, width, levels, prec):
+    net = S.NetConfig(levels=levels, log2_table=14, mlp_depth=depth, mlp_width=width)
+    dt = torch.bfloat16 if prec == "bf16" else torch.float16
+    p = nif.NIF_BF16 if prec == "bf16" else nif.NIF_FP16
+    h = nif.Nif(net, torus)
+    tables, ws, s = S.init_params(net, seed=131)
+    h.set_params(tables, ws, s)
+    rng = np.random.default_rng(132)
+    for n in (1, 128, 5 * 128 + 77, 40000):     # one row, one tile, ragged tail, many tiles per CTA
+        x = rng.normal(size=(n, net.in_dim)).astype(np.float32)
+        xt = torch.from_numpy(x).to(_dev()).to(dt)
+        out = nif.nif_mlp_forward(h.h, xt, precision=p).cpu().numpy()
+        ref = _mlp_lowp_reference(ws, x, dt)
+        scale = np.abs(ref).max()
+        err = np.abs(out - ref)
+        # FP32 accumulation vs FP64, plus rare one-ulp flips of rounded hidden activations
+        assert np.median(err) <= 1e-4 * scale, (n, np.median(err), scale)
+        assert err.max() <= 2e-2 * scale, (n, err.max(), scale)
+        assert np.all(out[:, net.out_dim:] == 0)
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_query_mixed_precision_error_vs_oracle(nif, torus, prec):
+    """FP16 tables + 16-bit MLP operands against the FP64 oracle on the same
+    weights. Bounds (stated, generous against the measured values): hit
+    agreement on rays whose occupancy logit is clear of 5 % of its range,
+    distance <= 2e-3, albedo <= 2e-2, normal within 2 degrees, material
+    agreement >= 99 % where the top two logits differ by > 5 % of the range."""
+    net = S.NetConfig()
+    p = nif.NIF_BF16 if prec == "bf16" else nif.NIF_FP16
+    h = nif.Nif(net, torus, precision=p)
+    tables = random_tables(net, 141)
+    ws, s = occupancy_biased_weights(net, 142)
+    h.set_params(tables, ws, s)
+    pose = (0.5, -0.8, 0.4)
+    rays_np = S.sphere_rays(2000, seed=143)
+    rays_np = rays_np[certain_rays(net.voxel_res, torus, pose, rays_np)]
+    hits = nif.nif_query(h.h, [pose], torch.from_numpy(rays_np).to(_dev())).cpu().numpy()
+    hits = hits.view(nif.HIT_DTYPE).reshape(-1)
+    occ, _, _ = O.voxelize(net.voxel_res, torus)
+    seg = O.segments(net.voxel_res, occ, pose, rays_np)
+    p0, p1, ld, lr = O.linearize(pose, rays_np, seg)
+    out = O.mlp_forward(ws, O.encode_segments(net, tables, p0, p1))[0]
+    res = O.reconstruct(net, pose, rays_np, seg, out, p0, p1, ld, lr)
+    zr = np.abs(out[:, 0]).max()
+    n_cmp, mat_ok, mat_n = 0, 0, 0
+    for r in range(len(rays_np)):
+        a, b = seg.off[r], seg.off[r + 1]
+        if np.any(np.abs(out[a:b, 0]) < 0.05 * zr):
+            continue
+        assert hits["hit"][r] == res["hit"][r], r
+        if res["hit"][r]:
+            j = a + res["k"][r]
+            assert abs(hits["D"][r] - res["D"][r]) < 2e-3, (r, hits["D"][r], res["D"][r])
+            np.testing.assert_allclose(hits["albedo"][r], res["albedo"][r], atol=2e-2)
+            assert np.dot(hits["n"][r], res["normal"][r]) > np.cos(np.radians(2.0))
+            m = np.sort(out[j, 8:12])
+            if m[-1] - m[-2] > 0.05 * (np.abs(out[:, 8:12]).max()):
+                mat_n += 1
+                mat_ok += hits["material"][r] == res["material"][r]
+        n_cmp += 1
+    assert n_cmp > 500
+    assert mat_n == 0 or mat_ok >= 0.99 * mat_n
+    h.close()
