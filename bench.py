@@ -337,11 +337,14 @@ def run_query(args, nif, S, dev, rank):
     w = S.WORKLOADS[QUERY_WORKLOAD]
     net = w["net"]
     mesh = S.make_mesh(w["shape"])
-    n = w["n_rays"]
+    n = args.query_rays or w["n_rays"]
     rays = torch.from_numpy(S.sphere_rays(n, seed=900 + rank)).to(dev)
     pose = S.poses(1, seed=901 + rank)
     res = {"workload": QUERY_WORKLOAD, "rays_per_step": n}
-    for name, prec in (("fp32", nif.NIF_FP32), ("bf16", nif.NIF_BF16), ("fp16", nif.NIF_FP16)):
+    hbm = _peaks()[0]
+    precs = [(nm, {"fp32": nif.NIF_FP32, "bf16": nif.NIF_BF16, "fp16": nif.NIF_FP16}[nm])
+             for nm in args.query_prec.split(",")]
+    for name, prec in precs:
         try:
             h = nif.Nif(net, mesh, precision=prec, seed=31)
             ws_, s_ = S.init_params(net, seed=32)[1:]
@@ -362,9 +365,18 @@ def run_query(args, nif, S, dev, rank):
             ms = e0.elapsed_time(e1) / k
             prof = nif.nif_profile_read(h.h)
             nif.nif_profile(h.h, 0)
-            res[name] = {"queries_per_s": n / (ms / 1e3), "ms_per_query_batch": ms,
-                         "stages_ms": {kk: v[0] / k for kk, v in prof.items()},
+            _, segs = nif.nif_segments(h.h, pose, rays)
+            n_seg = int(segs.shape[0])
+            del segs
+            st = {kk: v[0] / k for kk, v in prof.items()}
+            res["segments_per_step"] = n_seg
+            res[name] = {"queries_per_s": n / (ms / 1e3), "ms_per_query_batch": ms, "stages_ms": st,
                          "hit_rate": float((hits[:, 7].view(torch.int32) & 0xff).ne(0).float().mean().item())}
+            if "mlp_fwd_tc" in st:
+                by = n_seg * (net.in_dim * 2 + 16 * 4)          # 16-bit features in, FP32 outputs out
+                gbs = by / (st["mlp_fwd_tc"] / 1e3) / 1e9
+                res[name]["mlp_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                             "frac": gbs / hbm, "bytes_per_segment": net.in_dim * 2 + 64}
             h.close()
         except nif.NifError as e:
             res[name] = {"unavailable": str(e)}
@@ -379,11 +391,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-query", action="store_true", help="skip the inference-query measurement")
+    ap.add_argument("--only-query", action="store_true", help="measure only the inference queries (profiling aid)")
+    ap.add_argument("--query-rays", type=int, default=0, help="rays per query batch (default: the workload's 2^22)")
+    ap.add_argument("--query-prec", default="fp32,bf16,fp16", help="comma list of query precisions")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_query:
+        import torch
+        torch.cuda.set_device(0)
+        from paper_2604_24666_gb300 import build as B
+        B.build()
+        from paper_2604_24666_gb300 import nif, synth as S
+        print(json.dumps({"query": run_query(args, nif, S, torch.device("cuda:0"), 0)}), flush=True)
+        return 0
     return run_ours(args)
 
 

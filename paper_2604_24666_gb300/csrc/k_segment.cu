@@ -17,6 +17,8 @@
 // in Morton order whose boxes are refitted per pose) enumerates every occupied
 // hull the ray can meet, which yields the same segment set by definition and
 // needs no walk through empty voxels.
+#include <algorithm>
+
 #include "nif_internal.cuh"
 
 namespace {
@@ -183,69 +185,179 @@ __device__ __forceinline__ int find_inst(const int* inst_off, int n_inst, int r)
 }
 
 constexpr int kStack = 96;
+constexpr int kTravWarps = 4;      // warps per traversal block
 
-template <bool EMIT>
-__global__ void __launch_bounds__(128) k_seg_traverse(
+// Modes of the traversal kernel
+enum { kModeCount = 0, kModeEmit = 1, kModeTemp = 2 };
+
+// Ray / octree traversal with warp-pooled hull tests. Each thread walks the
+// octree of its own ray with a private stack; every leaf whose refitted box
+// the ray meets becomes a (lane, leaf) candidate in a per-warp queue in
+// shared memory. Whenever 32 candidates are queued (or no lane has work
+// left) the warp tests them against their rays' hulls with all 32 lanes at
+// once, so the 12-triangle hull test -- the bulk of the arithmetic -- runs
+// without divergence.
+//   kModeCount: per-ray segment counts;
+//   kModeEmit:  segments written to the CSR rows [offsets[r], offsets[r+1])
+//               of their ray, then each ray's list sorted by (t0, voxel);
+//   kModeTemp:  counts plus every segment appended to `temp` at a
+//               warp-reserved position (ray order is restored by a scatter).
+template <int MODE>
+__global__ void __launch_bounds__(kTravWarps * 32) k_seg_traverse(
     const nif_ray* __restrict__ rays, const int* __restrict__ inst_off, int n_inst, int n_rays,
     TreeView tree, const float* __restrict__ corners, const float4* __restrict__ aabb,
     uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets, nif_segment* __restrict__ segs,
-    int64_t cap, int* status) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rays) return;
-    int inst = find_inst(inst_off, n_inst, r);
-    RayPre ray = ray_pre(rays, r);
+    int64_t cap, uint32_t* __restrict__ temp_cursor, int* status) {
+    __shared__ RayPre s_ray[kTravWarps][32];
+    __shared__ uint32_t s_q[kTravWarps][64];
+    __shared__ uint32_t s_cnt[kTravWarps][32];
+    __shared__ int s_inst[kTravWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r_warp0 = blockIdx.x * blockDim.x + warp * 32;
+    const bool valid = r < n_rays;
+    int inst = valid ? find_inst(inst_off, n_inst, r) : 0;
+    RayPre ray;
+    if (valid) ray = ray_pre(rays, r);
+    else ray = RayPre{};
+    s_ray[warp][lane] = ray;
+    s_cnt[warp][lane] = 0;
+    s_inst[warp][lane] = inst;
     const float4* A = aabb + (int64_t)inst * tree.n_nodes * 2;
-    const float* Cbase = corners + (int64_t)inst * tree.n_leaves * 24;
-    int64_t base = EMIT ? (int64_t)offsets[r] : 0;
-    int64_t end = EMIT ? (int64_t)offsets[r + 1] : 0;
-    uint32_t n = 0;
     int stack[kStack];
     int sp = 0;
-    for (int q = tree.top_begin + tree.top_count - 1; q >= tree.top_begin; q--) stack[sp++] = q;
-    while (sp > 0) {
-        int node = stack[--sp];
-        if (node < tree.n_leaves) {
-            if (!slab(ray, __ldg(A + 2 * node), __ldg(A + 2 * node + 1))) continue;
-            float t0, t1;
-            if (hull_segment(ray, Cbase + (int64_t)node * 24, t0, t1)) {
-                if (EMIT) {
-                    int64_t pos = base + n;
-                    if (pos < end && pos < cap) {
-                        nif_segment sg;
-                        sg.ray = (uint32_t)r;
-                        sg.voxel = __ldg(tree.leaf_vox + node);
-                        sg.t0 = t0;
-                        sg.t1 = t1;
-                        segs[pos] = sg;
+    if (valid)
+        for (int q = tree.top_begin + tree.top_count - 1; q >= tree.top_begin; q--) stack[sp++] = q;
+    __syncwarp();
+    int qn = 0;
+    while (true) {
+        // fill the queue with leaf candidates
+        while (qn < 32) {
+            bool want = sp > 0;
+            if (!__any_sync(FULL, want)) break;
+            int cand = -1;
+            if (want) {
+                int node = stack[--sp];
+                if (slab(ray, __ldg(A + 2 * node), __ldg(A + 2 * node + 1))) {
+                    if (node < tree.n_leaves) {
+                        cand = node;
+                    } else {
+                        int2 ch = __ldg(tree.child + (node - tree.n_leaves));
+                        if (sp + ch.y > kStack) {
+                            nif_set_status(status, NIF_ERR_CAPACITY);
+                            sp = 0;
+                        } else {
+                            for (int c = ch.x + ch.y - 1; c >= ch.x; c--) stack[sp++] = c;
+                        }
                     }
                 }
-                n++;
             }
-            continue;
+            unsigned m = __ballot_sync(FULL, cand >= 0);
+            if (cand >= 0) s_q[warp][qn + __popc(m & ((1u << lane) - 1u))] = ((uint32_t)lane << 27) | (uint32_t)cand;
+            qn += __popc(m);
         }
-        if (!slab(ray, __ldg(A + 2 * node), __ldg(A + 2 * node + 1))) continue;
-        int2 ch = __ldg(tree.child + (node - tree.n_leaves));
-        if (sp + ch.y > kStack) { nif_set_status(status, NIF_ERR_CAPACITY); break; }
-        for (int c = ch.x + ch.y - 1; c >= ch.x; c--) stack[sp++] = c;
+        __syncwarp();
+        if (qn == 0) break;
+        const int take = qn < 32 ? qn : 32;
+        bool hit = false;
+        int L = 0;
+        nif_segment sg;
+        if (lane < take) {
+            uint32_t c = s_q[warp][lane];
+            L = (int)(c >> 27);
+            int leaf = (int)(c & 0x7FFFFFFu);
+            float t0, t1;
+            const float* C = corners + ((int64_t)s_inst[warp][L] * tree.n_leaves + leaf) * 24;
+            if (hull_segment(s_ray[warp][L], C, t0, t1)) {
+                hit = true;
+                sg.ray = (uint32_t)(r_warp0 + L);
+                sg.voxel = __ldg(tree.leaf_vox + leaf);
+                sg.t0 = t0;
+                sg.t1 = t1;
+            }
+        }
+        if (MODE == kModeCount) {
+            if (hit) atomicAdd(&s_cnt[warp][L], 1u);
+        } else if (MODE == kModeEmit) {
+            if (hit) {
+                uint32_t pos = atomicAdd(&s_cnt[warp][L], 1u);
+                int64_t g = (int64_t)offsets[r_warp0 + L] + pos;
+                if (g < (int64_t)offsets[r_warp0 + L + 1] && g < cap) segs[g] = sg;
+            }
+        } else {
+            if (hit) atomicAdd(&s_cnt[warp][L], 1u);
+            unsigned hm = __ballot_sync(FULL, hit);
+            uint32_t wb = 0;
+            if (lane == 0 && hm) wb = atomicAdd(temp_cursor, (uint32_t)__popc(hm));
+            wb = __shfl_sync(FULL, wb, 0);
+            if (hit) {
+                int64_t g = (int64_t)wb + __popc(hm & ((1u << lane) - 1u));
+                if (g < cap) segs[g] = sg;
+            }
+        }
+        __syncwarp();
+        const int rest = qn - take;
+        uint32_t moved = lane < rest ? s_q[warp][32 + lane] : 0u;
+        __syncwarp();
+        if (lane < rest) s_q[warp][lane] = moved;
+        __syncwarp();
+        qn = rest;
     }
-    if (!EMIT) {
-        counts[r] = n;
+    __syncwarp();
+    if (!valid) return;
+    if (MODE != kModeEmit) {
+        counts[r] = s_cnt[warp][lane];
         return;
     }
-    // sort this ray's segments by (t0, voxel): short, nearly sorted runs
-    int64_t m = end - base;
-    if (base + m > cap) m = cap - base;
-    for (int64_t a = 1; a < m; a++) {
-        nif_segment key = segs[base + a];
+    // sort this ray's segments by (t0, voxel): short runs
+    int64_t base = offsets[r], end = offsets[r + 1];
+    if (end > cap) end = cap;
+    for (int64_t a = base + 1; a < end; a++) {
+        nif_segment key = segs[a];
         int64_t b = a - 1;
-        while (b >= 0) {
-            nif_segment o = segs[base + b];
+        while (b >= base) {
+            nif_segment o = segs[b];
             bool gt = o.t0 > key.t0 || (o.t0 == key.t0 && o.voxel > key.voxel);
             if (!gt) break;
-            segs[base + b + 1] = o;
+            segs[b + 1] = o;
             b--;
         }
-        segs[base + b + 1] = key;
+        segs[b + 1] = key;
+    }
+}
+
+// Moves the ray-unordered segments of kModeTemp to their ray's CSR rows
+// (fill[] zeroed, one counter per ray) ...
+__global__ void __launch_bounds__(256) k_seg_scatter(const nif_segment* __restrict__ temp, const uint32_t* __restrict__ n_temp,
+                                                     const uint32_t* __restrict__ offsets, uint32_t* __restrict__ fill,
+                                                     nif_segment* __restrict__ segs, int64_t cap) {
+    int64_t n = *n_temp;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        nif_segment sg = temp[i];
+        int64_t g = (int64_t)offsets[sg.ray] + atomicAdd(fill + sg.ray, 1u);
+        if (g < cap) segs[g] = sg;
+    }
+}
+
+// ... and sorts every ray's row by (t0, voxel).
+__global__ void __launch_bounds__(256) k_seg_sort(const uint32_t* __restrict__ offsets, int n_rays,
+                                                  nif_segment* __restrict__ segs, int64_t cap) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    int64_t base = offsets[r], end = offsets[r + 1];
+    if (end > cap) end = cap;
+    for (int64_t a = base + 1; a < end; a++) {
+        nif_segment key = segs[a];
+        int64_t b = a - 1;
+        while (b >= base) {
+            nif_segment o = segs[b];
+            bool gt = o.t0 > key.t0 || (o.t0 == key.t0 && o.voxel > key.voxel);
+            if (!gt) break;
+            segs[b + 1] = o;
+            b--;
+        }
+        segs[b + 1] = key;
     }
 }
 
@@ -402,9 +514,9 @@ nif_status nif_seg_count_run(nif_handle* h, const nif_ray* rays, const int* inst
         NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n_rays, s));
         return NIF_OK;
     }
-    k_seg_traverse<false><<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, tree_view(h),
-                                                                  h->d_corners, h->d_aabb, counts, nullptr,
-                                                                  nullptr, 0, h->d_status);
+    k_seg_traverse<kModeCount><<<nif_blocks(n_rays, kTravWarps * 32), kTravWarps * 32, 0, s>>>(
+        rays, inst_off, n_inst, n_rays, tree_view(h), h->d_corners, h->d_aabb, counts, nullptr, nullptr, 0, nullptr,
+        h->d_status);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
@@ -413,9 +525,43 @@ nif_status nif_seg_emit_run(nif_handle* h, const nif_ray* rays, const int* inst_
                             const uint32_t* offsets, nif_segment* segs, int64_t cap, cudaStream_t s) {
     NifProf prof_(h, "seg_emit", s);
     if (n_rays <= 0 || h->n_leaves == 0) return NIF_OK;
-    k_seg_traverse<true><<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, tree_view(h),
-                                                                 h->d_corners, h->d_aabb, nullptr, offsets, segs,
-                                                                 cap, h->d_status);
+    k_seg_traverse<kModeEmit><<<nif_blocks(n_rays, kTravWarps * 32), kTravWarps * 32, 0, s>>>(
+        rays, inst_off, n_inst, n_rays, tree_view(h), h->d_corners, h->d_aabb, nullptr, offsets, segs, cap, nullptr,
+        h->d_status);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+// One traversal: per-ray counts and all segments, ray-unordered, into temp
+// (capacity temp_cap; *cursor must be zero and ends as the total).
+nif_status nif_seg_temp_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                            uint32_t* counts, nif_segment* temp, int64_t temp_cap, uint32_t* cursor,
+                            cudaStream_t s) {
+    NifProf prof_(h, "seg_traverse", s);
+    if (n_rays <= 0) return NIF_OK;
+    if (h->n_leaves == 0) {
+        NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n_rays, s));
+        return NIF_OK;
+    }
+    k_seg_traverse<kModeTemp><<<nif_blocks(n_rays, kTravWarps * 32), kTravWarps * 32, 0, s>>>(
+        rays, inst_off, n_inst, n_rays, tree_view(h), h->d_corners, h->d_aabb, counts, nullptr, temp, temp_cap, cursor,
+        h->d_status);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+// temp -> CSR rows in ray order, then each row sorted; fill must hold n_rays zeroed words
+nif_status nif_seg_scatter_run(nif_handle* h, const nif_segment* temp, const uint32_t* n_temp,
+                               int64_t n_temp_max, const uint32_t* offsets, uint32_t* fill, int n_rays,
+                               nif_segment* segs, int64_t cap, cudaStream_t s) {
+    NifProf prof_(h, "seg_scatter", s);
+    if (n_rays <= 0) return NIF_OK;
+    unsigned g = nif_blocks(std::max<int64_t>(n_temp_max, 1), 256);
+    unsigned gcap = (unsigned)h->num_sms * 8;
+    if (g > gcap) g = gcap;
+    k_seg_scatter<<<g, 256, 0, s>>>(temp, n_temp, offsets, fill, segs, cap);
+    NIF_CK_LAUNCH(h);
+    k_seg_sort<<<nif_blocks(n_rays, 256), 256, 0, s>>>(offsets, n_rays, segs, cap);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

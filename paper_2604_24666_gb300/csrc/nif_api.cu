@@ -523,6 +523,10 @@ extern "C" nif_status nif_get_voxels(nif_handle* h, unsigned char* occ, int64_t*
     return NIF_OK;
 }
 
+static nif_status seg_single_pass(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                                  uint32_t* offs, nif_segment* segs, int64_t seg_cap, bool segs_grow,
+                                  int64_t* total_out, cudaStream_t s);
+
 static nif_status check_status(nif_handle* h, cudaStream_t s) {
     NIF_CK(h, cudaStreamSynchronize(s));
     int st = 0;
@@ -557,12 +561,18 @@ extern "C" nif_status nif_segments(nif_handle* h, const nif_pose* poses, int n_i
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
     if ((st = nif_refit_run(h, n_inst, s)) != NIF_OK) return st;
-    if ((st = nif_grow(h, h->b_counts, sizeof(uint32_t) * ((size_t)n_rays + 1))) != NIF_OK) return st;
-    uint32_t* counts = (uint32_t*)h->b_counts.p;
-    if ((st = nif_seg_count_run(h, rays, inst_off, n_inst, n_rays, counts, s)) != NIF_OK) return st;
-    if ((st = nif_scan_run(h, counts, ray_offsets, n_rays, s)) != NIF_OK) return st;
-    if ((st = nif_seg_emit_run(h, rays, inst_off, n_inst, n_rays, ray_offsets, segs, segs ? seg_cap : 0, s)) != NIF_OK)
-        return st;
+    if (segs) {
+        // one traversal into scratch, then scatter into the caller's rows
+        int64_t t = 0;
+        if ((st = seg_single_pass(h, rays, inst_off, n_inst, n_rays, ray_offsets, segs, seg_cap, false, &t, s)) !=
+            NIF_OK)
+            return st;
+    } else {
+        if ((st = nif_grow(h, h->b_counts, sizeof(uint32_t) * ((size_t)n_rays + 1))) != NIF_OK) return st;
+        uint32_t* counts = (uint32_t*)h->b_counts.p;
+        if ((st = nif_seg_count_run(h, rays, inst_off, n_inst, n_rays, counts, s)) != NIF_OK) return st;
+        if ((st = nif_scan_run(h, counts, ray_offsets, n_rays, s)) != NIF_OK) return st;
+    }
     NIF_CK(h, cudaStreamSynchronize(s));
     uint32_t tot = 0;
     NIF_CK(h, cudaMemcpy(&tot, ray_offsets + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost));
@@ -680,6 +690,46 @@ extern "C" nif_status nif_sample_rays(nif_handle* h, unsigned long long seed, in
 // Whole paths
 // ---------------------------------------------------------------------------
 
+// Single traversal (counts + ray-unordered segments into handle scratch),
+// scan, then scatter into the CSR rows `offs` / `segs` (capacity seg_cap,
+// or sized to the total when segs_grow is set). Blocks the host once to read
+// the total. Falls back to a second traversal when the scratch was short.
+static nif_status seg_single_pass(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                                  uint32_t* offs, nif_segment* segs, int64_t seg_cap, bool segs_grow,
+                                  int64_t* total_out, cudaStream_t s) {
+    nif_status st;
+    if ((st = nif_grow(h, h->b_counts, sizeof(uint32_t) * ((size_t)n_rays + 1))) != NIF_OK) return st;
+    uint32_t* counts = (uint32_t*)h->b_counts.p;
+    double hint = h->query_seg_per_ray > 0.0 ? h->query_seg_per_ray * 1.25 + 0.5 : 8.0;
+    int64_t tcap = std::max<int64_t>(4096, (int64_t)(hint * (double)n_rays));
+    if ((st = nif_grow(h, h->b_temp, sizeof(nif_segment) * (size_t)tcap)) != NIF_OK) return st;
+    tcap = (int64_t)(h->b_temp.bytes / sizeof(nif_segment));
+    uint32_t* cursor = reinterpret_cast<uint32_t*>(h->d_count + 1);
+    NIF_CK(h, cudaMemsetAsync(cursor, 0, sizeof(uint32_t), s));
+    if ((st = nif_seg_temp_run(h, rays, inst_off, n_inst, n_rays, counts, (nif_segment*)h->b_temp.p, tcap, cursor, s)) !=
+        NIF_OK)
+        return st;
+    if ((st = nif_scan_run(h, counts, offs, n_rays, s)) != NIF_OK) return st;
+    NIF_CK(h, cudaMemcpyAsync(h->h_pinned, offs + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    NIF_CK(h, cudaStreamSynchronize(s));
+    int64_t total = (uint32_t)h->h_pinned[0];
+    *total_out = total;
+    if (n_rays > 0) h->query_seg_per_ray = (double)total / n_rays;
+    if (segs_grow) {
+        if ((st = nif_grow(h, h->b_segs, sizeof(nif_segment) * (size_t)std::max<int64_t>(total, 1))) != NIF_OK)
+            return st;
+        segs = (nif_segment*)h->b_segs.p;
+        seg_cap = total;
+    }
+    if (!segs) return NIF_OK;
+    if (total <= tcap) {
+        NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)n_rays, s));
+        return nif_seg_scatter_run(h, (const nif_segment*)h->b_temp.p, cursor, total, offs, counts, n_rays, segs,
+                                   seg_cap, s);
+    }
+    return nif_seg_emit_run(h, rays, inst_off, n_inst, n_rays, offs, segs, seg_cap, s);
+}
+
 // segments of the caller's rays into the handle's scratch; returns the device
 // pointer of the clamped total (<= cap)
 static nif_status segment_into_scratch(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
@@ -692,19 +742,21 @@ static nif_status segment_into_scratch(nif_handle* h, const nif_pose* poses, int
     if ((st = nif_grow(h, h->b_offsets, sizeof(uint32_t) * ((size_t)n_rays + 2))) != NIF_OK) return st;
     uint32_t* counts = (uint32_t*)h->b_counts.p;
     uint32_t* offs = (uint32_t*)h->b_offsets.p;
-    if ((st = nif_seg_count_run(h, rays, inst_off, n_inst, n_rays, counts, s)) != NIF_OK) return st;
-    if ((st = nif_scan_run(h, counts, offs, n_rays, s)) != NIF_OK) return st;
     if (host_total) {
-        uint32_t tot = 0;
-        NIF_CK(h, cudaMemcpyAsync(h->h_pinned, offs + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        NIF_CK(h, cudaStreamSynchronize(s));
-        tot = (uint32_t)h->h_pinned[0];
+        int64_t tot = 0;
+        if ((st = seg_single_pass(h, rays, inst_off, n_inst, n_rays, offs, nullptr, 0, true, &tot, s)) != NIF_OK)
+            return st;
         *total_host = tot;
         if (cap < 0) cap = tot;
+    } else {
+        if ((st = nif_seg_count_run(h, rays, inst_off, n_inst, n_rays, counts, s)) != NIF_OK) return st;
+        if ((st = nif_scan_run(h, counts, offs, n_rays, s)) != NIF_OK) return st;
+        if ((st = nif_grow(h, h->b_segs, sizeof(nif_segment) * (size_t)std::max<int64_t>(cap, 1))) != NIF_OK)
+            return st;
+        if ((st = nif_seg_emit_run(h, rays, inst_off, n_inst, n_rays, offs, (nif_segment*)h->b_segs.p, cap, s)) !=
+            NIF_OK)
+            return st;
     }
-    if ((st = nif_grow(h, h->b_segs, sizeof(nif_segment) * (size_t)std::max<int64_t>(cap, 1))) != NIF_OK) return st;
-    if ((st = nif_seg_emit_run(h, rays, inst_off, n_inst, n_rays, offs, (nif_segment*)h->b_segs.p, cap, s)) != NIF_OK)
-        return st;
     // clamped count lives right after the offsets
     return nif_clamp_count_run(h, offs, n_rays, cap, offs + n_rays + 1, s);
 }

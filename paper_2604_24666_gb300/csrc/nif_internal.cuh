@@ -94,7 +94,8 @@ struct nif_handle {
     // grown scratch buffers (query / train)
     struct Buf { void* p = nullptr; size_t bytes = 0; };
     Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
-        b_scan, b_rays, b_inst, b_feat2;
+        b_scan, b_rays, b_inst, b_feat2, b_temp;
+    double query_seg_per_ray = 0.0;     // segments per ray of the last query (temp capacity hint)
 
     std::string err;
     int num_sms = 0;
@@ -158,6 +159,12 @@ nif_status nif_refit_run(nif_handle* h, int n_inst, cudaStream_t s);
 nif_status nif_seg_count_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
                              int n_rays, uint32_t* counts, cudaStream_t s);
 nif_status nif_scan_run(nif_handle* h, const uint32_t* in, uint32_t* out, int n, cudaStream_t s);
+nif_status nif_seg_temp_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                            uint32_t* counts, nif_segment* temp, int64_t temp_cap, uint32_t* cursor,
+                            cudaStream_t s);
+nif_status nif_seg_scatter_run(nif_handle* h, const nif_segment* temp, const uint32_t* n_temp,
+                               int64_t n_temp_max, const uint32_t* offsets, uint32_t* fill, int n_rays,
+                               nif_segment* segs, int64_t cap, cudaStream_t s);
 nif_status nif_seg_emit_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
                             int n_rays, const uint32_t* offsets, nif_segment* segs, int64_t cap,
                             cudaStream_t s);
