@@ -304,6 +304,101 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_sm(GridInfo g, Coa
     }
 }
 
+// Backward with a run-length register cache. A warp owns 32/L (endpoint,
+// term) pairs x L levels (lane = level + L * pair) and walks a chunk of kRun
+// consecutive segments; segments come in ray order, so consecutive points of
+// one term are spatially close and a coarse cell repeats for many segments
+// (the low sin/cos bands of gamma cover only part of [0,1]). Each lane keeps
+// the row and the running sum of its 8 corners and reduces into the table
+// only when a corner's row changes: dense coarse levels into the block's
+// shared-memory copy, the rest into global memory.
+constexpr int kRun = 64;
+
+__global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coarse cs,
+                                                                 const nif_linseg* __restrict__ lin,
+                                                                 const uint32_t* __restrict__ n_dev, int64_t n_max,
+                                                                 const float* __restrict__ dfeats,
+                                                                 float* __restrict__ dtab) {
+    extern __shared__ float sacc[];
+    const int nsh = cs.soff[cs.Lc];
+    for (int i = threadIdx.x; i < nsh; i += blockDim.x) sacc[i] = 0.f;
+    __syncthreads();
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    const int lane = threadIdx.x & 31;
+    const int ppw = 32 / g.L;                          // (endpoint, term) pairs per warp
+    const int groups = (2 * g.P + ppw - 1) / ppw;
+    const int l = lane % g.L;
+    const int pair_in_warp = lane / g.L;
+    const int Nl = g.res[l];
+    const bool dense = (g.dense_mask >> l) & 1u;
+    const bool in_sh = l < cs.Lc;
+    float* dl = in_sh ? sacc + cs.soff[l] : dtab + (int64_t)l * g.T * 2;
+    const int64_t chunks = (n + kRun - 1) / kRun;
+    const int64_t tasks = chunks * groups;
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < tasks;
+         task += warps_total) {
+        const int64_t c = task / groups;
+        const int grp = (int)(task - c * groups);
+        const int pair = grp * ppw + pair_in_warp;        // (endpoint, term) index in [0, 2P)
+        const bool active = pair < 2 * g.P;
+        const int e = pair >= g.P;
+        const int t = pair - e * g.P;
+        uint32_t crow[8];
+        float2 cacc[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) { crow[q] = 0xffffffffu; cacc[q] = make_float2(0.f, 0.f); }
+        const int64_t s_end = (c + 1) * kRun < n ? (c + 1) * kRun : n;
+        for (int64_t s = c * kRun; s < s_end && active; s++) {
+            const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+            float3 u = term_u(clamp01(make_float3(L[0], L[1], L[2])), t);
+            Cell cl = cell_of(u, Nl);
+            float2 gr = *reinterpret_cast<const float2*>(dfeats + ((s * 2 * g.P + pair) * g.L + l) * 2);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                uint32_t row = grid_row(cl.ix + (q & 1), cl.iy + ((q >> 1) & 1), cl.iz + ((q >> 2) & 1), Nl, dense, g.T);
+                float w = ((q & 1) ? cl.wx : 1.f - cl.wx) * ((q & 2) ? cl.wy : 1.f - cl.wy) *
+                          ((q & 4) ? cl.wz : 1.f - cl.wz);
+                if (row != crow[q]) {
+                    if (crow[q] != 0xffffffffu) {
+                        if (in_sh) {
+                            atomicAdd(dl + 2 * crow[q], cacc[q].x);
+                            atomicAdd(dl + 2 * crow[q] + 1, cacc[q].y);
+                        } else {
+                            atomicAdd(reinterpret_cast<float2*>(dl) + crow[q], cacc[q]);
+                        }
+                    }
+                    crow[q] = row;
+                    cacc[q] = make_float2(w * gr.x, w * gr.y);
+                } else {
+                    cacc[q].x += w * gr.x;
+                    cacc[q].y += w * gr.y;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if (crow[q] == 0xffffffffu) continue;
+            if (in_sh) {
+                atomicAdd(dl + 2 * crow[q], cacc[q].x);
+                atomicAdd(dl + 2 * crow[q] + 1, cacc[q].y);
+            } else {
+                atomicAdd(reinterpret_cast<float2*>(dl) + crow[q], cacc[q]);
+            }
+        }
+    }
+    __syncthreads();
+    for (int lv = 0; lv < cs.Lc; lv++) {
+        int cnt = cs.soff[lv + 1] - cs.soff[lv];
+        float* dst = dtab + (int64_t)lv * g.T * 2;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            float v = sacc[cs.soff[lv] + i];
+            if (v != 0.f) atomicAdd(dst + i, v);
+        }
+    }
+}
+
 template <typename TT, typename OT>
 void launch_points(nif_handle* h, const TT* tab, const float* pts, int64_t n, void* feats, int32_t* rows,
                    cudaStream_t s) {
@@ -389,9 +484,15 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
     }
     size_t smem = sizeof(float) * (size_t)cs.soff[cs.Lc];
     if (cs.Lc > 0) {
-        NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024));
-        k_encode_segments_bwd_sm<<<h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables);
+        if (32 % h->L == 0) {
+            NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           200 * 1024));
+            k_encode_segments_bwd_rl<<<h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables);
+        } else {
+            NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           200 * 1024));
+            k_encode_segments_bwd_sm<<<h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables);
+        }
         NIF_CK_LAUNCH(h);
         return NIF_OK;
     }

@@ -71,20 +71,29 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait suspends the thread until the phase completes or a hardware
+// time limit passes, so it wakes up as soon as the barrier flips.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait: about one second of wall time, then the kernel gives up.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
-    if (mbar_test(bar, parity)) return true;
+    if (mbar_try(bar, parity)) return true;
     uint64_t t0 = globaltimer();
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if ((it & 63) == 63) {
-            if (*abort_flag) return false;
-            if (globaltimer() - t0 > 1000000000ull) {
-                *abort_flag = 1;
-                atomicCAS(status, 0, (int)NIF_ERR_TIMEOUT);
-                return false;
-            }
-            __nanosleep(64);
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > 1000000000ull) {
+            *abort_flag = 1;
+            atomicCAS(status, 0, (int)NIF_ERR_TIMEOUT);
+            return false;
         }
     }
 }
@@ -193,31 +202,36 @@ template <int W>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_tc(const __grid_constant__ CUtensorMap xmap, TcLayout lay, const uint16_t* __restrict__ wts,
              int K0, int H, int fmt, int64_t n, float* __restrict__ out, int* __restrict__ status) {
+    constexpr uint32_t kAccCols = W < 32 ? 32 : W;     // TMEM columns of one accumulator stage
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment of the dynamic buffer (swizzle atoms)
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = lay.stages;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + lay.bar_off);
-    // bars: [0,S) full, [S,2S) empty, 2S acc_full, 2S+1 act_full, 2S+2 drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + lay.bar_off + 8 * (2 * S + 4));
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + lay.bar_off + 8 * (2 * S + 4) + 8);
+    // bars: [0,S) full, [S,2S) empty, 2S+{0,1} acc_full, 2S+{2,3} act_full, 2S+4 drain
+    const int B_ACC = 2 * S, B_ACT = 2 * S + 2, B_DRAIN = 2 * S + 4;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + lay.bar_off + 8 * (2 * S + 6));
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + lay.bar_off + 8 * (2 * S + 6) + 8);
     const int64_t n_tiles = (n + kRows - 1) / kRows;
+    const int64_t nt = blockIdx.x < n_tiles ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
     if (tid == 0) {
         for (int i = 0; i < S; i++) {
             mbar_init(smem_u32(&bars[i]), 1);
             mbar_init(smem_u32(&bars[S + i]), 1);
         }
-        mbar_init(smem_u32(&bars[2 * S]), 1);
-        mbar_init(smem_u32(&bars[2 * S + 1]), 128);
-        mbar_init(smem_u32(&bars[2 * S + 2]), 1);
+        mbar_init(smem_u32(&bars[B_ACC]), 1);
+        mbar_init(smem_u32(&bars[B_ACC + 1]), 1);
+        mbar_init(smem_u32(&bars[B_ACT]), 128);
+        mbar_init(smem_u32(&bars[B_ACT + 1]), 128);
+        mbar_init(smem_u32(&bars[B_DRAIN]), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(W <= 32 ? 32u : (uint32_t)W)
+                     "r"(2 * kAccCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -231,6 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const uint32_t a_bytes = (uint32_t)lay.nbw * kRows * 128;   // one activation tile
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -240,7 +255,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t issued_parity_mask = 0, issued_mask = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            for (int64_t j = 0; j < nt && ok; j++) {
+                int64_t t = blockIdx.x + j * gridDim.x;
                 for (int b = 0; b < lay.nb0; b++) {
                     if (!mbar_wait(smem_u32(&bars[S + slot]), phase ^ 1u, abort_flag, status)) { ok = false; break; }
                     uint32_t fb = smem_u32(&bars[slot]);
@@ -260,116 +276,123 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
+        // ---------------- MMA issuer: tiles in pairs, one TMEM stage each ----------------
         if (lane == 0) {
             const uint32_t id_hid = idesc_f16(fmt, W);
             const uint32_t id_out = idesc_f16(fmt, 16);
             int slot = 0;
-            uint32_t phase = 0, act_phase = 0;
-            bool first = true, ok = true;
-            for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                // layer 0: accumulator must be free (previous tile's output read)
-                if (!first) {
-                    if (!mbar_wait(smem_u32(&bars[2 * S + 1]), act_phase, abort_flag, status)) break;
-                    act_phase ^= 1u;
-                    tc_fence_after();
-                }
-                first = false;
-                for (int b = 0; b < lay.nb0 && ok; b++) {
-                    if (!mbar_wait(smem_u32(&bars[slot]), phase, abort_flag, status)) { ok = false; break; }
-                    tc_fence_after();
-                    uint32_t base = smem_u32(sm + lay.x_off + (uint32_t)slot * kStageBytes);
-                    uint32_t wbase = smem_u32(sm + lay.w0_off + (uint32_t)b * W * 128);
-                    for (int j = 0; j < 4; j++) {
-                        int ks = b * 4 + j;
-                        if (ks >= lay.ks0) break;
-                        mma_f16(tmem, sdesc(base + 32 * j), sdesc(wbase + 32 * j), id_hid, ks > 0 ? 1u : 0u);
+            uint32_t phase = 0;
+            uint32_t act_par[2] = {0u, 0u};
+            bool ok = true;
+            for (int64_t j0 = 0; j0 < nt && ok; j0 += 2) {
+                const int cnt = nt - j0 < 2 ? (int)(nt - j0) : 2;
+                for (int q = 0; q < cnt && ok; q++) {
+                    const uint32_t acc = tmem + (uint32_t)q * kAccCols;
+                    if (j0 + q >= 2) {      // this stage's accumulator must have been read out
+                        if (!mbar_wait(smem_u32(&bars[B_ACT + q]), act_par[q], abort_flag, status)) { ok = false; break; }
+                        act_par[q] ^= 1u;
+                        tc_fence_after();
                     }
-                    mma_commit(smem_u32(&bars[S + slot]));   // frees the stage when these MMAs finish
-                    if (++slot == S) { slot = 0; phase ^= 1u; }
+                    for (int b = 0; b < lay.nb0; b++) {
+                        if (!mbar_wait(smem_u32(&bars[slot]), phase, abort_flag, status)) { ok = false; break; }
+                        tc_fence_after();
+                        uint32_t base = smem_u32(sm + lay.x_off + (uint32_t)slot * kStageBytes);
+                        uint32_t wbase = smem_u32(sm + lay.w0_off + (uint32_t)b * W * 128);
+                        for (int jj = 0; jj < 4; jj++) {
+                            int ks = b * 4 + jj;
+                            if (ks >= lay.ks0) break;
+                            mma_f16(acc, sdesc(base + 32 * jj), sdesc(wbase + 32 * jj), id_hid, ks > 0 ? 1u : 0u);
+                        }
+                        mma_commit(smem_u32(&bars[S + slot]));   // frees the stage when these MMAs finish
+                        if (++slot == S) { slot = 0; phase ^= 1u; }
+                    }
+                    if (!ok) break;
+                    mma_commit(smem_u32(&bars[B_ACC + q]));
                 }
-                if (!ok) break;
-                mma_commit(smem_u32(&bars[2 * S]));
-                // layers 1..H read the activation tile written by the epilogue
+                // layers 1..H read the activation tile the epilogue wrote for that stage
                 for (int l = 1; l <= H && ok; l++) {
-                    if (!mbar_wait(smem_u32(&bars[2 * S + 1]), act_phase, abort_flag, status)) { ok = false; break; }
-                    act_phase ^= 1u;
-                    tc_fence_after();
-                    bool last = l == H;
-                    uint32_t wb = last ? smem_u32(sm + lay.wo_off)
-                                       : smem_u32(sm + lay.wh_off + (uint32_t)(l - 1) * lay.nbw * W * 128);
-                    uint32_t ab = smem_u32(sm + lay.a_off);
-                    for (int ks = 0; ks < lay.ksw; ks++) {
-                        uint32_t blk = (uint32_t)(ks >> 2), j = (uint32_t)(ks & 3);
-                        uint32_t aoff = blk * kRows * 128 + 32 * j;
-                        uint32_t boff = blk * (uint32_t)(last ? 16 : W) * 128 + 32 * j;
-                        mma_f16(tmem, sdesc(ab + aoff), sdesc(wb + boff), last ? id_out : id_hid, ks > 0 ? 1u : 0u);
+                    for (int q = 0; q < cnt && ok; q++) {
+                        const uint32_t acc = tmem + (uint32_t)q * kAccCols;
+                        if (!mbar_wait(smem_u32(&bars[B_ACT + q]), act_par[q], abort_flag, status)) { ok = false; break; }
+                        act_par[q] ^= 1u;
+                        tc_fence_after();
+                        const bool last = l == H;
+                        uint32_t wb = last ? smem_u32(sm + lay.wo_off)
+                                           : smem_u32(sm + lay.wh_off + (uint32_t)(l - 1) * lay.nbw * W * 128);
+                        uint32_t ab = smem_u32(sm + lay.a_off + (uint32_t)q * a_bytes);
+                        for (int ks = 0; ks < lay.ksw; ks++) {
+                            uint32_t blk = (uint32_t)(ks >> 2), jj = (uint32_t)(ks & 3);
+                            uint32_t aoff = blk * kRows * 128 + 32 * jj;
+                            uint32_t boff = blk * (uint32_t)(last ? 16 : W) * 128 + 32 * jj;
+                            mma_f16(acc, sdesc(ab + aoff), sdesc(wb + boff), last ? id_out : id_hid, ks > 0 ? 1u : 0u);
+                        }
+                        mma_commit(smem_u32(&bars[B_ACC + q]));
                     }
-                    mma_commit(smem_u32(&bars[2 * S]));
                 }
             }
             // all MMAs of this CTA complete before TMEM is released
-            mma_commit(smem_u32(&bars[2 * S + 2]));
+            mma_commit(smem_u32(&bars[B_DRAIN]));
             volatile int dummy = 0;
-            mbar_wait(smem_u32(&bars[2 * S + 2]), 0, &dummy, status);
+            mbar_wait(smem_u32(&bars[B_DRAIN]), 0, &dummy, status);
         }
     } else {
-        // ---------------- epilogue (warps 2..5) ----------------
-        const int q = warp & 3;                   // TMEM lane quarter this warp may access
-        const int row = q * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-        uint32_t acc_phase = 0;
-        uint8_t* A = sm + lay.a_off;
-        for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-            bool ok = true;
-            for (int l = 0; l <= H; l++) {
-                int got = 0;
-                if (lane == 0) got = mbar_wait(smem_u32(&bars[2 * S]), acc_phase, abort_flag, status) ? 1 : 0;
-                got = __shfl_sync(0xffffffffu, got, 0);
-                if (!got) { ok = false; break; }
-                acc_phase ^= 1u;
-                tc_fence_after();
-                if (l < H) {
-                    float v[32];
+        // ---------------- epilogue (warps 2..5), same pair order ----------------
+        const int qw = warp & 3;                  // TMEM lane quarter this warp may access
+        const int row = qw * 32 + lane;
+        uint32_t acc_par[2] = {0u, 0u};
+        bool ok = true;
+        for (int64_t j0 = 0; j0 < nt && ok; j0 += 2) {
+            const int cnt = nt - j0 < 2 ? (int)(nt - j0) : 2;
+            for (int l = 0; l <= H && ok; l++) {
+                for (int q = 0; q < cnt; q++) {
+                    int got = 0;
+                    if (lane == 0) got = mbar_wait(smem_u32(&bars[B_ACC + q]), acc_par[q], abort_flag, status) ? 1 : 0;
+                    got = __shfl_sync(0xffffffffu, got, 0);
+                    if (!got) { ok = false; break; }
+                    acc_par[q] ^= 1u;
+                    tc_fence_after();
+                    const uint32_t lane_base = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)q * kAccCols;
+                    if (l < H) {
+                        uint8_t* A = sm + lay.a_off + (uint32_t)q * a_bytes;
+                        float v[32];
 #pragma unroll
-                    for (int c0 = 0; c0 < W; c0 += 32) {
-                        tmem_ld32(lane_base + (uint32_t)c0, v);
+                        for (int c0 = 0; c0 < W; c0 += 32) {
+                            tmem_ld32(lane_base + (uint32_t)c0, v);
 #pragma unroll
-                        for (int c = 0; c < 32; c += 8) {
-                            uint4 pk;
-                            pk.x = pack2(fmaxf(v[c], 0.f), fmaxf(v[c + 1], 0.f), fmt);
-                            pk.y = pack2(fmaxf(v[c + 2], 0.f), fmaxf(v[c + 3], 0.f), fmt);
-                            pk.z = pack2(fmaxf(v[c + 4], 0.f), fmaxf(v[c + 5], 0.f), fmt);
-                            pk.w = pack2(fmaxf(v[c + 6], 0.f), fmaxf(v[c + 7], 0.f), fmt);
-                            *reinterpret_cast<uint4*>(A + swz_off(row, c0 + c, kRows)) = pk;
+                            for (int c = 0; c < 32; c += 8) {
+                                uint4 pk;
+                                pk.x = pack2(fmaxf(v[c], 0.f), fmaxf(v[c + 1], 0.f), fmt);
+                                pk.y = pack2(fmaxf(v[c + 2], 0.f), fmaxf(v[c + 3], 0.f), fmt);
+                                pk.z = pack2(fmaxf(v[c + 4], 0.f), fmaxf(v[c + 5], 0.f), fmt);
+                                pk.w = pack2(fmaxf(v[c + 6], 0.f), fmaxf(v[c + 7], 0.f), fmt);
+                                *reinterpret_cast<uint4*>(A + swz_off(row, c0 + c, kRows)) = pk;
+                            }
+                        }
+                        fence_async_smem();
+                    } else {
+                        float v[16];
+                        tmem_ld16(lane_base, v);
+                        int64_t t = blockIdx.x + (j0 + q) * gridDim.x;
+                        int64_t grow = t * kRows + row;
+                        if (grow < n) {
+                            float4* o = reinterpret_cast<float4*>(out + grow * NIF_OUT);
+                            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                            o[2] = make_float4(v[8], v[9], v[10], v[11]);
+                            o[3] = make_float4(v[12], v[13], v[14], v[15]);
                         }
                     }
-                    fence_async_smem();
-                } else {
-                    float v[16];
-                    tmem_ld16(lane_base, v);
-                    int64_t grow = t * kRows + row;
-                    if (grow < n) {
-                        float4* o = reinterpret_cast<float4*>(out + grow * NIF_OUT);
-                        o[0] = make_float4(v[0], v[1], v[2], v[3]);
-                        o[1] = make_float4(v[4], v[5], v[6], v[7]);
-                        o[2] = make_float4(v[8], v[9], v[10], v[11]);
-                        o[3] = make_float4(v[12], v[13], v[14], v[15]);
-                    }
+                    tc_fence_before();
+                    mbar_arrive(smem_u32(&bars[B_ACT + q]));
                 }
-                tc_fence_before();
-                mbar_arrive(smem_u32(&bars[2 * S + 1]));
             }
-            if (!ok) break;
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(W <= 32 ? 32u : (uint32_t)W)
-                     : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kAccCols) : "memory");
     }
 }
 
@@ -400,16 +423,16 @@ TcLayout make_layout(int W, int K0, int H) {
     L.wh_off = off;
     off += (uint32_t)(H - 1) * L.nbw * W * 128;
     L.a_off = off;
-    off += (uint32_t)L.nbw * kRows * 128;
+    off += 2u * (uint32_t)L.nbw * kRows * 128;      // one activation tile per accumulator stage
     L.x_off = off;
     // ring depth from what is left of the shared memory budget
     const uint32_t budget = 220 * 1024;
     int S = (int)((budget - off - 1024 - 256) / kStageBytes);
-    if (S > 8) S = 8;
+    if (S > 12) S = 12;
     L.stages = S;
     off += (uint32_t)S * kStageBytes;
     L.bar_off = off;
-    off += 8 * (2 * S + 4) + 16;
+    off += 8 * (2 * S + 6) + 16;
     L.total = off + 1024;        // room to align the dynamic buffer to 1024 bytes
     return L;
 }

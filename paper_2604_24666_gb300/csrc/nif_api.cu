@@ -783,9 +783,11 @@ extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst
     if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, total, lin, s)) != NIF_OK) return st;
     int prec = h->cfg.precision;
     size_t esz = prec == NIF_FP32 ? 4 : 2;
-    // encode + MLP in chunks whose feature rows stay resident in L2 between
-    // the two kernels (about 48 MB of features per chunk)
-    int64_t chunk = std::max<int64_t>(4096, ((int64_t)48 << 20) / ((int64_t)esz * h->in_dim));
+    // encode + MLP in chunks: FP32 chunks stay resident in L2 between the two
+    // kernels (48 MB of features); the tensor-core MLP is a persistent kernel
+    // whose pipeline needs many tiles per CTA, so its chunks are 2^20 rows.
+    int64_t chunk = prec == NIF_FP32 ? std::max<int64_t>(4096, ((int64_t)48 << 20) / ((int64_t)esz * h->in_dim))
+                                     : ((int64_t)1 << 20);
     chunk = std::min<int64_t>(chunk, n);
     if ((st = nif_grow(h, h->b_feat, esz * (size_t)h->in_dim * chunk)) != NIF_OK) return st;
     if (prec == NIF_FP32 &&
