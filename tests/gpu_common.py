@@ -42,3 +42,21 @@ def occupancy_biased_weights(net, seed):
     _, ws, s = S.init_params(net, seed=seed)
     ws[-1][0, :] *= 4.0
     return ws, s
+
+
+def evaluate_hits(mesh, pose, rays_np, hit, D, nrm, alb, mat):
+    """Errors of predicted first hits against the exact deformed-mesh hits:
+    hit IoU, distance MAE, mean normal angle (degrees), albedo L1 and
+    material accuracy over rays where both hit."""
+    t, tri = O.exact_hits(mesh, pose, rays_np)
+    gt = np.isfinite(t)
+    both = hit & gt
+    dv = O.deform(pose, mesh.verts.astype(np.float64))
+    tv = dv[mesh.tris[tri[both]]]
+    gn = np.cross(tv[:, 1] - tv[:, 0], tv[:, 2] - tv[:, 0])
+    gn /= np.linalg.norm(gn, axis=1, keepdims=True)
+    c = np.clip((nrm[both] * gn).sum(1), -1, 1)
+    return dict(iou=both.sum() / max(1, (hit | gt).sum()), dist=float(np.abs(D[both] - t[both]).mean()),
+                normal=float(np.degrees(np.arccos(c)).mean()),
+                albedo=float(np.abs(alb[both] - mesh.albedo[tri[both]]).mean()),
+                material=float((mat[both] == mesh.material[tri[both]]).mean()))
