@@ -209,8 +209,9 @@ nif_status nif_encode_segments(nif_handle* h, const nif_linseg* lin_dev, int64_t
                                void* feats_dev, int out_dtype, int table_dtype, void* stream);
 
 /* Backward of nif_encode_points: adds d(sum dfeats * psi)/d(table) into
- * dtables_dev [L][T][F_d] (FP32 atomics) and, if dpts_dev is not NULL,
- * writes d/dp [n][3] (zero where p was clamped). */
+ * dtables_dev [L][T][F_d] (FP32 atomics; NULL = the handle's own gradient
+ * buffer) and, if dpts_dev is not NULL, writes d/dp [n][3] (zero where p was
+ * clamped). */
 nif_status nif_encode_points_backward(nif_handle* h, const float* pts_dev, int64_t n,
                                       const float* dfeats_dev, float* dtables_dev,
                                       float* dpts_dev, void* stream);
@@ -219,6 +220,19 @@ nif_status nif_encode_points_backward(nif_handle* h, const float* pts_dev, int64
  * sum(dfeats * features) into dtables_dev [L][T][F_d]. */
 nif_status nif_encode_segments_backward(nif_handle* h, const nif_linseg* lin_dev, int64_t n,
                                         const float* dfeats_dev, float* dtables_dev, void* stream);
+
+/* Gradient with respect to the deformation parameters (pose fitting; the
+ * paper lists learning deformations as future work). For segments whose
+ * deformed end points x0 = o + t0 d, x1 = o + t1 d are held fixed, the rest
+ * points are p = D^-1(x; theta); with the tables and weights frozen this adds
+ * d(sum dfeats * [psi(p0) (+) psi(p1)])/d(bend, twist, taper) into
+ * dposes_dev [n_inst][3] (FP32, accumulated). dfeats_dev [n][in_dim] is the
+ * gradient with respect to the MLP input (nif_mlp_backward's dx).
+ * dp_dev (nullable, [n][2][3]) receives the intermediate dL/dp0, dL/dp1. */
+nif_status nif_pose_gradient(nif_handle* h, const nif_pose* poses_host, int n_inst,
+                             const int* inst_offsets_dev, const nif_segment* segs_dev,
+                             const nif_linseg* lin_dev, int64_t n, const float* dfeats_dev,
+                             float* dposes_dev, float* dp_dev, void* stream);
 
 /* MLP forward (Sec. 2, Fig. 2d): H ReLU layers without bias and a linear
  * output layer; out_dev [n][16] FP32. x_dev [n][in_dim] of x_dtype.

@@ -493,3 +493,25 @@ def reconstruct(cfg, pose, rays, seg: Segments, out, p0, p1, l_def, l_rest):
             acc += delta + np.linalg.norm(x1 - x0)
             prev = x1
     return res
+
+
+# ---------------------------------------------------------------------------
+# Gradient with respect to the deformation parameters (pose fitting)
+# ---------------------------------------------------------------------------
+
+def pose_gradient(cfg, tables, pose, p0, p1, dfeat):
+    """d/d(bend, twist, taper) of sum(dfeat * [psi(p0) (+) psi(p1)]) where the
+    rest points are p = D^-1(x; pose) of fixed deformed points x.
+
+    By the implicit function theorem, D(p(theta); theta) = x gives
+    dp/dtheta = -J_D(p)^-1 dD/dtheta(p); the encoding's input gradient comes
+    from `encode_points_backward`.
+    """
+    half = dfeat.shape[1] // 2
+    g = np.zeros(3)
+    for p, df in ((p0, dfeat[:, :half]), (p1, dfeat[:, half:])):
+        _, dp = encode_points_backward(cfg, tables, p, df)
+        J, Jp = jacobians(pose, p)
+        dpdth = -np.linalg.solve(J, Jp)            # [n, 3, 3]: d p_i / d theta_j
+        g += np.einsum("ni,nij->j", dp, dpdth)
+    return g

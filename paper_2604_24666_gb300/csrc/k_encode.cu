@@ -399,6 +399,60 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
     }
 }
 
+// Input gradient of the segment encoding with the tables held fixed:
+// dp[s][e][3] += d(sum dfeats * psi)/d p_e of segment s (zero where clamped).
+__global__ void __launch_bounds__(256) k_encode_segments_dp(GridInfo g, const float* __restrict__ tab,
+                                                            const nif_linseg* __restrict__ lin, int64_t n,
+                                                            const float* __restrict__ dfeats,
+                                                            float* __restrict__ dp) {
+    int per = 2 * g.P;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n * per;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = gid / per;
+        int r = (int)(gid - s * per);
+        int e = r >= g.P;
+        int t = r - e * g.P;
+        const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+        float3 raw = make_float3(L[0], L[1], L[2]);
+        float3 p = clamp01(raw);
+        float3 u = term_u(p, t);
+        float3 du = make_float3(0.f, 0.f, 0.f);
+        const float* df = dfeats + gid * g.L * 2;
+        for (int l = 0; l < g.L; l++) {
+            int Nl = g.res[l];
+            bool dense = (g.dense_mask >> l) & 1u;
+            Cell c = cell_of(u, Nl);
+            float2 gr = *reinterpret_cast<const float2*>(df + 2 * l);
+            const float* tl = tab + (int64_t)l * g.T * 2;
+            float3 d = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                uint32_t row = grid_row(c.ix + (q & 1), c.iy + ((q >> 1) & 1), c.iz + ((q >> 2) & 1), Nl, dense, g.T);
+                float fx = (q & 1) ? c.wx : 1.f - c.wx;
+                float fy = (q & 2) ? c.wy : 1.f - c.wy;
+                float fz = (q & 4) ? c.wz : 1.f - c.wz;
+                float2 v = __ldg(reinterpret_cast<const float2*>(tl) + row);
+                float val = v.x * gr.x + v.y * gr.y;
+                d.x += ((q & 1) ? 1.f : -1.f) * fy * fz * val;
+                d.y += ((q & 2) ? 1.f : -1.f) * fx * fz * val;
+                d.z += ((q & 4) ? 1.f : -1.f) * fx * fy * val;
+            }
+            float fn = (float)Nl;
+            du.x += fn * d.x;
+            du.y += fn * d.y;
+            du.z += fn * d.z;
+        }
+        float3 j = term_dudp(p, t);
+        if (raw.x < 0.f || raw.x > 1.f) j.x = 0.f;
+        if (raw.y < 0.f || raw.y > 1.f) j.y = 0.f;
+        if (raw.z < 0.f || raw.z > 1.f) j.z = 0.f;
+        float* o = dp + s * 6 + e * 3;
+        atomicAdd(o, du.x * j.x);
+        atomicAdd(o + 1, du.y * j.y);
+        atomicAdd(o + 2, du.z * j.z);
+    }
+}
+
 template <typename TT, typename OT>
 void launch_points(nif_handle* h, const TT* tab, const float* pts, int64_t n, void* feats, int32_t* rows,
                    cudaStream_t s) {
@@ -501,6 +555,19 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
     if (g > cap) g = cap;
     k_encode_segments_bwd<<<g, 256, 0, s>>>(h->grid, h->d_params + h->off_tables, lin, n_dev, n_max, dfeats,
                                             dtables);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_encode_segments_dp_run(nif_handle* h, const nif_linseg* lin, int64_t n, const float* dfeats, float* dp,
+                                      cudaStream_t s) {
+    NifProf prof_(h, "encode_dp", s);
+    if (n <= 0) return NIF_OK;
+    NIF_CK(h, cudaMemsetAsync(dp, 0, sizeof(float) * 6 * n, s));
+    unsigned g = nif_blocks(n * 2 * h->P, 256);
+    unsigned cap = (unsigned)h->num_sms * 16;
+    if (g > cap) g = cap;
+    k_encode_segments_dp<<<g, 256, 0, s>>>(h->grid, h->d_params + h->off_tables, lin, n, dfeats, dp);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

@@ -608,8 +608,27 @@ extern "C" nif_status nif_encode_segments(nif_handle* h, const nif_linseg* lin, 
 
 extern "C" nif_status nif_encode_points_backward(nif_handle* h, const float* pts, int64_t n, const float* dfeats,
                                                  float* dtables, float* dpts, void* stream) {
-    if (!h || n < 0 || (n > 0 && (!pts || !dfeats || !dtables))) return NIF_ERR_ARG;
+    if (!h || n < 0 || (n > 0 && (!pts || !dfeats))) return NIF_ERR_ARG;
+    if (!dtables) dtables = h->d_grad + h->off_tables;
     return nif_encode_points_bwd_run(h, pts, n, dfeats, dtables, dpts, (cudaStream_t)stream);
+}
+
+extern "C" nif_status nif_pose_gradient(nif_handle* h, const nif_pose* poses, int n_inst, const int* inst_off,
+                                        const nif_segment* segs, const nif_linseg* lin, int64_t n,
+                                        const float* dfeats, float* dposes, float* dp_out, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = check_inst(h, poses, n_inst, inst_off, 0);
+    if (st != NIF_OK) return st;
+    if (n < 0 || (n > 0 && (!segs || !lin || !dfeats || !dposes))) return nif_fail(h, NIF_ERR_ARG, "buffers");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
+    float* dp = dp_out;
+    if (!dp) {
+        if ((st = nif_grow(h, h->b_dx, sizeof(float) * 6 * (size_t)std::max<int64_t>(n, 1))) != NIF_OK) return st;
+        dp = (float*)h->b_dx.p;
+    }
+    if ((st = nif_encode_segments_dp_run(h, lin, n, dfeats, dp, s)) != NIF_OK) return st;
+    return nif_pose_grad_run(h, segs, lin, dp, n, inst_off, n_inst, dposes, s);
 }
 
 extern "C" nif_status nif_encode_segments_backward(nif_handle* h, const nif_linseg* lin, int64_t n,

@@ -181,6 +181,10 @@ nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n,
 nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev,
                                        int64_t n_max, const float* dfeats, float* dtables,
                                        cudaStream_t s);
+nif_status nif_encode_segments_dp_run(nif_handle* h, const nif_linseg* lin, int64_t n, const float* dfeats,
+                                      float* dp, cudaStream_t s);
+nif_status nif_pose_grad_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const float* dp,
+                             int64_t n, const int* inst_off, int n_inst, float* dposes, cudaStream_t s);
 nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
                                 float* out, float* acts, cudaStream_t s);
 nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
@@ -271,6 +275,41 @@ __device__ __forceinline__ void nif_jacobian_cols(float3 x, float4 pose, float3&
     j0 = make_float3(cb * T00, T10, -sb * T00);
     j1 = make_float3(cb * T01, T11, -sb * T01);
     j2 = make_float3(cb * T02 + m * sb, T12, -sb * T02 + m * cb);
+}
+
+// Columns of dD/d(kappa, twist, taper) at the rest point x (kappa is the
+// curvature; dD/d(bend) = NIF_KBEND * dD/dkappa).
+__device__ __forceinline__ void nif_param_jacobian_cols(float3 x, float4 pose, float3& dk, float3& dth,
+                                                        float3& dta) {
+    float px = x.x - 0.5f, py = x.y - 0.5f, pz = x.z - 0.5f;
+    float s = 1.0f + pose.z * pz;
+    float ax = s * px, ay = s * py;
+    float sa, ca;
+    sincosf(pose.y * pz, &sa, &ca);
+    float bx = ca * ax - sa * ay, by = sa * ax + ca * ay;
+    float be = pose.x * pz;
+    float sb, cb;
+    sincosf(be, &sb, &cb);
+    float m = 1.0f - pose.x * bx;
+    // bend: d/dkappa at fixed (bx, pz) with h1 = (be sb - 1 + cb)/be^2, h2 = (be cb - sb)/be^2
+    float h1, h2;
+    if (fabsf(be) < 0.25f) {
+        float b2 = be * be;
+        h1 = 0.5f - b2 * (1.0f / 8.0f) + b2 * b2 * (1.0f / 144.0f) - b2 * b2 * b2 * (1.0f / 5760.0f);
+        h2 = be * (-1.0f / 3.0f + b2 * (1.0f / 30.0f) - b2 * b2 * (1.0f / 840.0f));
+    } else {
+        h1 = (be * sb - 1.0f + cb) / (be * be);
+        h2 = (be * cb - sb) / (be * be);
+    }
+    dk = make_float3(-bx * pz * sb + pz * pz * h1, 0.f, -bx * pz * cb + pz * pz * h2);
+    // twist: d(b)/dtheta = pz (-by, bx, 0), then through the bend Jacobian
+    float tx = -pz * by, ty = pz * bx;
+    dth = make_float3(cb * tx, ty, -sb * tx);
+    // taper: d(a)/dta = pz (px, py, 0), through the twist then the bend
+    float ux = pz * px, uy = pz * py;
+    float wx = ca * ux - sa * uy, wy = sa * ux + ca * uy;
+    dta = make_float3(cb * wx, wy, -sb * wx);
+    (void)m;
 }
 
 __device__ __forceinline__ float3 nif_cross(float3 a, float3 b) {

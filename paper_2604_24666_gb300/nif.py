@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
             "nif_encode_segments": ([_vp, _vp, _i64, _vp, ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
             "nif_encode_points_backward": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
             "nif_encode_segments_backward": ([_vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+            "nif_pose_gradient": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
             "nif_mlp_forward": ([_vp, _vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
             "nif_mlp_backward": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
             "nif_labels": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
@@ -281,7 +282,8 @@ def nif_encode_segments(h, lin, in_dim, out_dtype=NIF_FP32, table_dtype=NIF_FP32
     return feats
 
 
-def nif_encode_points_backward(h, pts, dfeats, dtables, want_dpts=True, stream=None):
+def nif_encode_points_backward(h, pts, dfeats, dtables=None, want_dpts=True, stream=None):
+    """dtables None accumulates into the handle's own gradient buffer."""
     dpts = torch.zeros_like(pts) if want_dpts else None
     _check(h, lib().nif_encode_points_backward(h, _ptr(pts), pts.shape[0], _ptr(dfeats), _ptr(dtables), _ptr(dpts),
                                                _stream(stream)))
@@ -291,6 +293,16 @@ def nif_encode_points_backward(h, pts, dfeats, dtables, want_dpts=True, stream=N
 def nif_encode_segments_backward(h, lin, dfeats, dtables, stream=None):
     _check(h, lib().nif_encode_segments_backward(h, _ptr(lin), lin.shape[0], _ptr(dfeats), _ptr(dtables),
                                                  _stream(stream)))
+
+
+def nif_pose_gradient(h, poses, segs, lin, dfeats, inst_offsets=None, want_dp=False, stream=None):
+    """dL/d(bend, twist, taper) [n_inst, 3] of sum(dfeats * features) for fixed deformed end points."""
+    p, n_inst = _poses(poses)
+    dposes = torch.zeros((n_inst, 3), dtype=torch.float32, device=lin.device)
+    dp = torch.zeros((lin.shape[0], 6), dtype=torch.float32, device=lin.device) if want_dp else None
+    _check(h, lib().nif_pose_gradient(h, p, n_inst, _ptr(inst_offsets), _ptr(segs), _ptr(lin), lin.shape[0],
+                                      _ptr(dfeats), _ptr(dposes), _ptr(dp), _stream(stream)))
+    return (dposes, dp) if want_dp else dposes
 
 
 def nif_mlp_forward(h, x, precision=NIF_FP32, acts=None, stream=None):

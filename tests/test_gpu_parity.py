@@ -557,3 +557,77 @@ def test_query_mixed_precision_error_vs_oracle(nif, torus, prec):
     assert n_cmp > 500
     assert mat_n == 0 or mat_ok >= 0.99 * mat_n
     h.close()
+
+
+# ---------------------------------------------------------------------------
+# Differentiation: autograd over the library, gradients w.r.t. the pose
+# ---------------------------------------------------------------------------
+def test_autograd_function_matches_oracle(nif, torus):
+    from paper_2604_24666_gb300.autograd import nif_segments_forward
+    net = S.NetConfig(levels=8, log2_table=12)
+    h = nif.Nif(net, torus)
+    tables = random_tables(net, 151, scale=0.5)
+    _, ws, s = S.init_params(net, seed=152)
+    h.set_params(tables, ws, s)
+    nif.nif_zero_grad(h.h)
+    rng = np.random.default_rng(153)
+    n = 700
+    p0 = rng.uniform(0.05, 0.95, (n, 3)).astype(np.float32)
+    p1 = np.clip(p0 + rng.normal(0, 0.03, (n, 3)), 0.01, 0.99).astype(np.float32)
+    wout = rng.normal(size=(n, 16)).astype(np.float32)
+    wout[:, net.out_dim:] = 0
+    t0 = torch.from_numpy(p0).to(_dev()).requires_grad_(True)
+    t1 = torch.from_numpy(p1).to(_dev()).requires_grad_(True)
+    out = nif_segments_forward(t0, t1, h)
+    (out * torch.from_numpy(wout).to(_dev())).sum().backward()
+    torch.cuda.synchronize()
+    x = O.encode_segments(net, tables, p0.astype(np.float64), p1.astype(np.float64))
+    ro, racts = O.mlp_forward(ws, x)
+    np.testing.assert_allclose(out.detach().cpu().numpy(), ro, atol=2e-5 * np.abs(ro).max())
+    rdw, rdx = O.mlp_backward(ws, racts, wout.astype(np.float64))
+    half = net.in_dim // 2
+    rt0, rp0 = O.encode_points_backward(net, tables, p0.astype(np.float64), rdx[:, :half])
+    rt1, rp1 = O.encode_points_backward(net, tables, p1.astype(np.float64), rdx[:, half:])
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(t0.grad.cpu().numpy(), rp0) < 1e-3
+    assert rel(t1.grad.cpu().numpy(), rp1) < 1e-3
+    gt, gws, _ = h.get_grads()
+    assert rel(gt, rt0 + rt1) < 1e-3
+    for a, b in zip(gws, rdw):
+        assert rel(a, b) < 1e-4
+    h.close()
+
+
+def test_pose_gradient_matches_oracle(nif, torus):
+    net = S.NetConfig(levels=8, log2_table=12)
+    N = net.voxel_res
+    poses = np.array([[0.5, -0.9, 0.4], [-0.7, 0.6, -0.3]], np.float32)
+    parts = []
+    for i, seed in enumerate((161, 164)):
+        r = S.sphere_rays(700, seed=seed)
+        parts.append(r[certain_rays(N, torus, poses[i], r)])   # identical segment lists on both sides
+    rays_np = np.concatenate(parts)
+    inst = np.array([0, len(parts[0]), len(rays_np)], np.int32)
+    h = nif.Nif(net, torus)
+    tables = random_tables(net, 162, scale=0.5)
+    h.set_params(tables, S.init_params(net)[1])
+    rays = torch.from_numpy(rays_np).to(_dev())
+    it = torch.from_numpy(inst).to(_dev())
+    offs, segs = nif.nif_segments(h.h, poses, rays, inst_offsets=it)
+    lin = nif.nif_linearize(h.h, poses, rays, segs, inst_offsets=it)
+    n = segs.shape[0]
+    rng = np.random.default_rng(163)
+    df = rng.normal(size=(n, net.in_dim)).astype(np.float32)
+    dposes = nif.nif_pose_gradient(h.h, poses, segs, lin, torch.from_numpy(df).to(_dev()), inst_offsets=it)
+    torch.cuda.synchronize()
+    occ, _, _ = O.voxelize(N, torus)
+    ref = np.zeros((2, 3))
+    start = 0
+    for i in range(2):
+        seg = O.segments(N, occ, poses[i], parts[i])
+        p0, p1, _, _ = O.linearize(poses[i], parts[i], seg)
+        ref[i] = O.pose_gradient(net, tables, poses[i], p0, p1, df[start:start + len(seg)].astype(np.float64))
+        start += len(seg)
+    assert start == n
+    np.testing.assert_allclose(dposes.cpu().numpy(), ref, rtol=5e-3, atol=5e-3 * np.abs(ref).max())
+    h.close()

@@ -586,3 +586,30 @@ def test_reconstruction_collinear_identity_and_normal():
             if pose == (0, 0, 0):
                 nn = out[j, 2:5] / np.linalg.norm(out[j, 2:5])
                 np.testing.assert_allclose(res["normal"][r], nn, atol=1e-12)
+
+
+def test_pose_gradient_matches_finite_differences():
+    """Gradient of sum(w * psi(D^-1(x; theta))) over theta for fixed deformed
+    points x, against central differences of the oracle's own forward."""
+    cfg = _tiny_cfg()
+    rng = np.random.default_rng(14)
+    T = 1 << cfg.log2_table
+    tables = rng.uniform(-1, 1, (cfg.levels, T, 2))
+    pose = np.array([0.4, -0.7, 0.5])
+    x0 = rng.uniform(0.2, 0.8, (8, 3))
+    x1 = x0 + rng.normal(0, 0.02, (8, 3))
+    w = rng.normal(size=(8, cfg.in_dim))
+
+    def f(th):
+        p0 = O.inverse(th, x0)
+        p1 = O.inverse(th, x1)
+        return (O.encode_segments(cfg, tables, p0, p1) * w).sum()
+
+    g = O.pose_gradient(cfg, tables, pose, O.inverse(pose, x0), O.inverse(pose, x1), w)
+    # the cell coordinate is rounded to float32 (~6e-8), so the step must stay
+    # large against that; the cells of this tiny grid are >= 1/4 wide
+    h = 1e-3
+    for j in range(3):
+        e = np.zeros(3); e[j] = h
+        fd = (f(pose + e) - f(pose - e)) / (2 * h)
+        assert abs(fd - g[j]) <= 5e-3 * max(1.0, abs(fd)), (j, fd, g[j])
