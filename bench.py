@@ -294,6 +294,7 @@ def run_ours(args):
 
     # ---- inference queries ------------------------------------------------
     query = run_query(args, nif, S, dev, rank) if not args.no_query else None
+    batch = run_batch(args, nif, S, dev, rank) if not args.no_batch else None
 
     if rank != 0:
         return 0
@@ -317,7 +318,7 @@ def run_ours(args):
                        "mlp": "-".join(str(x) for x in [net.in_dim] + [net.mlp_width] * net.mlp_depth + [16]),
                        "l2": "working set larger than L2 (tables, gradients, Adam state 256 MB; features 604 MB)"},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "loss": list(loss) if loss is not None else None, "query": query}
+            "clocks": clocks, "loss": list(loss) if loss is not None else None, "query": query, "batch": batch}
     print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -383,6 +384,49 @@ def run_query(args, nif, S, dev, rank):
     return res
 
 
+BATCH_WORKLOAD = "torus16x64_batch"
+
+
+def run_batch(args, nif, S, dev, rank):
+    """Batched mixed-precision queries of 64 deforming instances with Zipf ray
+    counts (about 2^22 rays), one autotuned CUDA-graph replay per step."""
+    import torch
+    w = S.WORKLOADS[BATCH_WORKLOAD]
+    net = w["net"]
+    mesh = S.make_mesh(w["shape"])
+    counts = S.zipf_ray_counts(w["n_inst"], seed=700 + rank)
+    rays_np = np.concatenate([S.sphere_rays(int(c), seed=1000 * rank + 710 + i) for i, c in enumerate(counts)])
+    inst = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    n = len(rays_np)
+    h = nif.Nif(net, mesh, precision=nif.NIF_BF16, seed=41)
+    rays = torch.from_numpy(rays_np).to(dev)
+    it = torch.from_numpy(inst).to(dev)
+    hits = torch.zeros((n, 8), dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(720 + rank)
+    poses = [rng.uniform(-1, 1, (w["n_inst"], 3)).astype(np.float32) for _ in range(args.steps + args.warmup)]
+    t0 = time.perf_counter()
+    plan = nif.QueryPlan(h.h, poses[0], rays, hits, inst_offsets=it, autotune=True)
+    tune_s = time.perf_counter() - t0
+    for i in range(args.warmup):
+        plan.run(poses[i])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        plan.run(poses[args.warmup + i])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    res = {"workload": BATCH_WORKLOAD, "instances": int(w["n_inst"]), "rays_per_step": int(n),
+           "rays_per_instance_min_max": [int(counts.min()), int(counts.max())], "precision": "bf16",
+           "queries_per_s": n / (ms / 1e3), "ms_per_batch": ms, "graph": True, "knobs": plan.info(),
+           "autotune_s": tune_s,
+           "hit_rate": float((hits[:, 7].view(torch.int32) & 0xff).ne(0).float().mean().item())}
+    plan.close()
+    h.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,6 +438,7 @@ def main():
     ap.add_argument("--only-query", action="store_true", help="measure only the inference queries (profiling aid)")
     ap.add_argument("--query-rays", type=int, default=0, help="rays per query batch (default: the workload's 2^22)")
     ap.add_argument("--query-prec", default="fp32,bf16,fp16", help="comma list of query precisions")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance query measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -325,6 +325,34 @@ nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses,
 nif_status nif_sample_rays(nif_handle* h, unsigned long long step_seed, int stream_id, int n,
                            nif_ray* rays_dev, void* stream);
 
+/* Batched query as one CUDA graph. A plan binds the caller's device buffers
+ * (n_rays rays split over n_inst instances by inst_offsets_dev, hits_dev)
+ * and a segment capacity (seg_capacity <= 0: 1.5 x the segments of
+ * poses_host), optionally autotunes the launch knobs on those buffers
+ * (traversal warps per block, encoding block size and grid, rows per
+ * encode + MLP chunk; the choice is kept in the handle and used by
+ * nif_query too) and captures the whole query path -- pose upload, refit,
+ * segments, linearization, encoding, MLP (cfg.precision), reconstruction --
+ * with every element count kept on the device. nif_query_plan_create blocks;
+ * nif_query_plan_run copies new poses into a pinned buffer (after the
+ * previous replay of this plan finished) and launches the graph on
+ * `stream` without further host synchronisation. Overflow of the segment
+ * capacity is latched in the status word (nif_sync_status). The rays'
+ * contents may change between runs; their buffers may not. A plan must be
+ * destroyed before its handle. */
+typedef struct nif_query_plan nif_query_plan;
+nif_status nif_query_plan_create(nif_handle* h, int n_inst, const nif_ray* rays_dev,
+                                 const int* inst_offsets_dev, int n_rays, nif_hit* hits_dev,
+                                 int64_t seg_capacity, unsigned flags, int autotune,
+                                 const nif_pose* poses_host, nif_query_plan** out);
+nif_status nif_query_plan_run(nif_query_plan* plan, const nif_pose* poses_host, void* stream);
+nif_status nif_query_plan_info(const nif_query_plan* plan, int* trav_warps, int* enc_threads,
+                               int* enc_blocks_per_sm, int64_t* tc_chunk, int64_t* seg_capacity);
+void nif_query_plan_destroy(nif_query_plan* plan);
+
+/* Synchronises `stream` and returns (and clears) the device status word. */
+nif_status nif_sync_status(nif_handle* h, void* stream);
+
 /* Allocation-free variant of nif_segments (the paper has no counterpart:
  * this is an integration aid). For callers that cannot call cudaMalloc -- a
  * host application that owns all device memory through its own fixed-budget

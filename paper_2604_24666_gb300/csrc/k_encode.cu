@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_encode_points(GridInfo g, const TT* __r
 }
 
 template <typename TT, typename OT>
-__global__ void __launch_bounds__(256) k_encode_segments(GridInfo g, const TT* __restrict__ tab,
+__global__ void __launch_bounds__(512) k_encode_segments(GridInfo g, const TT* __restrict__ tab,
                                                          const nif_linseg* __restrict__ lin,
                                                          const uint32_t* __restrict__ n_dev, int64_t n_max,
                                                          OT* __restrict__ out) {
@@ -462,10 +462,12 @@ void launch_points(nif_handle* h, const TT* tab, const float* pts, int64_t n, vo
 template <typename TT, typename OT>
 void launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
                      void* feats, cudaStream_t s) {
-    unsigned g = nif_blocks(n_max * 2 * h->P, 256);
-    unsigned cap = (unsigned)h->num_sms * 16;
+    // block size and resident blocks per SM are tuning knobs of the handle
+    int thr = h->tune.enc_threads;
+    unsigned g = nif_blocks(n_max * 2 * h->P, thr);
+    unsigned cap = (unsigned)h->num_sms * (unsigned)h->tune.enc_blocks_per_sm;
     if (g > cap) g = cap;
-    k_encode_segments<TT, OT><<<g, 256, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
+    k_encode_segments<TT, OT><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
 }
 
 }  // namespace

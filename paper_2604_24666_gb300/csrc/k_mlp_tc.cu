@@ -61,16 +61,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 // try_wait suspends the thread until the phase completes or a hardware
 // time limit passes, so it wakes up as soon as the barrier flips.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
@@ -201,7 +191,9 @@ __device__ void load_weight(uint8_t* dst, const uint16_t* __restrict__ src, int 
 template <int W>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mlp_tc(const __grid_constant__ CUtensorMap xmap, TcLayout lay, const uint16_t* __restrict__ wts,
-             int K0, int H, int fmt, int64_t n, float* __restrict__ out, int* __restrict__ status) {
+             int K0, int H, int fmt, int64_t n_max, const uint32_t* __restrict__ n_dev, float* __restrict__ out,
+             int* __restrict__ status) {
+    const int64_t n = n_dev ? ((int64_t)*n_dev < n_max ? (int64_t)*n_dev : n_max) : n_max;
     constexpr uint32_t kAccCols = W < 32 ? 32 : W;     // TMEM columns of one accumulator stage
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment of the dynamic buffer (swizzle atoms)
@@ -438,7 +430,8 @@ TcLayout make_layout(int W, int K0, int H) {
 }
 
 template <int W>
-nif_status launch_tc(nif_handle* h, const void* x, int dtype, int64_t n, float* out, cudaStream_t s) {
+nif_status launch_tc(nif_handle* h, const void* x, int dtype, int64_t n, const uint32_t* n_dev, float* out,
+                     cudaStream_t s) {
     TcLayout lay = make_layout(W, h->in_dim, h->H);
     for (int l = 0; l < h->n_layers; l++) {
         lay.woff[l] = (uint32_t)(h->off_layer[l] - h->off_layer[0]);
@@ -460,8 +453,8 @@ nif_status launch_tc(nif_handle* h, const void* x, int dtype, int64_t n, float* 
     int grid = (int)std::min<int64_t>(n_tiles, h->num_sms);
     const uint16_t* w = reinterpret_cast<const uint16_t*>(dtype == NIF_BF16 ? (const void*)h->d_w_bf16
                                                                              : (const void*)h->d_w_f16);
-    k_mlp_tc<W><<<grid, kThreads, lay.total, s>>>(map, lay, w, h->in_dim, h->H, dtype == NIF_BF16 ? 1 : 0, n, out,
-                                                  h->d_status);
+    k_mlp_tc<W><<<grid, kThreads, lay.total, s>>>(map, lay, w, h->in_dim, h->H, dtype == NIF_BF16 ? 1 : 0, n, n_dev,
+                                                  out, h->d_status);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
@@ -471,7 +464,6 @@ nif_status launch_tc(nif_handle* h, const void* x, int dtype, int64_t n, float* 
 nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev, int64_t n_max,
                               float* out, cudaStream_t s) {
     NifProf prof_(h, "mlp_fwd_tc", s);
-    if (n_dev) return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP needs a host row count");
     if (n_max <= 0) return NIF_OK;
     if (dtype != NIF_BF16 && dtype != NIF_FP16) return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP dtype");
     if (h->in_dim % 8 != 0) return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP needs in_dim % 8 == 0");
@@ -480,9 +472,9 @@ nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uin
     if (st != NIF_OK) return st;
     if ((st = nif_refresh_lowp(h, s)) != NIF_OK) return st;
     switch (h->W) {
-        case 32: return launch_tc<32>(h, x, dtype, n_max, out, s);
-        case 64: return launch_tc<64>(h, x, dtype, n_max, out, s);
-        case 128: return launch_tc<128>(h, x, dtype, n_max, out, s);
+        case 32: return launch_tc<32>(h, x, dtype, n_max, n_dev, out, s);
+        case 64: return launch_tc<64>(h, x, dtype, n_max, n_dev, out, s);
+        case 128: return launch_tc<128>(h, x, dtype, n_max, n_dev, out, s);
         default: return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP width must be 32, 64 or 128");
     }
 }

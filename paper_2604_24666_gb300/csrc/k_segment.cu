@@ -185,7 +185,6 @@ __device__ __forceinline__ int find_inst(const int* inst_off, int n_inst, int r)
 }
 
 constexpr int kStack = 96;
-constexpr int kTravWarps = 4;      // warps per traversal block
 
 // Modes of the traversal kernel
 enum { kModeCount = 0, kModeEmit = 1, kModeTemp = 2 };
@@ -202,7 +201,7 @@ enum { kModeCount = 0, kModeEmit = 1, kModeTemp = 2 };
 //               of their ray, then each ray's list sorted by (t0, voxel);
 //   kModeTemp:  counts plus every segment appended to `temp` at a
 //               warp-reserved position (ray order is restored by a scatter).
-template <int MODE>
+template <int MODE, int kTravWarps>
 __global__ void __launch_bounds__(kTravWarps * 32) k_seg_traverse(
     const nif_ray* __restrict__ rays, const int* __restrict__ inst_off, int n_inst, int n_rays,
     TreeView tree, const float* __restrict__ corners, const float4* __restrict__ aabb,
@@ -330,9 +329,11 @@ __global__ void __launch_bounds__(kTravWarps * 32) k_seg_traverse(
 // Moves the ray-unordered segments of kModeTemp to their ray's CSR rows
 // (fill[] zeroed, one counter per ray) ...
 __global__ void __launch_bounds__(256) k_seg_scatter(const nif_segment* __restrict__ temp, const uint32_t* __restrict__ n_temp,
-                                                     const uint32_t* __restrict__ offsets, uint32_t* __restrict__ fill,
-                                                     nif_segment* __restrict__ segs, int64_t cap) {
+                                                     int64_t temp_cap, const uint32_t* __restrict__ offsets,
+                                                     uint32_t* __restrict__ fill, nif_segment* __restrict__ segs,
+                                                     int64_t cap) {
     int64_t n = *n_temp;
+    if (n > temp_cap) n = temp_cap;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         nif_segment sg = temp[i];
         int64_t g = (int64_t)offsets[sg.ray] + atomicAdd(fill + sg.ray, 1u);
@@ -495,6 +496,32 @@ nif_status nif_refit_run(nif_handle* h, int n_inst, cudaStream_t s) {
     return NIF_OK;
 }
 
+static TreeView tree_view(nif_handle* h);
+
+// warps per traversal block: a tuning knob of the handle (2, 4 or 8)
+template <int MODE>
+static void launch_traverse(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                            uint32_t* counts, const uint32_t* offsets, nif_segment* segs, int64_t cap,
+                            uint32_t* cursor, cudaStream_t s) {
+    TreeView tv = tree_view(h);
+    switch (h->tune.trav_warps) {
+        case 2:
+            k_seg_traverse<MODE, 2><<<nif_blocks(n_rays, 64), 64, 0, s>>>(rays, inst_off, n_inst, n_rays, tv, h->d_corners,
+                                                                       h->d_aabb, counts, offsets, segs, cap, cursor,
+                                                                       h->d_status);
+            break;
+        case 8:
+            k_seg_traverse<MODE, 8><<<nif_blocks(n_rays, 256), 256, 0, s>>>(rays, inst_off, n_inst, n_rays, tv,
+                                                                         h->d_corners, h->d_aabb, counts, offsets, segs,
+                                                                         cap, cursor, h->d_status);
+            break;
+        default:
+            k_seg_traverse<MODE, 4><<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, tv,
+                                                                         h->d_corners, h->d_aabb, counts, offsets, segs,
+                                                                         cap, cursor, h->d_status);
+    }
+}
+
 static TreeView tree_view(nif_handle* h) {
     TreeView t;
     t.n_leaves = h->n_leaves;
@@ -514,9 +541,7 @@ nif_status nif_seg_count_run(nif_handle* h, const nif_ray* rays, const int* inst
         NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n_rays, s));
         return NIF_OK;
     }
-    k_seg_traverse<kModeCount><<<nif_blocks(n_rays, kTravWarps * 32), kTravWarps * 32, 0, s>>>(
-        rays, inst_off, n_inst, n_rays, tree_view(h), h->d_corners, h->d_aabb, counts, nullptr, nullptr, 0, nullptr,
-        h->d_status);
+    launch_traverse<kModeCount>(h, rays, inst_off, n_inst, n_rays, counts, nullptr, nullptr, 0, nullptr, s);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
@@ -525,9 +550,7 @@ nif_status nif_seg_emit_run(nif_handle* h, const nif_ray* rays, const int* inst_
                             const uint32_t* offsets, nif_segment* segs, int64_t cap, cudaStream_t s) {
     NifProf prof_(h, "seg_emit", s);
     if (n_rays <= 0 || h->n_leaves == 0) return NIF_OK;
-    k_seg_traverse<kModeEmit><<<nif_blocks(n_rays, kTravWarps * 32), kTravWarps * 32, 0, s>>>(
-        rays, inst_off, n_inst, n_rays, tree_view(h), h->d_corners, h->d_aabb, nullptr, offsets, segs, cap, nullptr,
-        h->d_status);
+    launch_traverse<kModeEmit>(h, rays, inst_off, n_inst, n_rays, nullptr, offsets, segs, cap, nullptr, s);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
@@ -543,9 +566,7 @@ nif_status nif_seg_temp_run(nif_handle* h, const nif_ray* rays, const int* inst_
         NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n_rays, s));
         return NIF_OK;
     }
-    k_seg_traverse<kModeTemp><<<nif_blocks(n_rays, kTravWarps * 32), kTravWarps * 32, 0, s>>>(
-        rays, inst_off, n_inst, n_rays, tree_view(h), h->d_corners, h->d_aabb, counts, nullptr, temp, temp_cap, cursor,
-        h->d_status);
+    launch_traverse<kModeTemp>(h, rays, inst_off, n_inst, n_rays, counts, nullptr, temp, temp_cap, cursor, s);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
@@ -559,7 +580,7 @@ nif_status nif_seg_scatter_run(nif_handle* h, const nif_segment* temp, const uin
     unsigned g = nif_blocks(std::max<int64_t>(n_temp_max, 1), 256);
     unsigned gcap = (unsigned)h->num_sms * 8;
     if (g > gcap) g = gcap;
-    k_seg_scatter<<<g, 256, 0, s>>>(temp, n_temp, offsets, fill, segs, cap);
+    k_seg_scatter<<<g, 256, 0, s>>>(temp, n_temp, n_temp_max, offsets, fill, segs, cap);
     NIF_CK_LAUNCH(h);
     k_seg_sort<<<nif_blocks(n_rays, 256), 256, 0, s>>>(offsets, n_rays, segs, cap);
     NIF_CK_LAUNCH(h);

@@ -806,7 +806,7 @@ extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst
     // kernels (48 MB of features); the tensor-core MLP is a persistent kernel
     // whose pipeline needs many tiles per CTA, so its chunks are 2^20 rows.
     int64_t chunk = prec == NIF_FP32 ? std::max<int64_t>(4096, ((int64_t)48 << 20) / ((int64_t)esz * h->in_dim))
-                                     : ((int64_t)1 << 20);
+                                     : h->tune.tc_chunk;
     chunk = std::min<int64_t>(chunk, n);
     if ((st = nif_grow(h, h->b_feat, esz * (size_t)h->in_dim * chunk)) != NIF_OK) return st;
     if (prec == NIF_FP32 &&

@@ -97,6 +97,14 @@ struct nif_handle {
         b_scan, b_rays, b_inst, b_feat2, b_temp;
     double query_seg_per_ray = 0.0;     // segments per ray of the last query (temp capacity hint)
 
+    // launch knobs chosen by the autotuner (nif_query_plan_create)
+    struct Tune {
+        int trav_warps = 4;             // warps per traversal block
+        int enc_threads = 256;          // encoding block size
+        int enc_blocks_per_sm = 16;     // encoding grid cap per SM (grid-stride beyond)
+        int64_t tc_chunk = 1 << 20;     // rows per encode + tensor-core MLP chunk
+    } tune;
+
     std::string err;
     int num_sms = 0;
     double seg_per_ray = 0.0;           // measured segments per sampled training ray
@@ -290,7 +298,6 @@ __device__ __forceinline__ void nif_param_jacobian_cols(float3 x, float4 pose, f
     float be = pose.x * pz;
     float sb, cb;
     sincosf(be, &sb, &cb);
-    float m = 1.0f - pose.x * bx;
     // bend: d/dkappa at fixed (bx, pz) with h1 = (be sb - 1 + cb)/be^2, h2 = (be cb - sb)/be^2
     float h1, h2;
     if (fabsf(be) < 0.25f) {
@@ -309,7 +316,6 @@ __device__ __forceinline__ void nif_param_jacobian_cols(float3 x, float4 pose, f
     float ux = pz * px, uy = pz * py;
     float wx = ca * ux - sa * uy, wy = sa * ux + ca * uy;
     dta = make_float3(cb * wx, wy, -sb * wx);
-    (void)m;
 }
 
 __device__ __forceinline__ float3 nif_cross(float3 a, float3 b) {

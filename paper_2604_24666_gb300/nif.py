@@ -106,6 +106,14 @@ def lib() -> ctypes.CDLL:
             "nif_sample_rays": ([_vp, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
             "nif_segments_noalloc": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _i64,
                                       ctypes.POINTER(_i64), _vp], ctypes.c_int),
+            "nif_query_plan_create": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _i64, ctypes.c_uint,
+                                       ctypes.c_int, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+            "nif_query_plan_run": ([_vp, _vp, _vp], ctypes.c_int),
+            "nif_query_plan_info": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), ctypes.POINTER(_i64)],
+                                    ctypes.c_int),
+            "nif_query_plan_destroy": ([_vp], None),
+            "nif_sync_status": ([_vp, _vp], ctypes.c_int),
             "nif_kernel_launches": ([], ctypes.c_ulonglong),
             "nif_profile": ([_vp, ctypes.c_int], ctypes.c_int),
             "nif_profile_read": ([_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -370,6 +378,43 @@ def nif_sample_rays(h, step_seed, stream_id, n, device="cuda", stream=None):
     rays = torch.zeros((n, 8), dtype=torch.float32, device=device)
     _check(h, lib().nif_sample_rays(h, step_seed, stream_id, n, _ptr(rays), _stream(stream)))
     return rays
+
+
+class QueryPlan:
+    """A captured batched query (nif_query_plan_*); buffers stay bound to it."""
+
+    def __init__(self, h, poses, rays, hits, inst_offsets=None, seg_capacity=0, flags=0, autotune=True):
+        p, n_inst = _poses(poses)
+        self.h = h
+        self.n_inst = n_inst
+        self._keep = (rays, hits, inst_offsets)
+        out = ctypes.c_void_p()
+        _check(h, lib().nif_query_plan_create(h, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0], _ptr(hits),
+                                              int(seg_capacity), flags, int(autotune), p, ctypes.byref(out)))
+        self.p = out
+
+    def run(self, poses, stream=None):
+        p, n_inst = _poses(poses)
+        if n_inst != self.n_inst:
+            raise ValueError("pose count differs from the plan's")
+        _check(self.h, lib().nif_query_plan_run(self.p, p, _stream(stream)))
+
+    def info(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        d, e = _i64(), _i64()
+        _check(self.h, lib().nif_query_plan_info(self.p, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                                 ctypes.byref(d), ctypes.byref(e)))
+        return dict(trav_warps=a.value, enc_threads=b.value, enc_blocks_per_sm=c.value, tc_chunk=d.value,
+                    seg_capacity=e.value)
+
+    def close(self):
+        if self.p:
+            lib().nif_query_plan_destroy(self.p)
+            self.p = None
+
+
+def nif_sync_status(h, stream=None):
+    _check(h, lib().nif_sync_status(h, _stream(stream)))
 
 
 def nif_kernel_launches() -> int:

@@ -631,3 +631,34 @@ def test_pose_gradient_matches_oracle(nif, torus):
     assert start == n
     np.testing.assert_allclose(dposes.cpu().numpy(), ref, rtol=5e-3, atol=5e-3 * np.abs(ref).max())
     h.close()
+
+
+# ---------------------------------------------------------------------------
+# Batched query captured as a CUDA graph
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_query_plan_graph_replays_match_query(nif, torus, prec):
+    net = S.NetConfig()
+    p = nif.NIF_BF16 if prec == "bf16" else nif.NIF_FP32
+    h = nif.Nif(net, torus, precision=p)
+    tables = random_tables(net, 171)
+    ws, s = occupancy_biased_weights(net, 172)
+    h.set_params(tables, ws, s)
+    counts = [900, 0, 1300, 17]
+    inst = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)).to(_dev())
+    rays = torch.from_numpy(S.sphere_rays(sum(counts), seed=173)).to(_dev())
+    hits = torch.zeros((sum(counts), 8), dtype=torch.float32, device=_dev())
+    poses_a = S.poses(4, seed=174)
+    poses_b = S.poses(4, seed=175)
+    plan = nif.QueryPlan(h.h, poses_a, rays, hits, inst_offsets=inst, autotune=True)
+    knobs = plan.info()
+    assert knobs["trav_warps"] in (2, 4, 8) and knobs["enc_threads"] in (128, 256, 512)
+    for poses in (poses_a, poses_b, poses_a):
+        plan.run(poses)
+        nif.nif_sync_status(h.h)
+        ref = nif.nif_query(h.h, poses, rays, inst_offsets=inst)
+        torch.cuda.synchronize()
+        assert torch.equal(hits.view(torch.int32), ref.view(torch.int32))
+    assert int((hits[:, 7].view(torch.int32) & 0xff).ne(0).sum()) > 100
+    plan.close()
+    h.close()
