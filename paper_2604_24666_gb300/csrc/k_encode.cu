@@ -141,6 +141,109 @@ __global__ void __launch_bounds__(256) k_encode_points(GridInfo g, const TT* __r
     grid_all_levels<TT, OT>(g, tab, u, out, gid * g.L * 2, rows, gid * g.L);
 }
 
+// Forward over segments, all levels of one (segment, endpoint, term) in
+// registers: corner rows from one base index (dense) or three partial hashes,
+// weights from the x-y products, and the L feature pairs written with 16-byte
+// stores at the end (LMAX >= L, compile-time for full unrolling).
+template <typename OT>
+struct OutPair;
+template <>
+struct OutPair<float> {
+    using T = float2;
+    static __device__ __forceinline__ T make(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct OutPair<__nv_bfloat16> {
+    using T = __nv_bfloat162;
+    static __device__ __forceinline__ T make(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+template <>
+struct OutPair<__half> {
+    using T = __half2;
+    static __device__ __forceinline__ T make(float a, float b) { return __floats2half2_rn(a, b); }
+};
+
+template <typename TT, typename OT, int LMAX>
+__global__ void __launch_bounds__(512) k_encode_segments_v(GridInfo g, const TT* __restrict__ tab,
+                                                           const nif_linseg* __restrict__ lin,
+                                                           const uint32_t* __restrict__ n_dev, int64_t n_max,
+                                                           OT* __restrict__ out) {
+    using P2 = typename OutPair<OT>::T;
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    const int per = 2 * g.P;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n * per;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = gid / per;
+        int r = (int)(gid - s * per);
+        int e = r >= g.P;
+        int t = r - e * g.P;
+        const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+        float3 u = term_u(clamp01(make_float3(L[0], L[1], L[2])), t);
+        P2 res[LMAX];
+#pragma unroll
+        for (int l = 0; l < LMAX; l++) {
+            if (l >= g.L) break;
+            const int Nl = g.res[l];
+            const Cell c = cell_of(u, Nl);
+            const TT* tl = tab + (int64_t)l * g.T * 2;
+            uint32_t rows[8];
+            if ((g.dense_mask >> l) & 1u) {
+                const uint32_t sy = (uint32_t)Nl + 1u, sz = sy * sy;
+                const uint32_t b = (uint32_t)c.ix + (uint32_t)c.iy * sy + (uint32_t)c.iz * sz;
+                rows[0] = b; rows[1] = b + 1u; rows[2] = b + sy; rows[3] = b + sy + 1u;
+                rows[4] = b + sz; rows[5] = b + sz + 1u; rows[6] = b + sz + sy; rows[7] = b + sz + sy + 1u;
+            } else {
+                const uint32_t m = g.T - 1u;
+                const uint32_t x0 = (uint32_t)c.ix, x1 = x0 + 1u;
+                const uint32_t y0 = (uint32_t)c.iy * 2654435761u, y1 = y0 + 2654435761u;
+                const uint32_t z0 = (uint32_t)c.iz * 805459861u, z1 = z0 + 805459861u;
+                rows[0] = (x0 ^ y0 ^ z0) & m; rows[1] = (x1 ^ y0 ^ z0) & m;
+                rows[2] = (x0 ^ y1 ^ z0) & m; rows[3] = (x1 ^ y1 ^ z0) & m;
+                rows[4] = (x0 ^ y0 ^ z1) & m; rows[5] = (x1 ^ y0 ^ z1) & m;
+                rows[6] = (x0 ^ y1 ^ z1) & m; rows[7] = (x1 ^ y1 ^ z1) & m;
+            }
+            float2 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) v[q] = load_row<TT>(tl, rows[q]);
+            const float wx1 = c.wx, wx0 = 1.f - c.wx, wy1 = c.wy, wy0 = 1.f - c.wy;
+            const float wz1 = c.wz, wz0 = 1.f - c.wz;
+            const float wxy[4] = {wx0 * wy0, wx1 * wy0, wx0 * wy1, wx1 * wy1};
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const float w = wxy[q & 3] * ((q & 4) ? wz1 : wz0);
+                acc.x += w * v[q].x;
+                acc.y += w * v[q].y;
+            }
+            res[l] = OutPair<OT>::make(acc.x, acc.y);
+        }
+        P2* o = reinterpret_cast<P2*>(out + gid * g.L * 2);
+        constexpr int per16 = 16 / sizeof(P2);           // pairs per 16-byte store
+        if ((g.L % per16) == 0) {
+#pragma unroll
+            for (int l = 0; l < LMAX; l += per16) {
+                if (l >= g.L) break;
+                uint4 w4;
+                uint32_t* w = reinterpret_cast<uint32_t*>(&w4);
+#pragma unroll
+                for (int k = 0; k < per16; k++) {
+                    const uint32_t* src = reinterpret_cast<const uint32_t*>(&res[l + k]);
+#pragma unroll
+                    for (int q = 0; q < (int)(sizeof(P2) / 4); q++) w[k * (sizeof(P2) / 4) + q] = src[q];
+                }
+                *reinterpret_cast<uint4*>(o + l) = w4;
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l < LMAX; l++) {
+                if (l >= g.L) break;
+                o[l] = res[l];
+            }
+        }
+    }
+}
+
 template <typename TT, typename OT>
 __global__ void __launch_bounds__(512) k_encode_segments(GridInfo g, const TT* __restrict__ tab,
                                                          const nif_linseg* __restrict__ lin,
@@ -467,7 +570,12 @@ void launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, const 
     unsigned g = nif_blocks(n_max * 2 * h->P, thr);
     unsigned cap = (unsigned)h->num_sms * (unsigned)h->tune.enc_blocks_per_sm;
     if (g > cap) g = cap;
-    k_encode_segments<TT, OT><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
+    if (h->L <= 8)
+        k_encode_segments_v<TT, OT, 8><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
+    else if (h->L <= 16)
+        k_encode_segments_v<TT, OT, 16><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
+    else
+        k_encode_segments<TT, OT><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
 }
 
 }  // namespace
