@@ -95,10 +95,192 @@ __global__ void __launch_bounds__(256) k_sgemm(GemmArgs a) {
     }
 }
 
+// Register-blocked SGEMM for the large products (N a multiple of 64, K a
+// multiple of 16 apart from a device-side tail): BMT x 64 output tile, 16-deep
+// K slices double-buffered in shared memory (k-major, so each thread reads
+// its rows and columns as float4), fed by float4 global loads held in
+// registers while the previous slice is multiplied; each of the 256 threads
+// owns a (BMT/16) x 4 block of outputs.
+template <int EPI, int BMT>
+__global__ void __launch_bounds__(256) k_sgemm_big(GemmArgs a) {
+    constexpr int BNT = 64, BKT = 16, TM = BMT / 16, LA = BMT / 16;
+    __shared__ __align__(16) float sA[2][BKT][BMT];
+    __shared__ __align__(16) float sB[2][BKT][BNT];
+    int64_t M = a.M, K = a.K;
+    if (a.M_dev) {
+        int64_t m = (int64_t)*a.M_dev;
+        if (a.m_is_k) K = m < K ? m : K;
+        else M = m < M ? m : M;
+    }
+    const int64_t i0 = (int64_t)blockIdx.y * BMT;
+    const int j0 = blockIdx.x * BNT;
+    if (i0 >= M) return;
+    int64_t kb = 0, ke = K;
+    if (EPI == kAtomic) {
+        kb = (int64_t)blockIdx.z * a.k_chunk;
+        ke = kb + a.k_chunk < K ? kb + a.k_chunk : K;
+        if (kb >= ke) return;
+    }
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const bool a_krow = a.sak == 1;
+    const bool b_jrow = a.sbj == 1;
+    // global -> register staging of one K slice
+    float ra[LA], rb[4];
+    auto load_slice = [&](int64_t k0) {
+        const bool full = k0 + BKT <= ke;
+        if (a_krow) {
+            const int row = tid / (BKT / LA), kk = (tid % (BKT / LA)) * LA;
+            const int64_t gi = i0 + row;
+            const float* src = a.A + gi * a.sai + (k0 + kk);
+#pragma unroll
+            for (int q = 0; q < LA; q += 4) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (gi < M) {
+                    if (full) v = *reinterpret_cast<const float4*>(src + q);
+                    else {
+                        if (k0 + kk + q + 0 < ke) v.x = src[q + 0];
+                        if (k0 + kk + q + 1 < ke) v.y = src[q + 1];
+                        if (k0 + kk + q + 2 < ke) v.z = src[q + 2];
+                        if (k0 + kk + q + 3 < ke) v.w = src[q + 3];
+                    }
+                }
+                ra[q] = v.x; ra[q + 1] = v.y; ra[q + 2] = v.z; ra[q + 3] = v.w;
+            }
+        } else {
+            const int k = tid / 16, ii = (tid % 16) * LA;
+            const bool kin = k0 + k < ke;
+#pragma unroll
+            for (int q = 0; q < LA; q += 4) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                const int64_t gi = i0 + ii + q;
+                const float* src = a.A + gi + (k0 + k) * a.sak;
+                if (kin) {
+                    if (gi + 3 < M) v = *reinterpret_cast<const float4*>(src);
+                    else {
+                        if (gi + 0 < M) v.x = src[0];
+                        if (gi + 1 < M) v.y = src[1];
+                        if (gi + 2 < M) v.z = src[2];
+                    }
+                }
+                ra[q] = v.x; ra[q + 1] = v.y; ra[q + 2] = v.z; ra[q + 3] = v.w;
+            }
+        }
+        if (b_jrow) {
+            const int k = tid / 16, jj = (tid % 16) * 4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k0 + k < ke) v = *reinterpret_cast<const float4*>(a.B + (k0 + k) * a.sbk + (j0 + jj));
+            rb[0] = v.x; rb[1] = v.y; rb[2] = v.z; rb[3] = v.w;
+        } else {
+            const int j = tid / 4, kk = (tid % 4) * 4;
+            const float* src = a.B + (int64_t)(j0 + j) * a.sbj + (k0 + kk);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (full) v = *reinterpret_cast<const float4*>(src);
+            else {
+                if (k0 + kk + 0 < ke) v.x = src[0];
+                if (k0 + kk + 1 < ke) v.y = src[1];
+                if (k0 + kk + 2 < ke) v.z = src[2];
+                if (k0 + kk + 3 < ke) v.w = src[3];
+            }
+            rb[0] = v.x; rb[1] = v.y; rb[2] = v.z; rb[3] = v.w;
+        }
+    };
+    auto store_slice = [&](int buf) {
+        if (a_krow) {
+            const int row = tid / (BKT / LA), kk = (tid % (BKT / LA)) * LA;
+#pragma unroll
+            for (int q = 0; q < LA; q++) sA[buf][kk + q][row] = ra[q];
+        } else {
+            const int k = tid / 16, ii = (tid % 16) * LA;
+#pragma unroll
+            for (int q = 0; q < LA; q += 4)
+                *reinterpret_cast<float4*>(&sA[buf][k][ii + q]) = make_float4(ra[q], ra[q + 1], ra[q + 2], ra[q + 3]);
+        }
+        if (b_jrow) {
+            const int k = tid / 16, jj = (tid % 16) * 4;
+            *reinterpret_cast<float4*>(&sB[buf][k][jj]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+        } else {
+            const int j = tid / 4, kk = (tid % 4) * 4;
+#pragma unroll
+            for (int q = 0; q < 4; q++) sB[buf][kk + q][j] = rb[q];
+        }
+    };
+    float acc[TM][4];
+#pragma unroll
+    for (int r = 0; r < TM; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = 0.f;
+    load_slice(kb);
+    store_slice(0);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t k0 = kb; k0 < ke; k0 += BKT) {
+        const bool more = k0 + BKT < ke;
+        if (more) load_slice(k0 + BKT);
+#pragma unroll
+        for (int kk = 0; kk < BKT; kk++) {
+            float av[TM];
+#pragma unroll
+            for (int r = 0; r < TM; r += 4) {
+                float4 v = *reinterpret_cast<const float4*>(&sA[buf][kk][ty * TM + r]);
+                av[r] = v.x; av[r + 1] = v.y; av[r + 2] = v.z; av[r + 3] = v.w;
+            }
+            float4 bv = *reinterpret_cast<const float4*>(&sB[buf][kk][tx * 4]);
+#pragma unroll
+            for (int r = 0; r < TM; r++) {
+                acc[r][0] += av[r] * bv.x;
+                acc[r][1] += av[r] * bv.y;
+                acc[r][2] += av[r] * bv.z;
+                acc[r][3] += av[r] * bv.w;
+            }
+        }
+        if (more) {
+            store_slice(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < TM; r++) {
+        const int64_t gi = i0 + ty * TM + r;
+        if (gi >= M) continue;
+        const int gj = j0 + tx * 4;
+        float* dst = a.C + gi * a.ldc + gj;
+        if (EPI == kAtomic) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) atomicAdd(dst + c, acc[r][c]);
+            continue;
+        }
+        float4 v = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+        if (EPI == kRelu) {
+            v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f); v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f);
+        } else if (EPI == kMask) {
+            float4 m = *reinterpret_cast<const float4*>(a.mask + gi * a.ldc + gj);
+            v.x = m.x > 0.f ? v.x : 0.f; v.y = m.y > 0.f ? v.y : 0.f;
+            v.z = m.z > 0.f ? v.z : 0.f; v.w = m.w > 0.f ? v.w : 0.f;
+        }
+        *reinterpret_cast<float4*>(dst) = v;
+    }
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 template <int EPI>
 nif_status gemm(nif_handle* h, GemmArgs a, cudaStream_t s, int splits = 1) {
-    dim3 grid((a.N + BN - 1) / BN, (unsigned)((a.M + BM - 1) / BM), splits);
-    k_sgemm<EPI><<<grid, 256, 0, s>>>(a);
+    // the register-blocked kernel serves aligned shapes with N % 64 == 0 and K-slices of 16
+    bool big = a.N % 64 == 0 && (a.sak == 1 || a.sai == 1) && (a.sbj == 1 || a.sbk == 1) && aligned16(a.A) &&
+               aligned16(a.B) && aligned16(a.C) && a.ldc % 4 == 0 && (a.sak == 1 ? a.sai % 4 == 0 : a.sak % 4 == 0) &&
+               (a.sbj == 1 ? a.sbk % 4 == 0 : a.sbj % 4 == 0) && (EPI != kAtomic || a.k_chunk % 16 == 0) &&
+               (!a.mask || aligned16(a.mask)) && (a.m_is_k || a.K % 16 == 0);
+    if (big && a.M >= 96) {
+        dim3 grid(a.N / 64, (unsigned)((a.M + 127) / 128), splits);
+        k_sgemm_big<EPI, 128><<<grid, 256, 0, s>>>(a);
+    } else if (big) {
+        dim3 grid(a.N / 64, (unsigned)((a.M + 63) / 64), splits);
+        k_sgemm_big<EPI, 64><<<grid, 256, 0, s>>>(a);
+    } else {
+        dim3 grid((a.N + BN - 1) / BN, (unsigned)((a.M + BM - 1) / BM), splits);
+        k_sgemm<EPI><<<grid, 256, 0, s>>>(a);
+    }
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
