@@ -6,6 +6,8 @@
 // tiles, 16-deep K slices staged in shared memory, 4x4 outputs per thread,
 // and an epilogue chosen per call: store, ReLU, ReLU-derivative mask, or
 // split-K atomic accumulation (for weight gradients summed over rows).
+#include <algorithm>
+
 #include "nif_internal.cuh"
 
 namespace {
@@ -269,9 +271,21 @@ nif_status gemm(nif_handle* h, GemmArgs a, cudaStream_t s, int splits = 1) {
     // the register-blocked kernel serves aligned shapes with N % 64 == 0 and K-slices of 16
     bool big = a.N % 64 == 0 && (a.sak == 1 || a.sai == 1) && (a.sbj == 1 || a.sbk == 1) && aligned16(a.A) &&
                aligned16(a.B) && aligned16(a.C) && a.ldc % 4 == 0 && (a.sak == 1 ? a.sai % 4 == 0 : a.sak % 4 == 0) &&
-               (a.sbj == 1 ? a.sbk % 4 == 0 : a.sbj % 4 == 0) && (EPI != kAtomic || a.k_chunk % 16 == 0) &&
-               (!a.mask || aligned16(a.mask)) && (a.m_is_k || a.K % 16 == 0);
-    if (big && a.M >= 96) {
+               (a.sbj == 1 ? a.sbk % 4 == 0 : a.sbj % 4 == 0) && (!a.mask || aligned16(a.mask)) &&
+               (a.m_is_k || a.K % 16 == 0);
+    // 128-row tiles for long reductions over many rows, 64-row tiles otherwise (more resident blocks)
+    const bool tall = big && a.M >= 96 && !a.m_is_k && a.K > 64;
+    const int bm = big ? (tall ? 128 : 64) : BM;
+    if (EPI == kAtomic) {
+        // split the row reduction so that the grid covers the GPU about four times
+        int64_t tiles = (int64_t)((a.N + 63) / 64) * ((a.M + bm - 1) / bm);
+        int64_t want = std::max<int64_t>(1, (4 * (int64_t)h->num_sms + tiles - 1) / tiles);
+        int64_t chunk = (a.K + want - 1) / want;
+        chunk = std::max<int64_t>(256, (chunk + 15) / 16 * 16);
+        a.k_chunk = chunk;
+        splits = (int)((a.K + chunk - 1) / chunk);
+    }
+    if (big && tall) {
         dim3 grid(a.N / 64, (unsigned)((a.M + 127) / 128), splits);
         k_sgemm_big<EPI, 128><<<grid, 256, 0, s>>>(a);
     } else if (big) {
@@ -326,8 +340,6 @@ nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n
     const float* g = dout;
     int64_t g_ld = NIF_OUT;
     int cur = 0;
-    const int64_t chunk = 4096;
-    int splits = (int)((n_max + chunk - 1) / chunk);
     for (int l = h->n_layers - 1; l >= 0; l--) {
         const float* in = l == 0 ? x : acts + (int64_t)(l - 1) * n_max * h->W;
         int64_t in_ld = l == 0 ? h->in_dim : h->W;
@@ -337,8 +349,8 @@ nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n
         w.A = g; w.sai = 1; w.sak = g_ld;
         w.B = in; w.sbk = in_ld; w.sbj = 1;
         w.C = h->d_grad + h->off_layer[l]; w.ldc = nin;
-        w.M = nout; w.N = nin; w.K = n_max; w.M_dev = n_dev; w.m_is_k = 1; w.k_chunk = chunk;
-        st = gemm<kAtomic>(h, w, s, splits);
+        w.M = nout; w.N = nin; w.K = n_max; w.M_dev = n_dev; w.m_is_k = 1; w.k_chunk = 0;
+        st = gemm<kAtomic>(h, w, s);
         if (st != NIF_OK) return st;
         // d(in) = g W_l : [n x nin], masked by the ReLU of the layer below
         if (l == 0 && !dx) break;
