@@ -295,6 +295,7 @@ def run_ours(args):
     # ---- inference queries ------------------------------------------------
     query = run_query(args, nif, S, dev, rank) if not args.no_query else None
     batch = run_batch(args, nif, S, dev, rank) if not args.no_batch else None
+    precision = run_precision(args, nif, S, dev) if (not args.no_precision and rank == 0) else None
 
     if rank != 0:
         return 0
@@ -318,7 +319,8 @@ def run_ours(args):
                        "mlp": "-".join(str(x) for x in [net.in_dim] + [net.mlp_width] * net.mlp_depth + [16]),
                        "l2": "working set larger than L2 (tables, gradients, Adam state 256 MB; features 604 MB)"},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "loss": list(loss) if loss is not None else None, "query": query, "batch": batch}
+            "clocks": clocks, "loss": list(loss) if loss is not None else None, "query": query, "batch": batch,
+            "precision": precision}
     print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -427,6 +429,62 @@ def run_batch(args, nif, S, dev, rank):
     return res
 
 
+def run_precision(args, nif, S, dev):
+    """Per-output error of the BF16 / FP16 query paths against the FP32 GPU
+    path on a trained network: the 16^3 torus workload (L = 8, T = 2^14,
+    MLP 288-32-32-16) trained on the GPU (FP32, 4000 steps of 2^16 segments,
+    poses U[-1,1]^3), then queried with 2^22 rays. (The 128^3 voxel grid is
+    finer than this encoding's finest level, 68 cells, so a network trained
+    there predicts few hits; the comparison with the FP64 oracle is
+    tests/test_gpu_precision.py.)"""
+    import torch
+    w = S.WORKLOADS["torus16_fwd"]
+    net = w["net"]
+    mesh = S.make_mesh(w["shape"])
+    t0 = time.perf_counter()
+    h32 = nif.Nif(net, mesh, precision=nif.NIF_FP32, seed=51)
+    for step in range(4000):
+        loss, _ = nif.nif_train_step(h32.h, 1 << 16, 16, 5000 + step, lr_grid=1e-2, lr_mlp=5e-3,
+                                     want_loss=(step == 3999))
+    train_s = time.perf_counter() - t0
+    tables, ws, s = h32.get_params()
+    hs = {"fp32": h32}
+    for name, p in (("bf16", nif.NIF_BF16), ("fp16", nif.NIF_FP16)):
+        hs[name] = nif.Nif(net, mesh, precision=p, seed=51)
+        hs[name].set_params(tables, ws, s)
+    pose = S.poses(1, seed=52)[0]          # U[-1,1]^3, the training distribution
+
+    def fields(hits):
+        a = hits.cpu().numpy().view(nif.HIT_DTYPE).reshape(-1)
+        return (a["hit"] > 0, a["D"].astype(np.float64), a["n"].astype(np.float64), a["albedo"].astype(np.float64),
+                a["material"])
+
+    def errs(ref, got):
+        h0, d0, n0, a0, m0 = ref
+        h1, d1, n1, a1, m1 = got
+        both = h0 & h1
+        ang = np.degrees(np.arccos(np.clip((n0[both] * n1[both]).sum(1), -1, 1)))
+        dd = np.abs(d0[both] - d1[both])
+        da = np.abs(a0[both] - a1[both]).max(1)
+        return {"hit_iou": float(both.sum() / max(1, (h0 | h1).sum())),
+                "D_abs_median": float(np.median(dd)) if both.any() else None,
+                "D_abs_p99": float(np.percentile(dd, 99)) if both.any() else None,
+                "normal_deg_median": float(np.median(ang)) if both.any() else None,
+                "normal_deg_p99": float(np.percentile(ang, 99)) if both.any() else None,
+                "albedo_abs_p99": float(np.percentile(da, 99)) if both.any() else None,
+                "material_acc": float((m0[both] == m1[both]).mean()) if both.any() else None}
+
+    rays_np = S.sphere_rays(1 << 22, seed=53)
+    rays = torch.from_numpy(rays_np).to(dev)
+    got = {k: fields(nif.nif_query(hh.h, [pose], rays)) for k, hh in hs.items()}
+    vs_fp32 = {k: errs(got["fp32"], got[k]) for k in ("bf16", "fp16")}
+    for hh in hs.values():
+        hh.close()
+    return {"workload": "torus16_fwd (trained)", "train_steps": 4000, "train_s": train_s,
+            "train_loss": [float(x) for x in loss], "rays": 1 << 22,
+            "vs_fp32_gpu_all_rays": vs_fp32}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -439,6 +497,7 @@ def main():
     ap.add_argument("--query-rays", type=int, default=0, help="rays per query batch (default: the workload's 2^22)")
     ap.add_argument("--query-prec", default="fp32,bf16,fp16", help="comma list of query precisions")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance query measurement")
+    ap.add_argument("--no-precision", action="store_true", help="skip the per-output precision study")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
