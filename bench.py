@@ -39,6 +39,10 @@ QUERY_WORKLOAD = "torus128_query"
 N_SEG = 1 << 18
 N_POSES = 16
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max SM clock
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernel on this workload (profiles/encode_bwd_ellipsoids64.md); a stage
+# missing here reports traffic null.
+NCU_TRAFFIC = {"encode_bwd": 655.6e6}
 
 
 def _peaks():
@@ -249,7 +253,8 @@ def run_ours(args):
         if unit == "bytes":
             ach = amount / (avg_ms / 1e3) / 1e9
             roof = {"bound": bound, "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "peak_source": f"{peak_src} hbm_gbs", "traffic": None}
+                    "peak_source": f"{peak_src} hbm_gbs", "traffic": NCU_TRAFFIC.get(dom),
+                    "algorithmic_bytes": amount}
         else:
             ach = amount / (avg_ms / 1e3) / 1e12
             roof = {"bound": bound, "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
