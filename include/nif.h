@@ -155,6 +155,17 @@ nif_status nif_set_params(nif_handle* h, int group, const void* src_host, size_t
 /* Reset the Adam moments and step counter of the handle. */
 nif_status nif_reset_optimizer(nif_handle* h);
 
+/* Checkpoint of the trainable state: a 64-byte header (magic "NIFCKPT1",
+ * format version, the sizes of the configuration that must match, the Adam
+ * step count), then the FP32 parameters, Adam first and second moments, and a
+ * CRC-32 (IEEE) of everything before it. nif_checkpoint_bytes gives the size;
+ * save writes into host memory, load checks the header, sizes and CRC
+ * (NIF_ERR_ARG on any mismatch, leaving the handle unchanged) and restores
+ * parameters, moments and step. Both block the host. */
+nif_status nif_checkpoint_bytes(const nif_handle* h, size_t* bytes);
+nif_status nif_checkpoint_save(nif_handle* h, void* dst_host, size_t bytes);
+nif_status nif_checkpoint_load(nif_handle* h, const void* src_host, size_t bytes);
+
 /* Rest-space voxelization (Sec. 2): occ_host [N^3] (x fastest) gets 1 for
  * occupied voxels. If tri_ptr_host is not NULL it receives [N^3 + 1] offsets
  * and tri_idx_host (capacity `cap`) the ascending triangle ids overlapping

@@ -504,6 +504,101 @@ extern "C" nif_status nif_adam_step(nif_handle* h, float lr_grid, float lr_mlp, 
     return nif_adam_run(h, lr_grid, lr_mlp, (cudaStream_t)stream);
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoints
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, n_params_lo, n_params_hi, L, T, W, H, in_dim, N, P;
+    int64_t adam_step;
+    uint32_t pad[2];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+
+uint32_t crc32_ieee(const uint8_t* p, size_t n) {
+    static uint32_t table[256];
+    static bool init = false;
+    if (!init) {
+        for (uint32_t i = 0; i < 256; i++) {
+            uint32_t c = i;
+            for (int k = 0; k < 8; k++) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+            table[i] = c;
+        }
+        init = true;
+    }
+    uint32_t c = 0xFFFFFFFFu;
+    for (size_t i = 0; i < n; i++) c = table[(c ^ p[i]) & 0xFFu] ^ (c >> 8);
+    return c ^ 0xFFFFFFFFu;
+}
+
+CkptHeader ckpt_header(const nif_handle* h) {
+    CkptHeader hd{};
+    std::memcpy(hd.magic, "NIFCKPT1", 8);
+    hd.version = 1;
+    hd.n_params_lo = (uint32_t)(h->n_params & 0xFFFFFFFFu);
+    hd.n_params_hi = (uint32_t)(h->n_params >> 32);
+    hd.L = (uint32_t)h->L;
+    hd.T = h->T;
+    hd.W = (uint32_t)h->W;
+    hd.H = (uint32_t)h->H;
+    hd.in_dim = (uint32_t)h->in_dim;
+    hd.N = (uint32_t)h->N;
+    hd.P = (uint32_t)h->P;
+    hd.adam_step = h->adam_step;
+    return hd;
+}
+
+}  // namespace
+
+extern "C" nif_status nif_checkpoint_bytes(const nif_handle* h, size_t* bytes) {
+    if (!h || !bytes) return NIF_ERR_ARG;
+    *bytes = sizeof(CkptHeader) + 3 * sizeof(float) * h->n_params + sizeof(uint32_t);
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_checkpoint_save(nif_handle* h, void* dst, size_t bytes) {
+    size_t need = 0;
+    if (nif_checkpoint_bytes(h, &need) != NIF_OK || !dst || bytes != need)
+        return h ? nif_fail(h, NIF_ERR_ARG, "checkpoint buffer size") : NIF_ERR_ARG;
+    uint8_t* o = static_cast<uint8_t*>(dst);
+    CkptHeader hd = ckpt_header(h);
+    std::memcpy(o, &hd, sizeof hd);
+    size_t nb = sizeof(float) * h->n_params;
+    NIF_CK(h, cudaDeviceSynchronize());
+    NIF_CK(h, cudaMemcpy(o + sizeof hd, h->d_params, nb, cudaMemcpyDeviceToHost));
+    NIF_CK(h, cudaMemcpy(o + sizeof hd + nb, h->d_m, nb, cudaMemcpyDeviceToHost));
+    NIF_CK(h, cudaMemcpy(o + sizeof hd + 2 * nb, h->d_v, nb, cudaMemcpyDeviceToHost));
+    uint32_t crc = crc32_ieee(o, sizeof hd + 3 * nb);
+    std::memcpy(o + sizeof hd + 3 * nb, &crc, sizeof crc);
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_checkpoint_load(nif_handle* h, const void* src, size_t bytes) {
+    size_t need = 0;
+    if (nif_checkpoint_bytes(h, &need) != NIF_OK || !src) return NIF_ERR_ARG;
+    if (bytes != need) return nif_fail(h, NIF_ERR_ARG, "checkpoint size does not match this configuration");
+    const uint8_t* in = static_cast<const uint8_t*>(src);
+    CkptHeader hd;
+    std::memcpy(&hd, in, sizeof hd);
+    CkptHeader mine = ckpt_header(h);
+    mine.adam_step = hd.adam_step;
+    if (std::memcmp(&hd, &mine, sizeof hd) != 0) return nif_fail(h, NIF_ERR_ARG, "checkpoint header mismatch");
+    size_t nb = sizeof(float) * h->n_params;
+    uint32_t crc = 0;
+    std::memcpy(&crc, in + sizeof hd + 3 * nb, sizeof crc);
+    if (crc != crc32_ieee(in, sizeof hd + 3 * nb)) return nif_fail(h, NIF_ERR_ARG, "checkpoint CRC mismatch");
+    NIF_CK(h, cudaDeviceSynchronize());
+    NIF_CK(h, cudaMemcpy(h->d_params, in + sizeof hd, nb, cudaMemcpyHostToDevice));
+    NIF_CK(h, cudaMemcpy(h->d_m, in + sizeof hd + nb, nb, cudaMemcpyHostToDevice));
+    NIF_CK(h, cudaMemcpy(h->d_v, in + sizeof hd + 2 * nb, nb, cudaMemcpyHostToDevice));
+    NIF_CK(h, cudaMemset(h->d_grad, 0, nb));
+    h->adam_step = hd.adam_step;
+    h->lowp_dirty = true;
+    return NIF_OK;
+}
+
 extern "C" nif_status nif_get_voxels(nif_handle* h, unsigned char* occ, int64_t* tri_ptr, int32_t* tri_idx,
                                      int64_t cap, int64_t* n_pairs) {
     if (!h || !occ) return NIF_ERR_ARG;
@@ -898,14 +993,15 @@ extern "C" nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_po
     }
     if (poses_out) std::memcpy(poses_out, poses.data(), sizeof(nif_pose) * n_poses);
     nif_status st;
-    // rays per pose: from the measured segments per ray (probed once)
+    // rays per pose: from the segments per ray of a fixed probe (identity pose,
+    // a fixed sample stream), so the batch layout depends only on the shape
     if (h->seg_per_ray <= 0.0) {
         const int probe = 8192;
         if ((st = nif_grow(h, h->b_rays, sizeof(nif_ray) * probe)) != NIF_OK) return st;
-        if ((st = nif_sample_rays_run(h, step_seed ^ 0x5bd1e995ull, 0, probe, (nif_ray*)h->b_rays.p, s)) != NIF_OK)
-            return st;
+        if ((st = nif_sample_rays_run(h, 0x5bd1e995ull, 0, probe, (nif_ray*)h->b_rays.p, s)) != NIF_OK) return st;
         int64_t tot = 0;
-        if ((st = segment_into_scratch(h, poses.data(), 1, (nif_ray*)h->b_rays.p, nullptr, probe, -1, true, &tot, s)) !=
+        const nif_pose identity{0.f, 0.f, 0.f};
+        if ((st = segment_into_scratch(h, &identity, 1, (nif_ray*)h->b_rays.p, nullptr, probe, -1, true, &tot, s)) !=
             NIF_OK)
             return st;
         h->seg_per_ray = std::max(0.05, (double)tot / probe);

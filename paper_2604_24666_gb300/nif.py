@@ -114,6 +114,9 @@ def lib() -> ctypes.CDLL:
                                     ctypes.c_int),
             "nif_query_plan_destroy": ([_vp], None),
             "nif_sync_status": ([_vp, _vp], ctypes.c_int),
+            "nif_checkpoint_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+            "nif_checkpoint_save": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
+            "nif_checkpoint_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
             "nif_kernel_launches": ([], ctypes.c_ulonglong),
             "nif_profile": ([_vp, ctypes.c_int], ctypes.c_int),
             "nif_profile_read": ([_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -415,6 +418,19 @@ class QueryPlan:
 
 def nif_sync_status(h, stream=None):
     _check(h, lib().nif_sync_status(h, _stream(stream)))
+
+
+def nif_checkpoint_save(h) -> bytes:
+    n = ctypes.c_size_t()
+    _check(h, lib().nif_checkpoint_bytes(h, ctypes.byref(n)))
+    buf = (ctypes.c_uint8 * n.value)()
+    _check(h, lib().nif_checkpoint_save(h, ctypes.cast(buf, ctypes.c_void_p), n.value))
+    return bytes(buf)
+
+
+def nif_checkpoint_load(h, blob: bytes):
+    buf = (ctypes.c_uint8 * len(blob)).from_buffer_copy(blob)
+    _check(h, lib().nif_checkpoint_load(h, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
 
 
 def nif_kernel_launches() -> int:

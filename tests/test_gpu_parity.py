@@ -662,3 +662,42 @@ def test_query_plan_graph_replays_match_query(nif, torus, prec):
     assert int((hits[:, 7].view(torch.int32) & 0xff).ne(0).sum()) > 100
     plan.close()
     h.close()
+
+
+# ---------------------------------------------------------------------------
+# Checkpoint / resume
+# ---------------------------------------------------------------------------
+def test_checkpoint_roundtrip_and_resume(nif, torus):
+    import zlib
+    net = S.NetConfig(levels=8, log2_table=12)
+    a = nif.Nif(net, torus, seed=3)
+    for step in range(5):
+        nif.nif_train_step(a.h, 1 << 13, 4, 100 + step, want_loss=False)
+    blob = nif.nif_checkpoint_save(a.h)
+    # format: header magic, CRC-32 (IEEE, as zlib computes it) of everything before the trailer
+    assert blob[:8] == b"NIFCKPT1"
+    assert int.from_bytes(blob[-4:], "little") == zlib.crc32(blob[:-4])
+    b = nif.Nif(net, torus, seed=99)
+    nif.nif_checkpoint_load(b.h, blob)
+    assert nif.nif_checkpoint_save(b.h) == blob               # state restored exactly
+    la, _ = nif.nif_train_step(a.h, 1 << 13, 4, 777)
+    lb, _ = nif.nif_train_step(b.h, 1 << 13, 4, 777)
+    np.testing.assert_allclose(la, lb, rtol=1e-6)              # same batch, same state, same loss
+    ta, wa, sa = a.get_params()
+    tb, wb, sb = b.get_params()
+    # gradients are summed with float atomics (order varies), so the updated state
+    # agrees up to rounding; an entry whose tiny gradient flips sign on its first
+    # Adam step moves by 2 lr, which only a handful of entries may do
+    assert np.mean(np.abs(tb - ta) > 1e-6) < 1e-3
+    for x, y in zip(wa, wb):
+        np.testing.assert_allclose(y, x, atol=1e-5)
+    bad = bytearray(blob)
+    bad[100] ^= 1
+    with pytest.raises(nif.NifError) as e:
+        nif.nif_checkpoint_load(b.h, bytes(bad))
+    assert e.value.status == nif.NIF_ERR_ARG
+    other = nif.Nif(S.NetConfig(levels=4, log2_table=12), torus)
+    with pytest.raises(nif.NifError):
+        nif.nif_checkpoint_load(other.h, blob)
+    for x in (a, b, other):
+        x.close()
