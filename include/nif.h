@@ -71,9 +71,20 @@ typedef struct {
     int mlp_width;          /* W: hidden width; 16, 32, 64 or 128 */
     int n_materials;        /* M material classes; 1..8 */
     int precision;          /* nif_precision of nif_query's encoding + MLP */
-    unsigned flags;         /* reserved, 0 */
+    unsigned flags;         /* NIF_FLAG_* below; 0 = the paper's method */
     unsigned long long seed;/* parameter initialisation and training-sample seed */
 } nif_config;
+
+/* Ablation switches (the paper's "Deformed" baseline of Table 1 / Sec. 3.2
+ * drops its training and encoding modifications):
+ * NIF_FLAG_FIXED_TASK_WEIGHTS  task log-variances s held at 0 (no uncertainty
+ *                              weighting, Sec. 2.4): 0.5 L_reg + L_cls;
+ * NIF_FLAG_SIGMOID_DISTANCE    distance head sqrt(3) * sigmoid(z) in voxel
+ *                              units with a plain squared error, instead of
+ *                              the ReLU head and log-space error of Sec. 2.4.
+ * (No positional encoding is pe_bands = 0.) */
+#define NIF_FLAG_FIXED_TASK_WEIGHTS 1u
+#define NIF_FLAG_SIGMOID_DISTANCE 2u
 
 /* Rest-space triangle mesh inside [0,1]^3 (host memory, copied by nif_create). */
 typedef struct {

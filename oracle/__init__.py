@@ -373,7 +373,12 @@ def _softplus(z):
     return np.maximum(z, 0.0) + np.log1p(np.exp(-np.abs(z)))
 
 
-def loss(cfg, out, lab, s, l_rest):
+FLAG_FIXED_TASK_WEIGHTS = 1
+FLAG_SIGMOID_DISTANCE = 2
+SQRT3 = float(np.sqrt(3.0))
+
+
+def loss(cfg, out, lab, s, l_rest, flags=0):
     """Uncertainty-weighted multi-task loss and its gradients.
 
     out   [S, O] network outputs: 0 occupancy logit, 1 distance (ReLU),
@@ -382,6 +387,9 @@ def loss(cfg, out, lab, s, l_rest):
     s     [5] log-variances (distance, normal, albedo, material, occlusion).
     l_rest [S] rest-segment lengths; the distance target is the rest hit
           distance in voxel units, tpar * l_rest * N.
+    flags (ablation, the "Deformed" baseline): FLAG_FIXED_TASK_WEIGHTS holds
+    s at 0 (total = sum 0.5 L_reg + L_cls, ds = 0); FLAG_SIGMOID_DISTANCE uses
+    the head sqrt(3) sigmoid(z) with a plain squared error.
     Returns (total, parts [5], dout [S, O], ds [5]).
     """
     out = np.asarray(out, np.float64)
@@ -392,15 +400,24 @@ def loss(cfg, out, lab, s, l_rest):
     nh = int(hit.sum())
     dout = np.zeros_like(out)
     parts = np.zeros(5)
+    fixed = bool(flags & FLAG_FIXED_TASK_WEIGHTS)
+    if fixed:
+        s = np.zeros(5)
     es = np.exp(-s)
     if nh > 0:
         zh = out[hit]
-        # distance: ReLU head, MSE of logs
-        dh = np.maximum(zh[:, 1], 0.0)
         y = lab["tpar"][hit] * np.asarray(l_rest)[hit] * cfg.voxel_res
-        e = np.log(dh + EPS_DIST) - np.log(y + EPS_DIST)
-        parts[0] = (e * e).sum() / nh
-        gd = 0.5 * es[0] * 2.0 * e / (dh + EPS_DIST) / nh * (zh[:, 1] > 0)
+        if flags & FLAG_SIGMOID_DISTANCE:
+            sg = _sigmoid(zh[:, 1])
+            e = SQRT3 * sg - y
+            parts[0] = (e * e).sum() / nh
+            gd = 0.5 * es[0] * 2.0 * e * SQRT3 * sg * (1 - sg) / nh
+        else:
+            # distance: ReLU head, MSE of logs
+            dh = np.maximum(zh[:, 1], 0.0)
+            e = np.log(dh + EPS_DIST) - np.log(y + EPS_DIST)
+            parts[0] = (e * e).sum() / nh
+            gd = 0.5 * es[0] * 2.0 * e / (dh + EPS_DIST) / nh * (zh[:, 1] > 0)
         # normal: 1 - cosine
         nhat = zh[:, 2:5]
         n = lab["normal"][hit]
@@ -434,6 +451,8 @@ def loss(cfg, out, lab, s, l_rest):
     parts[4] = (_softplus(z0) - occ * z0).sum() / S
     dout[:, 0] = (_sigmoid(z0) - occ) * (es[4] / S)
     wreg = np.array([0.5, 0.5, 0.5, 1.0, 1.0])
+    if fixed:
+        return float((wreg * parts).sum()), parts, dout, np.zeros(5)
     total = float((wreg * es * parts + 0.5 * s).sum())
     ds = -wreg * es * parts + 0.5
     return total, parts, dout, ds
@@ -456,7 +475,7 @@ def adam(theta, m, v, g, step, lr, b1=0.9, b2=0.99, eps=1e-15):
 # Reconstruction along the segmented ray (Sec. 2.2)
 # ---------------------------------------------------------------------------
 
-def reconstruct(cfg, pose, rays, seg: Segments, out, p0, p1, l_def, l_rest):
+def reconstruct(cfg, pose, rays, seg: Segments, out, p0, p1, l_def, l_rest, flags=0):
     """Per ray: first segment k (in list order) with sigmoid(occ) > 0.5;
     D = sum_{j<k} (delta_j + l_j) + delta_k + t_k with t_k the predicted rest
     distance mapped to deformed length, t_k = (dist/N) * l_def/l_rest, clamped
@@ -476,7 +495,8 @@ def reconstruct(cfg, pose, rays, seg: Segments, out, p0, p1, l_def, l_rest):
             x1 = rays[r, 0:3] + seg.t1[j] * rays[r, 3:6]
             delta = np.linalg.norm(x0 - prev)
             if out[j, 0] > 0.0:
-                trest = max(out[j, 1], 0.0) / cfg.voxel_res
+                dvox = SQRT3 * _sigmoid(out[j, 1]) if flags & FLAG_SIGMOID_DISTANCE else max(out[j, 1], 0.0)
+                trest = dvox / cfg.voxel_res
                 tk = trest * l_def[j] / l_rest[j] if l_rest[j] > 0 else 0.0
                 tk = min(max(tk, 0.0), l_def[j])
                 res["hit"][r] = 1

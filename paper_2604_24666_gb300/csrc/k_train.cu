@@ -90,7 +90,7 @@ __device__ __forceinline__ float softplusf_(float z) { return fmaxf(z, 0.f) + lo
 __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ out, const nif_label* __restrict__ labels,
                                               const nif_linseg* __restrict__ lin, const uint32_t* __restrict__ n_dev,
                                               int64_t n_max, const int* __restrict__ n_hit,
-                                              const float* __restrict__ s_par, int N, int M,
+                                              const float* __restrict__ s_par, int N, int M, unsigned flags,
                                               float* __restrict__ dout, double* __restrict__ acc) {
     int64_t n = n_dev ? (int64_t)*n_dev : n_max;
     if (n > n_max) n = n_max;
@@ -98,8 +98,10 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ out, con
     float inv_h = nh > 0 ? 1.0f / (float)nh : 0.f;
     float inv_n = n > 0 ? 1.0f / (float)n : 0.f;
     float es[5];
+    const bool fixed_w = flags & NIF_FLAG_FIXED_TASK_WEIGHTS;
+    const bool sig_d = flags & NIF_FLAG_SIGMOID_DISTANCE;
 #pragma unroll
-    for (int i = 0; i < 5; i++) es[i] = expf(-s_par[i]);
+    for (int i = 0; i < 5; i++) es[i] = fixed_w ? 1.0f : expf(-s_par[i]);
     float part[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         const float* z = out + s * NIF_OUT;
@@ -113,12 +115,20 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ out, con
         part[4] += softplusf_(z[0]) - occ * z[0];
         g[0] = (sigmoidf_(z[0]) - occ) * es[4] * inv_n;
         if (lab.occ) {
-            // distance: ReLU head, MSE of logs, target in voxel units
-            float dh = fmaxf(z[1], 0.f);
             float y = lab.tpar * lin[s].l_rest * (float)N;
-            float e = logf(dh + NIF_EPS_DIST) - logf(y + NIF_EPS_DIST);
-            part[0] += e * e;
-            g[1] = z[1] > 0.f ? 0.5f * es[0] * 2.0f * e / (dh + NIF_EPS_DIST) * inv_h : 0.f;
+            if (sig_d) {
+                // ablation: bounded sigmoid head, squared error of the distance itself
+                float sg = sigmoidf_(z[1]);
+                float e = 1.7320508075688772f * sg - y;
+                part[0] += e * e;
+                g[1] = 0.5f * es[0] * 2.0f * e * 1.7320508075688772f * sg * (1.f - sg) * inv_h;
+            } else {
+                // distance: ReLU head, MSE of logs, target in voxel units
+                float dh = fmaxf(z[1], 0.f);
+                float e = logf(dh + NIF_EPS_DIST) - logf(y + NIF_EPS_DIST);
+                part[0] += e * e;
+                g[1] = z[1] > 0.f ? 0.5f * es[0] * 2.0f * e / (dh + NIF_EPS_DIST) * inv_h : 0.f;
+            }
             // normal: 1 - cos
             float nx = z[2], ny = z[3], nz = z[4];
             float nn = fmaxf(sqrtf(nx * nx + ny * ny + nz * nz), 1e-8f);
@@ -172,7 +182,7 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ out, con
 
 // parts -> total and dL/ds (added into the gradient buffer)
 __global__ void k_loss_final(double* acc, const uint32_t* __restrict__ n_dev, int64_t n_max,
-                             const int* __restrict__ n_hit, const float* __restrict__ s_par,
+                             const int* __restrict__ n_hit, const float* __restrict__ s_par, unsigned flags,
                              float* __restrict__ ds, int* status) {
     if (threadIdx.x != 0) return;
     int64_t n = n_dev ? (int64_t)*n_dev : n_max;
@@ -183,7 +193,12 @@ __global__ void k_loss_final(double* acc, const uint32_t* __restrict__ n_dev, in
     L[4] = n > 0 ? acc[4] / n : 0.0;
     const double wreg[5] = {0.5, 0.5, 0.5, 1.0, 1.0};
     double total = 0;
+    const bool fixed_w = flags & NIF_FLAG_FIXED_TASK_WEIGHTS;
     for (int i = 0; i < 5; i++) {
+        if (fixed_w) {
+            total += wreg[i] * L[i];
+            continue;
+        }
         double es = exp(-(double)s_par[i]);
         total += wreg[i] * es * L[i] + 0.5 * s_par[i];
         if (ds) ds[i] += (float)(-wreg[i] * es * L[i] + 0.5);
@@ -231,7 +246,7 @@ __global__ void __launch_bounds__(128) k_reconstruct(const nif_ray* __restrict__
                                                      const nif_segment* __restrict__ segs,
                                                      const nif_linseg* __restrict__ lin,
                                                      const float* __restrict__ out, int64_t seg_cap, int N, int M,
-                                                     nif_hit* __restrict__ hits, unsigned flags) {
+                                                     unsigned cfg_flags, nif_hit* __restrict__ hits, unsigned flags) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
     int64_t a = offsets[r], b = offsets[r + 1];
@@ -252,7 +267,8 @@ __global__ void __launch_bounds__(128) k_reconstruct(const nif_ray* __restrict__
         float4 r0 = R[0], r1 = R[1];
         float dn = sqrtf(r0.w * r0.w + r1.x * r1.x + r1.y * r1.y);
         nif_linseg L = lin[s];
-        float trest = fmaxf(z[1], 0.f) / (float)N;
+        float dvox = (cfg_flags & NIF_FLAG_SIGMOID_DISTANCE) ? 1.7320508075688772f * sigmoidf_(z[1]) : fmaxf(z[1], 0.f);
+        float trest = dvox / (float)N;
         float tk = L.l_rest > 0.f ? trest * L.l_def / L.l_rest : 0.f;
         tk = fminf(fmaxf(tk, 0.f), L.l_def);
         // collinear entry/exit points: sum_{j<k} (delta_j + l_j) + delta_k = t0(k) |d|
@@ -362,10 +378,10 @@ nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels
         unsigned cap = (unsigned)h->num_sms * 8;
         if (g > cap) g = cap;
         k_loss<<<g, 256, 0, s>>>(out, labels, lin, n_dev, n_max, h->d_count, h->d_params + h->off_s, h->N,
-                                 h->cfg.n_materials, dout, h->d_lossacc);
+                                 h->cfg.n_materials, h->cfg.flags, dout, h->d_lossacc);
         NIF_CK_LAUNCH(h);
     }
-    k_loss_final<<<1, 32, 0, s>>>(h->d_lossacc, n_dev, n_max, h->d_count, h->d_params + h->off_s,
+    k_loss_final<<<1, 32, 0, s>>>(h->d_lossacc, n_dev, n_max, h->d_count, h->d_params + h->off_s, h->cfg.flags,
                                   h->d_grad + h->off_s, h->d_status);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
@@ -393,7 +409,8 @@ nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* in
     NifProf prof_(h, "reconstruct", s);
     if (n_rays <= 0) return NIF_OK;
     k_reconstruct<<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, h->d_pose, offsets, segs,
-                                                          lin, out, seg_cap, h->N, h->cfg.n_materials, hits, flags);
+                                                          lin, out, seg_cap, h->N, h->cfg.n_materials, h->cfg.flags,
+                                                          hits, flags);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

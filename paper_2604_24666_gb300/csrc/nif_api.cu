@@ -209,6 +209,8 @@ static nif_status validate(const nif_config* c, const nif_mesh* m) {
         return nif_fail(nullptr, NIF_ERR_ARG, "mlp_width in {16, 32, 64, 128}");
     if (c->n_materials < 1 || c->n_materials > 8) return nif_fail(nullptr, NIF_ERR_ARG, "n_materials in [1, 8]");
     if (c->precision < NIF_FP32 || c->precision > NIF_FP16) return nif_fail(nullptr, NIF_ERR_ARG, "precision");
+    if (c->flags & ~(NIF_FLAG_FIXED_TASK_WEIGHTS | NIF_FLAG_SIGMOID_DISTANCE))
+        return nif_fail(nullptr, NIF_ERR_ARG, "unknown flags");
     if (m->n_tris < 0 || m->n_verts < 0 || (m->n_tris > 0 && (!m->tris || !m->verts)))
         return nif_fail(nullptr, NIF_ERR_ARG, "mesh arrays");
     for (int t = 0; t < m->n_tris * 3; t++)

@@ -22,6 +22,7 @@ NIF_OK, NIF_ERR_ARG, NIF_ERR_CUDA, NIF_ERR_OOM, NIF_ERR_CAPACITY, NIF_ERR_TIMEOU
 NIF_FP32, NIF_BF16, NIF_FP16 = 0, 1, 2
 NIF_PARAM_TABLES, NIF_PARAM_LOGVAR, NIF_PARAM_LAYER0 = 0, 1, 16
 NIF_SHADOW_ONLY = 1
+NIF_FLAG_FIXED_TASK_WEIGHTS, NIF_FLAG_SIGMOID_DISTANCE = 1, 2
 
 _STATUS = {0: "NIF_OK", -1: "NIF_ERR_ARG", -2: "NIF_ERR_CUDA", -3: "NIF_ERR_OOM", -4: "NIF_ERR_CAPACITY",
            -5: "NIF_ERR_TIMEOUT", -6: "NIF_ERR_NAN", -7: "NIF_ERR_STATE"}
@@ -170,13 +171,14 @@ def _check(h, st):
 # C-ABI functions (same names)
 # ---------------------------------------------------------------------------
 
-def make_config(net, precision=NIF_FP32, seed=0) -> nif_config:
+def make_config(net, precision=NIF_FP32, seed=0, flags=0) -> nif_config:
     return nif_config(net.voxel_res, net.pe_bands, net.levels, net.feats, net.log2_table, net.base_res,
-                      float(net.growth), net.mlp_depth, net.mlp_width, net.n_materials, int(precision), 0, int(seed))
+                      float(net.growth), net.mlp_depth, net.mlp_width, net.n_materials, int(precision), int(flags),
+                      int(seed))
 
 
-def nif_create(net, mesh, precision=NIF_FP32, seed=0):
-    cfg = make_config(net, precision, seed)
+def nif_create(net, mesh, precision=NIF_FP32, seed=0, flags=0):
+    cfg = make_config(net, precision, seed, flags)
     v = np.ascontiguousarray(mesh.verts, np.float32)
     t = np.ascontiguousarray(mesh.tris, np.int32)
     a = np.ascontiguousarray(mesh.albedo, np.float32)
@@ -462,9 +464,10 @@ def nif_profile_read(h):
 class Nif:
     """Owns a nif_handle for one shape and configuration (see synth.NetConfig)."""
 
-    def __init__(self, net, mesh, precision=NIF_FP32, seed=0):
+    def __init__(self, net, mesh, precision=NIF_FP32, seed=0, flags=0):
         self.net = net
-        self.h = nif_create(net, mesh, precision, seed)
+        self.flags = flags
+        self.h = nif_create(net, mesh, precision, seed, flags)
 
     def close(self):
         if self.h is not None:

@@ -304,9 +304,10 @@ def test_labels_match_oracle(nif, torus):
     h.close()
 
 
-def test_loss_matches_oracle(nif, torus):
+@pytest.mark.parametrize("flags", [0, 1, 2, 3])
+def test_loss_matches_oracle(nif, torus, flags):
     net = S.NetConfig()
-    h = nif.Nif(net, torus)
+    h = nif.Nif(net, torus, flags=flags)
     rng = np.random.default_rng(91)
     n = 3001
     out = rng.normal(size=(n, 16)).astype(np.float32)
@@ -331,7 +332,7 @@ def test_loss_matches_oracle(nif, torus):
     rl = dict(occ=lab["occ"], tpar=lab["tpar"].astype(np.float64), normal=lab["normal"].astype(np.float64),
               albedo=lab["albedo"].astype(np.float64), material=lab["material"])
     tot, rparts, rdout, rds = O.loss(net, out.astype(np.float64), rl, s.astype(np.float64),
-                                     lin["l_rest"].astype(np.float64))
+                                     lin["l_rest"].astype(np.float64), flags)
     np.testing.assert_allclose(parts[1:], rparts, rtol=1e-5)
     assert abs(parts[0] - tot) < 1e-5 * max(1, abs(tot))
     np.testing.assert_allclose(dout.cpu().numpy(), rdout, atol=1e-5 * np.abs(rdout).max())

@@ -484,7 +484,8 @@ def _rand_labels(rng, n, M=4):
                 material=rng.integers(0, M, n).astype(np.uint8))
 
 
-def test_loss_and_mlp_gradients_match_finite_differences():
+@pytest.mark.parametrize("flags", [0, O.FLAG_FIXED_TASK_WEIGHTS | O.FLAG_SIGMOID_DISTANCE])
+def test_loss_and_mlp_gradients_match_finite_differences(flags):
     cfg = _tiny_cfg()
     rng = np.random.default_rng(12)
     n = 12
@@ -496,10 +497,10 @@ def test_loss_and_mlp_gradients_match_finite_differences():
 
     def total(ws_, x_, s_):
         out, _ = O.mlp_forward(ws_, x_)
-        return O.loss(cfg, out, lab, s_, lrest)[0]
+        return O.loss(cfg, out, lab, s_, lrest, flags)[0]
 
     out, acts = O.mlp_forward(ws, x)
-    tot, parts, dout, ds = O.loss(cfg, out, lab, s, lrest)
+    tot, parts, dout, ds = O.loss(cfg, out, lab, s, lrest, flags)
     dws, dx = O.mlp_backward(ws, acts, dout)
     h = 1e-6
     for li in range(3):
@@ -550,6 +551,27 @@ def test_loss_closed_forms():
     assert abs(ds[0]) < 1e-12 and abs(ds[4]) < 1e-12
     # occlusion loss of a zero logit is log 2
     np.testing.assert_allclose(parts[4], math.log(2))
+
+
+def test_ablation_loss_closed_forms():
+    """Fixed task weights: total = 0.5 (L_d + L_n + L_a) + L_m + L_o and no
+    gradient for s; sigmoid distance head: exact when sqrt(3) sigmoid(z) = y."""
+    cfg = _tiny_cfg()
+    rng = np.random.default_rng(21)
+    n = 40
+    lab = _rand_labels(rng, n)
+    lrest = np.full(n, 1.0 / cfg.voxel_res)
+    out = rng.normal(size=(n, 16))
+    s = rng.normal(size=5)
+    tot, parts, _, ds = O.loss(cfg, out, lab, s, lrest, O.FLAG_FIXED_TASK_WEIGHTS)
+    np.testing.assert_allclose(tot, 0.5 * parts[:3].sum() + parts[3:].sum())
+    assert not ds.any()
+    lab["occ"][:] = 1
+    y = lab["tpar"] * lrest * cfg.voxel_res             # in [0, 1] < sqrt(3)
+    q = y / np.sqrt(3.0)
+    out[:, 1] = np.log(q / (1 - q))
+    _, parts, _, _ = O.loss(cfg, out, lab, s, lrest, O.FLAG_SIGMOID_DISTANCE)
+    assert parts[0] < 1e-20
 
 
 def test_adam_first_step_is_signed_lr():
