@@ -86,6 +86,19 @@ typedef struct {
 #define NIF_FLAG_FIXED_TASK_WEIGHTS 1u
 #define NIF_FLAG_SIGMOID_DISTANCE 2u
 
+/* NIF_FLAG_MIXED_TRAINING  nif_train_step / nif_train_step_rays run the
+ * mixed-precision training path in cfg.precision (BF16 or FP16; W 32 or 64):
+ * features encoded from the FP16 table copy into 16-bit rows, tensor-core
+ * MLP forward keeping 16-bit activations, loss on the FP32 outputs,
+ * tensor-core backward and weight gradients on S * loss with FP32
+ * accumulation, FP32 atomic table gradients, FP32 master parameters and
+ * Adam on the gradient divided by S. A step whose gradient holds a
+ * non-finite value is skipped. S (the loss scale) starts at 2^15 for FP16
+ * (halved on a skipped step, doubled after 2000 finite steps) and stays 1
+ * for BF16. Sec. 3 of the paper trains with FP16 hash features and FP32
+ * master copies; the scaling rule is ours. */
+#define NIF_FLAG_MIXED_TRAINING 4u
+
 /* Rest-space triangle mesh inside [0,1]^3 (host memory, copied by nif_create). */
 typedef struct {
     const float* verts;                 /* [n_verts * 3] */
@@ -269,6 +282,29 @@ nif_status nif_mlp_forward(nif_handle* h, const void* x_dev, int x_dtype, int64_
  * writes dx_dev [n][in_dim] (nullable). */
 nif_status nif_mlp_backward(nif_handle* h, const float* x_dev, int64_t n, const float* acts_dev,
                             const float* dout_dev, float* dx_dev, void* stream);
+
+/* MLP backward of the mixed-precision path (tensor cores, cfg.precision BF16
+ * or FP16, W 32 or 64, in_dim % 16 == 0). x_dev [n][in_dim] of x_dtype ==
+ * cfg.precision (16-byte aligned); the hidden activations are recomputed
+ * from x_dev with the current weights. With S the handle's loss scale
+ * (nif_loss_scale): dY_H = 16-bit(S * dout_dev), dY_l = 16-bit((dY_{l+1}
+ * W_{l+1}) * [act_l > 0]); adds S * dL/dW (FP32 accumulation of the 16-bit
+ * products) into the gradient buffer and writes dx_dev [n][in_dim] = FP32
+ * dY_0 W_0 (nullable). */
+nif_status nif_mlp_backward_lowp(nif_handle* h, const void* x_dev, int x_dtype, int64_t n, const float* dout_dev,
+                                 float* dx_dev, void* stream);
+
+/* Loss scale of the mixed-precision path. nif_loss_scale reads S and the
+ * number of skipped steps (blocking); nif_set_loss_scale sets S (> 0,
+ * blocking). nif_adam_step_scaled: if any weight or table gradient is not
+ * finite the step is skipped (gradient cleared, skipped + 1, S halved for
+ * FP16 handles); otherwise Adam runs on gradient / S for the tables and
+ * weights (the log-variance gradient is taken as it is) with bias
+ * correction over the steps taken, and S doubles for FP16 handles after
+ * 2000 finite steps in a row. nif_reset_optimizer also resets S. */
+nif_status nif_loss_scale(nif_handle* h, float* scale_host, int* skipped_host);
+nif_status nif_set_loss_scale(nif_handle* h, float scale);
+nif_status nif_adam_step_scaled(nif_handle* h, float lr_grid, float lr_mlp, void* stream);
 
 /* Ground-truth labels (Sec. 2): the straight rest segment p0 -> p1 of lin[s]
  * against the triangles overlapping voxel segs[s].voxel; first hit in

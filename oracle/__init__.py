@@ -10,7 +10,8 @@ The oracle follows the paper step by step, in float64:
   (Sec. 2), ray / deformed-voxel segments (Sec. 2.1-2.2), linearized-segment
   labels (Sec. 2), exact deformed-space hits;
 * the hybrid encoding psi = phi o gamma (Eq. 1, Sec. 2.3), its backward;
-* the MLP (Sec. 2, Fig. 2d) forward and backward;
+* the MLP (Sec. 2, Fig. 2d) forward and backward, and the same with the
+  16-bit storage points of the mixed-precision path rounded (Sec. 3);
 * the task losses and the uncertainty weighting (Sec. 2.4);
 * Adam;
 * the segmented-ray distance and hit reconstruction (Sec. 2.2).
@@ -358,6 +359,42 @@ def mlp_backward(ws, acts, dout):
         g = g @ w
         if i > 0:
             g = g * (acts[i] > 0)
+    return dws, g
+
+
+def mlp_forward_rounded(ws, x, rnd):
+    """MLP forward of the mixed-precision path (Sec. 3 trains with 16-bit
+    operands): inputs, weights and the stored hidden activations pass through
+    `rnd` (rounding to the 16-bit type, given by the caller); products and
+    sums are exact (float64). Returns (out, acts) like mlp_forward, acts being
+    the rounded inputs of each layer."""
+    h = rnd(np.asarray(x, np.float64))
+    acts = [h]
+    for i, w in enumerate(ws):
+        z = h @ rnd(np.asarray(w, np.float64)).T
+        if i < len(ws) - 1:
+            h = rnd(np.maximum(z, 0.0))
+            acts.append(h)
+        else:
+            h = z
+    return h, acts
+
+
+def mlp_backward_rounded(ws, acts, dout, scale, rnd):
+    """Backward of the mixed-precision path for the loss multiplied by
+    `scale` (loss scaling): the output gradient and each layer's gradient are
+    rounded by `rnd` where the path stores them in 16 bits, i.e.
+    dY_H = rnd(scale * dout), dY_l = rnd((dY_{l+1} W_{l+1}) * [act > 0]),
+    weights rounded as in the forward. Returns (dws, dx), both multiplied by
+    `scale` (dx = dY_0 W_0 unrounded)."""
+    g = rnd(scale * np.asarray(dout, np.float64))
+    dws = [None] * len(ws)
+    for i in range(len(ws) - 1, -1, -1):
+        w = rnd(np.asarray(ws[i], np.float64))
+        dws[i] = g.T @ acts[i]
+        g = g @ w
+        if i > 0:
+            g = rnd(g * (acts[i] > 0))
     return dws, g
 
 

@@ -437,10 +437,10 @@ __global__ void __launch_bounds__(kScanT) k_scan_add(uint32_t* __restrict__ out,
 }
 
 __global__ void k_clamp_count(const uint32_t* offsets, int n_rays, int64_t cap, uint32_t* n_out,
-                              int* status) {
+                              int* status, int latch) {
     uint32_t tot = offsets[n_rays];
     if ((int64_t)tot > cap) {
-        nif_set_status(status, NIF_ERR_CAPACITY);
+        if (latch) nif_set_status(status, NIF_ERR_CAPACITY);
         tot = (uint32_t)cap;
     }
     *n_out = tot;
@@ -607,8 +607,8 @@ nif_status nif_scan_run(nif_handle* h, const uint32_t* in, uint32_t* out, int n,
 }
 
 nif_status nif_clamp_count_run(nif_handle* h, const uint32_t* offsets, int n_rays, int64_t cap, uint32_t* n_out,
-                               cudaStream_t s) {
-    k_clamp_count<<<1, 1, 0, s>>>(offsets, n_rays, cap, n_out, h->d_status);
+                               bool latch, cudaStream_t s) {
+    k_clamp_count<<<1, 1, 0, s>>>(offsets, n_rays, cap, n_out, h->d_status, latch ? 1 : 0);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

@@ -228,6 +228,72 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __re
 }
 
 // ---------------------------------------------------------------------------
+// Mixed-precision training: gradient check, Adam on the unscaled gradient
+// with overflow skip, dynamic loss scale update.
+// ---------------------------------------------------------------------------
+constexpr float kScaleGrowth = 2.0f, kScaleBackoff = 0.5f;
+constexpr int kScaleInterval = 2000;        // clean steps before S doubles
+constexpr float kScaleMax = 16777216.0f, kScaleMin = 1.0f / 16384.0f;
+
+__global__ void __launch_bounds__(256) k_grad_check(const float* __restrict__ g, size_t n, NifLossScale* ls) {
+    bool bad = false;
+    const size_t n4 = n / 4;
+    const float4* g4 = reinterpret_cast<const float4*>(g);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        float4 v = g4[i];
+        bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+    }
+    for (size_t i = n4 * 4 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(g[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&ls->overflow, 1);
+}
+
+// Adam (same constants as k_adam) on g / S for [0, unscale_end) and g beyond
+// (the task log-variances, whose gradient the loss writes unscaled); the whole
+// step is skipped when the check found a non-finite gradient. Bias
+// correction counts the steps taken: t = step - skipped.
+__global__ void __launch_bounds__(256) k_adam_scaled(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
+                                                     float* __restrict__ v, size_t n, size_t mlp_begin, size_t mlp_end,
+                                                     size_t unscale_end, float lr_grid, float lr_mlp, long step,
+                                                     const NifLossScale* __restrict__ ls) {
+    const float b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
+    __shared__ float c1s, c2s;
+    const bool skip = ls->overflow != 0;
+    if (threadIdx.x == 0) {
+        const double t = (double)(step - ls->skipped);
+        c1s = (float)(1.0 / (1.0 - pow(0.9, t)));
+        c2s = (float)(1.0 / (1.0 - pow(0.99, t)));
+    }
+    __syncthreads();
+    const float inv = 1.0f / ls->scale;
+    const float c1 = c1s, c2 = c2s;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        g[i] = 0.f;
+        if (skip) continue;
+        if (i < unscale_end) gi *= inv;
+        float mi = b1 * m[i] + (1.f - b1) * gi;
+        float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        float lr = (i >= mlp_begin && i < mlp_end) ? lr_mlp : lr_grid;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+__global__ void k_scale_update(NifLossScale* ls, int dynamic) {
+    if (ls->overflow) {
+        ls->overflow = 0;
+        ls->skipped++;
+        ls->clean = 0;
+        if (dynamic) ls->scale = fmaxf(ls->scale * kScaleBackoff, kScaleMin);
+    } else if (++ls->clean >= kScaleInterval) {
+        ls->clean = 0;
+        if (dynamic) ls->scale = fminf(ls->scale * kScaleGrowth, kScaleMax);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Reconstruction along the segmented ray (Sec. 2.2)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int find_inst_r(const int* inst_off, int n_inst, int r) {
@@ -397,6 +463,31 @@ nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t
     if (g > cap) g = cap;
     k_adam<<<g, 256, 0, s>>>(h->d_params, h->d_grad, h->d_m, h->d_v, h->n_params, h->off_layer[0], h->off_s,
                              lr_grid, lr_mlp, (float)c1, (float)c2);
+    NIF_CK_LAUNCH(h);
+    h->lowp_dirty = true;
+    return NIF_OK;
+}
+
+nif_status nif_grad_check_run(nif_handle* h, cudaStream_t s) {
+    NifProf prof_(h, "grad_check", s);
+    unsigned g = nif_blocks((int64_t)(h->off_s / 4 + 1), 256);
+    unsigned cap = (unsigned)h->num_sms * 8;
+    if (g > cap) g = cap;
+    k_grad_check<<<g, 256, 0, s>>>(h->d_grad, h->off_s, h->d_ls);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_adam_scaled_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s) {
+    NifProf prof_(h, "adam", s);
+    h->adam_step++;
+    unsigned g = nif_blocks((int64_t)h->n_params, 256);
+    unsigned cap = (unsigned)h->num_sms * 16;
+    if (g > cap) g = cap;
+    k_adam_scaled<<<g, 256, 0, s>>>(h->d_params, h->d_grad, h->d_m, h->d_v, h->n_params, h->off_layer[0], h->off_s,
+                                    h->off_s, lr_grid, lr_mlp, h->adam_step, h->d_ls);
+    NIF_CK_LAUNCH(h);
+    k_scale_update<<<1, 1, 0, s>>>(h->d_ls, h->cfg.precision == NIF_FP16 ? 1 : 0);
     NIF_CK_LAUNCH(h);
     h->lowp_dirty = true;
     return NIF_OK;

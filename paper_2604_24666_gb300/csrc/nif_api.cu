@@ -124,6 +124,29 @@ __global__ void k_to_lowp(const float* __restrict__ src, size_t n, __half* __res
     }
 }
 
+// transposed 16-bit copies of the weight matrices: layer l [out_l][in_l] -> [in_l][out_l]
+struct LayerDims {
+    int n;
+    size_t off[NIF_MAX_LAYERS + 1];   // element offsets relative to layer 0
+    int in[NIF_MAX_LAYERS], out[NIF_MAX_LAYERS];
+};
+
+__global__ void k_to_lowp_t(const float* __restrict__ w, LayerDims d, __half* __restrict__ h16,
+                            __nv_bfloat16* __restrict__ b16) {
+    const size_t total = d.off[d.n];
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < d.n && e >= d.off[l + 1]) l++;
+        const size_t r = e - d.off[l];
+        if (r >= (size_t)d.in[l] * d.out[l]) continue;      // alignment padding between layers
+        const int o = (int)(r / d.in[l]), i = (int)(r % d.in[l]);
+        const float v = w[e];
+        const size_t t = d.off[l] + (size_t)i * d.out[l] + o;
+        h16[t] = __float2half_rn(v);
+        b16[t] = __float2bfloat16_rn(v);
+    }
+}
+
 uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
@@ -160,7 +183,23 @@ nif_status nif_refresh_lowp(nif_handle* h, cudaStream_t s) {
     k_to_lowp<<<std::max(1, std::min(h->num_sms * 8, (int)((nw + 255) / 256))), 256, 0, s>>>(
         h->d_params + h->off_layer[0], nw, h->d_w_f16, h->d_w_bf16);
     NIF_CK_LAUNCH(h);
+    LayerDims d{};
+    d.n = h->n_layers;
+    for (int l = 0; l <= h->n_layers; l++) d.off[l] = h->off_layer[l] - h->off_layer[0];
+    for (int l = 0; l < h->n_layers; l++) {
+        d.in[l] = h->lay_in[l];
+        d.out[l] = h->lay_out[l];
+    }
+    k_to_lowp_t<<<std::max(1, std::min(h->num_sms * 4, (int)((nw + 255) / 256))), 256, 0, s>>>(
+        h->d_params + h->off_layer[0], d, h->d_wt_f16, h->d_wt_bf16);
+    NIF_CK_LAUNCH(h);
     h->lowp_dirty = false;
+    return NIF_OK;
+}
+
+nif_status reset_loss_scale(nif_handle* h) {
+    NifLossScale ls{h->cfg.precision == NIF_FP16 ? 32768.0f : 1.0f, 0, 0, 0};
+    NIF_CK(h, cudaMemcpy(h->d_ls, &ls, sizeof(ls), cudaMemcpyHostToDevice));
     return NIF_OK;
 }
 
@@ -209,8 +248,10 @@ static nif_status validate(const nif_config* c, const nif_mesh* m) {
         return nif_fail(nullptr, NIF_ERR_ARG, "mlp_width in {16, 32, 64, 128}");
     if (c->n_materials < 1 || c->n_materials > 8) return nif_fail(nullptr, NIF_ERR_ARG, "n_materials in [1, 8]");
     if (c->precision < NIF_FP32 || c->precision > NIF_FP16) return nif_fail(nullptr, NIF_ERR_ARG, "precision");
-    if (c->flags & ~(NIF_FLAG_FIXED_TASK_WEIGHTS | NIF_FLAG_SIGMOID_DISTANCE))
+    if (c->flags & ~(NIF_FLAG_FIXED_TASK_WEIGHTS | NIF_FLAG_SIGMOID_DISTANCE | NIF_FLAG_MIXED_TRAINING))
         return nif_fail(nullptr, NIF_ERR_ARG, "unknown flags");
+    if ((c->flags & NIF_FLAG_MIXED_TRAINING) && c->precision == NIF_FP32)
+        return nif_fail(nullptr, NIF_ERR_ARG, "NIF_FLAG_MIXED_TRAINING needs precision NIF_BF16 or NIF_FP16");
     if (m->n_tris < 0 || m->n_verts < 0 || (m->n_tris > 0 && (!m->tris || !m->verts)))
         return nif_fail(nullptr, NIF_ERR_ARG, "mesh arrays");
     for (int t = 0; t < m->n_tris * 3; t++)
@@ -403,7 +444,13 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
     CKC(cudaMalloc(&h->d_tables_h, sizeof(__half) * (size_t)h->L * h->T * h->Fd));
     CKC(cudaMalloc(&h->d_w_bf16, sizeof(__nv_bfloat16) * (h->off_s - h->off_layer[0])));
     CKC(cudaMalloc(&h->d_w_f16, sizeof(__half) * (h->off_s - h->off_layer[0])));
+    CKC(cudaMalloc(&h->d_wt_bf16, sizeof(__nv_bfloat16) * (h->off_s - h->off_layer[0])));
+    CKC(cudaMalloc(&h->d_wt_f16, sizeof(__half) * (h->off_s - h->off_layer[0])));
+    CKC(cudaMemset(h->d_wt_bf16, 0, sizeof(__nv_bfloat16) * (h->off_s - h->off_layer[0])));
+    CKC(cudaMemset(h->d_wt_f16, 0, sizeof(__half) * (h->off_s - h->off_layer[0])));
+    CKC(cudaMalloc(&h->d_ls, sizeof(NifLossScale)));
 #undef CKC
+    if ((st = reset_loss_scale(h)) != NIF_OK) return fail(st);
     st = init_params(h);
     if (st != NIF_OK) return fail(st);
     st = nif_ensure_instances(h, 1);
@@ -417,13 +464,13 @@ extern "C" void nif_destroy(nif_handle* h) {
     cudaDeviceSynchronize();
     void* ptrs[] = {h->d_verts, h->d_tris, h->d_alb, h->d_mat, h->d_occ, h->d_tri_ptr, h->d_tri_idx, h->d_child,
                     h->d_leaf_vox, h->d_leaf_lat, h->d_corners, h->d_aabb, h->d_pose, h->d_params, h->d_grad,
-                    h->d_m, h->d_v, h->d_tables_h, h->d_w_bf16, h->d_w_f16, h->d_status, h->d_lossacc,
-                    h->d_count};
+                    h->d_m, h->d_v, h->d_tables_h, h->d_w_bf16, h->d_w_f16, h->d_wt_bf16, h->d_wt_f16, h->d_ls,
+                    h->d_status, h->d_lossacc, h->d_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
                                &h->b_acts, &h->b_dout, &h->b_dx, &h->b_labels, &h->b_scan, &h->b_rays,
-                               &h->b_inst, &h->b_feat2};
+                               &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys};
     for (auto* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -498,6 +545,32 @@ extern "C" nif_status nif_reset_optimizer(nif_handle* h) {
     NIF_CK(h, cudaMemset(h->d_m, 0, sizeof(float) * h->n_params));
     NIF_CK(h, cudaMemset(h->d_v, 0, sizeof(float) * h->n_params));
     h->adam_step = 0;
+    return reset_loss_scale(h);
+}
+
+extern "C" nif_status nif_adam_step_scaled(nif_handle* h, float lr_grid, float lr_mlp, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    nif_status st = nif_grad_check_run(h, s);
+    if (st != NIF_OK) return st;
+    return nif_adam_scaled_run(h, lr_grid, lr_mlp, s);
+}
+
+extern "C" nif_status nif_loss_scale(nif_handle* h, float* scale, int* skipped) {
+    if (!h) return NIF_ERR_ARG;
+    NifLossScale ls;
+    NIF_CK(h, cudaDeviceSynchronize());
+    NIF_CK(h, cudaMemcpy(&ls, h->d_ls, sizeof(ls), cudaMemcpyDeviceToHost));
+    if (scale) *scale = ls.scale;
+    if (skipped) *skipped = ls.skipped;
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_set_loss_scale(nif_handle* h, float scale) {
+    if (!h) return NIF_ERR_ARG;
+    if (!(scale > 0.f) || !std::isfinite(scale)) return nif_fail(h, NIF_ERR_ARG, "loss scale must be positive and finite");
+    NIF_CK(h, cudaDeviceSynchronize());
+    NIF_CK(h, cudaMemcpy(&h->d_ls->scale, &scale, sizeof(float), cudaMemcpyHostToDevice));
     return NIF_OK;
 }
 
@@ -759,6 +832,45 @@ extern "C" nif_status nif_mlp_backward(nif_handle* h, const float* x, int64_t n,
     return nif_mlp_bwd_fp32_run(h, x, nullptr, n, acts, dout, dx, (cudaStream_t)stream);
 }
 
+// 16-bit activations and output gradients of the mixed path: [layers][n_pad][kLd]
+static constexpr int kLd = 64;
+
+static int64_t pad128(int64_t n) { return (n + 127) / 128 * 128; }
+
+static nif_status check_mixed(nif_handle* h) {
+    if (h->cfg.precision != NIF_BF16 && h->cfg.precision != NIF_FP16)
+        return nif_fail(h, NIF_ERR_ARG, "mixed-precision training needs a BF16 or FP16 handle");
+    if (h->W != 32 && h->W != 64) return nif_fail(h, NIF_ERR_ARG, "mixed-precision training needs W = 32 or 64");
+    if (h->in_dim % 16 != 0) return nif_fail(h, NIF_ERR_ARG, "mixed-precision training needs in_dim % 16 == 0");
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_mlp_backward_lowp(nif_handle* h, const void* x, int x_dtype, int64_t n, const float* dout,
+                                            float* dx, void* stream) {
+    if (!h || n < 0 || (n > 0 && (!x || !dout))) return NIF_ERR_ARG;
+    nif_status st = check_mixed(h);
+    if (st != NIF_OK) return st;
+    if (x_dtype != h->cfg.precision) return nif_fail(h, NIF_ERR_ARG, "x_dtype must equal the handle's precision");
+    if ((reinterpret_cast<uintptr_t>(x) & 15) != 0) return nif_fail(h, NIF_ERR_ARG, "x not 16-byte aligned");
+    if (n == 0) return NIF_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t np = pad128(n);
+    if ((st = nif_grow(h, h->b_acts, 2 * (size_t)np * kLd * h->H)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_dys, 2 * (size_t)np * kLd * (h->H + 1))) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * (size_t)np)) != NIF_OK) return st;
+    if (!dx) {
+        if ((st = nif_grow(h, h->b_dx, sizeof(float) * (size_t)h->in_dim * n)) != NIF_OK) return st;
+        dx = (float*)h->b_dx.p;
+    }
+    uint16_t* acts = (uint16_t*)h->b_acts.p;
+    uint16_t* dys = (uint16_t*)h->b_dys.p;
+    // activations recomputed from x with the current weights
+    if ((st = nif_mlp_fwd_tc_acts_run(h, x, x_dtype, nullptr, n, (float*)h->b_out.p, acts, np, kLd, s)) != NIF_OK)
+        return st;
+    if ((st = nif_mlp_bwd_tc_run(h, dout, acts, nullptr, n, np, kLd, dys, dx, s)) != NIF_OK) return st;
+    return nif_mlp_dw_tc_run(h, x, acts, dys, nullptr, n, np, kLd, s);
+}
+
 extern "C" nif_status nif_labels(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, int64_t n,
                                  nif_label* labels, void* stream) {
     if (!h || n < 0 || (n > 0 && (!segs || !lin || !labels))) return NIF_ERR_ARG;
@@ -873,8 +985,9 @@ static nif_status segment_into_scratch(nif_handle* h, const nif_pose* poses, int
             NIF_OK)
             return st;
     }
-    // clamped count lives right after the offsets
-    return nif_clamp_count_run(h, offs, n_rays, cap, offs + n_rays + 1, s);
+    // clamped count lives right after the offsets; a training batch that the
+    // rays overfill is the normal case and latches nothing
+    return nif_clamp_count_run(h, offs, n_rays, cap, offs + n_rays + 1, host_total, s);
 }
 
 extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
@@ -934,6 +1047,8 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
     nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
     if (st != NIF_OK) return st;
     if (n_segments < 1 || !rays) return nif_fail(h, NIF_ERR_ARG, "n_segments / rays");
+    const bool mixed = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
+    if (mixed && (st = check_mixed(h)) != NIF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, n_segments, false, nullptr, s)) != NIF_OK)
         return st;
@@ -947,7 +1062,14 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
     if ((st = nif_grow(h, h->b_dx, sizeof(float) * (size_t)h->in_dim * n)) != NIF_OK) return st;
     if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
     if ((st = nif_grow(h, h->b_feat2, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
-    if ((st = nif_grow(h, h->b_acts, sizeof(float) * (size_t)n * h->W * h->H)) != NIF_OK) return st;
+    const int64_t np = pad128(n);
+    if ((st = nif_grow(h, h->b_acts, mixed ? 2 * (size_t)np * kLd * h->H : sizeof(float) * (size_t)n * h->W * h->H)) !=
+        NIF_OK)
+        return st;
+    if (mixed) {
+        if ((st = nif_grow(h, h->b_feat, 2 * (size_t)h->in_dim * np)) != NIF_OK) return st;
+        if ((st = nif_grow(h, h->b_dys, 2 * (size_t)np * kLd * (h->H + 1))) != NIF_OK) return st;
+    }
     nif_segment* segs = (nif_segment*)h->b_segs.p;
     nif_linseg* lin = (nif_linseg*)h->b_lin.p;
     nif_label* lab = (nif_label*)h->b_labels.p;
@@ -958,12 +1080,31 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
     float* acts = (float*)h->b_acts.p;
     if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, n, lin, s)) != NIF_OK) return st;
     if ((st = nif_labels_run(h, segs, lin, n_dev, n, lab, s)) != NIF_OK) return st;
-    if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s)) != NIF_OK) return st;
-    if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
-    if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s)) != NIF_OK) return st;
-    if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s)) != NIF_OK) return st;
-    if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK) return st;
-    if ((st = nif_adam_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
+    if (mixed) {
+        // 16-bit features from the FP16 table copy, tensor-core MLP forward
+        // keeping its activations, loss on FP32 outputs, scaled tensor-core
+        // backward and weight gradients, FP32 table gradients, checked Adam
+        const int prec = h->cfg.precision;
+        uint16_t* acts16 = (uint16_t*)h->b_acts.p;
+        uint16_t* dys = (uint16_t*)h->b_dys.p;
+        if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, prec, NIF_FP16, s)) != NIF_OK) return st;
+        if ((st = nif_mlp_fwd_tc_acts_run(h, feat, prec, n_dev, n, out, acts16, np, kLd, s)) != NIF_OK) return st;
+        if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s)) != NIF_OK) return st;
+        if ((st = nif_mlp_bwd_tc_run(h, dout, acts16, n_dev, n, np, kLd, dys, dx, s)) != NIF_OK) return st;
+        if ((st = nif_mlp_dw_tc_run(h, feat, acts16, dys, n_dev, n, np, kLd, s)) != NIF_OK) return st;
+        if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK)
+            return st;
+        if ((st = nif_grad_check_run(h, s)) != NIF_OK) return st;
+        if ((st = nif_adam_scaled_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
+    } else {
+        if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s)) != NIF_OK) return st;
+        if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
+        if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s)) != NIF_OK) return st;
+        if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s)) != NIF_OK) return st;
+        if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK)
+            return st;
+        if ((st = nif_adam_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
+    }
     if (loss_host) {
         double acc[16];
         NIF_CK(h, cudaStreamSynchronize(s));
@@ -972,11 +1113,10 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
         for (int i = 0; i < 5; i++) loss_host[1 + i] = acc[9 + i];
         int dst = 0;
         NIF_CK(h, cudaMemcpy(&dst, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-        if (dst == NIF_ERR_NAN) {
+        if (dst != 0) {
             cudaMemset(h->d_status, 0, sizeof(int));
-            return nif_fail(h, NIF_ERR_NAN, "non-finite loss");
+            return nif_fail(h, (nif_status)dst, dst == NIF_ERR_NAN ? "non-finite loss" : "device-side error latched by a kernel");
         }
-        if (dst == NIF_ERR_CAPACITY) cudaMemset(h->d_status, 0, sizeof(int));   // a full batch
     }
     return NIF_OK;
 }

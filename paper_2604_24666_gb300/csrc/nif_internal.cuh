@@ -39,6 +39,16 @@ struct TreeView {
     const uint32_t* leaf_vox; // [n_leaves] rest voxel id of each leaf
 };
 
+// Dynamic loss scaling state (device): gradients of the 16-bit training path
+// are computed for S * loss; Adam unscales them, or skips the step when any
+// is not finite.
+struct NifLossScale {
+    float scale;      // S
+    int clean;        // consecutive finite steps since the last change of S
+    int overflow;     // set by the gradient check of the current step
+    int skipped;      // steps skipped so far (Adam's bias correction counts the others)
+};
+
 struct nif_handle {
     nif_config cfg{};
     int N = 0, L = 0, Fd = 2, P = 0, in_dim = 0, W = 0, H = 0, n_layers = 0;
@@ -82,6 +92,9 @@ struct nif_handle {
     __half* d_tables_h = nullptr;       // FP16 copy of the tables
     __nv_bfloat16* d_w_bf16 = nullptr;  // BF16 copy of the weights (layers back to back)
     __half* d_w_f16 = nullptr;          // FP16 copy of the weights
+    __nv_bfloat16* d_wt_bf16 = nullptr; // BF16 copy of the transposed weights (layer l: [in_l][out_l])
+    __half* d_wt_f16 = nullptr;         // FP16 copy of the transposed weights
+    NifLossScale* d_ls = nullptr;       // dynamic loss scale of the mixed-precision training path
     bool lowp_dirty = true;
     long adam_step = 0;
 
@@ -94,7 +107,7 @@ struct nif_handle {
     // grown scratch buffers (query / train)
     struct Buf { void* p = nullptr; size_t bytes = 0; };
     Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
-        b_scan, b_rays, b_inst, b_feat2, b_temp;
+        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys;
     double query_seg_per_ray = 0.0;     // segments per ray of the last query (temp capacity hint)
 
     // launch knobs chosen by the autotuner (nif_query_plan_create)
@@ -140,6 +153,8 @@ nif_status nif_grow(nif_handle* h, nif_handle::Buf& b, size_t bytes);
 nif_status nif_ensure_instances(nif_handle* h, int n_inst);
 nif_status nif_upload_poses(nif_handle* h, const nif_pose* poses, int n_inst, cudaStream_t s);
 nif_status nif_refresh_lowp(nif_handle* h, cudaStream_t s);
+// loss scale back to its initial value (FP16 handles 2^15, others 1), counters cleared (blocking)
+nif_status reset_loss_scale(nif_handle* h);
 
 #define NIF_CK(h, call)                                                   \
     do {                                                                  \
@@ -199,6 +214,18 @@ nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n
                                 const float* acts, const float* dout, float* dx, cudaStream_t s);
 nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev,
                               int64_t n_max, float* out, cudaStream_t s);
+// acts_out (nullable): 16-bit hidden activations, layer l row r at (l * acts_rows + r) * acts_ld
+nif_status nif_mlp_fwd_tc_acts_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev, int64_t n_max,
+                                   float* out, uint16_t* acts_out, int64_t acts_rows, int acts_ld, cudaStream_t s);
+// 16-bit backward in the handle's precision: dY_l (scaled by the loss scale) into
+// dys [H+1][n_pad][ld], dx [n][in_dim] FP32 (scaled)
+nif_status nif_mlp_bwd_tc_run(nif_handle* h, const float* dout, const uint16_t* acts, const uint32_t* n_dev,
+                              int64_t n_max, int64_t n_pad, int ld, uint16_t* dys, float* dx, cudaStream_t s);
+// dW_l += dY_l^T X_l into the gradient buffer (FP32, scaled)
+nif_status nif_mlp_dw_tc_run(nif_handle* h, const void* x16, const uint16_t* acts, const uint16_t* dys,
+                             const uint32_t* n_dev, int64_t n_max, int64_t n_pad, int ld, cudaStream_t s);
+nif_status nif_grad_check_run(nif_handle* h, cudaStream_t s);
+nif_status nif_adam_scaled_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s);
 nif_status nif_labels_count_hits(nif_handle* h, const nif_label* labels, int64_t n, cudaStream_t s);
 nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin,
                           const uint32_t* n_dev, int64_t n_max, nif_label* labels, cudaStream_t s);
@@ -214,8 +241,10 @@ nif_status nif_sample_rays_run(nif_handle* h, unsigned long long seed, int strea
                                nif_ray* rays, cudaStream_t s);
 nif_status nif_scan_run_with(nif_handle* h, const uint32_t* in, uint32_t* out, int n, uint32_t* bsum,
                              cudaStream_t s);
+// n_out = min(offsets[n_rays], cap); latch: an overflow latches NIF_ERR_CAPACITY
+// (a truncated query), otherwise it is the normal end of a training batch
 nif_status nif_clamp_count_run(nif_handle* h, const uint32_t* offsets, int n_rays, int64_t cap,
-                               uint32_t* n_out, cudaStream_t s);
+                               uint32_t* n_out, bool latch, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Device math: deformation D = Bend o Twist o Taper about c = (0.5,0.5,0.5)

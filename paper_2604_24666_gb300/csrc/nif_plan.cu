@@ -68,7 +68,7 @@ nif_status plan_enqueue(nif_query_plan* p, cudaStream_t s) {
     if ((st = nif_seg_temp_run(h, p->rays, p->inst_off, p->n_inst, n, counts, temp, p->cap, cursor, s)) != NIF_OK)
         return st;
     if ((st = nif_scan_run(h, counts, offs, n, s)) != NIF_OK) return st;
-    if ((st = nif_clamp_count_run(h, offs, n, p->cap, n_dev, s)) != NIF_OK) return st;
+    if ((st = nif_clamp_count_run(h, offs, n, p->cap, n_dev, true, s)) != NIF_OK) return st;
     NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)n, s));
     if ((st = nif_seg_scatter_run(h, temp, cursor, p->cap, offs, counts, n, segs, p->cap, s)) != NIF_OK) return st;
     if ((st = nif_linearize_run(h, p->rays, p->inst_off, p->n_inst, segs, n_dev, p->cap, lin, s)) != NIF_OK) return st;

@@ -22,7 +22,7 @@ NIF_OK, NIF_ERR_ARG, NIF_ERR_CUDA, NIF_ERR_OOM, NIF_ERR_CAPACITY, NIF_ERR_TIMEOU
 NIF_FP32, NIF_BF16, NIF_FP16 = 0, 1, 2
 NIF_PARAM_TABLES, NIF_PARAM_LOGVAR, NIF_PARAM_LAYER0 = 0, 1, 16
 NIF_SHADOW_ONLY = 1
-NIF_FLAG_FIXED_TASK_WEIGHTS, NIF_FLAG_SIGMOID_DISTANCE = 1, 2
+NIF_FLAG_FIXED_TASK_WEIGHTS, NIF_FLAG_SIGMOID_DISTANCE, NIF_FLAG_MIXED_TRAINING = 1, 2, 4
 
 _STATUS = {0: "NIF_OK", -1: "NIF_ERR_ARG", -2: "NIF_ERR_CUDA", -3: "NIF_ERR_OOM", -4: "NIF_ERR_CAPACITY",
            -5: "NIF_ERR_TIMEOUT", -6: "NIF_ERR_NAN", -7: "NIF_ERR_STATE"}
@@ -95,6 +95,10 @@ def lib() -> ctypes.CDLL:
             "nif_pose_gradient": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
             "nif_mlp_forward": ([_vp, _vp, ctypes.c_int, _i64, _vp, ctypes.c_int, _vp, _vp], ctypes.c_int),
             "nif_mlp_backward": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], ctypes.c_int),
+            "nif_mlp_backward_lowp": ([_vp, _vp, ctypes.c_int, _i64, _vp, _vp, _vp], ctypes.c_int),
+            "nif_loss_scale": ([_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "nif_set_loss_scale": ([_vp, ctypes.c_float], ctypes.c_int),
+            "nif_adam_step_scaled": ([_vp, ctypes.c_float, ctypes.c_float, _vp], ctypes.c_int),
             "nif_labels": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
             "nif_loss": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
             "nif_reconstruct": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
@@ -329,6 +333,31 @@ def nif_mlp_backward(h, x, acts, dout, want_dx=True, stream=None):
     dx = torch.zeros_like(x) if want_dx else None
     _check(h, lib().nif_mlp_backward(h, _ptr(x), x.shape[0], _ptr(acts), _ptr(dout), _ptr(dx), _stream(stream)))
     return dx
+
+
+def nif_mlp_backward_lowp(h, x, dout, want_dx=True, stream=None):
+    """Tensor-core MLP backward of the mixed path: x [n][in_dim] BF16/FP16
+    (the handle's precision), dout [n][16] FP32. Adds S * dL/dW into the
+    gradient buffer and returns S * dL/dx (FP32) with S the loss scale."""
+    dt = {torch.bfloat16: NIF_BF16, torch.float16: NIF_FP16}[x.dtype]
+    dx = torch.zeros((x.shape[0], x.shape[1]), dtype=torch.float32, device=x.device) if want_dx else None
+    _check(h, lib().nif_mlp_backward_lowp(h, _ptr(x), dt, x.shape[0], _ptr(dout), _ptr(dx), _stream(stream)))
+    return dx
+
+
+def nif_loss_scale(h):
+    """(S, skipped steps) of the mixed-precision path."""
+    sc, sk = ctypes.c_float(), ctypes.c_int()
+    _check(h, lib().nif_loss_scale(h, ctypes.byref(sc), ctypes.byref(sk)))
+    return sc.value, sk.value
+
+
+def nif_set_loss_scale(h, scale):
+    _check(h, lib().nif_set_loss_scale(h, float(scale)))
+
+
+def nif_adam_step_scaled(h, lr_grid, lr_mlp, stream=None):
+    _check(h, lib().nif_adam_step_scaled(h, lr_grid, lr_mlp, _stream(stream)))
 
 
 def nif_labels(h, segs, lin, stream=None):

@@ -10,6 +10,7 @@ import math
 
 import numpy as np
 import pytest
+import torch
 
 import oracle as O
 from paper_2604_24666_gb300 import synth as S
@@ -635,3 +636,46 @@ def test_pose_gradient_matches_finite_differences():
         e = np.zeros(3); e[j] = h
         fd = (f(pose + e) - f(pose - e)) / (2 * h)
         assert abs(fd - g[j]) <= 5e-3 * max(1.0, abs(fd)), (j, fd, g[j])
+
+
+def _bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def test_rounded_mlp_reduces_to_exact_mlp():
+    """With no rounding and unit scale the mixed-path MLP is the FP64 MLP
+    (itself pinned by finite differences); the scale multiplies every
+    gradient (linearity)."""
+    rng = np.random.default_rng(14)
+    ws = [rng.normal(size=sh) for sh in [(8, 10), (8, 8), (16, 8)]]
+    x = rng.normal(size=(9, 10))
+    dout = rng.normal(size=(9, 16))
+    ident = lambda a: a
+    out_r, acts_r = O.mlp_forward_rounded(ws, x, ident)
+    out, acts = O.mlp_forward(ws, x)
+    np.testing.assert_allclose(out_r, out, rtol=1e-13)
+    dws, dx = O.mlp_backward(ws, acts, dout)
+    for scale in (1.0, 1024.0):
+        dws_r, dx_r = O.mlp_backward_rounded(ws, acts_r, dout, scale, ident)
+        np.testing.assert_allclose(dx_r, scale * dx, rtol=1e-12)
+        for a, b in zip(dws_r, dws):
+            np.testing.assert_allclose(a, scale * b, rtol=1e-12)
+
+
+def test_rounded_mlp_rounds_where_it_stores():
+    """Hand-worked case in BF16 (8 significant bits, spacing 2^-7 in [1, 2)):
+    one hidden unit, x = 1, W0 = 1 + 2^-9 -> 1, W1 = 3 + 2^-6 -> 3 (spacing
+    2^-6 in [2, 4) keeps it: 3.015625). Forward: act = rnd(1 * 1) = 1, out =
+    3.015625. Backward with dout = 1 + 2^-9 (-> 1) and scale 4: dY_1 = 4,
+    dW1 = 4, dX = 4 * 3.015625 = 12.0625 -> rnd (spacing 2^-4 in [8, 16)) =
+    12.0625, masked by act > 0; dW0 = 12.0625, dx = 12.0625 * 1."""
+    ws = [np.array([[1 + 2.0 ** -9]]), np.array([[3 + 2.0 ** -6]])]
+    out, acts = O.mlp_forward_rounded(ws, np.array([[1.0]]), _bf16)
+    assert out[0, 0] == 3.015625 and acts[1][0, 0] == 1.0
+    dws, dx = O.mlp_backward_rounded(ws, acts, np.array([[1 + 2.0 ** -9]]), 4.0, _bf16)
+    assert dws[1][0, 0] == 4.0
+    assert dws[0][0, 0] == 12.0625 and dx[0, 0] == 12.0625
+    # a negative pre-activation: the ReLU mask zeroes the hidden gradient
+    out, acts = O.mlp_forward_rounded([-ws[0], ws[1]], np.array([[1.0]]), _bf16)
+    dws, dx = O.mlp_backward_rounded([-ws[0], ws[1]], acts, np.array([[1.0]]), 4.0, _bf16)
+    assert out[0, 0] == 0.0 and dws[0][0, 0] == 0.0 and dx[0, 0] == 0.0 and dws[1][0, 0] == 0.0
