@@ -299,6 +299,9 @@ def run_ours(args):
            "h2d_bytes_per_step": int(rays_host.numel() * 4), "d2h_bytes_per_step": 48}
     h.close()
 
+    # ---- mixed-precision training, same workload ---------------------------
+    mixed = run_train_mixed(args, nif, S, dev, rank, hbm) if not args.no_mixed else None
+
     # ---- inference queries ------------------------------------------------
     query = run_query(args, nif, S, dev, rank) if not args.no_query else None
     batch = run_batch(args, nif, S, dev, rank) if not args.no_batch else None
@@ -326,13 +329,59 @@ def run_ours(args):
                        "mlp": "-".join(str(x) for x in [net.in_dim] + [net.mlp_width] * net.mlp_depth + [16]),
                        "l2": "working set larger than L2 (tables, gradients, Adam state 256 MB; features 604 MB)"},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "loss": list(loss) if loss is not None else None, "query": query, "batch": batch,
+            "clocks": clocks, "loss": list(loss) if loss is not None else None, "train_mixed": mixed,
+            "query": query, "batch": batch,
             "precision": precision}
     print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def run_train_mixed(args, nif, S, dev, rank, hbm):
+    """The training step of the same workload on the mixed-precision path
+    (FP16 / BF16 tensor-core MLP forward and backward, FP16 table copy,
+    FP32 masters, loss scaling): segments/s and the per-stage split."""
+    import torch
+    w = S.WORKLOADS[TRAIN_WORKLOAD]
+    net = w["net"]
+    mesh = S.make_mesh(w["shape"])
+    res = {}
+    for name, prec in (("fp16", nif.NIF_FP16), ("bf16", nif.NIF_BF16)):
+        h = nif.Nif(net, mesh, precision=prec, seed=1234 + rank, flags=nif.NIF_FLAG_MIXED_TRAINING)
+        stream = torch.cuda.current_stream()
+        seed0 = 91 + 1000003 * rank
+        for i in range(args.warmup):
+            nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + i, want_loss=False)
+        torch.cuda.synchronize()
+        nif.nif_profile(h.h, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.steps):
+            nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + args.warmup + i, want_loss=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = nif.nif_profile_read(h.h)
+        nif.nif_profile(h.h, 0)
+        loss, _ = nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + 99999, want_loss=True)
+        scale, skipped = nif.nif_loss_scale(h.h)
+        tot = sum(v[0] for v in prof.values())
+        stages = {k: {"ms_per_step": v[0] / max(args.steps, 1), "share": v[0] / tot if tot else None}
+                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+        for k in ("encode_fwd", "encode_bwd"):
+            if k in stages:
+                amount = _stage_work(net, k, N_SEG)[0]
+                if k == "encode_fwd":       # FP16 table corners, 16-bit feature rows
+                    P, L = net.n_terms, net.levels
+                    amount = N_SEG * (2 * P * L * 8 * 4 + 32 + net.in_dim * 2)
+                stages[k]["GB/s"] = amount / (stages[k]["ms_per_step"] / 1e3) / 1e9
+                stages[k]["frac_hbm"] = stages[k]["GB/s"] / hbm
+        res[name] = {"value": args.steps * N_SEG / (ms / 1e3), "unit": "segments/s", "ms_per_step": ms / args.steps,
+                     "loss_scale": scale, "skipped_steps": skipped, "loss": list(loss), "kernels": stages}
+        h.close()
+    return res
 
 
 def h_seg_per_ray(h, nif):
@@ -505,6 +554,7 @@ def main():
     ap.add_argument("--query-prec", default="fp32,bf16,fp16", help="comma list of query precisions")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance query measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-output precision study")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision training measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -407,14 +407,16 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_sm(GridInfo g, Coa
     }
 }
 
-// Backward with a run-length register cache. A warp owns 32/L (endpoint,
-// term) pairs x L levels (lane = level + L * pair) and walks a chunk of kRun
-// consecutive segments; segments come in ray order, so consecutive points of
-// one term are spatially close and a coarse cell repeats for many segments
-// (the low sin/cos bands of gamma cover only part of [0,1]). Each lane keeps
-// the row and the running sum of its 8 corners and reduces into the table
-// only when a corner's row changes: dense coarse levels into the block's
-// shared-memory copy, the rest into global memory.
+// Backward with a run-length register cache. A warp owns 32/L gamma terms x
+// L levels (lane = level + L * term) and walks a chunk of kRun consecutive
+// segments, visiting each segment's two end points in turn: p0(s), p1(s),
+// p0(s+1), ... Segments come in ray order, and where two voxels share a face
+// the exit point of one is the entry point of the next (the same deformed
+// point through the same inverse), so p1(s) and p0(s+1) fall in the same cell
+// at every level; coarse cells also repeat over many segments. Each lane
+// keeps the row and the running sum of its 8 corners and reduces into the
+// table only when a corner's row changes: dense coarse levels into the
+// block's shared-memory copy, the rest into global memory.
 constexpr int kRun = 64;
 
 __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coarse cs,
@@ -429,10 +431,10 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
     int64_t n = n_dev ? (int64_t)*n_dev : n_max;
     if (n > n_max) n = n_max;
     const int lane = threadIdx.x & 31;
-    const int ppw = 32 / g.L;                          // (endpoint, term) pairs per warp
-    const int groups = (2 * g.P + ppw - 1) / ppw;
+    const int tpw = 32 / g.L;                          // gamma terms per warp
+    const int groups = (g.P + tpw - 1) / tpw;
     const int l = lane % g.L;
-    const int pair_in_warp = lane / g.L;
+    const int term_in_warp = lane / g.L;
     const int Nl = g.res[l];
     const bool dense = (g.dense_mask >> l) & 1u;
     const bool in_sh = l < cs.Lc;
@@ -444,39 +446,41 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
          task += warps_total) {
         const int64_t c = task / groups;
         const int grp = (int)(task - c * groups);
-        const int pair = grp * ppw + pair_in_warp;        // (endpoint, term) index in [0, 2P)
-        const bool active = pair < 2 * g.P;
-        const int e = pair >= g.P;
-        const int t = pair - e * g.P;
+        const int t = grp * tpw + term_in_warp;           // gamma term in [0, P)
+        const bool active = t < g.P;
         uint32_t crow[8];
         float2 cacc[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) { crow[q] = 0xffffffffu; cacc[q] = make_float2(0.f, 0.f); }
         const int64_t s_end = (c + 1) * kRun < n ? (c + 1) * kRun : n;
         for (int64_t s = c * kRun; s < s_end && active; s++) {
-            const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
-            float3 u = term_u(clamp01(make_float3(L[0], L[1], L[2])), t);
-            Cell cl = cell_of(u, Nl);
-            float2 gr = *reinterpret_cast<const float2*>(dfeats + ((s * 2 * g.P + pair) * g.L + l) * 2);
+#pragma unroll 1
+            for (int e = 0; e < 2; e++) {
+                const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+                float3 u = term_u(clamp01(make_float3(L[0], L[1], L[2])), t);
+                Cell cl = cell_of(u, Nl);
+                float2 gr = *reinterpret_cast<const float2*>(dfeats + ((s * 2 * g.P + e * g.P + t) * g.L + l) * 2);
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                uint32_t row = grid_row(cl.ix + (q & 1), cl.iy + ((q >> 1) & 1), cl.iz + ((q >> 2) & 1), Nl, dense, g.T);
-                float w = ((q & 1) ? cl.wx : 1.f - cl.wx) * ((q & 2) ? cl.wy : 1.f - cl.wy) *
-                          ((q & 4) ? cl.wz : 1.f - cl.wz);
-                if (row != crow[q]) {
-                    if (crow[q] != 0xffffffffu) {
-                        if (in_sh) {
-                            atomicAdd(dl + 2 * crow[q], cacc[q].x);
-                            atomicAdd(dl + 2 * crow[q] + 1, cacc[q].y);
-                        } else {
-                            atomicAdd(reinterpret_cast<float2*>(dl) + crow[q], cacc[q]);
+                for (int q = 0; q < 8; q++) {
+                    uint32_t row =
+                        grid_row(cl.ix + (q & 1), cl.iy + ((q >> 1) & 1), cl.iz + ((q >> 2) & 1), Nl, dense, g.T);
+                    float w = ((q & 1) ? cl.wx : 1.f - cl.wx) * ((q & 2) ? cl.wy : 1.f - cl.wy) *
+                              ((q & 4) ? cl.wz : 1.f - cl.wz);
+                    if (row != crow[q]) {
+                        if (crow[q] != 0xffffffffu) {
+                            if (in_sh) {
+                                atomicAdd(dl + 2 * crow[q], cacc[q].x);
+                                atomicAdd(dl + 2 * crow[q] + 1, cacc[q].y);
+                            } else {
+                                atomicAdd(reinterpret_cast<float2*>(dl) + crow[q], cacc[q]);
+                            }
                         }
+                        crow[q] = row;
+                        cacc[q] = make_float2(w * gr.x, w * gr.y);
+                    } else {
+                        cacc[q].x += w * gr.x;
+                        cacc[q].y += w * gr.y;
                     }
-                    crow[q] = row;
-                    cacc[q] = make_float2(w * gr.x, w * gr.y);
-                } else {
-                    cacc[q].x += w * gr.x;
-                    cacc[q].y += w * gr.y;
                 }
             }
         }

@@ -251,26 +251,24 @@ __global__ void __launch_bounds__(256) k_grad_check(const float* __restrict__ g,
 // Adam (same constants as k_adam) on g / S for [0, unscale_end) and g beyond
 // (the task log-variances, whose gradient the loss writes unscaled); the whole
 // step is skipped when the check found a non-finite gradient. Bias
-// correction counts the steps taken: t = step - skipped.
+// correction counts the steps taken (its factors are kept in the loss-scale
+// state, updated by k_scale_update).
 __global__ void __launch_bounds__(256) k_adam_scaled(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
                                                      float* __restrict__ v, size_t n, size_t mlp_begin, size_t mlp_end,
-                                                     size_t unscale_end, float lr_grid, float lr_mlp, long step,
+                                                     size_t unscale_end, float lr_grid, float lr_mlp,
                                                      const NifLossScale* __restrict__ ls) {
     const float b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
-    __shared__ float c1s, c2s;
-    const bool skip = ls->overflow != 0;
-    if (threadIdx.x == 0) {
-        const double t = (double)(step - ls->skipped);
-        c1s = (float)(1.0 / (1.0 - pow(0.9, t)));
-        c2s = (float)(1.0 / (1.0 - pow(0.99, t)));
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    if (ls->overflow) {
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) g[i] = 0.f;
+        return;
     }
-    __syncthreads();
+    const float c1 = ls->c1, c2 = ls->c2;
     const float inv = 1.0f / ls->scale;
-    const float c1 = c1s, c2 = c2s;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    // loads first and the gradient cleared last, as in k_adam (clearing it
+    // right after its load serialises each iteration's memory accesses: 7x)
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         float gi = g[i];
-        g[i] = 0.f;
-        if (skip) continue;
         if (i < unscale_end) gi *= inv;
         float mi = b1 * m[i] + (1.f - b1) * gi;
         float vi = b2 * v[i] + (1.f - b2) * gi * gi;
@@ -278,10 +276,17 @@ __global__ void __launch_bounds__(256) k_adam_scaled(float* __restrict__ p, floa
         v[i] = vi;
         float lr = (i >= mlp_begin && i < mlp_end) ? lr_mlp : lr_grid;
         p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+        g[i] = 0.f;
     }
 }
 
 __global__ void k_scale_update(NifLossScale* ls, int dynamic) {
+    if (!ls->overflow) {
+        ls->b1t *= 0.9;
+        ls->b2t *= 0.99;
+        ls->c1 = (float)(1.0 / (1.0 - ls->b1t * 0.9));
+        ls->c2 = (float)(1.0 / (1.0 - ls->b2t * 0.99));
+    }
     if (ls->overflow) {
         ls->overflow = 0;
         ls->skipped++;
@@ -485,7 +490,7 @@ nif_status nif_adam_scaled_run(nif_handle* h, float lr_grid, float lr_mlp, cudaS
     unsigned cap = (unsigned)h->num_sms * 16;
     if (g > cap) g = cap;
     k_adam_scaled<<<g, 256, 0, s>>>(h->d_params, h->d_grad, h->d_m, h->d_v, h->n_params, h->off_layer[0], h->off_s,
-                                    h->off_s, lr_grid, lr_mlp, h->adam_step, h->d_ls);
+                                    h->off_s, lr_grid, lr_mlp, h->d_ls);
     NIF_CK_LAUNCH(h);
     k_scale_update<<<1, 1, 0, s>>>(h->d_ls, h->cfg.precision == NIF_FP16 ? 1 : 0);
     NIF_CK_LAUNCH(h);

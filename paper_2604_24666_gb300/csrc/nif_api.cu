@@ -198,7 +198,8 @@ nif_status nif_refresh_lowp(nif_handle* h, cudaStream_t s) {
 }
 
 nif_status reset_loss_scale(nif_handle* h) {
-    NifLossScale ls{h->cfg.precision == NIF_FP16 ? 32768.0f : 1.0f, 0, 0, 0};
+    NifLossScale ls{h->cfg.precision == NIF_FP16 ? 32768.0f : 1.0f, 0, 0, 0, 1.0, 1.0,
+                    (float)(1.0 / (1.0 - 0.9)), (float)(1.0 / (1.0 - 0.99))};
     NIF_CK(h, cudaMemcpy(h->d_ls, &ls, sizeof(ls), cudaMemcpyHostToDevice));
     return NIF_OK;
 }

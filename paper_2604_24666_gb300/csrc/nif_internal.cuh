@@ -46,7 +46,9 @@ struct NifLossScale {
     float scale;      // S
     int clean;        // consecutive finite steps since the last change of S
     int overflow;     // set by the gradient check of the current step
-    int skipped;      // steps skipped so far (Adam's bias correction counts the others)
+    int skipped;      // steps skipped so far
+    double b1t, b2t;  // beta1^t, beta2^t over the t steps taken
+    float c1, c2;     // Adam's bias corrections for the next step: 1 / (1 - beta^(t+1))
 };
 
 struct nif_handle {
