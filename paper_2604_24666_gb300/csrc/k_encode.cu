@@ -13,6 +13,8 @@
 // One thread owns one (point, term) pair: it evaluates the term's sines once
 // and loops over the L levels, issuing the 8 corner loads of a level
 // back-to-back (float2 = both features of an FP32 row, half2 of an FP16 row).
+#include <algorithm>
+
 #include "nif_internal.cuh"
 
 namespace {
@@ -414,10 +416,43 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_sm(GridInfo g, Coa
 // the exit point of one is the entry point of the next (the same deformed
 // point through the same inverse), so p1(s) and p0(s+1) fall in the same cell
 // at every level; coarse cells also repeat over many segments. Each lane
-// keeps the row and the running sum of its 8 corners and reduces into the
-// table only when a corner's row changes: dense coarse levels into the
-// block's shared-memory copy, the rest into global memory.
+// keeps its current cell and the running weighted sums of its 8 corners and
+// reduces them into the table only when the cell changes: dense coarse levels
+// into the block's shared-memory copy, the rest into global memory, where the
+// two corners of an x-edge whose rows are 2m and 2m+1 (always for an even
+// cell x index on a hashed level: the rows differ in bit 0 only; for an even
+// base row on a dense level) share one 16-byte vector reduction.
 constexpr int kRun = 64;
+
+__device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void flush_cell(float* dl, bool in_sh, int ix, int iy, int iz, int Nl, bool dense,
+                                           uint32_t T, const float2* acc) {
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+        const uint32_t r0 = grid_row(ix, iy + ((q >> 1) & 1), iz + ((q >> 2) & 1), Nl, dense, T);
+        const uint32_t r1 = grid_row(ix + 1, iy + ((q >> 1) & 1), iz + ((q >> 2) & 1), Nl, dense, T);
+        if (in_sh) {
+            atomicAdd(dl + 2 * r0, acc[q].x);
+            atomicAdd(dl + 2 * r0 + 1, acc[q].y);
+            atomicAdd(dl + 2 * r1, acc[q + 1].x);
+            atomicAdd(dl + 2 * r1 + 1, acc[q + 1].y);
+        } else if (r1 == (r0 ^ 1u)) {
+            if (r0 & 1u) red_add_v4(dl + 2 * r1, acc[q + 1].x, acc[q + 1].y, acc[q].x, acc[q].y);
+            else red_add_v4(dl + 2 * r0, acc[q].x, acc[q].y, acc[q + 1].x, acc[q + 1].y);
+        } else {
+            red_add_v2(dl + 2 * r0, acc[q].x, acc[q].y);
+            red_add_v2(dl + 2 * r1, acc[q + 1].x, acc[q + 1].y);
+        }
+    }
+}
 
 __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coarse cs,
                                                                  const nif_linseg* __restrict__ lin,
@@ -448,52 +483,55 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
         const int grp = (int)(task - c * groups);
         const int t = grp * tpw + term_in_warp;           // gamma term in [0, P)
         const bool active = t < g.P;
-        uint32_t crow[8];
+        const int tc = active ? t : 0;
+        int cx = -1, cy = 0, cz = 0;                      // current cell (cx < 0: none)
         float2 cacc[8];
 #pragma unroll
-        for (int q = 0; q < 8; q++) { crow[q] = 0xffffffffu; cacc[q] = make_float2(0.f, 0.f); }
+        for (int q = 0; q < 8; q++) cacc[q] = make_float2(0.f, 0.f);
         const int64_t s_end = (c + 1) * kRun < n ? (c + 1) * kRun : n;
-        for (int64_t s = c * kRun; s < s_end && active; s++) {
+        const int base = term_in_warp * g.L;              // first lane of this term's level group
+        for (int64_t s = c * kRun; s < s_end; s++) {      // warp-uniform trip count (shuffles below)
 #pragma unroll 1
             for (int e = 0; e < 2; e++) {
-                const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
-                float3 u = term_u(clamp01(make_float3(L[0], L[1], L[2])), t);
+                // the term's u is the same for all L levels: lanes base..base+2
+                // evaluate one coordinate each and the group shares them
+                const float* Lp = reinterpret_cast<const float*>(lin + s) + 3 * e;
+                const int cc = l < 3 ? l : 0;
+                const float pc = fminf(fmaxf(Lp[cc], 0.f), 1.f);
+                float uc;
+                if (tc == 0) {
+                    uc = pc;
+                } else {
+                    const float f = (float)(1 << ((tc - 1) >> 1));
+                    float sn, cn;
+                    sincosf(f * pc, &sn, &cn);
+                    uc = (((tc - 1) & 1) ? cn + 1.0f : sn + 1.0f) * 0.5f;
+                }
+                float3 u;
+                u.x = __shfl_sync(0xffffffffu, uc, base);
+                u.y = __shfl_sync(0xffffffffu, uc, base + 1);
+                u.z = __shfl_sync(0xffffffffu, uc, base + 2);
+                if (!active) continue;
                 Cell cl = cell_of(u, Nl);
                 float2 gr = *reinterpret_cast<const float2*>(dfeats + ((s * 2 * g.P + e * g.P + t) * g.L + l) * 2);
+                if (cl.ix != cx || cl.iy != cy || cl.iz != cz) {
+                    if (cx >= 0) flush_cell(dl, in_sh, cx, cy, cz, Nl, dense, g.T, cacc);
+                    cx = cl.ix;
+                    cy = cl.iy;
+                    cz = cl.iz;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) cacc[q] = make_float2(0.f, 0.f);
+                }
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
-                    uint32_t row =
-                        grid_row(cl.ix + (q & 1), cl.iy + ((q >> 1) & 1), cl.iz + ((q >> 2) & 1), Nl, dense, g.T);
                     float w = ((q & 1) ? cl.wx : 1.f - cl.wx) * ((q & 2) ? cl.wy : 1.f - cl.wy) *
                               ((q & 4) ? cl.wz : 1.f - cl.wz);
-                    if (row != crow[q]) {
-                        if (crow[q] != 0xffffffffu) {
-                            if (in_sh) {
-                                atomicAdd(dl + 2 * crow[q], cacc[q].x);
-                                atomicAdd(dl + 2 * crow[q] + 1, cacc[q].y);
-                            } else {
-                                atomicAdd(reinterpret_cast<float2*>(dl) + crow[q], cacc[q]);
-                            }
-                        }
-                        crow[q] = row;
-                        cacc[q] = make_float2(w * gr.x, w * gr.y);
-                    } else {
-                        cacc[q].x += w * gr.x;
-                        cacc[q].y += w * gr.y;
-                    }
+                    cacc[q].x += w * gr.x;
+                    cacc[q].y += w * gr.y;
                 }
             }
         }
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            if (crow[q] == 0xffffffffu) continue;
-            if (in_sh) {
-                atomicAdd(dl + 2 * crow[q], cacc[q].x);
-                atomicAdd(dl + 2 * crow[q] + 1, cacc[q].y);
-            } else {
-                atomicAdd(reinterpret_cast<float2*>(dl) + crow[q], cacc[q]);
-            }
-        }
+        if (cx >= 0) flush_cell(dl, in_sh, cx, cy, cz, Nl, dense, g.T, cacc);
     }
     __syncthreads();
     for (int lv = 0; lv < cs.Lc; lv++) {
@@ -642,7 +680,7 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
     Coarse cs{};
     cs.Lc = 0;
     cs.soff[0] = 0;
-    for (int l = 0; l < h->L; l++) {
+    for (int l = 0; l < std::min(h->L, h->tune.bwd_smem_levels); l++) {
         if (!((h->grid.dense_mask >> l) & 1u)) break;
         int64_t r = (int64_t)h->grid.res[l] + 1;
         int64_t need = r * r * r * 2;
@@ -651,16 +689,19 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
         cs.Lc = l + 1;
     }
     size_t smem = sizeof(float) * (size_t)cs.soff[cs.Lc];
+    if (32 % h->L == 0 && h->L >= 4) {      // a level group holds the 3 lanes that evaluate u
+        NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+        const int per_sm = cs.Lc > 0 ? 1 : 2;
+        k_encode_segments_bwd_rl<<<h->num_sms * per_sm, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats,
+                                                                         dtables);
+        NIF_CK_LAUNCH(h);
+        return NIF_OK;
+    }
     if (cs.Lc > 0) {
-        if (32 % h->L == 0) {
-            NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           200 * 1024));
-            k_encode_segments_bwd_rl<<<h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables);
-        } else {
-            NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           200 * 1024));
-            k_encode_segments_bwd_sm<<<h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables);
-        }
+        NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_sm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+        k_encode_segments_bwd_sm<<<h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables);
         NIF_CK_LAUNCH(h);
         return NIF_OK;
     }
