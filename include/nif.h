@@ -377,6 +377,29 @@ nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses,
                           unsigned long long step_seed, float lr_grid, float lr_mlp,
                           nif_pose* poses_out_host, double* loss_host, void* stream);
 
+/* Pose fitting (the paper names learned deformations as future work): the
+ * gradient of the task loss of Sec. 2.4 with respect to the n_inst
+ * deformation parameters, tables, weights and s held fixed, for the
+ * segments of rays_dev (at most n_segments in ray order; rays for instance i
+ * are rays_dev[inst_offsets_dev[i] .. [i+1])): segments -> linearization ->
+ * labels -> encoding and MLP in cfg.precision -> loss -> MLP input gradient
+ * (FP32, or the tensor-core backward divided by the loss scale) -> the
+ * encoding's dL/dp0, dL/dp1 -> through D^-1 as in nif_pose_gradient.
+ * Writes dposes_dev [n_inst][3] = dL/d(bend, twist, taper) (FP32); adds
+ * nothing to the gradient buffer. loss_host as nif_train_step_rays. */
+nif_status nif_pose_step(nif_handle* h, const nif_pose* poses_host, int n_inst, const nif_ray* rays_dev,
+                         const int* inst_offsets_dev, int n_rays, int64_t n_segments, float* dposes_dev,
+                         double* loss_host, void* stream);
+
+/* Shadow rays for a frame loop (occlusion queries with NIF_SHADOW_ONLY):
+ * for a primary ray that hit, origin o + D d, direction the normalised
+ * light_dir_host, interval [eps, tmax]; for a miss an empty interval
+ * [0, 0] (no segments, reported as no hit). shadow_rays_dev [n] may not
+ * alias rays_dev. */
+nif_status nif_shadow_rays(nif_handle* h, const nif_ray* rays_dev, const nif_hit* hits_dev, int n,
+                           const float* light_dir_host, float eps, float tmax, nif_ray* shadow_rays_dev,
+                           void* stream);
+
 /* Draws the training rays of nif_train_step: rays_dev [n] for stream id
  * `stream_id` of step_seed (uniforms are the top 24 bits of splitmix64 of
  * (step_seed, stream_id, index)). */
@@ -397,7 +420,10 @@ nif_status nif_sample_rays(nif_handle* h, unsigned long long step_seed, int stre
  * `stream` without further host synchronisation. Overflow of the segment
  * capacity is latched in the status word (nif_sync_status). The rays'
  * contents may change between runs; their buffers may not. A plan must be
- * destroyed before its handle. */
+ * destroyed before its handle. Other calls on the handle (queries, training,
+ * further plans) may run between replays on the same stream: while a plan
+ * lives, scratch that must grow is reallocated and the old allocation the
+ * plan's graph uses is kept until the handle's last plan is destroyed. */
 typedef struct nif_query_plan nif_query_plan;
 nif_status nif_query_plan_create(nif_handle* h, int n_inst, const nif_ray* rays_dev,
                                  const int* inst_offsets_dev, int n_rays, nif_hit* hits_dev,

@@ -547,9 +547,12 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
 // Input gradient of the segment encoding with the tables held fixed:
 // dp[s][e][3] += d(sum dfeats * psi)/d p_e of segment s (zero where clamped).
 __global__ void __launch_bounds__(256) k_encode_segments_dp(GridInfo g, const float* __restrict__ tab,
-                                                            const nif_linseg* __restrict__ lin, int64_t n,
+                                                            const nif_linseg* __restrict__ lin,
+                                                            const uint32_t* __restrict__ n_dev, int64_t n_max,
                                                             const float* __restrict__ dfeats,
                                                             float* __restrict__ dp) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
     int per = 2 * g.P;
     for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n * per;
          gid += (int64_t)gridDim.x * blockDim.x) {
@@ -714,15 +717,15 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
     return NIF_OK;
 }
 
-nif_status nif_encode_segments_dp_run(nif_handle* h, const nif_linseg* lin, int64_t n, const float* dfeats, float* dp,
-                                      cudaStream_t s) {
+nif_status nif_encode_segments_dp_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n,
+                                      const float* dfeats, float* dp, cudaStream_t s) {
     NifProf prof_(h, "encode_dp", s);
     if (n <= 0) return NIF_OK;
     NIF_CK(h, cudaMemsetAsync(dp, 0, sizeof(float) * 6 * n, s));
     unsigned g = nif_blocks(n * 2 * h->P, 256);
     unsigned cap = (unsigned)h->num_sms * 16;
     if (g > cap) g = cap;
-    k_encode_segments_dp<<<g, 256, 0, s>>>(h->grid, h->d_params + h->off_tables, lin, n, dfeats, dp);
+    k_encode_segments_dp<<<g, 256, 0, s>>>(h->grid, h->d_params + h->off_tables, lin, n_dev, n, dfeats, dp);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

@@ -331,7 +331,7 @@ nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n
 }
 
 nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
-                                const float* acts, const float* dout, float* dx, cudaStream_t s) {
+                                const float* acts, const float* dout, float* dx, cudaStream_t s, bool want_dw) {
     NifProf prof_(h, "mlp_bwd_fp32", s);
     if (n_max <= 0) return NIF_OK;
     nif_status st = nif_grow(h, h->b_dout, sizeof(float) * (size_t)n_max * h->W * 2);
@@ -350,8 +350,7 @@ nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n
         w.B = in; w.sbk = in_ld; w.sbj = 1;
         w.C = h->d_grad + h->off_layer[l]; w.ldc = nin;
         w.M = nout; w.N = nin; w.K = n_max; w.M_dev = n_dev; w.m_is_k = 1; w.k_chunk = 0;
-        st = gemm<kAtomic>(h, w, s);
-        if (st != NIF_OK) return st;
+        if (want_dw && (st = gemm<kAtomic>(h, w, s)) != NIF_OK) return st;
         // d(in) = g W_l : [n x nin], masked by the ReLU of the layer below
         if (l == 0 && !dx) break;
         GemmArgs d{};

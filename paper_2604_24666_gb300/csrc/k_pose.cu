@@ -20,8 +20,11 @@ __device__ __forceinline__ int find_inst_p(const int* inst_off, int n_inst, int 
 
 __global__ void __launch_bounds__(256) k_pose_grad(const nif_segment* __restrict__ segs,
                                                    const nif_linseg* __restrict__ lin, const float* __restrict__ dp,
-                                                   int64_t n, const int* __restrict__ inst_off, int n_inst,
+                                                   const uint32_t* __restrict__ n_dev, int64_t n_max,
+                                                   const int* __restrict__ inst_off, int n_inst,
                                                    const float4* __restrict__ poses, float* __restrict__ dposes) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         int inst = find_inst_p(inst_off, n_inst, (int)segs[s].ray);
         float4 pose = poses[inst];
@@ -74,14 +77,15 @@ __global__ void __launch_bounds__(256) k_pose_grad(const nif_segment* __restrict
 
 }  // namespace
 
-nif_status nif_pose_grad_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const float* dp, int64_t n,
-                             const int* inst_off, int n_inst, float* dposes, cudaStream_t s) {
+nif_status nif_pose_grad_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const float* dp,
+                             const uint32_t* n_dev, int64_t n, const int* inst_off, int n_inst, float* dposes,
+                             cudaStream_t s) {
     NifProf prof_(h, "pose_grad", s);
     if (n <= 0) return NIF_OK;
     unsigned g = nif_blocks(n, 256);
     unsigned cap = (unsigned)h->num_sms * 8;
     if (g > cap) g = cap;
-    k_pose_grad<<<g, 256, 0, s>>>(segs, lin, dp, n, inst_off, n_inst, h->d_pose, dposes);
+    k_pose_grad<<<g, 256, 0, s>>>(segs, lin, dp, n_dev, n, inst_off, n_inst, h->d_pose, dposes);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

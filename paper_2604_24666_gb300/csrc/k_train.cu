@@ -299,6 +299,38 @@ __global__ void k_scale_update(NifLossScale* ls, int dynamic) {
 }
 
 // ---------------------------------------------------------------------------
+// Frame-loop helpers: shadow rays from primary hits, rescaling of a gradient
+// computed on the loss-scaled path.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_shadow_rays(const nif_ray* __restrict__ rays, const nif_hit* __restrict__ hits,
+                                                     int n, float lx, float ly, float lz, float eps, float tmax,
+                                                     nif_ray* __restrict__ out) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const nif_ray ray = rays[r];
+    const nif_hit hit = hits[r];
+    nif_ray o;
+    o.d[0] = lx; o.d[1] = ly; o.d[2] = lz;
+    if (hit.hit) {
+        o.o[0] = ray.o[0] + hit.D * ray.d[0];
+        o.o[1] = ray.o[1] + hit.D * ray.d[1];
+        o.o[2] = ray.o[2] + hit.D * ray.d[2];
+        o.tmin = eps;
+        o.tmax = tmax;
+    } else {           // nothing to shade: an empty interval
+        o.o[0] = ray.o[0]; o.o[1] = ray.o[1]; o.o[2] = ray.o[2];
+        o.tmin = 0.f;
+        o.tmax = 0.f;
+    }
+    out[r] = o;
+}
+
+__global__ void k_unscale(float* __restrict__ v, int n, const NifLossScale* __restrict__ ls) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] /= ls->scale;
+}
+
+// ---------------------------------------------------------------------------
 // Reconstruction along the segmented ray (Sec. 2.2)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int find_inst_r(const int* inst_off, int n_inst, int r) {
@@ -441,7 +473,7 @@ nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_lins
 }
 
 nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels, const nif_linseg* lin,
-                        const uint32_t* n_dev, int64_t n_max, float* dout, cudaStream_t s) {
+                        const uint32_t* n_dev, int64_t n_max, float* dout, cudaStream_t s, bool want_ds) {
     NifProf prof_(h, "loss", s);
     NIF_CK(h, cudaMemsetAsync(h->d_lossacc, 0, sizeof(double) * 16, s));
     if (n_max > 0) {
@@ -453,7 +485,7 @@ nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels
         NIF_CK_LAUNCH(h);
     }
     k_loss_final<<<1, 32, 0, s>>>(h->d_lossacc, n_dev, n_max, h->d_count, h->d_params + h->off_s, h->cfg.flags,
-                                  h->d_grad + h->off_s, h->d_status);
+                                  want_ds ? h->d_grad + h->off_s : nullptr, h->d_status);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
@@ -470,6 +502,22 @@ nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t
                              lr_grid, lr_mlp, (float)c1, (float)c2);
     NIF_CK_LAUNCH(h);
     h->lowp_dirty = true;
+    return NIF_OK;
+}
+
+nif_status nif_shadow_rays_run(nif_handle* h, const nif_ray* rays, const nif_hit* hits, int n, const float* light,
+                               float eps, float tmax, nif_ray* out, cudaStream_t s) {
+    NifProf prof_(h, "shadow_rays", s);
+    if (n <= 0) return NIF_OK;
+    k_shadow_rays<<<nif_blocks(n, 256), 256, 0, s>>>(rays, hits, n, light[0], light[1], light[2], eps, tmax, out);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_unscale_run(nif_handle* h, float* v, int n, cudaStream_t s) {
+    if (n <= 0) return NIF_OK;
+    k_unscale<<<nif_blocks(n, 256), 256, 0, s>>>(v, n, h->d_ls);
+    NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
 

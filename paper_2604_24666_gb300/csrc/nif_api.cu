@@ -91,11 +91,24 @@ nif_status nif_cuda_fail(nif_handle* h, cudaError_t e, const char* what) {
     return nif_fail(h, e == cudaErrorMemoryAllocation ? NIF_ERR_OOM : NIF_ERR_CUDA, m);
 }
 
+void nif_retire(nif_handle* h, void* p) {
+    if (!p) return;
+    if (h->n_plans > 0) h->graveyard.push_back(p);
+    else cudaFree(p);
+}
+
+void nif_free_retired(nif_handle* h) {
+    if (h->graveyard.empty()) return;
+    cudaDeviceSynchronize();
+    for (void* p : h->graveyard) cudaFree(p);
+    h->graveyard.clear();
+}
+
 nif_status nif_grow(nif_handle* h, nif_handle::Buf& b, size_t bytes) {
     if (bytes <= b.bytes) return NIF_OK;
     if (b.p) {
         NIF_CK(h, cudaDeviceSynchronize());
-        cudaFree(b.p);
+        nif_retire(h, b.p);
         b.p = nullptr;
         b.bytes = 0;
     }
@@ -207,9 +220,9 @@ nif_status reset_loss_scale(nif_handle* h) {
 nif_status nif_ensure_instances(nif_handle* h, int n_inst) {
     if (n_inst <= h->inst_cap) return NIF_OK;
     NIF_CK(h, cudaDeviceSynchronize());
-    cudaFree(h->d_corners);
-    cudaFree(h->d_aabb);
-    cudaFree(h->d_pose);
+    nif_retire(h, h->d_corners);
+    nif_retire(h, h->d_aabb);
+    nif_retire(h, h->d_pose);
     h->d_corners = nullptr;
     h->d_aabb = nullptr;
     h->d_pose = nullptr;
@@ -476,6 +489,8 @@ extern "C" void nif_destroy(nif_handle* h) {
         if (b->p) cudaFree(b->p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
     for (auto e : h->prof_pool) cudaEventDestroy(e);
+    h->n_plans = 0;
+    nif_free_retired(h);
     delete h;
 }
 
@@ -798,8 +813,8 @@ extern "C" nif_status nif_pose_gradient(nif_handle* h, const nif_pose* poses, in
         if ((st = nif_grow(h, h->b_dx, sizeof(float) * 6 * (size_t)std::max<int64_t>(n, 1))) != NIF_OK) return st;
         dp = (float*)h->b_dx.p;
     }
-    if ((st = nif_encode_segments_dp_run(h, lin, n, dfeats, dp, s)) != NIF_OK) return st;
-    return nif_pose_grad_run(h, segs, lin, dp, n, inst_off, n_inst, dposes, s);
+    if ((st = nif_encode_segments_dp_run(h, lin, nullptr, n, dfeats, dp, s)) != NIF_OK) return st;
+    return nif_pose_grad_run(h, segs, lin, dp, nullptr, n, inst_off, n_inst, dposes, s);
 }
 
 extern "C" nif_status nif_encode_segments_backward(nif_handle* h, const nif_linseg* lin, int64_t n,
@@ -1120,6 +1135,83 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
         }
     }
     return NIF_OK;
+}
+
+extern "C" nif_status nif_pose_step(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                    const int* inst_off, int n_rays, int64_t n_segments, float* dposes,
+                                    double* loss_host, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    if (n_segments < 1 || !rays || !dposes) return nif_fail(h, NIF_ERR_ARG, "n_segments / rays / dposes");
+    const int prec = h->cfg.precision;
+    if (prec != NIF_FP32 && (st = check_mixed(h)) != NIF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, n_segments, false, nullptr, s)) != NIF_OK)
+        return st;
+    uint32_t* offs = (uint32_t*)h->b_offsets.p;
+    const uint32_t* n_dev = offs + n_rays + 1;
+    const int64_t n = n_segments, np = pad128(n);
+    const size_t esz = prec == NIF_FP32 ? 4 : 2;
+    if ((st = nif_grow(h, h->b_lin, sizeof(nif_linseg) * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_labels, sizeof(nif_label) * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_feat, esz * (size_t)h->in_dim * np)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_dx, sizeof(float) * (size_t)h->in_dim * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_feat2, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_acts, prec == NIF_FP32 ? sizeof(float) * (size_t)n * h->W * h->H
+                                                      : 2 * (size_t)np * kLd * h->H)) != NIF_OK)
+        return st;
+    if (prec != NIF_FP32 && (st = nif_grow(h, h->b_dys, 2 * (size_t)np * kLd * (h->H + 1))) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_temp, sizeof(float) * 6 * (size_t)n)) != NIF_OK) return st;
+    nif_segment* segs = (nif_segment*)h->b_segs.p;
+    nif_linseg* lin = (nif_linseg*)h->b_lin.p;
+    nif_label* lab = (nif_label*)h->b_labels.p;
+    float* dx = (float*)h->b_dx.p;
+    float* out = (float*)h->b_out.p;
+    float* dout = (float*)h->b_feat2.p;
+    float* dp = (float*)h->b_temp.p;
+    if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, n, lin, s)) != NIF_OK) return st;
+    if ((st = nif_labels_run(h, segs, lin, n_dev, n, lab, s)) != NIF_OK) return st;
+    if (prec == NIF_FP32) {
+        float* feat = (float*)h->b_feat.p;
+        float* acts = (float*)h->b_acts.p;
+        if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s)) != NIF_OK) return st;
+        if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
+        if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, false)) != NIF_OK) return st;
+        if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s, false)) != NIF_OK) return st;
+    } else {
+        uint16_t* acts16 = (uint16_t*)h->b_acts.p;
+        if ((st = nif_encode_segments_run(h, lin, n_dev, n, h->b_feat.p, prec, NIF_FP16, s)) != NIF_OK) return st;
+        if ((st = nif_mlp_fwd_tc_acts_run(h, h->b_feat.p, prec, n_dev, n, out, acts16, np, kLd, s)) != NIF_OK)
+            return st;
+        if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, false)) != NIF_OK) return st;
+        if ((st = nif_mlp_bwd_tc_run(h, dout, acts16, n_dev, n, np, kLd, (uint16_t*)h->b_dys.p, dx, s)) != NIF_OK)
+            return st;
+    }
+    NIF_CK(h, cudaMemsetAsync(dposes, 0, sizeof(float) * 3 * n_inst, s));
+    if ((st = nif_encode_segments_dp_run(h, lin, n_dev, n, dx, dp, s)) != NIF_OK) return st;
+    if ((st = nif_pose_grad_run(h, segs, lin, dp, n_dev, n, inst_off, n_inst, dposes, s)) != NIF_OK) return st;
+    if (prec != NIF_FP32 && (st = nif_unscale_run(h, dposes, 3 * n_inst, s)) != NIF_OK) return st;
+    if (loss_host) {
+        double acc[16];
+        NIF_CK(h, cudaStreamSynchronize(s));
+        NIF_CK(h, cudaMemcpy(acc, h->d_lossacc, sizeof(acc), cudaMemcpyDeviceToHost));
+        loss_host[0] = acc[8];
+        for (int i = 0; i < 5; i++) loss_host[1 + i] = acc[9 + i];
+    }
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_shadow_rays(nif_handle* h, const nif_ray* rays, const nif_hit* hits, int n,
+                                      const float* light_dir_host, float eps, float tmax, nif_ray* shadow_rays,
+                                      void* stream) {
+    if (!h || n < 0 || (n > 0 && (!rays || !hits || !shadow_rays || !light_dir_host))) return NIF_ERR_ARG;
+    const float* L = light_dir_host;
+    float len = std::sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
+    if (!(len > 0.f) || !(tmax > eps)) return nif_fail(h, NIF_ERR_ARG, "light direction / interval");
+    float u[3] = {L[0] / len, L[1] / len, L[2] / len};
+    return nif_shadow_rays_run(h, rays, hits, n, u, eps, tmax, shadow_rays, (cudaStream_t)stream);
 }
 
 extern "C" nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses, unsigned long long step_seed,

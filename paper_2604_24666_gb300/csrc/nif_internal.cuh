@@ -121,6 +121,12 @@ struct nif_handle {
         int bwd_smem_levels = 32;       // encoding backward: at most this many dense coarse levels in shared memory
     } tune;
 
+    // CUDA graphs of live query plans hold the scratch and per-instance
+    // buffers by address: while any plan exists, a buffer that has to grow is
+    // replaced and the old allocation kept here until the last plan is gone
+    int n_plans = 0;
+    std::vector<void*> graveyard;
+
     std::string err;
     int num_sms = 0;
     double seg_per_ray = 0.0;           // measured segments per sampled training ray
@@ -153,6 +159,10 @@ struct NifProf {
 nif_status nif_fail(nif_handle* h, nif_status st, const std::string& msg);
 nif_status nif_cuda_fail(nif_handle* h, cudaError_t e, const char* what);
 nif_status nif_grow(nif_handle* h, nif_handle::Buf& b, size_t bytes);
+// frees `p` now, or keeps it until the last query plan of the handle is destroyed
+void nif_retire(nif_handle* h, void* p);
+// frees the retired buffers (no plan may be alive)
+void nif_free_retired(nif_handle* h);
 nif_status nif_ensure_instances(nif_handle* h, int n_inst);
 nif_status nif_upload_poses(nif_handle* h, const nif_pose* poses, int n_inst, cudaStream_t s);
 nif_status nif_refresh_lowp(nif_handle* h, cudaStream_t s);
@@ -207,14 +217,17 @@ nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n,
 nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev,
                                        int64_t n_max, const float* dfeats, float* dtables,
                                        cudaStream_t s);
-nif_status nif_encode_segments_dp_run(nif_handle* h, const nif_linseg* lin, int64_t n, const float* dfeats,
-                                      float* dp, cudaStream_t s);
+nif_status nif_encode_segments_dp_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n,
+                                      const float* dfeats, float* dp, cudaStream_t s);
 nif_status nif_pose_grad_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const float* dp,
-                             int64_t n, const int* inst_off, int n_inst, float* dposes, cudaStream_t s);
+                             const uint32_t* n_dev, int64_t n, const int* inst_off, int n_inst, float* dposes,
+                             cudaStream_t s);
 nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
                                 float* out, float* acts, cudaStream_t s);
+// want_dw: add dL/dW into the gradient buffer (off for an input gradient only)
 nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
-                                const float* acts, const float* dout, float* dx, cudaStream_t s);
+                                const float* acts, const float* dout, float* dx, cudaStream_t s,
+                                bool want_dw = true);
 nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev,
                               int64_t n_max, float* out, cudaStream_t s);
 // acts_out (nullable): 16-bit hidden activations, layer l row r at (l * acts_rows + r) * acts_ld
@@ -228,13 +241,18 @@ nif_status nif_mlp_bwd_tc_run(nif_handle* h, const float* dout, const uint16_t* 
 nif_status nif_mlp_dw_tc_run(nif_handle* h, const void* x16, const uint16_t* acts, const uint16_t* dys,
                              const uint32_t* n_dev, int64_t n_max, int64_t n_pad, int ld, cudaStream_t s);
 nif_status nif_grad_check_run(nif_handle* h, cudaStream_t s);
+nif_status nif_shadow_rays_run(nif_handle* h, const nif_ray* rays, const nif_hit* hits, int n, const float* light,
+                               float eps, float tmax, nif_ray* out, cudaStream_t s);
+// v[0..n) /= the loss scale (device)
+nif_status nif_unscale_run(nif_handle* h, float* v, int n, cudaStream_t s);
 nif_status nif_adam_scaled_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s);
 nif_status nif_labels_count_hits(nif_handle* h, const nif_label* labels, int64_t n, cudaStream_t s);
 nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin,
                           const uint32_t* n_dev, int64_t n_max, nif_label* labels, cudaStream_t s);
+// want_ds: add dL/ds into the gradient buffer (off for a gradient with respect to the poses only)
 nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels,
                         const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max, float* dout,
-                        cudaStream_t s);
+                        cudaStream_t s, bool want_ds = true);
 nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s);
 nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
                                int n_rays, const uint32_t* offsets, const nif_segment* segs,

@@ -32,6 +32,7 @@ struct nif_query_plan {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t done = nullptr;
     bool launched = false;
+    bool counted = false;        // holds a place in the handle's live-plan count
 };
 
 namespace {
@@ -240,6 +241,8 @@ extern "C" nif_status nif_query_plan_create(nif_handle* h, int n_inst, const nif
     p->graph = g;
     e = cudaGraphInstantiate(&p->exec, g, 0);
     if (e != cudaSuccess) return fail(nif_cuda_fail(h, e, "cudaGraphInstantiate"));
+    p->counted = true;
+    h->n_plans++;
     *out = p;
     return NIF_OK;
 }
@@ -277,6 +280,7 @@ extern "C" void nif_query_plan_destroy(nif_query_plan* p) {
     if (!p) return;
     if (p->cap_stream) cudaStreamSynchronize(p->cap_stream);
     if (p->done && p->launched) cudaEventSynchronize(p->done);
+    if (p->counted && --p->h->n_plans == 0) nif_free_retired(p->h);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->chunk_counts) cudaFree(p->chunk_counts);

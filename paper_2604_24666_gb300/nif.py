@@ -99,6 +99,9 @@ def lib() -> ctypes.CDLL:
             "nif_loss_scale": ([_vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "nif_set_loss_scale": ([_vp, ctypes.c_float], ctypes.c_int),
             "nif_adam_step_scaled": ([_vp, ctypes.c_float, ctypes.c_float, _vp], ctypes.c_int),
+            "nif_pose_step": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _i64, _vp, _vp, _vp], ctypes.c_int),
+            "nif_shadow_rays": ([_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp],
+                                ctypes.c_int),
             "nif_labels": ([_vp, _vp, _vp, _i64, _vp, _vp], ctypes.c_int),
             "nif_loss": ([_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
             "nif_reconstruct": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
@@ -358,6 +361,29 @@ def nif_set_loss_scale(h, scale):
 
 def nif_adam_step_scaled(h, lr_grid, lr_mlp, stream=None):
     _check(h, lib().nif_adam_step_scaled(h, lr_grid, lr_mlp, _stream(stream)))
+
+
+def nif_pose_step(h, poses, rays, n_segments, inst_offsets=None, want_loss=False, dposes=None, stream=None):
+    """dL/d(bend, twist, taper) [n_inst, 3] of the task loss on the segments of `rays`
+    (tables, weights and s fixed); returns (dposes, loss parts or None)."""
+    p, n_inst = _poses(poses)
+    if dposes is None:
+        dposes = torch.zeros((n_inst, 3), dtype=torch.float32, device=rays.device)
+    parts = np.zeros(6, np.float64) if want_loss else None
+    _check(h, lib().nif_pose_step(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0], int(n_segments),
+                                  _ptr(dposes), _ptr(parts), _stream(stream)))
+    return dposes, parts
+
+
+def nif_shadow_rays(h, rays, hits, light_dir, eps=1e-4, tmax=4.0, out=None, stream=None):
+    """Shadow rays [n, 8] from primary rays and their hits toward a directional light."""
+    if out is None:
+        out = torch.empty_like(rays)
+    L = (ctypes.c_float * 3)(*[float(v) for v in light_dir])
+    _check(h, lib().nif_shadow_rays(h, _ptr(rays), _ptr(hits), rays.shape[0], ctypes.cast(L, ctypes.c_void_p),
+                                    float(eps), float(tmax),
+                                    _ptr(out), _stream(stream)))
+    return out
 
 
 def nif_labels(h, segs, lin, stream=None):
