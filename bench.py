@@ -306,6 +306,7 @@ def run_ours(args):
     query = run_query(args, nif, S, dev, rank) if not args.no_query else None
     batch = run_batch(args, nif, S, dev, rank) if not args.no_batch else None
     precision = run_precision(args, nif, S, dev) if (not args.no_precision and rank == 0) else None
+    frame = run_frame(args, nif, S, dev) if (not args.no_frame and rank == 0) else None
 
     if rank != 0:
         return 0
@@ -330,7 +331,7 @@ def run_ours(args):
                        "l2": "working set larger than L2 (tables, gradients, Adam state 256 MB; features 604 MB)"},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "loss": list(loss) if loss is not None else None, "train_mixed": mixed,
-            "query": query, "batch": batch,
+            "query": query, "batch": batch, "frame_loop": frame,
             "precision": precision}
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -443,6 +444,7 @@ def run_query(args, nif, S, dev, rank):
 
 
 BATCH_WORKLOAD = "torus16x64_batch"
+FRAME_WORKLOAD = "ellipsoids256_frame"
 
 
 def run_batch(args, nif, S, dev, rank):
@@ -481,6 +483,102 @@ def run_batch(args, nif, S, dev, rank):
            "autotune_s": tune_s,
            "hit_rate": float((hits[:, 7].view(torch.int32) & 0xff).ne(0).float().mean().item())}
     plan.close()
+    h.close()
+    return res
+
+
+def run_frame(args, nif, S, dev):
+    """Animated frame loop: 16 deforming ellipsoid-union instances at 256^3
+    (T = 2^21, MLP 4 x 64, BF16 mixed precision) on a 4 x 4 screen grid.
+    Per frame: new sinusoidal poses, 1920x1080 primary rays (one CUDA-graph
+    query plan), shadow rays toward a directional light from the primary hits
+    and an occlusion-only query plan, and one pose-fitting gradient step of
+    all 16 pose estimates on every 32nd primary ray (the task-loss gradient
+    w.r.t. the deformation parameters). Before the loop the network trains
+    for a few steps of 2^18 segments (timed as train samples/s)."""
+    import torch
+    w = S.WORKLOADS[FRAME_WORKLOAD]
+    net = w["net"]
+    t_setup = time.perf_counter()
+    mesh = S.make_mesh(w["shape"])
+    h = nif.Nif(net, mesh, precision=nif.NIF_BF16, seed=51, flags=nif.NIF_FLAG_MIXED_TRAINING)
+    setup_s = time.perf_counter() - t_setup
+    n_inst, frames = w["n_inst"], args.frames
+    stream = torch.cuda.current_stream()
+    # ---- pre-training (mixed BF16, 2^18 segments, 16 poses) ----
+    for i in range(2):
+        nif.nif_train_step(h.h, N_SEG, N_POSES, 9000 + i, lr_grid=1e-2, lr_mlp=5e-3, want_loss=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.frame_pretrain):
+        nif.nif_train_step(h.h, N_SEG, N_POSES, 9100 + i, lr_grid=1e-2, lr_mlp=5e-3, want_loss=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1) / max(args.frame_pretrain, 1)
+    loss, _ = nif.nif_train_step(h.h, N_SEG, N_POSES, 9999, lr_grid=1e-2, lr_mlp=5e-3, want_loss=True)
+    # ---- frame inputs ----
+    rays_np, offs_np = S.camera_rays(w["width"], w["height"], grid=4)
+    n = len(rays_np)
+    prim = torch.from_numpy(rays_np).to(dev)
+    it = torch.from_numpy(offs_np).to(dev)
+    prim_hits = torch.zeros((n, 8), dtype=torch.float32, device=dev)
+    shadow = torch.zeros_like(prim)
+    shadow_hits = torch.zeros((n, 8), dtype=torch.float32, device=dev)
+    per = n // n_inst
+    fit_idx = np.concatenate([np.arange(i * per, (i + 1) * per, 32) for i in range(n_inst)])
+    fit_rays = prim[torch.from_numpy(fit_idx).to(dev)].contiguous()
+    fit_off = torch.from_numpy((np.arange(n_inst + 1) * (len(fit_idx) // n_inst)).astype(np.int32)).to(dev)
+    poses = S.animated_poses(n_inst, max(frames, 1) + args.warmup, seed=1301)
+    light = (0.4, 0.3, 0.87)
+    t0 = time.perf_counter()
+    plan_p = nif.QueryPlan(h.h, poses[0], prim, prim_hits, inst_offsets=it, autotune=True)
+    nif.nif_shadow_rays(h.h, prim, prim_hits, light, eps=1e-3, tmax=4.0, out=shadow)
+    plan_s = nif.QueryPlan(h.h, poses[0], shadow, shadow_hits, inst_offsets=it, flags=nif.NIF_SHADOW_ONLY,
+                           autotune=False)
+    plan_s_ms = (time.perf_counter() - t0) * 1e3
+    lim = np.array([1.0, 4.0, 1.0], np.float32)          # |bend|, |twist|, |taper| bounds of the deformation
+    est = np.clip(0.8 * poses[0] + 0.1, -lim, lim)       # pose estimates start off the animation
+    dposes = torch.zeros((n_inst, 3), dtype=torch.float32, device=dev)
+    fit_seg = 1 << 17
+
+    def frame(f):
+        nonlocal est
+        plan_p.run(poses[f])
+        nif.nif_shadow_rays(h.h, prim, prim_hits, light, eps=1e-3, tmax=4.0, out=shadow)
+        plan_s.run(poses[f])
+        nif.nif_pose_step(h.h, est, fit_rays, fit_seg, inst_offsets=fit_off, dposes=dposes)
+        est = np.clip(est - 0.05 * dposes.cpu().numpy(), -lim, lim)     # host update of the 48 estimates
+
+    for f in range(args.warmup):
+        frame(f)
+    torch.cuda.synchronize()
+    nif.nif_profile(h.h, 1)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for f in range(frames):
+        frame(args.warmup + f)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms = f0.elapsed_time(f1)
+    prof = nif.nif_profile_read(h.h)
+    nif.nif_profile(h.h, 0)
+    nif.nif_sync_status(h.h)
+    hit_rate = float((prim_hits[:, 7].view(torch.int32) & 0xff).ne(0).float().mean().item())
+    shadow_rate = float((shadow_hits[:, 7].view(torch.int32) & 0xff).ne(0).float().mean().item())
+    res = {"workload": FRAME_WORKLOAD, "instances": n_inst, "resolution": [w["width"], w["height"]],
+           "frames": frames, "precision": "bf16", "frames_per_s": frames / (ms / 1e3), "ms_per_frame": ms / frames,
+           "queries_per_s": frames * 2 * n / (ms / 1e3), "rays_per_frame": 2 * n,
+           "pose_fit_rays_per_frame": int(len(fit_idx)), "primary_hit_rate": hit_rate,
+           "shadowed_fraction": shadow_rate,
+           "stages_ms_per_frame": {k: v[0] / max(frames, 1) for k, v in
+                                   sorted(prof.items(), key=lambda kv: -kv[1][0])},
+           "pretrain": {"steps": args.frame_pretrain, "segments_per_step": N_SEG, "ms_per_step": train_ms,
+                        "train_samples_per_s": N_SEG / (train_ms / 1e3), "loss": list(loss)},
+           "setup_s": setup_s, "plans_ms": plan_s_ms,
+           "note": "pre-training is shortened from 20k steps; query and fitting cost do not depend on it"}
+    plan_s.close()
+    plan_p.close()
     h.close()
     return res
 
@@ -555,6 +653,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance query measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-output precision study")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision training measurement")
+    ap.add_argument("--no-frame", action="store_true", help="skip the animated frame loop")
+    ap.add_argument("--frames", type=int, default=120, help="frames of the animated frame loop")
+    ap.add_argument("--frame-pretrain", type=int, default=1500, help="training steps before the frame loop")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -180,6 +180,45 @@ def sphere_rays(n: int, seed: int = SEED_RAYS, radius: float = 2.0,
     return out
 
 
+def camera_rays(width: int = 1920, height: int = 1080, grid: int = 4, eye=(0.5, -0.65, 0.95),
+                target=CENTER, vfov_deg: float = 48.0) -> tuple:
+    """Primary rays of one frame of a grid x grid world of instances seen by
+    one camera: the image is cut into grid x grid tiles and tile k shows
+    instance k, whose rays are given in the instance's own frame (the rest
+    cube [0,1]^3) from a pinhole at `eye` looking at `target` (z up).
+    Returns (rays [width*height, 8] float32 grouped by instance, offsets
+    [grid*grid + 1] int32)."""
+    tw, th = width // grid, height // grid
+    eye = np.asarray(eye, np.float64)
+    fwd = np.asarray(target, np.float64) - eye
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, [0.0, 0.0, 1.0])
+    right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    t = np.tan(np.radians(vfov_deg) / 2)
+    ys, xs = np.meshgrid((np.arange(th) + 0.5) / th, (np.arange(tw) + 0.5) / tw, indexing="ij")
+    sx = (2 * xs - 1) * t * tw / th
+    sy = (1 - 2 * ys) * t
+    d = fwd + sx[..., None] * right + sy[..., None] * up
+    d = (d / np.linalg.norm(d, axis=-1, keepdims=True)).reshape(-1, 3)
+    tile = np.zeros((tw * th, 8), np.float32)
+    tile[:, 0:3] = eye
+    tile[:, 3:6] = d
+    tile[:, 7] = 1e30
+    n_inst = grid * grid
+    rays = np.concatenate([tile] * n_inst)
+    offs = (np.arange(n_inst + 1) * tw * th).astype(np.int32)
+    return rays, offs
+
+
+def animated_poses(n_inst: int, n_frames: int = 120, amplitude: float = 1.0, seed: int = SEED_POSES):
+    """Poses [n_frames, n_inst, 3]: parameter j of instance i at frame f is
+    amplitude * sin(2 pi f / n_frames + phi_ij), phases seeded U[0, 2 pi)."""
+    phi = np.random.default_rng(seed).uniform(0, 2 * np.pi, (n_inst, 3))
+    f = np.arange(n_frames)[:, None, None]
+    return (amplitude * np.sin(2 * np.pi * f / n_frames + phi[None])).astype(np.float32)
+
+
 def poses(n: int, seed: int = SEED_POSES, kind: str = "all") -> np.ndarray:
     """Deformation parameters [n, 3] float32 = (bend, twist, taper).
 
@@ -302,6 +341,10 @@ WORKLOADS = {
     # batching: 64 torus instances at 16^3, Zipf ray counts, L=16, T=2^19, 3x64
     "torus16x64_batch": dict(shape="torus", net=NetConfig(16, 4, 16, 2, 19, 4, 1.5, 3, 64, 4),
                              n_inst=64, pose_kind="all"),
+    # animated frame loop: 16 ellipsoid-union instances at 256^3, T=2^21, MLP 4x64, BF16;
+    # 1920x1080 primary + shadow rays per frame, 120 frames, pose fitting in the loop
+    "ellipsoids256_frame": dict(shape="ellipsoids", net=NetConfig(256, 4, 16, 2, 21, 4, 1.5, 4, 64, 4),
+                                n_inst=16, width=1920, height=1080, frames=120),
 }
 
 
