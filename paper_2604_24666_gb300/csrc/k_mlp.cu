@@ -264,6 +264,178 @@ __global__ void __launch_bounds__(256) k_sgemm_big(GemmArgs a) {
     }
 }
 
+// Register-tiled SGEMM, 8 x 8 outputs per thread: BM x 64 block tile
+// ((BM/8) x 8 threads), 16-deep K slices double-buffered in shared memory
+// (k-major), the next slice held in registers while the current one is
+// multiplied. Per k a thread reads two float4 of A and two of B and issues 64
+// FMAs, so shared-memory traffic stays well below the FMA rate. Serves
+// N % 64 == 0 with A contiguous along k or i and B along j or k.
+template <int EPI, int BMR>
+__global__ void __launch_bounds__(BMR) k_sgemm_rt(GemmArgs a) {
+    constexpr int BNR = 64, BKR = 16, T8 = 8, NT = BMR;          // (BMR/8) x (64/8) threads
+    constexpr int A4 = BMR * BKR / 4 / NT, B4 = BKR * BNR / 4 / NT;  // float4 per thread per slice
+    __shared__ __align__(16) float sA[2][BKR][BMR + 4];
+    __shared__ __align__(16) float sB[2][BKR][BNR + 4];
+    int64_t M = a.M, K = a.K;
+    if (a.M_dev) {
+        int64_t m = (int64_t)*a.M_dev;
+        if (a.m_is_k) K = m < K ? m : K;
+        else M = m < M ? m : M;
+    }
+    const int64_t i0 = (int64_t)blockIdx.y * BMR;
+    const int j0 = blockIdx.x * BNR;
+    if (i0 >= M) return;
+    int64_t kb = 0, ke = K;
+    if (EPI == kAtomic) {
+        kb = (int64_t)blockIdx.z * a.k_chunk;
+        ke = kb + a.k_chunk < K ? kb + a.k_chunk : K;
+        if (kb >= ke) return;
+    }
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    const bool a_krow = a.sak == 1;
+    const bool b_jrow = a.sbj == 1;
+    float4 ra[A4], rb[B4];
+    auto load_slice = [&](int64_t k0) {
+#pragma unroll
+        for (int q = 0; q < A4; q++) {
+            const int idx = tid + q * NT;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a_krow) {
+                const int row = idx / (BKR / 4), k4 = (idx % (BKR / 4)) * 4;
+                const int64_t gi = i0 + row, gk = k0 + k4;
+                const float* src = a.A + gi * a.sai + gk;
+                if (gi < M) {
+                    if (gk + 3 < ke) v = *reinterpret_cast<const float4*>(src);
+                    else {
+                        if (gk + 0 < ke) v.x = src[0];
+                        if (gk + 1 < ke) v.y = src[1];
+                        if (gk + 2 < ke) v.z = src[2];
+                    }
+                }
+            } else {
+                const int k = idx / (BMR / 4), i4 = (idx % (BMR / 4)) * 4;
+                const int64_t gi = i0 + i4, gk = k0 + k;
+                const float* src = a.A + gi + gk * a.sak;
+                if (gk < ke) {
+                    if (gi + 3 < M) v = *reinterpret_cast<const float4*>(src);
+                    else {
+                        if (gi + 0 < M) v.x = src[0];
+                        if (gi + 1 < M) v.y = src[1];
+                        if (gi + 2 < M) v.z = src[2];
+                    }
+                }
+            }
+            ra[q] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < B4; q++) {
+            const int idx = tid + q * NT;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (b_jrow) {
+                const int k = idx / (BNR / 4), j4 = (idx % (BNR / 4)) * 4;
+                const int64_t gk = k0 + k;
+                if (gk < ke) v = *reinterpret_cast<const float4*>(a.B + gk * a.sbk + (j0 + j4));
+            } else {
+                const int j = idx / (BKR / 4), k4 = (idx % (BKR / 4)) * 4;
+                const int64_t gk = k0 + k4;
+                const float* src = a.B + (int64_t)(j0 + j) * a.sbj + gk;
+                if (gk + 3 < ke) v = *reinterpret_cast<const float4*>(src);
+                else {
+                    if (gk + 0 < ke) v.x = src[0];
+                    if (gk + 1 < ke) v.y = src[1];
+                    if (gk + 2 < ke) v.z = src[2];
+                }
+            }
+            rb[q] = v;
+        }
+    };
+    auto store_slice = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < A4; q++) {
+            const int idx = tid + q * NT;
+            if (a_krow) {
+                const int row = idx / (BKR / 4), k4 = (idx % (BKR / 4)) * 4;
+                sA[buf][k4 + 0][row] = ra[q].x;
+                sA[buf][k4 + 1][row] = ra[q].y;
+                sA[buf][k4 + 2][row] = ra[q].z;
+                sA[buf][k4 + 3][row] = ra[q].w;
+            } else {
+                const int k = idx / (BMR / 4), i4 = (idx % (BMR / 4)) * 4;
+                *reinterpret_cast<float4*>(&sA[buf][k][i4]) = ra[q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < B4; q++) {
+            const int idx = tid + q * NT;
+            if (b_jrow) {
+                const int k = idx / (BNR / 4), j4 = (idx % (BNR / 4)) * 4;
+                *reinterpret_cast<float4*>(&sB[buf][k][j4]) = rb[q];
+            } else {
+                const int j = idx / (BKR / 4), k4 = (idx % (BKR / 4)) * 4;
+                sB[buf][k4 + 0][j] = rb[q].x;
+                sB[buf][k4 + 1][j] = rb[q].y;
+                sB[buf][k4 + 2][j] = rb[q].z;
+                sB[buf][k4 + 3][j] = rb[q].w;
+            }
+        }
+    };
+    float acc[T8][T8];
+#pragma unroll
+    for (int r = 0; r < T8; r++)
+#pragma unroll
+        for (int c = 0; c < T8; c++) acc[r][c] = 0.f;
+    load_slice(kb);
+    store_slice(0);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t k0 = kb; k0 < ke; k0 += BKR) {
+        const bool more = k0 + BKR < ke;
+        if (more) load_slice(k0 + BKR);
+#pragma unroll
+        for (int kk = 0; kk < BKR; kk++) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&sA[buf][kk][ty * T8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&sA[buf][kk][ty * T8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&sB[buf][kk][tx * T8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&sB[buf][kk][tx * T8 + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int r = 0; r < T8; r++)
+#pragma unroll
+                for (int c = 0; c < T8; c++) acc[r][c] += av[r] * bv[c];
+        }
+        if (more) {
+            store_slice(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < T8; r++) {
+        const int64_t gi = i0 + ty * T8 + r;
+        if (gi >= M) continue;
+        const int gj = j0 + tx * T8;
+        float* dst = a.C + gi * a.ldc + gj;
+        if (EPI == kAtomic) {
+#pragma unroll
+            for (int c = 0; c < T8; c++) atomicAdd(dst + c, acc[r][c]);
+        } else {
+#pragma unroll
+        for (int h4 = 0; h4 < 2; h4++) {
+            float4 v = make_float4(acc[r][4 * h4], acc[r][4 * h4 + 1], acc[r][4 * h4 + 2], acc[r][4 * h4 + 3]);
+            if (EPI == kRelu) {
+                v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f); v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f);
+            } else if (EPI == kMask) {
+                float4 m = *reinterpret_cast<const float4*>(a.mask + gi * a.ldc + gj + 4 * h4);
+                v.x = m.x > 0.f ? v.x : 0.f; v.y = m.y > 0.f ? v.y : 0.f;
+                v.z = m.z > 0.f ? v.z : 0.f; v.w = m.w > 0.f ? v.w : 0.f;
+            }
+            *reinterpret_cast<float4*>(dst + 4 * h4) = v;
+        }
+        }
+    }
+}
+
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 template <int EPI>
@@ -276,16 +448,28 @@ nif_status gemm(nif_handle* h, GemmArgs a, cudaStream_t s, int splits = 1) {
     // 128-row tiles for long reductions over many rows, 64-row tiles otherwise (more resident blocks)
     const bool tall = big && a.M >= 96 && !a.m_is_k && a.K > 64;
     const int bm = big ? (tall ? 128 : 64) : BM;
-    if (EPI == kAtomic) {
-        // split the row reduction so that the grid covers the GPU about four times
-        int64_t tiles = (int64_t)((a.N + 63) / 64) * ((a.M + bm - 1) / bm);
-        int64_t want = std::max<int64_t>(1, (4 * (int64_t)h->num_sms + tiles - 1) / tiles);
+    const int64_t tiles = (int64_t)((a.N + 63) / 64) * ((a.M + bm - 1) / bm);
+    auto split_rows = [&](int64_t waves_sms) {
+        int64_t want = std::max<int64_t>(1, (waves_sms + tiles - 1) / tiles);
         int64_t chunk = (a.K + want - 1) / want;
-        chunk = std::max<int64_t>(256, (chunk + 15) / 16 * 16);
-        a.k_chunk = chunk;
-        splits = (int)((a.K + chunk - 1) / chunk);
+        return std::max<int64_t>(256, (chunk + 15) / 16 * 16);
+    };
+    // split the row reduction so that the grid covers the GPU about four times
+    if (EPI == kAtomic) a.k_chunk = split_rows(4 * (int64_t)h->num_sms);
+    // the 8x8-per-thread kernel pays off when each block reduces over >= 512
+    // (it holds fewer warps per SM; short reductions are prologue-bound)
+    const bool rt = big && (EPI == kAtomic ? a.k_chunk : a.K) >= 512;
+    if (EPI == kAtomic) {
+        if (rt) a.k_chunk = std::max<int64_t>(512, split_rows(8 * (int64_t)h->num_sms));
+        splits = (int)((a.K + a.k_chunk - 1) / a.k_chunk);
     }
-    if (big && tall) {
+    if (rt && tall) {
+        dim3 grid(a.N / 64, (unsigned)((a.M + 127) / 128), splits);
+        k_sgemm_rt<EPI, 128><<<grid, 128, 0, s>>>(a);
+    } else if (rt) {
+        dim3 grid(a.N / 64, (unsigned)((a.M + 63) / 64), splits);
+        k_sgemm_rt<EPI, 64><<<grid, 64, 0, s>>>(a);
+    } else if (big && tall) {
         dim3 grid(a.N / 64, (unsigned)((a.M + 127) / 128), splits);
         k_sgemm_big<EPI, 128><<<grid, 256, 0, s>>>(a);
     } else if (big) {
