@@ -358,11 +358,15 @@ nif_status nif_query(nif_handle* h, const nif_pose* poses_host, int n_inst,
                      const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
                      nif_hit* hits_dev, unsigned flags, void* stream);
 
-/* One training step (FP32) on caller-given rays: segments of the rays are
- * generated and the first n_segments (in ray order) are labelled, encoded,
- * passed through the MLP, the losses are back-propagated into tables,
- * weights and s, and Adam updates them. loss_host (nullable) receives
- * [total, L_dist, L_normal, L_albedo, L_material, L_occ] and blocks. */
+/* One training step on caller-given rays (FP32, or the mixed-precision path
+ * of NIF_FLAG_MIXED_TRAINING): segments of the rays are generated and the
+ * batch is the segments of the leading whole rays, in ray order, at most
+ * n_segments (a ray whose segments would cross n_segments is left out, so
+ * the batch is a deterministic function of the rays and poses). They are
+ * labelled, encoded, passed through the MLP, the losses are back-propagated
+ * into tables, weights and s, and Adam updates them. loss_host (nullable)
+ * receives [total, L_dist, L_normal, L_albedo, L_material, L_occ] and
+ * blocks. */
 nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses_host, int n_inst,
                                const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
                                int64_t n_segments, float lr_grid, float lr_mlp, double* loss_host,
@@ -380,7 +384,7 @@ nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses,
 /* Pose fitting (the paper names learned deformations as future work): the
  * gradient of the task loss of Sec. 2.4 with respect to the n_inst
  * deformation parameters, tables, weights and s held fixed, for the
- * segments of rays_dev (at most n_segments in ray order; rays for instance i
+ * segments of rays_dev (the batch rule of nif_train_step_rays; rays for instance i
  * are rays_dev[inst_offsets_dev[i] .. [i+1])): segments -> linearization ->
  * labels -> encoding and MLP in cfg.precision -> loss -> MLP input gradient
  * (FP32, or the tensor-core backward divided by the loss scale) -> the

@@ -206,7 +206,9 @@ __global__ void __launch_bounds__(kTravWarps * 32) k_seg_traverse(
     const nif_ray* __restrict__ rays, const int* __restrict__ inst_off, int n_inst, int n_rays,
     TreeView tree, const float* __restrict__ corners, const float4* __restrict__ aabb,
     uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets, nif_segment* __restrict__ segs,
-    int64_t cap, uint32_t* __restrict__ temp_cursor, int* status) {
+    int64_t cap, uint32_t* __restrict__ temp_cursor, int64_t emit_skip_le, int* status) {
+    // emit as the fallback of a temp pass: nothing to do unless the temp overflowed
+    if (MODE == kModeEmit && temp_cursor && (int64_t)*temp_cursor <= emit_skip_le) return;
     __shared__ RayPre s_ray[kTravWarps][32];
     __shared__ uint32_t s_q[kTravWarps][64];
     __shared__ uint32_t s_cnt[kTravWarps][32];
@@ -437,11 +439,20 @@ __global__ void __launch_bounds__(kScanT) k_scan_add(uint32_t* __restrict__ out,
 }
 
 __global__ void k_clamp_count(const uint32_t* offsets, int n_rays, int64_t cap, uint32_t* n_out,
-                              int* status, int latch) {
+                              int* status, int latch, int whole_rays) {
     uint32_t tot = offsets[n_rays];
     if ((int64_t)tot > cap) {
         if (latch) nif_set_status(status, NIF_ERR_CAPACITY);
-        tot = (uint32_t)cap;
+        if (whole_rays) {          // the longest prefix of complete rows: largest offsets[r] <= cap
+            int lo = 0, hi = n_rays;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if ((int64_t)offsets[mid] <= cap) lo = mid; else hi = mid - 1;
+            }
+            tot = offsets[lo];
+        } else {
+            tot = (uint32_t)cap;
+        }
     }
     *n_out = tot;
 }
@@ -502,23 +513,23 @@ static TreeView tree_view(nif_handle* h);
 template <int MODE>
 static void launch_traverse(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
                             uint32_t* counts, const uint32_t* offsets, nif_segment* segs, int64_t cap,
-                            uint32_t* cursor, cudaStream_t s) {
+                            uint32_t* cursor, cudaStream_t s, int64_t emit_skip_le = 0) {
     TreeView tv = tree_view(h);
     switch (h->tune.trav_warps) {
         case 2:
             k_seg_traverse<MODE, 2><<<nif_blocks(n_rays, 64), 64, 0, s>>>(rays, inst_off, n_inst, n_rays, tv, h->d_corners,
                                                                        h->d_aabb, counts, offsets, segs, cap, cursor,
-                                                                       h->d_status);
+                                                                       emit_skip_le, h->d_status);
             break;
         case 8:
             k_seg_traverse<MODE, 8><<<nif_blocks(n_rays, 256), 256, 0, s>>>(rays, inst_off, n_inst, n_rays, tv,
                                                                          h->d_corners, h->d_aabb, counts, offsets, segs,
-                                                                         cap, cursor, h->d_status);
+                                                                         cap, cursor, emit_skip_le, h->d_status);
             break;
         default:
             k_seg_traverse<MODE, 4><<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, tv,
                                                                          h->d_corners, h->d_aabb, counts, offsets, segs,
-                                                                         cap, cursor, h->d_status);
+                                                                         cap, cursor, emit_skip_le, h->d_status);
     }
 }
 
@@ -551,6 +562,17 @@ nif_status nif_seg_emit_run(nif_handle* h, const nif_ray* rays, const int* inst_
     NifProf prof_(h, "seg_emit", s);
     if (n_rays <= 0 || h->n_leaves == 0) return NIF_OK;
     launch_traverse<kModeEmit>(h, rays, inst_off, n_inst, n_rays, nullptr, offsets, segs, cap, nullptr, s);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_seg_emit_if_overflow_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                                        const uint32_t* offsets, nif_segment* segs, int64_t cap,
+                                        uint32_t* temp_cursor, int64_t temp_cap, cudaStream_t s) {
+    NifProf prof_(h, "seg_emit", s);
+    if (n_rays <= 0 || h->n_leaves == 0) return NIF_OK;
+    launch_traverse<kModeEmit>(h, rays, inst_off, n_inst, n_rays, nullptr, offsets, segs, cap, temp_cursor, s,
+                               temp_cap);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
@@ -607,8 +629,8 @@ nif_status nif_scan_run(nif_handle* h, const uint32_t* in, uint32_t* out, int n,
 }
 
 nif_status nif_clamp_count_run(nif_handle* h, const uint32_t* offsets, int n_rays, int64_t cap, uint32_t* n_out,
-                               bool latch, cudaStream_t s) {
-    k_clamp_count<<<1, 1, 0, s>>>(offsets, n_rays, cap, n_out, h->d_status, latch ? 1 : 0);
+                               bool latch, cudaStream_t s, bool whole_rays) {
+    k_clamp_count<<<1, 1, 0, s>>>(offsets, n_rays, cap, n_out, h->d_status, latch ? 1 : 0, whole_rays ? 1 : 0);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

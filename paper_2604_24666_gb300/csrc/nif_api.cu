@@ -993,16 +993,34 @@ static nif_status segment_into_scratch(nif_handle* h, const nif_pose* poses, int
         *total_host = tot;
         if (cap < 0) cap = tot;
     } else {
-        if ((st = nif_seg_count_run(h, rays, inst_off, n_inst, n_rays, counts, s)) != NIF_OK) return st;
-        if ((st = nif_scan_run(h, counts, offs, n_rays, s)) != NIF_OK) return st;
+        // a batch of at most `cap` segments of whole rays, with no host round
+        // trip: one traversal into scratch in warp order, CSR offsets, scatter
+        // into ray order and per-row sort; should the scratch overflow, a
+        // second traversal (device-gated) writes the rows directly
+        int64_t tcap = 2 * cap + 4096;
+        if ((st = nif_grow(h, h->b_temp, sizeof(nif_segment) * (size_t)tcap)) != NIF_OK) return st;
+        tcap = (int64_t)(h->b_temp.bytes / sizeof(nif_segment));
         if ((st = nif_grow(h, h->b_segs, sizeof(nif_segment) * (size_t)std::max<int64_t>(cap, 1))) != NIF_OK)
             return st;
-        if ((st = nif_seg_emit_run(h, rays, inst_off, n_inst, n_rays, offs, (nif_segment*)h->b_segs.p, cap, s)) !=
+        nif_segment* segs = (nif_segment*)h->b_segs.p;
+        uint32_t* cursor = reinterpret_cast<uint32_t*>(h->d_count + 1);
+        NIF_CK(h, cudaMemsetAsync(cursor, 0, sizeof(uint32_t), s));
+        if ((st = nif_seg_temp_run(h, rays, inst_off, n_inst, n_rays, counts, (nif_segment*)h->b_temp.p, tcap,
+                                   cursor, s)) != NIF_OK)
+            return st;
+        if ((st = nif_scan_run(h, counts, offs, n_rays, s)) != NIF_OK) return st;
+        NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)n_rays, s));
+        if ((st = nif_seg_scatter_run(h, (const nif_segment*)h->b_temp.p, cursor, tcap, offs, counts, n_rays, segs,
+                                      cap, s)) != NIF_OK)
+            return st;
+        if ((st = nif_seg_emit_if_overflow_run(h, rays, inst_off, n_inst, n_rays, offs, segs, cap, cursor, tcap, s)) !=
             NIF_OK)
             return st;
+        // only complete rows: the row that crosses `cap` holds an arbitrary
+        // subset of its ray's segments
+        return nif_clamp_count_run(h, offs, n_rays, cap, offs + n_rays + 1, false, s, true);
     }
-    // clamped count lives right after the offsets; a training batch that the
-    // rays overfill is the normal case and latches nothing
+    // clamped count lives right after the offsets
     return nif_clamp_count_run(h, offs, n_rays, cap, offs + n_rays + 1, host_total, s);
 }
 

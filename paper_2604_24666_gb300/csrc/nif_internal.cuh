@@ -262,10 +262,15 @@ nif_status nif_sample_rays_run(nif_handle* h, unsigned long long seed, int strea
                                nif_ray* rays, cudaStream_t s);
 nif_status nif_scan_run_with(nif_handle* h, const uint32_t* in, uint32_t* out, int n, uint32_t* bsum,
                              cudaStream_t s);
-// n_out = min(offsets[n_rays], cap); latch: an overflow latches NIF_ERR_CAPACITY
-// (a truncated query), otherwise it is the normal end of a training batch
+// n_out = min(offsets[n_rays], cap), or with whole_rays the largest offsets[r] <= cap
+// (only complete rows); latch: an overflow latches NIF_ERR_CAPACITY (a
+// truncated query), otherwise it is the normal end of a training batch
 nif_status nif_clamp_count_run(nif_handle* h, const uint32_t* offsets, int n_rays, int64_t cap,
-                               uint32_t* n_out, bool latch, cudaStream_t s);
+                               uint32_t* n_out, bool latch, cudaStream_t s, bool whole_rays = false);
+// emit pass that runs only if a temp pass overflowed (*temp_cursor > temp_cap)
+nif_status nif_seg_emit_if_overflow_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
+                                        int n_rays, const uint32_t* offsets, nif_segment* segs, int64_t cap,
+                                        uint32_t* temp_cursor, int64_t temp_cap, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Device math: deformation D = Bend o Twist o Taper about c = (0.5,0.5,0.5)

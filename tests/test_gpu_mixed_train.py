@@ -170,29 +170,28 @@ def test_scaled_adam_and_overflow_skip(nif, torus):
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_mixed_training_converges_like_fp32(nif, torus, prec):
-    """2000 steps of 2^16 segments on the 16^3 torus from the same seed; the
+    """4000 steps of 2^16 segments on the 16^3 torus from the same seed; the
     occupancy BCE and log-distance error are the means of the last 10 steps.
-    FP32 and FP16 bring each below a quarter of its initial value and FP16
-    ends within a factor 2 (+0.01) of FP32. BF16 (8 significant bits in the
-    features, against FP16's 11) learns more slowly and less steadily: below
-    half of the initial value and within a factor 4 (+0.02) of FP32
-    (measured over five runs: BCE 0.12-0.23 against FP32's 0.07-0.11,
-    distance 0.15-0.30 against 0.15-0.27). The gap is the 16-bit
-    forward's own: at equal parameters the mixed gradient matches the rounded
-    chain to 1e-5, but 16-bit features, weights and activations move the
-    predicted distance by ~1e-3 voxel units, which the log-distance loss
-    (eps = 1e-2 voxel units) amplifies near the surface and through the ReLU
-    head (measured dL/dout differences: 19 % FP16, 49 % BF16 in L2; final
-    losses FP16 1.1x / 1.4x, BF16 1.8x / 1.25x of FP32's occupancy /
-    distance)."""
+    The occupancy loss of every path sits on a plateau near 0.45-0.5 for the
+    first 1200-1800 steps and then falls (FP32 earliest, BF16 latest), so the
+    comparison is made well after it. Both paths end below a tenth (BCE) and
+    a fiftieth (distance) of the initial loss; the mixed path's BCE within a
+    factor 4 (+0.02) of FP32's and its distance error within a factor 1.5
+    (+0.02). Measured: BCE FP32 0.019, FP16 0.040, BF16 0.049; distance
+    0.115, 0.110, 0.121. The gap is the 16-bit forward's own: at equal
+    parameters the mixed gradient matches the rounded chain to 1e-5, but
+    16-bit features, weights and activations move the predicted distance by
+    ~1e-3 voxel units, which the log-distance loss (eps = 1e-2 voxel units)
+    amplifies near the surface and through the ReLU head (measured dL/dout
+    differences: 19 % FP16, 49 % BF16 in L2)."""
     net = S.NetConfig()
     _, p = _prec(nif, prec)
     runs = {}
     for name, kw in (("fp32", {}), ("mixed", dict(precision=p, flags=nif.NIF_FLAG_MIXED_TRAINING))):
         h = nif.Nif(net, torus, seed=7, **kw)
         first, tail = None, []
-        for step in range(2000):
-            want = step == 0 or step >= 1990
+        for step in range(4000):
+            want = step == 0 or step >= 3990
             loss, _ = nif.nif_train_step(h.h, 1 << 16, 16, 1000 + step, lr_grid=1e-2, lr_mlp=5e-3, want_loss=want)
             if step == 0:
                 first = np.array([loss[5], loss[1]])
@@ -202,12 +201,10 @@ def test_mixed_training_converges_like_fp32(nif, torus, prec):
         if name == "mixed":
             sc, skipped = nif.nif_loss_scale(h.h)
             print(prec, "loss scale", sc, "skipped", skipped)
-            assert skipped <= 5
+            assert skipped <= 8
         h.close()
     print(prec, runs)
     (f0, l0), (f1, l1) = runs["fp32"], runs["mixed"]
-    assert np.all(l0 < 0.25 * f0)
-    if prec == "fp16":
-        assert np.all(l1 < 0.25 * f1) and np.all(l1 <= 2.0 * l0 + 0.01), (l0, l1)
-    else:
-        assert np.all(l1 < 0.5 * f1) and np.all(l1 <= 4.0 * l0 + 0.02), (l0, l1)
+    for f, l in ((f0, l0), (f1, l1)):
+        assert l[0] < 0.1 * f[0] and l[1] < 0.02 * f[1], (f, l)
+    assert l1[0] <= 4.0 * l0[0] + 0.02 and l1[1] <= 1.5 * l0[1] + 0.02, (l0, l1)
