@@ -408,8 +408,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 // so arrivals and waits alternate strictly on both barriers (the first
 // arrival of a tile follows the read of the previous tile's last chunk).
 // ---------------------------------------------------------------------------
+constexpr int kStg = 36;                 // row stride (floats) of an epilogue warp's 32 x 32 staging tile
+
 struct TcBwdLayout {
-    uint32_t wt0_off, wth_off, wto_off, a_off, bar_off, total;
+    uint32_t wt0_off, wth_off, wto_off, a_off, st_off, bar_off, total;
     int nbw, ksw;
     uint32_t wtoff[NIF_MAX_LAYERS];
 };
@@ -546,8 +548,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // layers H .. 1: TMEM holds dX_l; mask with act_{l-1} > 0 -> dY_{l-1}
             for (int l = H; l >= 1; l--) {
-                if (!wait_acc()) { ok = false; break; }
+                // the activation row for the mask is loaded before waiting on
+                // the accumulator, so its latency overlaps the MMAs
                 const uint16_t* arow = live ? acts + ((int64_t)(l - 1) * n_pad + grow) * ld : nullptr;
+                uint4 am[W / 8];
+#pragma unroll
+                for (int k = 0; k < W / 8; k++)
+                    am[k] = arow ? *reinterpret_cast<const uint4*>(arow + 8 * k) : make_uint4(0, 0, 0, 0);
+                if (!wait_acc()) { ok = false; break; }
                 uint16_t* drow = live ? dys + ((int64_t)(l - 1) * n_pad + grow) * ld : nullptr;
 #pragma unroll
                 for (int c0 = 0; c0 < W; c0 += 32) {
@@ -555,8 +563,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_ld32(lane_base + (uint32_t)c0, v);
 #pragma unroll
                     for (int c = 0; c < 32; c += 8) {
-                        uint4 am = arow ? *reinterpret_cast<const uint4*>(arow + c0 + c) : make_uint4(0, 0, 0, 0);
-                        const uint16_t* a16 = reinterpret_cast<const uint16_t*>(&am);
+                        const uint16_t* a16 = reinterpret_cast<const uint16_t*>(&am[(c0 + c) / 8]);
                         float m[8];
 #pragma unroll
                         for (int k = 0; k < 8; k++) m[k] = unpack16(a16[k], fmt) > 0.f ? v[c + k] : 0.f;
@@ -573,24 +580,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_before();
                 mbar_arrive(smem_u32(&bars[1]));
             }
-            // dX_0 chunks -> FP32 rows of dx
+            // dX_0 chunks -> FP32 rows of dx: each 32 x 32 block of the warp's
+            // rows goes through a shared-memory tile so that a store
+            // instruction writes 4 rows x 128 contiguous bytes
+            float* stg = reinterpret_cast<float*>(sm + lay.st_off) + qw * 32 * kStg;
             for (int c = 0; c < n_chunks && ok; c++) {
                 if (!wait_acc()) { ok = false; break; }
                 const int c0 = c * (int)kCols;
                 const int nc = in_dim - c0 < (int)kCols ? in_dim - c0 : (int)kCols;
-                float* xrow = live ? dx + grow * in_dim + c0 : nullptr;
                 for (int p = 0; p < nc; p += 32) {
                     float v[32];
                     tmem_ld32(lane_base + (uint32_t)p, v);
-                    if (xrow) {
-                        if (p + 32 <= nc) {
 #pragma unroll
-                            for (int k = 0; k < 32; k += 4)
-                                *reinterpret_cast<float4*>(xrow + p + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-                        } else {
-                            for (int k = 0; k < nc - p; k++) xrow[p + k] = v[k];
-                        }
+                    for (int k = 0; k < 32; k += 4)
+                        *reinterpret_cast<float4*>(stg + lane * kStg + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                    __syncwarp();
+                    const int col4 = (lane & 7) * 4;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int r = q * 4 + (lane >> 3);
+                        const int64_t gr = t * kRows + qw * 32 + r;
+                        if (gr < n && col4 < nc - p)
+                            *reinterpret_cast<float4*>(dx + gr * in_dim + c0 + p + col4) =
+                                *reinterpret_cast<const float4*>(stg + r * kStg + col4);
                     }
+                    __syncwarp();
                 }
                 if (c + 1 < n_chunks) {
                     tc_fence_before();
@@ -909,6 +923,8 @@ static nif_status launch_tc_bwd(nif_handle* h, const float* dout, const uint16_t
     off = (off + 1023) & ~1023u;
     lay.a_off = off;
     off += (uint32_t)lay.nbw * kRows * 128;
+    lay.st_off = off;
+    off += 4u * 32u * kStg * 4u;
     lay.bar_off = off;
     off += 64;
     lay.total = off + 1024;
