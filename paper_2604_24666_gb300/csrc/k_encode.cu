@@ -409,7 +409,12 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_sm(GridInfo g, Coa
     }
 }
 
-// Backward with a run-length register cache. A warp owns 32/L gamma terms x
+// Backward with a run-length register cache (the smallest dense levels,
+// whose few rows every warp hits, are privatised in shared memory; a
+// shared-memory float reduction costs more issue slots than a reduction in
+// L2, so only levels of a few hundred rows pay off there: measured, levels of
+// <= 512 rows in shared memory 1.37 ms, all five dense levels 1.59 ms, none
+// 1.97 ms on the training workload). A warp owns 32/L gamma terms x
 // L levels (lane = level + L * term) and walks a chunk of kRun consecutive
 // segments, visiting each segment's two end points in turn: p0(s), p1(s),
 // p0(s+1), ... Segments come in ray order, and where two voxels share a face
@@ -683,9 +688,10 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
     Coarse cs{};
     cs.Lc = 0;
     cs.soff[0] = 0;
-    for (int l = 0; l < std::min(h->L, h->tune.bwd_smem_levels); l++) {
+    for (int l = 0; l < h->L; l++) {
         if (!((h->grid.dense_mask >> l) & 1u)) break;
         int64_t r = (int64_t)h->grid.res[l] + 1;
+        if (r * r * r > h->tune.bwd_smem_rows) break;
         int64_t need = r * r * r * 2;
         if (cs.soff[l] + need > budget) break;
         cs.soff[l + 1] = cs.soff[l] + (int)need;
@@ -695,7 +701,7 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
     if (32 % h->L == 0 && h->L >= 4) {      // a level group holds the 3 lanes that evaluate u
         NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
-        const int per_sm = cs.Lc > 0 ? 1 : 2;
+        const int per_sm = smem <= 100 * 1024 ? 2 : 1;      // 1024-thread blocks, two per SM when they fit
         k_encode_segments_bwd_rl<<<h->num_sms * per_sm, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats,
                                                                          dtables);
         NIF_CK_LAUNCH(h);

@@ -118,7 +118,8 @@ struct nif_handle {
         int enc_threads = 256;          // encoding block size
         int enc_blocks_per_sm = 16;     // encoding grid cap per SM (grid-stride beyond)
         int64_t tc_chunk = 1 << 20;     // rows per encode + tensor-core MLP chunk
-        int bwd_smem_levels = 32;       // encoding backward: at most this many dense coarse levels in shared memory
+        int bwd_smem_rows = 512;        // encoding backward: dense coarse levels of at most this many rows
+                                        // go to shared memory (measured: larger ones reduce faster in L2)
     } tune;
 
     // CUDA graphs of live query plans hold the scratch and per-instance
