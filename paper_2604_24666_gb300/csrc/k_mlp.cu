@@ -515,7 +515,8 @@ nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n
 }
 
 nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
-                                const float* acts, const float* dout, float* dx, cudaStream_t s, bool want_dw) {
+                                const float* acts, const float* dout, float* dx, cudaStream_t s, bool want_dw,
+                                cudaStream_t aux) {
     NifProf prof_(h, "mlp_bwd_fp32", s);
     if (n_max <= 0) return NIF_OK;
     nif_status st = nif_grow(h, h->b_dout, sizeof(float) * (size_t)n_max * h->W * 2);
@@ -534,7 +535,18 @@ nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n
         w.B = in; w.sbk = in_ld; w.sbj = 1;
         w.C = h->d_grad + h->off_layer[l]; w.ldc = nin;
         w.M = nout; w.N = nin; w.K = n_max; w.M_dev = n_dev; w.m_is_k = 1; w.k_chunk = 0;
-        if (want_dw && (st = gemm<kAtomic>(h, w, s)) != NIF_OK) return st;
+        if (want_dw && l == 0 && aux) {
+            // dY_0 is final: the layer-0 weight gradient overlaps dX_0 and what follows
+            NIF_CK(h, cudaEventRecord(h->ev_fork, s));
+            NIF_CK(h, cudaStreamWaitEvent(aux, h->ev_fork, 0));
+            {
+                NifProf prof_dw(h, "mlp_dw0_fp32", aux);
+                if ((st = gemm<kAtomic>(h, w, aux)) != NIF_OK) return st;
+            }
+            NIF_CK(h, cudaEventRecord(h->ev_join, aux));
+        } else if (want_dw && (st = gemm<kAtomic>(h, w, s)) != NIF_OK) {
+            return st;
+        }
         // d(in) = g W_l : [n x nin], masked by the ReLU of the layer below
         if (l == 0 && !dx) break;
         GemmArgs d{};

@@ -426,6 +426,9 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
     CKC(cudaMalloc(&h->d_count, sizeof(int) * 4));
     CKC(cudaMemset(h->d_count, 0, sizeof(int) * 4));
     CKC(cudaMallocHost(&h->h_pinned, sizeof(int) * 16));
+    CKC(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    CKC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
 
     st = nif_voxelize_run(h);
     if (st != NIF_OK) return fail(st);
@@ -488,6 +491,9 @@ extern "C" void nif_destroy(nif_handle* h) {
     for (auto* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) cudaStreamDestroy(h->aux);
     for (auto e : h->prof_pool) cudaEventDestroy(e);
     h->n_plans = 0;
     nif_free_retired(h);
@@ -1125,15 +1131,23 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
         if ((st = nif_mlp_fwd_tc_acts_run(h, feat, prec, n_dev, n, out, acts16, np, kLd, s)) != NIF_OK) return st;
         if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s)) != NIF_OK) return st;
         if ((st = nif_mlp_bwd_tc_run(h, dout, acts16, n_dev, n, np, kLd, dys, dx, s)) != NIF_OK) return st;
-        if ((st = nif_mlp_dw_tc_run(h, feat, acts16, dys, n_dev, n, np, kLd, s)) != NIF_OK) return st;
+        // weight gradients on the second stream, beside the encoding backward
+        NIF_CK(h, cudaEventRecord(h->ev_fork, s));
+        NIF_CK(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+        if ((st = nif_mlp_dw_tc_run(h, feat, acts16, dys, n_dev, n, np, kLd, h->aux)) != NIF_OK) return st;
+        NIF_CK(h, cudaEventRecord(h->ev_join, h->aux));
         if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK)
             return st;
+        NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
         if ((st = nif_grad_check_run(h, s)) != NIF_OK) return st;
         if ((st = nif_adam_scaled_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
     } else {
         if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s)) != NIF_OK) return st;
         if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
         if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s)) != NIF_OK) return st;
+        // (the layer-0 weight gradient could overlap the encoding backward on
+        // h->aux: measured 5.66 -> 5.56 ms, but both then run ~30 % slower, so
+        // the FP32 step keeps them in sequence)
         if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s)) != NIF_OK) return st;
         if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK)
             return st;

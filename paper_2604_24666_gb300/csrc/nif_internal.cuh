@@ -100,6 +100,12 @@ struct nif_handle {
     bool lowp_dirty = true;
     long adam_step = 0;
 
+    // a second stream for work of a training step that can overlap the main
+    // stream's (the layer-0 weight gradient beside the encoding backward);
+    // it always forks from and joins back into the caller's stream
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
     // device status word + scratch
     int* d_status = nullptr;
     double* d_lossacc = nullptr;        // [16] loss accumulators
@@ -225,10 +231,12 @@ nif_status nif_pose_grad_run(nif_handle* h, const nif_segment* segs, const nif_l
                              cudaStream_t s);
 nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
                                 float* out, float* acts, cudaStream_t s);
-// want_dw: add dL/dW into the gradient buffer (off for an input gradient only)
+// want_dw: add dL/dW into the gradient buffer (off for an input gradient only);
+// with `aux`, the layer-0 weight gradient runs there (forked from s after
+// dY_0 is ready; the caller joins with h->ev_join before reading gradients)
 nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
                                 const float* acts, const float* dout, float* dx, cudaStream_t s,
-                                bool want_dw = true);
+                                bool want_dw = true, cudaStream_t aux = nullptr);
 nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev,
                               int64_t n_max, float* out, cudaStream_t s);
 // acts_out (nullable): 16-bit hidden activations, layer l row r at (l * acts_rows + r) * acts_ld
