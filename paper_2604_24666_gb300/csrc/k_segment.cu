@@ -226,10 +226,15 @@ __global__ void __launch_bounds__(kTravWarps * 32) k_seg_traverse(
     s_cnt[warp][lane] = 0;
     s_inst[warp][lane] = inst;
     const float4* A = aabb + (int64_t)inst * tree.n_nodes * 2;
+    // the stack holds nodes whose boxes the ray is known to meet: a node's
+    // children are box-tested together when it is expanded (their boxes are
+    // contiguous, so the loads go out back to back) and only those hit are
+    // pushed; a popped leaf goes straight to the queue
     int stack[kStack];
     int sp = 0;
     if (valid)
-        for (int q = tree.top_begin + tree.top_count - 1; q >= tree.top_begin; q--) stack[sp++] = q;
+        for (int q = tree.top_begin + tree.top_count - 1; q >= tree.top_begin; q--)
+            if (slab(ray, __ldg(A + 2 * q), __ldg(A + 2 * q + 1))) stack[sp++] = q;
     __syncwarp();
     int qn = 0;
     while (true) {
@@ -240,17 +245,16 @@ __global__ void __launch_bounds__(kTravWarps * 32) k_seg_traverse(
             int cand = -1;
             if (want) {
                 int node = stack[--sp];
-                if (slab(ray, __ldg(A + 2 * node), __ldg(A + 2 * node + 1))) {
-                    if (node < tree.n_leaves) {
-                        cand = node;
+                if (node < tree.n_leaves) {
+                    cand = node;
+                } else {
+                    int2 ch = __ldg(tree.child + (node - tree.n_leaves));
+                    if (sp + ch.y > kStack) {
+                        nif_set_status(status, NIF_ERR_CAPACITY);
+                        sp = 0;
                     } else {
-                        int2 ch = __ldg(tree.child + (node - tree.n_leaves));
-                        if (sp + ch.y > kStack) {
-                            nif_set_status(status, NIF_ERR_CAPACITY);
-                            sp = 0;
-                        } else {
-                            for (int c = ch.x + ch.y - 1; c >= ch.x; c--) stack[sp++] = c;
-                        }
+                        for (int c = ch.x + ch.y - 1; c >= ch.x; c--)
+                            if (slab(ray, __ldg(A + 2 * c), __ldg(A + 2 * c + 1))) stack[sp++] = c;
                     }
                 }
             }
