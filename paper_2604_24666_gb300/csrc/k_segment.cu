@@ -202,7 +202,7 @@ enum { kModeCount = 0, kModeEmit = 1, kModeTemp = 2 };
 //   kModeTemp:  counts plus every segment appended to `temp` at a
 //               warp-reserved position (ray order is restored by a scatter).
 template <int MODE, int kTravWarps>
-__global__ void __launch_bounds__(kTravWarps * 32) k_seg_traverse(
+__global__ void __launch_bounds__(kTravWarps * 32, 32 / kTravWarps) k_seg_traverse(
     const nif_ray* __restrict__ rays, const int* __restrict__ inst_off, int n_inst, int n_rays,
     TreeView tree, const float* __restrict__ corners, const float4* __restrict__ aabb,
     uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets, nif_segment* __restrict__ segs,
