@@ -414,9 +414,12 @@ __device__ __forceinline__ float uni(uint64_t seed, uint64_t counter) {
     return (float)(z >> 40) * (1.0f / 16777216.0f);
 }
 
-__global__ void k_sample_rays(uint64_t seed, int stream_id, int n, nif_ray* __restrict__ rays) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// rays[j * n + i] is index i of stream stream0 + j, for j < n_streams
+__global__ void k_sample_rays(uint64_t seed, int stream0, int n, int n_streams, nif_ray* __restrict__ rays) {
+    int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)n * n_streams) return;
+    const int j = (int)(gid / n), i = (int)(gid - (int64_t)j * n);
+    const int stream_id = stream0 + j;
     uint64_t base = (((uint64_t)(uint32_t)stream_id << 32) + (uint64_t)i) * 8ull;
     float u0 = uni(seed, base), u1 = uni(seed, base + 1), u2 = uni(seed, base + 2), u3 = uni(seed, base + 3),
           u4 = uni(seed, base + 4);
@@ -433,7 +436,7 @@ __global__ void k_sample_rays(uint64_t seed, int stream_id, int n, nif_ray* __re
     r.d[0] = dx * il; r.d[1] = dy * il; r.d[2] = dz * il;
     r.tmin = 0.f;
     r.tmax = 1e30f;
-    rays[i] = r;
+    rays[gid] = r;
 }
 
 __global__ void k_count_hits(const nif_label* __restrict__ labels, int64_t n, int* __restrict__ n_hit) {
@@ -560,10 +563,10 @@ nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* in
 }
 
 nif_status nif_sample_rays_run(nif_handle* h, unsigned long long seed, int stream_id, int n, nif_ray* rays,
-                               cudaStream_t s) {
+                               cudaStream_t s, int n_streams) {
     NifProf prof_(h, "sample_rays", s);
-    if (n <= 0) return NIF_OK;
-    k_sample_rays<<<nif_blocks(n, 256), 256, 0, s>>>(seed, stream_id, n, rays);
+    if (n <= 0 || n_streams <= 0) return NIF_OK;
+    k_sample_rays<<<nif_blocks((int64_t)n * n_streams, 256), 256, 0, s>>>(seed, stream_id, n, n_streams, rays);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

@@ -160,6 +160,23 @@ __global__ void k_to_lowp_t(const float* __restrict__ w, LayerDims d, __half* __
     }
 }
 
+// up to kPoseArg poses passed by value (the kernel-argument block holds 4 KB)
+constexpr int kPoseArg = 128;
+struct PoseArg {
+    int n;
+    float4 p[kPoseArg];
+};
+
+__global__ void k_set_poses(PoseArg a, float4* __restrict__ d) {
+    if ((int)threadIdx.x < a.n) d[threadIdx.x] = a.p[threadIdx.x];
+}
+
+// offsets[i] = i * per for i <= n
+__global__ void k_iota_offsets(int* __restrict__ offsets, int n, int per) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) offsets[i] = i * per;
+}
+
 uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
@@ -237,6 +254,16 @@ nif_status nif_ensure_instances(nif_handle* h, int n_inst) {
 nif_status nif_upload_poses(nif_handle* h, const nif_pose* poses, int n_inst, cudaStream_t s) {
     nif_status st = nif_ensure_instances(h, n_inst);
     if (st != NIF_OK) return st;
+    if (n_inst <= kPoseArg) {
+        // small batches travel as a kernel argument: no host round trip
+        PoseArg a;
+        a.n = n_inst;
+        for (int i = 0; i < n_inst; i++)
+            a.p[i] = make_float4(NIF_KBEND * poses[i].bend, poses[i].twist, poses[i].taper, 0.f);
+        k_set_poses<<<1, kPoseArg, 0, s>>>(a, h->d_pose);
+        NIF_CK_LAUNCH(h);
+        return NIF_OK;
+    }
     std::vector<float4> p(n_inst);
     for (int i = 0; i < n_inst; i++) p[i] = make_float4(NIF_KBEND * poses[i].bend, poses[i].twist, poses[i].taper, 0.f);
     NIF_CK(h, cudaMemcpyAsync(h->d_pose, p.data(), sizeof(float4) * n_inst, cudaMemcpyHostToDevice, s));
@@ -1278,12 +1305,9 @@ extern "C" nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_po
     if ((st = nif_grow(h, h->b_rays, sizeof(nif_ray) * (size_t)n_rays)) != NIF_OK) return st;
     if ((st = nif_grow(h, h->b_inst, sizeof(int) * (size_t)(n_poses + 1))) != NIF_OK) return st;
     nif_ray* rays = (nif_ray*)h->b_rays.p;
-    for (int i = 0; i < n_poses; i++)
-        if ((st = nif_sample_rays_run(h, step_seed, i, per, rays + (size_t)i * per, s)) != NIF_OK) return st;
-    std::vector<int> off(n_poses + 1);
-    for (int i = 0; i <= n_poses; i++) off[i] = i * per;
-    NIF_CK(h, cudaMemcpyAsync(h->b_inst.p, off.data(), sizeof(int) * (n_poses + 1), cudaMemcpyHostToDevice, s));
-    NIF_CK(h, cudaStreamSynchronize(s));
+    if ((st = nif_sample_rays_run(h, step_seed, 0, per, rays, s, n_poses)) != NIF_OK) return st;
+    k_iota_offsets<<<nif_blocks(n_poses + 1, 256), 256, 0, s>>>((int*)h->b_inst.p, n_poses, per);
+    NIF_CK_LAUNCH(h);
     return nif_train_step_rays(h, poses.data(), n_poses, rays, (const int*)h->b_inst.p, n_rays, n_segments, lr_grid,
                                lr_mlp, loss_host, stream);
 }

@@ -267,8 +267,9 @@ nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* in
                                int n_rays, const uint32_t* offsets, const nif_segment* segs,
                                int64_t seg_cap, const nif_linseg* lin, const float* out,
                                nif_hit* hits, unsigned flags, cudaStream_t s);
+// n rays of each of the streams stream_id .. stream_id + n_streams - 1, stream after stream
 nif_status nif_sample_rays_run(nif_handle* h, unsigned long long seed, int stream_id, int n,
-                               nif_ray* rays, cudaStream_t s);
+                               nif_ray* rays, cudaStream_t s, int n_streams = 1);
 nif_status nif_scan_run_with(nif_handle* h, const uint32_t* in, uint32_t* out, int n, uint32_t* bsum,
                              cudaStream_t s);
 // n_out = min(offsets[n_rays], cap), or with whole_rays the largest offsets[r] <= cap
