@@ -165,21 +165,68 @@ struct OutPair<__half> {
     static __device__ __forceinline__ T make(float a, float b) { return __floats2half2_rn(a, b); }
 };
 
+// Along a ray the exit point of a voxel is, bit for bit, the entry point of
+// the next one where the two share a face (the same hull triangle in the same
+// vertex order gives the same t; the same inverse gives the same rest point):
+// about two thirds of the segments of the synthetic workloads. k_dup_flags
+// marks them (u = 1: p0 repeats the previous p1, u = 2: both end points are
+// new, u = 0: past the live count), a scan of u numbers the distinct points,
+// k_point_list lists them as 2 s + e, and the encoder runs once per distinct
+// point, writing a repeated point's features into both rows.
+__global__ void __launch_bounds__(256) k_dup_flags(const nif_linseg* __restrict__ lin,
+                                                   const uint32_t* __restrict__ n_dev, int64_t n_max,
+                                                   uint32_t* __restrict__ u) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_max;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t v = 0;
+        if (s < n) {
+            v = 2;
+            if (s > 0) {
+                const float* a = reinterpret_cast<const float*>(lin + s);
+                const float* b = reinterpret_cast<const float*>(lin + s - 1) + 3;
+                if (a[0] == b[0] && a[1] == b[1] && a[2] == b[2]) v = 1;
+            }
+        }
+        u[s] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_point_list(const uint32_t* __restrict__ u, const uint32_t* __restrict__ off,
+                                                    int64_t n_max, uint32_t* __restrict__ pts) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_max;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = u[s], o = off[s];
+        if (v == 2) {
+            pts[o] = (uint32_t)(2 * s);
+            pts[o + 1] = (uint32_t)(2 * s + 1);
+        } else if (v == 1) {
+            pts[o] = (uint32_t)(2 * s + 1);
+        }
+    }
+}
+
+// pts (nullable): the distinct points (2 s + e, *n_pts_dev of them) and dupf
+// the flags of k_dup_flags; without them every (segment, end point) is encoded
 template <typename TT, typename OT, int LMAX>
 __global__ void __launch_bounds__(512) k_encode_segments_v(GridInfo g, const TT* __restrict__ tab,
                                                            const nif_linseg* __restrict__ lin,
                                                            const uint32_t* __restrict__ n_dev, int64_t n_max,
-                                                           OT* __restrict__ out) {
+                                                           OT* __restrict__ out, const uint32_t* __restrict__ pts,
+                                                           const uint32_t* __restrict__ n_pts_dev,
+                                                           const uint32_t* __restrict__ dupf) {
     using P2 = typename OutPair<OT>::T;
     int64_t n = n_dev ? (int64_t)*n_dev : n_max;
     if (n > n_max) n = n_max;
-    const int per = 2 * g.P;
-    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n * per;
+    const int64_t n_points = pts ? (int64_t)*n_pts_dev : 2 * n;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n_points * g.P;
          gid += (int64_t)gridDim.x * blockDim.x) {
-        int64_t s = gid / per;
-        int r = (int)(gid - s * per);
-        int e = r >= g.P;
-        int t = r - e * g.P;
+        const int64_t k = gid / g.P;
+        const int t = (int)(gid - k * g.P);
+        const int64_t pt = pts ? (int64_t)pts[k] : k;
+        const int64_t s = pt >> 1;
+        const int e = (int)(pt & 1);
         const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
         float3 u = term_u(clamp01(make_float3(L[0], L[1], L[2])), t);
         P2 res[LMAX];
@@ -220,7 +267,10 @@ __global__ void __launch_bounds__(512) k_encode_segments_v(GridInfo g, const TT*
             }
             res[l] = OutPair<OT>::make(acc.x, acc.y);
         }
-        P2* o = reinterpret_cast<P2*>(out + gid * g.L * 2);
+        // the row of (s, e, t), and of (s + 1, 0, t) when that end point repeats this one
+        const bool twice = pts && e == 1 && s + 1 < n_max && dupf[s + 1] == 1;
+        P2* o = reinterpret_cast<P2*>(out + ((s * 2 + e) * g.P + t) * g.L * 2);
+        P2* o2 = reinterpret_cast<P2*>(out + ((s + 1) * 2 * g.P + t) * g.L * 2);
         constexpr int per16 = 16 / sizeof(P2);           // pairs per 16-byte store
         if ((g.L % per16) == 0) {
 #pragma unroll
@@ -229,18 +279,20 @@ __global__ void __launch_bounds__(512) k_encode_segments_v(GridInfo g, const TT*
                 uint4 w4;
                 uint32_t* w = reinterpret_cast<uint32_t*>(&w4);
 #pragma unroll
-                for (int k = 0; k < per16; k++) {
-                    const uint32_t* src = reinterpret_cast<const uint32_t*>(&res[l + k]);
+                for (int kk = 0; kk < per16; kk++) {
+                    const uint32_t* src = reinterpret_cast<const uint32_t*>(&res[l + kk]);
 #pragma unroll
-                    for (int q = 0; q < (int)(sizeof(P2) / 4); q++) w[k * (sizeof(P2) / 4) + q] = src[q];
+                    for (int q = 0; q < (int)(sizeof(P2) / 4); q++) w[kk * (sizeof(P2) / 4) + q] = src[q];
                 }
                 *reinterpret_cast<uint4*>(o + l) = w4;
+                if (twice) *reinterpret_cast<uint4*>(o2 + l) = w4;
             }
         } else {
 #pragma unroll
             for (int l = 0; l < LMAX; l++) {
                 if (l >= g.L) break;
                 o[l] = res[l];
+                if (twice) o2[l] = res[l];
             }
         }
     }
@@ -613,19 +665,38 @@ void launch_points(nif_handle* h, const TT* tab, const float* pts, int64_t n, vo
 }
 
 template <typename TT, typename OT>
-void launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
-                     void* feats, cudaStream_t s) {
+nif_status launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
+                           void* feats, cudaStream_t s) {
     // block size and resident blocks per SM are tuning knobs of the handle
     int thr = h->tune.enc_threads;
     unsigned g = nif_blocks(n_max * 2 * h->P, thr);
     unsigned cap = (unsigned)h->num_sms * (unsigned)h->tune.enc_blocks_per_sm;
     if (g > cap) g = cap;
-    if (h->L <= 8)
-        k_encode_segments_v<TT, OT, 8><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
-    else if (h->L <= 16)
-        k_encode_segments_v<TT, OT, 16><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
-    else
+    if (h->L <= 16) {
+        // distinct end points only (device-side list, see k_dup_flags)
+        nif_status st;
+        if ((st = nif_grow(h, h->b_dup, sizeof(uint32_t) * (2 * (size_t)n_max + 1))) != NIF_OK) return st;
+        if ((st = nif_grow(h, h->b_pts, sizeof(uint32_t) * 2 * (size_t)n_max)) != NIF_OK) return st;
+        const int nb = (int)nif_blocks(n_max, 1024);
+        if ((st = nif_grow(h, h->b_scan, sizeof(uint32_t) * ((size_t)nb + 1))) != NIF_OK) return st;
+        uint32_t* u = (uint32_t*)h->b_dup.p;
+        uint32_t* off = u + n_max;
+        uint32_t* pts = (uint32_t*)h->b_pts.p;
+        unsigned gs = std::min<unsigned>(nif_blocks(n_max, 256), (unsigned)h->num_sms * 16);
+        k_dup_flags<<<gs, 256, 0, s>>>(lin, n_dev, n_max, u);
+        NIF_CK_LAUNCH(h);
+        if ((st = nif_scan_run_with(h, u, off, (int)n_max, (uint32_t*)h->b_scan.p, s)) != NIF_OK) return st;
+        k_point_list<<<gs, 256, 0, s>>>(u, off, n_max, pts);
+        NIF_CK_LAUNCH(h);
+        if (h->L <= 8)
+            k_encode_segments_v<TT, OT, 8><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats, pts,
+                                                            off + n_max, u);
+        else
+            k_encode_segments_v<TT, OT, 16><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats, pts,
+                                                             off + n_max, u);
+    } else
         k_encode_segments<TT, OT><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
+    return NIF_OK;
 }
 
 }  // namespace
@@ -647,23 +718,25 @@ nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const u
                                    void* feats, int out_dtype, int table_dtype, cudaStream_t s) {
     NifProf prof_(h, "encode_fwd", s);
     if (n_max <= 0) return NIF_OK;
+    nif_status st = NIF_OK;
     if (table_dtype == NIF_FP16) {
-        nif_status st = nif_refresh_lowp(h, s);
+        st = nif_refresh_lowp(h, s);
         if (st != NIF_OK) return st;
         const __half* tab = h->d_tables_h;
-        if (out_dtype == NIF_FP32) launch_segments<__half, float>(h, tab, lin, n_dev, n_max, feats, s);
-        else if (out_dtype == NIF_BF16) launch_segments<__half, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s);
-        else if (out_dtype == NIF_FP16) launch_segments<__half, __half>(h, tab, lin, n_dev, n_max, feats, s);
+        if (out_dtype == NIF_FP32) st = launch_segments<__half, float>(h, tab, lin, n_dev, n_max, feats, s);
+        else if (out_dtype == NIF_BF16) st = launch_segments<__half, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s);
+        else if (out_dtype == NIF_FP16) st = launch_segments<__half, __half>(h, tab, lin, n_dev, n_max, feats, s);
         else return nif_fail(h, NIF_ERR_ARG, "out_dtype");
     } else if (table_dtype == NIF_FP32) {
         const float* tab = h->d_params + h->off_tables;
-        if (out_dtype == NIF_FP32) launch_segments<float, float>(h, tab, lin, n_dev, n_max, feats, s);
-        else if (out_dtype == NIF_BF16) launch_segments<float, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s);
-        else if (out_dtype == NIF_FP16) launch_segments<float, __half>(h, tab, lin, n_dev, n_max, feats, s);
+        if (out_dtype == NIF_FP32) st = launch_segments<float, float>(h, tab, lin, n_dev, n_max, feats, s);
+        else if (out_dtype == NIF_BF16) st = launch_segments<float, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s);
+        else if (out_dtype == NIF_FP16) st = launch_segments<float, __half>(h, tab, lin, n_dev, n_max, feats, s);
         else return nif_fail(h, NIF_ERR_ARG, "out_dtype");
     } else {
         return nif_fail(h, NIF_ERR_ARG, "table_dtype");
     }
+    if (st != NIF_OK) return st;
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

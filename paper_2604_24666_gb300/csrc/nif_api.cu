@@ -514,7 +514,7 @@ extern "C" void nif_destroy(nif_handle* h) {
         if (p) cudaFree(p);
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
                                &h->b_acts, &h->b_dout, &h->b_dx, &h->b_labels, &h->b_scan, &h->b_rays,
-                               &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys};
+                               &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys, &h->b_dup, &h->b_pts};
     for (auto* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);

@@ -115,7 +115,7 @@ struct nif_handle {
     // grown scratch buffers (query / train)
     struct Buf { void* p = nullptr; size_t bytes = 0; };
     Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
-        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys;
+        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts;
     double query_seg_per_ray = 0.0;     // segments per ray of the last query (temp capacity hint)
 
     // launch knobs chosen by the autotuner (nif_query_plan_create)
