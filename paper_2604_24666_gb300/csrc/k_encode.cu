@@ -515,7 +515,10 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
                                                                  const nif_linseg* __restrict__ lin,
                                                                  const uint32_t* __restrict__ n_dev, int64_t n_max,
                                                                  const float* __restrict__ dfeats,
-                                                                 float* __restrict__ dtab) {
+                                                                 float* __restrict__ dtab,
+                                                                 const uint32_t* __restrict__ pts,
+                                                                 const uint32_t* __restrict__ n_pts_dev,
+                                                                 const uint32_t* __restrict__ dupf) {
     extern __shared__ float sacc[];
     const int nsh = cs.soff[cs.Lc];
     for (int i = threadIdx.x; i < nsh; i += blockDim.x) sacc[i] = 0.f;
@@ -531,7 +534,10 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
     const bool dense = (g.dense_mask >> l) & 1u;
     const bool in_sh = l < cs.Lc;
     float* dl = in_sh ? sacc + cs.soff[l] : dtab + (int64_t)l * g.T * 2;
-    const int64_t chunks = (n + kRun - 1) / kRun;
+    // the distinct end points in order (a repeated entry point adds its
+    // feature gradient to the exit point it repeats), 2 kRun per chunk
+    const int64_t n_points = *n_pts_dev;
+    const int64_t chunks = (n_points + 2 * kRun - 1) / (2 * kRun);
     const int64_t tasks = chunks * groups;
     const int warps_total = gridDim.x * (blockDim.x >> 5);
     for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < tasks;
@@ -545,11 +551,13 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
         float2 cacc[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) cacc[q] = make_float2(0.f, 0.f);
-        const int64_t s_end = (c + 1) * kRun < n ? (c + 1) * kRun : n;
+        const int64_t k_end = (c + 1) * 2 * kRun < n_points ? (c + 1) * 2 * kRun : n_points;
         const int base = term_in_warp * g.L;              // first lane of this term's level group
-        for (int64_t s = c * kRun; s < s_end; s++) {      // warp-uniform trip count (shuffles below)
-#pragma unroll 1
-            for (int e = 0; e < 2; e++) {
+        for (int64_t k = c * 2 * kRun; k < k_end; k++) {  // warp-uniform trip count (shuffles below)
+            {
+                const uint32_t pt = pts[k];
+                const int64_t s = pt >> 1;
+                const int e = (int)(pt & 1);
                 // the term's u is the same for all L levels: lanes base..base+2
                 // evaluate one coordinate each and the group shares them
                 const float* Lp = reinterpret_cast<const float*>(lin + s) + 3 * e;
@@ -571,6 +579,11 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
                 if (!active) continue;
                 Cell cl = cell_of(u, Nl);
                 float2 gr = *reinterpret_cast<const float2*>(dfeats + ((s * 2 * g.P + e * g.P + t) * g.L + l) * 2);
+                if (e == 1 && s + 1 < n_max && dupf[s + 1] == 1) {
+                    const float2 g2 = *reinterpret_cast<const float2*>(dfeats + (((s + 1) * 2 * g.P + t) * g.L + l) * 2);
+                    gr.x += g2.x;
+                    gr.y += g2.y;
+                }
                 if (cl.ix != cx || cl.iy != cy || cl.iz != cz) {
                     if (cx >= 0) flush_cell(dl, in_sh, cx, cy, cz, Nl, dense, g.T, cacc);
                     cx = cl.ix;
@@ -664,6 +677,31 @@ void launch_points(nif_handle* h, const TT* tab, const float* pts, int64_t n, vo
     k_encode_points<TT, OT><<<nif_blocks(n * h->P, 256), 256, 0, s>>>(h->grid, tab, pts, n, (OT*)feats, rows);
 }
 
+// The list of distinct end points of segments [0, n) (flags in *dupf, count in
+// *n_pts on the device) in the handle's scratch.
+nif_status distinct_points(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
+                           const uint32_t** pts_out, const uint32_t** n_pts_out, const uint32_t** dupf_out,
+                           cudaStream_t s) {
+    nif_status st;
+    if ((st = nif_grow(h, h->b_dup, sizeof(uint32_t) * (2 * (size_t)n_max + 1))) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_pts, sizeof(uint32_t) * 2 * (size_t)n_max)) != NIF_OK) return st;
+    const int nb = (int)nif_blocks(n_max, 1024);
+    if ((st = nif_grow(h, h->b_scan, sizeof(uint32_t) * ((size_t)nb + 1))) != NIF_OK) return st;
+    uint32_t* u = (uint32_t*)h->b_dup.p;
+    uint32_t* off = u + n_max;
+    uint32_t* pts = (uint32_t*)h->b_pts.p;
+    unsigned gs = std::min<unsigned>(nif_blocks(n_max, 256), (unsigned)h->num_sms * 16);
+    k_dup_flags<<<gs, 256, 0, s>>>(lin, n_dev, n_max, u);
+    NIF_CK_LAUNCH(h);
+    if ((st = nif_scan_run_with(h, u, off, (int)n_max, (uint32_t*)h->b_scan.p, s)) != NIF_OK) return st;
+    k_point_list<<<gs, 256, 0, s>>>(u, off, n_max, pts);
+    NIF_CK_LAUNCH(h);
+    *pts_out = pts;
+    *n_pts_out = off + n_max;
+    *dupf_out = u;
+    return NIF_OK;
+}
+
 template <typename TT, typename OT>
 nif_status launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
                            void* feats, cudaStream_t s) {
@@ -674,26 +712,15 @@ nif_status launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, 
     if (g > cap) g = cap;
     if (h->L <= 16) {
         // distinct end points only (device-side list, see k_dup_flags)
-        nif_status st;
-        if ((st = nif_grow(h, h->b_dup, sizeof(uint32_t) * (2 * (size_t)n_max + 1))) != NIF_OK) return st;
-        if ((st = nif_grow(h, h->b_pts, sizeof(uint32_t) * 2 * (size_t)n_max)) != NIF_OK) return st;
-        const int nb = (int)nif_blocks(n_max, 1024);
-        if ((st = nif_grow(h, h->b_scan, sizeof(uint32_t) * ((size_t)nb + 1))) != NIF_OK) return st;
-        uint32_t* u = (uint32_t*)h->b_dup.p;
-        uint32_t* off = u + n_max;
-        uint32_t* pts = (uint32_t*)h->b_pts.p;
-        unsigned gs = std::min<unsigned>(nif_blocks(n_max, 256), (unsigned)h->num_sms * 16);
-        k_dup_flags<<<gs, 256, 0, s>>>(lin, n_dev, n_max, u);
-        NIF_CK_LAUNCH(h);
-        if ((st = nif_scan_run_with(h, u, off, (int)n_max, (uint32_t*)h->b_scan.p, s)) != NIF_OK) return st;
-        k_point_list<<<gs, 256, 0, s>>>(u, off, n_max, pts);
-        NIF_CK_LAUNCH(h);
+        const uint32_t *pts, *n_pts, *dupf;
+        nif_status st = distinct_points(h, lin, n_dev, n_max, &pts, &n_pts, &dupf, s);
+        if (st != NIF_OK) return st;
         if (h->L <= 8)
             k_encode_segments_v<TT, OT, 8><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats, pts,
-                                                            off + n_max, u);
+                                                            n_pts, dupf);
         else
             k_encode_segments_v<TT, OT, 16><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats, pts,
-                                                             off + n_max, u);
+                                                             n_pts, dupf);
     } else
         k_encode_segments<TT, OT><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats);
     return NIF_OK;
@@ -772,11 +799,14 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
     }
     size_t smem = sizeof(float) * (size_t)cs.soff[cs.Lc];
     if (32 % h->L == 0 && h->L >= 4) {      // a level group holds the 3 lanes that evaluate u
+        const uint32_t *pts, *n_pts, *dupf;
+        nif_status st = distinct_points(h, lin, n_dev, n_max, &pts, &n_pts, &dupf, s);
+        if (st != NIF_OK) return st;
         NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
         const int per_sm = smem <= 100 * 1024 ? 2 : 1;      // 1024-thread blocks, two per SM when they fit
         k_encode_segments_bwd_rl<<<h->num_sms * per_sm, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats,
-                                                                         dtables);
+                                                                         dtables, pts, n_pts, dupf);
         NIF_CK_LAUNCH(h);
         return NIF_OK;
     }
