@@ -446,7 +446,7 @@ nif_status gemm(nif_handle* h, GemmArgs a, cudaStream_t s, int splits = 1) {
                (a.sbj == 1 ? a.sbk % 4 == 0 : a.sbj % 4 == 0) && (!a.mask || aligned16(a.mask)) &&
                (a.m_is_k || a.K % 16 == 0);
     // 128-row tiles for long reductions over many rows, 64-row tiles otherwise (more resident blocks)
-    const bool tall = big && a.M >= 96 && !a.m_is_k && a.K > 64;
+    const bool tall = big && a.M >= 96 && !a.m_is_k && (a.K > 64 || a.N >= 512);
     const int bm = big ? (tall ? 128 : 64) : BM;
     const int64_t tiles = (int64_t)((a.N + 63) / 64) * ((a.M + bm - 1) / bm);
     auto split_rows = [&](int64_t waves_sms) {
@@ -458,7 +458,7 @@ nif_status gemm(nif_handle* h, GemmArgs a, cudaStream_t s, int splits = 1) {
     if (EPI == kAtomic) a.k_chunk = split_rows(4 * (int64_t)h->num_sms);
     // the 8x8-per-thread kernel pays off when each block reduces over >= 512
     // (it holds fewer warps per SM; short reductions are prologue-bound)
-    const bool rt = big && (EPI == kAtomic ? a.k_chunk : a.K) >= 512;
+    const bool rt = big && ((EPI == kAtomic ? a.k_chunk : a.K) >= 512 || (tall && a.N >= 512));
     if (EPI == kAtomic) {
         if (rt) a.k_chunk = std::max<int64_t>(512, split_rows(8 * (int64_t)h->num_sms));
         splits = (int)((a.K + a.k_chunk - 1) / a.k_chunk);
