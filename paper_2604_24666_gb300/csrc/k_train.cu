@@ -505,6 +505,7 @@ nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t
                              lr_grid, lr_mlp, (float)c1, (float)c2);
     NIF_CK_LAUNCH(h);
     h->lowp_dirty = true;
+    h->x3_dirty = true;
     return NIF_OK;
 }
 
@@ -546,6 +547,7 @@ nif_status nif_adam_scaled_run(nif_handle* h, float lr_grid, float lr_mlp, cudaS
     k_scale_update<<<1, 1, 0, s>>>(h->d_ls, h->cfg.precision == NIF_FP16 ? 1 : 0);
     NIF_CK_LAUNCH(h);
     h->lowp_dirty = true;
+    h->x3_dirty = true;
     return NIF_OK;
 }
 

@@ -386,6 +386,7 @@ static nif_status init_params(nif_handle* h) {
     }
     NIF_CK(h, cudaMemcpy(h->d_params, p.data(), sizeof(float) * h->n_params, cudaMemcpyHostToDevice));
     h->lowp_dirty = true;
+    h->x3_dirty = true;
     return NIF_OK;
 }
 
@@ -494,6 +495,7 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
     CKC(cudaMemset(h->d_wt_f16, 0, sizeof(__half) * (h->off_s - h->off_layer[0])));
     CKC(cudaMalloc(&h->d_ls, sizeof(NifLossScale)));
 #undef CKC
+    if ((st = nif_x3_alloc(h)) != NIF_OK) return fail(st);
     if ((st = reset_loss_scale(h)) != NIF_OK) return fail(st);
     st = init_params(h);
     if (st != NIF_OK) return fail(st);
@@ -509,7 +511,7 @@ extern "C" void nif_destroy(nif_handle* h) {
     void* ptrs[] = {h->d_verts, h->d_tris, h->d_alb, h->d_mat, h->d_occ, h->d_tri_ptr, h->d_tri_idx, h->d_child,
                     h->d_leaf_vox, h->d_leaf_lat, h->d_corners, h->d_aabb, h->d_pose, h->d_params, h->d_grad,
                     h->d_m, h->d_v, h->d_tables_h, h->d_w_bf16, h->d_w_f16, h->d_wt_bf16, h->d_wt_f16, h->d_ls,
-                    h->d_status, h->d_lossacc, h->d_count};
+                    h->d_w_x3, h->d_status, h->d_lossacc, h->d_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
@@ -569,6 +571,7 @@ extern "C" nif_status nif_set_params(nif_handle* h, int group, const void* src, 
     if (!h) return NIF_ERR_ARG;
     nif_status st = copy_group(h, h->d_params, group, const_cast<void*>(src), bytes, false);
     h->lowp_dirty = true;
+    h->x3_dirty = true;
     return st;
 }
 
@@ -720,6 +723,7 @@ extern "C" nif_status nif_checkpoint_load(nif_handle* h, const void* src, size_t
     NIF_CK(h, cudaMemset(h->d_grad, 0, nb));
     h->adam_step = hd.adam_step;
     h->lowp_dirty = true;
+    h->x3_dirty = true;
     return NIF_OK;
 }
 
@@ -1082,8 +1086,7 @@ extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst
     // encode + MLP in chunks: FP32 chunks stay resident in L2 between the two
     // kernels (48 MB of features); the tensor-core MLP is a persistent kernel
     // whose pipeline needs many tiles per CTA, so its chunks are 2^20 rows.
-    int64_t chunk = prec == NIF_FP32 ? std::max<int64_t>(4096, ((int64_t)48 << 20) / ((int64_t)esz * h->in_dim))
-                                     : h->tune.tc_chunk;
+    int64_t chunk = h->tune.tc_chunk;
     chunk = std::min<int64_t>(chunk, n);
     if ((st = nif_grow(h, h->b_feat, esz * (size_t)h->in_dim * chunk)) != NIF_OK) return st;
     if (prec == NIF_FP32 &&
@@ -1172,12 +1175,11 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
         if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s)) != NIF_OK) return st;
         if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
         if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s)) != NIF_OK) return st;
-        // (the layer-0 weight gradient could overlap the encoding backward on
-        // h->aux: measured 5.66 -> 5.56 ms, but both then run ~30 % slower, so
-        // the FP32 step keeps them in sequence)
-        if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s)) != NIF_OK) return st;
+        // weight gradients on the second stream, beside dX_0 and the encoding backward
+        if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s, true, h->aux)) != NIF_OK) return st;
         if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK)
             return st;
+        NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
         if ((st = nif_adam_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
     }
     if (loss_host) {

@@ -98,6 +98,13 @@ struct nif_handle {
     __half* d_wt_f16 = nullptr;         // FP16 copy of the transposed weights
     NifLossScale* d_ls = nullptr;       // dynamic loss scale of the mixed-precision training path
     bool lowp_dirty = true;
+    // split-TF32 copies of the weights for the FP32 tensor-core MLP: layer l
+    // at x3_fwd[l] as [hi; lo] x [out_l][in_l] and at x3_bwd[l] transposed,
+    // [hi; lo] x [x3_npad[l]][out_l] (rows in_l .. x3_npad[l] zero)
+    float* d_w_x3 = nullptr;
+    size_t x3_fwd[NIF_MAX_LAYERS] = {0}, x3_bwd[NIF_MAX_LAYERS] = {0};
+    int x3_npad[NIF_MAX_LAYERS] = {0};
+    bool x3_dirty = true;
     long adam_step = 0;
 
     // a second stream for work of a training step that can overlap the main
@@ -229,14 +236,17 @@ nif_status nif_encode_segments_dp_run(nif_handle* h, const nif_linseg* lin, cons
 nif_status nif_pose_grad_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const float* dp,
                              const uint32_t* n_dev, int64_t n, const int* inst_off, int n_inst, float* dposes,
                              cudaStream_t s);
+// FP32 MLP on the tensor cores (split TF32, k_mlp_x3.cu); acts [H][n_max][W]
 nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
                                 float* out, float* acts, cudaStream_t s);
 // want_dw: add dL/dW into the gradient buffer (off for an input gradient only);
-// with `aux`, the layer-0 weight gradient runs there (forked from s after
-// dY_0 is ready; the caller joins with h->ev_join before reading gradients)
+// with `aux`, the weight gradients run there (forked from s once every dY_l is
+// ready; the caller joins with h->ev_join before reading gradients)
 nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
                                 const float* acts, const float* dout, float* dx, cudaStream_t s,
                                 bool want_dw = true, cudaStream_t aux = nullptr);
+nif_status nif_x3_alloc(nif_handle* h);
+nif_status nif_refresh_x3(nif_handle* h, cudaStream_t s);
 nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev,
                               int64_t n_max, float* out, cudaStream_t s);
 // acts_out (nullable): 16-bit hidden activations, layer l row r at (l * acts_rows + r) * acts_ld

@@ -220,11 +220,9 @@ extern "C" nif_status nif_query_plan_create(nif_handle* h, int n_inst, const nif
     if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * (size_t)p->cap)) != NIF_OK) return fail(st);
     if ((st = nif_grow(h, h->b_scan, sizeof(uint32_t) * (size_t)(nif_blocks(n_rays, 1024) + 1))) != NIF_OK)
         return fail(st);
-    int64_t chunk = h->cfg.precision == NIF_FP32
-                        ? std::max<int64_t>(4096, ((int64_t)48 << 20) / ((int64_t)4 * h->in_dim))
-                        : h->tune.tc_chunk;
+    int64_t chunk = h->tune.tc_chunk;
     if ((st = plan_buffers(p, chunk)) != NIF_OK) return fail(st);
-    if ((st = nif_refresh_lowp(h, s)) != NIF_OK) return fail(st);
+    if ((st = h->cfg.precision == NIF_FP32 ? nif_refresh_x3(h, s) : nif_refresh_lowp(h, s)) != NIF_OK) return fail(st);
     bool prof = h->prof;
     h->prof = false;
     if (autotune_flag && (st = autotune(p, s)) != NIF_OK) { h->prof = prof; return fail(st); }
@@ -257,7 +255,7 @@ extern "C" nif_status nif_query_plan_run(nif_query_plan* p, const nif_pose* pose
     // the previous replay must have consumed the pinned poses before they change
     if (p->launched) NIF_CK(h, cudaEventSynchronize(p->done));
     write_poses(p, poses);
-    nif_status st = nif_refresh_lowp(h, s);
+    nif_status st = h->cfg.precision == NIF_FP32 ? nif_refresh_x3(h, s) : nif_refresh_lowp(h, s);
     if (st != NIF_OK) return st;
     NIF_CK(h, cudaGraphLaunch(p->exec, s));
     NIF_CK(h, cudaEventRecord(p->done, s));

@@ -171,7 +171,10 @@ def test_scaled_adam_and_overflow_skip(nif, torus):
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_mixed_training_converges_like_fp32(nif, torus, prec):
     """4000 steps of 2^16 segments on the 16^3 torus from the same seed; the
-    occupancy BCE and log-distance error are the means of the last 10 steps.
+    occupancy BCE and log-distance error are the means of the last 100 steps
+    (training is not bitwise reproducible -- float atomics reduce in any order
+    -- and a 10-step mean caught one late spike of the distance loss: repeated
+    BF16 runs gave 0.123, 0.126, 0.137 and once 0.239).
     The occupancy loss of every path sits on a plateau near 0.45-0.5 for the
     first 1200-1800 steps and then falls (FP32 earliest, BF16 latest), so the
     comparison is made well after it. Both paths end below a tenth (BCE) and
@@ -191,7 +194,7 @@ def test_mixed_training_converges_like_fp32(nif, torus, prec):
         h = nif.Nif(net, torus, seed=7, **kw)
         first, tail = None, []
         for step in range(4000):
-            want = step == 0 or step >= 3990
+            want = step == 0 or step >= 3900
             loss, _ = nif.nif_train_step(h.h, 1 << 16, 16, 1000 + step, lr_grid=1e-2, lr_mlp=5e-3, want_loss=want)
             if step == 0:
                 first = np.array([loss[5], loss[1]])
