@@ -184,6 +184,23 @@ __device__ __forceinline__ int find_inst(const int* inst_off, int n_inst, int r)
     return lo;
 }
 
+// Sorting one ray's row of segments by (t0, voxel), in place by insertion
+// (rows are short: a few segments per ray).
+__device__ __forceinline__ void sort_row_inplace(nif_segment* segs, int64_t base, int64_t end) {
+    for (int64_t a = base + 1; a < end; a++) {
+        nif_segment key = segs[a];
+        int64_t b = a - 1;
+        while (b >= base) {
+            nif_segment o = segs[b];
+            bool gt = o.t0 > key.t0 || (o.t0 == key.t0 && o.voxel > key.voxel);
+            if (!gt) break;
+            segs[b + 1] = o;
+            b--;
+        }
+        segs[b + 1] = key;
+    }
+}
+
 constexpr int kStack = 96;
 
 // Modes of the traversal kernel
@@ -318,18 +335,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 32 / kTravWarps) k_seg_traver
     // sort this ray's segments by (t0, voxel): short runs
     int64_t base = offsets[r], end = offsets[r + 1];
     if (end > cap) end = cap;
-    for (int64_t a = base + 1; a < end; a++) {
-        nif_segment key = segs[a];
-        int64_t b = a - 1;
-        while (b >= base) {
-            nif_segment o = segs[b];
-            bool gt = o.t0 > key.t0 || (o.t0 == key.t0 && o.voxel > key.voxel);
-            if (!gt) break;
-            segs[b + 1] = o;
-            b--;
-        }
-        segs[b + 1] = key;
-    }
+    sort_row_inplace(segs, base, end);
 }
 
 // Moves the ray-unordered segments of kModeTemp to their ray's CSR rows
@@ -347,25 +353,35 @@ __global__ void __launch_bounds__(256) k_seg_scatter(const nif_segment* __restri
     }
 }
 
-// ... and sorts every ray's row by (t0, voxel).
+// ... and sorts every ray's row by (t0, voxel). A warp takes 32 consecutive
+// rays, whose rows are one contiguous range: it is loaded into shared memory
+// with coalesced 16-byte accesses, each lane sorts its ray's row there, and
+// the range goes back the same way (a range longer than kSortCap segments is
+// sorted in place in global memory).
+constexpr int kSortCap = 256;
+
 __global__ void __launch_bounds__(256) k_seg_sort(const uint32_t* __restrict__ offsets, int n_rays,
                                                   nif_segment* __restrict__ segs, int64_t cap) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rays) return;
-    int64_t base = offsets[r], end = offsets[r + 1];
-    if (end > cap) end = cap;
-    for (int64_t a = base + 1; a < end; a++) {
-        nif_segment key = segs[a];
-        int64_t b = a - 1;
-        while (b >= base) {
-            nif_segment o = segs[b];
-            bool gt = o.t0 > key.t0 || (o.t0 == key.t0 && o.voxel > key.voxel);
-            if (!gt) break;
-            segs[b + 1] = o;
-            b--;
-        }
-        segs[b + 1] = key;
+    __shared__ nif_segment sh[8][kSortCap];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = (blockIdx.x * 8 + warp) * 32;
+    if (r0 >= n_rays) return;
+    const int r = r0 + lane;
+    const int r1 = r0 + 32 < n_rays ? r0 + 32 : n_rays;
+    auto clampc = [&](int64_t v) { return v < cap ? v : cap; };
+    const int64_t b = clampc(offsets[r0]), e = clampc(offsets[r1]);
+    const int64_t mb = r < n_rays ? clampc(offsets[r]) : e;
+    const int64_t me = r < n_rays ? clampc(offsets[r + 1]) : e;
+    const int64_t len = e - b;
+    if (len > kSortCap) {
+        sort_row_inplace(segs, mb, me);
+        return;
     }
+    for (int64_t i = lane; i < len; i += 32) sh[warp][i] = segs[b + i];
+    __syncwarp();
+    sort_row_inplace(sh[warp], mb - b, me - b);
+    __syncwarp();
+    for (int64_t i = lane; i < len; i += 32) segs[b + i] = sh[warp][i];
 }
 
 // ---------------------------------------------------------------------------
@@ -608,7 +624,7 @@ nif_status nif_seg_scatter_run(nif_handle* h, const nif_segment* temp, const uin
     if (g > gcap) g = gcap;
     k_seg_scatter<<<g, 256, 0, s>>>(temp, n_temp, n_temp_max, offsets, fill, segs, cap);
     NIF_CK_LAUNCH(h);
-    k_seg_sort<<<nif_blocks(n_rays, 256), 256, 0, s>>>(offsets, n_rays, segs, cap);
+    k_seg_sort<<<nif_blocks(n_rays, 256), 256, 0, s>>>(offsets, n_rays, segs, cap);   // 8 warps x 32 rays
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
