@@ -306,6 +306,7 @@ def run_ours(args):
     batch = run_batch(args, nif, S, dev, rank) if not args.no_batch else None
     precision = run_precision(args, nif, S, dev) if (not args.no_precision and rank == 0) else None
     frame = run_frame(args, nif, S, dev) if (not args.no_frame and rank == 0) else None
+    trav = run_traversal(args, nif, S, dev) if (not args.no_traversal and rank == 0) else None
 
     if rank != 0:
         return 0
@@ -330,7 +331,7 @@ def run_ours(args):
                        "l2": "working set larger than L2 (tables, gradients, Adam state 256 MB; features 604 MB)"},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "loss": list(loss) if loss is not None else None, "train_mixed": mixed,
-            "query": query, "batch": batch, "frame_loop": frame,
+            "query": query, "batch": batch, "frame_loop": frame, "traversal": trav,
             "precision": precision}
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -389,6 +390,58 @@ def h_seg_per_ray(h, nif):
     rays = nif.nif_sample_rays(h.h, 4242, 0, 8192)
     _, segs = nif.nif_segments(h.h, [(0.0, 0.0, 0.0)], rays)
     return segs.shape[0] / 8192
+
+
+def run_traversal(args, nif, S, dev):
+    """Segment generation two ways on the same rays and pose: the library's
+    enumeration of every occupied hull through the octree, and the paper's
+    traversal (Sec. 2.1: BVH first hit, then the walk through the exit faces of
+    the deformed voxels, a new BVH query after leaving the grid); plus the
+    walk's first BVH query alone, the BVH part the paper quotes at 2-3 % of its
+    cost (Sec. 3.2). Count passes only (per-ray counts, which the segment lists
+    are written from), GPU time of each stage from the library's profile."""
+    import ctypes
+    import torch
+    out = {}
+    for wname, n in ((QUERY_WORKLOAD, 1 << 22), (TRAIN_WORKLOAD, 1 << 20)):
+        w = S.WORKLOADS[wname]
+        mesh = S.make_mesh(w["shape"])
+        rays = torch.from_numpy(S.sphere_rays(n, seed=950)).to(dev)
+        p, n_inst = nif._poses(S.poses(1, seed=951))
+        h = nif.Nif(w["net"], mesh, seed=31)
+        offs = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+        total = nif._i64()
+        L = nif.lib()
+
+        def enumerate_():
+            nif._check(h.h, L.nif_segments(h.h, p, n_inst, nif._ptr(rays), None, n, nif._ptr(offs), None, 0,
+                                           ctypes.byref(total), None))
+
+        def walk(flags):
+            nif._check(h.h, L.nif_segments_walk(h.h, p, n_inst, nif._ptr(rays), None, n, nif._ptr(offs), None, 0,
+                                                ctypes.byref(total), flags, None))
+
+        enumerate_()
+        n_seg = total.value
+        walk(0)
+        n_seg_walk = total.value          # equal to n_seg but for rays through tied hull decisions
+        walk(nif.NIF_WALK_FIRST_HIT)
+        reps = 3
+        nif.nif_profile(h.h, 1)
+        for _ in range(reps):
+            enumerate_()
+            walk(0)
+            walk(nif.NIF_WALK_FIRST_HIT)
+        prof = nif.nif_profile_read(h.h)
+        nif.nif_profile(h.h, 0)
+        h.close()
+        ms = {k: v[0] / reps for k, v in prof.items()}
+        e, wk, lt, f = ms.get("seg_count", 0.0), ms.get("walk_count", 0.0), ms.get("walk_lattice", 0.0), ms.get(
+            "walk_first", 0.0)
+        out[wname] = {"rays": n, "segments": n_seg, "segments_walk": n_seg_walk, "enumerate_ms": e, "walk_ms": wk, "walk_lattice_ms": lt,
+                      "bvh_first_hit_ms": f, "walk_over_enumerate": (wk + lt) / e if e else None,
+                      "bvh_share_of_walk": f / (wk + lt) if wk else None}
+    return out
 
 
 def run_query(args, nif, S, dev, rank):
@@ -653,6 +706,8 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the per-output precision study")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision training measurement")
     ap.add_argument("--no-frame", action="store_true", help="skip the animated frame loop")
+    ap.add_argument("--no-traversal", action="store_true", help="skip the enumeration vs exit-face walk comparison")
+    ap.add_argument("--only-traversal", action="store_true", help="measure only the traversal comparison (profiling aid)")
     ap.add_argument("--frames", type=int, default=120, help="frames of the animated frame loop")
     ap.add_argument("--frame-pretrain", type=int, default=1500, help="training steps before the frame loop")
     args = ap.parse_args()
@@ -667,6 +722,14 @@ def main():
         B.build()
         from paper_2604_24666_gb300 import nif, synth as S
         print(json.dumps({"query": run_query(args, nif, S, torch.device("cuda:0"), 0)}), flush=True)
+        return 0
+    if args.only_traversal:
+        import torch
+        torch.cuda.set_device(0)
+        from paper_2604_24666_gb300 import build as B
+        B.build()
+        from paper_2604_24666_gb300 import nif, synth as S
+        print(json.dumps({"traversal": run_traversal(args, nif, S, torch.device("cuda:0"))}), flush=True)
         return 0
     return run_ours(args)
 

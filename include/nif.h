@@ -221,6 +221,25 @@ nif_status nif_segments(nif_handle* h, const nif_pose* poses_host, int n_inst,
                         uint32_t* ray_offsets_dev, nif_segment* segs_dev, int64_t seg_cap,
                         int64_t* n_segs_host, void* stream);
 
+/* Segment list by the traversal the paper describes (Sec. 2.1): a BVH query
+ * for the first occupied deformed voxel on the ray, then a walk through the
+ * exit faces of the deformed voxels (empty ones included), emitting every
+ * occupied voxel entered, and a new BVH query past the exit whenever the ray
+ * leaves the deformed grid. Same arguments, definition of a segment and
+ * outputs as nif_segments (the two lists are equal wherever no hull decision
+ * is tied); it exists to compare the paper's traversal with nif_segments'
+ * enumeration of every occupied hull. flags: 0, or NIF_WALK_FIRST_HIT to run
+ * only the first BVH query (segs_dev must then be NULL; ray_offsets_dev gets
+ * the prefix sum of 1 per ray whose query finds a hull) -- the BVH part of
+ * the traversal alone, for timing. Uses a device copy of the deformed
+ * lattice, (N+1)^3 x 16 bytes per instance, grown on demand. Blocks the host
+ * like nif_segments. */
+#define NIF_WALK_FIRST_HIT 1u
+nif_status nif_segments_walk(nif_handle* h, const nif_pose* poses_host, int n_inst,
+                             const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
+                             uint32_t* ray_offsets_dev, nif_segment* segs_dev, int64_t seg_cap,
+                             int64_t* n_segs_host, unsigned flags, void* stream);
+
 /* Local linearization (Sec. 2): lin_dev[s] from segs_dev[s] for s < n_segs. */
 nif_status nif_linearize(nif_handle* h, const nif_pose* poses_host, int n_inst,
                          const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,

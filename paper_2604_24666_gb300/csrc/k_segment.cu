@@ -338,6 +338,259 @@ __global__ void __launch_bounds__(kTravWarps * 32, 32 / kTravWarps) k_seg_traver
     sort_row_inplace(segs, base, end);
 }
 
+// ---------------------------------------------------------------------------
+// Exit-face walk: the traversal the paper describes (Sec. 2.1). A BVH query
+// finds the first occupied hull on the ray; from there the ray walks from
+// voxel to voxel through the faces of the deformed hexahedra, empty voxels
+// included, emitting the segment of every occupied voxel it enters; when it
+// leaves the deformed grid (which is not convex under bending) the BVH is
+// queried again for the next occupied hull past the exit. The emitted set is
+// the one the enumeration above gives by definition (every segment's t comes
+// from the same hull test on the same corners); the walk exists to measure
+// the paper's design against the enumeration on this hardware.
+// ---------------------------------------------------------------------------
+// every lattice point of every instance deformed: [inst][(N+1)^3] (x, y, z, 0),
+// computed as k_refit_leaves computes the corners of the occupied voxels
+__global__ void k_lattice(int N, int n_inst, const float4* __restrict__ poses, float4* __restrict__ lat) {
+    const int M = N + 1;
+    const int64_t per = (int64_t)M * M * M;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= per * n_inst) return;
+    const int inst = (int)(gid / per);
+    const int64_t p = gid - (int64_t)inst * per;
+    const int i = (int)(p % M), j = (int)((p / M) % M), k = (int)(p / ((int64_t)M * M));
+    const float invN = 1.0f / (float)N;
+    const float3 y = nif_deform(make_float3((float)i * invN, (float)j * invN, (float)k * invN), poses[inst]);
+    lat[gid] = make_float4(y.x, y.y, y.z, 0.f);
+}
+
+// voxel id -> leaf index of the octree (-1: empty)
+__global__ void k_vox_leaf(const uint32_t* __restrict__ leaf_vox, int n_leaves, int* __restrict__ map) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < n_leaves) map[leaf_vox[l]] = l;
+}
+
+// Woop et al. on one canonical triangle: true and t when the ray meets it
+__device__ __forceinline__ bool tri_t(const float* X, const float* Y, const float* Zs, int A, int B, int C,
+                                      float& t) {
+    float U = -edge_fn(X, Y, B, C);
+    float V = edge_fn(X, Y, A, C);
+    float W = -edge_fn(X, Y, A, B);
+    bool neg = (U < 0.f) || (V < 0.f) || (W < 0.f);
+    bool pos = (U > 0.f) || (V > 0.f) || (W > 0.f);
+    if (neg && pos) return false;
+    float det = __fadd_rn(__fadd_rn(U, V), W);
+    if (det == 0.f) return false;
+    float T = __fadd_rn(__fadd_rn(__fmul_rn(U, Zs[A]), __fmul_rn(V, Zs[B])), __fmul_rn(W, Zs[C]));
+    t = __fdiv_rn(T, det);
+    return true;
+}
+
+// Exit of a hull (8 corners c[3*k..] in lattice order): the face other than
+// f_in hit at the smallest t >= t_in (t > t_in when f_in < 0); -1 when none.
+// Faces 0..5 are x = 0, x = 1, y = 0, y = 1, z = 0, z = 1; their triangles
+// are the canonical ones of hull_segment, so the two voxels of a shared face
+// take the same decisions.
+__device__ __forceinline__ int hull_exit(const RayPre& r, const float* c, int f_in, float t_in, float& t_out) {
+    float X[8], Y[8], Zs[8];
+    const float o[3] = {r.ox, r.oy, r.oz};
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        float A[3] = {__fsub_rn(c[3 * k], o[0]), __fsub_rn(c[3 * k + 1], o[1]), __fsub_rn(c[3 * k + 2], o[2])};
+        float ax = r.kx == 0 ? A[0] : (r.kx == 1 ? A[1] : A[2]);
+        float ay = r.ky == 0 ? A[0] : (r.ky == 1 ? A[1] : A[2]);
+        float az = r.kz == 0 ? A[0] : (r.kz == 1 ? A[1] : A[2]);
+        X[k] = __fsub_rn(ax, __fmul_rn(r.Sx, az));
+        Y[k] = __fsub_rn(ay, __fmul_rn(r.Sy, az));
+        Zs[k] = __fmul_rn(r.Sz, az);
+    }
+    // triangles (lo, s1, hi), (lo, s2, hi) of each face
+    const int tri[6][4] = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5}, {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
+    int best = -1;
+    float bt = 3.0e38f;
+#pragma unroll
+    for (int f = 0; f < 6; f++) {
+        if (f == f_in) continue;
+        const int lo = tri[f][0], s1 = tri[f][1], s2 = tri[f][2], hi = tri[f][3];
+        float tt;
+#pragma unroll
+        for (int h2 = 0; h2 < 2; h2++) {
+            if (tri_t(X, Y, Zs, lo, h2 ? s2 : s1, hi, tt)) {
+                const bool ahead = f_in < 0 ? tt > t_in : tt >= t_in;
+                if (ahead && tt < bt) { bt = tt; best = f; }
+            }
+        }
+    }
+    t_out = bt;
+    return best;
+}
+
+// slab entry distance of a box, +inf when the ray misses it within [tmin, tmax]
+__device__ __forceinline__ float slab_t(const RayPre& r, float4 lo, float4 hi) {
+    float t0x = (lo.x - r.ox) * r.ix, t1x = (hi.x - r.ox) * r.ix;
+    float t0y = (lo.y - r.oy) * r.iy, t1y = (hi.y - r.oy) * r.iy;
+    float t0z = (lo.z - r.oz) * r.iz, t1z = (hi.z - r.oz) * r.iz;
+    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), r.tmin));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), r.tmax));
+    return tn <= tf ? tn : 3.0e38f;
+}
+
+// BVH query: the occupied hull whose segment starts first, t0 > t_after
+// (t0 >= t_after when incl); ties to the lower voxel id. Boxes that start
+// after the best t0 so far are not opened.
+__device__ __forceinline__ bool bvh_first(const RayPre& r, const TreeView& tree, const float4* A,
+                                          const float* corners, float t_after, bool incl, int& leaf_out,
+                                          float& t0_out, float& t1_out, int* status) {
+    int stack[kStack];
+    int sp = 0;
+    for (int q = tree.top_begin + tree.top_count - 1; q >= tree.top_begin; q--)
+        if (slab_t(r, __ldg(A + 2 * q), __ldg(A + 2 * q + 1)) < 3.0e38f) stack[sp++] = q;
+    float best = 3.0e38f;
+    uint32_t best_vox = 0xFFFFFFFFu;
+    leaf_out = -1;
+    while (sp > 0) {
+        const int node = stack[--sp];
+        if (node < tree.n_leaves) {
+            float t0, t1;
+            if (hull_segment(r, corners + (int64_t)node * 24, t0, t1)) {
+                const uint32_t vox = __ldg(tree.leaf_vox + node);
+                const bool after = incl ? t0 >= t_after : t0 > t_after;
+                if (after && (t0 < best || (t0 == best && vox < best_vox))) {
+                    best = t0;
+                    best_vox = vox;
+                    leaf_out = node;
+                    t0_out = t0;
+                    t1_out = t1;
+                }
+            }
+            continue;
+        }
+        const int2 ch = __ldg(tree.child + (node - tree.n_leaves));
+        if (sp + ch.y > kStack || ch.y > 8) {
+            nif_set_status(status, NIF_ERR_CAPACITY);
+            return false;
+        }
+        // children the ray meets before the best start so far, pushed farthest
+        // first so that the nearest box is opened next
+        float ct[8];
+        int cn[8];
+        int m = 0;
+        for (int c = ch.x; c < ch.x + ch.y; c++) {
+            const float tn = slab_t(r, __ldg(A + 2 * c), __ldg(A + 2 * c + 1));
+            if (tn < 3.0e38f && tn <= best) {
+                int k = m++;
+                while (k > 0 && ct[k - 1] < tn) {
+                    ct[k] = ct[k - 1];
+                    cn[k] = cn[k - 1];
+                    k--;
+                }
+                ct[k] = tn;
+                cn[k] = c;
+            }
+        }
+        for (int k = 0; k < m; k++) stack[sp++] = cn[k];
+    }
+    return leaf_out >= 0;
+}
+
+enum { kWalkCount = 0, kWalkEmit = 1, kWalkFirst = 2 };
+constexpr int kWalkRecent = 8;   // voxels emitted last, for re-entries of non-convex hulls
+
+// One thread per ray.
+//   kWalkCount: per-ray segment counts;
+//   kWalkEmit:  segments into the CSR rows [offsets[r], offsets[r+1]), each row
+//               then sorted by (t0, voxel);
+//   kWalkFirst: 1 where the first BVH query finds a hull (the walk skipped):
+//               the BVH part of the traversal alone, for timing.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_seg_walk(const nif_ray* __restrict__ rays, const int* __restrict__ inst_off,
+                                                  int n_inst, int n_rays, int N, TreeView tree,
+                                                  const float* __restrict__ corners, const float4* __restrict__ aabb,
+                                                  const float4* __restrict__ lat, const int* __restrict__ vox_leaf,
+                                                  uint32_t* __restrict__ counts, const uint32_t* __restrict__ offsets,
+                                                  nif_segment* __restrict__ segs, int64_t cap, int* status) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const int inst = find_inst(inst_off, n_inst, r);
+    const RayPre ray = ray_pre(rays, r);
+    const float4* A = aabb + (int64_t)inst * tree.n_nodes * 2;
+    const float* C = corners + (int64_t)inst * tree.n_leaves * 24;
+    const int M = N + 1;
+    const float4* Lt = lat + (int64_t)inst * M * M * M;
+    int64_t base = 0, lim = 0;
+    if (MODE == kWalkEmit) {
+        base = offsets[r];
+        lim = (int64_t)offsets[r + 1] < cap ? (int64_t)offsets[r + 1] : cap;
+    }
+    uint32_t cnt = 0;
+    uint32_t recent[kWalkRecent];
+    int nrec = 0;
+    float t_after = ray.tmin;
+    bool incl = true;
+    const int max_steps = 4 * N + 16;
+    // every query past the first starts beyond the voxels walked so far and
+    // finds a new hull, so the number of queries is bounded by the leaves
+    for (int q = 0; q <= tree.n_leaves; q++) {
+        int leaf;
+        float t0, t1;
+        if (!bvh_first(ray, tree, A, C, t_after, incl, leaf, t0, t1, status)) break;
+        if (MODE == kWalkFirst) { cnt = 1; break; }
+        const uint32_t vox0 = __ldg(tree.leaf_vox + leaf);
+        int ci = (int)(vox0 % (uint32_t)N), cj = (int)((vox0 / (uint32_t)N) % (uint32_t)N),
+            ck = (int)(vox0 / ((uint32_t)N * (uint32_t)N));
+        int f_in = -1;
+        float t_in = t0, t_exit = t0;
+        bool first = true;
+        for (int step = 0; step < max_steps; step++) {
+            const uint32_t v = (uint32_t)ci + (uint32_t)N * ((uint32_t)cj + (uint32_t)N * (uint32_t)ck);
+            const int lf = first ? leaf : __ldg(vox_leaf + v);
+            if (lf >= 0) {
+                bool seen = false;
+                for (int i = 0; i < kWalkRecent && i < nrec; i++) seen |= recent[i] == v;
+                float s0 = t0, s1 = t1;
+                if (!seen && (first || hull_segment(ray, C + (int64_t)lf * 24, s0, s1))) {
+                    if (MODE == kWalkEmit && base + cnt < lim) segs[base + cnt] = nif_segment{(uint32_t)r, v, s0, s1};
+                    cnt++;
+                    recent[nrec % kWalkRecent] = v;
+                    nrec++;
+                }
+            }
+            first = false;
+            float c[24];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int64_t idx = (int64_t)(ci + (k & 1)) +
+                                    (int64_t)M * ((cj + ((k >> 1) & 1)) + (int64_t)M * (ck + ((k >> 2) & 1)));
+                const float4 pnt = __ldg(Lt + idx);
+                c[3 * k] = pnt.x;
+                c[3 * k + 1] = pnt.y;
+                c[3 * k + 2] = pnt.z;
+            }
+            float t_out;
+            const int f = hull_exit(ray, c, f_in, t_in, t_out);
+            if (f < 0 || t_out > ray.tmax) {   // no exit found (or past tmax): query again past this entry
+                t_exit = t_in;
+                break;
+            }
+            ci += f == 0 ? -1 : (f == 1 ? 1 : 0);
+            cj += f == 2 ? -1 : (f == 3 ? 1 : 0);
+            ck += f == 4 ? -1 : (f == 5 ? 1 : 0);
+            t_exit = t_out;
+            if (ci < 0 || ci >= N || cj < 0 || cj >= N || ck < 0 || ck >= N) break;   // left the deformed grid
+            f_in = f ^ 1;
+            t_in = t_out;
+        }
+        t_after = t_exit;
+        incl = false;
+    }
+    if (MODE != kWalkEmit) {
+        counts[r] = cnt;
+        return;
+    }
+    const int64_t end = base + (int64_t)cnt < lim ? base + (int64_t)cnt : lim;
+    sort_row_inplace(segs, base, end);
+}
+
 // Moves the ray-unordered segments of kModeTemp to their ray's CSR rows
 // (fill[] zeroed, one counter per ray) ...
 __global__ void __launch_bounds__(256) k_seg_scatter(const nif_segment* __restrict__ temp, const uint32_t* __restrict__ n_temp,
@@ -562,6 +815,52 @@ static TreeView tree_view(nif_handle* h) {
     t.child = h->d_child;
     t.leaf_vox = h->d_leaf_vox;
     return t;
+}
+
+// Exit-face walk (k_seg_walk): the deformed lattice of every instance (the
+// handle's current poses), the voxel -> leaf map on first use, then one walk
+// launch. mode: 0 counts, 1 emits into `offsets` rows, 2 first BVH query only.
+nif_status nif_seg_walk_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                            uint32_t* counts, const uint32_t* offsets, nif_segment* segs, int64_t cap, int mode,
+                            cudaStream_t s) {
+    if (n_rays <= 0) return NIF_OK;
+    if (h->n_leaves == 0) {
+        if (mode != 1) NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * n_rays, s));
+        return NIF_OK;
+    }
+    nif_status st;
+    if (mode != 2) {
+        NifProf prof_(h, "walk_lattice", s);
+        const int64_t M = h->N + 1, per = M * M * M;
+        if ((st = nif_grow(h, h->b_lattice, sizeof(float4) * (size_t)(per * n_inst))) != NIF_OK) return st;
+        k_lattice<<<nif_blocks(per * n_inst, 256), 256, 0, s>>>(h->N, n_inst, h->d_pose, (float4*)h->b_lattice.p);
+        NIF_CK_LAUNCH(h);
+        if (!h->d_vox_leaf) {
+            const size_t nv = (size_t)h->N * h->N * h->N;
+            NIF_CK(h, cudaMalloc(&h->d_vox_leaf, sizeof(int) * nv));
+            NIF_CK(h, cudaMemsetAsync(h->d_vox_leaf, 0xFF, sizeof(int) * nv, s));
+            k_vox_leaf<<<nif_blocks(h->n_leaves, 256), 256, 0, s>>>(h->d_leaf_vox, h->n_leaves, h->d_vox_leaf);
+            NIF_CK_LAUNCH(h);
+        }
+    }
+    const TreeView tv = tree_view(h);
+    const float4* lat = (const float4*)h->b_lattice.p;
+    const unsigned g = nif_blocks(n_rays, 128);
+    if (mode == 0) {
+        NifProf prof_(h, "walk_count", s);
+        k_seg_walk<kWalkCount><<<g, 128, 0, s>>>(rays, inst_off, n_inst, n_rays, h->N, tv, h->d_corners, h->d_aabb,
+                                                 lat, h->d_vox_leaf, counts, nullptr, nullptr, 0, h->d_status);
+    } else if (mode == 1) {
+        NifProf prof_(h, "walk_emit", s);
+        k_seg_walk<kWalkEmit><<<g, 128, 0, s>>>(rays, inst_off, n_inst, n_rays, h->N, tv, h->d_corners, h->d_aabb,
+                                                lat, h->d_vox_leaf, nullptr, offsets, segs, cap, h->d_status);
+    } else {
+        NifProf prof_(h, "walk_first", s);
+        k_seg_walk<kWalkFirst><<<g, 128, 0, s>>>(rays, inst_off, n_inst, n_rays, h->N, tv, h->d_corners, h->d_aabb,
+                                                 lat, h->d_vox_leaf, counts, nullptr, nullptr, 0, h->d_status);
+    }
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
 }
 
 nif_status nif_seg_count_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,

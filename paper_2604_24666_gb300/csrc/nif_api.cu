@@ -511,12 +511,13 @@ extern "C" void nif_destroy(nif_handle* h) {
     void* ptrs[] = {h->d_verts, h->d_tris, h->d_alb, h->d_mat, h->d_occ, h->d_tri_ptr, h->d_tri_idx, h->d_child,
                     h->d_leaf_vox, h->d_leaf_lat, h->d_corners, h->d_aabb, h->d_pose, h->d_params, h->d_grad,
                     h->d_m, h->d_v, h->d_tables_h, h->d_w_bf16, h->d_w_f16, h->d_wt_bf16, h->d_wt_f16, h->d_ls,
-                    h->d_w_x3, h->d_status, h->d_lossacc, h->d_count};
+                    h->d_w_x3, h->d_vox_leaf, h->d_status, h->d_lossacc, h->d_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
                                &h->b_acts, &h->b_dout, &h->b_dx, &h->b_labels, &h->b_scan, &h->b_rays,
-                               &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys, &h->b_dup, &h->b_pts};
+                               &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys, &h->b_dup, &h->b_pts,
+                               &h->b_lattice};
     for (auto* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -796,6 +797,37 @@ extern "C" nif_status nif_segments(nif_handle* h, const nif_pose* poses, int n_i
         if ((st = nif_seg_count_run(h, rays, inst_off, n_inst, n_rays, counts, s)) != NIF_OK) return st;
         if ((st = nif_scan_run(h, counts, ray_offsets, n_rays, s)) != NIF_OK) return st;
     }
+    NIF_CK(h, cudaStreamSynchronize(s));
+    uint32_t tot = 0;
+    NIF_CK(h, cudaMemcpy(&tot, ray_offsets + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    if (n_segs_host) *n_segs_host = tot;
+    st = check_status(h, s);
+    if (st != NIF_OK) return st;
+    if (segs && (int64_t)tot > seg_cap) return nif_fail(h, NIF_ERR_CAPACITY, "segment capacity exceeded");
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_segments_walk(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                        const int* inst_off, int n_rays, uint32_t* ray_offsets, nif_segment* segs,
+                                        int64_t seg_cap, int64_t* n_segs_host, unsigned flags, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    if (!ray_offsets || (n_rays > 0 && !rays)) return nif_fail(h, NIF_ERR_ARG, "buffers");
+    if (flags & ~NIF_WALK_FIRST_HIT) return nif_fail(h, NIF_ERR_ARG, "unknown walk flags");
+    if ((flags & NIF_WALK_FIRST_HIT) && segs) return nif_fail(h, NIF_ERR_ARG, "NIF_WALK_FIRST_HIT counts only: segs must be NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
+    if ((st = nif_refit_run(h, n_inst, s)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_counts, sizeof(uint32_t) * ((size_t)n_rays + 1))) != NIF_OK) return st;
+    uint32_t* counts = (uint32_t*)h->b_counts.p;
+    const int mode = (flags & NIF_WALK_FIRST_HIT) ? 2 : 0;
+    if ((st = nif_seg_walk_run(h, rays, inst_off, n_inst, n_rays, counts, nullptr, nullptr, 0, mode, s)) != NIF_OK)
+        return st;
+    if ((st = nif_scan_run(h, counts, ray_offsets, n_rays, s)) != NIF_OK) return st;
+    if (segs && (st = nif_seg_walk_run(h, rays, inst_off, n_inst, n_rays, nullptr, ray_offsets, segs, seg_cap, 1, s)) !=
+                    NIF_OK)
+        return st;
     NIF_CK(h, cudaStreamSynchronize(s));
     uint32_t tot = 0;
     NIF_CK(h, cudaMemcpy(&tot, ray_offsets + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost));

@@ -122,7 +122,8 @@ struct nif_handle {
     // grown scratch buffers (query / train)
     struct Buf { void* p = nullptr; size_t bytes = 0; };
     Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
-        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts;
+        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts, b_lattice;
+    int* d_vox_leaf = nullptr;          // [N^3] octree leaf of each voxel, -1 when empty (exit-face walk)
     double query_seg_per_ray = 0.0;     // segments per ray of the last query (temp capacity hint)
 
     // launch knobs chosen by the autotuner (nif_query_plan_create)
@@ -245,6 +246,11 @@ nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n
 nif_status nif_mlp_bwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
                                 const float* acts, const float* dout, float* dx, cudaStream_t s,
                                 bool want_dw = true, cudaStream_t aux = nullptr);
+// exit-face walk of the deformed grid (k_segment.cu); mode 0 counts, 1 emits
+// into the rows of `offsets`, 2 counts 1 per ray whose first BVH query finds a hull
+nif_status nif_seg_walk_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
+                            uint32_t* counts, const uint32_t* offsets, nif_segment* segs, int64_t cap, int mode,
+                            cudaStream_t s);
 nif_status nif_x3_alloc(nif_handle* h);
 nif_status nif_refresh_x3(nif_handle* h, cudaStream_t s);
 nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev,

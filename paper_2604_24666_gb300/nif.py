@@ -114,6 +114,8 @@ def lib() -> ctypes.CDLL:
             "nif_sample_rays": ([_vp, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
             "nif_segments_noalloc": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _i64,
                                       ctypes.POINTER(_i64), _vp], ctypes.c_int),
+            "nif_segments_walk": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _i64,
+                                   ctypes.POINTER(_i64), ctypes.c_uint, _vp], ctypes.c_int),
             "nif_query_plan_create": ([_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _i64, ctypes.c_uint,
                                        ctypes.c_int, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
             "nif_query_plan_run": ([_vp, _vp, _vp], ctypes.c_int),
@@ -266,6 +268,28 @@ def nif_segments(h, poses, rays, inst_offsets=None, seg_cap=None, stream=None):
     total = _i64()
     _check(h, lib().nif_segments(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), n, _ptr(offs), _ptr(segs), seg_cap,
                                  ctypes.byref(total), _stream(stream)))
+    return offs, segs[:total.value]
+
+
+NIF_WALK_FIRST_HIT = 1
+
+
+def nif_segments_walk(h, poses, rays, inst_offsets=None, seg_cap=None, flags=0, stream=None):
+    """Segments by BVH first hit + exit-face walk (same outputs as nif_segments).
+    flags=NIF_WALK_FIRST_HIT: only the first BVH query; returns (ray_offsets, None)."""
+    p, n_inst = _poses(poses)
+    n = rays.shape[0]
+    offs = torch.zeros(n + 1, dtype=torch.int32, device=rays.device)
+    total = _i64()
+    if seg_cap is None or flags:
+        _check(h, lib().nif_segments_walk(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), n, _ptr(offs), None, 0,
+                                          ctypes.byref(total), flags, _stream(stream)))
+        if flags:
+            return offs, None
+        seg_cap = max(1, total.value)
+    segs = torch.zeros((seg_cap, 4), dtype=torch.int32, device=rays.device)
+    _check(h, lib().nif_segments_walk(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), n, _ptr(offs), _ptr(segs),
+                                      seg_cap, ctypes.byref(total), flags, _stream(stream)))
     return offs, segs[:total.value]
 
 
