@@ -10,6 +10,7 @@ The oracle follows the paper step by step, in float64:
   (Sec. 2), ray / deformed-voxel segments (Sec. 2.1-2.2), linearized-segment
   labels (Sec. 2), exact deformed-space hits;
 * the hybrid encoding psi = phi o gamma (Eq. 1, Sec. 2.3), its backward;
+  and the other reading of Eq. 1, the concatenation psi = [gamma, phi];
 * the MLP (Sec. 2, Fig. 2d) forward and backward, and the same with the
   16-bit storage points of the mixed-precision path rounded (Sec. 3);
 * the task losses and the uncertainty weighting (Sec. 2.4);
@@ -290,8 +291,23 @@ def encode_points(cfg, tables, p):
     return feats.reshape(n, -1)
 
 
+def encode_points_concat(cfg, tables, p):
+    """The concatenation reading of Eq. 1: psi(p) = [gamma(p), phi(p)] for rest
+    points p [n,3]: [n, 3P + L*F_d]. gamma as its raw values ordered
+    [term][coordinate] (x, then sin(2^k x), cos(2^k x) for k < F), phi the
+    grid at u = p (clamped to [0,1]^3), ordered [level][feature]."""
+    g, u = gamma(cfg, p)
+    n = g.shape[0]
+    return np.concatenate([g.reshape(n, -1), grid_encode(cfg, tables, u[:, 0]).reshape(n, -1)], 1)
+
+
 def encode_segments(cfg, tables, p0, p1):
-    """MLP input of a segment: psi(p0) (+) psi(p1) [S, 2*P*L*F_d]."""
+    """MLP input of a segment: psi(p0) (+) psi(p1), [S, 2*P*L*F_d]; with the
+    concatenation reading the two [S, 3P + L*F_d] halves, zero-padded to
+    cfg.in_dim columns."""
+    if getattr(cfg, "encoding", "composed") == "concat":
+        x = np.concatenate([encode_points_concat(cfg, tables, p0), encode_points_concat(cfg, tables, p1)], 1)
+        return np.pad(x, ((0, 0), (0, cfg.in_dim - x.shape[1])))
     return np.concatenate([encode_points(cfg, tables, p0), encode_points(cfg, tables, p1)], 1)
 
 
@@ -329,6 +345,41 @@ def encode_points_backward(cfg, tables, p, dfeat):
         dp += du[:, 2 + 2 * k, :] * (-0.5) * f * np.sin(f * pcl)
     dp = np.where(inside, dp, 0.0)
     return dtab, dp
+
+
+def encode_points_concat_backward(cfg, tables, p, dfeat):
+    """Gradients of sum(dfeat * [gamma(p), phi(p)]) (dfeat [n, 3P + L*F_d]):
+    (dtables [L,T,F_d], dp [n,3]). The table gradient comes from the phi part
+    only; dp adds d gamma/dp (1 for x, 2^k cos(2^k p) for sin, -2^k sin(2^k p)
+    for cos, per coordinate) and d phi/dp (the trilinear weights'
+    derivatives times N_l), zero where p was clamped."""
+    tables = np.asarray(tables, np.float64)
+    res = level_res(cfg)
+    pc = np.asarray(p, np.float64)
+    inside = (pc >= 0.0) & (pc <= 1.0)
+    pcl = np.clip(pc, 0.0, 1.0)
+    n, P = len(pc), cfg.n_terms
+    dfeat = np.asarray(dfeat, np.float64)
+    dg = dfeat[:, :3 * P].reshape(n, P, 3)
+    dphi = dfeat[:, 3 * P:3 * P + cfg.levels * cfg.feats].reshape(n, cfg.levels, cfg.feats)
+    dp = dg[:, 0, :].copy()
+    for k in range(cfg.pe_bands):
+        f = 2.0 ** k
+        dp += dg[:, 1 + 2 * k, :] * f * np.cos(f * pcl)
+        dp -= dg[:, 2 + 2 * k, :] * f * np.sin(f * pcl)
+    dtab = np.zeros_like(tables)
+    for l in range(cfg.levels):
+        i0, w = _cell(cfg, l, pcl)
+        gl = dphi[:, l, :]
+        for c in _CORNERS:
+            idx = grid_index(cfg, l, i0 + c)
+            fw = np.where(c == 1, w, 1.0 - w)
+            np.add.at(dtab[l], idx, np.prod(fw, axis=1)[:, None] * gl)
+            val = (tables[l][idx] * gl).sum(1)
+            for a in range(3):
+                sgn = 1.0 if c[a] == 1 else -1.0
+                dp[:, a] += sgn * np.prod(np.delete(fw, a, axis=1), axis=1) * res[l] * val
+    return dtab, np.where(inside, dp, 0.0)
 
 
 # ---------------------------------------------------------------------------
@@ -564,10 +615,12 @@ def pose_gradient(cfg, tables, pose, p0, p1, dfeat):
     dp/dtheta = -J_D(p)^-1 dD/dtheta(p); the encoding's input gradient comes
     from `encode_points_backward`.
     """
-    half = dfeat.shape[1] // 2
+    concat = getattr(cfg, "encoding", "composed") == "concat"
+    half = cfg.point_width if concat else dfeat.shape[1] // 2
+    back = encode_points_concat_backward if concat else encode_points_backward
     g = np.zeros(3)
-    for p, df in ((p0, dfeat[:, :half]), (p1, dfeat[:, half:])):
-        _, dp = encode_points_backward(cfg, tables, p, df)
+    for p, df in ((p0, dfeat[:, :half]), (p1, dfeat[:, half:2 * half])):
+        _, dp = back(cfg, tables, p, df)
         J, Jp = jacobians(pose, p)
         dpdth = -np.linalg.solve(J, Jp)            # [n, 3, 3]: d p_i / d theta_j
         g += np.einsum("ni,nij->j", dp, dpdth)

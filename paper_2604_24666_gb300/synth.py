@@ -249,14 +249,23 @@ class NetConfig:
     mlp_depth: int = 2         # hidden layers H
     mlp_width: int = 32        # W
     n_materials: int = 4       # M
+    encoding: str = "composed"  # Eq. 1 read as psi = phi o gamma ("composed") or [gamma, phi] ("concat")
 
     @property
     def n_terms(self) -> int:            # P = 1 + 2F
         return 1 + 2 * self.pe_bands
 
     @property
-    def in_dim(self) -> int:             # 2 endpoints * P * L * F_d
-        return 2 * self.n_terms * self.levels * self.feats
+    def point_width(self) -> int:        # features of one end point: P*L*F_d, or 3P + L*F_d concatenated
+        if self.encoding == "concat":
+            return 3 * self.n_terms + self.levels * self.feats
+        return self.n_terms * self.levels * self.feats
+
+    @property
+    def in_dim(self) -> int:             # 2 end points, padded to 16 columns when concatenated
+        if self.encoding == "concat":
+            return (2 * self.point_width + 15) // 16 * 16
+        return 2 * self.point_width
 
     @property
     def out_dim(self) -> int:            # occ, dist, normal(3), albedo(3), material(M)

@@ -463,6 +463,93 @@ def test_encoding_backward_matches_finite_differences():
             assert abs(fd - dp[s, a]) < 2e-3 * max(1, abs(dp[s, a])), (s, a)
 
 
+# The concatenation reading of Eq. 1, psi = [gamma, phi]
+def _tiny_concat_cfg():
+    return S.NetConfig(voxel_res=8, pe_bands=2, levels=3, feats=2, log2_table=6, base_res=2,
+                       growth=1.5, mlp_depth=2, mlp_width=8, n_materials=4, encoding="concat")
+
+
+def test_concat_gamma_bands_and_layout():
+    """gamma's raw values are pinned by identities between consecutive bands
+    (sin 2a = 2 sin a cos a, cos 2a = 1 - 2 sin^2 a), sin^2 + cos^2 = 1, and
+    a Taylor series for band 0; phi is the composed reading's x-term block;
+    the segment row is [psi(p0), psi(p1), zeros]."""
+    cfg = _tiny_concat_cfg()
+    rng = np.random.default_rng(20)
+    T = 1 << cfg.log2_table
+    tables = rng.uniform(-1, 1, (cfg.levels, T, 2))
+    p = rng.uniform(-0.1, 1.1, (50, 3))
+    p[0] = [1e-3, 2e-3, 0.5]
+    x = O.encode_points_concat(cfg, tables, p)
+    P = cfg.n_terms
+    assert x.shape == (50, 3 * P + cfg.levels * 2) and cfg.point_width == x.shape[1]
+    g = x[:, :3 * P].reshape(50, P, 3)
+    pc = np.clip(p, 0, 1)
+    np.testing.assert_array_equal(g[:, 0], pc)
+    for k in range(cfg.pe_bands):
+        s, c = g[:, 1 + 2 * k], g[:, 2 + 2 * k]
+        np.testing.assert_allclose(s * s + c * c, 1.0, atol=1e-14)
+        if k + 1 < cfg.pe_bands:
+            np.testing.assert_allclose(g[:, 3 + 2 * k], 2 * s * c, atol=1e-14)
+            np.testing.assert_allclose(g[:, 4 + 2 * k], 1 - 2 * s * s, atol=1e-14)
+    a = pc[0, :2]
+    np.testing.assert_allclose(g[0, 1, :2], a - a ** 3 / 6 + a ** 5 / 120, rtol=1e-12)
+    composed = S.NetConfig(**{**cfg.asdict(), "encoding": "composed"})
+    np.testing.assert_array_equal(x[:, 3 * P:], O.encode_points(composed, tables, p)[:, :cfg.levels * 2])
+    q = rng.uniform(0, 1, (50, 3))
+    row = O.encode_segments(cfg, tables, p, q)
+    w = cfg.point_width
+    assert row.shape == (50, cfg.in_dim) and cfg.in_dim % 16 == 0 and cfg.in_dim >= 2 * w
+    np.testing.assert_array_equal(row[:, :w], x)
+    np.testing.assert_array_equal(row[:, w:2 * w], O.encode_points_concat(cfg, tables, q))
+    assert not row[:, 2 * w:].any()
+
+
+def test_concat_backward_matches_finite_differences():
+    cfg = _tiny_concat_cfg()
+    rng = np.random.default_rng(21)
+    T = 1 << cfg.log2_table
+    tables = rng.uniform(-1, 1, (cfg.levels, T, 2))
+    p = rng.uniform(0.05, 0.95, (6, 3))
+    p[5] = [1.02, 0.43, -0.01]                      # clamped x and z: zero gradient there (y off every cell face)
+    w = rng.normal(size=(6, cfg.point_width))
+    dtab, dp = O.encode_points_concat_backward(cfg, tables, p, w)
+    f = lambda tb, pp: (O.encode_points_concat(cfg, tb, pp) * w).sum()
+    h = 1e-6
+    for (l, i, c) in [(0, 3, 0), (1, 10, 1), (2, 17, 0), (2, 40, 1)]:
+        e = np.zeros_like(tables); e[l, i, c] = h
+        fd = (f(tables + e, p) - f(tables - e, p)) / (2 * h)
+        assert abs(fd - dtab[l, i, c]) < 1e-7
+    hp = 1e-4
+    for s in range(len(p)):
+        for a in range(3):
+            e1 = np.zeros_like(p); e1[s, a] = hp
+            fd = (f(tables, p + e1) - f(tables, p - e1)) / (2 * hp)
+            assert abs(fd - dp[s, a]) < 2e-3 * max(1, abs(dp[s, a])), (s, a, fd, dp[s, a])
+    assert dp[5, 0] == 0 and dp[5, 2] == 0
+
+
+def test_concat_pose_gradient_matches_finite_differences():
+    cfg = _tiny_concat_cfg()
+    rng = np.random.default_rng(22)
+    T = 1 << cfg.log2_table
+    tables = rng.uniform(-1, 1, (cfg.levels, T, 2))
+    pose = np.array([0.4, -0.7, 0.5])
+    x0 = rng.uniform(0.2, 0.8, (8, 3))
+    x1 = x0 + rng.normal(0, 0.02, (8, 3))
+    w = rng.normal(size=(8, cfg.in_dim))
+
+    def f(th):
+        return (O.encode_segments(cfg, tables, O.inverse(th, x0), O.inverse(th, x1)) * w).sum()
+
+    g = O.pose_gradient(cfg, tables, pose, O.inverse(pose, x0), O.inverse(pose, x1), w)
+    h = 1e-3
+    for j in range(3):
+        e = np.zeros(3); e[j] = h
+        fd = (f(pose + e) - f(pose - e)) / (2 * h)
+        assert abs(fd - g[j]) <= 5e-3 * max(1.0, abs(fd)), (j, fd, g[j])
+
+
 # ---------------------------------------------------------------------------
 # MLP, losses, Adam
 # ---------------------------------------------------------------------------
