@@ -98,6 +98,15 @@ typedef struct {
  * for BF16. Sec. 3 of the paper trains with FP16 hash features and FP32
  * master copies; the scaling rule is ours. */
 #define NIF_FLAG_MIXED_TRAINING 4u
+/* NIF_FLAG_CONCAT_ENCODING: read Eq. 1 (Sec. 2.3) as the concatenation
+ * psi(p) = [gamma(p), phi(p)] instead of the default phi(gamma(p)). An end
+ * point then gives 3P + L*F_d features: gamma's raw values ordered
+ * [term][coordinate] (x, then sin(2^k x), cos(2^k x) for k < F) and the grid
+ * features at u = p ordered [level][feature]; a segment's MLP input is
+ * [psi(p0), psi(p1)] zero-padded to in_dim = 2(3P + L*F_d) rounded up to a
+ * multiple of 16. The point-encoding calls (nif_encode_points and its
+ * backward) keep the composed layout and refuse such a handle. */
+#define NIF_FLAG_CONCAT_ENCODING 8u
 
 /* Rest-space triangle mesh inside [0,1]^3 (host memory, copied by nif_create). */
 typedef struct {

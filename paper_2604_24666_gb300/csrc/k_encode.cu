@@ -726,12 +726,174 @@ nif_status launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, 
     return NIF_OK;
 }
 
+// ---------------------------------------------------------------------------
+// The concatenation reading of Eq. 1: psi(p) = [gamma(p), phi(p)]. A segment's
+// row is [psi(p0) | psi(p1) | zeros] of in_dim columns, W = 3P + L*F_d per
+// end point: gamma's raw values ordered [term][coordinate] (x, then
+// sin(2^k x), cos(2^k x) for k < F) and the grid features at u = p (p
+// clamped to [0,1]^3), ordered [level][feature].
+// ---------------------------------------------------------------------------
+template <typename OT>
+__device__ __forceinline__ OT to_out(float v);
+template <>
+__device__ __forceinline__ float to_out<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_out<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_out<__half>(float v) { return __float2half_rn(v); }
+
+// one thread per (segment, end point)
+template <typename TT, typename OT>
+__global__ void __launch_bounds__(256) k_encode_cat(GridInfo g, const TT* __restrict__ tab,
+                                                    const nif_linseg* __restrict__ lin,
+                                                    const uint32_t* __restrict__ n_dev, int64_t n_max, int in_dim,
+                                                    OT* __restrict__ out) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    const int W = 3 * g.P + g.L * 2;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < 2 * n;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = gid >> 1;
+        const int e = (int)(gid & 1);
+        const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+        const float3 p = clamp01(make_float3(L[0], L[1], L[2]));
+        OT* row = out + s * in_dim + e * W;
+        row[0] = to_out<OT>(p.x);
+        row[1] = to_out<OT>(p.y);
+        row[2] = to_out<OT>(p.z);
+        for (int k = 0; k < g.F; k++) {
+            const float f = (float)(1 << k);
+            float sx, cx, sy, cy, sz, cz;
+            sincosf(f * p.x, &sx, &cx);
+            sincosf(f * p.y, &sy, &cy);
+            sincosf(f * p.z, &sz, &cz);
+            OT* r = row + 3 + 6 * k;
+            r[0] = to_out<OT>(sx); r[1] = to_out<OT>(sy); r[2] = to_out<OT>(sz);
+            r[3] = to_out<OT>(cx); r[4] = to_out<OT>(cy); r[5] = to_out<OT>(cz);
+        }
+        OT* fr = row + 3 * g.P;
+        for (int l = 0; l < g.L; l++) {
+            const int Nl = g.res[l];
+            const bool dense = (g.dense_mask >> l) & 1u;
+            const Cell c = cell_of(p, Nl);
+            const TT* tl = tab + (int64_t)l * g.T * 2;
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint32_t rw = grid_row(c.ix + (q & 1), c.iy + ((q >> 1) & 1), c.iz + ((q >> 2) & 1), Nl, dense, g.T);
+                const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) *
+                                ((q & 4) ? c.wz : 1.f - c.wz);
+                const float2 v = load_row<TT>(tl, rw);
+                acc.x += w * v.x;
+                acc.y += w * v.y;
+            }
+            fr[2 * l] = to_out<OT>(acc.x);
+            fr[2 * l + 1] = to_out<OT>(acc.y);
+        }
+        if (e == 1)
+            for (int j = 2 * W; j < in_dim; j++) out[s * in_dim + j] = to_out<OT>(0.f);
+    }
+}
+
+// table gradient of the phi part: one thread per (segment, end point, level)
+__global__ void __launch_bounds__(256) k_encode_cat_bwd(GridInfo g, const nif_linseg* __restrict__ lin,
+                                                        const uint32_t* __restrict__ n_dev, int64_t n_max, int in_dim,
+                                                        const float* __restrict__ dfeats, float* __restrict__ dtab) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    const int W = 3 * g.P + g.L * 2;
+    const int per = 2 * g.L;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n * per;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = gid / per;
+        const int r = (int)(gid - s * per);
+        const int e = r / g.L, l = r - e * g.L;
+        const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+        const float3 p = clamp01(make_float3(L[0], L[1], L[2]));
+        const float* df = dfeats + s * in_dim + e * W + 3 * g.P + 2 * l;
+        const float gx = df[0], gy = df[1];
+        const int Nl = g.res[l];
+        const bool dense = (g.dense_mask >> l) & 1u;
+        const Cell c = cell_of(p, Nl);
+        float2* dl = reinterpret_cast<float2*>(dtab + (int64_t)l * g.T * 2);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint32_t rw = grid_row(c.ix + (q & 1), c.iy + ((q >> 1) & 1), c.iz + ((q >> 2) & 1), Nl, dense, g.T);
+            const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) *
+                            ((q & 4) ? c.wz : 1.f - c.wz);
+            atomicAdd(dl + rw, make_float2(w * gx, w * gy));
+        }
+    }
+}
+
+// input gradient with the tables fixed: dp[s][e][3] = d(sum dfeats * psi)/d p_e
+// (gamma's derivative plus the grid's), zero where p was clamped
+__global__ void __launch_bounds__(256) k_encode_cat_dp(GridInfo g, const float* __restrict__ tab,
+                                                       const nif_linseg* __restrict__ lin,
+                                                       const uint32_t* __restrict__ n_dev, int64_t n_max, int in_dim,
+                                                       const float* __restrict__ dfeats, float* __restrict__ dp) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    const int W = 3 * g.P + g.L * 2;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < 2 * n;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = gid >> 1;
+        const int e = (int)(gid & 1);
+        const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+        const float3 raw = make_float3(L[0], L[1], L[2]);
+        const float3 p = clamp01(raw);
+        const float* df = dfeats + s * in_dim + e * W;
+        float3 d = make_float3(df[0], df[1], df[2]);
+        for (int k = 0; k < g.F; k++) {
+            const float f = (float)(1 << k);
+            float sx, cx, sy, cy, sz, cz;
+            sincosf(f * p.x, &sx, &cx);
+            sincosf(f * p.y, &sy, &cy);
+            sincosf(f * p.z, &sz, &cz);
+            const float* r = df + 3 + 6 * k;
+            d.x += f * (r[0] * cx - r[3] * sx);
+            d.y += f * (r[1] * cy - r[4] * sy);
+            d.z += f * (r[2] * cz - r[5] * sz);
+        }
+        const float* fr = df + 3 * g.P;
+        for (int l = 0; l < g.L; l++) {
+            const int Nl = g.res[l];
+            const bool dense = (g.dense_mask >> l) & 1u;
+            const Cell c = cell_of(p, Nl);
+            const float gx = fr[2 * l], gy = fr[2 * l + 1];
+            const float* tl = tab + (int64_t)l * g.T * 2;
+            float3 dl = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint32_t rw = grid_row(c.ix + (q & 1), c.iy + ((q >> 1) & 1), c.iz + ((q >> 2) & 1), Nl, dense, g.T);
+                const float fx = (q & 1) ? c.wx : 1.f - c.wx;
+                const float fy = (q & 2) ? c.wy : 1.f - c.wy;
+                const float fz = (q & 4) ? c.wz : 1.f - c.wz;
+                const float2 v = __ldg(reinterpret_cast<const float2*>(tl) + rw);
+                const float val = v.x * gx + v.y * gy;
+                dl.x += ((q & 1) ? 1.f : -1.f) * fy * fz * val;
+                dl.y += ((q & 2) ? 1.f : -1.f) * fx * fz * val;
+                dl.z += ((q & 4) ? 1.f : -1.f) * fx * fy * val;
+            }
+            const float fn = (float)Nl;
+            d.x += fn * dl.x;
+            d.y += fn * dl.y;
+            d.z += fn * dl.z;
+        }
+        float* o = dp + s * 6 + e * 3;
+        o[0] = (raw.x < 0.f || raw.x > 1.f) ? 0.f : d.x;
+        o[1] = (raw.y < 0.f || raw.y > 1.f) ? 0.f : d.y;
+        o[2] = (raw.z < 0.f || raw.z > 1.f) ? 0.f : d.z;
+    }
+}
+
 }  // namespace
 
 nif_status nif_encode_points_run(nif_handle* h, const float* pts, int64_t n, void* feats, int out_dtype,
                                  int32_t* rows, cudaStream_t s) {
     NifProf prof_(h, "encode_points", s);
     if (n <= 0) return NIF_OK;
+    if (h->concat) return nif_fail(h, NIF_ERR_ARG, "point encoding is the composed reading; this handle concatenates");
     const float* tab = h->d_params + h->off_tables;
     if (out_dtype == NIF_FP32) launch_points<float, float>(h, tab, pts, n, feats, rows, s);
     else if (out_dtype == NIF_BF16) launch_points<float, __nv_bfloat16>(h, tab, pts, n, feats, rows, s);
@@ -741,11 +903,35 @@ nif_status nif_encode_points_run(nif_handle* h, const float* pts, int64_t n, voi
     return NIF_OK;
 }
 
+// forward of the concatenation reading: FP32 master tables or their FP16 copy, FP32/BF16/FP16 rows
+static nif_status launch_cat(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max, void* feats,
+                             int out_dtype, int table_dtype, cudaStream_t s) {
+    const unsigned g = (unsigned)std::min<int64_t>(nif_blocks(2 * n_max, 256), (int64_t)h->num_sms * 16);
+    if (table_dtype != NIF_FP32 && table_dtype != NIF_FP16) return nif_fail(h, NIF_ERR_ARG, "table_dtype");
+    if (out_dtype != NIF_FP32 && out_dtype != NIF_BF16 && out_dtype != NIF_FP16) return nif_fail(h, NIF_ERR_ARG, "out_dtype");
+    if (table_dtype == NIF_FP16) {
+        nif_status st = nif_refresh_lowp(h, s);
+        if (st != NIF_OK) return st;
+        const __half* tab = h->d_tables_h;
+        if (out_dtype == NIF_FP32) k_encode_cat<__half, float><<<g, 256, 0, s>>>(h->grid, tab, lin, n_dev, n_max, h->in_dim, (float*)feats);
+        else if (out_dtype == NIF_BF16) k_encode_cat<__half, __nv_bfloat16><<<g, 256, 0, s>>>(h->grid, tab, lin, n_dev, n_max, h->in_dim, (__nv_bfloat16*)feats);
+        else k_encode_cat<__half, __half><<<g, 256, 0, s>>>(h->grid, tab, lin, n_dev, n_max, h->in_dim, (__half*)feats);
+    } else {
+        const float* tab = h->d_params + h->off_tables;
+        if (out_dtype == NIF_FP32) k_encode_cat<float, float><<<g, 256, 0, s>>>(h->grid, tab, lin, n_dev, n_max, h->in_dim, (float*)feats);
+        else if (out_dtype == NIF_BF16) k_encode_cat<float, __nv_bfloat16><<<g, 256, 0, s>>>(h->grid, tab, lin, n_dev, n_max, h->in_dim, (__nv_bfloat16*)feats);
+        else k_encode_cat<float, __half><<<g, 256, 0, s>>>(h->grid, tab, lin, n_dev, n_max, h->in_dim, (__half*)feats);
+    }
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
 nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
                                    void* feats, int out_dtype, int table_dtype, cudaStream_t s) {
     NifProf prof_(h, "encode_fwd", s);
     if (n_max <= 0) return NIF_OK;
     nif_status st = NIF_OK;
+    if (h->concat) return launch_cat(h, lin, n_dev, n_max, feats, out_dtype, table_dtype, s);
     if (table_dtype == NIF_FP16) {
         st = nif_refresh_lowp(h, s);
         if (st != NIF_OK) return st;
@@ -772,6 +958,7 @@ nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n,
                                      float* dtables, float* dpts, cudaStream_t s) {
     NifProf prof_(h, "encode_points_bwd", s);
     if (n <= 0) return NIF_OK;
+    if (h->concat) return nif_fail(h, NIF_ERR_ARG, "point encoding is the composed reading; this handle concatenates");
     if (dpts) NIF_CK(h, cudaMemsetAsync(dpts, 0, sizeof(float) * 3 * n, s));
     k_encode_points_bwd<<<nif_blocks(n * h->P, 256), 256, 0, s>>>(h->grid, h->d_params + h->off_tables, pts, n,
                                                                  dfeats, dtables, dpts);
@@ -783,6 +970,13 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
                                        const float* dfeats, float* dtables, cudaStream_t s) {
     NifProf prof_(h, "encode_bwd", s);
     if (n_max <= 0) return NIF_OK;
+    if (h->concat) {
+        const int64_t work = n_max * 2 * h->L;
+        k_encode_cat_bwd<<<(unsigned)std::min<int64_t>(nif_blocks(work, 256), (int64_t)h->num_sms * 16), 256, 0, s>>>(
+            h->grid, lin, n_dev, n_max, h->in_dim, dfeats, dtables);
+        NIF_CK_LAUNCH(h);
+        return NIF_OK;
+    }
     // dense prefix of levels that fits the shared-memory budget
     const int budget = 200 * 1024 / 4;
     Coarse cs{};
@@ -831,6 +1025,12 @@ nif_status nif_encode_segments_dp_run(nif_handle* h, const nif_linseg* lin, cons
     NifProf prof_(h, "encode_dp", s);
     if (n <= 0) return NIF_OK;
     NIF_CK(h, cudaMemsetAsync(dp, 0, sizeof(float) * 6 * n, s));
+    if (h->concat) {
+        k_encode_cat_dp<<<(unsigned)std::min<int64_t>(nif_blocks(2 * n, 256), (int64_t)h->num_sms * 16), 256, 0, s>>>(
+            h->grid, h->d_params + h->off_tables, lin, n_dev, n, h->in_dim, dfeats, dp);
+        NIF_CK_LAUNCH(h);
+        return NIF_OK;
+    }
     unsigned g = nif_blocks(n * 2 * h->P, 256);
     unsigned cap = (unsigned)h->num_sms * 16;
     if (g > cap) g = cap;

@@ -289,7 +289,8 @@ static nif_status validate(const nif_config* c, const nif_mesh* m) {
         return nif_fail(nullptr, NIF_ERR_ARG, "mlp_width in {16, 32, 64, 128}");
     if (c->n_materials < 1 || c->n_materials > 8) return nif_fail(nullptr, NIF_ERR_ARG, "n_materials in [1, 8]");
     if (c->precision < NIF_FP32 || c->precision > NIF_FP16) return nif_fail(nullptr, NIF_ERR_ARG, "precision");
-    if (c->flags & ~(NIF_FLAG_FIXED_TASK_WEIGHTS | NIF_FLAG_SIGMOID_DISTANCE | NIF_FLAG_MIXED_TRAINING))
+    if (c->flags & ~(NIF_FLAG_FIXED_TASK_WEIGHTS | NIF_FLAG_SIGMOID_DISTANCE | NIF_FLAG_MIXED_TRAINING |
+                     NIF_FLAG_CONCAT_ENCODING))
         return nif_fail(nullptr, NIF_ERR_ARG, "unknown flags");
     if ((c->flags & NIF_FLAG_MIXED_TRAINING) && c->precision == NIF_FP32)
         return nif_fail(nullptr, NIF_ERR_ARG, "NIF_FLAG_MIXED_TRAINING needs precision NIF_BF16 or NIF_FP16");
@@ -405,7 +406,9 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
     h->W = cfg->mlp_width;
     h->H = cfg->mlp_depth;
     h->n_layers = h->H + 1;
-    h->in_dim = 2 * h->P * h->L * h->Fd;
+    h->concat = (cfg->flags & NIF_FLAG_CONCAT_ENCODING) != 0;
+    h->point_w = h->concat ? 3 * h->P + h->L * h->Fd : h->P * h->L * h->Fd;
+    h->in_dim = h->concat ? (2 * h->point_w + 15) / 16 * 16 : 2 * h->point_w;
     h->grid.L = h->L;
     h->grid.Fd = h->Fd;
     h->grid.P = h->P;

@@ -54,6 +54,8 @@ struct NifLossScale {
 struct nif_handle {
     nif_config cfg{};
     int N = 0, L = 0, Fd = 2, P = 0, in_dim = 0, W = 0, H = 0, n_layers = 0;
+    bool concat = false;                // Eq. 1 read as [gamma, phi] (NIF_FLAG_CONCAT_ENCODING)
+    int point_w = 0;                    // features of one end point: P*L*F_d, or 3P + L*F_d concatenated
     uint32_t T = 0;
     GridInfo grid{};
 
