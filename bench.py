@@ -529,7 +529,13 @@ def run_batch(args, nif, S, dev, rank):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    offs = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    total = nif._i64()
+    p_, n_inst = nif._poses(poses[args.warmup])
+    nif._check(h.h, nif.lib().nif_segments(h.h, p_, n_inst, nif._ptr(rays), nif._ptr(it), n, nif._ptr(offs), None, 0,
+                                           nif.ctypes.byref(total), None))
     res = {"workload": BATCH_WORKLOAD, "instances": int(w["n_inst"]), "rays_per_step": int(n),
+           "segments_per_step": int(total.value),
            "rays_per_instance_min_max": [int(counts.min()), int(counts.max())], "precision": "bf16",
            "queries_per_s": n / (ms / 1e3), "ms_per_batch": ms, "graph": True, "knobs": plan.info(),
            "autotune_s": tune_s,
@@ -707,6 +713,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision training measurement")
     ap.add_argument("--no-frame", action="store_true", help="skip the animated frame loop")
     ap.add_argument("--no-traversal", action="store_true", help="skip the enumeration vs exit-face walk comparison")
+    ap.add_argument("--only-batch", action="store_true", help="measure only the batched query (profiling aid)")
     ap.add_argument("--only-traversal", action="store_true", help="measure only the traversal comparison (profiling aid)")
     ap.add_argument("--frames", type=int, default=120, help="frames of the animated frame loop")
     ap.add_argument("--frame-pretrain", type=int, default=1500, help="training steps before the frame loop")
@@ -722,6 +729,14 @@ def main():
         B.build()
         from paper_2604_24666_gb300 import nif, synth as S
         print(json.dumps({"query": run_query(args, nif, S, torch.device("cuda:0"), 0)}), flush=True)
+        return 0
+    if args.only_batch:
+        import torch
+        torch.cuda.set_device(0)
+        from paper_2604_24666_gb300 import build as B
+        B.build()
+        from paper_2604_24666_gb300 import nif, synth as S
+        print(json.dumps({"batch": run_batch(args, nif, S, torch.device("cuda:0"), 0)}), flush=True)
         return 0
     if args.only_traversal:
         import torch
