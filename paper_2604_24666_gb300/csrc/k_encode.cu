@@ -220,10 +220,16 @@ __global__ void __launch_bounds__(512) k_encode_segments_v(GridInfo g, const TT*
     int64_t n = n_dev ? (int64_t)*n_dev : n_max;
     if (n > n_max) n = n_max;
     const int64_t n_points = pts ? (int64_t)*n_pts_dev : 2 * n;
-    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n_points * g.P;
+    // a warp takes one gamma term of 32 consecutive points: points along a ray
+    // fall in the same coarse cells, so their corner loads merge into fewer
+    // L1 wavefronts than 32 lanes spread over every term of a few points
+    const int64_t n_work = (n_points + 31) / 32 * 32 * g.P;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n_work;
          gid += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = gid / g.P;
-        const int t = (int)(gid - k * g.P);
+        const int64_t grp = gid >> 5;
+        const int t = (int)(grp % g.P);
+        const int64_t k = (grp / g.P) * 32 + (gid & 31);
+        if (k >= n_points) continue;
         const int64_t pt = pts ? (int64_t)pts[k] : k;
         const int64_t s = pt >> 1;
         const int e = (int)(pt & 1);
