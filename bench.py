@@ -42,9 +42,11 @@ N_POSES = 16
 # the current encoding-backward kernel on this workload; a stage missing here
 # reports traffic null.
 NCU_TRAFFIC = {"encode_bwd": 659.2e6}
-# stages the library runs on its second stream, beside the main stream's work:
-# their event intervals include the overlap, so they are not the step's critical path
-OVERLAPPED = {"mlp_dw_fp32", "mlp_dw_tc"}
+# stages the library runs beside the main stream's work (weight gradients on
+# its second stream, the next step's batch on its third): their event
+# intervals include the overlap, so they are not the step's critical path
+OVERLAPPED = {"mlp_dw_fp32", "mlp_dw_tc", "sample_rays", "refit", "seg_traverse", "scan", "seg_scatter", "seg_emit",
+              "linearize", "labels"}
 
 
 def _peaks():
@@ -226,8 +228,9 @@ def run_ours(args):
 
     # ---- device-resident training steps -------------------------------
     seed0 = 77 + 1000003 * rank
-    for i in range(args.warmup):
-        nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + i, want_loss=False)
+    # K steps in one call: each step's batch (sampling, segments, linearization,
+    # labels) is built on the library's third stream beside the previous step
+    nif.nif_train_steps(h.h, args.warmup, N_SEG, N_POSES, seed0, lr_grid=1e-2, lr_mlp=1e-3)
     torch.cuda.synchronize()
     nif.nif_profile(h.h, 1)
     clk = Clocks(local) if rank == 0 else None
@@ -236,8 +239,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for i in range(args.steps):
-        nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + args.warmup + i, want_loss=False)
+    nif.nif_train_steps(h.h, args.steps, N_SEG, N_POSES, seed0 + args.warmup, lr_grid=1e-2, lr_mlp=1e-3)
     e1.record(stream)
     torch.cuda.synchronize()
     _barrier(ws)
@@ -353,14 +355,12 @@ def run_train_mixed(args, nif, S, dev, rank, hbm):
         h = nif.Nif(net, mesh, precision=prec, seed=1234 + rank, flags=nif.NIF_FLAG_MIXED_TRAINING)
         stream = torch.cuda.current_stream()
         seed0 = 91 + 1000003 * rank
-        for i in range(args.warmup):
-            nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + i, want_loss=False)
+        nif.nif_train_steps(h.h, args.warmup, N_SEG, N_POSES, seed0, lr_grid=1e-2, lr_mlp=1e-3)
         torch.cuda.synchronize()
         nif.nif_profile(h.h, 1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for i in range(args.steps):
-            nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + args.warmup + i, want_loss=False)
+        nif.nif_train_steps(h.h, args.steps, N_SEG, N_POSES, seed0 + args.warmup, lr_grid=1e-2, lr_mlp=1e-3)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
@@ -369,7 +369,8 @@ def run_train_mixed(args, nif, S, dev, rank, hbm):
         loss, _ = nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + 99999, want_loss=True)
         scale, skipped = nif.nif_loss_scale(h.h)
         tot = sum(v[0] for v in prof.values())
-        stages = {k: {"ms_per_step": v[0] / max(args.steps, 1), "share": v[0] / tot if tot else None}
+        stages = {k: {"ms_per_step": v[0] / max(args.steps, 1), "share": v[0] / tot if tot else None,
+                      **({"overlapped": True} if k in OVERLAPPED else {})}
                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
         for k in ("encode_fwd", "encode_bwd"):
             if k in stages:

@@ -409,6 +409,18 @@ nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses,
                           unsigned long long step_seed, float lr_grid, float lr_mlp,
                           nif_pose* poses_out_host, double* loss_host, void* stream);
 
+/* n_steps training steps, exactly what n_steps calls of nif_train_step with
+ * the seeds first_seed, first_seed + 1, ... compute, in one call. The batch
+ * of a step (sampling, segments, linearization, labels: nothing that depends
+ * on the parameters) is built on a second internal stream, into a second set
+ * of batch buffers, while the previous step trains, so it costs no time on
+ * `stream` after the first. loss_host (nullable): the loss parts of the last
+ * step, as nif_train_step gives them. Enqueues on `stream`; the host blocks
+ * only to read loss_host and the first time buffers grow. */
+nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segments, int n_poses,
+                           unsigned long long first_seed, float lr_grid, float lr_mlp, double* loss_host,
+                           void* stream);
+
 /* Pose fitting (the paper names learned deformations as future work): the
  * gradient of the task loss of Sec. 2.4 with respect to the n_inst
  * deformation parameters, tables, weights and s held fixed, for the

@@ -462,32 +462,35 @@ nif_status nif_labels_count_hits(nif_handle* h, const nif_label* labels, int64_t
 }
 
 nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const uint32_t* n_dev,
-                          int64_t n_max, nif_label* labels, cudaStream_t s) {
+                          int64_t n_max, nif_label* labels, cudaStream_t s, int* n_hit) {
     NifProf prof_(h, "labels", s);
+    if (!n_hit) n_hit = h->d_count;
     if (n_max <= 0) return NIF_OK;
-    NIF_CK(h, cudaMemsetAsync(h->d_count, 0, sizeof(int), s));
+    NIF_CK(h, cudaMemsetAsync(n_hit, 0, sizeof(int), s));
     unsigned g = nif_blocks(n_max, 256);
     unsigned cap = (unsigned)h->num_sms * 8;
     if (g > cap) g = cap;
     k_labels<<<g, 256, 0, s>>>(segs, lin, n_dev, n_max, h->d_tri_ptr, h->d_tri_idx, h->d_verts, h->d_tris, h->d_alb,
-                               h->d_mat, labels, h->d_count, (uint32_t)((int64_t)h->N * h->N * h->N));
+                               h->d_mat, labels, n_hit, (uint32_t)((int64_t)h->N * h->N * h->N));
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
 
 nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels, const nif_linseg* lin,
-                        const uint32_t* n_dev, int64_t n_max, float* dout, cudaStream_t s, bool want_ds) {
+                        const uint32_t* n_dev, int64_t n_max, float* dout, cudaStream_t s, bool want_ds,
+                        const int* n_hit) {
     NifProf prof_(h, "loss", s);
+    if (!n_hit) n_hit = h->d_count;
     NIF_CK(h, cudaMemsetAsync(h->d_lossacc, 0, sizeof(double) * 16, s));
     if (n_max > 0) {
         unsigned g = nif_blocks(n_max, 256);
         unsigned cap = (unsigned)h->num_sms * 8;
         if (g > cap) g = cap;
-        k_loss<<<g, 256, 0, s>>>(out, labels, lin, n_dev, n_max, h->d_count, h->d_params + h->off_s, h->N,
+        k_loss<<<g, 256, 0, s>>>(out, labels, lin, n_dev, n_max, n_hit, h->d_params + h->off_s, h->N,
                                  h->cfg.n_materials, h->cfg.flags, dout, h->d_lossacc);
         NIF_CK_LAUNCH(h);
     }
-    k_loss_final<<<1, 32, 0, s>>>(h->d_lossacc, n_dev, n_max, h->d_count, h->d_params + h->off_s, h->cfg.flags,
+    k_loss_final<<<1, 32, 0, s>>>(h->d_lossacc, n_dev, n_max, n_hit, h->d_params + h->off_s, h->cfg.flags,
                                   want_ds ? h->d_grad + h->off_s : nullptr, h->d_status);
     NIF_CK_LAUNCH(h);
     return NIF_OK;

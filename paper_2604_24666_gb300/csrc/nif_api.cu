@@ -458,6 +458,9 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
     CKC(cudaMemset(h->d_count, 0, sizeof(int) * 4));
     CKC(cudaMallocHost(&h->h_pinned, sizeof(int) * 16));
     CKC(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking));
+    CKC(cudaEventCreateWithFlags(&h->ev_batch, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&h->ev_step, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
 
@@ -520,13 +523,17 @@ extern "C" void nif_destroy(nif_handle* h) {
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
                                &h->b_acts, &h->b_dout, &h->b_dx, &h->b_labels, &h->b_scan, &h->b_rays,
                                &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys, &h->b_dup, &h->b_pts,
-                               &h->b_lattice};
+                               &h->b_lattice, &h->alt_counts, &h->alt_offsets, &h->alt_temp, &h->alt_segs,
+                               &h->alt_scan, &h->alt_rays, &h->alt_inst, &h->alt_lin, &h->alt_labels};
     for (auto* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->aux2) cudaStreamDestroy(h->aux2);
+    if (h->ev_batch) cudaEventDestroy(h->ev_batch);
+    if (h->ev_step) cudaEventDestroy(h->ev_step);
     for (auto e : h->prof_pool) cudaEventDestroy(e);
     h->n_plans = 0;
     nif_free_retired(h);
@@ -1145,24 +1152,35 @@ extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst
     return nif_reconstruct_run(h, rays, inst_off, n_inst, n_rays, offs, segs, total, lin, out, hits, flags, s);
 }
 
-extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
-                                          const int* inst_off, int n_rays, int64_t n_segments, float lr_grid,
-                                          float lr_mlp, double* loss_host, void* stream) {
-    if (!h) return NIF_ERR_ARG;
-    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
-    if (st != NIF_OK) return st;
-    if (n_segments < 1 || !rays) return nif_fail(h, NIF_ERR_ARG, "n_segments / rays");
-    const bool mixed = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
-    if (mixed && (st = check_mixed(h)) != NIF_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
+// The batch of one training step: segments of whole rays (at most n_segments,
+// in ray order), their linearization and labels, into the handle's batch
+// buffers; the hit count goes to *n_hit (device).
+static nif_status train_batch(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                              const int* inst_off, int n_rays, int64_t n_segments, int* n_hit, cudaStream_t s) {
+    nif_status st;
     if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, n_segments, false, nullptr, s)) != NIF_OK)
         return st;
-    // the capacity clamp marks overflow; for training a full batch is the normal case
     uint32_t* offs = (uint32_t*)h->b_offsets.p;
     const uint32_t* n_dev = offs + n_rays + 1;
-    int64_t n = n_segments;
+    const int64_t n = n_segments;
     if ((st = nif_grow(h, h->b_lin, sizeof(nif_linseg) * n)) != NIF_OK) return st;
     if ((st = nif_grow(h, h->b_labels, sizeof(nif_label) * n)) != NIF_OK) return st;
+    nif_segment* segs = (nif_segment*)h->b_segs.p;
+    nif_linseg* lin = (nif_linseg*)h->b_lin.p;
+    if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, n, lin, s)) != NIF_OK) return st;
+    return nif_labels_run(h, segs, lin, n_dev, n, (nif_label*)h->b_labels.p, s, n_hit);
+}
+
+// Forward, losses, backward and optimizer step on the batch in the handle's
+// batch buffers (n_rays rays, at most n_segments segments; hit count *n_hit).
+// ev_bwd (nullable) is recorded on s before the encoding backward.
+static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, const int* n_hit, float lr_grid,
+                                float lr_mlp, double* loss_host, cudaStream_t s, cudaEvent_t ev_bwd = nullptr) {
+    nif_status st;
+    const bool mixed = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
+    uint32_t* offs = (uint32_t*)h->b_offsets.p;
+    const uint32_t* n_dev = offs + n_rays + 1;
+    const int64_t n = n_segments;
     if ((st = nif_grow(h, h->b_feat, sizeof(float) * (size_t)h->in_dim * n)) != NIF_OK) return st;
     if ((st = nif_grow(h, h->b_dx, sizeof(float) * (size_t)h->in_dim * n)) != NIF_OK) return st;
     if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
@@ -1175,7 +1193,6 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
         if ((st = nif_grow(h, h->b_feat, 2 * (size_t)h->in_dim * np)) != NIF_OK) return st;
         if ((st = nif_grow(h, h->b_dys, 2 * (size_t)np * kLd * (h->H + 1))) != NIF_OK) return st;
     }
-    nif_segment* segs = (nif_segment*)h->b_segs.p;
     nif_linseg* lin = (nif_linseg*)h->b_lin.p;
     nif_label* lab = (nif_label*)h->b_labels.p;
     float* feat = (float*)h->b_feat.p;
@@ -1183,8 +1200,6 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
     float* out = (float*)h->b_out.p;
     float* dout = (float*)h->b_feat2.p;
     float* acts = (float*)h->b_acts.p;
-    if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, n, lin, s)) != NIF_OK) return st;
-    if ((st = nif_labels_run(h, segs, lin, n_dev, n, lab, s)) != NIF_OK) return st;
     if (mixed) {
         // 16-bit features from the FP16 table copy, tensor-core MLP forward
         // keeping its activations, loss on FP32 outputs, scaled tensor-core
@@ -1194,13 +1209,14 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
         uint16_t* dys = (uint16_t*)h->b_dys.p;
         if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, prec, NIF_FP16, s)) != NIF_OK) return st;
         if ((st = nif_mlp_fwd_tc_acts_run(h, feat, prec, n_dev, n, out, acts16, np, kLd, s)) != NIF_OK) return st;
-        if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s)) != NIF_OK) return st;
+        if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, true, n_hit)) != NIF_OK) return st;
         if ((st = nif_mlp_bwd_tc_run(h, dout, acts16, n_dev, n, np, kLd, dys, dx, s)) != NIF_OK) return st;
         // weight gradients on the second stream, beside the encoding backward
         NIF_CK(h, cudaEventRecord(h->ev_fork, s));
         NIF_CK(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
         if ((st = nif_mlp_dw_tc_run(h, feat, acts16, dys, n_dev, n, np, kLd, h->aux)) != NIF_OK) return st;
         NIF_CK(h, cudaEventRecord(h->ev_join, h->aux));
+        if (ev_bwd) NIF_CK(h, cudaEventRecord(ev_bwd, s));
         if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK)
             return st;
         NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
@@ -1209,9 +1225,10 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
     } else {
         if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s)) != NIF_OK) return st;
         if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
-        if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s)) != NIF_OK) return st;
+        if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, true, n_hit)) != NIF_OK) return st;
         // weight gradients on the second stream, beside dX_0 and the encoding backward
         if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s, true, h->aux)) != NIF_OK) return st;
+        if (ev_bwd) NIF_CK(h, cudaEventRecord(ev_bwd, s));
         if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK)
             return st;
         NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
@@ -1231,6 +1248,20 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
         }
     }
     return NIF_OK;
+}
+
+extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                          const int* inst_off, int n_rays, int64_t n_segments, float lr_grid,
+                                          float lr_mlp, double* loss_host, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    if (n_segments < 1 || !rays) return nif_fail(h, NIF_ERR_ARG, "n_segments / rays");
+    const bool mixed = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
+    if (mixed && (st = check_mixed(h)) != NIF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = train_batch(h, poses, n_inst, rays, inst_off, n_rays, n_segments, h->d_count, s)) != NIF_OK) return st;
+    return train_compute(h, n_rays, n_segments, h->d_count, lr_grid, lr_mlp, loss_host, s);
 }
 
 extern "C" nif_status nif_pose_step(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
@@ -1310,11 +1341,10 @@ extern "C" nif_status nif_shadow_rays(nif_handle* h, const nif_ray* rays, const 
     return nif_shadow_rays_run(h, rays, hits, n, u, eps, tmax, shadow_rays, (cudaStream_t)stream);
 }
 
-extern "C" nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses, unsigned long long step_seed,
-                                     float lr_grid, float lr_mlp, nif_pose* poses_out, double* loss_host,
-                                     void* stream) {
-    if (!h || n_segments < 1 || n_poses < 1) return NIF_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
+// The sampled batch of one training step of nif_train_step: n_poses poses
+// U[-1,1]^3 from step_seed, rays per pose from the sampler, then train_batch.
+static nif_status sampled_batch(nif_handle* h, int64_t n_segments, int n_poses, unsigned long long step_seed,
+                                nif_pose* poses_out, int* n_rays_out, int* n_hit, cudaStream_t s) {
     std::vector<nif_pose> poses(n_poses);
     for (int i = 0; i < n_poses; i++) {
         uint64_t base = ((0xFFFFull << 32) + (uint64_t)i) * 8ull;
@@ -1345,6 +1375,83 @@ extern "C" nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_po
     if ((st = nif_sample_rays_run(h, step_seed, 0, per, rays, s, n_poses)) != NIF_OK) return st;
     k_iota_offsets<<<nif_blocks(n_poses + 1, 256), 256, 0, s>>>((int*)h->b_inst.p, n_poses, per);
     NIF_CK_LAUNCH(h);
-    return nif_train_step_rays(h, poses.data(), n_poses, rays, (const int*)h->b_inst.p, n_rays, n_segments, lr_grid,
-                               lr_mlp, loss_host, stream);
+    *n_rays_out = n_rays;
+    return train_batch(h, poses.data(), n_poses, rays, (const int*)h->b_inst.p, n_rays, n_segments, n_hit, s);
+}
+
+extern "C" nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses, unsigned long long step_seed,
+                                     float lr_grid, float lr_mlp, nif_pose* poses_out, double* loss_host,
+                                     void* stream) {
+    if (!h || n_segments < 1 || n_poses < 1) return NIF_ERR_ARG;
+    nif_status st;
+    if ((h->cfg.flags & NIF_FLAG_MIXED_TRAINING) && (st = check_mixed(h)) != NIF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int n_rays = 0;
+    if ((st = sampled_batch(h, n_segments, n_poses, step_seed, poses_out, &n_rays, h->d_count, s)) != NIF_OK)
+        return st;
+    return train_compute(h, n_rays, n_segments, h->d_count, lr_grid, lr_mlp, loss_host, s);
+}
+
+// The buffers one training batch lives in, exchanged with the handle's own
+// while nif_train_steps builds the next batch beside the current step.
+static void swap_batch(nif_handle* h) {
+    std::swap(h->b_counts, h->alt_counts);
+    std::swap(h->b_offsets, h->alt_offsets);
+    std::swap(h->b_temp, h->alt_temp);
+    std::swap(h->b_segs, h->alt_segs);
+    std::swap(h->b_scan, h->alt_scan);
+    std::swap(h->b_rays, h->alt_rays);
+    std::swap(h->b_inst, h->alt_inst);
+    std::swap(h->b_lin, h->alt_lin);
+    std::swap(h->b_labels, h->alt_labels);
+}
+
+extern "C" nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segments, int n_poses,
+                                      unsigned long long first_seed, float lr_grid, float lr_mlp, double* loss_host,
+                                      void* stream) {
+    if (!h || n_steps < 1 || n_segments < 1 || n_poses < 1) return NIF_ERR_ARG;
+    nif_status st;
+    if ((h->cfg.flags & NIF_FLAG_MIXED_TRAINING) && (st = check_mixed(h)) != NIF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // batch i sits in buffer set i % 2 with its hit count in counter word 2 + i % 2;
+    // the handle's own buffers are always the set of the next thing enqueued
+    int n_rays = 0, nr = 0;
+    if ((st = sampled_batch(h, n_segments, n_poses, first_seed, nullptr, &n_rays, h->d_count + 2, s)) != NIF_OK)
+        return st;
+    NIF_CK(h, cudaEventRecord(h->ev_batch, s));
+    // Where the next batch starts: the FP32 path's persistent split-TF32
+    // GEMMs lose SMs to a concurrent batch (measured: forward 0.28 -> 0.59 ms),
+    // so its next batch starts beside the encoding backward (step 3.30 ms vs
+    // 3.34 ms); the mixed path's forward shares the GPU well and its next
+    // batch starts with the step (2.79 ms vs 2.91 ms).
+    const bool early = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
+    auto next_batch = [&](int i) -> nif_status {
+        swap_batch(h);
+        NIF_CK(h, cudaStreamWaitEvent(h->aux2, h->ev_batch, 0));   // batch i built: geometry and cursor free
+        NIF_CK(h, cudaStreamWaitEvent(h->aux2, h->ev_step, 0));    // step i - 1 done with this set
+        nif_status r = sampled_batch(h, n_segments, n_poses, first_seed + (unsigned long long)(i + 1), nullptr, &nr,
+                                     h->d_count + 2 + (i + 1) % 2, h->aux2);
+        if (r != NIF_OK) return r;
+        if (nr != n_rays) return nif_fail(h, NIF_ERR_STATE, "training batches of one call differ in ray count");
+        NIF_CK(h, cudaEventRecord(h->ev_batch, h->aux2));
+        return NIF_OK;
+    };
+    NIF_CK(h, cudaEventRecord(h->ev_step, s));
+    for (int i = 0; i < n_steps; i++) {
+        const bool more = i + 1 < n_steps;
+        if (i > 0) NIF_CK(h, cudaStreamWaitEvent(s, h->ev_batch, 0));      // batch i is built
+        if (more && early) {
+            if ((st = next_batch(i)) != NIF_OK) return st;
+            swap_batch(h);                                                  // back to step i's set
+        }
+        if ((st = train_compute(h, n_rays, n_segments, h->d_count + 2 + i % 2, lr_grid, lr_mlp,
+                                more ? nullptr : loss_host, s, early ? nullptr : h->ev_step)) != NIF_OK)
+            return st;
+        if (more && !early && (st = next_batch(i)) != NIF_OK) return st;
+        if (early) {
+            NIF_CK(h, cudaEventRecord(h->ev_step, s));                      // end of step i
+            if (more) swap_batch(h);
+        }
+    }
+    return NIF_OK;
 }

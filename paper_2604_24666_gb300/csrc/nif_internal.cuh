@@ -114,6 +114,9 @@ struct nif_handle {
     // it always forks from and joins back into the caller's stream
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // a third stream for nif_train_steps' next batch, and its ordering events
+    cudaStream_t aux2 = nullptr;
+    cudaEvent_t ev_batch = nullptr, ev_step = nullptr;
 
     // device status word + scratch
     int* d_status = nullptr;
@@ -126,6 +129,9 @@ struct nif_handle {
     Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
         b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts, b_lattice;
     int* d_vox_leaf = nullptr;          // [N^3] octree leaf of each voxel, -1 when empty (exit-face walk)
+    // the second set of training-batch buffers of nif_train_steps (the next
+    // step's batch is built into it while the current step trains)
+    Buf alt_counts, alt_offsets, alt_temp, alt_segs, alt_scan, alt_rays, alt_inst, alt_lin, alt_labels;
     double query_seg_per_ray = 0.0;     // segments per ray of the last query (temp capacity hint)
 
     // launch knobs chosen by the autotuner (nif_query_plan_create)
@@ -274,12 +280,15 @@ nif_status nif_shadow_rays_run(nif_handle* h, const nif_ray* rays, const nif_hit
 nif_status nif_unscale_run(nif_handle* h, float* v, int n, cudaStream_t s);
 nif_status nif_adam_scaled_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s);
 nif_status nif_labels_count_hits(nif_handle* h, const nif_label* labels, int64_t n, cudaStream_t s);
+// n_hit (device int, default the handle's first counter word): the count of
+// labelled hits, written by nif_labels_run and read by nif_loss_run
 nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin,
-                          const uint32_t* n_dev, int64_t n_max, nif_label* labels, cudaStream_t s);
+                          const uint32_t* n_dev, int64_t n_max, nif_label* labels, cudaStream_t s,
+                          int* n_hit = nullptr);
 // want_ds: add dL/ds into the gradient buffer (off for a gradient with respect to the poses only)
 nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels,
                         const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max, float* dout,
-                        cudaStream_t s, bool want_ds = true);
+                        cudaStream_t s, bool want_ds = true, const int* n_hit = nullptr);
 nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s);
 nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
                                int n_rays, const uint32_t* offsets, const nif_segment* segs,

@@ -112,6 +112,8 @@ def lib() -> ctypes.CDLL:
                                      ctypes.c_float, _vp, _vp], ctypes.c_int),
             "nif_train_step": ([_vp, _i64, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_float, ctypes.c_float, _vp, _vp,
                                 _vp], ctypes.c_int),
+            "nif_train_steps": ([_vp, ctypes.c_int, _i64, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_float, ctypes.c_float,
+                                 _vp, _vp], ctypes.c_int),
             "nif_sample_rays": ([_vp, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
             "nif_segments_noalloc": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _i64,
                                       ctypes.POINTER(_i64), _vp], ctypes.c_int),
@@ -450,6 +452,16 @@ def nif_train_step_rays(h, poses, rays, n_segments, inst_offsets=None, lr_grid=1
     loss = np.zeros(6, np.float64) if want_loss else None
     _check(h, lib().nif_train_step_rays(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0], n_segments,
                                         lr_grid, lr_mlp, _ptr(loss), _stream(stream)))
+    return loss
+
+
+def nif_train_steps(h, n_steps, n_segments, n_poses, first_seed, lr_grid=1e-2, lr_mlp=5e-3, want_loss=False,
+                    stream=None):
+    """n_steps training steps with seeds first_seed.. (the next batch built beside each step);
+    returns the last step's loss parts [6] when want_loss."""
+    loss = np.zeros(6, np.float64) if want_loss else None
+    _check(h, lib().nif_train_steps(h, n_steps, n_segments, n_poses, first_seed, lr_grid, lr_mlp, _ptr(loss),
+                                    _stream(stream)))
     return loss
 
 
