@@ -456,6 +456,7 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
     CKC(cudaMemset(h->d_lossacc, 0, sizeof(double) * 16));
     CKC(cudaMalloc(&h->d_count, sizeof(int) * 4));
     CKC(cudaMemset(h->d_count, 0, sizeof(int) * 4));
+    CKC(cudaMalloc(&h->d_ray_next, sizeof(uint32_t) * 4));
     CKC(cudaMallocHost(&h->h_pinned, sizeof(int) * 16));
     CKC(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking));
@@ -517,7 +518,8 @@ extern "C" void nif_destroy(nif_handle* h) {
     void* ptrs[] = {h->d_verts, h->d_tris, h->d_alb, h->d_mat, h->d_occ, h->d_tri_ptr, h->d_tri_idx, h->d_child,
                     h->d_leaf_vox, h->d_leaf_lat, h->d_corners, h->d_aabb, h->d_pose, h->d_params, h->d_grad,
                     h->d_m, h->d_v, h->d_tables_h, h->d_w_bf16, h->d_w_f16, h->d_wt_bf16, h->d_wt_f16, h->d_ls,
-                    h->d_w_x3, h->d_vox_leaf, h->d_status, h->d_lossacc, h->d_count};
+                    h->d_w_x3, h->d_vox_leaf, h->d_status, h->d_lossacc, h->d_count,
+                    h->d_ray_next};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,

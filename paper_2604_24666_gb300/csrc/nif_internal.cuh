@@ -122,6 +122,7 @@ struct nif_handle {
     int* d_status = nullptr;
     double* d_lossacc = nullptr;        // [16] loss accumulators
     int* d_count = nullptr;             // [4] counters
+    uint32_t* d_ray_next = nullptr;     // ray counter of the persistent traversal
     int* h_pinned = nullptr;            // pinned host word(s)
 
     // grown scratch buffers (query / train)
