@@ -708,6 +708,78 @@ nif_status distinct_points(nif_handle* h, const nif_linseg* lin, const uint32_t*
     return NIF_OK;
 }
 
+// The distinct points in rest-space order: a counting sort by the Morton
+// code of each point's cell in a 64^3 grid over the cube. A warp of the
+// encoder then takes 32 points of one small region, whose corner rows at the
+// coarse levels (and the low bands of gamma) coincide, so their loads merge
+// into far fewer L1 wavefronts than points taken along rays; the gather is
+// bound by L1 wavefronts. The order within a cell is arbitrary and does not
+// matter: every point's features go to its own rows.
+constexpr int kOrderBits = 6;
+constexpr uint32_t kOrderCells = 1u << (3 * kOrderBits);
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+    v &= 0x3Fu;
+    v = (v | (v << 8)) & 0x0000F00Fu;
+    v = (v | (v << 4)) & 0x000C30C3u;
+    v = (v | (v << 2)) & 0x00249249u;
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_point_keys(const nif_linseg* __restrict__ lin, const uint32_t* __restrict__ pts,
+                                                    const uint32_t* __restrict__ n_pts_dev, uint32_t* __restrict__ keys,
+                                                    uint32_t* __restrict__ hist) {
+    const int64_t n = *n_pts_dev;
+    const float cells = (float)(1 << kOrderBits);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t pt = pts[k];
+        const float* L = reinterpret_cast<const float*>(lin + (pt >> 1)) + 3 * (pt & 1u);
+        const float3 p = clamp01(make_float3(L[0], L[1], L[2]));
+        const uint32_t ix = min((uint32_t)(p.x * cells), (1u << kOrderBits) - 1u);
+        const uint32_t iy = min((uint32_t)(p.y * cells), (1u << kOrderBits) - 1u);
+        const uint32_t iz = min((uint32_t)(p.z * cells), (1u << kOrderBits) - 1u);
+        const uint32_t key = spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+        keys[k] = key;
+        atomicAdd(hist + key, 1u);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_point_scatter(const uint32_t* __restrict__ pts,
+                                                       const uint32_t* __restrict__ n_pts_dev,
+                                                       const uint32_t* __restrict__ keys,
+                                                       const uint32_t* __restrict__ off, uint32_t* __restrict__ fill,
+                                                       uint32_t* __restrict__ sorted) {
+    const int64_t n = *n_pts_dev;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = keys[k];
+        sorted[off[key] + atomicAdd(fill + key, 1u)] = pts[k];
+    }
+}
+
+// sorted (out): the *n_pts_dev points of pts in rest-space order
+nif_status spatial_order(nif_handle* h, const nif_linseg* lin, const uint32_t* pts, const uint32_t* n_pts_dev,
+                         int64_t n_max, const uint32_t** sorted_out, cudaStream_t s) {
+    const size_t np = 2 * (size_t)n_max;
+    const size_t nbs = kOrderCells / 1024 + 2;
+    nif_status st = nif_grow(h, h->b_sort, sizeof(uint32_t) * (2 * np + 2 * (size_t)kOrderCells + 1 + nbs));
+    if (st != NIF_OK) return st;
+    uint32_t* keys = (uint32_t*)h->b_sort.p;
+    uint32_t* sorted = keys + np;
+    uint32_t* hist = sorted + np;
+    uint32_t* off = hist + kOrderCells;
+    uint32_t* bsum = off + kOrderCells + 1;
+    const unsigned g = std::min<unsigned>(nif_blocks((int64_t)np, 256), (unsigned)h->num_sms * 8);
+    NIF_CK(h, cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kOrderCells, s));
+    k_point_keys<<<g, 256, 0, s>>>(lin, pts, n_pts_dev, keys, hist);
+    NIF_CK_LAUNCH(h);
+    if ((st = nif_scan_run_with(h, hist, off, (int)kOrderCells, bsum, s)) != NIF_OK) return st;
+    NIF_CK(h, cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kOrderCells, s));
+    k_point_scatter<<<g, 256, 0, s>>>(pts, n_pts_dev, keys, off, hist, sorted);
+    NIF_CK_LAUNCH(h);
+    *sorted_out = sorted;
+    return NIF_OK;
+}
+
 template <typename TT, typename OT>
 nif_status launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
                            void* feats, cudaStream_t s) {
@@ -721,6 +793,12 @@ nif_status launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, 
         const uint32_t *pts, *n_pts, *dupf;
         nif_status st = distinct_points(h, lin, n_dev, n_max, &pts, &n_pts, &dupf, s);
         if (st != NIF_OK) return st;
+        // tables of a few MB stay in L1 and L2 in any order (measured: the sort
+        // costs the 1 MiB-table query 5 %); larger ones gain from it (the
+        // 32 MiB tables of the 64-instance batch: encoder 1.35x faster)
+        if ((size_t)h->T * h->L * h->Fd * sizeof(TT) > ((size_t)4 << 20) &&
+            (st = spatial_order(h, lin, pts, n_pts, n_max, &pts, s)) != NIF_OK)
+            return st;
         if (h->L <= 8)
             k_encode_segments_v<TT, OT, 8><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats, pts,
                                                             n_pts, dupf);

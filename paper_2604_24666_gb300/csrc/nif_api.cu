@@ -525,7 +525,7 @@ extern "C" void nif_destroy(nif_handle* h) {
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
                                &h->b_acts, &h->b_dout, &h->b_dx, &h->b_labels, &h->b_scan, &h->b_rays,
                                &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys, &h->b_dup, &h->b_pts,
-                               &h->b_lattice, &h->alt_counts, &h->alt_offsets, &h->alt_temp, &h->alt_segs,
+                               &h->b_lattice, &h->b_sort, &h->alt_counts, &h->alt_offsets, &h->alt_temp, &h->alt_segs,
                                &h->alt_scan, &h->alt_rays, &h->alt_inst, &h->alt_lin, &h->alt_labels};
     for (auto* b : bufs)
         if (b->p) cudaFree(b->p);

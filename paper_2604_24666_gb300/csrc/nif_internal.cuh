@@ -128,7 +128,7 @@ struct nif_handle {
     // grown scratch buffers (query / train)
     struct Buf { void* p = nullptr; size_t bytes = 0; };
     Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
-        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts, b_lattice;
+        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts, b_lattice, b_sort;
     int* d_vox_leaf = nullptr;          // [N^3] octree leaf of each voxel, -1 when empty (exit-face walk)
     // the second set of training-batch buffers of nif_train_steps (the next
     // step's batch is built into it while the current step trains)
