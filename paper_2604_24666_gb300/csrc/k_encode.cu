@@ -1080,6 +1080,11 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
         const uint32_t *pts, *n_pts, *dupf;
         nif_status st = distinct_points(h, lin, n_dev, n_max, &pts, &n_pts, &dupf, s);
         if (st != NIF_OK) return st;
+        // rest-space order: a lane's run of points stays in one small region,
+        // so its cell cache flushes less at the middle levels
+        if ((size_t)h->T * h->L * h->Fd * sizeof(float) > ((size_t)4 << 20) &&
+            (st = spatial_order(h, lin, pts, n_pts, n_max, &pts, s)) != NIF_OK)
+            return st;
         NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
         const int per_sm = smem <= 100 * 1024 ? 2 : 1;      // 1024-thread blocks, two per SM when they fit
