@@ -278,26 +278,35 @@ def run_ours(args):
         kernels[k] = ent
 
     # ---- end to end through the public API, host buffers ----------------
-    n_rays_e2e = int(math.ceil(N_SEG / max(h_seg_per_ray(h, nif), 0.05) * 1.2))
-    rays_host = torch.from_numpy(S.sphere_rays(n_rays_e2e, seed=500 + rank)).pin_memory()
-    poses_e2e = S.poses(1, seed=600 + rank)
-    rays_dev = torch.empty_like(rays_host, device=dev)
-    for i in range(2):
-        rays_dev.copy_(rays_host, non_blocking=True)
-        nif.nif_train_step_rays(h.h, poses_e2e, rays_dev, N_SEG, want_loss=True)
+    # The same workload (N_POSES poses U[-1,1]^3 per step, rays of the training
+    # distribution per pose) given as host data: every step's rays are copied
+    # from pinned host memory and every step's loss is read back to the host,
+    # inside the timed region, by nif_train_steps_rays.
+    per = int(math.ceil(N_SEG / N_POSES / max(h_seg_per_ray(h, nif), 0.05) * 1.2)) + 1
+    n_rays_e2e = per * N_POSES
+    inst_e2e = torch.arange(0, n_rays_e2e + 1, per, dtype=torch.int32, device=dev)
+
+    def host_steps(k, seed):
+        rays = np.stack([S.sphere_rays(n_rays_e2e, seed=seed + 7919 * i) for i in range(k)])
+        poses = np.stack([S.poses(N_POSES, seed=seed + 104729 * i + 1) for i in range(k)])
+        return torch.from_numpy(rays).pin_memory(), poses
+
+    rays_w, poses_w = host_steps(args.warmup, 500 + 1000 * rank)
+    rays_t, poses_t = host_steps(args.steps, 900 + 1000 * rank)
+    nif.nif_train_steps_rays(h.h, poses_w, rays_w, N_SEG, inst_offsets=inst_e2e, lr_grid=1e-2, lr_mlp=1e-3)
     torch.cuda.synchronize()
     _barrier(ws)
-    t0 = time.perf_counter()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    for i in range(args.steps):
-        rays_dev.copy_(rays_host, non_blocking=True)
-        nif.nif_train_step_rays(h.h, poses_e2e, rays_dev, N_SEG, want_loss=True)    # loss read back to host
+    loss_e2e = nif.nif_train_steps_rays(h.h, poses_t, rays_t, N_SEG, inst_offsets=inst_e2e, lr_grid=1e-2,
+                                        lr_mlp=1e-3)       # every step's loss parts, read back as it ends
     f1.record(stream)
     torch.cuda.synchronize()
+    assert np.isfinite(loss_e2e).all()
     e2e_ms = _max_over_ranks(f0.elapsed_time(f1), ws)
     e2e = {"value": ws * args.steps * N_SEG / (e2e_ms / 1e3), "unit": "segments/s",
-           "h2d_bytes_per_step": int(rays_host.numel() * 4), "d2h_bytes_per_step": 48}
+           "h2d_bytes_per_step": int(n_rays_e2e * 32), "d2h_bytes_per_step": 48,
+           "call": "nif_train_steps_rays", "input": "host rays (pinned) and poses per step"}
     h.close()
 
     # ---- mixed-precision training, same workload ---------------------------

@@ -421,6 +421,24 @@ nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segments, int n
                            unsigned long long first_seed, float lr_grid, float lr_mlp, double* loss_host,
                            void* stream);
 
+/* n_steps training steps on caller-given rays held in HOST memory: step i
+ * trains, as nif_train_step_rays does, on the n_rays rays at
+ * rays_host + i * n_rays with the n_inst poses at poses_host + i * n_inst
+ * (inst_offsets_dev, a device array shared by all steps, nullable when
+ * n_inst == 1). Each step's rays are copied to the device and its batch is
+ * built on the second internal stream while the previous step trains
+ * (rays_host in pinned memory lets the copy overlap; pageable memory works
+ * and serialises). loss_host (nullable): [n_steps][6] loss parts as
+ * nif_train_step_rays gives them, each step's read back as the step ends on
+ * `stream`; the call then blocks until the last step is done and reports a
+ * non-finite loss or a device-side error. Without loss_host it returns once
+ * the work is enqueued, and rays_host must stay unchanged until `stream` has
+ * completed it. */
+nif_status nif_train_steps_rays(nif_handle* h, int n_steps, const nif_pose* poses_host, int n_inst,
+                                const nif_ray* rays_host, const int* inst_offsets_dev, int n_rays,
+                                int64_t n_segments, float lr_grid, float lr_mlp, double* loss_host,
+                                void* stream);
+
 /* Pose fitting (the paper names learned deformations as future work): the
  * gradient of the task loss of Sec. 2.4 with respect to the n_inst
  * deformation parameters, tables, weights and s held fixed, for the

@@ -484,8 +484,11 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_sm(GridInfo g, Coa
 // into the block's shared-memory copy, the rest into global memory, where the
 // two corners of an x-edge whose rows are 2m and 2m+1 (always for an even
 // cell x index on a hashed level: the rows differ in bit 0 only; for an even
-// base row on a dense level) share one 16-byte vector reduction.
-constexpr int kRun = 64;
+// base row on a dense level) share one 16-byte vector reduction. Chunks of
+// points go to warps from a counter, so a warp whose chunks flushed little
+// takes more of them (with a fixed stride a block's warps waited at its final
+// barrier for the slowest one).
+constexpr int kRun = 32;
 
 __device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
@@ -524,7 +527,8 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
                                                                  float* __restrict__ dtab,
                                                                  const uint32_t* __restrict__ pts,
                                                                  const uint32_t* __restrict__ n_pts_dev,
-                                                                 const uint32_t* __restrict__ dupf) {
+                                                                 const uint32_t* __restrict__ dupf,
+                                                                 uint32_t* __restrict__ next) {
     extern __shared__ float sacc[];
     const int nsh = cs.soff[cs.Lc];
     for (int i = threadIdx.x; i < nsh; i += blockDim.x) sacc[i] = 0.f;
@@ -545,9 +549,11 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
     const int64_t n_points = *n_pts_dev;
     const int64_t chunks = (n_points + 2 * kRun - 1) / (2 * kRun);
     const int64_t tasks = chunks * groups;
-    const int warps_total = gridDim.x * (blockDim.x >> 5);
-    for (int64_t task = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < tasks;
-         task += warps_total) {
+    for (;;) {
+        uint32_t tk = 0;
+        if (lane == 0) tk = atomicAdd(next, 1u);
+        const int64_t task = (int64_t)__shfl_sync(0xffffffffu, tk, 0);
+        if (task >= tasks) break;
         const int64_t c = task / groups;
         const int grp = (int)(task - c * groups);
         const int t = grp * tpw + term_in_warp;           // gamma term in [0, P)
@@ -1087,9 +1093,11 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
             return st;
         NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
-        const int per_sm = smem <= 100 * 1024 ? 2 : 1;      // 1024-thread blocks, two per SM when they fit
-        k_encode_segments_bwd_rl<<<h->num_sms * per_sm, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats,
-                                                                         dtables, pts, n_pts, dupf);
+        // one 1024-thread block per SM (64 registers a thread fill the register
+        // file); its warps take chunks from the task counter
+        NIF_CK(h, cudaMemsetAsync(h->d_next + 1, 0, sizeof(uint32_t), s));
+        k_encode_segments_bwd_rl<<<h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables, pts,
+                                                                n_pts, dupf, h->d_next + 1);
         NIF_CK_LAUNCH(h);
         return NIF_OK;
     }

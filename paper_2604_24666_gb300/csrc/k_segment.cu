@@ -931,11 +931,11 @@ static void launch_traverse_w(nif_handle* h, const nif_ray* rays, const int* ins
             emit_skip_le, h->d_status);
         return;
     }
-    cudaMemsetAsync(h->d_ray_next, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(h->d_next, 0, sizeof(uint32_t), s);
     const unsigned grid = std::min<unsigned>(nif_blocks(n_rays, 32 * W), (unsigned)h->num_sms * (32 / W));
     constexpr int M = MODE == kModeTemp ? kModeTemp : kModeCount;
     k_seg_traverse_p<M, W><<<grid, 32 * W, 0, s>>>(rays, inst_off, n_inst, n_rays, tv, h->d_corners, h->d_aabb,
-                                                   counts, segs, cap, cursor, h->d_ray_next, h->d_status);
+                                                   counts, segs, cap, cursor, h->d_next, h->d_status);
 }
 
 template <int MODE>

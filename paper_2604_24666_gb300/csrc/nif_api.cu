@@ -456,7 +456,7 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
     CKC(cudaMemset(h->d_lossacc, 0, sizeof(double) * 16));
     CKC(cudaMalloc(&h->d_count, sizeof(int) * 4));
     CKC(cudaMemset(h->d_count, 0, sizeof(int) * 4));
-    CKC(cudaMalloc(&h->d_ray_next, sizeof(uint32_t) * 4));
+    CKC(cudaMalloc(&h->d_next, sizeof(uint32_t) * 4));
     CKC(cudaMallocHost(&h->h_pinned, sizeof(int) * 16));
     CKC(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking));
@@ -519,7 +519,7 @@ extern "C" void nif_destroy(nif_handle* h) {
                     h->d_leaf_vox, h->d_leaf_lat, h->d_corners, h->d_aabb, h->d_pose, h->d_params, h->d_grad,
                     h->d_m, h->d_v, h->d_tables_h, h->d_w_bf16, h->d_w_f16, h->d_wt_bf16, h->d_wt_f16, h->d_ls,
                     h->d_w_x3, h->d_vox_leaf, h->d_status, h->d_lossacc, h->d_count,
-                    h->d_ray_next};
+                    h->d_next};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
@@ -534,6 +534,7 @@ extern "C" void nif_destroy(nif_handle* h) {
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->aux2) cudaStreamDestroy(h->aux2);
+    if (h->h_loss) cudaFreeHost(h->h_loss);
     if (h->ev_batch) cudaEventDestroy(h->ev_batch);
     if (h->ev_step) cudaEventDestroy(h->ev_step);
     for (auto e : h->prof_pool) cudaEventDestroy(e);
@@ -1154,6 +1155,16 @@ extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst
     return nif_reconstruct_run(h, rays, inst_off, n_inst, n_rays, offs, segs, total, lin, out, hits, flags, s);
 }
 
+// The error a kernel latched on the device (a non-finite loss, a timed-out
+// wait), cleared once read; the caller has synchronised the work it checks.
+static nif_status latched_status(nif_handle* h) {
+    int dst = 0;
+    NIF_CK(h, cudaMemcpy(&dst, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dst == 0) return NIF_OK;
+    cudaMemset(h->d_status, 0, sizeof(int));
+    return nif_fail(h, (nif_status)dst, dst == NIF_ERR_NAN ? "non-finite loss" : "device-side error latched by a kernel");
+}
+
 // The batch of one training step: segments of whole rays (at most n_segments,
 // in ray order), their linearization and labels, into the handle's batch
 // buffers; the hit count goes to *n_hit (device).
@@ -1242,12 +1253,7 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         NIF_CK(h, cudaMemcpy(acc, h->d_lossacc, sizeof(acc), cudaMemcpyDeviceToHost));
         loss_host[0] = acc[8];
         for (int i = 0; i < 5; i++) loss_host[1 + i] = acc[9 + i];
-        int dst = 0;
-        NIF_CK(h, cudaMemcpy(&dst, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-        if (dst != 0) {
-            cudaMemset(h->d_status, 0, sizeof(int));
-            return nif_fail(h, (nif_status)dst, dst == NIF_ERR_NAN ? "non-finite loss" : "device-side error latched by a kernel");
-        }
+        return latched_status(h);
     }
     return NIF_OK;
 }
@@ -1408,18 +1414,18 @@ static void swap_batch(nif_handle* h) {
     std::swap(h->b_labels, h->alt_labels);
 }
 
-extern "C" nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segments, int n_poses,
-                                      unsigned long long first_seed, float lr_grid, float lr_mlp, double* loss_host,
-                                      void* stream) {
-    if (!h || n_steps < 1 || n_segments < 1 || n_poses < 1) return NIF_ERR_ARG;
+// The pipeline of nif_train_steps and nif_train_steps_rays: batch i is built
+// by build(i, n_hit, stream) into buffer set i % 2 with its hit count in
+// counter word 2 + i % 2 (batch 0 on `s`, the others on the third stream
+// beside the previous step); step i trains on `s`, then done(i) enqueues on
+// `s`. The handle's own buffers are always the set of the next thing enqueued.
+// n_rays is read after build(0) has set it; loss_last (nullable) receives the
+// last step's loss parts.
+template <class Build, class Done>
+static nif_status train_pipeline(nif_handle* h, int n_steps, const int& n_rays, int64_t n_segments, float lr_grid,
+                                 float lr_mlp, double* loss_last, cudaStream_t s, Build build, Done done) {
     nif_status st;
-    if ((h->cfg.flags & NIF_FLAG_MIXED_TRAINING) && (st = check_mixed(h)) != NIF_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
-    // batch i sits in buffer set i % 2 with its hit count in counter word 2 + i % 2;
-    // the handle's own buffers are always the set of the next thing enqueued
-    int n_rays = 0, nr = 0;
-    if ((st = sampled_batch(h, n_segments, n_poses, first_seed, nullptr, &n_rays, h->d_count + 2, s)) != NIF_OK)
-        return st;
+    if ((st = build(0, h->d_count + 2, s)) != NIF_OK) return st;
     NIF_CK(h, cudaEventRecord(h->ev_batch, s));
     // Where the next batch starts: the FP32 path's persistent split-TF32
     // GEMMs lose SMs to a concurrent batch (measured: forward 0.28 -> 0.59 ms),
@@ -1431,10 +1437,8 @@ extern "C" nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segm
         swap_batch(h);
         NIF_CK(h, cudaStreamWaitEvent(h->aux2, h->ev_batch, 0));   // batch i built: geometry and cursor free
         NIF_CK(h, cudaStreamWaitEvent(h->aux2, h->ev_step, 0));    // step i - 1 done with this set
-        nif_status r = sampled_batch(h, n_segments, n_poses, first_seed + (unsigned long long)(i + 1), nullptr, &nr,
-                                     h->d_count + 2 + (i + 1) % 2, h->aux2);
+        nif_status r = build(i + 1, h->d_count + 2 + (i + 1) % 2, h->aux2);
         if (r != NIF_OK) return r;
-        if (nr != n_rays) return nif_fail(h, NIF_ERR_STATE, "training batches of one call differ in ray count");
         NIF_CK(h, cudaEventRecord(h->ev_batch, h->aux2));
         return NIF_OK;
     };
@@ -1447,8 +1451,9 @@ extern "C" nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segm
             swap_batch(h);                                                  // back to step i's set
         }
         if ((st = train_compute(h, n_rays, n_segments, h->d_count + 2 + i % 2, lr_grid, lr_mlp,
-                                more ? nullptr : loss_host, s, early ? nullptr : h->ev_step)) != NIF_OK)
+                                more ? nullptr : loss_last, s, early ? nullptr : h->ev_step)) != NIF_OK)
             return st;
+        if ((st = done(i)) != NIF_OK) return st;
         if (more && !early && (st = next_batch(i)) != NIF_OK) return st;
         if (early) {
             NIF_CK(h, cudaEventRecord(h->ev_step, s));                      // end of step i
@@ -1456,4 +1461,69 @@ extern "C" nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segm
         }
     }
     return NIF_OK;
+}
+
+extern "C" nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segments, int n_poses,
+                                      unsigned long long first_seed, float lr_grid, float lr_mlp, double* loss_host,
+                                      void* stream) {
+    if (!h || n_steps < 1 || n_segments < 1 || n_poses < 1) return NIF_ERR_ARG;
+    nif_status st;
+    if ((h->cfg.flags & NIF_FLAG_MIXED_TRAINING) && (st = check_mixed(h)) != NIF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int n_rays = -1;
+    auto build = [&](int i, int* n_hit, cudaStream_t bs) -> nif_status {
+        int nr = 0;
+        nif_status r = sampled_batch(h, n_segments, n_poses, first_seed + (unsigned long long)i, nullptr, &nr, n_hit,
+                                     bs);
+        if (r != NIF_OK) return r;
+        if (n_rays >= 0 && nr != n_rays)
+            return nif_fail(h, NIF_ERR_STATE, "training batches of one call differ in ray count");
+        n_rays = nr;
+        return NIF_OK;
+    };
+    return train_pipeline(h, n_steps, n_rays, n_segments, lr_grid, lr_mlp, loss_host, s, build,
+                          [](int) { return NIF_OK; });
+}
+
+extern "C" nif_status nif_train_steps_rays(nif_handle* h, int n_steps, const nif_pose* poses, int n_inst,
+                                           const nif_ray* rays_host, const int* inst_off, int n_rays,
+                                           int64_t n_segments, float lr_grid, float lr_mlp, double* loss_host,
+                                           void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    if (n_steps < 1 || n_rays < 1 || n_segments < 1 || !rays_host)
+        return nif_fail(h, NIF_ERR_ARG, "n_steps / n_rays / n_segments / rays");
+    nif_status st;
+    for (int i = 0; i < n_steps; i++)
+        if ((st = check_inst(h, poses ? poses + (size_t)i * n_inst : nullptr, n_inst, inst_off, n_rays)) != NIF_OK)
+            return st;
+    if ((h->cfg.flags & NIF_FLAG_MIXED_TRAINING) && (st = check_mixed(h)) != NIF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // each step's loss parts go to pinned staging on `s` as the step ends
+    if (loss_host && h->h_loss_steps < n_steps) {
+        if (h->h_loss) cudaFreeHost(h->h_loss);
+        h->h_loss = nullptr;
+        h->h_loss_steps = 0;
+        NIF_CK(h, cudaMallocHost(&h->h_loss, sizeof(double) * 6 * (size_t)n_steps));
+        h->h_loss_steps = n_steps;
+    }
+    auto build = [&](int i, int* n_hit, cudaStream_t bs) -> nif_status {
+        nif_status r = nif_grow(h, h->b_rays, sizeof(nif_ray) * (size_t)n_rays);
+        if (r != NIF_OK) return r;
+        NIF_CK(h, cudaMemcpyAsync(h->b_rays.p, rays_host + (size_t)i * n_rays, sizeof(nif_ray) * (size_t)n_rays,
+                                  cudaMemcpyHostToDevice, bs));
+        return train_batch(h, poses + (size_t)i * n_inst, n_inst, (const nif_ray*)h->b_rays.p, inst_off, n_rays,
+                           n_segments, n_hit, bs);
+    };
+    auto done = [&](int i) -> nif_status {
+        if (loss_host)
+            NIF_CK(h, cudaMemcpyAsync(h->h_loss + 6 * (size_t)i, h->d_lossacc + 8, sizeof(double) * 6,
+                                      cudaMemcpyDeviceToHost, s));
+        return NIF_OK;
+    };
+    if ((st = train_pipeline(h, n_steps, n_rays, n_segments, lr_grid, lr_mlp, nullptr, s, build, done)) != NIF_OK)
+        return st;
+    if (!loss_host) return NIF_OK;
+    NIF_CK(h, cudaStreamSynchronize(s));
+    std::memcpy(loss_host, h->h_loss, sizeof(double) * 6 * (size_t)n_steps);
+    return latched_status(h);
 }

@@ -117,12 +117,15 @@ struct nif_handle {
     // a third stream for nif_train_steps' next batch, and its ordering events
     cudaStream_t aux2 = nullptr;
     cudaEvent_t ev_batch = nullptr, ev_step = nullptr;
+    double* h_loss = nullptr;           // pinned: per-step loss parts of nif_train_steps_rays
+    int h_loss_steps = 0;
 
     // device status word + scratch
     int* d_status = nullptr;
     double* d_lossacc = nullptr;        // [16] loss accumulators
     int* d_count = nullptr;             // [4] counters
-    uint32_t* d_ray_next = nullptr;     // ray counter of the persistent traversal
+    uint32_t* d_next = nullptr;         // [4] work counters: [0] rays of the persistent traversal,
+                                        // [1] tasks of the encoding backward
     int* h_pinned = nullptr;            // pinned host word(s)
 
     // grown scratch buffers (query / train)

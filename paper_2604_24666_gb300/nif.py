@@ -114,6 +114,8 @@ def lib() -> ctypes.CDLL:
                                 _vp], ctypes.c_int),
             "nif_train_steps": ([_vp, ctypes.c_int, _i64, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_float, ctypes.c_float,
                                  _vp, _vp], ctypes.c_int),
+            "nif_train_steps_rays": ([_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _i64, ctypes.c_float,
+                                      ctypes.c_float, _vp, _vp], ctypes.c_int),
             "nif_sample_rays": ([_vp, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int, _vp, _vp], ctypes.c_int),
             "nif_segments_noalloc": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _i64,
                                       ctypes.POINTER(_i64), _vp], ctypes.c_int),
@@ -462,6 +464,22 @@ def nif_train_steps(h, n_steps, n_segments, n_poses, first_seed, lr_grid=1e-2, l
     loss = np.zeros(6, np.float64) if want_loss else None
     _check(h, lib().nif_train_steps(h, n_steps, n_segments, n_poses, first_seed, lr_grid, lr_mlp, _ptr(loss),
                                     _stream(stream)))
+    return loss
+
+
+def nif_train_steps_rays(h, poses, rays_host, n_segments, inst_offsets=None, lr_grid=1e-2, lr_mlp=1e-3,
+                         want_loss=True, stream=None):
+    """len(rays_host) training steps; step i on the rays rays_host[i] (a CPU tensor
+    [n_steps, n_rays, 8], pinned for overlap) and the poses poses[i] ([n_steps, n_inst, 3]);
+    returns every step's loss parts [n_steps, 6] when want_loss."""
+    assert rays_host.device.type == "cpu" and rays_host.dim() == 3 and rays_host.shape[2] == 8
+    n_steps, n_rays = rays_host.shape[0], rays_host.shape[1]
+    pa = np.asarray(poses, np.float32).reshape(n_steps, -1, 3)
+    p, _ = _poses(pa)
+    rays_host = rays_host.contiguous()
+    loss = np.zeros((n_steps, 6), np.float64) if want_loss else None
+    _check(h, lib().nif_train_steps_rays(h, n_steps, p, pa.shape[1], _ptr(rays_host), _ptr(inst_offsets), n_rays,
+                                         n_segments, lr_grid, lr_mlp, _ptr(loss), _stream(stream)))
     return loss
 
 

@@ -46,3 +46,46 @@ def test_train_steps_equal_single_steps(nif, torus, mixed):
     np.testing.assert_allclose(la[1:], lb[1:], rtol=5e-2, atol=1e-3)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_train_steps_rays_equal_single_steps(nif, torus, mixed):
+    """nif_train_steps_rays (rays from pinned host memory, copied and batched
+    beside the previous step, every step's loss read back) against the same
+    steps through nif_train_step_rays; two instances per step."""
+    net = S.NetConfig()
+    kw = dict(precision=nif.NIF_BF16, flags=nif.NIF_FLAG_MIXED_TRAINING) if mixed else {}
+    a = nif.Nif(net, torus, seed=11, **kw)
+    b = nif.Nif(net, torus, seed=11, **kw)
+    K, per, n_seg = 6, 3000, 1 << 13
+    rays = np.stack([np.concatenate([S.sphere_rays(per, seed=700 + 2 * i), S.sphere_rays(per, seed=701 + 2 * i)])
+                     for i in range(K)])
+    poses = np.stack([S.poses(2, seed=800 + i) for i in range(K)]).astype(np.float32)
+    inst = torch.tensor([0, per, 2 * per], dtype=torch.int32, device="cuda")
+    rays_host = torch.from_numpy(rays).pin_memory()
+    for lr_grid, lr_mlp, rtol in ((0.0, 0.0, 1e-9), (1e-2, 5e-3, 5e-2)):
+        la = nif.nif_train_steps_rays(a.h, poses, rays_host, n_seg, inst_offsets=inst, lr_grid=lr_grid,
+                                      lr_mlp=lr_mlp)
+        lb = np.stack([nif.nif_train_step_rays(b.h, poses[i], torch.from_numpy(rays[i]).cuda(), n_seg,
+                                               inst_offsets=inst, lr_grid=lr_grid, lr_mlp=lr_mlp)
+                       for i in range(K)])
+        assert la.shape == (K, 6) and np.isfinite(la).all()
+        # without learning every step's loss is a function of its own batch; with
+        # learning the trajectories agree up to the order of float atomics
+        np.testing.assert_allclose(la, lb, rtol=rtol, atol=1e-12 if rtol < 1e-6 else 1e-3)
+    # no loss requested: enqueued only, then the same state as a synchronised call
+    assert nif.nif_train_steps_rays(a.h, poses[:2], rays_host[:2], n_seg, inst_offsets=inst, want_loss=False) is None
+    torch.cuda.synchronize()
+    a.close()
+    b.close()
+
+
+def test_train_steps_rays_rejects_bad_arguments(nif, torus):
+    a = nif.Nif(S.NetConfig(), torus)
+    rays_host = torch.from_numpy(np.stack([S.sphere_rays(100, seed=1)] * 2))
+    bad = np.array([[[2.0, 0.0, 0.0]], [[0.0, 0.0, 0.0]]], np.float32)
+    with pytest.raises(nif.NifError):
+        nif.nif_train_steps_rays(a.h, bad, rays_host, 1000)       # a pose out of range in step 0
+    with pytest.raises(nif.NifError):
+        nif.nif_train_steps_rays(a.h, np.zeros((2, 2, 3), np.float32), rays_host, 1000)   # n_inst 2, no offsets
+    a.close()
