@@ -556,18 +556,28 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
         if (task >= tasks) break;
         const int64_t c = task / groups;
         const int grp = (int)(task - c * groups);
-        const int t = grp * tpw + term_in_warp;           // gamma term in [0, P)
-        const bool active = t < g.P;
-        const int tc = active ? t : 0;
+        // a group with fewer terms than level groups (the last one when tpw
+        // does not divide P) gives each term nr of them, each walking its own
+        // part of the chunk, instead of leaving them idle
+        const int a = min(g.P - grp * tpw, tpw);          // terms in this group
+        const int nr = tpw / a;                           // parts per term
+        const int t = grp * tpw + term_in_warp % a;       // gamma term in [0, P)
+        const int sub = term_in_warp / a;                 // part of the chunk (idle when >= nr)
+        const int tc = t;
         int cx = -1, cy = 0, cz = 0;                      // current cell (cx < 0: none)
         float2 cacc[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) cacc[q] = make_float2(0.f, 0.f);
-        const int64_t k_end = (c + 1) * 2 * kRun < n_points ? (c + 1) * 2 * kRun : n_points;
+        const int64_t k0 = c * 2 * kRun;
+        const int span = (int)(k0 + 2 * kRun < n_points ? 2 * kRun : n_points - k0);
+        const int part = (span + nr - 1) / nr;
+        const int kb = sub < nr ? sub * part : span;      // this part's points: k0 + [kb, ke)
+        const int ke = min(kb + part, span);
         const int base = term_in_warp * g.L;              // first lane of this term's level group
-        for (int64_t k = c * 2 * kRun; k < k_end; k++) {  // warp-uniform trip count (shuffles below)
+        for (int i = 0; i < part; i++) {                  // warp-uniform trip count (shuffles below)
+            const bool active = kb + i < ke;
             {
-                const uint32_t pt = pts[k];
+                const uint32_t pt = pts[k0 + (active ? kb + i : 0)];
                 const int64_t s = pt >> 1;
                 const int e = (int)(pt & 1);
                 // the term's u is the same for all L levels: lanes base..base+2
@@ -695,6 +705,7 @@ nif_status distinct_points(nif_handle* h, const nif_linseg* lin, const uint32_t*
                            const uint32_t** pts_out, const uint32_t** n_pts_out, const uint32_t** dupf_out,
                            cudaStream_t s) {
     nif_status st;
+    h->enc_points = nif_handle::PointList{};             // its buffers are rewritten here
     if ((st = nif_grow(h, h->b_dup, sizeof(uint32_t) * (2 * (size_t)n_max + 1))) != NIF_OK) return st;
     if ((st = nif_grow(h, h->b_pts, sizeof(uint32_t) * 2 * (size_t)n_max)) != NIF_OK) return st;
     const int nb = (int)nif_blocks(n_max, 1024);
@@ -802,9 +813,9 @@ nif_status launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, 
         // tables of a few MB stay in L1 and L2 in any order (measured: the sort
         // costs the 1 MiB-table query 5 %); larger ones gain from it (the
         // 32 MiB tables of the 64-instance batch: encoder 1.35x faster)
-        if ((size_t)h->T * h->L * h->Fd * sizeof(TT) > ((size_t)4 << 20) &&
-            (st = spatial_order(h, lin, pts, n_pts, n_max, &pts, s)) != NIF_OK)
-            return st;
+        const bool sorted = (size_t)h->T * h->L * h->Fd * sizeof(TT) > ((size_t)4 << 20);
+        if (sorted && (st = spatial_order(h, lin, pts, n_pts, n_max, &pts, s)) != NIF_OK) return st;
+        h->enc_points = nif_handle::PointList{lin, n_dev, n_max, pts, n_pts, dupf, sorted};
         if (h->L <= 8)
             k_encode_segments_v<TT, OT, 8><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats, pts,
                                                             n_pts, dupf);
@@ -1057,7 +1068,7 @@ nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n,
 }
 
 nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
-                                       const float* dfeats, float* dtables, cudaStream_t s) {
+                                       const float* dfeats, float* dtables, cudaStream_t s, bool reuse_points) {
     NifProf prof_(h, "encode_bwd", s);
     if (n_max <= 0) return NIF_OK;
     if (h->concat) {
@@ -1084,13 +1095,20 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
     size_t smem = sizeof(float) * (size_t)cs.soff[cs.Lc];
     if (32 % h->L == 0 && h->L >= 4) {      // a level group holds the 3 lanes that evaluate u
         const uint32_t *pts, *n_pts, *dupf;
-        nif_status st = distinct_points(h, lin, n_dev, n_max, &pts, &n_pts, &dupf, s);
-        if (st != NIF_OK) return st;
         // rest-space order: a lane's run of points stays in one small region,
         // so its cell cache flushes less at the middle levels
-        if ((size_t)h->T * h->L * h->Fd * sizeof(float) > ((size_t)4 << 20) &&
-            (st = spatial_order(h, lin, pts, n_pts, n_max, &pts, s)) != NIF_OK)
-            return st;
+        const bool sorted = (size_t)h->T * h->L * h->Fd * sizeof(float) > ((size_t)4 << 20);
+        const nif_handle::PointList& pl = h->enc_points;
+        if (reuse_points && pl.pts && pl.lin == lin && pl.n_dev == n_dev && pl.n_max == n_max &&
+            pl.sorted == sorted) {
+            pts = pl.pts;                                 // as the forward of this step left them
+            n_pts = pl.n_pts;
+            dupf = pl.dupf;
+        } else {
+            nif_status st = distinct_points(h, lin, n_dev, n_max, &pts, &n_pts, &dupf, s);
+            if (st != NIF_OK) return st;
+            if (sorted && (st = spatial_order(h, lin, pts, n_pts, n_max, &pts, s)) != NIF_OK) return st;
+        }
         NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
         // one 1024-thread block per SM (64 registers a thread fill the register

@@ -1230,7 +1230,7 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         if ((st = nif_mlp_dw_tc_run(h, feat, acts16, dys, n_dev, n, np, kLd, h->aux)) != NIF_OK) return st;
         NIF_CK(h, cudaEventRecord(h->ev_join, h->aux));
         if (ev_bwd) NIF_CK(h, cudaEventRecord(ev_bwd, s));
-        if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK)
+        if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s, true)) != NIF_OK)
             return st;
         NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
         if ((st = nif_grad_check_run(h, s)) != NIF_OK) return st;
@@ -1242,7 +1242,7 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         // weight gradients on the second stream, beside dX_0 and the encoding backward
         if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s, true, h->aux)) != NIF_OK) return st;
         if (ev_bwd) NIF_CK(h, cudaEventRecord(ev_bwd, s));
-        if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK)
+        if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s, true)) != NIF_OK)
             return st;
         NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
         if ((st = nif_adam_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;

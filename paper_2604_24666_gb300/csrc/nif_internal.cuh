@@ -132,6 +132,16 @@ struct nif_handle {
     struct Buf { void* p = nullptr; size_t bytes = 0; };
     Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
         b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts, b_lattice, b_sort;
+    // the distinct end points of the last segment encoding (in b_dup, b_pts,
+    // b_sort; sorted: in rest-space order), which the backward of the same
+    // segments in a training step takes instead of listing them again
+    struct PointList {
+        const nif_linseg* lin = nullptr;
+        const uint32_t* n_dev = nullptr;
+        int64_t n_max = 0;
+        const uint32_t *pts = nullptr, *n_pts = nullptr, *dupf = nullptr;
+        bool sorted = false;
+    } enc_points;
     int* d_vox_leaf = nullptr;          // [N^3] octree leaf of each voxel, -1 when empty (exit-face walk)
     // the second set of training-batch buffers of nif_train_steps (the next
     // step's batch is built into it while the current step trains)
@@ -241,9 +251,11 @@ nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const u
                                    cudaStream_t s);
 nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n, const float* dfeats,
                                      float* dtables, float* dpts, cudaStream_t s);
+// reuse_points: the segment encoding just before, on the same stream, read the
+// same lin / n_dev / n_max; its list of distinct end points is taken as it is
 nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev,
                                        int64_t n_max, const float* dfeats, float* dtables,
-                                       cudaStream_t s);
+                                       cudaStream_t s, bool reuse_points = false);
 nif_status nif_encode_segments_dp_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n,
                                       const float* dfeats, float* dp, cudaStream_t s);
 nif_status nif_pose_grad_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const float* dp,
