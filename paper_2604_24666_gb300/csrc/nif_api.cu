@@ -1186,9 +1186,10 @@ static nif_status train_batch(nif_handle* h, const nif_pose* poses, int n_inst, 
 
 // Forward, losses, backward and optimizer step on the batch in the handle's
 // batch buffers (n_rays rays, at most n_segments segments; hit count *n_hit).
-// ev_bwd (nullable) is recorded on s before the encoding backward.
+// ev_next (nullable) is recorded on s where the next batch may start beside
+// the step: after the encoding forward (FP32 path only).
 static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, const int* n_hit, float lr_grid,
-                                float lr_mlp, double* loss_host, cudaStream_t s, cudaEvent_t ev_bwd = nullptr) {
+                                float lr_mlp, double* loss_host, cudaStream_t s, cudaEvent_t ev_next = nullptr) {
     nif_status st;
     const bool mixed = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
     uint32_t* offs = (uint32_t*)h->b_offsets.p;
@@ -1229,7 +1230,6 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         NIF_CK(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
         if ((st = nif_mlp_dw_tc_run(h, feat, acts16, dys, n_dev, n, np, kLd, h->aux)) != NIF_OK) return st;
         NIF_CK(h, cudaEventRecord(h->ev_join, h->aux));
-        if (ev_bwd) NIF_CK(h, cudaEventRecord(ev_bwd, s));
         if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s, true)) != NIF_OK)
             return st;
         NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
@@ -1237,11 +1237,11 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         if ((st = nif_adam_scaled_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
     } else {
         if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s)) != NIF_OK) return st;
+        if (ev_next) NIF_CK(h, cudaEventRecord(ev_next, s));
         if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
         if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, true, n_hit)) != NIF_OK) return st;
         // weight gradients on the second stream, beside dX_0 and the encoding backward
         if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s, true, h->aux)) != NIF_OK) return st;
-        if (ev_bwd) NIF_CK(h, cudaEventRecord(ev_bwd, s));
         if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s, true)) != NIF_OK)
             return st;
         NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
@@ -1427,11 +1427,13 @@ static nif_status train_pipeline(nif_handle* h, int n_steps, const int& n_rays, 
     nif_status st;
     if ((st = build(0, h->d_count + 2, s)) != NIF_OK) return st;
     NIF_CK(h, cudaEventRecord(h->ev_batch, s));
-    // Where the next batch starts: the FP32 path's persistent split-TF32
-    // GEMMs lose SMs to a concurrent batch (measured: forward 0.28 -> 0.59 ms),
-    // so its next batch starts beside the encoding backward (step 3.30 ms vs
-    // 3.34 ms); the mixed path's forward shares the GPU well and its next
-    // batch starts with the step (2.79 ms vs 2.91 ms).
+    // Where the next batch starts, measured: on the FP32 path after the
+    // encoding forward (step 3.12 ms; with the step 3.15 ms, where the
+    // persistent split-TF32 forward GEMMs lose SMs to it; beside the
+    // encoding backward 3.27 ms, where it competes with the backward and the
+    // weight gradients, both on whole SMs); the mixed path's forward shares
+    // the GPU well and its next batch starts with the step (2.79 ms vs
+    // 2.91 ms beside the encoding backward).
     const bool early = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
     auto next_batch = [&](int i) -> nif_status {
         swap_batch(h);

@@ -89,3 +89,55 @@ def test_train_steps_rays_rejects_bad_arguments(nif, torus):
     with pytest.raises(nif.NifError):
         nif.nif_train_steps_rays(a.h, np.zeros((2, 2, 3), np.float32), rays_host, 1000)   # n_inst 2, no offsets
     a.close()
+
+
+@pytest.mark.parametrize("levels,log2T", [(8, 14), (16, 19)])
+def test_train_step_table_gradient_matches_stages(nif, torus, levels, log2T):
+    """The table gradient of a whole training step equals the stage-by-stage
+    one on the same batch. The step's encoding backward takes the list of
+    distinct end points, and with 64 MiB tables their rest-space order, from
+    the step's forward. One Adam step from zero moments moves every parameter
+    by lr * g / (|g| + 1e-15), so the step's table change must be zero exactly
+    where the stage gradient is zero and must have its sign where it is
+    clearly nonzero."""
+    from tests.gpu_common import random_tables
+    net = S.NetConfig(levels=levels, log2_table=log2T)
+    pose = (0.4, -0.7, 0.3)
+    rays_np = S.sphere_rays(3000, seed=321)
+    tables = random_tables(net, 322, scale=0.5)
+    _, ws, _ = S.init_params(net, seed=323)
+    dev = torch.device("cuda:0")
+    rays = torch.from_numpy(rays_np).to(dev)
+    # stage by stage
+    a = nif.Nif(net, torus)
+    a.set_params(tables, ws)
+    offs, segs = nif.nif_segments(a.h, [pose], rays)
+    lin = nif.nif_linearize(a.h, [pose], rays, segs)
+    lab = nif.nif_labels(a.h, segs, lin)
+    feat = nif.nif_encode_segments(a.h, lin, net.in_dim)
+    n = feat.shape[0]
+    acts = torch.zeros((net.mlp_depth, n, net.mlp_width), dtype=torch.float32, device=dev)
+    out = nif.nif_mlp_forward(a.h, feat, acts=acts)
+    nif.nif_zero_grad(a.h)
+    _, dout = nif.nif_loss(a.h, out, lab, lin)
+    dx = nif.nif_mlp_backward(a.h, feat, acts, dout)
+    dtab = torch.zeros((net.levels, 1 << net.log2_table, 2), dtype=torch.float32, device=dev)
+    nif.nif_encode_segments_backward(a.h, lin, dx, dtab)
+    torch.cuda.synchronize()
+    g = dtab.cpu().numpy()
+    a.close()
+    # one training step on the same rays, every segment in the batch
+    b = nif.Nif(net, torus)
+    b.set_params(tables, ws)
+    t0 = b.get_params()[0].copy()
+    lr = 1e-3
+    nif.nif_train_step_rays(b.h, [pose], rays, 4 * n + 1024, lr_grid=lr, lr_mlp=0.0)
+    delta = t0 - b.get_params()[0]
+    b.close()
+    assert n > 1000 and np.count_nonzero(g) > 1000
+    np.testing.assert_array_equal(delta[g == 0], 0.0)
+    big = np.abs(g) > 1e-4 * np.abs(g).max()
+    # |delta| is lr up to the FP32 rounding of the parameter update
+    np.testing.assert_allclose(np.abs(delta[big]), lr, rtol=1e-3)
+    agree = np.sign(delta[big]) == np.sign(g[big])
+    assert agree.all(), (np.count_nonzero(~agree), big.sum())
