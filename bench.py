@@ -67,7 +67,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
 
@@ -126,17 +126,29 @@ def _max_over_ranks(x, ws):
 # ---------------------------------------------------------------------------
 # Oracle timing (the CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
+_ORACLE_SETUP = {}
+
+
+def _oracle_setup():
+    """The training workload's mesh, voxelization and initial parameters for
+    the oracle, built once per process (outside every timed interval)."""
+    if not _ORACLE_SETUP:
+        import oracle as O
+        from paper_2604_24666_gb300 import synth as S
+        net = S.WORKLOADS[TRAIN_WORKLOAD]["net"]
+        mesh = S.make_mesh(S.WORKLOADS[TRAIN_WORKLOAD]["shape"])
+        occ, ptr, idx = O.voxelize(net.voxel_res, mesh)
+        _ORACLE_SETUP["v"] = (net, mesh, occ, ptr, idx) + tuple(S.init_params(net))
+    return _ORACLE_SETUP["v"]
+
+
 def oracle_train_sample(n_rays=384, seed=0):
     """One oracle training step on a bounded sample of the training workload.
 
     Returns (segments processed, seconds, threads)."""
     import oracle as O
     from paper_2604_24666_gb300 import synth as S
-    w = S.WORKLOADS[TRAIN_WORKLOAD]
-    net = w["net"]
-    mesh = S.make_mesh(w["shape"])
-    occ, ptr, idx = O.voxelize(net.voxel_res, mesh)
-    tables, ws, s = S.init_params(net)
+    net, mesh, occ, ptr, idx, tables, ws, s = _oracle_setup()
     pose = S.poses(1, seed=100 + seed)[0]
     rays = S.sphere_rays(n_rays, seed=200 + seed)
     t0 = time.perf_counter()
@@ -163,12 +175,15 @@ def run_reference(args):
         return 0
     import oracle as O
     O.build()
+    # each step a bounded sample: 384 rays (about 1 s of oracle work) for up
+    # to 25 steps, fewer rays per step beyond, so a run stays near half a minute
+    n_rays = 384 if args.steps <= 25 else max(48, 384 * 25 // args.steps)
     for i in range(args.warmup):
-        oracle_train_sample(seed=i)
+        oracle_train_sample(n_rays=n_rays, seed=i)
     segs, secs = 0, 0.0
     thr = 1
     for i in range(args.steps):
-        n, t, thr = oracle_train_sample(seed=1000 + i)
+        n, t, thr = oracle_train_sample(n_rays=n_rays, seed=1000 + i)
         segs += n
         secs += t
     v = segs / secs
@@ -176,9 +191,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": TRAIN_WORKLOAD, "note": "FP64 oracle on the host cores; each step a bounded "
-                       "sample of 384 rays of the workload (one pose)"},
+                       f"sample of {n_rays} rays of the workload (one pose)"},
             "cpu_baseline": {"value": v, "unit": "segments/s", "cores": thr, "kind": "oracle",
-                             "sample": f"{args.steps} steps x 384 rays (~{segs // max(args.steps, 1)} segments/step)"},
+                             "sample": f"{args.steps} steps x {n_rays} rays (~{segs // max(args.steps, 1)} segments/step)"},
             "e2e": {"value": v, "unit": "segments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -710,7 +725,7 @@ def run_precision(args, nif, S, dev):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")

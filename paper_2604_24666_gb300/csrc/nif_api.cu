@@ -1432,8 +1432,8 @@ static nif_status train_pipeline(nif_handle* h, int n_steps, const int& n_rays, 
     // persistent split-TF32 forward GEMMs lose SMs to it; beside the
     // encoding backward 3.27 ms, where it competes with the backward and the
     // weight gradients, both on whole SMs); the mixed path's forward shares
-    // the GPU well and its next batch starts with the step (2.79 ms vs
-    // 2.91 ms beside the encoding backward).
+    // the GPU well and its next batch starts with the step (2.48 ms; 2.55 ms
+    // after the encoding forward, 2.91 ms beside the encoding backward).
     const bool early = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
     auto next_batch = [&](int i) -> nif_status {
         swap_batch(h);
