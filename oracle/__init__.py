@@ -76,7 +76,9 @@ def lib():
                                       ctypes.c_void_p, ctypes.c_long]
             L.or_voxelize.restype = ctypes.c_long
             L.or_segments.argtypes = [ctypes.c_int, u8, dp, fp, ctypes.c_long, ctypes.c_int, ip, ip,
-                                      dp, dp, dp]
+                                      dp, dp, dp, ctypes.c_int]
+            L.or_bilinear_hits.argtypes = [dp, dp, dp, dp, dp, dp, dp, dp, dp]
+            L.or_bilinear_hits.restype = ctypes.c_int
             L.or_segments.restype = ctypes.c_long
             L.or_labels.argtypes = [lp, ip, fp, ip, fp, u8, ctypes.c_long, ip, dp, dp, u8, dp, dp, dp,
                                     u8, dp]
@@ -159,7 +161,23 @@ class Segments:
         return int(self.off[-1])
 
 
-def segments(N: int, occ, pose, rays, max_per_ray: int = 512) -> Segments:
+def bilinear_hits(o, d, P00, P10, P01, P11):
+    """Hits of the line o + t d with the bilinear patch of the four corners
+    (u along P00 -> P10, v along P00 -> P01): list of (t, u, v), and the
+    distance between the two hit points when there are two (else inf)."""
+    f = lambda a: np.ascontiguousarray(a, np.float64).reshape(3)
+    t = np.zeros(2)
+    uv = np.zeros(4)
+    sep = np.zeros(1)
+    n = lib().or_bilinear_hits(f(o), f(d), f(P00), f(P10), f(P01), f(P11), t, uv, sep)
+    return [(t[i], uv[2 * i], uv[2 * i + 1]) for i in range(n)], (sep[0] if n == 2 else np.inf)
+
+
+def segments(N: int, occ, pose, rays, max_per_ray: int = 512, faces: str = "triangles") -> Segments:
+    """Ray / deformed voxel segments (Sec. 2.1, 2.2). faces: "triangles" (each
+    face split along the diagonal from its lowest lattice corner) or
+    "bilinear" (each face the bilinear patch of its four corners)."""
+    assert faces in ("triangles", "bilinear")
     rays = np.ascontiguousarray(rays, np.float32)
     n = len(rays)
     cnt = np.zeros(n, np.int32)
@@ -168,7 +186,7 @@ def segments(N: int, occ, pose, rays, max_per_ray: int = 512) -> Segments:
     t1 = np.zeros(n * max_per_ray)
     mar = np.zeros(n)
     ov = lib().or_segments(N, np.ascontiguousarray(occ, np.uint8), _pose(pose), rays, n,
-                           max_per_ray, cnt, vox, t0, t1, mar)
+                           max_per_ray, cnt, vox, t0, t1, mar, int(faces == "bilinear"))
     if ov:
         raise RuntimeError(f"{ov} rays exceed {max_per_ray} segments")
     sel = (np.arange(max_per_ray)[None, :] < cnt[:, None]).reshape(-1)

@@ -17,7 +17,8 @@
  *     paper names none),
  *   - rest-space voxelization of the mesh (Sec. 2),
  *   - ray / deformed-voxel segment lists (Sec. 2.1 and Sec. 2.2), defined as
- *     the hits of each occupied voxel's triangulated deformed hull,
+ *     the hits of each occupied voxel's triangulated deformed hull, or of its
+ *     six faces taken as bilinear patches (the paper fixes neither),
  *   - ground-truth labels of the locally linearized rest-space segment
  *     (Sec. 2: "intersect the locally linearized rays with the rest-space
  *     geometry"),
@@ -353,6 +354,86 @@ static void hull_corners(int N, int i, int j, int k, const double* pose, double 
     or_deform(pose, P, &X[0][0], 8);
 }
 
+/*
+ * Line / bilinear patch (the curved-face reading of a deformed voxel): the
+ * face with corners P00, P10, P01, P11 is the surface
+ *   S(u,v) = P00 + u (P10 - P00) + v (P01 - P00) + u v (P11 - P10 - P01 + P00),
+ * u, v in [0,1]. Points of the line o + t d are exactly those whose
+ * components along two vectors n1, n2 orthogonal to d (and to each other)
+ * vanish after subtracting o, so a hit solves the pair of scalar bilinear
+ * equations x(u,v) = y(u,v) = 0 of the projected corners. Eliminating v
+ * gives a quadratic in u: with h, e, f, g the projected P00 - o, P10 - P00,
+ * P01 - P00 and P11 - P10 - P01 + P00 and k(a,b) = a_x b_y - a_y b_x,
+ *   k(e,g) u^2 + (k(h,g) + k(e,f)) u + k(h,f) = 0,
+ * and v follows from h + u e + v (f + u g) = 0. Returns the hits (0..2) with
+ * u, v in [0,1]; t[i] along d (d of any length), sep = the distance between
+ * the two roots' points when both are hits, else 1e300.
+ */
+int or_bilinear_hits(const double o[3], const double d[3], const double* P00, const double* P10,
+                     const double* P01, const double* P11, double t[2], double uv[4], double* sep) {
+    *sep = 1e300;
+    /* n1 = d x (axis of the smallest |d| component), n2 = d x n1 */
+    int ax = fabs(d[0]) <= fabs(d[1]) ? (fabs(d[0]) <= fabs(d[2]) ? 0 : 2) : (fabs(d[1]) <= fabs(d[2]) ? 1 : 2);
+    double a[3] = {0.0, 0.0, 0.0};
+    a[ax] = 1.0;
+    double n1[3] = {d[1] * a[2] - d[2] * a[1], d[2] * a[0] - d[0] * a[2], d[0] * a[1] - d[1] * a[0]};
+    double n2[3] = {d[1] * n1[2] - d[2] * n1[1], d[2] * n1[0] - d[0] * n1[2], d[0] * n1[1] - d[1] * n1[0]};
+    const double* P[4] = {P00, P10, P01, P11};
+    double X[4], Y[4];
+    for (int c = 0; c < 4; c++) {
+        double w[3] = {P[c][0] - o[0], P[c][1] - o[1], P[c][2] - o[2]};
+        X[c] = n1[0] * w[0] + n1[1] * w[1] + n1[2] * w[2];
+        Y[c] = n2[0] * w[0] + n2[1] * w[1] + n2[2] * w[2];
+    }
+    double h[2] = {X[0], Y[0]};
+    double e[2] = {X[1] - X[0], Y[1] - Y[0]};
+    double f[2] = {X[2] - X[0], Y[2] - Y[0]};
+    double g[2] = {X[3] - X[2] - X[1] + X[0], Y[3] - Y[2] - Y[1] + Y[0]};
+#define OR_K(p, q) ((p)[0] * (q)[1] - (p)[1] * (q)[0])
+    double k2 = OR_K(e, g), k1 = OR_K(h, g) + OR_K(e, f), k0 = OR_K(h, f);
+#undef OR_K
+    double us[2];
+    int nu = 0;
+    double scale = fabs(k2) + fabs(k1) + fabs(k0);
+    if (scale == 0.0) return 0;
+    if (fabs(k2) <= 1e-14 * scale) {
+        if (k1 != 0.0) us[nu++] = -k0 / k1;
+    } else {
+        double disc = k1 * k1 - 4.0 * k2 * k0;
+        if (disc < 0.0) return 0;
+        double sq = sqrt(disc);
+        double q = -0.5 * (k1 + (k1 >= 0.0 ? sq : -sq));
+        us[nu++] = q / k2;
+        if (disc > 0.0 && q != 0.0) us[nu++] = k0 / q;
+    }
+    int n = 0;
+    double pts[2][3];
+    for (int i = 0; i < nu; i++) {
+        double u = us[i];
+        if (!(u >= 0.0 && u <= 1.0)) continue;
+        double w[2] = {f[0] + u * g[0], f[1] + u * g[1]};
+        double r[2] = {h[0] + u * e[0], h[1] + u * e[1]};
+        double ww = w[0] * w[0] + w[1] * w[1];
+        if (ww == 0.0) continue;
+        double v = -(r[0] * w[0] + r[1] * w[1]) / ww;
+        if (!(v >= 0.0 && v <= 1.0)) continue;
+        double S[3];
+        for (int k = 0; k < 3; k++)
+            S[k] = P00[k] + u * (P10[k] - P00[k]) + v * (P01[k] - P00[k]) + u * v * (P11[k] - P10[k] - P01[k] + P00[k]);
+        double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        t[n] = ((S[0] - o[0]) * d[0] + (S[1] - o[1]) * d[1] + (S[2] - o[2]) * d[2]) / dd;
+        uv[2 * n] = u;
+        uv[2 * n + 1] = v;
+        for (int k = 0; k < 3; k++) pts[n][k] = S[k];
+        n++;
+    }
+    if (n == 2) {
+        double q[3] = {pts[1][0] - pts[0][0], pts[1][1] - pts[0][1], pts[1][2] - pts[0][2]};
+        *sep = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    }
+    return n;
+}
+
 typedef struct { int v; double t0, t1; } or_seg;
 
 static int seg_cmp(const void* a, const void* b) {
@@ -365,8 +446,10 @@ static int seg_cmp(const void* a, const void* b) {
 
 /*
  * Segment list of every ray (Sec. 2.1, Sec. 2.2): for each occupied voxel v,
- * all hits of the ray line with the 12 hull triangles; with at least two
- * hits, t0 = max(min t, tmin), t1 = min(max t, tmax); a segment exists when
+ * all hits of the ray line with the 12 hull triangles (bilinear = 0) or with
+ * the 6 bilinear face patches (bilinear = 1, faces as corner quads
+ * (lo, s1, s2, hi) = (P00, P10, P01, P11)); with at least two hits,
+ * t0 = max(min t, tmin), t1 = min(max t, tmax); a segment exists when
  * t1 > t0. Segments are sorted by (t0, v).
  *
  * rays: float [n, 8] = o, d, tmin, tmax. Outputs per ray: count[r], and
@@ -376,7 +459,7 @@ static int seg_cmp(const void* a, const void* b) {
  * Returns the number of rays that overflowed max_per_ray.
  */
 long or_segments(int N, const uint8_t* occ, const double* pose, const float* rays, long n,
-                 int max_per_ray, int* count, int* vox, double* t0, double* t1, double* margin) {
+                 int max_per_ray, int* count, int* vox, double* t0, double* t1, double* margin, int bilinear) {
     long nvox = (long)N * N * N;
     long nocc = 0;
     for (long v = 0; v < nvox; v++) nocc += occ[v] != 0;
@@ -411,6 +494,17 @@ long or_segments(int N, const uint8_t* occ, const double* pose, const float* ray
             int hits = 0;
             for (int f = 0; f < 6; f++) {
                 const int* F = OR_FACES[f];
+                if (bilinear) {
+                    double tt[2], uv[4], sep;
+                    int k = or_bilinear_hits(o, d, X[q][F[0]], X[q][F[1]], X[q][F[2]], X[q][F[3]], tt, uv, &sep);
+                    for (int i = 0; i < k; i++) {
+                        hits++;
+                        if (tt[i] < tlo) tlo = tt[i];
+                        if (tt[i] > thi) thi = tt[i];
+                    }
+                    if (sep < mar) mar = sep;      /* a near-tangent pair of hits */
+                    continue;
+                }
                 for (int s = 1; s <= 2; s++) {
                     double t, u, w;
                     if (mt_hit(o, d, X[q][F[0]], X[q][F[s]], X[q][F[3]], &t, &u, &w)) {
@@ -430,8 +524,10 @@ long or_segments(int N, const uint8_t* occ, const double* pose, const float* ray
                     ns++;
                 }
             }
-            if (!made) {
-                /* near miss? distance to the hull's edges if the ray meets the slightly grown box */
+            if (!made || bilinear) {
+                /* near miss? distance to the hull's edges if the ray meets the slightly grown box
+                 * (curved faces: for hit hulls too, since a hit next to a face edge is not
+                 * decided identically from the two faces that share it in finite precision) */
                 double g = 1e-3, ta = -1e300, tb = 1e300;
                 for (int a = 0; a < 3; a++) {
                     double lo = bmin[q][a] - g, hi = bmax[q][a] + g;

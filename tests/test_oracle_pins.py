@@ -766,3 +766,73 @@ def test_rounded_mlp_rounds_where_it_stores():
     out, acts = O.mlp_forward_rounded([-ws[0], ws[1]], np.array([[1.0]]), _bf16)
     dws, dx = O.mlp_backward_rounded([-ws[0], ws[1]], acts, np.array([[1.0]]), 4.0, _bf16)
     assert out[0, 0] == 0.0 and dws[0][0, 0] == 0.0 and dx[0, 0] == 0.0 and dws[1][0, 0] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Curved-face reading of a deformed voxel: line / bilinear patch
+# ---------------------------------------------------------------------------
+
+def test_bilinear_patch_saddle_closed_form():
+    """The patch x = u, y = v, z = u v (corners (0,0,0), (1,0,0), (0,1,0),
+    (1,1,1)) meets the line x = s, y = 1 - s, z = c where s (1 - s) = c:
+    s = (1 +- sqrt(1 - 4c)) / 2, two hits for 0 < c < 1/4, at (u, v) = (s, 1 - s)."""
+    c = 0.16
+    o = np.array([0.0, 1.0, c])
+    d = np.array([1.0, -1.0, 0.0]) / math.sqrt(2.0)
+    hits, sep = O.bilinear_hits(o, d, [0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 1])
+    r = math.sqrt(1 - 4 * c)
+    want = sorted([(1 - r) / 2, (1 + r) / 2])
+    got = sorted(hits)
+    assert len(got) == 2
+    for (t, u, v), s in zip(got, want):
+        assert abs(t - s * math.sqrt(2.0)) < 1e-14 and abs(u - s) < 1e-14 and abs(v - (1 - s)) < 1e-14
+    assert abs(sep - r * math.sqrt(2.0)) < 1e-14
+    # c > 1/4: the line passes above the saddle; c < 0: below the patch's z range at those (x, y)
+    assert O.bilinear_hits(np.array([0.0, 1.0, 0.3]), d, [0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 1])[0] == []
+    assert O.bilinear_hits(np.array([0.0, 1.0, -0.1]), d, [0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 1])[0] == []
+
+
+def test_bilinear_patch_hits_constructed_points():
+    """Lines built through a known point S(u0, v0) of random twisted patches
+    must report that hit: t = t0, (u, v) = (u0, v0); swapping the u and v
+    corners swaps (u, v); reversing d negates t."""
+    rng = np.random.default_rng(61)
+    for _ in range(300):
+        P = rng.uniform(0, 1, (4, 3))
+        u0, v0 = rng.uniform(0.05, 0.95, 2)
+        S0 = P[0] + u0 * (P[1] - P[0]) + v0 * (P[2] - P[0]) + u0 * v0 * (P[3] - P[1] - P[2] + P[0])
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        t0 = rng.uniform(0.5, 2.0)
+        o = S0 - t0 * d
+        hits, _ = O.bilinear_hits(o, d, *P)
+        assert min(max(abs(t - t0), abs(u - u0), abs(v - v0)) for t, u, v in hits) < 1e-9
+        sw, _ = O.bilinear_hits(o, d, P[0], P[2], P[1], P[3])
+        assert min(max(abs(t - t0), abs(u - v0), abs(v - u0)) for t, u, v in sw) < 1e-9
+        rv, _ = O.bilinear_hits(o, -d, *P)
+        assert min(abs(t + t0) for t, _, _ in rv) < 1e-9
+
+
+def test_bilinear_faces_equal_triangles_when_faces_are_planar():
+    """At the identity pose every voxel hull is an axis-aligned cube whose
+    faces are planar squares: the bilinear patch of a face and its two
+    triangles are the same point set, so both readings give the same
+    segments (voxels, counts and distances)."""
+    N = 16
+    occ, _, _ = O.voxelize(N, S.torus_mesh())
+    rays = S.sphere_rays(2000, seed=62)
+    a = O.segments(N, occ, (0.0, 0.0, 0.0), rays)
+    b = O.segments(N, occ, (0.0, 0.0, 0.0), rays, faces="bilinear")
+    np.testing.assert_array_equal(a.count, b.count)
+    np.testing.assert_array_equal(a.vox, b.vox)
+    np.testing.assert_allclose(b.t0, a.t0, atol=1e-12)
+    np.testing.assert_allclose(b.t1, a.t1, atol=1e-12)
+    # deformed: the same voxels on rays decided with margin, distances within the faces' bulge
+    pose = (0.6, -0.8, 0.5)
+    a = O.segments(N, occ, pose, rays)
+    b = O.segments(N, occ, pose, rays, faces="bilinear")
+    keep = np.nonzero((a.margin > 1e-3) & (b.margin > 1e-3))[0]
+    assert len(keep) > 500
+    for r in keep:
+        np.testing.assert_array_equal(a.vox[a.off[r]:a.off[r + 1]], b.vox[b.off[r]:b.off[r + 1]])
+        np.testing.assert_allclose(a.t0[a.off[r]:a.off[r + 1]], b.t0[b.off[r]:b.off[r + 1]], atol=0.02)
