@@ -460,12 +460,27 @@ def run_traversal(args, nif, S, dev):
         prof = nif.nif_profile_read(h.h)
         nif.nif_profile(h.h, 0)
         h.close()
+        # the same enumeration with the faces read as bilinear patches
+        import dataclasses
+        hb = nif.Nif(dataclasses.replace(w["net"], faces="bilinear"), mesh, seed=31)
+        nif._check(hb.h, L.nif_segments(hb.h, p, n_inst, nif._ptr(rays), None, n, nif._ptr(offs), None, 0,
+                                        ctypes.byref(total), None))
+        n_seg_bil = total.value
+        nif.nif_profile(hb.h, 1)
+        for _ in range(reps):
+            nif._check(hb.h, L.nif_segments(hb.h, p, n_inst, nif._ptr(rays), None, n, nif._ptr(offs), None, 0,
+                                            ctypes.byref(total), None))
+        prof_b = nif.nif_profile_read(hb.h)
+        nif.nif_profile(hb.h, 0)
+        hb.close()
         ms = {k: v[0] / reps for k, v in prof.items()}
         e, wk, lt, f = ms.get("seg_count", 0.0), ms.get("walk_count", 0.0), ms.get("walk_lattice", 0.0), ms.get(
             "walk_first", 0.0)
+        eb = prof_b.get("seg_count", (0.0,))[0] / reps
         out[wname] = {"rays": n, "segments": n_seg, "segments_walk": n_seg_walk, "enumerate_ms": e, "walk_ms": wk, "walk_lattice_ms": lt,
                       "bvh_first_hit_ms": f, "walk_over_enumerate": (wk + lt) / e if e else None,
-                      "bvh_share_of_walk": f / (wk + lt) if wk else None}
+                      "bvh_share_of_walk": f / (wk + lt) if wk else None,
+                      "segments_bilinear_faces": n_seg_bil, "enumerate_bilinear_faces_ms": eb}
     return out
 
 

@@ -107,6 +107,16 @@ typedef struct {
  * multiple of 16. The point-encoding calls (nif_encode_points and its
  * backward) keep the composed layout and refuse such a handle. */
 #define NIF_FLAG_CONCAT_ENCODING 8u
+/* NIF_FLAG_BILINEAR_FACES: take each face of a deformed voxel (Sec. 2.1,
+ * Sec. 2.2) as the bilinear patch of its four deformed corners instead of
+ * the default two triangles split along the diagonal from the face's lowest
+ * lattice corner (the paper fixes neither). Segments are then [first, last]
+ * hit of the ray line with the six patches, by the same rule as for the
+ * triangulated hull. The hit test is not watertight: a ray passing within
+ * FP32 rounding of a face edge may miss both faces that share it. The
+ * exit-face walk (nif_segments_walk) is defined on the triangulated faces and
+ * refuses such a handle. */
+#define NIF_FLAG_BILINEAR_FACES 16u
 
 /* Rest-space triangle mesh inside [0,1]^3 (host memory, copied by nif_create). */
 typedef struct {

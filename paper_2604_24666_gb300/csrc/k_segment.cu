@@ -174,6 +174,101 @@ __device__ __forceinline__ bool hull_segment(const RayPre& r, const float* __res
     return t1 > t0;
 }
 
+// One face as the bilinear patch S(u,v) of its corners (lo, s1, s2, hi) =
+// (P00, P10, P01, P11) in the sheared ray frame, where the ray is the z axis
+// and Zs at a point of the ray is its t: a hit is a root of X(u,v) = Y(u,v) = 0
+// with u, v in [0,1]. With h, e, f, g the 2D terms of S (P00, P10 - P00,
+// P01 - P00, P11 - P10 - P01 + P00) and k(a,b) = a_x b_y - a_y b_x, u solves
+// k(e,g) u^2 + (k(h,g) + k(e,f)) u + k(h,f) = 0 and v follows from
+// h + u e + v (f + u g) = 0; t is the bilinear blend of the corners' Zs.
+__device__ __forceinline__ float cross2(float ax, float ay, float bx, float by) {
+    return fmaf(ax, by, -ay * bx);
+}
+
+__device__ __forceinline__ void patch_hit(const float* X, const float* Y, const float* Zs, int lo, int s1, int s2,
+                                          int hi, int& hits, float& tlo, float& thi) {
+    const float hx = X[lo], hy = Y[lo];
+    const float ex = X[s1] - hx, ey = Y[s1] - hy;
+    const float fx = X[s2] - hx, fy = Y[s2] - hy;
+    const float gx = (X[hi] - X[s1]) - (X[s2] - hx), gy = (Y[hi] - Y[s1]) - (Y[s2] - hy);
+    const float k2 = cross2(ex, ey, gx, gy);
+    const float k1 = cross2(hx, hy, gx, gy) + cross2(ex, ey, fx, fy);
+    const float k0 = cross2(hx, hy, fx, fy);
+    float us[2];
+    int nu = 0;
+    const float scale = fabsf(k2) + fabsf(k1) + fabsf(k0);
+    if (!(scale > 0.f)) return;
+    if (fabsf(k2) <= 1e-7f * scale) {
+        if (k1 != 0.f) us[nu++] = -k0 / k1;
+    } else {
+        const float disc = fmaf(k1, k1, -4.f * k2 * k0);
+        if (disc < 0.f) return;
+        const float sq = sqrtf(disc);
+        const float q = -0.5f * (k1 + copysignf(sq, k1));
+        us[nu++] = q / k2;
+        if (disc > 0.f && q != 0.f) us[nu++] = k0 / q;
+    }
+    const float zl = Zs[lo], ze = Zs[s1] - zl, zf = Zs[s2] - zl, zg = (Zs[hi] - Zs[s1]) - (Zs[s2] - zl);
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        if (i >= nu) break;
+        const float u = us[i];
+        if (!(u >= 0.f && u <= 1.f)) continue;
+        const float wx = fmaf(u, gx, fx), wy = fmaf(u, gy, fy);
+        const float rx = fmaf(u, ex, hx), ry = fmaf(u, ey, hy);
+        const float ww = fmaf(wx, wx, wy * wy);
+        if (!(ww > 0.f)) continue;
+        const float v = -fmaf(rx, wx, ry * wy) / ww;
+        if (!(v >= 0.f && v <= 1.f)) continue;
+        const float t = zl + u * ze + v * fmaf(u, zg, zf);
+        hits++;
+        tlo = fminf(tlo, t);
+        thi = fmaxf(thi, t);
+    }
+}
+
+// Hull of one voxel with bilinear faces (NIF_FLAG_BILINEAR_FACES): the same
+// segment rule as hull_segment, on the six patches.
+__device__ __forceinline__ bool hull_segment_bil(const RayPre& r, const float* __restrict__ C, float& t0,
+                                                 float& t1) {
+    float X[8], Y[8], Zs[8];
+    const float4* C4 = reinterpret_cast<const float4*>(C);
+    float c[24];
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        float4 v = __ldg(C4 + q);
+        c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+    }
+    float o[3] = {r.ox, r.oy, r.oz};
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        float A[3] = {c[3 * k] - o[0], c[3 * k + 1] - o[1], c[3 * k + 2] - o[2]};
+        float ax = r.kx == 0 ? A[0] : (r.kx == 1 ? A[1] : A[2]);
+        float ay = r.ky == 0 ? A[0] : (r.ky == 1 ? A[1] : A[2]);
+        float az = r.kz == 0 ? A[0] : (r.kz == 1 ? A[1] : A[2]);
+        X[k] = fmaf(-r.Sx, az, ax);
+        Y[k] = fmaf(-r.Sy, az, ay);
+        Zs[k] = r.Sz * az;
+    }
+    int hits = 0;
+    float tlo = 3.0e38f, thi = -3.0e38f;
+    patch_hit(X, Y, Zs, 0, 2, 4, 6, hits, tlo, thi);   // x = 0
+    patch_hit(X, Y, Zs, 1, 3, 5, 7, hits, tlo, thi);   // x = 1
+    patch_hit(X, Y, Zs, 0, 1, 4, 5, hits, tlo, thi);   // y = 0
+    patch_hit(X, Y, Zs, 2, 3, 6, 7, hits, tlo, thi);   // y = 1
+    patch_hit(X, Y, Zs, 0, 1, 2, 3, hits, tlo, thi);   // z = 0
+    patch_hit(X, Y, Zs, 4, 5, 6, 7, hits, tlo, thi);   // z = 1
+    if (hits < 2) return false;
+    t0 = fmaxf(tlo, r.tmin);
+    t1 = fminf(thi, r.tmax);
+    return t1 > t0;
+}
+
+template <bool BIL>
+__device__ __forceinline__ bool hull_test(const RayPre& r, const float* __restrict__ C, float& t0, float& t1) {
+    return BIL ? hull_segment_bil(r, C, t0, t1) : hull_segment(r, C, t0, t1);
+}
+
 __device__ __forceinline__ int find_inst(const int* inst_off, int n_inst, int r) {
     if (!inst_off || n_inst <= 1) return 0;
     int lo = 0, hi = n_inst - 1;     // largest i with inst_off[i] <= r
@@ -218,7 +313,7 @@ enum { kModeCount = 0, kModeEmit = 1, kModeTemp = 2 };
 //               of their ray, then each ray's list sorted by (t0, voxel);
 //   kModeTemp:  counts plus every segment appended to `temp` at a
 //               warp-reserved position (ray order is restored by a scatter).
-template <int MODE, int kTravWarps>
+template <int MODE, int kTravWarps, bool BIL = false>
 __global__ void __launch_bounds__(kTravWarps * 32, 32 / kTravWarps) k_seg_traverse(
     const nif_ray* __restrict__ rays, const int* __restrict__ inst_off, int n_inst, int n_rays,
     TreeView tree, const float* __restrict__ corners, const float4* __restrict__ aabb,
@@ -291,7 +386,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 32 / kTravWarps) k_seg_traver
             int leaf = (int)(c & 0x7FFFFFFu);
             float t0, t1;
             const float* C = corners + ((int64_t)s_inst[warp][L] * tree.n_leaves + leaf) * 24;
-            if (hull_segment(s_ray[warp][L], C, t0, t1)) {
+            if (hull_test<BIL>(s_ray[warp][L], C, t0, t1)) {
                 hit = true;
                 sg.ray = (uint32_t)(r_warp0 + L);
                 sg.voxel = __ldg(tree.leaf_vox + leaf);
@@ -599,7 +694,7 @@ __global__ void __launch_bounds__(128) k_seg_walk(const nif_ray* __restrict__ ra
 // one ray per thread). Queue entries name a lane, and a lane is refilled only
 // once its queued candidates are tested, so an entry always belongs to the
 // lane's current ray.
-template <int MODE, int kTravWarps>
+template <int MODE, int kTravWarps, bool BIL = false>
 __global__ void __launch_bounds__(kTravWarps * 32, 32 / kTravWarps) k_seg_traverse_p(
     const nif_ray* __restrict__ rays, const int* __restrict__ inst_off, int n_inst, int n_rays,
     TreeView tree, const float* __restrict__ corners, const float4* __restrict__ aabb,
@@ -690,7 +785,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 32 / kTravWarps) k_seg_traver
                 const int leaf = (int)(c & 0x7FFFFFFu);
                 float t0, t1;
                 const float* C = corners + ((int64_t)s_inst[warp][L] * tree.n_leaves + leaf) * 24;
-                if (hull_segment(s_ray[warp][L], C, t0, t1)) {
+                if (hull_test<BIL>(s_ray[warp][L], C, t0, t1)) {
                     hit = true;
                     sg.ray = (uint32_t)s_rid[warp][L];
                     sg.voxel = __ldg(tree.leaf_vox + leaf);
@@ -920,13 +1015,13 @@ static TreeView tree_view(nif_handle* h);
 
 // warps per traversal block: a tuning knob of the handle (2, 4 or 8); the
 // count and temp modes run the persistent kernel (grid: 32 warps per SM)
-template <int MODE, int W>
+template <int MODE, int W, bool BIL = false>
 static void launch_traverse_w(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
                               uint32_t* counts, const uint32_t* offsets, nif_segment* segs, int64_t cap,
                               uint32_t* cursor, cudaStream_t s, int64_t emit_skip_le) {
     const TreeView tv = tree_view(h);
     if (MODE == kModeEmit) {
-        k_seg_traverse<kModeEmit, W><<<nif_blocks(n_rays, 32 * W), 32 * W, 0, s>>>(
+        k_seg_traverse<kModeEmit, W, BIL><<<nif_blocks(n_rays, 32 * W), 32 * W, 0, s>>>(
             rays, inst_off, n_inst, n_rays, tv, h->d_corners, h->d_aabb, counts, offsets, segs, cap, cursor,
             emit_skip_le, h->d_status);
         return;
@@ -934,14 +1029,20 @@ static void launch_traverse_w(nif_handle* h, const nif_ray* rays, const int* ins
     cudaMemsetAsync(h->d_next, 0, sizeof(uint32_t), s);
     const unsigned grid = std::min<unsigned>(nif_blocks(n_rays, 32 * W), (unsigned)h->num_sms * (32 / W));
     constexpr int M = MODE == kModeTemp ? kModeTemp : kModeCount;
-    k_seg_traverse_p<M, W><<<grid, 32 * W, 0, s>>>(rays, inst_off, n_inst, n_rays, tv, h->d_corners, h->d_aabb,
-                                                   counts, segs, cap, cursor, h->d_next, h->d_status);
+    k_seg_traverse_p<M, W, BIL><<<grid, 32 * W, 0, s>>>(rays, inst_off, n_inst, n_rays, tv, h->d_corners,
+                                                        h->d_aabb, counts, segs, cap, cursor, h->d_next,
+                                                        h->d_status);
 }
 
 template <int MODE>
 static void launch_traverse(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
                             uint32_t* counts, const uint32_t* offsets, nif_segment* segs, int64_t cap,
                             uint32_t* cursor, cudaStream_t s, int64_t emit_skip_le = 0) {
+    if (h->cfg.flags & NIF_FLAG_BILINEAR_FACES) {   // one block size for the curved-face variant
+        launch_traverse_w<MODE, 4, true>(h, rays, inst_off, n_inst, n_rays, counts, offsets, segs, cap, cursor, s,
+                                         emit_skip_le);
+        return;
+    }
     switch (h->tune.trav_warps) {
         case 2:
             launch_traverse_w<MODE, 2>(h, rays, inst_off, n_inst, n_rays, counts, offsets, segs, cap, cursor, s,

@@ -290,7 +290,7 @@ static nif_status validate(const nif_config* c, const nif_mesh* m) {
     if (c->n_materials < 1 || c->n_materials > 8) return nif_fail(nullptr, NIF_ERR_ARG, "n_materials in [1, 8]");
     if (c->precision < NIF_FP32 || c->precision > NIF_FP16) return nif_fail(nullptr, NIF_ERR_ARG, "precision");
     if (c->flags & ~(NIF_FLAG_FIXED_TASK_WEIGHTS | NIF_FLAG_SIGMOID_DISTANCE | NIF_FLAG_MIXED_TRAINING |
-                     NIF_FLAG_CONCAT_ENCODING))
+                     NIF_FLAG_CONCAT_ENCODING | NIF_FLAG_BILINEAR_FACES))
         return nif_fail(nullptr, NIF_ERR_ARG, "unknown flags");
     if ((c->flags & NIF_FLAG_MIXED_TRAINING) && c->precision == NIF_FP32)
         return nif_fail(nullptr, NIF_ERR_ARG, "NIF_FLAG_MIXED_TRAINING needs precision NIF_BF16 or NIF_FP16");
@@ -829,6 +829,8 @@ extern "C" nif_status nif_segments_walk(nif_handle* h, const nif_pose* poses, in
     if (!ray_offsets || (n_rays > 0 && !rays)) return nif_fail(h, NIF_ERR_ARG, "buffers");
     if (flags & ~NIF_WALK_FIRST_HIT) return nif_fail(h, NIF_ERR_ARG, "unknown walk flags");
     if ((flags & NIF_WALK_FIRST_HIT) && segs) return nif_fail(h, NIF_ERR_ARG, "NIF_WALK_FIRST_HIT counts only: segs must be NULL");
+    if (h->cfg.flags & NIF_FLAG_BILINEAR_FACES)
+        return nif_fail(h, NIF_ERR_ARG, "the exit-face walk is defined on the triangulated faces");
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
     if ((st = nif_refit_run(h, n_inst, s)) != NIF_OK) return st;

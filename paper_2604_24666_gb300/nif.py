@@ -24,6 +24,7 @@ NIF_PARAM_TABLES, NIF_PARAM_LOGVAR, NIF_PARAM_LAYER0 = 0, 1, 16
 NIF_SHADOW_ONLY = 1
 NIF_FLAG_FIXED_TASK_WEIGHTS, NIF_FLAG_SIGMOID_DISTANCE, NIF_FLAG_MIXED_TRAINING = 1, 2, 4
 NIF_FLAG_CONCAT_ENCODING = 8
+NIF_FLAG_BILINEAR_FACES = 16
 
 _STATUS = {0: "NIF_OK", -1: "NIF_ERR_ARG", -2: "NIF_ERR_CUDA", -3: "NIF_ERR_OOM", -4: "NIF_ERR_CAPACITY",
            -5: "NIF_ERR_TIMEOUT", -6: "NIF_ERR_NAN", -7: "NIF_ERR_STATE"}
@@ -188,6 +189,8 @@ def _check(h, st):
 def make_config(net, precision=NIF_FP32, seed=0, flags=0) -> nif_config:
     if getattr(net, "encoding", "composed") == "concat":
         flags |= NIF_FLAG_CONCAT_ENCODING
+    if getattr(net, "faces", "triangles") == "bilinear":
+        flags |= NIF_FLAG_BILINEAR_FACES
     return nif_config(net.voxel_res, net.pe_bands, net.levels, net.feats, net.log2_table, net.base_res,
                       float(net.growth), net.mlp_depth, net.mlp_width, net.n_materials, int(precision), int(flags),
                       int(seed))

@@ -250,6 +250,7 @@ class NetConfig:
     mlp_width: int = 32        # W
     n_materials: int = 4       # M
     encoding: str = "composed"  # Eq. 1 read as psi = phi o gamma ("composed") or [gamma, phi] ("concat")
+    faces: str = "triangles"    # deformed voxel faces: two triangles each, or bilinear patches ("bilinear")
 
     @property
     def n_terms(self) -> int:            # P = 1 + 2F
