@@ -211,18 +211,42 @@ __global__ void k_loss_final(double* acc, const uint32_t* __restrict__ n_dev, in
 // ---------------------------------------------------------------------------
 // Adam over the whole parameter buffer; zeroes the gradient afterwards.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void adam_elem(float& p, float gi, float& m, float& v, float lr, float c1, float c2) {
+    const float b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
+    const float mi = b1 * m + (1.f - b1) * gi;
+    const float vi = b2 * v + (1.f - b2) * gi * gi;
+    m = mi;
+    v = vi;
+    p -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+// Four parameters a thread per iteration through 16-byte accesses (the four
+// buffers come from cudaMalloc, so element 4j starts a 16-byte boundary),
+// then the n % 4 tail one by one.
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
                                               float* __restrict__ v, size_t n, size_t mlp_begin, size_t mlp_end,
                                               float lr_grid, float lr_mlp, float c1, float c2) {
-    const float b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        float gi = g[i];
-        float mi = b1 * m[i] + (1.f - b1) * gi;
-        float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        float lr = (i >= mlp_begin && i < mlp_end) ? lr_mlp : lr_grid;
-        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n4 = n / 4;
+    for (size_t j = tid; j < n4; j += stride) {
+        const float4 g4 = reinterpret_cast<const float4*>(g)[j];
+        float4 p4 = reinterpret_cast<float4*>(p)[j];
+        float4 m4 = reinterpret_cast<float4*>(m)[j];
+        float4 v4 = reinterpret_cast<float4*>(v)[j];
+        const size_t i = 4 * j;
+        auto lr = [&](size_t k) { return (k >= mlp_begin && k < mlp_end) ? lr_mlp : lr_grid; };
+        adam_elem(p4.x, g4.x, m4.x, v4.x, lr(i), c1, c2);
+        adam_elem(p4.y, g4.y, m4.y, v4.y, lr(i + 1), c1, c2);
+        adam_elem(p4.z, g4.z, m4.z, v4.z, lr(i + 2), c1, c2);
+        adam_elem(p4.w, g4.w, m4.w, v4.w, lr(i + 3), c1, c2);
+        reinterpret_cast<float4*>(m)[j] = m4;
+        reinterpret_cast<float4*>(v)[j] = v4;
+        reinterpret_cast<float4*>(p)[j] = p4;
+        reinterpret_cast<float4*>(g)[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (size_t i = 4 * n4 + tid; i < n; i += stride) {
+        adam_elem(p[i], g[i], m[i], v[i], (i >= mlp_begin && i < mlp_end) ? lr_mlp : lr_grid, c1, c2);
         g[i] = 0.f;
     }
 }
@@ -257,7 +281,6 @@ __global__ void __launch_bounds__(256) k_adam_scaled(float* __restrict__ p, floa
                                                      float* __restrict__ v, size_t n, size_t mlp_begin, size_t mlp_end,
                                                      size_t unscale_end, float lr_grid, float lr_mlp,
                                                      const NifLossScale* __restrict__ ls) {
-    const float b1 = 0.9f, b2 = 0.99f, eps = 1e-15f;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     if (ls->overflow) {
         for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) g[i] = 0.f;
@@ -266,16 +289,29 @@ __global__ void __launch_bounds__(256) k_adam_scaled(float* __restrict__ p, floa
     const float c1 = ls->c1, c2 = ls->c2;
     const float inv = 1.0f / ls->scale;
     // loads first and the gradient cleared last, as in k_adam (clearing it
-    // right after its load serialises each iteration's memory accesses: 7x)
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        float gi = g[i];
-        if (i < unscale_end) gi *= inv;
-        float mi = b1 * m[i] + (1.f - b1) * gi;
-        float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        float lr = (i >= mlp_begin && i < mlp_end) ? lr_mlp : lr_grid;
-        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    // right after its load serialises each iteration's memory accesses: 7x);
+    // four parameters per iteration through 16-byte accesses, then the tail
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n4 = n / 4;
+    auto lr = [&](size_t k) { return (k >= mlp_begin && k < mlp_end) ? lr_mlp : lr_grid; };
+    auto unscaled = [&](float gi, size_t k) { return k < unscale_end ? gi * inv : gi; };
+    for (size_t j = tid; j < n4; j += stride) {
+        const float4 g4 = reinterpret_cast<const float4*>(g)[j];
+        float4 p4 = reinterpret_cast<float4*>(p)[j];
+        float4 m4 = reinterpret_cast<float4*>(m)[j];
+        float4 v4 = reinterpret_cast<float4*>(v)[j];
+        const size_t i = 4 * j;
+        adam_elem(p4.x, unscaled(g4.x, i), m4.x, v4.x, lr(i), c1, c2);
+        adam_elem(p4.y, unscaled(g4.y, i + 1), m4.y, v4.y, lr(i + 1), c1, c2);
+        adam_elem(p4.z, unscaled(g4.z, i + 2), m4.z, v4.z, lr(i + 2), c1, c2);
+        adam_elem(p4.w, unscaled(g4.w, i + 3), m4.w, v4.w, lr(i + 3), c1, c2);
+        reinterpret_cast<float4*>(m)[j] = m4;
+        reinterpret_cast<float4*>(v)[j] = v4;
+        reinterpret_cast<float4*>(p)[j] = p4;
+        reinterpret_cast<float4*>(g)[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (size_t i = 4 * n4 + tid; i < n; i += stride) {
+        adam_elem(p[i], unscaled(g[i], i), m[i], v[i], lr(i), c1, c2);
         g[i] = 0.f;
     }
 }
