@@ -80,6 +80,21 @@ def test_train_steps_rays_equal_single_steps(nif, torus, mixed):
     b.close()
 
 
+def test_train_steps_rays_pageable_host_memory(nif, torus):
+    """Rays in pageable host memory: the copies serialise with the host but
+    the steps compute the same losses as from pinned memory."""
+    net = S.NetConfig()
+    a = nif.Nif(net, torus, seed=13)
+    b = nif.Nif(net, torus, seed=13)
+    rays = np.stack([S.sphere_rays(4000, seed=900 + i) for i in range(3)])
+    poses = np.stack([S.poses(1, seed=910 + i) for i in range(3)]).astype(np.float32)
+    la = nif.nif_train_steps_rays(a.h, poses, torch.from_numpy(rays).pin_memory(), 1 << 13, lr_grid=0.0, lr_mlp=0.0)
+    lb = nif.nif_train_steps_rays(b.h, poses, torch.from_numpy(rays), 1 << 13, lr_grid=0.0, lr_mlp=0.0)
+    np.testing.assert_allclose(lb, la, rtol=1e-9, atol=1e-12)
+    a.close()
+    b.close()
+
+
 def test_train_steps_rays_rejects_bad_arguments(nif, torus):
     a = nif.Nif(S.NetConfig(), torus)
     rays_host = torch.from_numpy(np.stack([S.sphere_rays(100, seed=1)] * 2))
