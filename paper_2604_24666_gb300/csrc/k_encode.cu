@@ -797,9 +797,25 @@ nif_status spatial_order(nif_handle* h, const nif_linseg* lin, const uint32_t* p
     return NIF_OK;
 }
 
+// The distinct end points of lin's segments, in rest-space order when the
+// tables (of table_bytes per entry) exceed 4 MiB: tables of a few MB stay in
+// L1 and L2 in any order (measured: the sort costs the 1 MiB-table query 5 %);
+// larger ones gain from it (the 32 MiB tables of the 64-instance batch:
+// encoder 1.35x faster). Recorded in h->enc_points.
+static nif_status point_list(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
+                             size_t table_bytes, cudaStream_t s) {
+    const uint32_t *pts, *n_pts, *dupf;
+    nif_status st = distinct_points(h, lin, n_dev, n_max, &pts, &n_pts, &dupf, s);
+    if (st != NIF_OK) return st;
+    const bool sorted = (size_t)h->T * h->L * h->Fd * table_bytes > ((size_t)4 << 20);
+    if (sorted && (st = spatial_order(h, lin, pts, n_pts, n_max, &pts, s)) != NIF_OK) return st;
+    h->enc_points = nif_handle::PointList{lin, n_dev, n_max, pts, n_pts, dupf, sorted};
+    return NIF_OK;
+}
+
 template <typename TT, typename OT>
 nif_status launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
-                           void* feats, cudaStream_t s) {
+                           void* feats, cudaStream_t s, bool reuse_points) {
     // block size and resident blocks per SM are tuning knobs of the handle
     int thr = h->tune.enc_threads;
     unsigned g = nif_blocks(n_max * 2 * h->P, thr);
@@ -807,15 +823,14 @@ nif_status launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, 
     if (g > cap) g = cap;
     if (h->L <= 16) {
         // distinct end points only (device-side list, see k_dup_flags)
-        const uint32_t *pts, *n_pts, *dupf;
-        nif_status st = distinct_points(h, lin, n_dev, n_max, &pts, &n_pts, &dupf, s);
-        if (st != NIF_OK) return st;
-        // tables of a few MB stay in L1 and L2 in any order (measured: the sort
-        // costs the 1 MiB-table query 5 %); larger ones gain from it (the
-        // 32 MiB tables of the 64-instance batch: encoder 1.35x faster)
+        const nif_handle::PointList& pl = h->enc_points;
         const bool sorted = (size_t)h->T * h->L * h->Fd * sizeof(TT) > ((size_t)4 << 20);
-        if (sorted && (st = spatial_order(h, lin, pts, n_pts, n_max, &pts, s)) != NIF_OK) return st;
-        h->enc_points = nif_handle::PointList{lin, n_dev, n_max, pts, n_pts, dupf, sorted};
+        if (!(reuse_points && pl.pts && pl.lin == lin && pl.n_dev == n_dev && pl.n_max == n_max &&
+              pl.sorted == sorted)) {
+            nif_status st = point_list(h, lin, n_dev, n_max, sizeof(TT), s);
+            if (st != NIF_OK) return st;
+        }
+        const uint32_t *pts = pl.pts, *n_pts = pl.n_pts, *dupf = pl.dupf;
         if (h->L <= 8)
             k_encode_segments_v<TT, OT, 8><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats, pts,
                                                             n_pts, dupf);
@@ -990,6 +1005,13 @@ __global__ void __launch_bounds__(256) k_encode_cat_dp(GridInfo g, const float* 
 
 }  // namespace
 
+nif_status nif_encode_points_prepare(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
+                                     int table_dtype, cudaStream_t s) {
+    if (n_max <= 0 || h->concat || h->L > 16) return NIF_OK;
+    return point_list(h, lin, n_dev, n_max, table_dtype == NIF_FP16 ? 2 : 4, s);
+}
+
+
 nif_status nif_encode_points_run(nif_handle* h, const float* pts, int64_t n, void* feats, int out_dtype,
                                  int32_t* rows, cudaStream_t s) {
     NifProf prof_(h, "encode_points", s);
@@ -1028,7 +1050,7 @@ static nif_status launch_cat(nif_handle* h, const nif_linseg* lin, const uint32_
 }
 
 nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
-                                   void* feats, int out_dtype, int table_dtype, cudaStream_t s) {
+                                   void* feats, int out_dtype, int table_dtype, cudaStream_t s, bool reuse_points) {
     NifProf prof_(h, "encode_fwd", s);
     if (n_max <= 0) return NIF_OK;
     nif_status st = NIF_OK;
@@ -1037,15 +1059,15 @@ nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const u
         st = nif_refresh_lowp(h, s);
         if (st != NIF_OK) return st;
         const __half* tab = h->d_tables_h;
-        if (out_dtype == NIF_FP32) st = launch_segments<__half, float>(h, tab, lin, n_dev, n_max, feats, s);
-        else if (out_dtype == NIF_BF16) st = launch_segments<__half, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s);
-        else if (out_dtype == NIF_FP16) st = launch_segments<__half, __half>(h, tab, lin, n_dev, n_max, feats, s);
+        if (out_dtype == NIF_FP32) st = launch_segments<__half, float>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
+        else if (out_dtype == NIF_BF16) st = launch_segments<__half, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
+        else if (out_dtype == NIF_FP16) st = launch_segments<__half, __half>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
         else return nif_fail(h, NIF_ERR_ARG, "out_dtype");
     } else if (table_dtype == NIF_FP32) {
         const float* tab = h->d_params + h->off_tables;
-        if (out_dtype == NIF_FP32) st = launch_segments<float, float>(h, tab, lin, n_dev, n_max, feats, s);
-        else if (out_dtype == NIF_BF16) st = launch_segments<float, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s);
-        else if (out_dtype == NIF_FP16) st = launch_segments<float, __half>(h, tab, lin, n_dev, n_max, feats, s);
+        if (out_dtype == NIF_FP32) st = launch_segments<float, float>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
+        else if (out_dtype == NIF_BF16) st = launch_segments<float, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
+        else if (out_dtype == NIF_FP16) st = launch_segments<float, __half>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
         else return nif_fail(h, NIF_ERR_ARG, "out_dtype");
     } else {
         return nif_fail(h, NIF_ERR_ARG, "table_dtype");

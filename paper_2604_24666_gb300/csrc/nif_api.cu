@@ -526,7 +526,8 @@ extern "C" void nif_destroy(nif_handle* h) {
                                &h->b_acts, &h->b_dout, &h->b_dx, &h->b_labels, &h->b_scan, &h->b_rays,
                                &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys, &h->b_dup, &h->b_pts,
                                &h->b_lattice, &h->b_sort, &h->alt_counts, &h->alt_offsets, &h->alt_temp, &h->alt_segs,
-                               &h->alt_scan, &h->alt_rays, &h->alt_inst, &h->alt_lin, &h->alt_labels};
+                               &h->alt_scan, &h->alt_rays, &h->alt_inst, &h->alt_lin, &h->alt_labels,
+                               &h->alt_dup, &h->alt_pts, &h->alt_sort};
     for (auto* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -1173,6 +1174,8 @@ static nif_status latched_status(nif_handle* h) {
 static nif_status train_batch(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
                               const int* inst_off, int n_rays, int64_t n_segments, int* n_hit, cudaStream_t s) {
     nif_status st;
+    // the point list of the set's previous batch names the same buffers: drop it
+    h->enc_points = nif_handle::PointList{};
     if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, n_segments, false, nullptr, s)) != NIF_OK)
         return st;
     uint32_t* offs = (uint32_t*)h->b_offsets.p;
@@ -1183,7 +1186,14 @@ static nif_status train_batch(nif_handle* h, const nif_pose* poses, int n_inst, 
     nif_segment* segs = (nif_segment*)h->b_segs.p;
     nif_linseg* lin = (nif_linseg*)h->b_lin.p;
     if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, n, lin, s)) != NIF_OK) return st;
-    return nif_labels_run(h, segs, lin, n_dev, n, (nif_label*)h->b_labels.p, s, n_hit);
+    if ((st = nif_labels_run(h, segs, lin, n_dev, n, (nif_label*)h->b_labels.p, s, n_hit)) != NIF_OK) return st;
+    // FP32 path: the distinct end points that the step's encodings (forward
+    // and backward) walk are listed with the batch, off the step's stream
+    // when the batch is built beside the previous step (step 3.08 -> 3.06 ms).
+    // The mixed path lists them in its forward: its batch runs beside the
+    // step's forward, and the longer batch cost more there (2.40 vs 2.47 ms).
+    if (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) return NIF_OK;
+    return nif_encode_points_prepare(h, lin, n_dev, n, NIF_FP32, s);
 }
 
 // Forward, losses, backward and optimizer step on the batch in the handle's
@@ -1223,7 +1233,7 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         const int prec = h->cfg.precision;
         uint16_t* acts16 = (uint16_t*)h->b_acts.p;
         uint16_t* dys = (uint16_t*)h->b_dys.p;
-        if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, prec, NIF_FP16, s)) != NIF_OK) return st;
+        if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, prec, NIF_FP16, s, true)) != NIF_OK) return st;
         if ((st = nif_mlp_fwd_tc_acts_run(h, feat, prec, n_dev, n, out, acts16, np, kLd, s)) != NIF_OK) return st;
         if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, true, n_hit)) != NIF_OK) return st;
         if ((st = nif_mlp_bwd_tc_run(h, dout, acts16, n_dev, n, np, kLd, dys, dx, s)) != NIF_OK) return st;
@@ -1238,7 +1248,7 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         if ((st = nif_grad_check_run(h, s)) != NIF_OK) return st;
         if ((st = nif_adam_scaled_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
     } else {
-        if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s)) != NIF_OK) return st;
+        if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s, true)) != NIF_OK) return st;
         if (ev_next) NIF_CK(h, cudaEventRecord(ev_next, s));
         if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
         if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, true, n_hit)) != NIF_OK) return st;
@@ -1414,6 +1424,10 @@ static void swap_batch(nif_handle* h) {
     std::swap(h->b_inst, h->alt_inst);
     std::swap(h->b_lin, h->alt_lin);
     std::swap(h->b_labels, h->alt_labels);
+    std::swap(h->b_dup, h->alt_dup);
+    std::swap(h->b_pts, h->alt_pts);
+    std::swap(h->b_sort, h->alt_sort);
+    std::swap(h->enc_points, h->alt_enc_points);
 }
 
 // The pipeline of nif_train_steps and nif_train_steps_rays: batch i is built

@@ -145,7 +145,9 @@ struct nif_handle {
     int* d_vox_leaf = nullptr;          // [N^3] octree leaf of each voxel, -1 when empty (exit-face walk)
     // the second set of training-batch buffers of nif_train_steps (the next
     // step's batch is built into it while the current step trains)
-    Buf alt_counts, alt_offsets, alt_temp, alt_segs, alt_scan, alt_rays, alt_inst, alt_lin, alt_labels;
+    Buf alt_counts, alt_offsets, alt_temp, alt_segs, alt_scan, alt_rays, alt_inst, alt_lin, alt_labels, alt_dup,
+        alt_pts, alt_sort;
+    PointList alt_enc_points;
     double query_seg_per_ray = 0.0;     // segments per ray of the last query (temp capacity hint)
 
     // launch knobs chosen by the autotuner (nif_query_plan_create)
@@ -246,9 +248,16 @@ nif_status nif_linearize_run(nif_handle* h, const nif_ray* rays, const int* inst
                              nif_linseg* lin, cudaStream_t s);
 nif_status nif_encode_points_run(nif_handle* h, const float* pts, int64_t n, void* feats,
                                  int out_dtype, int32_t* rows, cudaStream_t s);
+// reuse_points: the list of distinct end points that nif_encode_points_prepare
+// (or an earlier encoding) made for the same lin / n_dev / n_max, on this
+// stream, is taken as it is
 nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev,
                                    int64_t n_max, void* feats, int out_dtype, int table_dtype,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool reuse_points = false);
+// the distinct end points of a training batch, built with the batch (on its
+// stream) for the forward and backward encodings of the step that trains on it
+nif_status nif_encode_points_prepare(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev,
+                                     int64_t n_max, int table_dtype, cudaStream_t s);
 nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n, const float* dfeats,
                                      float* dtables, float* dpts, cudaStream_t s);
 // reuse_points: the segment encoding just before, on the same stream, read the
