@@ -37,3 +37,28 @@ def test_create_without_device_fails_cleanly():
     with pytest.raises(nif.NifError) as e:
         nif.nif_create(bad, S.torus_mesh())
     assert e.value.status == nif.NIF_ERR_ARG
+
+
+def test_binding_constants_match_the_header():
+    """Every NIF_* integer constant the binding defines has the header's value."""
+    from paper_2604_24666_gb300 import nif
+    src = open(os.path.join(ROOT, "include", "nif.h")).read()
+    vals = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(NIF_[A-Z0-9_]+)\s+(\d+)u?\b", src)}
+    for m in re.finditer(r"\b(NIF_[A-Z0-9_]+)\s*=\s*(-?\d+)", src):
+        vals.setdefault(m.group(1), int(m.group(2)))
+    checked = 0
+    for name, v in vals.items():
+        if hasattr(nif, name) and isinstance(getattr(nif, name), int):
+            assert getattr(nif, name) == v, name
+            checked += 1
+    assert checked >= 10
+    assert nif.NIF_FLAG_BILINEAR_FACES == 16 and nif.NIF_FLAG_CONCAT_ENCODING == 8
+
+
+def test_unknown_flag_fails_validation_without_device():
+    """A config with a flag bit the library does not define fails in argument
+    validation, before any device call."""
+    from paper_2604_24666_gb300 import nif, synth as S
+    with pytest.raises(nif.NifError) as e:
+        nif.nif_create(S.NetConfig(), S.torus_mesh(), flags=1 << 20)
+    assert e.value.status == nif.NIF_ERR_ARG and "flag" in str(e.value)
