@@ -62,3 +62,19 @@ def test_unknown_flag_fails_validation_without_device():
     with pytest.raises(nif.NifError) as e:
         nif.nif_create(S.NetConfig(), S.torus_mesh(), flags=1 << 20)
     assert e.value.status == nif.NIF_ERR_ARG and "flag" in str(e.value)
+
+
+def test_product_code_never_touches_the_oracle():
+    """The library and its binding neither import, load nor name a path of
+    the oracle package: it is test infrastructure only."""
+    pkg = os.path.join(ROOT, "paper_2604_24666_gb300")
+    offenders = []
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                src = open(os.path.join(dirpath, f), encoding="utf-8").read()
+                if re.search(r"^\s*(import|from)\s+oracle\b|nif_oracle|oracle/", src, flags=re.M):
+                    offenders.append(f)
+    assert not offenders, offenders
