@@ -175,9 +175,12 @@ def run_reference(args):
         return 0
     import oracle as O
     O.build()
-    # each step a bounded sample: 384 rays (about 1 s of oracle work) for up
-    # to 25 steps, fewer rays per step beyond, so a run stays near half a minute
-    n_rays = 384 if args.steps <= 25 else max(48, 384 * 25 // args.steps)
+    # each step a bounded sample: 384 rays (about 1 s of oracle work on 16
+    # Arm cores, the sample of the CPU-baseline leg) for up to 100 steps, fewer
+    # rays per step beyond, so a run stays within about two minutes (a step
+    # also pays a fixed cost for Adam over the whole tables, so fewer rays per
+    # step lower the segments/s)
+    n_rays = 384 if args.steps <= 100 else max(48, 384 * 100 // args.steps)
     for i in range(args.warmup):
         oracle_train_sample(n_rays=n_rays, seed=i)
     segs, secs = 0, 0.0
