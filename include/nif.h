@@ -509,6 +509,25 @@ void nif_query_plan_destroy(nif_query_plan* plan);
 /* Synchronises `stream` and returns (and clears) the device status word. */
 nif_status nif_sync_status(nif_handle* h, void* stream);
 
+/* Knobs of a handle, for failure testing and tuning (the paper has none).
+ * NIF_KNOB_WAIT_NS: the bound, in nanoseconds, of the waits in the work
+ *   loops of the tensor-core kernels (the MLP forward, backward and weight
+ *   gradients): a wait that takes longer makes the kernel latch
+ *   NIF_ERR_TIMEOUT in the status word, stop its work, wait (with the fixed
+ *   one-second bound) for its own copies and tensor-core operations in
+ *   flight, free its tensor memory and return; the outputs of that launch
+ *   are then undefined and the handle stays usable. 0 restores the default,
+ *   one second; the value must lie in [0, 6e10]. Synchronises the device.
+ * NIF_KNOB_SEG_SCRATCH: scale in (0, 1] of the scratch into which one
+ *   traversal writes the segments of a query or training batch before they
+ *   are put in ray order (default 1); below 1 the scratch overflows sooner
+ *   and the device-gated second traversal writes the rows instead. Results
+ *   do not depend on it.
+ * NIF_ERR_ARG for an unknown knob or a value out of range. */
+#define NIF_KNOB_WAIT_NS 1
+#define NIF_KNOB_SEG_SCRATCH 2
+nif_status nif_set_knob(nif_handle* h, int knob, double value);
+
 /* Allocation-free variant of nif_segments (the paper has no counterpart:
  * this is an integration aid). For callers that cannot call cudaMalloc -- a
  * host application that owns all device memory through its own fixed-budget
@@ -522,10 +541,11 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  * instances the handle already holds buffers for (1 after nif_create, more
  * after an allocating call with more instances); otherwise NIF_ERR_ARG.
  * The first call on a device looks the array's device address up (with that
- * device current); make that first call before any stream capture. Every
- * call shares the one array: calls that overlap on the GPU (other streams,
- * other handles, other threads) race and must be serialised by the caller.
- * Blocks the host like nif_segments. */
+ * device current). Every call shares the one array: calls that overlap on the
+ * GPU (other streams, other handles, other threads) race and must be
+ * serialised by the caller. Like nif_segments it blocks the host (it reads
+ * the total back), so it must not be called while `stream` is being captured
+ * into a CUDA graph. segs_dev == NULL only counts. */
 #define NIF_NOALLOC_MAX_RAYS (1 << 20)
 nif_status nif_segments_noalloc(nif_handle* h, const nif_pose* poses_host, int n_inst,
                                 const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,

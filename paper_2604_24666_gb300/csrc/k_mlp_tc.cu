@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t n = n_dev ? ((int64_t)*n_dev < n_max ? (int64_t)*n_dev : n_max) : n_max;
     constexpr uint32_t kAccCols = W < 32 ? 32 : W;     // TMEM columns of one accumulator stage
     extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint64_t wlim = wait_limit(status);   // bound of the work loop's waits
     // 1024-byte alignment of the dynamic buffer (swizzle atoms)
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int64_t j = 0; j < nt && ok; j++) {
                 int64_t t = blockIdx.x + j * gridDim.x;
                 for (int b = 0; b < lay.nb0; b++) {
-                    if (!mbar_wait(smem_u32(&bars[S + slot]), phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&bars[S + slot]), phase ^ 1u, abort_flag, status, wlim)) { ok = false; break; }
                     uint32_t fb = smem_u32(&bars[slot]);
                     mbar_expect_tx(fb, kStageBytes);
                     tma_load_2d(smem_u32(sm + lay.x_off + (uint32_t)slot * kStageBytes), &xmap, b * 64,
@@ -164,12 +165,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int q = 0; q < cnt && ok; q++) {
                     const uint32_t acc = tmem + (uint32_t)q * kAccCols;
                     if (j0 + q >= 2) {      // this stage's accumulator must have been read out
-                        if (!mbar_wait(smem_u32(&bars[B_ACT + q]), act_par[q], abort_flag, status)) { ok = false; break; }
+                        if (!mbar_wait(smem_u32(&bars[B_ACT + q]), act_par[q], abort_flag, status, wlim)) { ok = false; break; }
                         act_par[q] ^= 1u;
                         tc_fence_after();
                     }
                     for (int b = 0; b < lay.nb0; b++) {
-                        if (!mbar_wait(smem_u32(&bars[slot]), phase, abort_flag, status)) { ok = false; break; }
+                        if (!mbar_wait(smem_u32(&bars[slot]), phase, abort_flag, status, wlim)) { ok = false; break; }
                         tc_fence_after();
                         uint32_t base = smem_u32(sm + lay.x_off + (uint32_t)slot * kStageBytes);
                         uint32_t wbase = smem_u32(sm + lay.w0_off + (uint32_t)b * W * 128);
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int l = 1; l <= H && ok; l++) {
                     for (int q = 0; q < cnt && ok; q++) {
                         const uint32_t acc = tmem + (uint32_t)q * kAccCols;
-                        if (!mbar_wait(smem_u32(&bars[B_ACT + q]), act_par[q], abort_flag, status)) { ok = false; break; }
+                        if (!mbar_wait(smem_u32(&bars[B_ACT + q]), act_par[q], abort_flag, status, wlim)) { ok = false; break; }
                         act_par[q] ^= 1u;
                         tc_fence_after();
                         const bool last = l == H;
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int l = 0; l <= H && ok; l++) {
                 for (int q = 0; q < cnt; q++) {
                     int got = 0;
-                    if (lane == 0) got = mbar_wait(smem_u32(&bars[B_ACC + q]), acc_par[q], abort_flag, status) ? 1 : 0;
+                    if (lane == 0) got = mbar_wait(smem_u32(&bars[B_ACC + q]), acc_par[q], abort_flag, status, wlim) ? 1 : 0;
                     got = __shfl_sync(0xffffffffu, got, 0);
                     if (!got) { ok = false; break; }
                     acc_par[q] ^= 1u;
@@ -312,6 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  uint16_t* __restrict__ dys, float* __restrict__ dx, int* __restrict__ status) {
     constexpr uint32_t kCols = 256;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint64_t wlim = wait_limit(status);   // bound of the work loop's waits
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + lay.bar_off);   // 0 acc_full, 1 act_ready, 2 drain
@@ -354,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 // layers H .. 1: D = dY_l W_l  (B = W_l^T, K = out_l)
                 for (int l = H; l >= 1; l--) {
-                    if (!mbar_wait(smem_u32(&bars[1]), act_par, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&bars[1]), act_par, abort_flag, status, wlim)) { ok = false; break; }
                     act_par ^= 1u;
                     tc_fence_after();
                     const int ks_n = l == H ? 1 : lay.ksw;
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 // layer 0: dX_0 = dY_0 W_0 in column chunks (B = rows c0.. of W_0^T)
                 for (int c = 0; c < n_chunks && ok; c++) {
-                    if (!mbar_wait(smem_u32(&bars[1]), act_par, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&bars[1]), act_par, abort_flag, status, wlim)) { ok = false; break; }
                     act_par ^= 1u;
                     tc_fence_after();
                     const int c0 = c * (int)kCols;
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         auto wait_acc = [&]() -> bool {
             int got = 0;
-            if (lane == 0) got = mbar_wait(smem_u32(&bars[0]), acc_par, abort_flag, status) ? 1 : 0;
+            if (lane == 0) got = mbar_wait(smem_u32(&bars[0]), acc_par, abort_flag, status, wlim) ? 1 : 0;
             got = __shfl_sync(0xffffffffu, got, 0);
             acc_par ^= 1u;
             if (got) tc_fence_after();
@@ -555,6 +557,7 @@ __global__ void __launch_bounds__(kDwThreads, 1)
                 const __grid_constant__ CUtensorMap dmap, DwJobs jobs, int fmt, int64_t n_max, int64_t n_pad,
                 const uint32_t* __restrict__ n_dev, float* __restrict__ grad, int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint64_t wlim = wait_limit(status);   // bound of the work loop's waits
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kDwStages * kDwStage + kDwSlack);
@@ -599,7 +602,7 @@ __global__ void __launch_bounds__(kDwThreads, 1)
             const uint32_t bytes = (uint32_t)(nbox + 1) * kDwBox;
             for (int64_t j = 0; j < my; j++) {
                 const int64_t c = blockIdx.y + j * gridDim.y;
-                if (!mbar_wait(smem_u32(&bars[kDwStages + slot]), phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                if (!mbar_wait(smem_u32(&bars[kDwStages + slot]), phase ^ 1u, abort_flag, status, wlim)) { ok = false; break; }
                 const uint32_t fb = smem_u32(&bars[slot]);
                 const uint32_t st = smem_u32(sm + (uint32_t)slot * kDwStage);
                 mbar_expect_tx(fb, bytes);
@@ -623,7 +626,7 @@ __global__ void __launch_bounds__(kDwThreads, 1)
             int slot = 0;
             uint32_t phase = 0;
             for (int64_t j = 0; j < my; j++) {
-                if (!mbar_wait(smem_u32(&bars[slot]), phase, abort_flag, status)) { ok = false; break; }
+                if (!mbar_wait(smem_u32(&bars[slot]), phase, abort_flag, status, wlim)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t st = smem_u32(sm + (uint32_t)slot * kDwStage);
 #pragma unroll
@@ -642,7 +645,7 @@ __global__ void __launch_bounds__(kDwThreads, 1)
     // epilogue: lane i of the tile holds D[i][0..out_l) = dW_l[0..out_l)[i0 + i]
     if (my > 0) {
         int got = 0;
-        if (lane == 0) got = mbar_wait(smem_u32(&bars[2 * kDwStages]), 0, abort_flag, status) ? 1 : 0;
+        if (lane == 0) got = mbar_wait(smem_u32(&bars[2 * kDwStages]), 0, abort_flag, status, wlim) ? 1 : 0;
         got = __shfl_sync(0xffffffffu, got, 0);
         if (got && !*abort_flag) {
             tc_fence_after();

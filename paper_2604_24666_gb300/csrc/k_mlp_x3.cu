@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(kX3Threads, 1)
               const __grid_constant__ CUtensorMap mmap, X3Args a, const uint32_t* __restrict__ n_dev,
               int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint64_t wlim = wait_limit(status);   // bound of the work loop's waits
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = a.stages;
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(kX3Threads, 1)
                     // the job's mask tile, once the epilogue is done with the buffer's previous job
                     const int q = (int)(j & 1);
                     if (j >= 2) {
-                        if (!mbar_wait(smem_u32(&bars[B_ACCE + q]), me_par[q], abort_flag, status)) { ok = false; break; }
+                        if (!mbar_wait(smem_u32(&bars[B_ACCE + q]), me_par[q], abort_flag, status, wlim)) { ok = false; break; }
                         me_par[q] ^= 1u;
                     }
                     const uint32_t mb = smem_u32(&bars[B_MSK + q]);
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(kX3Threads, 1)
                     mf_par = (mf_par & ~(1u << q)) | ((uint32_t)((j >> 1) & 1) << q);
                 }
                 for (int kb = 0; kb < a.nkb; kb++) {
-                    if (!mbar_wait(smem_u32(&bars[B_EMPTY + slot]), phase ^ 1u, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&bars[B_EMPTY + slot]), phase ^ 1u, abort_flag, status, wlim)) { ok = false; break; }
                     const uint32_t fb = smem_u32(&bars[slot]);
                     const uint32_t st = smem_u32(sm + (uint32_t)slot * a.stage_bytes);
                     mbar_expect_tx(fb, kABox + 2u * a.b_bytes);
@@ -243,12 +244,12 @@ __global__ void __launch_bounds__(kX3Threads, 1)
                 const int q = (int)(j & 1);
                 const uint32_t acc = tmem + (uint32_t)q * a.acc_stride;
                 if (j >= 2) {   // the epilogue must have read this accumulator out
-                    if (!mbar_wait(smem_u32(&bars[B_ACCE + q]), ae_par[q], abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&bars[B_ACCE + q]), ae_par[q], abort_flag, status, wlim)) { ok = false; break; }
                     ae_par[q] ^= 1u;
                     tc_fence_after();
                 }
                 for (int kb = 0; kb < a.nkb; kb++) {
-                    if (!mbar_wait(smem_u32(&bars[B_CONV + slot]), phase, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&bars[B_CONV + slot]), phase, abort_flag, status, wlim)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t ah = smem_u32(sm + (uint32_t)slot * a.stage_bytes);
                     const uint32_t al = ah + kABox, bh = ah + 2u * kABox, bl = bh + a.b_bytes;
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(kX3Threads, 1)
         for (int64_t j = 0; j < my; j++) {
             bool ok = true;
             for (int kb = 0; kb < a.nkb; kb++) {
-                if (!mbar_wait(smem_u32(&bars[slot]), phase, abort_flag, status)) { ok = false; break; }
+                if (!mbar_wait(smem_u32(&bars[slot]), phase, abort_flag, status, wlim)) { ok = false; break; }
                 float4* A = reinterpret_cast<float4*>(sm + (uint32_t)slot * a.stage_bytes);
                 float4* Al = reinterpret_cast<float4*>(sm + (uint32_t)slot * a.stage_bytes + kABox);
 #pragma unroll
@@ -302,12 +303,12 @@ __global__ void __launch_bounds__(kX3Threads, 1)
             const int64_t tile = job / a.n_chunks;
             const int chunk = (int)(job % a.n_chunks);
             int got = 0;
-            if (lane == 0) got = mbar_wait(smem_u32(&bars[B_ACC + q]), af_par[q], abort_flag, status) ? 1 : 0;
+            if (lane == 0) got = mbar_wait(smem_u32(&bars[B_ACC + q]), af_par[q], abort_flag, status, wlim) ? 1 : 0;
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) break;
             af_par[q] ^= 1u;
             if (EPI == kX3Mask) {
-                if (!mbar_wait(smem_u32(&bars[B_MSK + q]), mk_par[q], abort_flag, status)) break;
+                if (!mbar_wait(smem_u32(&bars[B_MSK + q]), mk_par[q], abort_flag, status, wlim)) break;
                 mk_par[q] ^= 1u;
             }
             tc_fence_after();
@@ -418,6 +419,7 @@ __global__ void __launch_bounds__(kDwX3Threads, 1)
     k_dw_x3(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dmap, DwX3Args a,
             const uint32_t* __restrict__ n_dev, int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint64_t wlim = wait_limit(status);   // bound of the work loop's waits
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int RS = a.raw_stages, OS = a.op_stages;
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(kDwX3Threads, 1)
             uint32_t phase = 0, issued_mask = 0, issued_par = 0;
             for (int64_t j = 0; j < my; j++) {
                 const int64_t kb = blockIdx.y + j * gridDim.y;
-                if (!mbar_wait(smem_u32(&bars[B_RE + slot]), phase ^ 1u, abort_flag, status)) break;
+                if (!mbar_wait(smem_u32(&bars[B_RE + slot]), phase ^ 1u, abort_flag, status, wlim)) break;
                 const uint32_t fb = smem_u32(&bars[slot]);
                 const uint32_t st = smem_u32(sm + (uint32_t)slot * a.raw_bytes);
                 mbar_expect_tx(fb, a.raw_tx);
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(kDwX3Threads, 1)
             int slot = 0;
             uint32_t phase = 0;
             for (int64_t j = 0; j < my; j++) {
-                if (!mbar_wait(smem_u32(&bars[B_OF + slot]), phase, abort_flag, status)) break;
+                if (!mbar_wait(smem_u32(&bars[B_OF + slot]), phase, abort_flag, status, wlim)) break;
                 tc_fence_after();
                 const uint32_t ah = smem_u32(sm + a.op_off + (uint32_t)slot * a.op_bytes);
                 const uint32_t al = ah + kABox, bh = ah + 2u * kABox, bl = bh + (uint32_t)OUT * 128u;
@@ -514,8 +516,8 @@ __global__ void __launch_bounds__(kDwX3Threads, 1)
         uint32_t rph = 0, oph = 0;
         for (int64_t j = 0; j < my; j++) {
             const int64_t kb = blockIdx.y + j * gridDim.y;
-            if (!mbar_wait(smem_u32(&bars[rs]), rph, abort_flag, status)) break;
-            if (!mbar_wait(smem_u32(&bars[B_OE + os]), oph ^ 1u, abort_flag, status)) break;
+            if (!mbar_wait(smem_u32(&bars[rs]), rph, abort_flag, status, wlim)) break;
+            if (!mbar_wait(smem_u32(&bars[B_OE + os]), oph ^ 1u, abort_flag, status, wlim)) break;
             const float* xs = reinterpret_cast<const float*>(sm + (uint32_t)rs * a.raw_bytes);
             const float* ds = reinterpret_cast<const float*>(sm + (uint32_t)rs * a.raw_bytes + a.xs_bytes);
             uint8_t* ah = sm + a.op_off + (uint32_t)os * a.op_bytes;
@@ -532,7 +534,7 @@ __global__ void __launch_bounds__(kDwX3Threads, 1)
         // epilogue (warps 2..5): TMEM lane i holds D[i][0..OUT) = dW_l[0..OUT)[i0 + i]
         if (my > 0 && warp < 6) {
             int got = 0;
-            if (lane == 0) got = mbar_wait(smem_u32(&bars[B_ACC]), 0, abort_flag, status) ? 1 : 0;
+            if (lane == 0) got = mbar_wait(smem_u32(&bars[B_ACC]), 0, abort_flag, status, wlim) ? 1 : 0;
             got = __shfl_sync(0xffffffffu, got, 0);
             if (got && !*abort_flag) {
                 tc_fence_after();

@@ -7,7 +7,6 @@
 // scratch on demand; this variant keeps its scratch -- the per-ray counts and
 // the scan's block sums -- in one file-scope device array of fixed size that
 // every GPU loading the library holds until the process exits.
-#include <cmath>
 #include <mutex>
 
 #include "nif_internal.cuh"
@@ -15,7 +14,10 @@
 namespace {
 
 constexpr int kMaxRays = NIF_NOALLOC_MAX_RAYS;
-constexpr int kBlockSums = 2048;          // >= ceil(kMaxRays / 1024) + 1
+// the scan of kMaxRays counts needs one block sum per NIF_SCAN_BLOCK rays and the total
+constexpr int kBlockSums = 2048;
+static_assert(kBlockSums >= (kMaxRays + NIF_SCAN_BLOCK - 1) / NIF_SCAN_BLOCK + 1,
+              "block-sum part of the static scratch too small for NIF_NOALLOC_MAX_RAYS");
 
 // [0, kMaxRays): per-ray segment counts; [kMaxRays, +kBlockSums): scan block sums
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kMaxRays + kBlockSums];
@@ -49,48 +51,33 @@ extern "C" nif_status nif_segments_noalloc(nif_handle* h, const nif_pose* poses,
                                            nif_segment* segs, int64_t seg_cap, int64_t* n_segs_host,
                                            void* stream) {
     if (!h) return NIF_ERR_ARG;
-    if (!poses || n_inst < 1 || (n_inst > 1 && !inst_off)) return nif_fail(h, NIF_ERR_ARG, "poses / inst_offsets");
-    if (n_rays < 0 || n_rays > kMaxRays)
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    if (n_rays > kMaxRays)
         return nif_fail(h, NIF_ERR_ARG, "nif_segments_noalloc: n_rays must be in [0, NIF_NOALLOC_MAX_RAYS]");
+    // checked before nif_upload_poses, which would otherwise grow the
+    // per-instance buffers: within inst_cap it allocates nothing
     if (n_inst > h->inst_cap)
         return nif_fail(h, NIF_ERR_ARG,
                         "nif_segments_noalloc: more instances than the handle holds buffers for "
                         "(an earlier allocating call with that many instances provides them)");
     if (!ray_offsets || (n_rays > 0 && !rays)) return nif_fail(h, NIF_ERR_ARG, "buffers");
-    for (int i = 0; i < n_inst; i++)
-        if (!(std::fabs(poses[i].bend) <= 1.0f && std::fabs(poses[i].twist) <= 4.0f &&
-              std::fabs(poses[i].taper) <= 1.0f))
-            return nif_fail(h, NIF_ERR_ARG, "pose outside |bend| <= 1, |twist| <= 4, |taper| <= 1");
     cudaStream_t s = (cudaStream_t)stream;
     uint32_t* scratch = nullptr;
-    nif_status st = scratch_address(h, &scratch);
-    if (st != NIF_OK) return st;
-    // poses -> device, in small stack-staged batches
-    for (int i0 = 0; i0 < n_inst; i0 += 64) {
-        float4 p[64];
-        int m = n_inst - i0 < 64 ? n_inst - i0 : 64;
-        for (int i = 0; i < m; i++)
-            p[i] = make_float4(NIF_KBEND * poses[i0 + i].bend, poses[i0 + i].twist, poses[i0 + i].taper, 0.f);
-        NIF_CK(h, cudaMemcpyAsync(h->d_pose + i0, p, sizeof(float4) * m, cudaMemcpyHostToDevice, s));
-        NIF_CK(h, cudaStreamSynchronize(s));
-    }
+    if ((st = scratch_address(h, &scratch)) != NIF_OK) return st;
+    if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
     uint32_t* counts = scratch;
     uint32_t* bsum = scratch + kMaxRays;
     if ((st = nif_refit_run(h, n_inst, s)) != NIF_OK) return st;
     if ((st = nif_seg_count_run(h, rays, inst_off, n_inst, n_rays, counts, s)) != NIF_OK) return st;
     if ((st = nif_scan_run_with(h, counts, ray_offsets, n_rays, bsum, s)) != NIF_OK) return st;
-    if ((st = nif_seg_emit_run(h, rays, inst_off, n_inst, n_rays, ray_offsets, segs, segs ? seg_cap : 0, s)) != NIF_OK)
+    if (segs && (st = nif_seg_emit_run(h, rays, inst_off, n_inst, n_rays, ray_offsets, segs, seg_cap, s)) != NIF_OK)
         return st;
     NIF_CK(h, cudaStreamSynchronize(s));
     uint32_t tot = 0;
     NIF_CK(h, cudaMemcpy(&tot, ray_offsets + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     if (n_segs_host) *n_segs_host = tot;
-    int dst = 0;
-    NIF_CK(h, cudaMemcpy(&dst, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-    if (dst != 0) {
-        NIF_CK(h, cudaMemset(h->d_status, 0, sizeof(int)));
-        return nif_fail(h, (nif_status)dst, "device-side error latched by a kernel");
-    }
+    if ((st = nif_check_status(h, s)) != NIF_OK) return st;
     if (segs && (int64_t)tot > seg_cap) return nif_fail(h, NIF_ERR_CAPACITY, "segment capacity exceeded");
     return NIF_OK;
 }

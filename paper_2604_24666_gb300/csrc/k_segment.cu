@@ -872,6 +872,7 @@ __global__ void __launch_bounds__(256) k_seg_sort(const uint32_t* __restrict__ o
 // Exclusive scan of uint32 (three passes, 1024 elements per block)
 // ---------------------------------------------------------------------------
 constexpr int kScanT = 256, kScanE = 4, kScanB = kScanT * kScanE;
+static_assert(kScanB == NIF_SCAN_BLOCK, "block-sum sizes of the scan's callers use NIF_SCAN_BLOCK");
 
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sh, uint32_t& total) {
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

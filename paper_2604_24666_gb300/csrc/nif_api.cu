@@ -765,7 +765,7 @@ static nif_status seg_single_pass(nif_handle* h, const nif_ray* rays, const int*
                                   uint32_t* offs, nif_segment* segs, int64_t seg_cap, bool segs_grow,
                                   int64_t* total_out, cudaStream_t s);
 
-static nif_status check_status(nif_handle* h, cudaStream_t s) {
+nif_status nif_check_status(nif_handle* h, cudaStream_t s) {
     NIF_CK(h, cudaStreamSynchronize(s));
     int st = 0;
     NIF_CK(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -779,7 +779,7 @@ static nif_status check_status(nif_handle* h, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Stages
 // ---------------------------------------------------------------------------
-static nif_status check_inst(nif_handle* h, const nif_pose* poses, int n_inst, const int* inst_off, int n_rays) {
+nif_status nif_check_inst(nif_handle* h, const nif_pose* poses, int n_inst, const int* inst_off, int n_rays) {
     if (!poses || n_inst < 1) return nif_fail(h, NIF_ERR_ARG, "poses");
     if (n_inst > 1 && !inst_off) return nif_fail(h, NIF_ERR_ARG, "inst_offsets required for n_inst > 1");
     if (n_rays < 0) return nif_fail(h, NIF_ERR_ARG, "n_rays");
@@ -793,7 +793,7 @@ extern "C" nif_status nif_segments(nif_handle* h, const nif_pose* poses, int n_i
                                    const int* inst_off, int n_rays, uint32_t* ray_offsets, nif_segment* segs,
                                    int64_t seg_cap, int64_t* n_segs_host, void* stream) {
     if (!h) return NIF_ERR_ARG;
-    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
     if (st != NIF_OK) return st;
     if (!ray_offsets || (n_rays > 0 && !rays)) return nif_fail(h, NIF_ERR_ARG, "buffers");
     cudaStream_t s = (cudaStream_t)stream;
@@ -815,7 +815,7 @@ extern "C" nif_status nif_segments(nif_handle* h, const nif_pose* poses, int n_i
     uint32_t tot = 0;
     NIF_CK(h, cudaMemcpy(&tot, ray_offsets + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     if (n_segs_host) *n_segs_host = tot;
-    st = check_status(h, s);
+    st = nif_check_status(h, s);
     if (st != NIF_OK) return st;
     if (segs && (int64_t)tot > seg_cap) return nif_fail(h, NIF_ERR_CAPACITY, "segment capacity exceeded");
     return NIF_OK;
@@ -825,7 +825,7 @@ extern "C" nif_status nif_segments_walk(nif_handle* h, const nif_pose* poses, in
                                         const int* inst_off, int n_rays, uint32_t* ray_offsets, nif_segment* segs,
                                         int64_t seg_cap, int64_t* n_segs_host, unsigned flags, void* stream) {
     if (!h) return NIF_ERR_ARG;
-    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
     if (st != NIF_OK) return st;
     if (!ray_offsets || (n_rays > 0 && !rays)) return nif_fail(h, NIF_ERR_ARG, "buffers");
     if (flags & ~NIF_WALK_FIRST_HIT) return nif_fail(h, NIF_ERR_ARG, "unknown walk flags");
@@ -848,7 +848,7 @@ extern "C" nif_status nif_segments_walk(nif_handle* h, const nif_pose* poses, in
     uint32_t tot = 0;
     NIF_CK(h, cudaMemcpy(&tot, ray_offsets + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost));
     if (n_segs_host) *n_segs_host = tot;
-    st = check_status(h, s);
+    st = nif_check_status(h, s);
     if (st != NIF_OK) return st;
     if (segs && (int64_t)tot > seg_cap) return nif_fail(h, NIF_ERR_CAPACITY, "segment capacity exceeded");
     return NIF_OK;
@@ -858,7 +858,7 @@ extern "C" nif_status nif_linearize(nif_handle* h, const nif_pose* poses, int n_
                                     const int* inst_off, int n_rays, const nif_segment* segs, int64_t n_segs,
                                     nif_linseg* lin, void* stream) {
     if (!h) return NIF_ERR_ARG;
-    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
     if (st != NIF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
@@ -888,7 +888,7 @@ extern "C" nif_status nif_pose_gradient(nif_handle* h, const nif_pose* poses, in
                                         const nif_segment* segs, const nif_linseg* lin, int64_t n,
                                         const float* dfeats, float* dposes, float* dp_out, void* stream) {
     if (!h) return NIF_ERR_ARG;
-    nif_status st = check_inst(h, poses, n_inst, inst_off, 0);
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, 0);
     if (st != NIF_OK) return st;
     if (n < 0 || (n > 0 && (!segs || !lin || !dfeats || !dposes))) return nif_fail(h, NIF_ERR_ARG, "buffers");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1001,7 +1001,7 @@ extern "C" nif_status nif_reconstruct(nif_handle* h, const nif_pose* poses, int 
                                       const nif_segment* segs, const nif_linseg* lin, const float* out,
                                       nif_hit* hits, unsigned flags, void* stream) {
     if (!h) return NIF_ERR_ARG;
-    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
     if (st != NIF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
@@ -1030,9 +1030,10 @@ static nif_status seg_single_pass(nif_handle* h, const nif_ray* rays, const int*
     if ((st = nif_grow(h, h->b_counts, sizeof(uint32_t) * ((size_t)n_rays + 1))) != NIF_OK) return st;
     uint32_t* counts = (uint32_t*)h->b_counts.p;
     double hint = h->query_seg_per_ray > 0.0 ? h->query_seg_per_ray * 1.25 + 0.5 : 8.0;
-    int64_t tcap = std::max<int64_t>(4096, (int64_t)(hint * (double)n_rays));
+    int64_t tcap = std::max<int64_t>(4096, (int64_t)(hint * h->seg_scratch_scale * (double)n_rays));
     if ((st = nif_grow(h, h->b_temp, sizeof(nif_segment) * (size_t)tcap)) != NIF_OK) return st;
-    tcap = (int64_t)(h->b_temp.bytes / sizeof(nif_segment));
+    // the whole buffer, unless the scratch knob asks for less
+    if (h->seg_scratch_scale >= 1.0) tcap = (int64_t)(h->b_temp.bytes / sizeof(nif_segment));
     uint32_t* cursor = reinterpret_cast<uint32_t*>(h->d_count + 1);
     NIF_CK(h, cudaMemsetAsync(cursor, 0, sizeof(uint32_t), s));
     if ((st = nif_seg_temp_run(h, rays, inst_off, n_inst, n_rays, counts, (nif_segment*)h->b_temp.p, tcap, cursor, s)) !=
@@ -1082,9 +1083,9 @@ static nif_status segment_into_scratch(nif_handle* h, const nif_pose* poses, int
         // trip: one traversal into scratch in warp order, CSR offsets, scatter
         // into ray order and per-row sort; should the scratch overflow, a
         // second traversal (device-gated) writes the rows directly
-        int64_t tcap = 2 * cap + 4096;
+        int64_t tcap = (int64_t)(2.0 * h->seg_scratch_scale * (double)cap) + 4096;
         if ((st = nif_grow(h, h->b_temp, sizeof(nif_segment) * (size_t)tcap)) != NIF_OK) return st;
-        tcap = (int64_t)(h->b_temp.bytes / sizeof(nif_segment));
+        if (h->seg_scratch_scale >= 1.0) tcap = (int64_t)(h->b_temp.bytes / sizeof(nif_segment));
         if ((st = nif_grow(h, h->b_segs, sizeof(nif_segment) * (size_t)std::max<int64_t>(cap, 1))) != NIF_OK)
             return st;
         nif_segment* segs = (nif_segment*)h->b_segs.p;
@@ -1112,7 +1113,7 @@ static nif_status segment_into_scratch(nif_handle* h, const nif_pose* poses, int
 extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
                                 const int* inst_off, int n_rays, nif_hit* hits, unsigned flags, void* stream) {
     if (!h) return NIF_ERR_ARG;
-    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
     if (st != NIF_OK) return st;
     if (n_rays == 0) return NIF_OK;
     if (!rays || !hits) return nif_fail(h, NIF_ERR_ARG, "rays / hits");
@@ -1274,7 +1275,7 @@ extern "C" nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses, 
                                           const int* inst_off, int n_rays, int64_t n_segments, float lr_grid,
                                           float lr_mlp, double* loss_host, void* stream) {
     if (!h) return NIF_ERR_ARG;
-    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
     if (st != NIF_OK) return st;
     if (n_segments < 1 || !rays) return nif_fail(h, NIF_ERR_ARG, "n_segments / rays");
     const bool mixed = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
@@ -1288,7 +1289,7 @@ extern "C" nif_status nif_pose_step(nif_handle* h, const nif_pose* poses, int n_
                                     const int* inst_off, int n_rays, int64_t n_segments, float* dposes,
                                     double* loss_host, void* stream) {
     if (!h) return NIF_ERR_ARG;
-    nif_status st = check_inst(h, poses, n_inst, inst_off, n_rays);
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
     if (st != NIF_OK) return st;
     if (n_segments < 1 || !rays || !dposes) return nif_fail(h, NIF_ERR_ARG, "n_segments / rays / dposes");
     const int prec = h->cfg.precision;
@@ -1512,7 +1513,7 @@ extern "C" nif_status nif_train_steps_rays(nif_handle* h, int n_steps, const nif
         return nif_fail(h, NIF_ERR_ARG, "n_steps / n_rays / n_segments / rays");
     nif_status st;
     for (int i = 0; i < n_steps; i++)
-        if ((st = check_inst(h, poses ? poses + (size_t)i * n_inst : nullptr, n_inst, inst_off, n_rays)) != NIF_OK)
+        if ((st = nif_check_inst(h, poses ? poses + (size_t)i * n_inst : nullptr, n_inst, inst_off, n_rays)) != NIF_OK)
             return st;
     if ((h->cfg.flags & NIF_FLAG_MIXED_TRAINING) && (st = check_mixed(h)) != NIF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1544,4 +1545,27 @@ extern "C" nif_status nif_train_steps_rays(nif_handle* h, int n_steps, const nif
     NIF_CK(h, cudaStreamSynchronize(s));
     std::memcpy(loss_host, h->h_loss, sizeof(double) * 6 * (size_t)n_steps);
     return latched_status(h);
+}
+
+// ---------------------------------------------------------------------------
+// Knobs
+// ---------------------------------------------------------------------------
+extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
+    if (!h) return NIF_ERR_ARG;
+    switch (knob) {
+        case NIF_KNOB_WAIT_NS: {
+            if (!(value >= 0.0 && value <= 6.0e10)) return nif_fail(h, NIF_ERR_ARG, "wait bound must be in [0, 60 s]");
+            const uint64_t ns = (uint64_t)value;
+            // after the work already enqueued on any stream of this handle
+            NIF_CK(h, cudaDeviceSynchronize());
+            NIF_CK(h, cudaMemcpy(h->d_status + 2, &ns, sizeof(ns), cudaMemcpyHostToDevice));
+            return NIF_OK;
+        }
+        case NIF_KNOB_SEG_SCRATCH:
+            if (!(value > 0.0 && value <= 1.0)) return nif_fail(h, NIF_ERR_ARG, "segment scratch scale must be in (0, 1]");
+            h->seg_scratch_scale = value;
+            return NIF_OK;
+        default:
+            return nif_fail(h, NIF_ERR_ARG, "unknown knob");
+    }
 }

@@ -121,7 +121,7 @@ struct nif_handle {
     int h_loss_steps = 0;
 
     // device status word + scratch
-    int* d_status = nullptr;
+    int* d_status = nullptr;            // [0] latched status; [2..3] 64-bit wait bound (ns, 0 = 1 s)
     double* d_lossacc = nullptr;        // [16] loss accumulators
     int* d_count = nullptr;             // [4] counters
     uint32_t* d_next = nullptr;         // [4] work counters: [0] rays of the persistent traversal,
@@ -149,6 +149,7 @@ struct nif_handle {
         alt_pts, alt_sort;
     PointList alt_enc_points;
     double query_seg_per_ray = 0.0;     // segments per ray of the last query (temp capacity hint)
+    double seg_scratch_scale = 1.0;     // NIF_KNOB_SEG_SCRATCH: scale of the single-traversal segment scratch
 
     // launch knobs chosen by the autotuner (nif_query_plan_create)
     struct Tune {
@@ -205,6 +206,10 @@ void nif_free_retired(nif_handle* h);
 nif_status nif_ensure_instances(nif_handle* h, int n_inst);
 nif_status nif_upload_poses(nif_handle* h, const nif_pose* poses, int n_inst, cudaStream_t s);
 nif_status nif_refresh_lowp(nif_handle* h, cudaStream_t s);
+// argument checks shared by the entry points that take poses and rays
+nif_status nif_check_inst(nif_handle* h, const nif_pose* poses, int n_inst, const int* inst_off, int n_rays);
+// synchronises s, then returns (and clears) the device status word
+nif_status nif_check_status(nif_handle* h, cudaStream_t s);
 // loss scale back to its initial value (FP16 handles 2^15, others 1), counters cleared (blocking)
 nif_status reset_loss_scale(nif_handle* h);
 
@@ -324,6 +329,9 @@ nif_status nif_sample_rays_run(nif_handle* h, unsigned long long seed, int strea
                                nif_ray* rays, cudaStream_t s, int n_streams = 1);
 nif_status nif_scan_run_with(nif_handle* h, const uint32_t* in, uint32_t* out, int n, uint32_t* bsum,
                              cudaStream_t s);
+// elements per block of the scan: nif_scan_run_with needs a block-sum buffer of
+// ceil(n / NIF_SCAN_BLOCK) + 1 words
+constexpr int NIF_SCAN_BLOCK = 1024;
 // n_out = min(offsets[n_rays], cap), or with whole_rays the largest offsets[r] <= cap
 // (only complete rows); latch: an overflow latches NIF_ERR_CAPACITY (a
 // truncated query), otherwise it is the normal end of a training batch

@@ -46,14 +46,27 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: about one second of wall time, then the kernel gives up.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+// Default bound of a wait: about one second of wall time.
+constexpr uint64_t kWaitNs = 1000000000ull;
+
+// The handle's bound for the waits of a kernel's work loop, kept in the
+// 64-bit word after its status word (0: kWaitNs). Waits that drain a CTA's
+// own copies and MMAs before it exits keep kWaitNs, so that a shorter bound
+// never lets a CTA leave with work in flight.
+__device__ __forceinline__ uint64_t wait_limit(const int* status) {
+    const uint64_t v = *reinterpret_cast<const volatile uint64_t*>(status + 2);
+    return v ? v : kWaitNs;
+}
+
+// Bounded wait: `limit_ns` of wall time, then the kernel gives up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                          uint64_t limit_ns = kWaitNs) {
     if (mbar_try(bar, parity)) return true;
     uint64_t t0 = globaltimer();
     while (true) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > 1000000000ull) {
+        if (globaltimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicCAS(status, 0, (int)NIF_ERR_TIMEOUT);
             return false;

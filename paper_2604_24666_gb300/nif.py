@@ -25,6 +25,7 @@ NIF_SHADOW_ONLY = 1
 NIF_FLAG_FIXED_TASK_WEIGHTS, NIF_FLAG_SIGMOID_DISTANCE, NIF_FLAG_MIXED_TRAINING = 1, 2, 4
 NIF_FLAG_CONCAT_ENCODING = 8
 NIF_FLAG_BILINEAR_FACES = 16
+NIF_KNOB_WAIT_NS, NIF_KNOB_SEG_SCRATCH = 1, 2
 
 _STATUS = {0: "NIF_OK", -1: "NIF_ERR_ARG", -2: "NIF_ERR_CUDA", -3: "NIF_ERR_OOM", -4: "NIF_ERR_CAPACITY",
            -5: "NIF_ERR_TIMEOUT", -6: "NIF_ERR_NAN", -7: "NIF_ERR_STATE"}
@@ -130,6 +131,7 @@ def lib() -> ctypes.CDLL:
                                     ctypes.c_int),
             "nif_query_plan_destroy": ([_vp], None),
             "nif_sync_status": ([_vp, _vp], ctypes.c_int),
+            "nif_set_knob": ([_vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
             "nif_checkpoint_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
             "nif_checkpoint_save": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
             "nif_checkpoint_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
@@ -304,11 +306,13 @@ def nif_segments_walk(h, poses, rays, inst_offsets=None, seg_cap=None, flags=0, 
 
 
 def nif_segments_noalloc(h, poses, rays, ray_offsets, segs, inst_offsets=None, stream=None):
-    """Allocation-free segments into the caller's ray_offsets [n+1] and segs [cap, 4]; returns the total."""
+    """Allocation-free segments into the caller's ray_offsets [n+1] and segs [cap, 4] (None: count only);
+    returns the total."""
     p, n_inst = _poses(poses)
     total = _i64()
+    cap = segs.shape[0] if segs is not None else 0
     _check(h, lib().nif_segments_noalloc(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0],
-                                         _ptr(ray_offsets), _ptr(segs), segs.shape[0], ctypes.byref(total),
+                                         _ptr(ray_offsets), _ptr(segs), cap, ctypes.byref(total),
                                          _stream(stream)))
     return total.value
 
@@ -535,6 +539,12 @@ class QueryPlan:
 
 def nif_sync_status(h, stream=None):
     _check(h, lib().nif_sync_status(h, _stream(stream)))
+
+
+def nif_set_knob(h, knob, value):
+    """NIF_KNOB_WAIT_NS (bound of the tensor-core kernels' waits, ns; 0 = default) or
+    NIF_KNOB_SEG_SCRATCH (scale in (0, 1] of the single-traversal segment scratch)."""
+    _check(h, lib().nif_set_knob(h, knob, float(value)))
 
 
 def nif_checkpoint_save(h) -> bytes:

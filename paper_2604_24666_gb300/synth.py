@@ -180,6 +180,58 @@ def sphere_rays(n: int, seed: int = SEED_RAYS, radius: float = 2.0,
     return out
 
 
+def chained_segments(n: int, seed: int, voxel_res: int = 64, gap: float = 0.1,
+                     margin: float = 0.01) -> tuple:
+    """Linearized segments shaped like a training batch, without any method
+    arithmetic: straight lines through the cube (origin uniform on the
+    radius-2 sphere about the centre, aimed at a uniform point of the cube),
+    each clipped to [-margin, 1+margin]^3 and cut at spacings U[0.2, 1.2]/N
+    along the line; piece j runs from cut j to cut j+1, so a piece's entry
+    point is the previous piece's exit point bit for bit (float32), except
+    where a piece is left out (probability `gap`, like a ray crossing an
+    empty voxel). Points up to `margin` outside the cube occur near the
+    faces.
+
+    Returns (lin [n, 8] float32 = p0.xyz, p1.xyz, l_def, l_rest with both
+    lengths |p1 - p0|, voxel [n] uint32 = the voxel i + N(j + Nk) holding the
+    piece's midpoint, clamped into the grid)."""
+    rng = np.random.default_rng(seed)
+    rows, vox = [], []
+    total = 0
+    lo, hi = -margin, 1.0 + margin
+    while total < n:
+        z = rng.uniform(-1, 1)
+        a = rng.uniform(0, 2 * np.pi)
+        r = math.sqrt(1 - z * z)
+        o = CENTER + 2.0 * np.array([r * math.cos(a), r * math.sin(a), z])
+        d = rng.uniform(0, 1, 3) - o
+        d /= np.linalg.norm(d)
+        with np.errstate(divide="ignore"):
+            t1 = (lo - o) / d
+            t2 = (hi - o) / d
+        ta = np.max(np.minimum(t1, t2))
+        tb = np.min(np.maximum(t1, t2))
+        if not tb > ta:
+            continue
+        cuts = [ta]
+        while True:
+            c = cuts[-1] + rng.uniform(0.2, 1.2) / voxel_res
+            if c >= tb:
+                break
+            cuts.append(c)
+        cuts.append(tb)
+        pts = (o[None, :] + np.asarray(cuts)[:, None] * d[None, :]).astype(np.float32)
+        keep = rng.random(len(pts) - 1) >= gap
+        for j in np.nonzero(keep)[0]:
+            p0, p1 = pts[j], pts[j + 1]
+            ln = np.float32(np.linalg.norm(p1.astype(np.float64) - p0.astype(np.float64)))
+            rows.append(np.concatenate([p0, p1, [ln, ln]]).astype(np.float32))
+            mid = np.clip(np.floor(0.5 * (p0.astype(np.float64) + p1) * voxel_res), 0, voxel_res - 1).astype(np.int64)
+            vox.append(mid[0] + voxel_res * (mid[1] + voxel_res * mid[2]))
+        total = len(rows)
+    return np.stack(rows[:n]), np.asarray(vox[:n], np.uint32)
+
+
 def camera_rays(width: int = 1920, height: int = 1080, grid: int = 4, eye=(0.5, -0.65, 0.95),
                 target=CENTER, vfov_deg: float = 48.0) -> tuple:
     """Primary rays of one frame of a grid x grid world of instances seen by
