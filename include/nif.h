@@ -388,16 +388,21 @@ nif_status nif_reconstruct(nif_handle* h, const nif_pose* poses_host, int n_inst
 /* Whole paths                                                               */
 /* ------------------------------------------------------------------------ */
 
-/* Query (the inference hot path): segments -> linearization -> encoding ->
- * MLP (cfg.precision) -> reconstruction, for n_inst deformed instances of
- * the handle's shape. Rays and hits are device buffers of n_rays entries.
+/* Query (the inference hot path; the problem of Sec. 2: where does a ray in
+ * the deformed space first hit the deformed shape): segments (Sec. 2.1,
+ * Sec. 2.2) -> linearization (Sec. 2, Fig. 2c) -> encoding (Sec. 2.3, Eq. 1)
+ * -> MLP (cfg.precision; Sec. 2, Fig. 2d) -> reconstruction along the
+ * segmented ray (Sec. 2.2), for n_inst deformed instances of the handle's
+ * shape. Rays and hits are device buffers of n_rays entries.
  * Does not block the host; scratch grows on demand (growing synchronises). */
 nif_status nif_query(nif_handle* h, const nif_pose* poses_host, int n_inst,
                      const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
                      nif_hit* hits_dev, unsigned flags, void* stream);
 
-/* One training step on caller-given rays (FP32, or the mixed-precision path
- * of NIF_FLAG_MIXED_TRAINING): segments of the rays are generated and the
+/* One training step on caller-given rays (Sec. 2: ground truth from the rest
+ * mesh along the linearized segments; Sec. 2.4: task losses with learned
+ * uncertainty weights; FP32, or the mixed-precision path of
+ * NIF_FLAG_MIXED_TRAINING): segments of the rays are generated and the
  * batch is the segments of the leading whole rays, in ray order, at most
  * n_segments (a ray whose segments would cross n_segments is left out, so
  * the batch is a deterministic function of the rays and poses). They are
@@ -410,8 +415,10 @@ nif_status nif_train_step_rays(nif_handle* h, const nif_pose* poses_host, int n_
                                int64_t n_segments, float lr_grid, float lr_mlp, double* loss_host,
                                void* stream);
 
-/* One training step with samples drawn on the device from step_seed:
- * n_poses poses with every parameter U[-1,1] and, per pose, rays whose
+/* One training step with samples drawn on the device from step_seed (the
+ * training of Sec. 2 and Sec. 2.4 over random poses, so that one network
+ * serves every deformation): n_poses poses with every parameter U[-1,1] and,
+ * per pose, rays whose
  * origins are uniform on the radius-2 sphere about the cube centre aimed at
  * points uniform in [0,1]^3 (counter-based splitmix64 stream), enough rays
  * for n_segments segments. poses_out_host (nullable) receives the poses. */
@@ -419,8 +426,9 @@ nif_status nif_train_step(nif_handle* h, int64_t n_segments, int n_poses,
                           unsigned long long step_seed, float lr_grid, float lr_mlp,
                           nif_pose* poses_out_host, double* loss_host, void* stream);
 
-/* n_steps training steps, exactly what n_steps calls of nif_train_step with
- * the seeds first_seed, first_seed + 1, ... compute, in one call. The batch
+/* n_steps training steps (Sec. 2, Sec. 2.4), exactly what n_steps calls of
+ * nif_train_step with the seeds first_seed, first_seed + 1, ... compute, in
+ * one call. The batch
  * of a step (sampling, segments, linearization, labels: nothing that depends
  * on the parameters) is built on a second internal stream, into a second set
  * of batch buffers, while the previous step trains, so it costs no time on
@@ -431,8 +439,8 @@ nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segments, int n
                            unsigned long long first_seed, float lr_grid, float lr_mlp, double* loss_host,
                            void* stream);
 
-/* n_steps training steps on caller-given rays held in HOST memory: step i
- * trains, as nif_train_step_rays does, on the n_rays rays at
+/* n_steps training steps (Sec. 2, Sec. 2.4) on caller-given rays held in
+ * HOST memory: step i trains, as nif_train_step_rays does, on the n_rays rays at
  * rays_host + i * n_rays with the n_inst poses at poses_host + i * n_inst
  * (inst_offsets_dev, a device array shared by all steps, nullable when
  * n_inst == 1). Each step's rays are copied to the device and its batch is

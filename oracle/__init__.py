@@ -76,7 +76,7 @@ def lib():
                                       ctypes.c_void_p, ctypes.c_long]
             L.or_voxelize.restype = ctypes.c_long
             L.or_segments.argtypes = [ctypes.c_int, u8, dp, fp, ctypes.c_long, ctypes.c_int, ip, ip,
-                                      dp, dp, dp, ctypes.c_int]
+                                      dp, dp, dp, ctypes.c_int, ctypes.c_void_p]
             L.or_bilinear_hits.argtypes = [dp, dp, dp, dp, dp, dp, dp, dp, dp]
             L.or_bilinear_hits.restype = ctypes.c_int
             L.or_segments.restype = ctypes.c_long
@@ -173,11 +173,18 @@ def bilinear_hits(o, d, P00, P10, P01, P11):
     return [(t[i], uv[2 * i], uv[2 * i + 1]) for i in range(n)], (sep[0] if n == 2 else np.inf)
 
 
-def segments(N: int, occ, pose, rays, max_per_ray: int = 512, faces: str = "triangles") -> Segments:
+def segments(N: int, occ, pose, rays, max_per_ray: int = 512, faces: str = "triangles", field=None) -> Segments:
     """Ray / deformed voxel segments (Sec. 2.1, 2.2). faces: "triangles" (each
     face split along the diagonal from its lowest lattice corner) or
-    "bilinear" (each face the bilinear patch of its four corners)."""
+    "bilinear" (each face the bilinear patch of its four corners). With a
+    learned deformation field (`field`, see `deform_field`) the hull corners
+    are D(lattice corners) of the composed deformation."""
     assert faces in ("triangles", "bilinear")
+    lattice = None
+    if field is not None:
+        g = np.arange(N + 1, dtype=np.float64) / N
+        Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+        lattice = np.ascontiguousarray(deform_field(pose, field, np.stack([X, Y, Z], -1).reshape(-1, 3)))
     rays = np.ascontiguousarray(rays, np.float32)
     n = len(rays)
     cnt = np.zeros(n, np.int32)
@@ -186,17 +193,19 @@ def segments(N: int, occ, pose, rays, max_per_ray: int = 512, faces: str = "tria
     t1 = np.zeros(n * max_per_ray)
     mar = np.zeros(n)
     ov = lib().or_segments(N, np.ascontiguousarray(occ, np.uint8), _pose(pose), rays, n,
-                           max_per_ray, cnt, vox, t0, t1, mar, int(faces == "bilinear"))
+                           max_per_ray, cnt, vox, t0, t1, mar, int(faces == "bilinear"),
+                           None if lattice is None else lattice.ctypes.data_as(ctypes.c_void_p))
     if ov:
         raise RuntimeError(f"{ov} rays exceed {max_per_ray} segments")
     sel = (np.arange(max_per_ray)[None, :] < cnt[:, None]).reshape(-1)
     return Segments(cnt, vox[sel], t0[sel], t1[sel], mar)
 
 
-def linearize(pose, rays, seg: Segments):
+def linearize(pose, rays, seg: Segments, field=None):
     """Rest-space straight segment of every (ray, voxel) segment (Sec. 2).
 
-    x0 = o + t0 d, x1 = o + t1 d in deformed space; p0 = D^-1(x0), p1 = D^-1(x1).
+    x0 = o + t0 d, x1 = o + t1 d in deformed space; p0 = D^-1(x0), p1 = D^-1(x1)
+    (with `field`, the inverse of the composed deformation, `inverse_field`).
     Returns p0, p1 [S,3], l_def = |x1 - x0|, l_rest = |p1 - p0|.
     """
     rays = np.asarray(rays, np.float64)
@@ -204,8 +213,9 @@ def linearize(pose, rays, seg: Segments):
     d = rays[seg.ray, 3:6]
     x0 = o + seg.t0[:, None] * d
     x1 = o + seg.t1[:, None] * d
-    p0 = inverse(pose, x0)
-    p1 = inverse(pose, x1)
+    inv = (lambda y: inverse_field(pose, field, y)) if field is not None else (lambda y: inverse(pose, y))
+    p0 = inv(x0)
+    p1 = inv(x1)
     return p0, p1, np.linalg.norm(x1 - x0, axis=1), np.linalg.norm(p1 - p0, axis=1)
 
 
@@ -581,7 +591,7 @@ def adam(theta, m, v, g, step, lr, b1=0.9, b2=0.99, eps=1e-15):
 # Reconstruction along the segmented ray (Sec. 2.2)
 # ---------------------------------------------------------------------------
 
-def reconstruct(cfg, pose, rays, seg: Segments, out, p0, p1, l_def, l_rest, flags=0):
+def reconstruct(cfg, pose, rays, seg: Segments, out, p0, p1, l_def, l_rest, flags=0, field=None):
     """Per ray: first segment k (in list order) with sigmoid(occ) > 0.5;
     D = sum_{j<k} (delta_j + l_j) + delta_k + t_k with t_k the predicted rest
     distance mapped to deformed length, t_k = (dist/N) * l_def/l_rest, clamped
@@ -610,8 +620,8 @@ def reconstruct(cfg, pose, rays, seg: Segments, out, p0, p1, l_def, l_rest, flag
                 res["D"][r] = acc + delta + tk
                 frac = trest / l_rest[j] if l_rest[j] > 0 else 0.0
                 ph = p0[j] + frac * (p1[j] - p0[j])
-                J, _ = jacobians(pose, ph[None])
-                nd = np.linalg.solve(J[0].T, out[j, 2:5])
+                J = jacobian_field(pose, field, ph[None])[0] if field is not None else jacobians(pose, ph[None])[0][0]
+                nd = np.linalg.solve(J.T, out[j, 2:5])
                 res["normal"][r] = nd / max(np.linalg.norm(nd), 1e-30)
                 res["albedo"][r] = _sigmoid(out[j, 5:8])
                 res["material"][r] = int(np.argmax(out[j, 8:8 + cfg.n_materials]))
@@ -643,3 +653,151 @@ def pose_gradient(cfg, tables, pose, p0, p1, dfeat):
         dpdth = -np.linalg.solve(J, Jp)            # [n, 3, 3]: d p_i / d theta_j
         g += np.einsum("ni,nij->j", dp, dpdth)
     return g
+
+
+# ---------------------------------------------------------------------------
+# Learned deformation field (the paper's Sec. 4 names learning deformation
+# fields jointly with intersection prediction as future work and defines no
+# field; this is our reading)
+# ---------------------------------------------------------------------------
+#
+# A field is an array delta [G, G, G, 3] (index [k, j, i] = node
+# (i, j, k)/(G-1) of a lattice over the rest cube, G >= 2) of rest-space
+# displacements, interpolated trilinearly: u(p) = sum_n w_n(p) delta_n with
+# p clamped to [0,1]^3 first. The deformation of an instance with pose theta
+# and field delta is the composition
+#     D(p) = D_theta(p + u(p)),
+# the field acting in rest space before the parameterised deformation, so
+# that a zero field is the analytic deformation and a zero pose the field
+# alone. Voxel hulls are the hexahedra of D(lattice corners) as for the
+# analytic deformation. Its inverse takes q = D_theta^-1(x) (closed form)
+# and solves F(p) = p + u(p) - q = 0. While the Lipschitz bound l of u
+# (`field_lipschitz`) is below 1, p -> q - u(p) is a contraction, so the
+# root is unique, and |p - p*| <= |F(p)| / (1 - l) for any p.
+
+
+def field_cell(field, p):
+    """Cell, weights and clamping of rest points p [n,3] in the field's
+    lattice: (i0 [n,3] int, t [n,3] in [0,1], inside [n,3] bool)."""
+    G = field.shape[0]
+    p = np.asarray(p, np.float64)
+    inside = (p >= 0.0) & (p <= 1.0)
+    s = np.clip(p, 0.0, 1.0) * (G - 1)
+    i0 = np.minimum(np.floor(s), G - 2).astype(np.int64)
+    return i0, s - i0, inside
+
+
+def field_displacement(field, p):
+    """u(p) [n,3]: trilinear interpolation of the node displacements."""
+    field = np.asarray(field, np.float64)
+    i0, t, _ = field_cell(field, p)
+    u = np.zeros((len(i0), 3))
+    for c in _CORNERS:
+        w = np.prod(np.where(c == 1, t, 1.0 - t), axis=1)
+        n = i0 + c
+        u += w[:, None] * field[n[:, 2], n[:, 1], n[:, 0]]
+    return u
+
+
+def field_grad(field, p):
+    """du/dp [n,3,3] (row: component of u, column: coordinate of p); zero
+    along a coordinate where p lies outside [0,1] (u is constant there)."""
+    field = np.asarray(field, np.float64)
+    G = field.shape[0]
+    i0, t, inside = field_cell(field, p)
+    g = np.zeros((len(i0), 3, 3))
+    for c in _CORNERS:
+        n = i0 + c
+        d = field[n[:, 2], n[:, 1], n[:, 0]]
+        f = np.where(c == 1, t, 1.0 - t)
+        for a in range(3):
+            others = np.prod(np.delete(f, a, axis=1), axis=1)
+            sgn = 1.0 if c[a] == 1 else -1.0
+            g[:, :, a] += (sgn * (G - 1) * others)[:, None] * d
+    return g * inside[:, None, :]
+
+
+def deform_field(pose, field, p):
+    """D(p) = D_theta(p + u(p))."""
+    p = np.asarray(p, np.float64).reshape(-1, 3)
+    return deform(pose, p + field_displacement(field, p))
+
+
+def jacobian_field(pose, field, p):
+    """dD/dp [n,3,3] = J_theta(p + u(p)) (I + du/dp)."""
+    p = np.asarray(p, np.float64).reshape(-1, 3)
+    J, _ = jacobians(pose, p + field_displacement(field, p))
+    return np.einsum("nij,njk->nik", J, np.eye(3)[None] + field_grad(field, p))
+
+
+def field_lipschitz(field):
+    """Bound l on the spectral norm of du/dp over the cube: within a cell,
+    du/dp_a is a convex combination of the cell's four edge differences
+    along a times (G-1), so ||du/dp||_2 <= ||du/dp||_F <= the root of the
+    sum over a of (G-1)^2 max_edge |delta_b - delta_a|^2."""
+    f = np.asarray(field, np.float64)
+    G = f.shape[0]
+    m = np.zeros((G - 1, G - 1, G - 1, 3))
+    # axis 0 of the array is z (k), 1 is y (j), 2 is x (i)
+    for a, ax in ((0, 2), (1, 1), (2, 0)):
+        e = np.linalg.norm(np.diff(f, axis=ax), axis=-1) * (G - 1)     # edges along this axis
+        # the four edges of a cell along this axis: max over the other two axes' two positions
+        others = [o for o in (0, 1, 2) if o != ax]
+        for o in others:
+            e = np.maximum(np.take(e, range(0, e.shape[o] - 1), axis=o), np.take(e, range(1, e.shape[o]), axis=o))
+        m[..., a] = e
+    return float(np.sqrt((m ** 2).sum(-1)).max())
+
+
+def field_inverse(field, q, tol=1e-14, max_iter=100):
+    """p with p + u(p) = q, by Newton's method on F(p) = p + u(p) - q from
+    p = q - u(q); the field must satisfy field_lipschitz < 1."""
+    q = np.asarray(q, np.float64).reshape(-1, 3)
+    p = q - field_displacement(field, q)
+    for _ in range(max_iter):
+        F = p + field_displacement(field, p) - q
+        if np.abs(F).max() <= tol:
+            break
+        J = np.eye(3)[None] + field_grad(field, p)
+        p = p - np.linalg.solve(J, F[..., None])[..., 0]
+    return p
+
+
+def inverse_field(pose, field, x):
+    """D^-1(x) of the composed deformation: Newton on the field after the
+    closed-form inverse of the pose."""
+    return field_inverse(field, inverse(pose, x))
+
+
+def field_from_pose(G, pose):
+    """Field whose nodes carry the analytic deformation: delta_n =
+    D_theta(x_n) - x_n, so that the field alone (zero pose) agrees with the
+    pose at every node and between nodes up to the trilinear interpolation
+    error."""
+    g = np.arange(G, dtype=np.float64) / (G - 1)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    x = np.stack([X, Y, Z], -1).reshape(-1, 3)
+    return (deform(pose, x) - x).reshape(G, G, G, 3)
+
+
+def field_gradient(cfg, tables, pose, field, p0, p1, dfeat):
+    """d/d(delta) [G,G,G,3] of sum(dfeat * [psi(p0) (+) psi(p1)]) where the
+    rest points are p = D^-1(x) of fixed deformed points x. With q =
+    D_theta^-1(x) fixed, p + u(p) = q gives dp/d(delta_n) = -(I + du/dp)^-1
+    w_n(p), so the gradient is -sum over points of w_n(p) (I + du/dp)^-T dL/dp
+    with dL/dp from `encode_points_backward`."""
+    concat = getattr(cfg, "encoding", "composed") == "concat"
+    half = cfg.point_width if concat else dfeat.shape[1] // 2
+    back = encode_points_concat_backward if concat else encode_points_backward
+    field = np.asarray(field, np.float64)
+    out = np.zeros_like(field)
+    for p, df in ((p0, dfeat[:, :half]), (p1, dfeat[:, half:2 * half])):
+        _, dp = back(cfg, tables, p, df)
+        A = np.eye(3)[None] + field_grad(field, p)
+        v = np.linalg.solve(np.transpose(A, (0, 2, 1)), dp[..., None])[..., 0]     # (I + du/dp)^-T dL/dp
+        i0, t, _ = field_cell(field, p)
+        for c in _CORNERS:
+            w = np.prod(np.where(c == 1, t, 1.0 - t), axis=1)
+            n = i0 + c
+            np.add.at(out, (n[:, 2], n[:, 1], n[:, 0]), -w[:, None] * v)
+    return out

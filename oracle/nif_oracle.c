@@ -343,8 +343,22 @@ static double point_seg_dist(const double X[3], const double* A, const double* B
     return sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
 }
 
-/* Deformed corners of voxel (i,j,k): X[8][3], local id = a + 2b + 4c. */
-static void hull_corners(int N, int i, int j, int k, const double* pose, double X[8][3]) {
+/* Deformed corners of voxel (i,j,k): X[8][3], local id = a + 2b + 4c. With
+ * `lattice` (deformed positions of all (N+1)^3 lattice corners, index
+ * a + (N+1)(b + (N+1)c), as a learned deformation field gives them) the
+ * corners are read from it instead of deforming by the pose. */
+static void hull_corners(int N, int i, int j, int k, const double* pose, const double* lattice, double X[8][3]) {
+    if (lattice) {
+        const long M = N + 1;
+        for (int c = 0; c < 8; c++) {
+            const long a = i + (c & 1), b = j + ((c >> 1) & 1), e = k + ((c >> 2) & 1);
+            const double* L = lattice + 3 * (a + M * (b + M * e));
+            X[c][0] = L[0];
+            X[c][1] = L[1];
+            X[c][2] = L[2];
+        }
+        return;
+    }
     double P[24];
     for (int c = 0; c < 8; c++) {
         P[3 * c + 0] = (double)(i + (c & 1)) / N;
@@ -459,7 +473,8 @@ static int seg_cmp(const void* a, const void* b) {
  * Returns the number of rays that overflowed max_per_ray.
  */
 long or_segments(int N, const uint8_t* occ, const double* pose, const float* rays, long n,
-                 int max_per_ray, int* count, int* vox, double* t0, double* t1, double* margin, int bilinear) {
+                 int max_per_ray, int* count, int* vox, double* t0, double* t1, double* margin, int bilinear,
+                 const double* lattice) {
     long nvox = (long)N * N * N;
     long nocc = 0;
     for (long v = 0; v < nvox; v++) nocc += occ[v] != 0;
@@ -472,7 +487,7 @@ long or_segments(int N, const uint8_t* occ, const double* pose, const float* ray
     double (*bmax)[3] = (double (*)[3])malloc(sizeof(double) * 3 * (size_t)(nocc ? nocc : 1));
     for (long q = 0; q < nocc; q++) {
         int v = list[q];
-        hull_corners(N, v % N, (v / N) % N, v / (N * N), pose, X[q]);
+        hull_corners(N, v % N, (v / N) % N, v / (N * N), pose, lattice, X[q]);
         for (int a = 0; a < 3; a++) { bmin[q][a] = 1e300; bmax[q][a] = -1e300; }
         for (int c = 0; c < 8; c++)
             for (int a = 0; a < 3; a++) {

@@ -443,6 +443,109 @@ __device__ __forceinline__ void nif_param_jacobian_cols(float3 x, float4 pose, f
     dta = make_float3(cb * wx, wy, -sb * wx);
 }
 
+// ---------------------------------------------------------------------------
+// Learned deformation field (our reading of the paper's future work, Sec. 4):
+// per instance a lattice of G^3 rest-space displacements delta (node (i,j,k)
+// at (i,j,k)/(G-1), stored [inst][k][j][i] as float4), interpolated
+// trilinearly at p clamped to [0,1]^3: u(p). The instance's deformation is
+// D(p) = D_pose(p + u(p)); its inverse takes q = D_pose^-1(x) and solves
+// p + u(p) = q by Newton's method. The field's Lipschitz bound is kept at
+// NIF_FIELD_MAX_LIPSCHITZ or below, so the root is unique and
+// |p - p*| <= |p + u(p) - q| / (1 - bound).
+// ---------------------------------------------------------------------------
+#define NIF_FIELD_MAX_G 33
+#define NIF_FIELD_MAX_LIPSCHITZ 0.5f
+struct FieldView {
+    const float4* d = nullptr;   // [n][G^3] (delta, 0); nullptr: no field
+    int G = 0;
+    int n = 0;                   // instances that have a field
+};
+
+__device__ __forceinline__ void nif_field_cell(int G, float3 p, int& i, int& j, int& k, float3& t) {
+    const float s = (float)(G - 1);
+    const float x = fminf(fmaxf(p.x, 0.f), 1.f) * s, y = fminf(fmaxf(p.y, 0.f), 1.f) * s,
+                z = fminf(fmaxf(p.z, 0.f), 1.f) * s;
+    i = min((int)floorf(x), G - 2);
+    j = min((int)floorf(y), G - 2);
+    k = min((int)floorf(z), G - 2);
+    t = make_float3(x - (float)i, y - (float)j, z - (float)k);
+}
+
+// u(p) and, if g != nullptr, the columns g[a] = du/dp_a (zero along a
+// coordinate where p lies outside [0,1], where u is constant)
+__device__ __forceinline__ float3 nif_field_eval(const FieldView& f, int inst, float3 p, float3* g) {
+    const int G = f.G;
+    int i, j, k;
+    float3 t;
+    nif_field_cell(G, p, i, j, k, t);
+    const float4* D = f.d + (int64_t)inst * G * G * G;
+    float3 u = make_float3(0.f, 0.f, 0.f);
+    float3 g0 = u, g1 = u, g2 = u;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const int a = c & 1, b = (c >> 1) & 1, e = (c >> 2) & 1;
+        const float4 v = __ldg(D + ((int64_t)(k + e) * G + (j + b)) * G + (i + a));
+        const float fx = a ? t.x : 1.f - t.x, fy = b ? t.y : 1.f - t.y, fz = e ? t.z : 1.f - t.z;
+        const float w = fx * fy * fz;
+        u.x += w * v.x;
+        u.y += w * v.y;
+        u.z += w * v.z;
+        if (g) {
+            const float s = (float)(G - 1);
+            const float wx = (a ? s : -s) * fy * fz, wy = (b ? s : -s) * fx * fz, wz = (e ? s : -s) * fx * fy;
+            g0.x += wx * v.x; g0.y += wx * v.y; g0.z += wx * v.z;
+            g1.x += wy * v.x; g1.y += wy * v.y; g1.z += wy * v.z;
+            g2.x += wz * v.x; g2.y += wz * v.y; g2.z += wz * v.z;
+        }
+    }
+    if (g) {
+        const float ox = (p.x >= 0.f && p.x <= 1.f) ? 1.f : 0.f, oy = (p.y >= 0.f && p.y <= 1.f) ? 1.f : 0.f,
+                    oz = (p.z >= 0.f && p.z <= 1.f) ? 1.f : 0.f;
+        g[0] = make_float3(g0.x * ox, g0.y * ox, g0.z * ox);
+        g[1] = make_float3(g1.x * oy, g1.y * oy, g1.z * oy);
+        g[2] = make_float3(g2.x * oz, g2.y * oz, g2.z * oz);
+    }
+    return u;
+}
+
+// x = A^-1 r for A with columns c0, c1, c2 (Cramer's rule)
+__device__ __forceinline__ float3 nif_solve3(float3 c0, float3 c1, float3 c2, float3 r) {
+    const float3 x01 = make_float3(c1.y * c2.z - c1.z * c2.y, c1.z * c2.x - c1.x * c2.z, c1.x * c2.y - c1.y * c2.x);
+    const float det = c0.x * x01.x + c0.y * x01.y + c0.z * x01.z;
+    const float inv = 1.0f / det;
+    const float3 a = make_float3(r.y * c2.z - r.z * c2.y, r.z * c2.x - r.x * c2.z, r.x * c2.y - r.y * c2.x);
+    const float3 b = make_float3(c1.y * r.z - c1.z * r.y, c1.z * r.x - c1.x * r.z, c1.x * r.y - c1.y * r.x);
+    return make_float3((r.x * x01.x + r.y * x01.y + r.z * x01.z) * inv,
+                       (c0.x * a.x + c0.y * a.y + c0.z * a.z) * inv,
+                       (c0.x * b.x + c0.y * b.y + c0.z * b.z) * inv);
+}
+
+// x = A^-T r for A with columns c0, c1, c2: the rows of A^T are c0, c1, c2
+__device__ __forceinline__ float3 nif_solve3_t(float3 c0, float3 c1, float3 c2, float3 r) {
+    return nif_solve3(make_float3(c0.x, c1.x, c2.x), make_float3(c0.y, c1.y, c2.y), make_float3(c0.z, c1.z, c2.z), r);
+}
+
+// p with p + u(p) = q: Newton from one fixed-point step, until the FP32
+// residual stops shrinking (at most 8 iterations)
+__device__ __forceinline__ float3 nif_field_inverse(const FieldView& f, int inst, float3 q) {
+    float3 u = nif_field_eval(f, inst, q, nullptr);
+    float3 p = make_float3(q.x - u.x, q.y - u.y, q.z - u.z);
+    float prev = 3.0e38f;
+    for (int it = 0; it < 8; it++) {
+        float3 g[3];
+        u = nif_field_eval(f, inst, p, g);
+        const float3 F = make_float3(p.x + u.x - q.x, p.y + u.y - q.y, p.z + u.z - q.z);
+        const float r = fmaxf(fabsf(F.x), fmaxf(fabsf(F.y), fabsf(F.z)));
+        if (r == 0.f || r >= prev) break;
+        prev = r;
+        const float3 dp = nif_solve3(make_float3(1.f + g[0].x, g[0].y, g[0].z),
+                                     make_float3(g[1].x, 1.f + g[1].y, g[1].z),
+                                     make_float3(g[2].x, g[2].y, 1.f + g[2].z), F);
+        p = make_float3(p.x - dp.x, p.y - dp.y, p.z - dp.z);
+    }
+    return p;
+}
+
 __device__ __forceinline__ float3 nif_cross(float3 a, float3 b) {
     return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }

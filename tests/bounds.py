@@ -86,24 +86,45 @@ def feature_bound(net, tables, p):
     return out.reshape(n, -1)
 
 
+def loss_grad_bound(net, out, lab, s, l_rest, out_err, flags=0):
+    """[S, O] first-order bound on how much the loss gradient dL/dout moves
+    when each output column j moves by at most out_err[j]: rows are
+    independent, so perturbing a whole column at once and differencing the
+    oracle's own gradient gives sum_j |d(dL/dout)/d out_j| out_err[j] for
+    every row."""
+    out = np.asarray(out, np.float64)
+    err = np.zeros_like(out)
+    for j in range(out.shape[1]):
+        if out_err[j] == 0:
+            continue
+        e = np.zeros(out.shape[1])
+        e[j] = out_err[j]
+        hi = O.loss(net, out + e, lab, s, l_rest, flags)[2]
+        lo = O.loss(net, out - e, lab, s, l_rest, flags)[2]
+        err += 0.5 * np.abs(hi - lo)
+    return err
+
+
 def table_grad_bound(net, tables, p, dfeat, dfeat_err=0.0):
     """[L, T, F_d] bound on the FP32 table gradient of sum(dfeat * psi(p))
     against the oracle's (same cells). Entry e with contributions w_i d_i,
     i = 1..k_e:
         (k_e + 6) u sum w_i |d_i|          rounding of weights, products, sums
       + 3 N_l DU sum_{i sin/cos} |d_i|     sin/cos weights
-      + dfeat_err sum w_i                  error of the given gradients
-    Several (p, dfeat) pairs are summed by calling this on the stacked
-    arrays."""
+      + sum w_i dfeat_err_i                error of the given gradients
+    dfeat_err is a scalar or per element of dfeat. Several (p, dfeat) pairs
+    are summed by calling this on the stacked arrays."""
     tables = np.asarray(tables, np.float64)
     _, u = _terms(net, p)
     n, P = u.shape[0], u.shape[1]
     d = np.abs(np.asarray(dfeat, np.float64)).reshape(n, P, net.levels, net.feats)
+    de = np.broadcast_to(np.asarray(dfeat_err, np.float64), (n, P * net.levels * net.feats))
+    de = de.reshape(n, P, net.levels, net.feats)
     res = O.level_res(net)
     A = np.zeros_like(tables)
     B = np.zeros_like(tables)
+    E = np.zeros_like(tables)
     K = np.zeros(tables.shape[:2])
-    Wsum = np.zeros(tables.shape[:2])
     for t in range(P):
         for l in range(net.levels):
             i0, w = O._cell(net, l, u[:, t])
@@ -112,11 +133,11 @@ def table_grad_bound(net, tables, p, dfeat, dfeat_err=0.0):
                 wt = np.prod(np.where(c == 1, w, 1.0 - w), axis=1)
                 np.add.at(A[l], idx, wt[:, None] * d[:, t, l, :])
                 np.add.at(K[l], idx, 1.0)
-                np.add.at(Wsum[l], idx, wt)
+                np.add.at(E[l], idx, wt[:, None] * de[:, t, l, :])
                 if t > 0:
                     np.add.at(B[l], idx, d[:, t, l, :])
     res_col = np.asarray(res, np.float64)[:, None, None]
-    return (K[..., None] + 6) * U32 * A + 3 * res_col * DU * B + dfeat_err * Wsum[..., None]
+    return (K[..., None] + 6) * U32 * A + 3 * res_col * DU * B + E
 
 
 def point_grad_bound(net, tables, p, dfeat, dfeat_err=0.0):
