@@ -471,6 +471,69 @@ nif_status nif_pose_step(nif_handle* h, const nif_pose* poses_host, int n_inst, 
                          const int* inst_offsets_dev, int n_rays, int64_t n_segments, float* dposes_dev,
                          double* loss_host, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Learned deformation fields (the paper, Sec. 4, names learning deformation  */
+/* fields jointly with intersection prediction as future work and defines    */
+/* none; this parameterisation, its inverse and the fitting objective are     */
+/* our reading)                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* A field gives each instance i a lattice of G x G x G rest-space
+ * displacements delta_i (node (a, b, c) at (a, b, c)/(G-1) of the rest cube),
+ * interpolated trilinearly at p clamped to [0,1]^3: u_i(p). With a field the
+ * deformation of instance i is D(p) = D_pose_i(p + u_i(p)): a zero field is the
+ * parameterised deformation, a zero pose the field alone. Every call that
+ * takes poses then uses it: the voxel hulls are the hexahedra of D(lattice
+ * corners) (Sec. 2.1), the linearized rest points are D^-1(x) -- q =
+ * D_pose^-1(x) in closed form, then p + u(p) = q by Newton's method, whose
+ * root is unique because the field's Lipschitz bound (the root of the sum
+ * over the axes of ((G-1) x the largest displacement difference along that
+ * axis within a cell)^2, an upper bound of |du/dp|) is at most 0.9 -- and
+ * the normal of a hit is J_D^-T n (Sec. 2.2); n_inst may not exceed the
+ * field's instance count (NIF_ERR_ARG).
+ * nif_set_field: n_inst fields of G nodes per axis, 2 <= G <= 33, from
+ * delta_host [n_inst][G][G][G][3] (index [i][c][b][a], host, copied); the
+ * Adam moments of the field are reset. NIF_ERR_ARG if a displacement is not
+ * finite or a field's bound exceeds 0.9. n_inst == 0 removes the field.
+ * A query plan applies the field as it was when the plan was created: while
+ * plans exist, only the values of an existing field may change (same n_inst
+ * and G), otherwise NIF_ERR_STATE. Synchronises the device.
+ * nif_get_field: *n_inst_host and *G_host (nullable) receive the sizes;
+ * delta_host (nullable, `bytes` = n_inst G^3 3 sizeof(float)) the values.
+ * Synchronises the device. */
+nif_status nif_set_field(nif_handle* h, int n_inst, int G, const float* delta_host);
+nif_status nif_get_field(nif_handle* h, int* n_inst_host, int* G_host, float* delta_host, size_t bytes);
+
+/* Gradient with respect to the field (FP32): for segments whose deformed end
+ * points x0 = o + t0 d, x1 = o + t1 d are held fixed, the rest points are
+ * p = D^-1(x); with q = D_pose^-1(x) fixed, p + u(p) = q gives
+ * dp/d(delta_n) = -(I + du/dp)^-1 w_n(p), w_n the trilinear weight of node
+ * n. With tables and weights frozen this adds d(sum dfeats * [psi(p0) (+)
+ * psi(p1)])/d(delta) into dfield_dev [n_inst][G^3][3] (accumulated). Other
+ * arguments as nif_pose_gradient. NIF_ERR_STATE without a field. */
+nif_status nif_field_gradient(nif_handle* h, const nif_pose* poses_host, int n_inst,
+                              const int* inst_offsets_dev, const nif_segment* segs_dev,
+                              const nif_linseg* lin_dev, int64_t n, const float* dfeats_dev,
+                              float* dfield_dev, void* stream);
+
+/* One fitting step of the field against a target deformation (FP32 handles
+ * of the composed encoding): the segments of rays_dev under the current
+ * deformation (poses_host and the field; the batch rule of
+ * nif_train_step_rays) are labelled along their rest segments under the
+ * target deformation (target_poses_host, no field; Sec. 2's ground truth),
+ * the task loss of Sec. 2.4 is taken on the network's outputs at the current
+ * rest segments, and its gradient goes through the MLP, the encoding and
+ * the field's inverse into the field: Adam (beta 0.9, 0.99; learning rate
+ * lr_field) on the displacements, after which a field whose Lipschitz bound
+ * passed 0.9 is scaled back onto it. With lr_grid or lr_mlp > 0 the network
+ * is trained on the same loss in the same step (jointly); with both 0 it is
+ * frozen. loss_host (nullable, blocks): the loss parts as nif_train_step
+ * gives them. NIF_ERR_STATE without a field or on other handles. */
+nif_status nif_field_step(nif_handle* h, const nif_pose* poses_host, int n_inst, const nif_ray* rays_dev,
+                          const int* inst_offsets_dev, int n_rays, int64_t n_segments,
+                          const nif_pose* target_poses_host, float lr_field, float lr_grid, float lr_mlp,
+                          double* loss_host, void* stream);
+
 /* Shadow rays for a frame loop (occlusion queries with NIF_SHADOW_ONLY):
  * for a primary ray that hit, origin o + D d, direction the normalised
  * light_dir_host, interval [eps, tmax]; for a miss an empty interval

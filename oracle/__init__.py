@@ -635,13 +635,15 @@ def reconstruct(cfg, pose, rays, seg: Segments, out, p0, p1, l_def, l_rest, flag
 # Gradient with respect to the deformation parameters (pose fitting)
 # ---------------------------------------------------------------------------
 
-def pose_gradient(cfg, tables, pose, p0, p1, dfeat):
+def pose_gradient(cfg, tables, pose, p0, p1, dfeat, field=None):
     """d/d(bend, twist, taper) of sum(dfeat * [psi(p0) (+) psi(p1)]) where the
     rest points are p = D^-1(x; pose) of fixed deformed points x.
 
     By the implicit function theorem, D(p(theta); theta) = x gives
     dp/dtheta = -J_D(p)^-1 dD/dtheta(p); the encoding's input gradient comes
-    from `encode_points_backward`.
+    from `encode_points_backward`. With a learned field (D = D_theta o (I+u))
+    the pose acts at q = p + u(p): dp/dtheta = -(I + du/dp)^-1
+    J_theta(q)^-1 dD_theta/dtheta(q).
     """
     concat = getattr(cfg, "encoding", "composed") == "concat"
     half = cfg.point_width if concat else dfeat.shape[1] // 2
@@ -649,8 +651,11 @@ def pose_gradient(cfg, tables, pose, p0, p1, dfeat):
     g = np.zeros(3)
     for p, df in ((p0, dfeat[:, :half]), (p1, dfeat[:, half:2 * half])):
         _, dp = back(cfg, tables, p, df)
-        J, Jp = jacobians(pose, p)
-        dpdth = -np.linalg.solve(J, Jp)            # [n, 3, 3]: d p_i / d theta_j
+        q = p if field is None else p + field_displacement(field, p)
+        J, Jp = jacobians(pose, q)
+        dpdth = -np.linalg.solve(J, Jp)            # [n, 3, 3]: d q_i / d theta_j
+        if field is not None:
+            dpdth = np.linalg.solve(np.eye(3)[None] + field_grad(field, p), dpdth)
         g += np.einsum("ni,nij->j", dp, dpdth)
     return g
 

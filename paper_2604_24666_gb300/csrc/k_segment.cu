@@ -30,7 +30,7 @@ constexpr float kBoxPad = 4e-6f;   // absolute dilation of refitted boxes
 // ---------------------------------------------------------------------------
 __global__ void k_refit_leaves(int N, int n_leaves, int n_nodes, int n_inst,
                                const uint32_t* __restrict__ leaf_lat,
-                               const float4* __restrict__ poses, float* __restrict__ corners,
+                               const float4* __restrict__ poses, FieldView f, float* __restrict__ corners,
                                float4* __restrict__ aabb) {
     int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)n_leaves * n_inst) return;
@@ -46,6 +46,10 @@ __global__ void k_refit_leaves(int N, int n_leaves, int n_nodes, int n_inst,
     for (int c = 0; c < 8; c++) {
         float3 x = make_float3((float)(i + (c & 1)) * invN, (float)(j + ((c >> 1) & 1)) * invN,
                                (float)(k + ((c >> 2) & 1)) * invN);
+        if (f.d && inst < f.n) {          // learned field: D = D_pose(x + u(x))
+            const float3 u = nif_field_eval(f, inst, x, nullptr);
+            x = make_float3(x.x + u.x, x.y + u.y, x.z + u.z);
+        }
         float3 y = nif_deform(x, pose);
         C[3 * c + 0] = y.x;
         C[3 * c + 1] = y.y;
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 32 / kTravWarps) k_seg_traver
 // ---------------------------------------------------------------------------
 // every lattice point of every instance deformed: [inst][(N+1)^3] (x, y, z, 0),
 // computed as k_refit_leaves computes the corners of the occupied voxels
-__global__ void k_lattice(int N, int n_inst, const float4* __restrict__ poses, float4* __restrict__ lat) {
+__global__ void k_lattice(int N, int n_inst, const float4* __restrict__ poses, FieldView f, float4* __restrict__ lat) {
     const int M = N + 1;
     const int64_t per = (int64_t)M * M * M;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -455,7 +459,12 @@ __global__ void k_lattice(int N, int n_inst, const float4* __restrict__ poses, f
     const int64_t p = gid - (int64_t)inst * per;
     const int i = (int)(p % M), j = (int)((p / M) % M), k = (int)(p / ((int64_t)M * M));
     const float invN = 1.0f / (float)N;
-    const float3 y = nif_deform(make_float3((float)i * invN, (float)j * invN, (float)k * invN), poses[inst]);
+    float3 x = make_float3((float)i * invN, (float)j * invN, (float)k * invN);
+    if (f.d && inst < f.n) {
+        const float3 u = nif_field_eval(f, inst, x, nullptr);
+        x = make_float3(x.x + u.x, x.y + u.y, x.z + u.z);
+    }
+    const float3 y = nif_deform(x, poses[inst]);
     lat[gid] = make_float4(y.x, y.y, y.z, 0.f);
 }
 
@@ -966,7 +975,7 @@ __global__ void k_clamp_count(const uint32_t* offsets, int n_rays, int64_t cap, 
 // Linearization
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_linearize(const nif_ray* __restrict__ rays, const int* __restrict__ inst_off,
-                                                   int n_inst, const float4* __restrict__ poses,
+                                                   int n_inst, const float4* __restrict__ poses, FieldView f,
                                                    const nif_segment* __restrict__ segs,
                                                    const uint32_t* __restrict__ n_dev, int64_t n_max,
                                                    nif_linseg* __restrict__ lin) {
@@ -983,6 +992,10 @@ __global__ void __launch_bounds__(256) k_linearize(const nif_ray* __restrict__ r
         float3 x1 = make_float3(a.x + sg.t1 * a.w, a.y + sg.t1 * b.x, a.z + sg.t1 * b.y);
         float3 p0 = nif_inverse(x0, pose);
         float3 p1 = nif_inverse(x1, pose);
+        if (f.d && inst < f.n) {          // then p + u(p) = q by Newton
+            p0 = nif_field_inverse(f, inst, p0);
+            p1 = nif_field_inverse(f, inst, p1);
+        }
         float dn = sqrtf(a.w * a.w + b.x * b.x + b.y * b.y);
         float dx = p1.x - p0.x, dy = p1.y - p0.y, dz = p1.z - p0.z;
         float4* L4 = reinterpret_cast<float4*>(lin + s);
@@ -1001,7 +1014,7 @@ nif_status nif_refit_run(nif_handle* h, int n_inst, cudaStream_t s) {
     if (h->n_leaves == 0) return NIF_OK;
     int64_t nl = (int64_t)h->n_leaves * n_inst;
     k_refit_leaves<<<nif_blocks(nl, 128), 128, 0, s>>>(h->N, h->n_leaves, h->n_nodes, n_inst, h->d_leaf_lat,
-                                                      h->d_pose, h->d_corners, h->d_aabb);
+                                                      h->d_pose, nif_field_view(h), h->d_corners, h->d_aabb);
     NIF_CK_LAUNCH(h);
     for (size_t l = 0; l < h->level_begin.size(); l++) {
         int64_t nn = (int64_t)h->level_count[l] * n_inst;
@@ -1086,7 +1099,8 @@ nif_status nif_seg_walk_run(nif_handle* h, const nif_ray* rays, const int* inst_
         NifProf prof_(h, "walk_lattice", s);
         const int64_t M = h->N + 1, per = M * M * M;
         if ((st = nif_grow(h, h->b_lattice, sizeof(float4) * (size_t)(per * n_inst))) != NIF_OK) return st;
-        k_lattice<<<nif_blocks(per * n_inst, 256), 256, 0, s>>>(h->N, n_inst, h->d_pose, (float4*)h->b_lattice.p);
+        k_lattice<<<nif_blocks(per * n_inst, 256), 256, 0, s>>>(h->N, n_inst, h->d_pose, nif_field_view(h),
+                                                               (float4*)h->b_lattice.p);
         NIF_CK_LAUNCH(h);
         if (!h->d_vox_leaf) {
             const size_t nv = (size_t)h->N * h->N * h->N;
@@ -1207,17 +1221,23 @@ nif_status nif_clamp_count_run(nif_handle* h, const uint32_t* offsets, int n_ray
     return NIF_OK;
 }
 
-nif_status nif_linearize_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
-                             const nif_segment* segs, const uint32_t* n_dev, int64_t n_max, nif_linseg* lin,
-                             cudaStream_t s) {
+nif_status nif_linearize_with_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
+                                  const float4* poses_dev, FieldView f, const nif_segment* segs,
+                                  const uint32_t* n_dev, int64_t n_max, nif_linseg* lin, cudaStream_t s) {
     NifProf prof_(h, "linearize", s);
     if (n_max <= 0) return NIF_OK;
     unsigned g = nif_blocks(n_max, 256);
     unsigned cap = (unsigned)h->num_sms * 8;
     if (g > cap) g = cap;
-    k_linearize<<<g, 256, 0, s>>>(rays, inst_off, n_inst, h->d_pose, segs, n_dev, n_max, lin);
+    k_linearize<<<g, 256, 0, s>>>(rays, inst_off, n_inst, poses_dev, f, segs, n_dev, n_max, lin);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
+}
+
+nif_status nif_linearize_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
+                             const nif_segment* segs, const uint32_t* n_dev, int64_t n_max, nif_linseg* lin,
+                             cudaStream_t s) {
+    return nif_linearize_with_run(h, rays, inst_off, n_inst, h->d_pose, nif_field_view(h), segs, n_dev, n_max, lin, s);
 }
 
 // Exclusive scan with caller-provided block-sum storage (at least

@@ -381,7 +381,7 @@ __device__ __forceinline__ int find_inst_r(const int* inst_off, int n_inst, int 
 
 __global__ void __launch_bounds__(128) k_reconstruct(const nif_ray* __restrict__ rays, const int* __restrict__ inst_off,
                                                      int n_inst, int n_rays, const float4* __restrict__ poses,
-                                                     const uint32_t* __restrict__ offsets,
+                                                     FieldView f, const uint32_t* __restrict__ offsets,
                                                      const nif_segment* __restrict__ segs,
                                                      const nif_linseg* __restrict__ lin,
                                                      const float* __restrict__ out, int64_t seg_cap, int N, int M,
@@ -416,13 +416,23 @@ __global__ void __launch_bounds__(128) k_reconstruct(const nif_ray* __restrict__
         float3 ph = make_float3(L.p0[0] + frac * (L.p1[0] - L.p0[0]), L.p0[1] + frac * (L.p1[1] - L.p0[1]),
                                 L.p0[2] + frac * (L.p1[2] - L.p0[2]));
         int inst = find_inst_r(inst_off, n_inst, r);
+        float3 nr = make_float3(z[2], z[3], z[4]);
+        if (f.d && inst < f.n) {
+            // learned field: J_D = J_pose(q) (I + du/dp), q = ph + u(ph), so
+            // J_D^-T n = J_pose(q)^-T (I + du/dp)^-T n
+            float3 g[3];
+            const float3 u = nif_field_eval(f, inst, ph, g);
+            nr = nif_solve3_t(make_float3(1.f + g[0].x, g[0].y, g[0].z), make_float3(g[1].x, 1.f + g[1].y, g[1].z),
+                              make_float3(g[2].x, g[2].y, 1.f + g[2].z), nr);
+            ph = make_float3(ph.x + u.x, ph.y + u.y, ph.z + u.z);
+        }
         float3 j0, j1, j2;
         nif_jacobian_cols(ph, poses[inst], j0, j1, j2);
         // J^-T n is proportional to n.x (j1 x j2) + n.y (j2 x j0) + n.z (j0 x j1), det J > 0
         float3 c0 = nif_cross(j1, j2), c1 = nif_cross(j2, j0), c2 = nif_cross(j0, j1);
-        float nx = z[2] * c0.x + z[3] * c1.x + z[4] * c2.x;
-        float ny = z[2] * c0.y + z[3] * c1.y + z[4] * c2.y;
-        float nz = z[2] * c0.z + z[3] * c1.z + z[4] * c2.z;
+        float nx = nr.x * c0.x + nr.y * c1.x + nr.z * c2.x;
+        float ny = nr.x * c0.y + nr.y * c1.y + nr.z * c2.y;
+        float nz = nr.x * c0.z + nr.y * c1.z + nr.z * c2.z;
         float nl = sqrtf(nx * nx + ny * ny + nz * nz);
         float il = nl > 1e-30f ? 1.0f / nl : 0.f;
         hit.n[0] = nx * il; hit.n[1] = ny * il; hit.n[2] = nz * il;
@@ -596,7 +606,8 @@ nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* in
                                cudaStream_t s) {
     NifProf prof_(h, "reconstruct", s);
     if (n_rays <= 0) return NIF_OK;
-    k_reconstruct<<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, h->d_pose, offsets, segs,
+    k_reconstruct<<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, h->d_pose,
+                                                          nif_field_view(h), offsets, segs,
                                                           lin, out, seg_cap, h->N, h->cfg.n_materials, h->cfg.flags,
                                                           hits, flags);
     NIF_CK_LAUNCH(h);

@@ -525,7 +525,7 @@ extern "C" void nif_destroy(nif_handle* h) {
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
                                &h->b_acts, &h->b_dout, &h->b_dx, &h->b_labels, &h->b_scan, &h->b_rays,
                                &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys, &h->b_dup, &h->b_pts,
-                               &h->b_lattice, &h->b_sort, &h->alt_counts, &h->alt_offsets, &h->alt_temp, &h->alt_segs,
+                               &h->b_lattice, &h->b_sort, &h->b_lin_t, &h->alt_counts, &h->alt_offsets, &h->alt_temp, &h->alt_segs,
                                &h->alt_scan, &h->alt_rays, &h->alt_inst, &h->alt_lin, &h->alt_labels,
                                &h->alt_dup, &h->alt_pts, &h->alt_sort};
     for (auto* b : bufs)
@@ -541,6 +541,8 @@ extern "C" void nif_destroy(nif_handle* h) {
     for (auto e : h->prof_pool) cudaEventDestroy(e);
     h->n_plans = 0;
     nif_free_retired(h);
+    nif_field_free(h);
+    if (h->d_pose_t) cudaFree(h->d_pose_t);
     delete h;
 }
 
@@ -761,6 +763,22 @@ extern "C" nif_status nif_get_voxels(nif_handle* h, unsigned char* occ, int64_t*
     return NIF_OK;
 }
 
+// target poses of nif_field_step into their own device array
+static nif_status upload_target_poses(nif_handle* h, const nif_pose* poses, int n_inst, cudaStream_t s) {
+    if (n_inst > h->inst_cap_t) {
+        NIF_CK(h, cudaDeviceSynchronize());
+        if (h->d_pose_t) cudaFree(h->d_pose_t);
+        h->d_pose_t = nullptr;
+        NIF_CK(h, cudaMalloc(&h->d_pose_t, sizeof(float4) * (size_t)n_inst));
+        h->inst_cap_t = n_inst;
+    }
+    std::vector<float4> p(n_inst);
+    for (int i = 0; i < n_inst; i++) p[i] = make_float4(NIF_KBEND * poses[i].bend, poses[i].twist, poses[i].taper, 0.f);
+    NIF_CK(h, cudaMemcpyAsync(h->d_pose_t, p.data(), sizeof(float4) * n_inst, cudaMemcpyHostToDevice, s));
+    NIF_CK(h, cudaStreamSynchronize(s));     // the staging vector dies with this scope
+    return NIF_OK;
+}
+
 static nif_status seg_single_pass(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
                                   uint32_t* offs, nif_segment* segs, int64_t seg_cap, bool segs_grow,
                                   int64_t* total_out, cudaStream_t s);
@@ -781,6 +799,8 @@ nif_status nif_check_status(nif_handle* h, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 nif_status nif_check_inst(nif_handle* h, const nif_pose* poses, int n_inst, const int* inst_off, int n_rays) {
     if (!poses || n_inst < 1) return nif_fail(h, NIF_ERR_ARG, "poses");
+    if (h->field_G > 0 && n_inst > h->field_n)
+        return nif_fail(h, NIF_ERR_ARG, "more instances than the handle's field has (nif_set_field)");
     if (n_inst > 1 && !inst_off) return nif_fail(h, NIF_ERR_ARG, "inst_offsets required for n_inst > 1");
     if (n_rays < 0) return nif_fail(h, NIF_ERR_ARG, "n_rays");
     for (int i = 0; i < n_inst; i++)
@@ -1347,6 +1367,80 @@ extern "C" nif_status nif_pose_step(nif_handle* h, const nif_pose* poses, int n_
         NIF_CK(h, cudaMemcpy(acc, h->d_lossacc, sizeof(acc), cudaMemcpyDeviceToHost));
         loss_host[0] = acc[8];
         for (int i = 0; i < 5; i++) loss_host[1 + i] = acc[9 + i];
+    }
+    return NIF_OK;
+}
+
+// Fitting the learned deformation field (the paper's future work, Sec. 4;
+// the objective is our reading): the segments of the rays under the current
+// deformation (poses and field), each segment labelled along its rest segment
+// under the target deformation, the task loss of Sec. 2.4 on the network's
+// predictions at the current rest segments, and its gradient carried through
+// the encoding and the field's inverse into the field (Adam, then the
+// Lipschitz projection); with a learning rate for the network, the same
+// gradient also trains it (joint).
+extern "C" nif_status nif_field_step(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                     const int* inst_off, int n_rays, int64_t n_segments,
+                                     const nif_pose* target_poses, float lr_field, float lr_grid, float lr_mlp,
+                                     double* loss_host, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    if ((st = nif_check_inst(h, target_poses, n_inst, inst_off, n_rays)) != NIF_OK) return st;
+    if (h->field_G == 0) return nif_fail(h, NIF_ERR_STATE, "the handle has no field (nif_set_field)");
+    if (h->cfg.precision != NIF_FP32 || (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) || h->concat)
+        return nif_fail(h, NIF_ERR_STATE, "field fitting runs on FP32 handles of the composed encoding");
+    if (n_segments < 1 || !rays || !(lr_field >= 0.f) || !(lr_grid >= 0.f) || !(lr_mlp >= 0.f))
+        return nif_fail(h, NIF_ERR_ARG, "n_segments / rays / learning rates");
+    const bool joint = lr_grid > 0.f || lr_mlp > 0.f;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, n_segments, false, nullptr, s)) != NIF_OK)
+        return st;
+    uint32_t* offs = (uint32_t*)h->b_offsets.p;
+    const uint32_t* n_dev = offs + n_rays + 1;
+    const int64_t n = n_segments;
+    if ((st = nif_grow(h, h->b_lin, sizeof(nif_linseg) * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_lin_t, sizeof(nif_linseg) * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_labels, sizeof(nif_label) * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_feat, sizeof(float) * (size_t)h->in_dim * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_dx, sizeof(float) * (size_t)h->in_dim * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_feat2, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_acts, sizeof(float) * (size_t)n * h->W * h->H)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_temp, sizeof(float) * 6 * (size_t)n)) != NIF_OK) return st;
+    nif_segment* segs = (nif_segment*)h->b_segs.p;
+    nif_linseg* lin = (nif_linseg*)h->b_lin.p;
+    nif_linseg* lin_t = (nif_linseg*)h->b_lin_t.p;
+    nif_label* lab = (nif_label*)h->b_labels.p;
+    float* feat = (float*)h->b_feat.p;
+    float* dx = (float*)h->b_dx.p;
+    float* out = (float*)h->b_out.p;
+    float* dout = (float*)h->b_feat2.p;
+    float* acts = (float*)h->b_acts.p;
+    float* dp = (float*)h->b_temp.p;
+    if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, n, lin, s)) != NIF_OK) return st;
+    if ((st = upload_target_poses(h, target_poses, n_inst, s)) != NIF_OK) return st;
+    if ((st = nif_linearize_with_run(h, rays, inst_off, n_inst, h->d_pose_t, FieldView{}, segs, n_dev, n, lin_t, s)) !=
+        NIF_OK)
+        return st;
+    if ((st = nif_labels_run(h, segs, lin_t, n_dev, n, lab, s)) != NIF_OK) return st;
+    if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s)) != NIF_OK) return st;
+    if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
+    if ((st = nif_loss_run(h, out, lab, lin_t, n_dev, n, dout, s, joint)) != NIF_OK) return st;
+    if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s, joint)) != NIF_OK) return st;
+    if (joint && (st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s)) != NIF_OK)
+        return st;
+    if ((st = nif_encode_segments_dp_run(h, lin, n_dev, n, dx, dp, s)) != NIF_OK) return st;
+    if ((st = nif_field_grad_run(h, segs, lin, dp, n_dev, n, inst_off, n_inst, h->d_field_g, s)) != NIF_OK) return st;
+    if ((st = nif_field_adam_run(h, lr_field, s)) != NIF_OK) return st;
+    if (joint && (st = nif_adam_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
+    if (loss_host) {
+        double acc[16];
+        NIF_CK(h, cudaStreamSynchronize(s));
+        NIF_CK(h, cudaMemcpy(acc, h->d_lossacc, sizeof(acc), cudaMemcpyDeviceToHost));
+        loss_host[0] = acc[8];
+        for (int i = 0; i < 5; i++) loss_host[1 + i] = acc[9 + i];
+        return latched_status(h);
     }
     return NIF_OK;
 }

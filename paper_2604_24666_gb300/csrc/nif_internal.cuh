@@ -28,6 +28,15 @@ struct GridInfo {
     int res[NIF_MAX_LEVELS];  // N_l
 };
 
+// Learned deformation field of the instances (see the device math below).
+#define NIF_FIELD_MAX_G 33
+#define NIF_FIELD_MAX_LIPSCHITZ 0.9f
+struct FieldView {
+    const float4* d = nullptr;   // [n][G^3] (delta, 0); nullptr: no field
+    int G = 0;
+    int n = 0;                   // instances that have a field
+};
+
 // Octree over the occupied voxels (Morton order). Global node numbering:
 // leaves [0, n_leaves), then each internal level in turn; internal node i
 // (global index >= n_leaves) has children [child_begin, child_begin + count).
@@ -85,6 +94,20 @@ struct nif_handle {
     float4* d_aabb = nullptr;     // [inst][n_nodes][2] (lo, hi)
     float4* d_pose = nullptr;     // [inst] (kappa, twist, taper, 0)
 
+    // learned deformation field (nif_set_field): per instance G^3 rest-space
+    // displacements, [field_n][G^3] (delta, 0); its Adam moments in the same
+    // layout, its gradient [field_n][G^3][3], a device word for its Lipschitz
+    // bound; target poses of nif_field_step
+    float4* d_field = nullptr;
+    float4* d_field_m = nullptr;
+    float4* d_field_v = nullptr;
+    float* d_field_g = nullptr;
+    float* d_field_lip = nullptr;
+    int field_G = 0, field_n = 0;
+    long field_step = 0;
+    float4* d_pose_t = nullptr;         // [inst_cap_t] (kappa, twist, taper, 0) of target poses
+    int inst_cap_t = 0;
+
     // parameters: one FP32 buffer [tables | layer 0 .. layer H | s(8)]
     size_t n_params = 0, off_tables = 0, off_s = 0;
     size_t off_layer[NIF_MAX_LAYERS + 1] = {0};
@@ -131,7 +154,7 @@ struct nif_handle {
     // grown scratch buffers (query / train)
     struct Buf { void* p = nullptr; size_t bytes = 0; };
     Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
-        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts, b_lattice, b_sort;
+        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts, b_lattice, b_sort, b_lin_t;
     // the distinct end points of the last segment encoding (in b_dup, b_pts,
     // b_sort; sorted: in rest-space order), which the backward of the same
     // segments in a training step takes instead of listing them again
@@ -251,6 +274,19 @@ nif_status nif_seg_emit_run(nif_handle* h, const nif_ray* rays, const int* inst_
 nif_status nif_linearize_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
                              const nif_segment* segs, const uint32_t* n_segs_dev, int64_t n_max,
                              nif_linseg* lin, cudaStream_t s);
+// linearization by explicit device poses and field (no field: f.d == nullptr)
+nif_status nif_linearize_with_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
+                                  const float4* poses_dev, FieldView f, const nif_segment* segs,
+                                  const uint32_t* n_segs_dev, int64_t n_max, nif_linseg* lin, cudaStream_t s);
+// gradient of sum(dL/dp . p) with respect to the field: dfield [field_n][G^3][3] (accumulated)
+nif_status nif_field_grad_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const float* dp,
+                              const uint32_t* n_dev, int64_t n, const int* inst_off, int n_inst, float* dfield,
+                              cudaStream_t s);
+// Adam on the field from h->d_field_g (then cleared), then the field scaled
+// back to the Lipschitz bound NIF_FIELD_MAX_LIPSCHITZ where a step passed it
+nif_status nif_field_adam_run(nif_handle* h, float lr, cudaStream_t s);
+// frees the field's buffers (nif_destroy)
+void nif_field_free(nif_handle* h);
 nif_status nif_encode_points_run(nif_handle* h, const float* pts, int64_t n, void* feats,
                                  int out_dtype, int32_t* rows, cudaStream_t s);
 // reuse_points: the list of distinct end points that nif_encode_points_prepare
@@ -453,13 +489,14 @@ __device__ __forceinline__ void nif_param_jacobian_cols(float3 x, float4 pose, f
 // NIF_FIELD_MAX_LIPSCHITZ or below, so the root is unique and
 // |p - p*| <= |p + u(p) - q| / (1 - bound).
 // ---------------------------------------------------------------------------
-#define NIF_FIELD_MAX_G 33
-#define NIF_FIELD_MAX_LIPSCHITZ 0.5f
-struct FieldView {
-    const float4* d = nullptr;   // [n][G^3] (delta, 0); nullptr: no field
-    int G = 0;
-    int n = 0;                   // instances that have a field
-};
+
+inline FieldView nif_field_view(const nif_handle* h) {
+    FieldView f;
+    f.d = h->field_G > 0 ? h->d_field : nullptr;
+    f.G = h->field_G;
+    f.n = h->field_n;
+    return f;
+}
 
 __device__ __forceinline__ void nif_field_cell(int G, float3 p, int& i, int& j, int& k, float3& t) {
     const float s = (float)(G - 1);
@@ -526,12 +563,12 @@ __device__ __forceinline__ float3 nif_solve3_t(float3 c0, float3 c1, float3 c2, 
 }
 
 // p with p + u(p) = q: Newton from one fixed-point step, until the FP32
-// residual stops shrinking (at most 8 iterations)
+// residual stops shrinking (at most 12 iterations)
 __device__ __forceinline__ float3 nif_field_inverse(const FieldView& f, int inst, float3 q) {
     float3 u = nif_field_eval(f, inst, q, nullptr);
     float3 p = make_float3(q.x - u.x, q.y - u.y, q.z - u.z);
     float prev = 3.0e38f;
-    for (int it = 0; it < 8; it++) {
+    for (int it = 0; it < 12; it++) {
         float3 g[3];
         u = nif_field_eval(f, inst, p, g);
         const float3 F = make_float3(p.x + u.x - q.x, p.y + u.y - q.y, p.z + u.z - q.z);

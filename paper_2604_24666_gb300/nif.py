@@ -132,6 +132,12 @@ def lib() -> ctypes.CDLL:
             "nif_query_plan_destroy": ([_vp], None),
             "nif_sync_status": ([_vp, _vp], ctypes.c_int),
             "nif_set_knob": ([_vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+            "nif_set_field": ([_vp, ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
+            "nif_get_field": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _vp, ctypes.c_size_t],
+                              ctypes.c_int),
+            "nif_field_gradient": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _i64, _vp, _vp, _vp], ctypes.c_int),
+            "nif_field_step": ([_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _i64, _vp, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, _vp, _vp], ctypes.c_int),
             "nif_checkpoint_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
             "nif_checkpoint_save": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
             "nif_checkpoint_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
@@ -539,6 +545,51 @@ class QueryPlan:
 
 def nif_sync_status(h, stream=None):
     _check(h, lib().nif_sync_status(h, _stream(stream)))
+
+
+def nif_set_field(h, delta):
+    """Learned deformation field: delta [n_inst, G, G, G, 3] float32 (index
+    [i][c][b][a] of node (a, b, c)/(G-1)); None or an empty array removes it."""
+    if delta is None or np.size(delta) == 0:
+        _check(h, lib().nif_set_field(h, 0, 0, None))
+        return
+    d = np.ascontiguousarray(delta, np.float32)
+    assert d.ndim == 5 and d.shape[1] == d.shape[2] == d.shape[3] and d.shape[4] == 3
+    _check(h, lib().nif_set_field(h, d.shape[0], d.shape[1], _ptr(d)))
+
+
+def nif_get_field(h):
+    """The field [n_inst, G, G, G, 3] float32 (None without one)."""
+    n, G = ctypes.c_int(0), ctypes.c_int(0)
+    _check(h, lib().nif_get_field(h, ctypes.byref(n), ctypes.byref(G), None, 0))
+    if n.value == 0:
+        return None
+    d = np.zeros((n.value, G.value, G.value, G.value, 3), np.float32)
+    _check(h, lib().nif_get_field(h, None, None, _ptr(d), d.nbytes))
+    return d
+
+
+def nif_field_gradient(h, poses, segs, lin, dfeats, inst_offsets=None, stream=None):
+    """d/d(field) [n_inst, G, G, G, 3] of sum(dfeats * features) for fixed deformed end points."""
+    p, n_inst = _poses(poses)
+    n_f, G = ctypes.c_int(0), ctypes.c_int(0)
+    _check(h, lib().nif_get_field(h, ctypes.byref(n_f), ctypes.byref(G), None, 0))
+    out = torch.zeros((max(n_f.value, 1), G.value, G.value, G.value, 3), dtype=torch.float32, device=lin.device)
+    _check(h, lib().nif_field_gradient(h, p, n_inst, _ptr(inst_offsets), _ptr(segs), _ptr(lin), lin.shape[0],
+                                       _ptr(dfeats), _ptr(out), _stream(stream)))
+    return out
+
+
+def nif_field_step(h, poses, rays, n_segments, target_poses, inst_offsets=None, lr_field=1e-3, lr_grid=0.0,
+                   lr_mlp=0.0, want_loss=True, stream=None):
+    """One fitting step of the field towards the target poses' deformation; returns the loss parts."""
+    p, n_inst = _poses(poses)
+    t, n_t = _poses(target_poses)
+    assert n_t == n_inst
+    loss = np.zeros(6, np.float64) if want_loss else None
+    _check(h, lib().nif_field_step(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0], n_segments, t,
+                                   lr_field, lr_grid, lr_mlp, _ptr(loss), _stream(stream)))
+    return loss
 
 
 def nif_set_knob(h, knob, value):
