@@ -631,6 +631,33 @@ nif_status nif_segments_noalloc(nif_handle* h, const nif_pose* poses_host, int n
  * handles, all threads). */
 unsigned long long nif_kernel_launches(void);
 
+/* Measured ceilings of the memory patterns that bound the encoding kernels
+ * (the paper has no counterpart): `kind`
+ *   NIF_PROBE_RED8   random red.global.add.v2.f32 (8-byte FP32 reductions,
+ *                    the encoding backward's per-corner update),
+ *   NIF_PROBE_RED16  random red.global.add.v4.f32 into two adjacent rows
+ *                    (its paired x-edge corners),
+ *   NIF_PROBE_LOAD8  random 8-byte row loads (FP32 table rows, the forward),
+ *   NIF_PROBE_LOAD4  random 4-byte row loads (FP16 table rows),
+ * over buf_dev (caller-owned, `bytes` = a power-of-two number >= 1024 of
+ * rows, 16-byte aligned; its contents are changed by the reductions), which
+ * stays in L2 when it fits: one warm-up launch, then 5 launches of
+ * 8 x num_SMs blocks of 256 threads, each thread `iters` x 8 independent
+ * accesses, timed with CUDA events on `stream`. *gbs_host receives the
+ * payload bytes per second / 1e9, *ms_host the mean launch time. Blocks the
+ * host. */
+#define NIF_PROBE_RED8 1
+#define NIF_PROBE_RED16 2
+#define NIF_PROBE_LOAD8 3
+#define NIF_PROBE_LOAD4 4
+nif_status nif_probe_memory(nif_handle* h, int kind, void* buf_dev, size_t bytes, int iters, double* gbs_host,
+                            double* ms_host, void* stream);
+/* Distinct end points listed by the handle's last segment encoding (the
+ * forward writes a repeated entry point's features from its previous exit
+ * point's, and the backward walks the distinct points only) and the number
+ * of segments it encoded. Blocks the host; NIF_ERR_STATE before any. */
+nif_status nif_encoder_points(nif_handle* h, int64_t* n_points_host, int64_t* n_segments_host);
+
 /* Per-stage timing: with profiling on, every stage the handle runs is
  * bracketed by two CUDA events on its stream (a few microseconds of
  * overhead per stage). nif_profile(h, 1) clears the record and turns it on,

@@ -804,7 +804,7 @@ nif_status spatial_order(nif_handle* h, const nif_linseg* lin, const uint32_t* p
 // encoder 1.35x faster). Recorded in h->enc_points.
 static nif_status point_list(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
                              size_t table_bytes, cudaStream_t s) {
-    const uint32_t *pts, *n_pts, *dupf;
+    const uint32_t *pts = nullptr, *n_pts = nullptr, *dupf = nullptr;
     nif_status st = distinct_points(h, lin, n_dev, n_max, &pts, &n_pts, &dupf, s);
     if (st != NIF_OK) return st;
     const bool sorted = (size_t)h->T * h->L * h->Fd * table_bytes > ((size_t)4 << 20);

@@ -26,6 +26,7 @@ NIF_FLAG_FIXED_TASK_WEIGHTS, NIF_FLAG_SIGMOID_DISTANCE, NIF_FLAG_MIXED_TRAINING 
 NIF_FLAG_CONCAT_ENCODING = 8
 NIF_FLAG_BILINEAR_FACES = 16
 NIF_KNOB_WAIT_NS, NIF_KNOB_SEG_SCRATCH = 1, 2
+NIF_PROBE_RED8, NIF_PROBE_RED16, NIF_PROBE_LOAD8, NIF_PROBE_LOAD4 = 1, 2, 3, 4
 
 _STATUS = {0: "NIF_OK", -1: "NIF_ERR_ARG", -2: "NIF_ERR_CUDA", -3: "NIF_ERR_OOM", -4: "NIF_ERR_CAPACITY",
            -5: "NIF_ERR_TIMEOUT", -6: "NIF_ERR_NAN", -7: "NIF_ERR_STATE"}
@@ -132,6 +133,9 @@ def lib() -> ctypes.CDLL:
             "nif_query_plan_destroy": ([_vp], None),
             "nif_sync_status": ([_vp, _vp], ctypes.c_int),
             "nif_set_knob": ([_vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+            "nif_probe_memory": ([_vp, ctypes.c_int, _vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
+            "nif_encoder_points": ([_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)], ctypes.c_int),
             "nif_set_field": ([_vp, ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
             "nif_get_field": ([_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _vp, ctypes.c_size_t],
                               ctypes.c_int),
@@ -590,6 +594,21 @@ def nif_field_step(h, poses, rays, n_segments, target_poses, inst_offsets=None, 
     _check(h, lib().nif_field_step(h, p, n_inst, _ptr(rays), _ptr(inst_offsets), rays.shape[0], n_segments, t,
                                    lr_field, lr_grid, lr_mlp, _ptr(loss), _stream(stream)))
     return loss
+
+
+def nif_probe_memory(h, kind, buf, iters=64, stream=None):
+    """(GB/s of payload, ms per launch) of one memory pattern over the device buffer buf."""
+    g, ms = ctypes.c_double(0), ctypes.c_double(0)
+    _check(h, lib().nif_probe_memory(h, kind, _ptr(buf), buf.numel() * buf.element_size(), iters, ctypes.byref(g),
+                                     ctypes.byref(ms), _stream(stream)))
+    return g.value, ms.value
+
+
+def nif_encoder_points(h):
+    """(distinct end points, segments) of the handle's last segment encoding."""
+    a, b = _i64(0), _i64(0)
+    _check(h, lib().nif_encoder_points(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def nif_set_knob(h, knob, value):

@@ -178,32 +178,44 @@ def test_field_gradient_matches_oracle(nif, torus):
     h.close()
 
 
-def test_pose_gradient_under_a_field_matches_oracle(nif, torus):
-    net = S.NetConfig(levels=8, log2_table=12)
-    N = net.voxel_res
+@pytest.mark.parametrize("bands", [0, 4])
+def test_pose_gradient_under_a_field_matches_oracle(nif, torus, bands):
+    """d/d(bend, twist, taper) with a field under the pose, on identical rest
+    points (generated, cells certain) and feature gradients. Bound: each end
+    point's dL/dp bound (tests/bounds.py) carried through |dp/dtheta| =
+    |(I + du/dp)^-1 J_pose(q)^-1 dD_pose/dtheta(q)|, plus 1e-5 of the sum of
+    the absolute terms for the FP32 Jacobians and solves. Without the
+    positional bands the bound is rounding only (about 1e-3 of the result);
+    with them it carries the sincosf allowance of every sin/cos cell."""
+    net = S.NetConfig(levels=8, log2_table=12, pe_bands=bands)
     f = _field(4, 431, lip=0.35)
     f64 = f.astype(np.float64)
     pose = np.array([[0.5, -0.9, 0.4]], np.float32)
-    r = S.sphere_rays(900, seed=432)
-    occ, _, _ = O.voxelize(N, torus)
-    seg = O.segments(N, occ, pose[0], r, field=f64)
-    rays_np = r[seg.margin > SEG_MARGIN]
     h = nif.Nif(net, torus)
     tables = random_tables(net, 433, scale=0.5)
     h.set_params(tables, S.init_params(net)[1])
     nif.nif_set_field(h.h, f[None])
-    rays = torch.from_numpy(rays_np).to(_dev())
-    offs, segs = nif.nif_segments(h.h, pose, rays)
-    lin = nif.nif_linearize(h.h, pose, rays, segs)
-    n = segs.shape[0]
+    lin, _ = S.chained_segments(3000, seed=435, voxel_res=16, gap=0.2, margin=0.0)
+    ok = B.certain_cells(net, lin[:, 0:3]) & B.certain_cells(net, lin[:, 3:6])
+    lin = lin[ok][:1500]
+    n = len(lin)
+    segs = np.zeros((n, 4), np.int32)                # one instance
     df = np.random.default_rng(434).normal(size=(n, net.in_dim)).astype(np.float32)
-    dposes = nif.nif_pose_gradient(h.h, pose, segs, lin, torch.from_numpy(df).to(_dev()))
-    torch.cuda.synchronize()
-    seg = O.segments(N, occ, pose[0], rays_np, field=f64)
-    assert len(seg) == n
-    p0, p1, _, _ = O.linearize(pose[0], rays_np, seg, field=f64)
+    dposes = nif.nif_pose_gradient(h.h, pose, torch.from_numpy(segs).to(_dev()), torch.from_numpy(lin).to(_dev()),
+                                   torch.from_numpy(df).to(_dev()))
+    got = dposes.cpu().numpy()[0]
+    p0, p1 = lin[:, 0:3].astype(np.float64), lin[:, 3:6].astype(np.float64)
     ref = O.pose_gradient(net, tables, pose[0], p0, p1, df.astype(np.float64), field=f64)
-    np.testing.assert_allclose(dposes.cpu().numpy()[0], ref, rtol=5e-3, atol=5e-3 * np.abs(ref).max())
+    half = net.in_dim // 2
+    bound = np.zeros(3)
+    for p, d in ((p0, df[:, :half].astype(np.float64)), (p1, df[:, half:].astype(np.float64))):
+        _, dp = O.encode_points_backward(net, tables, p, d)
+        q = p + O.field_displacement(f64, p)
+        J, Jp = O.jacobians(pose[0], q)
+        A = -np.linalg.solve(np.eye(3)[None] + O.field_grad(f64, p), np.linalg.solve(J, Jp))   # dp/dtheta
+        bd = B.point_grad_bound(net, tables, p, d)
+        bound += np.einsum("na,naj->j", bd, np.abs(A)) + 1e-5 * np.einsum("na,naj->j", np.abs(dp), np.abs(A))
+    assert np.all(np.abs(got - ref) <= bound), (got, ref, bound)
     h.close()
 
 
