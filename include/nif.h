@@ -394,7 +394,13 @@ nif_status nif_reconstruct(nif_handle* h, const nif_pose* poses_host, int n_inst
  * -> MLP (cfg.precision; Sec. 2, Fig. 2d) -> reconstruction along the
  * segmented ray (Sec. 2.2), for n_inst deformed instances of the handle's
  * shape. Rays and hits are device buffers of n_rays entries.
- * Does not block the host; scratch grows on demand (growing synchronises). */
+ * Does not block the host: every count stays on the device. The segment
+ * capacity is 1.5 x the segments per ray of the last earlier query whose
+ * total has already come back (read without waiting), or NIF_KNOB_QUERY_SEGS
+ * (default 8) per ray before the first; growing scratch synchronises. When a
+ * query's segments exceed its capacity, the rays whose segment lists fit are
+ * answered, the others report no hit, and NIF_ERR_CAPACITY is latched in the
+ * status word (nif_sync_status); the next query sizes for the larger count. */
 nif_status nif_query(nif_handle* h, const nif_pose* poses_host, int n_inst,
                      const nif_ray* rays_dev, const int* inst_offsets_dev, int n_rays,
                      nif_hit* hits_dev, unsigned flags, void* stream);
@@ -594,9 +600,13 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   are put in ray order (default 1); below 1 the scratch overflows sooner
  *   and the device-gated second traversal writes the rows instead. Results
  *   do not depend on it.
+ * NIF_KNOB_QUERY_SEGS: segments per ray, in (0, 4096], that nif_query sizes
+ *   its capacity for until a query's total has come back (default 8); setting
+ *   it forgets the totals of earlier queries.
  * NIF_ERR_ARG for an unknown knob or a value out of range. */
 #define NIF_KNOB_WAIT_NS 1
 #define NIF_KNOB_SEG_SCRATCH 2
+#define NIF_KNOB_QUERY_SEGS 3
 nif_status nif_set_knob(nif_handle* h, int knob, double value);
 
 /* Allocation-free variant of nif_segments (the paper has no counterpart:

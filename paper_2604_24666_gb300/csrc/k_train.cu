@@ -384,12 +384,16 @@ __global__ void __launch_bounds__(128) k_reconstruct(const nif_ray* __restrict__
                                                      FieldView f, const uint32_t* __restrict__ offsets,
                                                      const nif_segment* __restrict__ segs,
                                                      const nif_linseg* __restrict__ lin,
-                                                     const float* __restrict__ out, int64_t seg_cap, int N, int M,
+                                                     const float* __restrict__ out, int64_t seg_cap,
+                                                     const uint32_t* __restrict__ n_valid, int N, int M,
                                                      unsigned cfg_flags, nif_hit* __restrict__ hits, unsigned flags) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
     int64_t a = offsets[r], b = offsets[r + 1];
     if (b > seg_cap) b = seg_cap;
+    // a ray whose segments lie past the processed count (a query whose
+    // segments exceeded its capacity) is reported without a hit
+    if (n_valid && b > (int64_t)*n_valid) b = a;
     nif_hit hit;
     hit.D = __int_as_float(0x7f800000);
     hit.n[0] = hit.n[1] = hit.n[2] = 0.f;
@@ -603,12 +607,13 @@ nif_status nif_adam_scaled_run(nif_handle* h, float lr_grid, float lr_mlp, cudaS
 nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst, int n_rays,
                                const uint32_t* offsets, const nif_segment* segs, int64_t seg_cap,
                                const nif_linseg* lin, const float* out, nif_hit* hits, unsigned flags,
-                               cudaStream_t s) {
+                               cudaStream_t s, const uint32_t* n_valid) {
     NifProf prof_(h, "reconstruct", s);
     if (n_rays <= 0) return NIF_OK;
     k_reconstruct<<<nif_blocks(n_rays, 128), 128, 0, s>>>(rays, inst_off, n_inst, n_rays, h->d_pose,
                                                           nif_field_view(h), offsets, segs,
-                                                          lin, out, seg_cap, h->N, h->cfg.n_materials, h->cfg.flags,
+                                                          lin, out, seg_cap, n_valid, h->N, h->cfg.n_materials,
+                                                          h->cfg.flags,
                                                           hits, flags);
     NIF_CK_LAUNCH(h);
     return NIF_OK;

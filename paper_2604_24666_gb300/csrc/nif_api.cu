@@ -264,11 +264,22 @@ nif_status nif_upload_poses(nif_handle* h, const nif_pose* poses, int n_inst, cu
         NIF_CK_LAUNCH(h);
         return NIF_OK;
     }
-    std::vector<float4> p(n_inst);
-    for (int i = 0; i < n_inst; i++) p[i] = make_float4(NIF_KBEND * poses[i].bend, poses[i].twist, poses[i].taper, 0.f);
-    NIF_CK(h, cudaMemcpyAsync(h->d_pose, p.data(), sizeof(float4) * n_inst, cudaMemcpyHostToDevice, s));
-    // the staging vector dies with this scope: make the copy complete first
-    NIF_CK(h, cudaStreamSynchronize(s));
+    // larger batches go through a pinned staging buffer; it is rewritten only
+    // once the previous copy from it has completed (an event, not a stream sync)
+    if (h->pose_pending) NIF_CK(h, cudaEventSynchronize(h->ev_pose));
+    h->pose_pending = false;
+    if (n_inst > h->pose_pinned_cap) {
+        if (h->h_pose_pinned) cudaFreeHost(h->h_pose_pinned);
+        h->h_pose_pinned = nullptr;
+        h->pose_pinned_cap = 0;
+        NIF_CK(h, cudaMallocHost(&h->h_pose_pinned, sizeof(float4) * (size_t)n_inst));
+        h->pose_pinned_cap = n_inst;
+    }
+    for (int i = 0; i < n_inst; i++)
+        h->h_pose_pinned[i] = make_float4(NIF_KBEND * poses[i].bend, poses[i].twist, poses[i].taper, 0.f);
+    NIF_CK(h, cudaMemcpyAsync(h->d_pose, h->h_pose_pinned, sizeof(float4) * n_inst, cudaMemcpyHostToDevice, s));
+    NIF_CK(h, cudaEventRecord(h->ev_pose, s));
+    h->pose_pending = true;
     return NIF_OK;
 }
 
@@ -464,6 +475,9 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
     CKC(cudaEventCreateWithFlags(&h->ev_step, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&h->ev_qtotal, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&h->ev_pose, cudaEventDisableTiming));
+    CKC(cudaMallocHost(&h->h_qtotal, sizeof(uint32_t) * 2));
 
     st = nif_voxelize_run(h);
     if (st != NIF_OK) return fail(st);
@@ -531,6 +545,11 @@ extern "C" void nif_destroy(nif_handle* h) {
     for (auto* b : bufs)
         if (b->p) cudaFree(b->p);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    if (h->h_qtotal) cudaFreeHost(h->h_qtotal);
+    if (h->h_pose_pinned) cudaFreeHost(h->h_pose_pinned);
+    if (h->d_chunk_counts) cudaFree(h->d_chunk_counts);
+    if (h->ev_qtotal) cudaEventDestroy(h->ev_qtotal);
+    if (h->ev_pose) cudaEventDestroy(h->ev_pose);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->aux) cudaStreamDestroy(h->aux);
@@ -1084,7 +1103,7 @@ static nif_status seg_single_pass(nif_handle* h, const nif_ray* rays, const int*
 // pointer of the clamped total (<= cap)
 static nif_status segment_into_scratch(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
                                        const int* inst_off, int n_rays, int64_t cap, bool host_total,
-                                       int64_t* total_host, cudaStream_t s) {
+                                       int64_t* total_host, cudaStream_t s, bool latch = false) {
     nif_status st;
     if ((st = nif_upload_poses(h, poses, n_inst, s)) != NIF_OK) return st;
     if ((st = nif_refit_run(h, n_inst, s)) != NIF_OK) return st;
@@ -1123,8 +1142,9 @@ static nif_status segment_into_scratch(nif_handle* h, const nif_pose* poses, int
             NIF_OK)
             return st;
         // only complete rows: the row that crosses `cap` holds an arbitrary
-        // subset of its ray's segments
-        return nif_clamp_count_run(h, offs, n_rays, cap, offs + n_rays + 1, false, s, true);
+        // subset of its ray's segments (latch: that is an error, not the end
+        // of a training batch)
+        return nif_clamp_count_run(h, offs, n_rays, cap, offs + n_rays + 1, latch, s, true);
     }
     // clamped count lives right after the offsets
     return nif_clamp_count_run(h, offs, n_rays, cap, offs + n_rays + 1, host_total, s);
@@ -1138,45 +1158,70 @@ extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst
     if (n_rays == 0) return NIF_OK;
     if (!rays || !hits) return nif_fail(h, NIF_ERR_ARG, "rays / hits");
     cudaStream_t s = (cudaStream_t)stream;
-    int64_t total = 0;
-    if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, -1, true, &total, s)) != NIF_OK)
+    // capacity: segments per ray of the last query whose total has come back
+    // (1.5 x, read without waiting), or the initial estimate
+    if (h->q_pending && cudaEventQuery(h->ev_qtotal) == cudaSuccess) {
+        h->q_hint = (double)h->h_qtotal[0] / (double)std::max(h->q_rays, 1);
+        h->q_pending = false;
+    }
+    const double spr = h->q_hint > 0.0 ? h->q_hint * 1.5 + 0.25 : h->q_init;
+    const int64_t cap = std::max<int64_t>(4096, (int64_t)std::ceil(spr * (double)n_rays));
+    // segments of whole rays within the capacity, counts on the device; more
+    // latches NIF_ERR_CAPACITY (the rays that did not fit report no hit)
+    if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, cap, false, nullptr, s, true)) != NIF_OK)
         return st;
     uint32_t* offs = (uint32_t*)h->b_offsets.p;
     const uint32_t* n_dev = offs + n_rays + 1;
-    int64_t n = std::max<int64_t>(total, 1);
-    if ((st = nif_grow(h, h->b_lin, sizeof(nif_linseg) * n)) != NIF_OK) return st;
-    if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * n)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_lin, sizeof(nif_linseg) * cap)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * cap)) != NIF_OK) return st;
     nif_segment* segs = (nif_segment*)h->b_segs.p;
     nif_linseg* lin = (nif_linseg*)h->b_lin.p;
     float* out = (float*)h->b_out.p;
-    if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, total, lin, s)) != NIF_OK) return st;
-    int prec = h->cfg.precision;
-    size_t esz = prec == NIF_FP32 ? 4 : 2;
-    // encode + MLP in chunks: FP32 chunks stay resident in L2 between the two
-    // kernels (48 MB of features); the tensor-core MLP is a persistent kernel
-    // whose pipeline needs many tiles per CTA, so its chunks are 2^20 rows.
-    int64_t chunk = h->tune.tc_chunk;
-    chunk = std::min<int64_t>(chunk, n);
+    if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, cap, lin, s)) != NIF_OK) return st;
+    const int prec = h->cfg.precision;
+    const size_t esz = prec == NIF_FP32 ? 4 : 2;
+    // encode + MLP in chunks with device-side counts: FP32 chunks stay
+    // resident in L2 between the two kernels; the tensor-core MLP is a
+    // persistent kernel whose pipeline needs many tiles per CTA
+    const int64_t chunk = std::min<int64_t>(h->tune.tc_chunk, cap);
+    const int n_chunks = (int)((cap + chunk - 1) / chunk);
     if ((st = nif_grow(h, h->b_feat, esz * (size_t)h->in_dim * chunk)) != NIF_OK) return st;
-    if (prec == NIF_FP32 &&
-        (st = nif_grow(h, h->b_acts, sizeof(float) * (size_t)chunk * h->W * h->H)) != NIF_OK)
+    if (prec == NIF_FP32 && (st = nif_grow(h, h->b_acts, sizeof(float) * (size_t)chunk * h->W * h->H)) != NIF_OK)
         return st;
-    for (int64_t c0 = 0; c0 < total; c0 += chunk) {
-        int64_t len = std::min(chunk, total - c0);
+    if (n_chunks > h->chunk_counts_cap) {
+        NIF_CK(h, cudaDeviceSynchronize());
+        if (h->d_chunk_counts) cudaFree(h->d_chunk_counts);
+        h->d_chunk_counts = nullptr;
+        h->chunk_counts_cap = 0;
+        NIF_CK(h, cudaMalloc(&h->d_chunk_counts, sizeof(uint32_t) * (size_t)n_chunks));
+        h->chunk_counts_cap = n_chunks;
+    }
+    if ((st = nif_chunk_counts_run(h, n_dev, chunk, n_chunks, h->d_chunk_counts, s)) != NIF_OK) return st;
+    for (int c = 0; c < n_chunks; c++) {
+        const int64_t c0 = (int64_t)c * chunk;
+        const int64_t len = std::min(chunk, cap - c0);
+        const uint32_t* cn = h->d_chunk_counts + c;
         if (prec == NIF_FP32) {
-            if ((st = nif_encode_segments_run(h, lin + c0, nullptr, len, h->b_feat.p, NIF_FP32, NIF_FP32, s)) != NIF_OK)
+            if ((st = nif_encode_segments_run(h, lin + c0, cn, len, h->b_feat.p, NIF_FP32, NIF_FP32, s)) != NIF_OK)
                 return st;
-            if ((st = nif_mlp_fwd_fp32_run(h, (const float*)h->b_feat.p, nullptr, len, out + c0 * NIF_OUT,
+            if ((st = nif_mlp_fwd_fp32_run(h, (const float*)h->b_feat.p, cn, len, out + c0 * NIF_OUT,
                                            (float*)h->b_acts.p, s)) != NIF_OK)
                 return st;
         } else {
-            if ((st = nif_encode_segments_run(h, lin + c0, nullptr, len, h->b_feat.p, prec, NIF_FP16, s)) != NIF_OK)
+            if ((st = nif_encode_segments_run(h, lin + c0, cn, len, h->b_feat.p, prec, NIF_FP16, s)) != NIF_OK)
                 return st;
-            if ((st = nif_mlp_fwd_tc_run(h, h->b_feat.p, prec, nullptr, len, out + c0 * NIF_OUT, s)) != NIF_OK)
-                return st;
+            if ((st = nif_mlp_fwd_tc_run(h, h->b_feat.p, prec, cn, len, out + c0 * NIF_OUT, s)) != NIF_OK) return st;
         }
     }
-    return nif_reconstruct_run(h, rays, inst_off, n_inst, n_rays, offs, segs, total, lin, out, hits, flags, s);
+    if ((st = nif_reconstruct_run(h, rays, inst_off, n_inst, n_rays, offs, segs, cap, lin, out, hits, flags, s,
+                                  n_dev)) != NIF_OK)
+        return st;
+    // this call's total, for the capacity of the next ones
+    NIF_CK(h, cudaMemcpyAsync(h->h_qtotal, offs + n_rays, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    NIF_CK(h, cudaEventRecord(h->ev_qtotal, s));
+    h->q_pending = true;
+    h->q_rays = n_rays;
+    return NIF_OK;
 }
 
 // The error a kernel latched on the device (a non-finite loss, a timed-out
@@ -1655,6 +1700,12 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
             NIF_CK(h, cudaMemcpy(h->d_status + 2, &ns, sizeof(ns), cudaMemcpyHostToDevice));
             return NIF_OK;
         }
+        case NIF_KNOB_QUERY_SEGS:
+            if (!(value > 0.0 && value <= 4096.0)) return nif_fail(h, NIF_ERR_ARG, "segments per ray must be in (0, 4096]");
+            h->q_init = value;
+            h->q_hint = 0.0;
+            h->q_pending = false;
+            return NIF_OK;
         case NIF_KNOB_SEG_SCRATCH:
             if (!(value > 0.0 && value <= 1.0)) return nif_fail(h, NIF_ERR_ARG, "segment scratch scale must be in (0, 1]");
             h->seg_scratch_scale = value;

@@ -171,7 +171,22 @@ struct nif_handle {
     Buf alt_counts, alt_offsets, alt_temp, alt_segs, alt_scan, alt_rays, alt_inst, alt_lin, alt_labels, alt_dup,
         alt_pts, alt_sort;
     PointList alt_enc_points;
-    double query_seg_per_ray = 0.0;     // segments per ray of the last query (temp capacity hint)
+    double query_seg_per_ray = 0.0;     // segments per ray of the last counted traversal (temp capacity hint)
+    // nif_query without host synchronisation: its segment capacity comes from
+    // the segments per ray of earlier queries, whose totals are read back
+    // asynchronously (pinned word + event), or q_init before the first
+    double q_hint = 0.0, q_init = 8.0;
+    uint32_t* h_qtotal = nullptr;       // pinned: unclamped total of the last query
+    cudaEvent_t ev_qtotal = nullptr;
+    bool q_pending = false;
+    int q_rays = 0;
+    uint32_t* d_chunk_counts = nullptr; // per-chunk segment counts of nif_query
+    int chunk_counts_cap = 0;
+    // pose uploads of more instances than a kernel argument holds
+    float4* h_pose_pinned = nullptr;
+    int pose_pinned_cap = 0;
+    cudaEvent_t ev_pose = nullptr;
+    bool pose_pending = false;
     double seg_scratch_scale = 1.0;     // NIF_KNOB_SEG_SCRATCH: scale of the single-traversal segment scratch
 
     // launch knobs chosen by the autotuner (nif_query_plan_create)
@@ -359,12 +374,15 @@ nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t
 nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
                                int n_rays, const uint32_t* offsets, const nif_segment* segs,
                                int64_t seg_cap, const nif_linseg* lin, const float* out,
-                               nif_hit* hits, unsigned flags, cudaStream_t s);
+                               nif_hit* hits, unsigned flags, cudaStream_t s, const uint32_t* n_valid = nullptr);
 // n rays of each of the streams stream_id .. stream_id + n_streams - 1, stream after stream
 nif_status nif_sample_rays_run(nif_handle* h, unsigned long long seed, int stream_id, int n,
                                nif_ray* rays, cudaStream_t s, int n_streams = 1);
 nif_status nif_scan_run_with(nif_handle* h, const uint32_t* in, uint32_t* out, int n, uint32_t* bsum,
                              cudaStream_t s);
+// counts[c] = clamp(*n_dev - c * chunk, 0, chunk) for c < n_chunks
+nif_status nif_chunk_counts_run(nif_handle* h, const uint32_t* n_dev, int64_t chunk, int n_chunks, uint32_t* counts,
+                                cudaStream_t s);
 // elements per block of the scan: nif_scan_run_with needs a block-sum buffer of
 // ceil(n / NIF_SCAN_BLOCK) + 1 words
 constexpr int NIF_SCAN_BLOCK = 1024;

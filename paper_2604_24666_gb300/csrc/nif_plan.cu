@@ -45,6 +45,18 @@ __global__ void k_chunk_counts(const uint32_t* __restrict__ n_dev, int64_t chunk
     counts[c] = (uint32_t)(rem <= 0 ? 0 : (rem < chunk ? rem : chunk));
 }
 
+}  // namespace
+
+nif_status nif_chunk_counts_run(nif_handle* h, const uint32_t* n_dev, int64_t chunk, int n_chunks, uint32_t* counts,
+                                cudaStream_t s) {
+    if (n_chunks <= 0) return NIF_OK;
+    k_chunk_counts<<<nif_blocks(n_chunks, 128), 128, 0, s>>>(n_dev, chunk, n_chunks, counts);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+namespace {
+
 void write_poses(nif_query_plan* p, const nif_pose* poses) {
     for (int i = 0; i < p->n_inst; i++)
         p->pinned_poses[i] = make_float4(NIF_KBEND * poses[i].bend, poses[i].twist, poses[i].taper, 0.f);
@@ -73,8 +85,7 @@ nif_status plan_enqueue(nif_query_plan* p, cudaStream_t s) {
     NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)n, s));
     if ((st = nif_seg_scatter_run(h, temp, cursor, p->cap, offs, counts, n, segs, p->cap, s)) != NIF_OK) return st;
     if ((st = nif_linearize_run(h, p->rays, p->inst_off, p->n_inst, segs, n_dev, p->cap, lin, s)) != NIF_OK) return st;
-    k_chunk_counts<<<nif_blocks(p->n_chunks, 128), 128, 0, s>>>(n_dev, p->chunk, p->n_chunks, p->chunk_counts);
-    NIF_CK_LAUNCH(h);
+    if ((st = nif_chunk_counts_run(h, n_dev, p->chunk, p->n_chunks, p->chunk_counts, s)) != NIF_OK) return st;
     const int prec = h->cfg.precision;
     for (int c = 0; c < p->n_chunks; c++) {
         int64_t c0 = (int64_t)c * p->chunk;

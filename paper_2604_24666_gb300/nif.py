@@ -25,7 +25,7 @@ NIF_SHADOW_ONLY = 1
 NIF_FLAG_FIXED_TASK_WEIGHTS, NIF_FLAG_SIGMOID_DISTANCE, NIF_FLAG_MIXED_TRAINING = 1, 2, 4
 NIF_FLAG_CONCAT_ENCODING = 8
 NIF_FLAG_BILINEAR_FACES = 16
-NIF_KNOB_WAIT_NS, NIF_KNOB_SEG_SCRATCH = 1, 2
+NIF_KNOB_WAIT_NS, NIF_KNOB_SEG_SCRATCH, NIF_KNOB_QUERY_SEGS = 1, 2, 3
 NIF_PROBE_RED8, NIF_PROBE_RED16, NIF_PROBE_LOAD8, NIF_PROBE_LOAD4 = 1, 2, 3, 4
 
 _STATUS = {0: "NIF_OK", -1: "NIF_ERR_ARG", -2: "NIF_ERR_CUDA", -3: "NIF_ERR_OOM", -4: "NIF_ERR_CAPACITY",
