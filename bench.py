@@ -236,9 +236,17 @@ def _l2_probe(nif, h, dev):
     buf = torch.zeros((16 << 20,), dtype=torch.float32, device=dev)          # 64 MiB
     for name, kind, nbytes in (("red8_64MiB", nif.NIF_PROBE_RED8, 64 << 20), ("red16_64MiB", nif.NIF_PROBE_RED16, 64 << 20),
                                ("load8_64MiB", nif.NIF_PROBE_LOAD8, 64 << 20), ("load4_32MiB", nif.NIF_PROBE_LOAD4, 32 << 20),
-                               ("load4_1MiB", nif.NIF_PROBE_LOAD4, 1 << 20)):
+                               ("load4_1MiB", nif.NIF_PROBE_LOAD4, 1 << 20),
+                               ("red8_64MiB_warp", nif.NIF_PROBE_RED8_WARP, 64 << 20),
+                               ("red16_64MiB_warp", nif.NIF_PROBE_RED16_WARP, 64 << 20),
+                               ("load8_64MiB_warp", nif.NIF_PROBE_LOAD8_WARP, 64 << 20),
+                               ("load4_32MiB_warp", nif.NIF_PROBE_LOAD4_WARP, 32 << 20)):
         gbs, ms = nif.nif_probe_memory(h.h, kind, buf[:nbytes // 4], iters=128)
         out[name] = {"GB/s": gbs, "ms_per_launch": ms}
+    # the ceilings: whole sectors (every fetched byte used); the random rows
+    # (one sector per 8-byte access) are the floor of the same pattern
+    out["ceiling_red"] = max(out["red8_64MiB_warp"]["GB/s"], out["red16_64MiB_warp"]["GB/s"])
+    out["ceiling_load8"] = out["load8_64MiB_warp"]["GB/s"]
     del buf
     return out
 
@@ -304,8 +312,10 @@ def run_ours(args):
     # kept beside it.
     n_pts, n_segs_enc = nif.nif_encoder_points(h.h)
     l2 = _l2_probe(nif, h, dev) if rank == 0 else None
-    l2_peak = {"encode_bwd": ("red8_64MiB", "random 8-byte FP32 reductions into 64 MiB held in L2"),
-               "encode_fwd": ("load8_64MiB", "random 8-byte row loads from 64 MiB held in L2")}
+    l2_peak = {"encode_bwd": ("ceiling_red", "red8_64MiB", "FP32 vector reductions into 64 MiB held in L2, whole "
+                              "sectors per warp (the better of 8- and 16-byte)"),
+               "encode_fwd": ("ceiling_load8", "load8_64MiB", "8-byte row loads from 64 MiB held in L2, whole sectors "
+                              "per warp")}
     stages = {k: v for k, v in prof.items()}
     tot_ms = sum(v[0] for v in stages.values())
     dom = max((k for k in stages if k not in OVERLAPPED), key=lambda k: stages[k][0])
@@ -321,10 +331,12 @@ def run_ours(args):
         roof = dict(hbm_roof, kernel=dom, traffic=NCU_TRAFFIC.get(dom))
         lw = _l2_work(net, dom, n_pts)
         if lw is not None and l2 is not None and dom in l2_peak:
-            key, what = l2_peak[dom]
+            key, floor_key, what = l2_peak[dom]
             ach2 = lw / (avg_ms / 1e3) / 1e9
-            roof = {"bound": "l2", "kernel": dom, "achieved": ach2, "peak": l2[key]["GB/s"], "unit": "GB/s",
-                    "frac": ach2 / l2[key]["GB/s"], "peak_source": f"measured: {what} (nif_probe_memory {key})",
+            roof = {"bound": "l2", "kernel": dom, "achieved": ach2, "peak": l2[key], "unit": "GB/s",
+                    "frac": ach2 / l2[key], "peak_source": f"measured: {what} (nif_probe_memory)",
+                    "floor": {"GB/s": l2[floor_key]["GB/s"], "what": "the same accesses at random rows, one sector "
+                              "each (nif_probe_memory " + floor_key + ")"},
                     "traffic": NCU_TRAFFIC.get(dom), "algorithmic_bytes": lw,
                     "per": f"distinct end point: P x L x 8 corners x 8 B ({n_pts} distinct end points of "
                            f"{n_segs_enc} segments)",
@@ -342,7 +354,7 @@ def run_ours(args):
         lw = _l2_work(net, k, n_pts)
         if lw is not None and l2 is not None and k in l2_peak:
             ent["l2_GB/s"] = lw / (ent["ms_per_step"] / 1e3) / 1e9
-            ent["frac_l2"] = ent["l2_GB/s"] / l2[l2_peak[k][0]]["GB/s"]
+            ent["frac_l2"] = ent["l2_GB/s"] / l2[l2_peak[k][0]]
         kernels[k] = ent
 
     # ---- end to end through the public API, host buffers ----------------
@@ -386,6 +398,7 @@ def run_ours(args):
     precision = run_precision(args, nif, S, dev) if (not args.no_precision and rank == 0) else None
     frame = run_frame(args, nif, S, dev) if (not args.no_frame and rank == 0) else None
     trav = run_traversal(args, nif, S, dev) if (not args.no_traversal and rank == 0) else None
+    field = run_field(args, nif, S, dev, rank) if not args.no_field else None
 
     if rank != 0:
         return 0
@@ -411,7 +424,7 @@ def run_ours(args):
             "roofline": roof, "kernels": kernels, "l2_probe": l2, "encoder_points": {"distinct": n_pts, "segments": n_segs_enc},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "loss": list(loss) if loss is not None else None, "train_mixed": mixed,
-            "query": query, "batch": batch, "frame_loop": frame, "traversal": trav,
+            "query": query, "batch": batch, "frame_loop": frame, "traversal": trav, "field": field,
             "precision": precision}
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -587,6 +600,83 @@ def run_query(args, nif, S, dev, rank):
         except nif.NifError as e:
             res[name] = {"unavailable": str(e)}
     return res
+
+
+def run_field(args, nif, S, dev, rank):
+    """The learned deformation field: (1) fitting steps (nif_field_step) on the
+    training workload's network and shape, 4 instances with their own 9^3
+    lattices under half of their target poses, 2^18 segments per step;
+    (2) the BF16 query of the 128^3 torus (2^22 rays) through a 9^3 lattice,
+    beside the same query without it."""
+    import torch
+    out = {}
+    w = S.WORKLOADS[TRAIN_WORKLOAD]
+    net = w["net"]
+    h = nif.Nif(net, S.make_mesh(w["shape"]), seed=55)
+    n_inst, G = 4, 9
+    nif.nif_set_field(h.h, np.zeros((n_inst, G, G, G, 3), np.float32))
+    target = S.poses(n_inst, seed=56)
+    pose = (0.5 * target).astype(np.float32)
+    per = int(N_SEG / n_inst / 4.0 * 1.3)
+    rays = torch.from_numpy(S.sphere_rays(per * n_inst, seed=57 + rank)).to(dev)
+    inst = torch.arange(0, per * n_inst + 1, per, dtype=torch.int32, device=dev)
+    for i in range(max(args.warmup, 1)):
+        nif.nif_field_step(h.h, pose, rays, N_SEG, target, inst_offsets=inst, lr_field=1e-3, want_loss=False)
+    torch.cuda.synchronize()
+    k = max(3, args.steps // 4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(k):
+        nif.nif_field_step(h.h, pose, rays, N_SEG, target, inst_offsets=inst, lr_field=1e-3, want_loss=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    out["fit"] = {"workload": TRAIN_WORKLOAD, "instances": n_inst, "lattice": G, "segments_per_step": N_SEG,
+                  "ms_per_step": ms, "segments_per_s": N_SEG / (ms / 1e3), "network": "frozen"}
+    h.close()
+    wq = S.WORKLOADS[QUERY_WORKLOAD]
+    netq = wq["net"]
+    n = args.query_rays or wq["n_rays"]
+    rq = torch.from_numpy(S.sphere_rays(n, seed=900 + rank)).to(dev)
+    pq = S.poses(1, seed=901 + rank)
+    fld = np.random.default_rng(58).normal(size=(1, G, G, G, 3))
+    res = {}
+    for with_field in (False, True):
+        hq = nif.Nif(netq, S.make_mesh(wq["shape"]), precision=nif.NIF_BF16, seed=31)
+        if with_field:
+            f = fld[0]
+            lip = _field_lipschitz(f)
+            nif.nif_set_field(hq.h, (fld * (0.5 / lip)).astype(np.float32))
+        hits = torch.zeros((n, 8), dtype=torch.float32, device=dev)
+        for i in range(max(args.warmup, 1)):
+            nif.nif_query(hq.h, pq, rq, hits=hits)
+        torch.cuda.synchronize()
+        kq = max(2, args.steps // 4)
+        e0.record()
+        for i in range(kq):
+            nif.nif_query(hq.h, pq, rq, hits=hits)
+        e1.record()
+        torch.cuda.synchronize()
+        msq = e0.elapsed_time(e1) / kq
+        res["with_field" if with_field else "without_field"] = {"ms_per_query_batch": msq,
+                                                                "queries_per_s": n / (msq / 1e3)}
+        nif.nif_sync_status(hq.h)
+        hq.close()
+    out["query_bf16"] = dict(res, workload=QUERY_WORKLOAD, rays=n, lattice=G, lipschitz=0.5)
+    return out
+
+
+def _field_lipschitz(f):
+    """Lipschitz bound of a [G,G,G,3] lattice as the library defines it (for
+    scaling a random benchmark field to a chosen bound)."""
+    G = f.shape[0]
+    m = []
+    for ax in (2, 1, 0):
+        e = np.linalg.norm(np.diff(f, axis=ax), axis=-1) * (G - 1)
+        for o in [o for o in (0, 1, 2) if o != ax]:
+            e = np.maximum(np.take(e, range(0, e.shape[o] - 1), axis=o), np.take(e, range(1, e.shape[o]), axis=o))
+        m.append(e)
+    return float(np.sqrt(sum(x ** 2 for x in m)).max())
 
 
 BATCH_WORKLOAD = "torus16x64_batch"
@@ -807,6 +897,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision training measurement")
     ap.add_argument("--no-frame", action="store_true", help="skip the animated frame loop")
     ap.add_argument("--no-traversal", action="store_true", help="skip the enumeration vs exit-face walk comparison")
+    ap.add_argument("--no-field", action="store_true", help="skip the learned deformation field measurement")
+    ap.add_argument("--only-field", action="store_true", help="measure only the learned deformation field (profiling aid)")
     ap.add_argument("--only-batch", action="store_true", help="measure only the batched query (profiling aid)")
     ap.add_argument("--only-traversal", action="store_true", help="measure only the traversal comparison (profiling aid)")
     ap.add_argument("--frames", type=int, default=120, help="frames of the animated frame loop")
@@ -831,6 +923,14 @@ def main():
         B.build()
         from paper_2604_24666_gb300 import nif, synth as S
         print(json.dumps({"batch": run_batch(args, nif, S, torch.device("cuda:0"), 0)}), flush=True)
+        return 0
+    if args.only_field:
+        import torch
+        torch.cuda.set_device(0)
+        from paper_2604_24666_gb300 import build as B
+        B.build()
+        from paper_2604_24666_gb300 import nif, synth as S
+        print(json.dumps({"field": run_field(args, nif, S, torch.device("cuda:0"), 0)}), flush=True)
         return 0
     if args.only_traversal:
         import torch

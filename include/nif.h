@@ -649,7 +649,10 @@ unsigned long long nif_kernel_launches(void);
  *                    (its paired x-edge corners),
  *   NIF_PROBE_LOAD8  random 8-byte row loads (FP32 table rows, the forward),
  *   NIF_PROBE_LOAD4  random 4-byte row loads (FP16 table rows),
- * over buf_dev (caller-owned, `bytes` = a power-of-two number >= 1024 of
+ * each lane at its own random row (one 32-byte sector per access: the L2's
+ * rate for scattered accesses), or, with the _WARP kinds, each warp's 32
+ * lanes at 32 consecutive rows of a random block (whole sectors: the rate
+ * when every fetched byte is used), over buf_dev (caller-owned, `bytes` = a power-of-two number >= 1024 of
  * rows, 16-byte aligned; its contents are changed by the reductions), which
  * stays in L2 when it fits: one warm-up launch, then 5 launches of
  * 8 x num_SMs blocks of 256 threads, each thread `iters` x 8 independent
@@ -660,6 +663,10 @@ unsigned long long nif_kernel_launches(void);
 #define NIF_PROBE_RED16 2
 #define NIF_PROBE_LOAD8 3
 #define NIF_PROBE_LOAD4 4
+#define NIF_PROBE_RED8_WARP 5
+#define NIF_PROBE_RED16_WARP 6
+#define NIF_PROBE_LOAD8_WARP 7
+#define NIF_PROBE_LOAD4_WARP 8
 nif_status nif_probe_memory(nif_handle* h, int kind, void* buf_dev, size_t bytes, int iters, double* gbs_host,
                             double* ms_host, void* stream);
 /* Distinct end points listed by the handle's last segment encoding (the

@@ -91,6 +91,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + lay.bar_off + 8 * (2 * S + 6) + 8);
     const int64_t n_tiles = (n + kRows - 1) / kRows;
     const int64_t nt = blockIdx.x < n_tiles ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    // a CTA without tiles (a chunk whose device count is short or zero) leaves
+    // before any barrier, tensor memory or weight load: uniform per CTA
+    if (nt == 0) return;
 
     if (tid == 0) {
         for (int i = 0; i < S; i++) {
@@ -321,6 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + lay.bar_off + 40);
     const int64_t n = n_dev ? ((int64_t)*n_dev < n_max ? (int64_t)*n_dev : n_max) : n_max;
     const int64_t n_tiles = (n + kRows - 1) / kRows;
+    if ((int64_t)blockIdx.x >= n_tiles) return;   // no tile for this CTA: leave before any setup
     const int n_chunks = (in_dim + (int)kCols - 1) / (int)kCols;
     if (tid == 0) {
         mbar_init(smem_u32(&bars[0]), 1);
@@ -570,6 +574,7 @@ __global__ void __launch_bounds__(kDwThreads, 1)
     const int64_t n = n_dev ? ((int64_t)*n_dev < n_max ? (int64_t)*n_dev : n_max) : n_max;
     const int64_t n_chunks = (n + 127) / 128;
     const int64_t my = (int64_t)blockIdx.y < n_chunks ? (n_chunks - blockIdx.y + gridDim.y - 1) / gridDim.y : 0;
+    if (my == 0) return;                          // nothing to add: leave before any setup
     constexpr uint32_t kCols = 64;
     if (tid == 0) {
         for (int i = 0; i < kDwStages; i++) {

@@ -152,6 +152,9 @@ __global__ void __launch_bounds__(kX3Threads, 1)
     const int64_t n = n_dev ? ((int64_t)*n_dev < a.n_max ? (int64_t)*n_dev : a.n_max) : a.n_max;
     const int64_t n_jobs = (n + 127) / 128 * a.n_chunks;
     const int64_t my = (int64_t)blockIdx.x < n_jobs ? (n_jobs - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    // a CTA without jobs (a chunk whose device count is short or zero) leaves
+    // before any barrier, tensor memory or copy: uniform per CTA
+    if (my == 0) return;
 
     if (tid == 0) {
         for (int i = 0; i < S; i++) {
@@ -431,6 +434,7 @@ __global__ void __launch_bounds__(kDwX3Threads, 1)
     const int64_t n = n_dev ? ((int64_t)*n_dev < a.n_max ? (int64_t)*n_dev : a.n_max) : a.n_max;
     const int64_t nkb = (n + 31) / 32;
     const int64_t my = (int64_t)blockIdx.y < nkb ? (nkb - blockIdx.y + gridDim.y - 1) / gridDim.y : 0;
+    if (my == 0) return;                          // nothing to add: leave before any setup
     const int i0 = blockIdx.x * 128;
 
     if (tid == 0) {
