@@ -684,8 +684,9 @@ FRAME_WORKLOAD = "ellipsoids256_frame"
 
 
 def run_batch(args, nif, S, dev, rank):
-    """Batched mixed-precision queries of 64 deforming instances with Zipf ray
-    counts (about 2^22 rays), one autotuned CUDA-graph replay per step."""
+    """Batched queries of 64 deforming instances with Zipf ray counts (about
+    2^22 rays), one autotuned CUDA-graph replay per step: mixed precision
+    (BF16 MLP, FP16 tables) and, on the same rays and poses, FP32."""
     import torch
     w = S.WORKLOADS[BATCH_WORKLOAD]
     net = w["net"]
@@ -694,38 +695,45 @@ def run_batch(args, nif, S, dev, rank):
     rays_np = np.concatenate([S.sphere_rays(int(c), seed=1000 * rank + 710 + i) for i, c in enumerate(counts)])
     inst = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
     n = len(rays_np)
-    h = nif.Nif(net, mesh, precision=nif.NIF_BF16, seed=41)
     rays = torch.from_numpy(rays_np).to(dev)
     it = torch.from_numpy(inst).to(dev)
-    hits = torch.zeros((n, 8), dtype=torch.float32, device=dev)
     rng = np.random.default_rng(720 + rank)
     poses = [rng.uniform(-1, 1, (w["n_inst"], 3)).astype(np.float32) for _ in range(args.steps + args.warmup)]
-    t0 = time.perf_counter()
-    plan = nif.QueryPlan(h.h, poses[0], rays, hits, inst_offsets=it, autotune=True)
-    tune_s = time.perf_counter() - t0
-    for i in range(args.warmup):
-        plan.run(poses[i])
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for i in range(args.steps):
-        plan.run(poses[args.warmup + i])
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    offs = torch.zeros(n + 1, dtype=torch.int32, device=dev)
-    total = nif._i64()
-    p_, n_inst = nif._poses(poses[args.warmup])
-    nif._check(h.h, nif.lib().nif_segments(h.h, p_, n_inst, nif._ptr(rays), nif._ptr(it), n, nif._ptr(offs), None, 0,
-                                           nif.ctypes.byref(total), None))
-    res = {"workload": BATCH_WORKLOAD, "instances": int(w["n_inst"]), "rays_per_step": int(n),
-           "segments_per_step": int(total.value),
-           "rays_per_instance_min_max": [int(counts.min()), int(counts.max())], "precision": "bf16",
-           "queries_per_s": n / (ms / 1e3), "ms_per_batch": ms, "graph": True, "knobs": plan.info(),
-           "autotune_s": tune_s,
-           "hit_rate": float((hits[:, 7].view(torch.int32) & 0xff).ne(0).float().mean().item())}
-    plan.close()
-    h.close()
+    res = None
+    for name, prec in (("bf16", nif.NIF_BF16), ("fp32", nif.NIF_FP32)):
+        h = nif.Nif(net, mesh, precision=prec, seed=41)
+        hits = torch.zeros((n, 8), dtype=torch.float32, device=dev)
+        t0 = time.perf_counter()
+        plan = nif.QueryPlan(h.h, poses[0], rays, hits, inst_offsets=it, autotune=True)
+        tune_s = time.perf_counter() - t0
+        for i in range(args.warmup):
+            plan.run(poses[i])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(args.steps):
+            plan.run(poses[args.warmup + i])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        nif.nif_sync_status(h.h)
+        ent = {"queries_per_s": n / (ms / 1e3), "ms_per_batch": ms, "knobs": plan.info(), "autotune_s": tune_s,
+               "hit_rate": float((hits[:, 7].view(torch.int32) & 0xff).ne(0).float().mean().item())}
+        if res is None:
+            offs = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+            total = nif._i64()
+            p_, n_inst = nif._poses(poses[args.warmup])
+            nif._check(h.h, nif.lib().nif_segments(h.h, p_, n_inst, nif._ptr(rays), nif._ptr(it), n, nif._ptr(offs),
+                                                   None, 0, nif.ctypes.byref(total), None))
+            res = {"workload": BATCH_WORKLOAD, "instances": int(w["n_inst"]), "rays_per_step": int(n),
+                   "segments_per_step": int(total.value),
+                   "rays_per_instance_min_max": [int(counts.min()), int(counts.max())], "precision": "bf16",
+                   "queries_per_s": ent["queries_per_s"], "ms_per_batch": ms, "graph": True, "knobs": ent["knobs"],
+                   "autotune_s": tune_s, "hit_rate": ent["hit_rate"]}
+        res[name] = ent
+        plan.close()
+        h.close()
+    res["mixed_over_fp32"] = res["bf16"]["queries_per_s"] / res["fp32"]["queries_per_s"]
     return res
 
 

@@ -207,6 +207,52 @@ __global__ void __launch_bounds__(256) k_point_list(const uint32_t* __restrict__
     }
 }
 
+// a table row as loaded (two FP32 or two FP16 features), converted at use
+template <typename TT>
+struct RawRow;
+template <>
+struct RawRow<float> {
+    using T = float2;
+    static __device__ __forceinline__ T load(const float* tab, uint32_t row) {
+        return __ldg(reinterpret_cast<const float2*>(tab) + row);
+    }
+    static __device__ __forceinline__ float2 f2(T v) { return v; }
+};
+template <>
+struct RawRow<__half> {
+    using T = __half2;
+    static __device__ __forceinline__ T load(const __half* tab, uint32_t row) {
+        return __ldg(reinterpret_cast<const __half2*>(tab) + row);
+    }
+    static __device__ __forceinline__ float2 f2(T v) { return __half22float2(v); }
+};
+
+// the 8 corner rows of level l's cell c (dense index or spatial hash), loaded
+template <typename TT>
+__device__ __forceinline__ void level_gather(const GridInfo& g, const TT* __restrict__ tab, int l, const Cell& c,
+                                             typename RawRow<TT>::T* v) {
+    const int Nl = g.res[l];
+    const TT* tl = tab + (int64_t)l * g.T * 2;
+    uint32_t rows[8];
+    if ((g.dense_mask >> l) & 1u) {
+        const uint32_t sy = (uint32_t)Nl + 1u, sz = sy * sy;
+        const uint32_t b = (uint32_t)c.ix + (uint32_t)c.iy * sy + (uint32_t)c.iz * sz;
+        rows[0] = b; rows[1] = b + 1u; rows[2] = b + sy; rows[3] = b + sy + 1u;
+        rows[4] = b + sz; rows[5] = b + sz + 1u; rows[6] = b + sz + sy; rows[7] = b + sz + sy + 1u;
+    } else {
+        const uint32_t m = g.T - 1u;
+        const uint32_t x0 = (uint32_t)c.ix, x1 = x0 + 1u;
+        const uint32_t y0 = (uint32_t)c.iy * 2654435761u, y1 = y0 + 2654435761u;
+        const uint32_t z0 = (uint32_t)c.iz * 805459861u, z1 = z0 + 805459861u;
+        rows[0] = (x0 ^ y0 ^ z0) & m; rows[1] = (x1 ^ y0 ^ z0) & m;
+        rows[2] = (x0 ^ y1 ^ z0) & m; rows[3] = (x1 ^ y1 ^ z0) & m;
+        rows[4] = (x0 ^ y0 ^ z1) & m; rows[5] = (x1 ^ y0 ^ z1) & m;
+        rows[6] = (x0 ^ y1 ^ z1) & m; rows[7] = (x1 ^ y1 ^ z1) & m;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q++) v[q] = RawRow<TT>::load(tl, rows[q]);
+}
+
 // pts (nullable): the distinct points (2 s + e, *n_pts_dev of them) and dupf
 // the flags of k_dup_flags; without them every (segment, end point) is encoded
 template <typename TT, typename OT, int LMAX>
@@ -239,28 +285,9 @@ __global__ void __launch_bounds__(512) k_encode_segments_v(GridInfo g, const TT*
 #pragma unroll
         for (int l = 0; l < LMAX; l++) {
             if (l >= g.L) break;
-            const int Nl = g.res[l];
-            const Cell c = cell_of(u, Nl);
-            const TT* tl = tab + (int64_t)l * g.T * 2;
-            uint32_t rows[8];
-            if ((g.dense_mask >> l) & 1u) {
-                const uint32_t sy = (uint32_t)Nl + 1u, sz = sy * sy;
-                const uint32_t b = (uint32_t)c.ix + (uint32_t)c.iy * sy + (uint32_t)c.iz * sz;
-                rows[0] = b; rows[1] = b + 1u; rows[2] = b + sy; rows[3] = b + sy + 1u;
-                rows[4] = b + sz; rows[5] = b + sz + 1u; rows[6] = b + sz + sy; rows[7] = b + sz + sy + 1u;
-            } else {
-                const uint32_t m = g.T - 1u;
-                const uint32_t x0 = (uint32_t)c.ix, x1 = x0 + 1u;
-                const uint32_t y0 = (uint32_t)c.iy * 2654435761u, y1 = y0 + 2654435761u;
-                const uint32_t z0 = (uint32_t)c.iz * 805459861u, z1 = z0 + 805459861u;
-                rows[0] = (x0 ^ y0 ^ z0) & m; rows[1] = (x1 ^ y0 ^ z0) & m;
-                rows[2] = (x0 ^ y1 ^ z0) & m; rows[3] = (x1 ^ y1 ^ z0) & m;
-                rows[4] = (x0 ^ y0 ^ z1) & m; rows[5] = (x1 ^ y0 ^ z1) & m;
-                rows[6] = (x0 ^ y1 ^ z1) & m; rows[7] = (x1 ^ y1 ^ z1) & m;
-            }
-            float2 v[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) v[q] = load_row<TT>(tl, rows[q]);
+            const Cell c = cell_of(u, g.res[l]);
+            typename RawRow<TT>::T vr[8];
+            level_gather<TT>(g, tab, l, c, vr);
             const float wx1 = c.wx, wx0 = 1.f - c.wx, wy1 = c.wy, wy0 = 1.f - c.wy;
             const float wz1 = c.wz, wz0 = 1.f - c.wz;
             const float wxy[4] = {wx0 * wy0, wx1 * wy0, wx0 * wy1, wx1 * wy1};
@@ -268,8 +295,9 @@ __global__ void __launch_bounds__(512) k_encode_segments_v(GridInfo g, const TT*
 #pragma unroll
             for (int q = 0; q < 8; q++) {
                 const float w = wxy[q & 3] * ((q & 4) ? wz1 : wz0);
-                acc.x += w * v[q].x;
-                acc.y += w * v[q].y;
+                const float2 v = RawRow<TT>::f2(vr[q]);
+                acc.x += w * v.x;
+                acc.y += w * v.y;
             }
             res[l] = OutPair<OT>::make(acc.x, acc.y);
         }
@@ -815,13 +843,22 @@ static nif_status point_list(nif_handle* h, const nif_linseg* lin, const uint32_
 
 template <typename TT, typename OT>
 nif_status launch_segments(nif_handle* h, const TT* tab, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
-                           void* feats, cudaStream_t s, bool reuse_points) {
+                           void* feats, cudaStream_t s, bool reuse_points, bool dedup) {
     // block size and resident blocks per SM are tuning knobs of the handle
     int thr = h->tune.enc_threads;
     unsigned g = nif_blocks(n_max * 2 * h->P, thr);
     unsigned cap = (unsigned)h->num_sms * (unsigned)h->tune.enc_blocks_per_sm;
     if (g > cap) g = cap;
-    if (h->L <= 16) {
+    if (h->L <= 16 && !dedup) {
+        // every (segment, end point): no point list to prepare, so a chunk
+        // whose device count is zero costs one early-exiting launch
+        if (h->L <= 8)
+            k_encode_segments_v<TT, OT, 8><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats, nullptr,
+                                                            nullptr, nullptr);
+        else
+            k_encode_segments_v<TT, OT, 16><<<g, thr, 0, s>>>(h->grid, tab, lin, n_dev, n_max, (OT*)feats, nullptr,
+                                                             nullptr, nullptr);
+    } else if (h->L <= 16) {
         // distinct end points only (device-side list, see k_dup_flags)
         const nif_handle::PointList& pl = h->enc_points;
         const bool sorted = (size_t)h->T * h->L * h->Fd * sizeof(TT) > ((size_t)4 << 20);
@@ -1050,7 +1087,8 @@ static nif_status launch_cat(nif_handle* h, const nif_linseg* lin, const uint32_
 }
 
 nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
-                                   void* feats, int out_dtype, int table_dtype, cudaStream_t s, bool reuse_points) {
+                                   void* feats, int out_dtype, int table_dtype, cudaStream_t s, bool reuse_points,
+                                   bool dedup) {
     NifProf prof_(h, "encode_fwd", s);
     if (n_max <= 0) return NIF_OK;
     nif_status st = NIF_OK;
@@ -1059,15 +1097,15 @@ nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const u
         st = nif_refresh_lowp(h, s);
         if (st != NIF_OK) return st;
         const __half* tab = h->d_tables_h;
-        if (out_dtype == NIF_FP32) st = launch_segments<__half, float>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
-        else if (out_dtype == NIF_BF16) st = launch_segments<__half, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
-        else if (out_dtype == NIF_FP16) st = launch_segments<__half, __half>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
+        if (out_dtype == NIF_FP32) st = launch_segments<__half, float>(h, tab, lin, n_dev, n_max, feats, s, reuse_points, dedup);
+        else if (out_dtype == NIF_BF16) st = launch_segments<__half, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s, reuse_points, dedup);
+        else if (out_dtype == NIF_FP16) st = launch_segments<__half, __half>(h, tab, lin, n_dev, n_max, feats, s, reuse_points, dedup);
         else return nif_fail(h, NIF_ERR_ARG, "out_dtype");
     } else if (table_dtype == NIF_FP32) {
         const float* tab = h->d_params + h->off_tables;
-        if (out_dtype == NIF_FP32) st = launch_segments<float, float>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
-        else if (out_dtype == NIF_BF16) st = launch_segments<float, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
-        else if (out_dtype == NIF_FP16) st = launch_segments<float, __half>(h, tab, lin, n_dev, n_max, feats, s, reuse_points);
+        if (out_dtype == NIF_FP32) st = launch_segments<float, float>(h, tab, lin, n_dev, n_max, feats, s, reuse_points, dedup);
+        else if (out_dtype == NIF_BF16) st = launch_segments<float, __nv_bfloat16>(h, tab, lin, n_dev, n_max, feats, s, reuse_points, dedup);
+        else if (out_dtype == NIF_FP16) st = launch_segments<float, __half>(h, tab, lin, n_dev, n_max, feats, s, reuse_points, dedup);
         else return nif_fail(h, NIF_ERR_ARG, "out_dtype");
     } else {
         return nif_fail(h, NIF_ERR_ARG, "table_dtype");

@@ -1197,18 +1197,27 @@ extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst
         h->chunk_counts_cap = n_chunks;
     }
     if ((st = nif_chunk_counts_run(h, n_dev, chunk, n_chunks, h->d_chunk_counts, s)) != NIF_OK) return st;
+    // chunks past the segments the last query found (+2 %) are expected to be
+    // empty: they skip the distinct-point list, whose preparation would cost
+    // the full chunk size even for a zero count (encoded correctly either way)
+    const int n_expected = h->q_hint > 0.0
+                               ? (int)std::min<int64_t>(n_chunks, (int64_t)std::ceil(h->q_hint * 1.02 * n_rays / chunk))
+                               : n_chunks;
     for (int c = 0; c < n_chunks; c++) {
         const int64_t c0 = (int64_t)c * chunk;
         const int64_t len = std::min(chunk, cap - c0);
         const uint32_t* cn = h->d_chunk_counts + c;
+        const bool dedup = c < n_expected;
         if (prec == NIF_FP32) {
-            if ((st = nif_encode_segments_run(h, lin + c0, cn, len, h->b_feat.p, NIF_FP32, NIF_FP32, s)) != NIF_OK)
+            if ((st = nif_encode_segments_run(h, lin + c0, cn, len, h->b_feat.p, NIF_FP32, NIF_FP32, s, false, dedup)) !=
+                NIF_OK)
                 return st;
             if ((st = nif_mlp_fwd_fp32_run(h, (const float*)h->b_feat.p, cn, len, out + c0 * NIF_OUT,
                                            (float*)h->b_acts.p, s)) != NIF_OK)
                 return st;
         } else {
-            if ((st = nif_encode_segments_run(h, lin + c0, cn, len, h->b_feat.p, prec, NIF_FP16, s)) != NIF_OK)
+            if ((st = nif_encode_segments_run(h, lin + c0, cn, len, h->b_feat.p, prec, NIF_FP16, s, false, dedup)) !=
+                NIF_OK)
                 return st;
             if ((st = nif_mlp_fwd_tc_run(h, h->b_feat.p, prec, cn, len, out + c0 * NIF_OUT, s)) != NIF_OK) return st;
         }

@@ -307,9 +307,11 @@ nif_status nif_encode_points_run(nif_handle* h, const float* pts, int64_t n, voi
 // reuse_points: the list of distinct end points that nif_encode_points_prepare
 // (or an earlier encoding) made for the same lin / n_dev / n_max, on this
 // stream, is taken as it is
+// dedup: encode only the distinct end points (a device-side list prepared
+// per call); off, every (segment, end point) is encoded without preparation
 nif_status nif_encode_segments_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev,
                                    int64_t n_max, void* feats, int out_dtype, int table_dtype,
-                                   cudaStream_t s, bool reuse_points = false);
+                                   cudaStream_t s, bool reuse_points = false, bool dedup = true);
 // the distinct end points of a training batch, built with the batch (on its
 // stream) for the forward and backward encodings of the step that trains on it
 nif_status nif_encode_points_prepare(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev,
