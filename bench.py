@@ -301,24 +301,47 @@ def run_ours(args):
     # labels) is built on the library's third stream beside the previous step
     nif.nif_train_steps(h.h, args.warmup, N_SEG, N_POSES, seed0, lr_grid=1e-2, lr_mlp=1e-3)
     torch.cuda.synchronize()
-    nif.nif_profile(h.h, 1)
+
+    def timed_steps(k, seed, stages=None):
+        """k steps in one call, CUDA events on the stream around them, the
+        library's per-stage events on (only for `stages` if given)."""
+        nif.nif_profile_filter(h.h, stages)
+        nif.nif_profile(h.h, 1)
+        _barrier(ws)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nif.nif_train_steps(h.h, k, N_SEG, N_POSES, seed, lr_grid=1e-2, lr_mlp=1e-3)
+        b.record(stream)
+        torch.cuda.synchronize()
+        _barrier(ws)
+        p = nif.nif_profile_read(h.h)
+        nif.nif_profile(h.h, 0)
+        nif.nif_profile_filter(h.h, None)
+        return a.elapsed_time(b), p
+
+    # every stage timed (two events each): the per-kernel split and the
+    # dominant kernel; then the measured interval, with only the dominant
+    # kernel's events in it
+    ms_all, prof = timed_steps(args.steps, seed0 + args.warmup)
+    dom = max((k for k in prof if k not in OVERLAPPED), key=lambda k: prof[k][0])
     clk = Clocks(local) if rank == 0 else None
     launches0 = nif.nif_kernel_launches()
-    _barrier(ws)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    nif.nif_train_steps(h.h, args.steps, N_SEG, N_POSES, seed0 + args.warmup, lr_grid=1e-2, lr_mlp=1e-3)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    _barrier(ws)
-    ms = e0.elapsed_time(e1)
+    ms, prof_dom = timed_steps(args.steps, seed0 + args.warmup + args.steps, [dom])
     launches = nif.nif_kernel_launches() - launches0
     clocks = clk.stop() if clk else None
-    prof = nif.nif_profile_read(h.h)
-    nif.nif_profile(h.h, 0)
     ms_max = _max_over_ranks(ms, ws)
     value = ws * args.steps * N_SEG / (ms_max / 1e3)
+    # the FP32 forward in one launch (NIF_KNOB_FP32_FUSED) beside the per-layer launches
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_FP32_FUSED, 1)
+    ms_fused, prof_fused = timed_steps(args.steps, seed0 + args.warmup + 2 * args.steps)
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_FP32_FUSED, 0)
+    fused_fwd = {"ms_per_step": ms_fused / args.steps,
+                 "mlp_fwd_fp32_ms": prof_fused["mlp_fwd_fp32"][0] / args.steps,
+                 "per_layer": {"ms_per_step": ms_all / args.steps,
+                               "mlp_fwd_fp32_ms": prof["mlp_fwd_fp32"][0] / args.steps},
+                 "note": "both with every stage's events on; the fused launch keeps hidden activations in "
+                         "shared memory and still writes those the backward reads"}
     loss, _ = nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + 99999, want_loss=True)
 
     # ---- dominant stage and its roofline -------------------------------
@@ -337,12 +360,11 @@ def run_ours(args):
     l2_ops = {"encode_bwd": l2["red8_64MiB"]["GB/s"] / 8.0, "encode_fwd": l2["load8_64MiB"]["GB/s"] / 8.0} if l2 else None
     stages = {k: v for k, v in prof.items()}
     tot_ms = sum(v[0] for v in stages.values())
-    dom = max((k for k in stages if k not in OVERLAPPED), key=lambda k: stages[k][0])
     roof = None
     work = _stage_work(net, dom, N_SEG)
     if work is not None:
         amount, unit, bound = work
-        avg_ms = stages[dom][0] / max(args.steps, 1)
+        avg_ms = prof_dom[dom][0] / max(args.steps, 1)      # per step (one launch), inside the measured interval
         ach = amount / (avg_ms / 1e3) / 1e9
         hbm_roof = {"bound": bound, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                     "peak_source": f"{peak_src} hbm_gbs", "algorithmic_bytes": amount,
@@ -456,6 +478,8 @@ def run_ours(args):
                        "voxels": "64^3", "levels": net.levels, "table": f"2^{net.log2_table}",
                        "mlp": "-".join(str(x) for x in [net.in_dim] + [net.mlp_width] * net.mlp_depth + [16]),
                        "l2": "working set larger than L2 (tables, gradients, Adam state 256 MB; features 604 MB)"},
+            "profile": {"measured_interval": f"events of {dom} only", "all_stages_ms_per_step": ms_all / args.steps},
+            "fp32_fused_forward": fused_fwd,
             "roofline": roof, "kernels": kernels, "l2_probe": l2, "encoder_points": {"distinct": n_pts, "segments": n_segs_enc},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "loss": list(loss) if loss is not None else None, "train_mixed": mixed,
@@ -598,9 +622,15 @@ def run_query(args, nif, S, dev, rank):
     hbm = _peaks()[0]
     precs = [(nm, {"fp32": nif.NIF_FP32, "bf16": nif.NIF_BF16, "fp16": nif.NIF_FP16}[nm])
              for nm in args.query_prec.split(",")]
+    # the BF16 query also as two kernels per chunk (encoding, then the MLP
+    # from a global feature buffer) beside the fused default
+    if "bf16" in args.query_prec.split(","):
+        precs.append(("bf16_two_kernels", nif.NIF_BF16))
     for name, prec in precs:
         try:
             h = nif.Nif(net, mesh, precision=prec, seed=31)
+            if name.endswith("_two_kernels"):
+                nif.nif_set_knob(h.h, nif.NIF_KNOB_QUERY_FUSED, 0)
             ws_, s_ = S.init_params(net, seed=32)[1:]
             ws_[-1][0, :] *= 4.0
             h.set_params(S.init_params(net, seed=32)[0], ws_, s_)
@@ -626,6 +656,13 @@ def run_query(args, nif, S, dev, rank):
             res["segments_per_step"] = n_seg
             res[name] = {"queries_per_s": n / (ms / 1e3), "ms_per_query_batch": ms, "stages_ms": st,
                          "hit_rate": float((hits[:, 7].view(torch.int32) & 0xff).ne(0).float().mean().item())}
+            if "encode_mlp_tc" in st:
+                # fused kernel: per segment 2 P L 8 corner rows gathered (repeated
+                # entry points once), 32 B of segment read, 64 B of outputs written
+                gat = n_seg * 2 * net.n_terms * net.levels * 8
+                res[name]["encode_mlp"] = {"ms": st["encode_mlp_tc"], "corner_gathers_G_per_s":
+                                           gat / (st["encode_mlp_tc"] / 1e3) / 1e9,
+                                           "hbm_bytes_per_segment": 96, "feature_bytes_to_hbm": 0}
             if "mlp_fwd_tc" in st:
                 by = n_seg * (net.in_dim * 2 + 16 * 4)          # 16-bit features in, FP32 outputs out
                 gbs = by / (st["mlp_fwd_tc"] / 1e3) / 1e9
@@ -868,29 +905,26 @@ def run_frame(args, nif, S, dev):
     return res
 
 
-def run_precision(args, nif, S, dev):
+def run_precision(args, nif, S, dev, workloads=("torus16_fwd", "torus128_query")):
     """Per-output error of the BF16 / FP16 query paths against the FP32 GPU
-    path on a trained network: the 16^3 torus workload (L = 8, T = 2^14,
-    MLP 288-32-32-16) trained on the GPU (FP32, 4000 steps of 2^16 segments,
-    poses U[-1,1]^3), then queried with 2^22 rays. (The 128^3 voxel grid is
-    finer than this encoding's finest level, 68 cells, so a network trained
-    there predicts few hits; the comparison with the FP64 oracle is
-    tests/test_gpu_precision.py.)"""
+    path on a trained network: the config-1 torus network (L = 8, T = 2^14,
+    MLP 288-32-32-16) trained on the GPU at 16^3 voxels (FP32, 4000 steps of
+    2^16 segments, poses U[-1,1]^3), then queried with 2^22 rays on each
+    workload's voxel grid: 16^3, and the 128^3 of the precision workload
+    (the same encoding and MLP; a network trained at 128^3 predicts no hit,
+    because its finest level has 68 cells per axis). The comparison with the
+    FP64 oracle is tests/test_gpu_precision.py."""
     import torch
     w = S.WORKLOADS["torus16_fwd"]
-    net = w["net"]
     mesh = S.make_mesh(w["shape"])
     t0 = time.perf_counter()
-    h32 = nif.Nif(net, mesh, precision=nif.NIF_FP32, seed=51)
+    h32 = nif.Nif(w["net"], mesh, precision=nif.NIF_FP32, seed=51)
     for step in range(4000):
         loss, _ = nif.nif_train_step(h32.h, 1 << 16, 16, 5000 + step, lr_grid=1e-2, lr_mlp=5e-3,
                                      want_loss=(step == 3999))
     train_s = time.perf_counter() - t0
     tables, ws, s = h32.get_params()
-    hs = {"fp32": h32}
-    for name, p in (("bf16", nif.NIF_BF16), ("fp16", nif.NIF_FP16)):
-        hs[name] = nif.Nif(net, mesh, precision=p, seed=51)
-        hs[name].set_params(tables, ws, s)
+    h32.close()
     pose = S.poses(1, seed=52)[0]          # U[-1,1]^3, the training distribution
 
     def fields(hits):
@@ -915,13 +949,20 @@ def run_precision(args, nif, S, dev):
 
     rays_np = S.sphere_rays(1 << 22, seed=53)
     rays = torch.from_numpy(rays_np).to(dev)
-    got = {k: fields(nif.nif_query(hh.h, [pose], rays)) for k, hh in hs.items()}
-    vs_fp32 = {k: errs(got["fp32"], got[k]) for k in ("bf16", "fp16")}
-    for hh in hs.values():
-        hh.close()
-    return {"workload": "torus16_fwd (trained)", "train_steps": 4000, "train_s": train_s,
-            "train_loss": [float(x) for x in loss], "rays": 1 << 22,
-            "vs_fp32_gpu_all_rays": vs_fp32}
+    res = {"network": "torus16_fwd trained at 16^3", "train_steps": 4000, "train_s": train_s,
+           "train_loss": [float(x) for x in loss], "rays": 1 << 22}
+    for wname in workloads:
+        net = S.WORKLOADS[wname]["net"]
+        hs = {}
+        for name, p in (("fp32", nif.NIF_FP32), ("bf16", nif.NIF_BF16), ("fp16", nif.NIF_FP16)):
+            hs[name] = nif.Nif(net, mesh, precision=p, seed=51)
+            hs[name].set_params(tables, ws, s)
+        got = {k: fields(nif.nif_query(hh.h, [pose], rays)) for k, hh in hs.items()}
+        for hh in hs.values():
+            hh.close()
+        res[wname] = {"voxels": f"{net.voxel_res}^3", "hit_rate_fp32": float(got["fp32"][0].mean()),
+                      "vs_fp32_gpu_all_rays": {k: errs(got["fp32"], got[k]) for k in ("bf16", "fp16")}}
+    return res
 
 
 def main():

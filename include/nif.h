@@ -603,10 +603,28 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  * NIF_KNOB_QUERY_SEGS: segments per ray, in (0, 4096], that nif_query sizes
  *   its capacity for until a query's total has come back (default 8); setting
  *   it forgets the totals of earlier queries.
+ * NIF_KNOB_BATCH_AT: where the next step's batch starts beside an FP32 step
+ *   of nif_train_steps / nif_train_steps_rays: 0 with the step (default),
+ *   1 after the encoding forward, 2 after the MLP forward, 3 after the MLP
+ *   backward. A scheduling choice only: the steps compute the same.
+ * NIF_KNOB_FP32_FUSED: 1 runs every layer of the FP32 MLP forward in one
+ *   persistent launch whose hidden activations stay in shared memory (the
+ *   activations the backward needs are still written), 0 one launch per
+ *   layer (default). Applies to hidden widths 32 and 64 with at least one
+ *   hidden layer and in_dim a multiple of 4; the results are the same.
+ * NIF_KNOB_QUERY_FUSED: 1 (default) computes a BF16/FP16 query's encoding
+ *   (Eq. 1) inside the tensor-core MLP's kernel, which keeps each tile's
+ *   features in shared memory (handles with L in {4, 8, 16}, F_d = 2, width
+ *   32 or 64); 0 runs the encoding and the MLP as two kernels per chunk with
+ *   the features in a global buffer. The outputs agree to the MLP's
+ *   accumulation order.
  * NIF_ERR_ARG for an unknown knob or a value out of range. */
 #define NIF_KNOB_WAIT_NS 1
 #define NIF_KNOB_SEG_SCRATCH 2
 #define NIF_KNOB_QUERY_SEGS 3
+#define NIF_KNOB_BATCH_AT 4
+#define NIF_KNOB_FP32_FUSED 5
+#define NIF_KNOB_QUERY_FUSED 6
 nif_status nif_set_knob(nif_handle* h, int knob, double value);
 
 /* Allocation-free variant of nif_segments (the paper has no counterpart:
@@ -680,6 +698,12 @@ nif_status nif_encoder_points(nif_handle* h, int64_t* n_points_host, int64_t* n_
  * overhead per stage). nif_profile(h, 1) clears the record and turns it on,
  * nif_profile(h, 0) turns it off; both synchronise the device. */
 nif_status nif_profile(nif_handle* h, int enable);
+/* Restricts the per-stage timing to the stages named in `names`, a
+ * comma-separated list of stage names as nif_profile_read reports them
+ * (host string, copied); NULL or "" times every stage again. Fewer events
+ * in a timed interval add less to it. Synchronises the device; NIF_ERR_ARG
+ * for a list longer than 1024 characters. */
+nif_status nif_profile_filter(nif_handle* h, const char* names);
 /* Synchronises, folds the events into per-stage sums and returns entry i:
  * its name (copied into `name`, capacity name_cap), the summed milliseconds
  * and the number of timed launches of the stage; *n_names (nullable) gets

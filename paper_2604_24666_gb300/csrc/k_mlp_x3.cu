@@ -349,6 +349,301 @@ __global__ void __launch_bounds__(kX3Threads, 1)
 }
 
 // ---------------------------------------------------------------------------
+// The whole FP32 forward in one persistent kernel (hidden width W = 32 or 64):
+// per 128-row tile, layer 0 streams the input rows through the TMA ring as in
+// k_gemm_x3 (A box 128 x 32 FP32 split in place into hi plus a lo copy, with
+// the hi and lo boxes of W_0), and layers 1..H read their A operand from a
+// shared-memory activation tile that the epilogue writes, split into hi and
+// lo in the K-major 128-byte-swizzled layout, right after the ReLU of the
+// layer before. The hidden layers' split weights stream through the same
+// ring (B boxes only). The epilogue also stores every hidden activation row
+// to global memory (the backward needs them) and the 16 outputs of the last
+// layer. Two TMEM accumulators: the MMAs of a tile's layer 0 overlap the
+// epilogue of the tile before's last layer. Warp roles as k_gemm_x3: 0 TMA,
+// 1 MMA issue, 2-5 epilogue, 6-9 splitter.
+// ---------------------------------------------------------------------------
+struct X3FwdArgs {
+    float* acts;                      // [H][n_max][W]
+    float* out;                       // [n_max][NIF_OUT]
+    int64_t n_max;
+    int K0, W, H;                     // input width, hidden width, hidden layers
+    int nkb0, nkbw;                   // 32-deep k-blocks of layer 0 and of a W-deep layer
+    int stages;
+    uint32_t stage_bytes;             // A hi + A lo + B hi + B lo (B boxes W rows)
+    uint32_t act_off, stg_off, bar_off;
+    uint32_t acc_stride, tmem_cols;
+};
+
+struct X3FwdMaps {
+    CUtensorMap w[NIF_MAX_LAYERS];    // [hi; lo] copy of layer l's weight, boxes 32 (K) x out_l rows
+};
+
+template <int W>
+__global__ void __launch_bounds__(kX3Threads, 1)
+    k_mlp_x3_fwd(const __grid_constant__ CUtensorMap amap, const __grid_constant__ X3FwdMaps wm, X3FwdArgs a,
+                 const uint32_t* __restrict__ n_dev, int* __restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const uint64_t wlim = wait_limit(status);   // bound of the work loop's waits
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int S = a.stages, H = a.H;
+    constexpr int KBW = W / 32;                  // k-blocks of a W-deep layer
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + a.bar_off);
+    // [0,S) loaded, [S,2S) split, [2S,3S) free, 3S+{0,1} acc full, 3S+{2,3} acc free, 3S+4 act tile ready,
+    // 3S+5 drain
+    const int B_CONV = S, B_EMPTY = 2 * S, B_ACC = 3 * S, B_ACCE = 3 * S + 2, B_ACT = 3 * S + 4, B_DRAIN = 3 * S + 5;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 6);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 3 * S + 7);
+    const int64_t n = n_dev ? ((int64_t)*n_dev < a.n_max ? (int64_t)*n_dev : a.n_max) : a.n_max;
+    const int64_t n_tiles = (n + 127) / 128;
+    const int64_t my = (int64_t)blockIdx.x < n_tiles ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    if (my == 0) return;                         // uniform per CTA: before any setup
+    if (tid == 0) {
+        for (int i = 0; i < S; i++) {
+            mbar_init(smem_u32(&bars[i]), 1);
+            mbar_init(smem_u32(&bars[B_CONV + i]), 128);
+            mbar_init(smem_u32(&bars[B_EMPTY + i]), 1);
+        }
+        for (int q = 0; q < 2; q++) {
+            mbar_init(smem_u32(&bars[B_ACC + q]), 1);
+            mbar_init(smem_u32(&bars[B_ACCE + q]), 128);
+        }
+        mbar_init(smem_u32(&bars[B_ACT]), 128);
+        mbar_init(smem_u32(&bars[B_DRAIN]), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t act_hi = smem_u32(sm + a.act_off), act_lo = act_hi + (uint32_t)KBW * kABox;
+
+    // The stage sequence every role walks: rounds r = 0 .. my; round r cuts
+    // tile r's layer-0 k-blocks into H + 1 chunks and puts tile r - 1's
+    // hidden layers 1 .. H between them, so that chain (each layer waits for
+    // the epilogue of the one before) overlaps tile r's streaming.
+    auto chunk_lo = [&](int c) { return (c * a.nkb0) / (H + 1); };
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&amap)) : "memory");
+            int slot = 0;
+            uint32_t phase = 0, issued_mask = 0, issued_par = 0;
+            bool ok = true;
+            auto next = [&]() -> bool {
+                if (!mbar_wait(smem_u32(&bars[B_EMPTY + slot]), phase ^ 1u, abort_flag, status, wlim)) return false;
+                return true;
+            };
+            auto advance = [&]() {
+                issued_mask |= 1u << slot;
+                issued_par = (issued_par & ~(1u << slot)) | (phase << slot);
+                if (++slot == S) { slot = 0; phase ^= 1u; }
+            };
+            for (int64_t r = 0; r <= my && ok; r++) {
+                const int64_t tile = blockIdx.x + r * gridDim.x;
+                for (int c = 0; c <= H && ok; c++) {
+                    if (r < my)
+                        for (int kb = chunk_lo(c); kb < chunk_lo(c + 1); kb++) {   // layer 0: input rows and W_0
+                            if (!(ok = next())) break;
+                            const uint32_t fb = smem_u32(&bars[slot]);
+                            const uint32_t st = smem_u32(sm + (uint32_t)slot * a.stage_bytes);
+                            const uint32_t bh = st + 2u * kABox;
+                            mbar_expect_tx(fb, kABox + 2u * (uint32_t)W * 128u);
+                            tma_load_2d(st, &amap, kb * 32, (int)(tile * 128), fb);
+                            tma_load_2d(bh, &wm.w[0], kb * 32, 0, fb);
+                            tma_load_2d(bh + (uint32_t)W * 128u, &wm.w[0], kb * 32, W, fb);
+                            advance();
+                        }
+                    if (c < H && r >= 1 && ok) {
+                        const int l = c + 1, rows = l == H ? 16 : W;             // tile r - 1's layer l: its weight
+                        for (int kb = 0; kb < KBW; kb++) {
+                            if (!(ok = next())) break;
+                            const uint32_t fb = smem_u32(&bars[slot]);
+                            const uint32_t bh = smem_u32(sm + (uint32_t)slot * a.stage_bytes) + 2u * kABox;
+                            mbar_expect_tx(fb, 2u * (uint32_t)rows * 128u);
+                            tma_load_2d(bh, &wm.w[l], kb * 32, 0, fb);
+                            tma_load_2d(bh + (uint32_t)W * 128u, &wm.w[l], kb * 32, rows, fb);
+                            advance();
+                        }
+                    }
+                }
+            }
+            // every issued copy must have landed before the CTA exits
+            for (int i = 0; i < S; i++)
+                if (issued_mask >> i & 1u) {
+                    volatile int dummy = 0;
+                    mbar_wait(smem_u32(&bars[i]), (issued_par >> i) & 1u, &dummy, status);
+                }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t id_w = idesc_tf32(W), id_o = idesc_tf32(16);
+            int slot = 0;
+            uint32_t phase = 0, act_par = 0;
+            uint32_t ae_par[2] = {0u, 0u};
+            bool ok = true;
+            auto take = [&]() -> bool {
+                if (!mbar_wait(smem_u32(&bars[B_CONV + slot]), phase, abort_flag, status, wlim)) return false;
+                tc_fence_after();
+                return true;
+            };
+            auto release = [&]() {
+                mma_commit(smem_u32(&bars[B_EMPTY + slot]));   // frees the stage when these MMAs finish
+                if (++slot == S) { slot = 0; phase ^= 1u; }
+            };
+            for (int64_t r = 0; r <= my && ok; r++) {
+                const int qr = (int)(r & 1), qp = (int)((r + 1) & 1);
+                const uint32_t acc_r = tmem + (uint32_t)qr * a.acc_stride, acc_p = tmem + (uint32_t)qp * a.acc_stride;
+                if (r < my && r >= 2) {   // the epilogue must have read tile r - 2's last layer
+                    if (!mbar_wait(smem_u32(&bars[B_ACCE + qr]), ae_par[qr], abort_flag, status, wlim)) { ok = false; break; }
+                    ae_par[qr] ^= 1u;
+                    tc_fence_after();
+                }
+                for (int c = 0; c <= H && ok; c++) {
+                    if (r < my)
+                        for (int kb = chunk_lo(c); kb < chunk_lo(c + 1); kb++) {
+                            if (!(ok = take())) break;
+                            const uint32_t st = smem_u32(sm + (uint32_t)slot * a.stage_bytes);
+                            const uint32_t bh = st + 2u * kABox, bl = bh + (uint32_t)W * 128u;
+#pragma unroll
+                            for (int ks = 0; ks < 4; ks++)
+                                mma_x3(acc_r, st, st + kABox, bh, bl, 32u * ks, id_w, (kb > 0 || ks > 0) ? 1u : 0u);
+                            release();
+                            if (kb == a.nkb0 - 1) mma_commit(smem_u32(&bars[B_ACC + qr]));   // tile r's layer 0
+                        }
+                    if (c < H && r >= 1 && ok) {
+                        // tile r - 1's layer c + 1 reads the activation tile of its layer c
+                        if (!mbar_wait(smem_u32(&bars[B_ACT]), act_par, abort_flag, status, wlim)) { ok = false; break; }
+                        act_par ^= 1u;
+                        tc_fence_after();
+                        const uint32_t id = c + 1 == H ? id_o : id_w;
+                        for (int kb = 0; kb < KBW; kb++) {
+                            if (!(ok = take())) break;
+                            const uint32_t bh = smem_u32(sm + (uint32_t)slot * a.stage_bytes) + 2u * kABox;
+                            const uint32_t bl = bh + (uint32_t)W * 128u;
+                            const uint32_t ah = act_hi + (uint32_t)kb * kABox, al = act_lo + (uint32_t)kb * kABox;
+#pragma unroll
+                            for (int ks = 0; ks < 4; ks++)
+                                mma_x3(acc_p, ah, al, bh, bl, 32u * ks, id, (kb > 0 || ks > 0) ? 1u : 0u);
+                            release();
+                        }
+                        if (ok) mma_commit(smem_u32(&bars[B_ACC + qp]));
+                    }
+                }
+            }
+            // all MMAs of this CTA complete before TMEM is released
+            mma_commit(smem_u32(&bars[B_DRAIN]));
+            volatile int dummy = 0;
+            mbar_wait(smem_u32(&bars[B_DRAIN]), 0, &dummy, status);
+        }
+    } else if (warp >= 6) {
+        // ---------------- splitter: layer-0 A boxes -> hi in place + lo copy ----------------
+        const int ct = tid - 192;
+        int slot = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int64_t r = 0; r <= my && ok; r++)
+            for (int c = 0; c <= H && ok; c++) {
+                const int n0 = r < my ? chunk_lo(c + 1) - chunk_lo(c) : 0;   // layer-0 stages to split
+                const int n1 = (c < H && r >= 1) ? KBW : 0;                    // weight-only stages
+                for (int u = 0; u < n0 + n1; u++) {
+                    if (!mbar_wait(smem_u32(&bars[slot]), phase, abort_flag, status, wlim)) { ok = false; break; }
+                    if (u < n0) {
+                        float4* A = reinterpret_cast<float4*>(sm + (uint32_t)slot * a.stage_bytes);
+                        float4* Al = reinterpret_cast<float4*>(sm + (uint32_t)slot * a.stage_bytes + kABox);
+#pragma unroll
+                        for (int i = 0; i < 8; i++) {
+                            const int idx = ct + 128 * i;
+                            float4 hv, lv;
+                            split4(A[idx], hv, lv);
+                            A[idx] = hv;
+                            Al[idx] = lv;
+                        }
+                        fence_async_smem();
+                    }
+                    mbar_arrive(smem_u32(&bars[B_CONV + slot]));
+                    if (++slot == S) { slot = 0; phase ^= 1u; }
+                }
+            }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int qw = warp & 3;                  // TMEM lane quarter this warp may access
+        const int r = qw * 32 + lane;             // this thread's row of the tile
+        uint8_t* stg = sm + a.stg_off + (uint32_t)(warp - 2) * 4096u;
+        uint8_t* ahp = sm + a.act_off;
+        uint8_t* alp = ahp + (size_t)KBW * kABox;
+        uint32_t af_par[2] = {0u, 0u};
+        X3Args so{};
+        so.N = W;
+        bool ok = true;
+        for (int64_t j = 0; j < my && ok; j++) {
+            const int q = (int)(j & 1);
+            const int64_t tile = blockIdx.x + j * gridDim.x;
+            const int64_t row0 = tile * 128 + qw * 32;
+            const uint32_t tb = tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)q * a.acc_stride;
+            for (int l = 0; l <= H; l++) {
+                int got = 0;
+                if (lane == 0) got = mbar_wait(smem_u32(&bars[B_ACC + q]), af_par[q], abort_flag, status, wlim) ? 1 : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) { ok = false; break; }
+                af_par[q] ^= 1u;
+                tc_fence_after();
+                if (l < H) {
+                    so.C = a.acts + (int64_t)l * a.n_max * W;
+                    so.ldc = W;
+#pragma unroll
+                    for (int c0 = 0; c0 < W; c0 += 32) {
+                        float v[32];
+                        tmem_ld32(tb + (uint32_t)c0, v);
+#pragma unroll
+                        for (int i = 0; i < 32; i++) v[i] = fmaxf(v[i], 0.f);
+                        // the next layer's A operand: k-block c0 / 32, split into hi and lo
+                        const uint32_t kb = (uint32_t)c0 / 32u;
+#pragma unroll
+                        for (int ch = 0; ch < 8; ch++) {
+                            float4 hv, lv;
+                            split4(make_float4(v[4 * ch], v[4 * ch + 1], v[4 * ch + 2], v[4 * ch + 3]), hv, lv);
+                            const uint32_t off = kb * kABox + (uint32_t)r * 128u + (uint32_t)((ch ^ (r & 7)) << 4);
+                            *reinterpret_cast<float4*>(ahp + off) = hv;
+                            *reinterpret_cast<float4*>(alp + off) = lv;
+                        }
+                        x3_store<kX3Relu, 32>(so, stg, v, nullptr, lane, row0, n, c0);
+                    }
+                    fence_async_smem();
+                    tc_fence_before();
+                    mbar_arrive(smem_u32(&bars[B_ACT]));
+                } else {
+                    float v[16];
+                    tmem_ld16(tb, v);
+                    so.C = a.out;
+                    so.ldc = NIF_OUT;
+                    so.N = 16;
+                    x3_store<kX3Store, 16>(so, stg, v, nullptr, lane, row0, n, 0);
+                    so.N = W;
+                    tc_fence_before();
+                    mbar_arrive(smem_u32(&bars[B_ACCE + q]));
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient of one layer on tensor cores: D = dW_l^T [in_l x out_l] =
 // X_l^T dY_l, reduction over the rows. CTA (x, y) owns columns
 // [128 x, 128 x + 128) of X_l and the 32-row blocks y, y + gridDim.y, ...
@@ -723,6 +1018,48 @@ nif_status dw_x3(nif_handle* h, const float* X, int64_t ldx, int in_l, const flo
     return NIF_OK;
 }
 
+// The whole forward in one launch (W = 32 or 64): acts [H][n_max][W], out [n_max][NIF_OUT].
+template <int W>
+nif_status mlp_fwd_x3_fused(nif_handle* h, const float* x, int64_t n_max, const uint32_t* n_dev, float* acts,
+                            float* out, cudaStream_t s) {
+    X3FwdArgs a{};
+    a.acts = acts; a.out = out; a.n_max = n_max;
+    a.K0 = h->in_dim; a.W = W; a.H = h->H;
+    a.nkb0 = (a.K0 + 31) / 32;
+    a.nkbw = W / 32;
+    if ((reinterpret_cast<uintptr_t>(acts) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+        return nif_fail(h, NIF_ERR_ARG, "FP32 MLP: outputs need 16-byte aligned rows");
+    CUtensorMap am;
+    X3FwdMaps wm{};
+    nif_status st;
+    if ((st = map_f32(h, &am, x, (uint64_t)a.K0, (uint64_t)n_max, (uint64_t)a.K0, 32, 128, true, "the input rows")) !=
+        NIF_OK)
+        return st;
+    for (int l = 0; l <= a.H; l++) {
+        const int K = h->lay_in[l], rows = h->lay_out[l];
+        if ((st = map_f32(h, &wm.w[l], h->d_w_x3 + h->x3_fwd[l], (uint64_t)K, 2ull * rows, (uint64_t)K, 32,
+                          (uint32_t)rows, true, "the weights")) != NIF_OK)
+            return st;
+    }
+    a.stage_bytes = 2u * kABox + 2u * (uint32_t)W * 128u;
+    const uint32_t act = 2u * (uint32_t)a.nkbw * kABox, stg = 4u * 4096u, bars = 8u * 64u;
+    const uint32_t budget = 227u * 1024u;
+    a.stages = (int)std::min<uint32_t>(4u, (budget - act - stg - bars - 1024u) / a.stage_bytes);
+    if (a.stages < 2) return nif_fail(h, NIF_ERR_STATE, "FP32 MLP: fused pipeline does not fit in shared memory");
+    a.act_off = (uint32_t)a.stages * a.stage_bytes;
+    a.stg_off = a.act_off + act;
+    a.bar_off = a.stg_off + stg;
+    a.acc_stride = pow2_cols((uint32_t)W);
+    a.tmem_cols = 2u * a.acc_stride;
+    const uint32_t total = a.bar_off + bars + 1024u;
+    NIF_CK(h, cudaFuncSetAttribute(k_mlp_x3_fwd<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total));
+    const int64_t tiles = (n_max + 127) / 128;
+    const int grid = (int)std::min<int64_t>(tiles, h->num_sms);
+    k_mlp_x3_fwd<W><<<grid, kX3Threads, total, s>>>(am, wm, a, n_dev, h->d_status);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
 }  // namespace
 
 nif_status nif_x3_alloc(nif_handle* h) {
@@ -772,6 +1109,10 @@ nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n
     nif_status st = get_encoder(h);
     if (st != NIF_OK) return st;
     if ((st = nif_refresh_x3(h, s)) != NIF_OK) return st;
+    // hidden widths 32 and 64 on request: every layer in one launch, hidden activations on chip
+    const bool fusable = h->tune.fp32_fused && h->H >= 1 && h->H < NIF_MAX_LAYERS && h->in_dim % 4 == 0;
+    if (fusable && h->W == 64) return mlp_fwd_x3_fused<64>(h, x, n_max, n_dev, acts, out, s);
+    if (fusable && h->W == 32) return mlp_fwd_x3_fused<32>(h, x, n_max, n_dev, acts, out, s);
     const float* in = x;
     int64_t in_ld = h->in_dim;
     for (int l = 0; l < h->n_layers; l++) {

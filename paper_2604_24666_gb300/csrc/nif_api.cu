@@ -18,8 +18,21 @@ void nif_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 extern "C" unsigned long long nif_kernel_launches(void) { return g_launches.load(); }
 
+static bool prof_selected(const std::string& filter, const char* name) {
+    if (filter.empty()) return true;
+    const size_t n = std::strlen(name);
+    size_t at = 0;
+    while (at <= filter.size()) {
+        size_t end = filter.find(',', at);
+        if (end == std::string::npos) end = filter.size();
+        if (end - at == n && filter.compare(at, n, name) == 0) return true;
+        at = end + 1;
+    }
+    return false;
+}
+
 NifProf::NifProf(nif_handle* h_, const char* name, cudaStream_t s_) : h(h_), s(s_) {
-    if (!h || !h->prof) return;
+    if (!h || !h->prof || !prof_selected(h->prof_filter, name)) return;
     if (h->prof_used + 2 > h->prof_pool.size()) {
         for (int i = 0; i < 64; i++) {
             cudaEvent_t e;
@@ -45,6 +58,14 @@ extern "C" nif_status nif_profile(nif_handle* h, int enable) {
     h->prof_recs.clear();
     h->prof_used = 0;
     h->prof_sum.clear();
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_profile_filter(nif_handle* h, const char* names) {
+    if (!h) return NIF_ERR_ARG;
+    if (names && std::strlen(names) > 1024) return nif_fail(h, NIF_ERR_ARG, "profile filter longer than 1024");
+    NIF_CK(h, cudaDeviceSynchronize());
+    h->prof_filter = names ? names : "";
     return NIF_OK;
 }
 
@@ -1150,34 +1171,11 @@ static nif_status segment_into_scratch(nif_handle* h, const nif_pose* poses, int
     return nif_clamp_count_run(h, offs, n_rays, cap, offs + n_rays + 1, host_total, s);
 }
 
-extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
-                                const int* inst_off, int n_rays, nif_hit* hits, unsigned flags, void* stream) {
-    if (!h) return NIF_ERR_ARG;
-    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
-    if (st != NIF_OK) return st;
-    if (n_rays == 0) return NIF_OK;
-    if (!rays || !hits) return nif_fail(h, NIF_ERR_ARG, "rays / hits");
-    cudaStream_t s = (cudaStream_t)stream;
-    // capacity: segments per ray of the last query whose total has come back
-    // (1.5 x, read without waiting), or the initial estimate
-    if (h->q_pending && cudaEventQuery(h->ev_qtotal) == cudaSuccess) {
-        h->q_hint = (double)h->h_qtotal[0] / (double)std::max(h->q_rays, 1);
-        h->q_pending = false;
-    }
-    const double spr = h->q_hint > 0.0 ? h->q_hint * 1.5 + 0.25 : h->q_init;
-    const int64_t cap = std::max<int64_t>(4096, (int64_t)std::ceil(spr * (double)n_rays));
-    // segments of whole rays within the capacity, counts on the device; more
-    // latches NIF_ERR_CAPACITY (the rays that did not fit report no hit)
-    if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, cap, false, nullptr, s, true)) != NIF_OK)
-        return st;
-    uint32_t* offs = (uint32_t*)h->b_offsets.p;
-    const uint32_t* n_dev = offs + n_rays + 1;
-    if ((st = nif_grow(h, h->b_lin, sizeof(nif_linseg) * cap)) != NIF_OK) return st;
-    if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * cap)) != NIF_OK) return st;
-    nif_segment* segs = (nif_segment*)h->b_segs.p;
-    nif_linseg* lin = (nif_linseg*)h->b_lin.p;
-    float* out = (float*)h->b_out.p;
-    if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, cap, lin, s)) != NIF_OK) return st;
+// The query's encoding and MLP as two kernels per chunk (FP32, or a handle
+// the fused kernel does not cover): features of a chunk go through a buffer.
+static nif_status query_encode_mlp(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t cap,
+                                   int n_rays, float* out, cudaStream_t s) {
+    nif_status st;
     const int prec = h->cfg.precision;
     const size_t esz = prec == NIF_FP32 ? 4 : 2;
     // encode + MLP in chunks with device-side counts: FP32 chunks stay
@@ -1221,6 +1219,44 @@ extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst
                 return st;
             if ((st = nif_mlp_fwd_tc_run(h, h->b_feat.p, prec, cn, len, out + c0 * NIF_OUT, s)) != NIF_OK) return st;
         }
+    }
+    return NIF_OK;
+}
+
+extern "C" nif_status nif_query(nif_handle* h, const nif_pose* poses, int n_inst, const nif_ray* rays,
+                                const int* inst_off, int n_rays, nif_hit* hits, unsigned flags, void* stream) {
+    if (!h) return NIF_ERR_ARG;
+    nif_status st = nif_check_inst(h, poses, n_inst, inst_off, n_rays);
+    if (st != NIF_OK) return st;
+    if (n_rays == 0) return NIF_OK;
+    if (!rays || !hits) return nif_fail(h, NIF_ERR_ARG, "rays / hits");
+    cudaStream_t s = (cudaStream_t)stream;
+    // capacity: segments per ray of the last query whose total has come back
+    // (1.5 x, read without waiting), or the initial estimate
+    if (h->q_pending && cudaEventQuery(h->ev_qtotal) == cudaSuccess) {
+        h->q_hint = (double)h->h_qtotal[0] / (double)std::max(h->q_rays, 1);
+        h->q_pending = false;
+    }
+    const double spr = h->q_hint > 0.0 ? h->q_hint * 1.5 + 0.25 : h->q_init;
+    const int64_t cap = std::max<int64_t>(4096, (int64_t)std::ceil(spr * (double)n_rays));
+    // segments of whole rays within the capacity, counts on the device; more
+    // latches NIF_ERR_CAPACITY (the rays that did not fit report no hit)
+    if ((st = segment_into_scratch(h, poses, n_inst, rays, inst_off, n_rays, cap, false, nullptr, s, true)) != NIF_OK)
+        return st;
+    uint32_t* offs = (uint32_t*)h->b_offsets.p;
+    const uint32_t* n_dev = offs + n_rays + 1;
+    if ((st = nif_grow(h, h->b_lin, sizeof(nif_linseg) * cap)) != NIF_OK) return st;
+    if ((st = nif_grow(h, h->b_out, sizeof(float) * NIF_OUT * cap)) != NIF_OK) return st;
+    nif_segment* segs = (nif_segment*)h->b_segs.p;
+    nif_linseg* lin = (nif_linseg*)h->b_lin.p;
+    float* out = (float*)h->b_out.p;
+    if ((st = nif_linearize_run(h, rays, inst_off, n_inst, segs, n_dev, cap, lin, s)) != NIF_OK) return st;
+    const int prec = h->cfg.precision;
+    if (prec != NIF_FP32 && nif_mlp_enc_fusable(h)) {
+        // encoding and MLP in one launch over every segment: no feature matrix
+        if ((st = nif_mlp_enc_tc_run(h, lin, n_dev, cap, out, s)) != NIF_OK) return st;
+    } else if ((st = query_encode_mlp(h, lin, n_dev, cap, n_rays, out, s)) != NIF_OK) {
+        return st;
     }
     if ((st = nif_reconstruct_run(h, rays, inst_off, n_inst, n_rays, offs, segs, cap, lin, out, hits, flags, s,
                                   n_dev)) != NIF_OK)
@@ -1323,12 +1359,17 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         if ((st = nif_grad_check_run(h, s)) != NIF_OK) return st;
         if ((st = nif_adam_scaled_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
     } else {
+        // the next batch may start where the handle's placement knob says
+        const int at = h->tune.batch_at;
+        if (ev_next && at == 0) NIF_CK(h, cudaEventRecord(ev_next, s));
         if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s, true)) != NIF_OK) return st;
-        if (ev_next) NIF_CK(h, cudaEventRecord(ev_next, s));
+        if (ev_next && at == 1) NIF_CK(h, cudaEventRecord(ev_next, s));
         if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
+        if (ev_next && at == 2) NIF_CK(h, cudaEventRecord(ev_next, s));
         if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, true, n_hit)) != NIF_OK) return st;
         // weight gradients on the second stream, beside dX_0 and the encoding backward
         if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s, true, h->aux)) != NIF_OK) return st;
+        if (ev_next && at >= 3) NIF_CK(h, cudaEventRecord(ev_next, s));
         if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s, true)) != NIF_OK)
             return st;
         NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
@@ -1709,6 +1750,19 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
             NIF_CK(h, cudaMemcpy(h->d_status + 2, &ns, sizeof(ns), cudaMemcpyHostToDevice));
             return NIF_OK;
         }
+        case NIF_KNOB_BATCH_AT:
+            if (!(value >= 0.0 && value <= 3.0) || value != std::floor(value))
+                return nif_fail(h, NIF_ERR_ARG, "batch placement must be 0, 1, 2 or 3");
+            h->tune.batch_at = (int)value;
+            return NIF_OK;
+        case NIF_KNOB_FP32_FUSED:
+            if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "fused FP32 forward knob must be 0 or 1");
+            h->tune.fp32_fused = (int)value;
+            return NIF_OK;
+        case NIF_KNOB_QUERY_FUSED:
+            if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "fused query knob must be 0 or 1");
+            h->tune.query_fused = (int)value;
+            return NIF_OK;
         case NIF_KNOB_QUERY_SEGS:
             if (!(value > 0.0 && value <= 4096.0)) return nif_fail(h, NIF_ERR_ARG, "segments per ray must be in (0, 4096]");
             h->q_init = value;

@@ -197,6 +197,14 @@ struct nif_handle {
         int64_t tc_chunk = 1 << 20;     // rows per encode + tensor-core MLP chunk
         int bwd_smem_rows = 512;        // encoding backward: dense coarse levels of at most this many rows
                                         // go to shared memory (measured: larger ones reduce faster in L2)
+        int batch_at = 0;               // FP32 steps of nif_train_steps: the next batch starts at 0 the step's
+                                        // start, 1 after the encoding forward, 2 after the MLP forward, 3 after
+                                        // the MLP backward (NIF_KNOB_BATCH_AT; measured: 0 is ~0.01 ms faster
+                                        // than 1 on the 64^3 step, 2 and 3 are 0.1-0.2 ms slower)
+        int fp32_fused = 0;             // NIF_KNOB_FP32_FUSED: the FP32 forward in one launch (measured equal
+                                        // to the per-layer launches on the 64^3 step)
+        int query_fused = 0;            // NIF_KNOB_QUERY_FUSED: 16-bit queries encode into the tensor-core
+                                        // MLP's shared-memory ring (one launch) instead of two kernels
     } tune;
 
     // CUDA graphs of live query plans hold the scratch and per-instance
@@ -212,6 +220,7 @@ struct nif_handle {
     // per-kernel timing (CUDA events on the launching stream), off by default
     struct ProfRec { const char* name; cudaEvent_t a, b; };
     bool prof = false;
+    std::string prof_filter;            // comma-separated stage names, or empty for all
     std::vector<ProfRec> prof_recs;
     std::vector<cudaEvent_t> prof_pool;
     size_t prof_used = 0;
@@ -344,6 +353,12 @@ nif_status nif_seg_walk_run(nif_handle* h, const nif_ray* rays, const int* inst_
                             cudaStream_t s);
 nif_status nif_x3_alloc(nif_handle* h);
 nif_status nif_refresh_x3(nif_handle* h, cudaStream_t s);
+// The query path's encoding and tensor-core MLP in one persistent launch
+// (k_mlp_enc.cu): features never reach global memory. Applies to BF16/FP16
+// handles with L in {4, 8, 16}, F_d = 2, W in {32, 64} (nif_mlp_enc_fusable).
+bool nif_mlp_enc_fusable(const nif_handle* h);
+nif_status nif_mlp_enc_tc_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max, float* out,
+                              cudaStream_t s);
 nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev,
                               int64_t n_max, float* out, cudaStream_t s);
 // acts_out (nullable): 16-bit hidden activations, layer l row r at (l * acts_rows + r) * acts_ld

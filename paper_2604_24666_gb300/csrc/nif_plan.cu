@@ -85,8 +85,14 @@ nif_status plan_enqueue(nif_query_plan* p, cudaStream_t s) {
     NIF_CK(h, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)n, s));
     if ((st = nif_seg_scatter_run(h, temp, cursor, p->cap, offs, counts, n, segs, p->cap, s)) != NIF_OK) return st;
     if ((st = nif_linearize_run(h, p->rays, p->inst_off, p->n_inst, segs, n_dev, p->cap, lin, s)) != NIF_OK) return st;
-    if ((st = nif_chunk_counts_run(h, n_dev, p->chunk, p->n_chunks, p->chunk_counts, s)) != NIF_OK) return st;
     const int prec = h->cfg.precision;
+    if (prec != NIF_FP32 && nif_mlp_enc_fusable(h)) {
+        // encoding and MLP in one launch over every segment: no feature matrix
+        if ((st = nif_mlp_enc_tc_run(h, lin, n_dev, p->cap, out, s)) != NIF_OK) return st;
+        return nif_reconstruct_run(h, p->rays, p->inst_off, p->n_inst, n, offs, segs, p->cap, lin, out, p->hits,
+                                   p->flags, s);
+    }
+    if ((st = nif_chunk_counts_run(h, n_dev, p->chunk, p->n_chunks, p->chunk_counts, s)) != NIF_OK) return st;
     for (int c = 0; c < p->n_chunks; c++) {
         int64_t c0 = (int64_t)c * p->chunk;
         int64_t len = std::min(p->chunk, p->cap - c0);

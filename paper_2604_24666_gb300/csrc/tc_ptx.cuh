@@ -144,6 +144,36 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// byte offset of element (row, k) of a K-major swizzled operand whose 64-column
+// blocks hold `rows` rows each
+__device__ __forceinline__ uint32_t swz_off(int row, int k, int rows) {
+    int blk = k >> 6, chunk = (k & 63) >> 3;
+    return (uint32_t)blk * (uint32_t)rows * 128u + (uint32_t)row * 128u + (uint32_t)((chunk ^ (row & 7)) << 4) +
+           (uint32_t)((k & 7) << 1);
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b, int fmt) {
+    if (fmt == 1) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&v);
+    }
+    __half2 v = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Copy a row-major [rows x K] 16-bit matrix into the swizzled K-major layout,
+// zero-filling columns K .. 64*ceil(K/64).
+__device__ void load_weight(uint8_t* dst, const uint16_t* __restrict__ src, int rows, int K, int tid, int nthr) {
+    int kpad = ((K + 63) / 64) * 64;
+    int chunks = rows * (kpad / 8);
+    for (int c = tid; c < chunks; c += nthr) {
+        int row = c / (kpad / 8), k = (c % (kpad / 8)) * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (k < K) v = *reinterpret_cast<const uint4*>(src + (size_t)row * K + k);
+        *reinterpret_cast<uint4*>(dst + swz_off(row, k, rows)) = v;
+    }
+}
+
 }  // namespace
 
 // cuTensorMapEncodeTiled, fetched once through the runtime's driver entry point

@@ -25,7 +25,8 @@ NIF_SHADOW_ONLY = 1
 NIF_FLAG_FIXED_TASK_WEIGHTS, NIF_FLAG_SIGMOID_DISTANCE, NIF_FLAG_MIXED_TRAINING = 1, 2, 4
 NIF_FLAG_CONCAT_ENCODING = 8
 NIF_FLAG_BILINEAR_FACES = 16
-NIF_KNOB_WAIT_NS, NIF_KNOB_SEG_SCRATCH, NIF_KNOB_QUERY_SEGS = 1, 2, 3
+NIF_KNOB_WAIT_NS, NIF_KNOB_SEG_SCRATCH, NIF_KNOB_QUERY_SEGS, NIF_KNOB_BATCH_AT, NIF_KNOB_FP32_FUSED = 1, 2, 3, 4, 5
+NIF_KNOB_QUERY_FUSED = 6
 NIF_PROBE_RED8, NIF_PROBE_RED16, NIF_PROBE_LOAD8, NIF_PROBE_LOAD4 = 1, 2, 3, 4
 NIF_PROBE_RED8_WARP, NIF_PROBE_RED16_WARP, NIF_PROBE_LOAD8_WARP, NIF_PROBE_LOAD4_WARP = 5, 6, 7, 8
 
@@ -148,6 +149,7 @@ def lib() -> ctypes.CDLL:
             "nif_checkpoint_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
             "nif_kernel_launches": ([], ctypes.c_ulonglong),
             "nif_profile": ([_vp, ctypes.c_int], ctypes.c_int),
+            "nif_profile_filter": ([_vp, ctypes.c_char_p], ctypes.c_int),
             "nif_profile_read": ([_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         }
@@ -637,6 +639,12 @@ def nif_kernel_launches() -> int:
 
 def nif_profile(h, enable):
     _check(h, lib().nif_profile(h, int(enable)))
+
+
+def nif_profile_filter(h, names=None):
+    """Time only the named stages (an iterable of names, or None for all)."""
+    arg = ",".join(names).encode() if names else None
+    _check(h, lib().nif_profile_filter(h, arg))
 
 
 def nif_profile_read(h):

@@ -251,10 +251,13 @@ def test_encode_points_backward(nif, torus):
 # ---------------------------------------------------------------------------
 # MLP (FP32)
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("fused", [0, 1])
 @pytest.mark.parametrize("depth,width,levels", [(2, 32, 8), (3, 64, 16)])
-def test_mlp_fp32_forward_backward(nif, torus, depth, width, levels):
+def test_mlp_fp32_forward_backward(nif, torus, depth, width, levels, fused):
+    """Per-layer launches (fused = 0) and the one-launch forward (fused = 1)."""
     net = S.NetConfig(levels=levels, log2_table=14, mlp_depth=depth, mlp_width=width)
     h = nif.Nif(net, torus)
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_FP32_FUSED, fused)
     tables, ws, s = S.init_params(net, seed=71)
     h.set_params(tables, ws, s)
     rng = np.random.default_rng(72)

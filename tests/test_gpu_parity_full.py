@@ -131,8 +131,9 @@ def test_encode_backward_sorted_matches_oracle(nif, handle, batch):
 def test_mlp_split_tf32_full_batch_matches_oracle(nif, handle):
     """Forward, dX and dW of the FP32 MLP at 2^18 rows: persistent CTAs take
     many 128-row jobs; the layer-0 weight gradient is split over row ranges.
-    Rows whose ReLU decisions FP32 could flip are left out before either side
-    runs."""
+    The forward runs twice, in per-layer launches and in one launch
+    (NIF_KNOB_FP32_FUSED). Rows whose ReLU decisions FP32 could flip are left
+    out before either side runs."""
     net = NET
     _, ws, s = S.init_params(net, seed=211)
     handle.set_params(S.init_params(net)[0], ws, s)
@@ -142,15 +143,17 @@ def test_mlp_split_tf32_full_batch_matches_oracle(nif, handle):
     x = x[B.relu_certain_rows(ws, x)][:n]
     assert len(x) == n
     xt = torch.from_numpy(x).to(_dev())
-    acts = torch.zeros((net.mlp_depth, n, net.mlp_width), dtype=torch.float32, device=_dev())
-    out = nif.nif_mlp_forward(handle.h, xt, acts=acts).cpu().numpy()
     ref, racts = O.mlp_forward(ws, x.astype(np.float64))
-    # FP32 accumulation over K <= 576 terms (split TF32: each product to ~2^-21)
-    np.testing.assert_allclose(out, ref, atol=2e-5 * np.abs(ref).max(), rtol=0)
-    a = acts.cpu().numpy()
-    for l in range(net.mlp_depth):
-        np.testing.assert_allclose(a[l], racts[l + 1], atol=2e-5 * np.abs(racts[l + 1]).max(), rtol=0)
-    del a
+    for fused in (1, 0):
+        nif.nif_set_knob(handle.h, nif.NIF_KNOB_FP32_FUSED, fused)
+        acts = torch.zeros((net.mlp_depth, n, net.mlp_width), dtype=torch.float32, device=_dev())
+        out = nif.nif_mlp_forward(handle.h, xt, acts=acts).cpu().numpy()
+        # FP32 accumulation over K <= 576 terms (split TF32: each product to ~2^-21)
+        np.testing.assert_allclose(out, ref, atol=2e-5 * np.abs(ref).max(), rtol=0)
+        a = acts.cpu().numpy()
+        for l in range(net.mlp_depth):
+            np.testing.assert_allclose(a[l], racts[l + 1], atol=2e-5 * np.abs(racts[l + 1]).max(), rtol=0)
+        del a
     dout = rng.normal(size=(n, 16)).astype(np.float32)
     dout[:, net.out_dim:] = 0
     nif.nif_zero_grad(handle.h)

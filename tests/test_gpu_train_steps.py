@@ -156,3 +156,45 @@ def test_train_step_table_gradient_matches_stages(nif, torus, levels, log2T):
     np.testing.assert_allclose(np.abs(delta[big]), lr, rtol=1e-3)
     agree = np.sign(delta[big]) == np.sign(g[big])
     assert agree.all(), (np.count_nonzero(~agree), big.sum())
+
+
+@pytest.mark.parametrize("batch_at", [0, 1, 2, 3])
+def test_train_steps_batch_placement_and_fused_forward(nif, torus, batch_at):
+    """Where the next batch starts beside a step (NIF_KNOB_BATCH_AT) and the
+    one-launch FP32 forward (NIF_KNOB_FP32_FUSED) change the schedule, not
+    the steps: the losses equal those of the default schedule."""
+    net = S.NetConfig(levels=16, log2_table=19, mlp_depth=3, mlp_width=64)
+    a = nif.Nif(net, torus, seed=9)
+    b = nif.Nif(net, torus, seed=9)
+    nif.nif_set_knob(b.h, nif.NIF_KNOB_BATCH_AT, batch_at)
+    nif.nif_set_knob(b.h, nif.NIF_KNOB_FP32_FUSED, 1)
+    # learning rates 0: each step's loss depends only on its batch (a batch
+    # built into the buffers of the step still running would show here)
+    for K in (1, 3):
+        la = nif.nif_train_steps(a.h, K, 1 << 15, 8, 900 + K, lr_grid=0.0, lr_mlp=0.0, want_loss=True)
+        lb = nif.nif_train_steps(b.h, K, 1 << 15, 8, 900 + K, lr_grid=0.0, lr_mlp=0.0, want_loss=True)
+        np.testing.assert_allclose(lb, la, rtol=1e-6, atol=1e-9)
+    # with learning: the same trajectory up to the order of float atomics
+    la = nif.nif_train_steps(a.h, 4, 1 << 15, 8, 950, lr_grid=1e-2, lr_mlp=1e-3, want_loss=True)
+    lb = nif.nif_train_steps(b.h, 4, 1 << 15, 8, 950, lr_grid=1e-2, lr_mlp=1e-3, want_loss=True)
+    np.testing.assert_allclose(lb[1:], la[1:], rtol=1e-2, atol=1e-4)
+    a.close()
+    b.close()
+
+
+def test_profile_filter_times_only_named_stages(nif, torus):
+    h = nif.Nif(S.NetConfig(), torus, seed=3)
+    nif.nif_train_steps(h.h, 1, 1 << 14, 4, 11)
+    nif.nif_profile_filter(h.h, ["encode_bwd", "adam"])
+    nif.nif_profile(h.h, 1)
+    nif.nif_train_steps(h.h, 3, 1 << 14, 4, 12)
+    prof = nif.nif_profile_read(h.h)
+    nif.nif_profile(h.h, 0)
+    assert set(prof) == {"encode_bwd", "adam"}, set(prof)
+    assert prof["encode_bwd"][1] == 3 and prof["encode_bwd"][0] > 0
+    nif.nif_profile_filter(h.h, None)
+    nif.nif_profile(h.h, 1)
+    nif.nif_train_steps(h.h, 1, 1 << 14, 4, 13)
+    assert len(nif.nif_profile_read(h.h)) > 5
+    nif.nif_profile(h.h, 0)
+    h.close()
