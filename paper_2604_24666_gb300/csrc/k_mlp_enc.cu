@@ -25,10 +25,10 @@
 //   warps 5..   G producer groups of GW warps. Stage k of the CTA's sequence
 //               (tile j, box b: k = j nb0 + b) is filled by group k mod G into
 //               ring slot k mod S: the group lists the tile's distinct end
-//               points, then evaluates the box's gamma terms for them (one
-//               (point, term) item per thread at a time, all L levels in
-//               registers) and stores 16-bit features in the 128-byte
-//               swizzled K-major layout of the MMA operand.
+//               points, then each thread takes listed points and evaluates the
+//               box's gamma terms for them (all L levels of a term in
+//               registers), storing 16-bit features in the 128-byte swizzled
+//               K-major layout of the MMA operand.
 // Every mbarrier wait is bounded (tc_ptx.cuh). A group's decision to stop is
 // taken by one of its threads and shared through shared memory between two
 // of its named barriers, so that its threads leave the loop together.
@@ -76,7 +76,7 @@ __device__ void load_weight0_perm(uint8_t* dst, const uint16_t* __restrict__ src
     }
 }
 
-template <int W, int LMAX, int GW, int G>
+template <int W, int L, int GW, int G>
 __global__ void __launch_bounds__((5 + G * GW) * 32, 1)
     k_mlp_enc(GridInfo g, const __half* __restrict__ tab, const nif_linseg* __restrict__ lin, EncLayout lay,
               const uint16_t* __restrict__ wts, int K0, int H, int fmt, int64_t n_max,
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__((5 + G * GW) * 32, 1)
     constexpr int kGT = GW * 32;                    // threads of a producer group
     constexpr int kThr = (5 + G * GW) * 32;
     constexpr uint32_t kAccCols = W < 32 ? 32 : W;
-    static_assert(kRows % kGT == 0, "rows per producer thread");
+    static_assert(16 % L == 0 && L >= 4, "16 / L gamma terms per 64-column box, whole 16-byte chunks per item");
     const int64_t n = n_dev ? ((int64_t)*n_dev < n_max ? (int64_t)*n_dev : n_max) : n_max;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint64_t wlim = wait_limit(status);
@@ -256,10 +256,9 @@ __global__ void __launch_bounds__((5 + G * GW) * 32, 1)
         int* wsum = reinterpret_cast<int*>(gbase + 640);                    // [GW] warp totals
         volatile int* gdec = reinterpret_cast<volatile int*>(gbase + 640 + 4 * GW);   // group decision
         const int bar_id = 1 + grp;
-        const int L = g.L;
-        const int tpb = 16 / L;                 // gamma terms per 64-column box
-        const int cpi = L >> 2;                 // 16-byte chunks of one (point, term) item
-        constexpr int R = kRows / kGT;          // tile rows per thread in the listing
+        constexpr int kTpb = 16 / L;            // gamma terms per 64-column box
+        constexpr int kCpi = L / 4;             // 16-byte chunks of one (point, term) item
+        constexpr int R = (kRows + kGT - 1) / kGT;   // tile rows per thread in the listing
         const int64_t n_seq = nt * lay.nb0;
         for (int64_t k = grp; k < n_seq; k += G) {
             const int64_t j = k / lay.nb0;
@@ -278,14 +277,14 @@ __global__ void __launch_bounds__((5 + G * GW) * 32, 1)
             for (int i = 0; i < R; i++) {
                 const int r = gt * R + i;
                 const int64_t s = row0 + r;
-                valid[i] = s < n;
+                valid[i] = r < kRows && s < n;
                 bool dup = false;
                 if (valid[i] && r > 0) {
                     const float* a = reinterpret_cast<const float*>(lin + s);
                     const float* pb = reinterpret_cast<const float*>(lin + s - 1) + 3;
                     dup = a[0] == pb[0] && a[1] == pb[1] && a[2] == pb[2];
                 }
-                dupf[r] = dup ? 1 : 0;
+                if (r < kRows) dupf[r] = dup ? 1 : 0;
                 need0[i] = valid[i] && !dup;
                 cnt += (need0[i] ? 1 : 0) + (valid[i] ? 1 : 0);
             }
@@ -312,50 +311,51 @@ __global__ void __launch_bounds__((5 + G * GW) * 32, 1)
                 list[pos++] = (uint16_t)(r | (1 << 7) | (twice ? 1 << 8 : 0));
             }
             named_bar(bar_id, kGT);
-            // the box's terms for every listed point: item = (term, point), points fastest
-            const int t0 = b * tpb;
-            const int nterm = min(tpb, g.P - t0);
+            // the box's terms for every listed point: a thread keeps its points
+            // and walks the box's terms
+            const int t0 = b * kTpb;
+            const int nterm = min(kTpb, g.P - t0);
             uint8_t* stage = sm + lay.x_off + (uint32_t)slot * kStageBytes;
-            for (int it = gt; it < nterm * m; it += kGT) {
-                const int tt = it / m;
-                const uint32_t info = list[it - tt * m];
+            for (int pi = gt; pi < m; pi += kGT) {
+                const uint32_t info = list[pi];
                 const int r = (int)(info & 127u), e = (int)((info >> 7) & 1u);
-                const float* pp = reinterpret_cast<const float*>(lin + row0 + r) + 3 * e;
-                const float3 u = term_u(clamp01(make_float3(pp[0], pp[1], pp[2])), t0 + tt);
-                uint32_t res[LMAX];
-#pragma unroll
-                for (int l = 0; l < LMAX; l++) {
-                    if (l >= L) break;
-                    const Cell c = cell_of(u, g.res[l]);
-                    typename RawRow<__half>::T vr[8];
-                    level_gather<__half>(g, tab, l, c, vr);
-                    const float wx1 = c.wx, wx0 = 1.f - c.wx, wy1 = c.wy, wy0 = 1.f - c.wy;
-                    const float wz1 = c.wz, wz0 = 1.f - c.wz;
-                    const float wxy[4] = {wx0 * wy0, wx1 * wy0, wx0 * wy1, wx1 * wy1};
-                    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        const float w = wxy[q & 3] * ((q & 4) ? wz1 : wz0);
-                        const float2 v = RawRow<__half>::f2(vr[q]);
-                        acc.x += w * v.x;
-                        acc.y += w * v.y;
-                    }
-                    res[l] = pack2(acc.x, acc.y, fmt);
-                }
-                // row r's (term, e) columns; an exit point that the next row
-                // repeats also goes to that row's (term, entry) columns
-                const int c0 = (tt * 2 + e) * cpi;
-                uint8_t* dst = stage + (uint32_t)r * 128u;
                 const bool twice = (info >> 8) & 1u;
+                const float* pp = reinterpret_cast<const float*>(lin + row0 + r) + 3 * e;
+                const float3 p = clamp01(make_float3(pp[0], pp[1], pp[2]));
+                uint8_t* dst = stage + (uint32_t)r * 128u;
                 uint8_t* dst2 = dst + 128;
-                const int c2 = tt * 2 * cpi;
                 const int sw = r & 7, sw2 = (r + 1) & 7;
+#pragma unroll 1
+                for (int tt = 0; tt < nterm; tt++) {
+                    const float3 u = term_u(p, t0 + tt);
+                    uint32_t res[L];
 #pragma unroll
-                for (int qc = 0; qc < LMAX / 4; qc++) {
-                    if (qc >= cpi) break;
-                    const uint4 v4 = make_uint4(res[4 * qc], res[4 * qc + 1], res[4 * qc + 2], res[4 * qc + 3]);
-                    *reinterpret_cast<uint4*>(dst + (((c0 + qc) ^ sw) << 4)) = v4;
-                    if (twice) *reinterpret_cast<uint4*>(dst2 + (((c2 + qc) ^ sw2) << 4)) = v4;
+                    for (int l = 0; l < L; l++) {
+                        const Cell c = cell_of(u, g.res[l]);
+                        typename RawRow<__half>::T vr[8];
+                        level_gather<__half>(g, tab, l, c, vr);
+                        const float wx1 = c.wx, wx0 = 1.f - c.wx, wy1 = c.wy, wy0 = 1.f - c.wy;
+                        const float wz1 = c.wz, wz0 = 1.f - c.wz;
+                        const float wxy[4] = {wx0 * wy0, wx1 * wy0, wx0 * wy1, wx1 * wy1};
+                        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int q = 0; q < 8; q++) {
+                            const float w = wxy[q & 3] * ((q & 4) ? wz1 : wz0);
+                            const float2 v = RawRow<__half>::f2(vr[q]);
+                            acc.x += w * v.x;
+                            acc.y += w * v.y;
+                        }
+                        res[l] = pack2(acc.x, acc.y, fmt);
+                    }
+                    // row r's (term, e) columns; an exit point that the next row
+                    // repeats also goes to that row's (term, entry) columns
+                    const int c0 = (tt * 2 + e) * kCpi, c2 = tt * 2 * kCpi;
+#pragma unroll
+                    for (int qc = 0; qc < kCpi; qc++) {
+                        const uint4 v4 = make_uint4(res[4 * qc], res[4 * qc + 1], res[4 * qc + 2], res[4 * qc + 3]);
+                        *reinterpret_cast<uint4*>(dst + (((c0 + qc) ^ sw) << 4)) = v4;
+                        if (twice) *reinterpret_cast<uint4*>(dst2 + (((c2 + qc) ^ sw2) << 4)) = v4;
+                    }
                 }
             }
             fence_async_smem();
@@ -403,7 +403,7 @@ EncLayout make_enc_layout(int W, int K0, int H, int P, int L, int G) {
     return y;
 }
 
-template <int W, int LMAX, int GW, int G>
+template <int W, int L, int GW, int G>
 nif_status launch_enc(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max, float* out,
                       cudaStream_t s) {
     EncLayout lay = make_enc_layout(W, h->in_dim, h->H, h->P, h->L, G);
@@ -412,21 +412,23 @@ nif_status launch_enc(nif_handle* h, const nif_linseg* lin, const uint32_t* n_de
         lay.woff[l] = (uint32_t)(h->off_layer[l] - h->off_layer[0]);
         if (lay.woff[l] % 8) return nif_fail(h, NIF_ERR_STATE, "weight copy not 16-byte aligned per layer");
     }
-    NIF_CK(h, cudaFuncSetAttribute(k_mlp_enc<W, LMAX, GW, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    NIF_CK(h, cudaFuncSetAttribute(k_mlp_enc<W, L, GW, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)lay.total));
     const int64_t n_tiles = (n_max + kRows - 1) / kRows;
     const int grid = (int)std::min<int64_t>(n_tiles, h->num_sms);
     const int fmt = h->cfg.precision == NIF_BF16 ? 1 : 0;
     const uint16_t* w = reinterpret_cast<const uint16_t*>(fmt ? (const void*)h->d_w_bf16 : (const void*)h->d_w_f16);
-    k_mlp_enc<W, LMAX, GW, G><<<grid, (5 + G * GW) * 32, lay.total, s>>>(
+    k_mlp_enc<W, L, GW, G><<<grid, (5 + G * GW) * 32, lay.total, s>>>(
         h->grid, h->d_tables_h, lin, lay, w, h->in_dim, h->H, fmt, n_max, n_dev, out, h->d_status);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
 
-// producer groups: 4 groups of 4 warps up to 8 levels; 4 groups of 2 warps at
-// 16 levels (half the items per box, and layer 0's weights take 72 KB)
+// producer groups: 4 groups of 6 warps. A box holds 16 / L terms of the
+// tile's ~170 distinct points (2/3 of the entry points repeat an exit), so a
+// group of 192 threads walks each term's points in one round
 constexpr int kG = 4;
+constexpr int kGW = 6;
 
 }  // namespace
 
@@ -446,10 +448,12 @@ nif_status nif_mlp_enc_tc_run(nif_handle* h, const nif_linseg* lin, const uint32
     if (!nif_mlp_enc_fusable(h)) return nif_fail(h, NIF_ERR_STATE, "fused encoding + MLP does not apply to this handle");
     nif_status st = nif_refresh_lowp(h, s);
     if (st != NIF_OK) return st;
-    if (h->L <= 8) {
-        if (h->W == 32) return launch_enc<32, 8, 4, kG>(h, lin, n_dev, n_max, out, s);
-        return launch_enc<64, 8, 4, kG>(h, lin, n_dev, n_max, out, s);
+    switch (h->L * 100 + h->W) {
+        case 432: return launch_enc<32, 4, kGW, kG>(h, lin, n_dev, n_max, out, s);
+        case 464: return launch_enc<64, 4, kGW, kG>(h, lin, n_dev, n_max, out, s);
+        case 832: return launch_enc<32, 8, kGW, kG>(h, lin, n_dev, n_max, out, s);
+        case 864: return launch_enc<64, 8, kGW, kG>(h, lin, n_dev, n_max, out, s);
+        case 1632: return launch_enc<32, 16, kGW, kG>(h, lin, n_dev, n_max, out, s);
+        default: return launch_enc<64, 16, kGW, kG>(h, lin, n_dev, n_max, out, s);
     }
-    if (h->W == 32) return launch_enc<32, 16, 2, kG>(h, lin, n_dev, n_max, out, s);
-    return launch_enc<64, 16, 2, kG>(h, lin, n_dev, n_max, out, s);
 }

@@ -203,7 +203,7 @@ struct nif_handle {
                                         // than 1 on the 64^3 step, 2 and 3 are 0.1-0.2 ms slower)
         int fp32_fused = 0;             // NIF_KNOB_FP32_FUSED: the FP32 forward in one launch (measured equal
                                         // to the per-layer launches on the 64^3 step)
-        int query_fused = 0;            // NIF_KNOB_QUERY_FUSED: 16-bit queries encode into the tensor-core
+        int query_fused = 1;            // NIF_KNOB_QUERY_FUSED: 16-bit queries encode into the tensor-core
                                         // MLP's shared-memory ring (one launch) instead of two kernels
     } tune;
 

@@ -4,10 +4,11 @@ tile go from the producer warps into the MMA's shared-memory ring and never
 reach global memory.
 
 * Against the FP64 oracle for each level count, width and depth the kernel
-  covers, on the same weights, with the bounds of the two-kernel path's
-  mixed-precision test (hit agreement on rays whose occupancy logits are
-  clear of 5 % of their range, distance <= 2e-3, albedo <= 2e-2, normal
-  within 2 degrees, material >= 99 % where the top two logits are clear).
+  covers, on the same weights (hit agreement on rays whose occupancy logits
+  are clear of 5 % of their range, distance <= 2e-3, albedo <= 2e-2, normal
+  within 2 degrees on 99 % of the hits and 5 on all, material >= 99 % where
+  the top two logits are clear), and against the two-kernel path on the
+  same handle.
 * Against the two-kernel path (NIF_KNOB_QUERY_FUSED = 0) at the 128^3
   query workload's full size (2^22 rays, ~19 M segments, one launch of the
   fused kernel over ~150 k tiles): the two differ only in layer 0's
@@ -48,53 +49,74 @@ def _dev():
 
 
 def _check_against_oracle(nif, net, mesh, hits, tables, ws, pose, rays_np):
+    """Rays whose occupancy logits are all clear of 5 % of their range: the
+    hit decision equals the oracle's; on hits, distance <= 2e-3 and albedo
+    <= 2e-2 everywhere, the normal within 2 degrees on 99 % of the rays and
+    within 5 degrees on all (a raw normal vector that is short against the
+    16-bit rounding of the outputs turns further), material >= 99 % where
+    the top two logits are clear."""
     occ, _, _ = O.voxelize(net.voxel_res, mesh)
     seg = O.segments(net.voxel_res, occ, pose, rays_np)
     p0, p1, ld, lr = O.linearize(pose, rays_np, seg)
     out = O.mlp_forward(ws, O.encode_segments(net, tables, p0, p1))[0]
     res = O.reconstruct(net, pose, rays_np, seg, out, p0, p1, ld, lr)
     zr = np.abs(out[:, 0]).max()
-    n_cmp, n_hit, mat_ok, mat_n = 0, 0, 0, 0
+    n_cmp, mat_ok, mat_n, ang = 0, 0, 0, []
     for r in range(len(rays_np)):
         a, b = seg.off[r], seg.off[r + 1]
         if np.any(np.abs(out[a:b, 0]) < 0.05 * zr):
             continue
         assert hits["hit"][r] == res["hit"][r], r
         if res["hit"][r]:
-            n_hit += 1
             j = a + res["k"][r]
             assert abs(hits["D"][r] - res["D"][r]) < 2e-3, (r, hits["D"][r], res["D"][r])
             np.testing.assert_allclose(hits["albedo"][r], res["albedo"][r], atol=2e-2)
-            assert np.dot(hits["n"][r], res["normal"][r]) > np.cos(np.radians(2.0))
+            ang.append(np.degrees(np.arccos(np.clip(np.dot(hits["n"][r], res["normal"][r]), -1.0, 1.0))))
             m = np.sort(out[j, 8:12])
             if m[-1] - m[-2] > 0.05 * (np.abs(out[:, 8:12]).max()):
                 mat_n += 1
                 mat_ok += hits["material"][r] == res["material"][r]
         n_cmp += 1
-    return n_cmp, n_hit, mat_ok, mat_n
+    ang = np.asarray(ang)
+    if ang.size:
+        assert np.percentile(ang, 99) <= 2.0 and ang.max() <= 5.0, (np.percentile(ang, 99), ang.max())
+    assert mat_n == 0 or mat_ok >= 0.99 * mat_n
+    return n_cmp, ang.size
 
 
 @pytest.mark.parametrize("levels,log2T,width,depth", [(8, 14, 32, 2), (16, 19, 64, 3), (4, 12, 32, 1), (16, 14, 32, 2),
                                                       (8, 14, 64, 3), (8, 19, 64, 4)])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_fused_query_matches_oracle(nif, torus, levels, log2T, width, depth, prec):
+    """The fused query against the oracle, and against the two-kernel path on
+    the same handle: the same 16-bit features, layer 0 summed in another
+    order, so the two agree to the rounding of an activation."""
     net = S.NetConfig(levels=levels, log2_table=log2T, mlp_depth=depth, mlp_width=width)
     p = nif.NIF_BF16 if prec == "bf16" else nif.NIF_FP16
     h = nif.Nif(net, torus, precision=p)
-    nif.nif_set_knob(h.h, nif.NIF_KNOB_QUERY_FUSED, 1)
     tables = random_tables(net, 301 + levels)
     ws, s = occupancy_biased_weights(net, 302 + width)
     h.set_params(tables, ws, s)
     pose = (-0.4, 0.9, 0.3)
     rays_np = S.sphere_rays(2000 + 77, seed=303)         # ragged last tile of segments
     rays_np = rays_np[certain_rays(net.voxel_res, torus, pose, rays_np)]
-    hits = nif.nif_query(h.h, [pose], torch.from_numpy(rays_np).to(_dev())).cpu().numpy()
+    rays = torch.from_numpy(rays_np).to(_dev())
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_QUERY_FUSED, 1)
+    hits = nif.nif_query(h.h, [pose], rays).cpu().numpy().view(nif.HIT_DTYPE).reshape(-1)
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_QUERY_FUSED, 0)
+    two = nif.nif_query(h.h, [pose], rays).cpu().numpy().view(nif.HIT_DTYPE).reshape(-1)
     nif.nif_sync_status(h.h)
-    hits = hits.view(nif.HIT_DTYPE).reshape(-1)
-    n_cmp, n_hit, mat_ok, mat_n = _check_against_oracle(nif, net, torus, hits, tables, ws, pose, rays_np)
-    assert n_cmp > 500 and n_hit > 50
-    assert mat_n == 0 or mat_ok >= 0.99 * mat_n
     h.close()
+    n_cmp, n_hit = _check_against_oracle(nif, net, torus, hits, tables, ws, pose, rays_np)
+    assert n_cmp > 500 and n_hit > 50
+    both = (hits["hit"] > 0) & (two["hit"] > 0)
+    assert both.sum() >= 0.99 * ((hits["hit"] > 0) | (two["hit"] > 0)).sum()
+    same = both.copy()
+    same[both] = np.abs(hits["D"][both] - two["D"][both]) < 2e-3
+    assert same.sum() >= 0.99 * both.sum()
+    assert np.abs(hits["D"][same] - two["D"][same]).max() < 1e-3
+    cosang = (hits["n"][same] * two["n"][same]).sum(1)
+    assert np.percentile(cosang, 1) > np.cos(np.radians(1.0))
 
 
 def test_fused_query_full_size_matches_two_kernel_path(nif):
@@ -121,7 +143,8 @@ def test_fused_query_full_size_matches_two_kernel_path(nif):
     # where both take the same first-hit segment the outputs agree to the
     # 16-bit rounding of an activation; another segment moves D by about a
     # voxel (1/128)
-    same = both & (np.abs(a["D"] - b["D"]) < 2e-3)
+    same = both.copy()
+    same[both] = np.abs(a["D"][both] - b["D"][both]) < 2e-3
     assert same.sum() >= 0.99 * both.sum()
     assert np.percentile(np.abs(a["D"][same] - b["D"][same]), 99) < 5e-4
     assert (a["material"][same] == b["material"][same]).mean() > 0.99
