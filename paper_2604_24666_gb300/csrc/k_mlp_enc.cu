@@ -53,6 +53,20 @@ struct EncLayout {
     uint32_t woff[NIF_MAX_LAYERS];   // element offset of each layer in the 16-bit weight copy
 };
 
+// u of gamma term t at p (clamped), with the fast sine and cosine: on the
+// 16-bit path the features are rounded to 8 or 11 bits, far above the
+// intrinsics' error at |x| <= 2^(F-1)
+__device__ __forceinline__ float3 term_u_fast(float3 p, int t) {
+    if (t == 0) return p;
+    const float f = (float)(1 << ((t - 1) >> 1));
+    float sx, cx, sy, cy, sz, cz;
+    __sincosf(f * p.x, &sx, &cx);
+    __sincosf(f * p.y, &sy, &cy);
+    __sincosf(f * p.z, &sz, &cz);
+    if ((t - 1) & 1) return make_float3((cx + 1.0f) * 0.5f, (cy + 1.0f) * 0.5f, (cz + 1.0f) * 0.5f);
+    return make_float3((sx + 1.0f) * 0.5f, (sy + 1.0f) * 0.5f, (sz + 1.0f) * 0.5f);
+}
+
 __device__ __forceinline__ void named_bar(int id, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
@@ -327,23 +341,28 @@ __global__ void __launch_bounds__((5 + G * GW) * 32, 1)
                 const int sw = r & 7, sw2 = (r + 1) & 7;
 #pragma unroll 1
                 for (int tt = 0; tt < nterm; tt++) {
-                    const float3 u = term_u(p, t0 + tt);
+                    const float3 u = term_u_fast(p, t0 + tt);
                     uint32_t res[L];
 #pragma unroll
                     for (int l = 0; l < L; l++) {
                         const Cell c = cell_of(u, g.res[l]);
                         typename RawRow<__half>::T vr[8];
                         level_gather<__half>(g, tab, l, c, vr);
-                        const float wx1 = c.wx, wx0 = 1.f - c.wx, wy1 = c.wy, wy0 = 1.f - c.wy;
-                        const float wz1 = c.wz, wz0 = 1.f - c.wz;
-                        const float wxy[4] = {wx0 * wy0, wx1 * wy0, wx0 * wy1, wx1 * wy1};
+                        // corner weights (x fastest), then both features of a
+                        // corner in one packed FP32 FMA
+                        const float2 wx = make_float2(1.f - c.wx, c.wx);
+                        const float wy0 = 1.f - c.wy, wy1 = c.wy, wz0 = 1.f - c.wz, wz1 = c.wz;
+                        const float2 wxy0 = __fmul2_rn(wx, make_float2(wy0, wy0));
+                        const float2 wxy1 = __fmul2_rn(wx, make_float2(wy1, wy1));
+                        const float2 wq[4] = {__fmul2_rn(wxy0, make_float2(wz0, wz0)),
+                                              __fmul2_rn(wxy1, make_float2(wz0, wz0)),
+                                              __fmul2_rn(wxy0, make_float2(wz1, wz1)),
+                                              __fmul2_rn(wxy1, make_float2(wz1, wz1))};
                         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int q = 0; q < 8; q++) {
-                            const float w = wxy[q & 3] * ((q & 4) ? wz1 : wz0);
-                            const float2 v = RawRow<__half>::f2(vr[q]);
-                            acc.x += w * v.x;
-                            acc.y += w * v.y;
+                            const float w = (q & 1) ? wq[q >> 1].y : wq[q >> 1].x;
+                            acc = __ffma2_rn(make_float2(w, w), RawRow<__half>::f2(vr[q]), acc);
                         }
                         res[l] = pack2(acc.x, acc.y, fmt);
                     }
