@@ -758,7 +758,8 @@ FRAME_WORKLOAD = "ellipsoids256_frame"
 def run_batch(args, nif, S, dev, rank):
     """Batched queries of 64 deforming instances with Zipf ray counts (about
     2^22 rays), one autotuned CUDA-graph replay per step: mixed precision
-    (BF16 MLP, FP16 tables) and, on the same rays and poses, FP32."""
+    (BF16 MLP, FP16 tables; the encoding inside the MLP kernel, and as two
+    kernels per chunk) and, on the same rays and poses, FP32."""
     import torch
     w = S.WORKLOADS[BATCH_WORKLOAD]
     net = w["net"]
@@ -772,8 +773,10 @@ def run_batch(args, nif, S, dev, rank):
     rng = np.random.default_rng(720 + rank)
     poses = [rng.uniform(-1, 1, (w["n_inst"], 3)).astype(np.float32) for _ in range(args.steps + args.warmup)]
     res = None
-    for name, prec in (("bf16", nif.NIF_BF16), ("fp32", nif.NIF_FP32)):
+    for name, prec in (("bf16", nif.NIF_BF16), ("bf16_two_kernels", nif.NIF_BF16), ("fp32", nif.NIF_FP32)):
         h = nif.Nif(net, mesh, precision=prec, seed=41)
+        if name.endswith("_two_kernels"):           # encoding and MLP as two kernels per chunk
+            nif.nif_set_knob(h.h, nif.NIF_KNOB_QUERY_FUSED, 0)
         hits = torch.zeros((n, 8), dtype=torch.float32, device=dev)
         t0 = time.perf_counter()
         plan = nif.QueryPlan(h.h, poses[0], rays, hits, inst_offsets=it, autotune=True)

@@ -615,9 +615,10 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  * NIF_KNOB_QUERY_FUSED: 1 (default) computes a BF16/FP16 query's encoding
  *   (Eq. 1) inside the tensor-core MLP's kernel, which keeps each tile's
  *   features in shared memory (handles with L in {4, 8, 16}, F_d = 2, width
- *   32 or 64); 0 runs the encoding and the MLP as two kernels per chunk with
- *   the features in a global buffer. The outputs agree to the MLP's
- *   accumulation order.
+ *   32 or 64 and an FP16 table copy of at most 4 MiB); 0 runs the encoding
+ *   and the MLP as two kernels per chunk with the features in a global
+ *   buffer. The outputs agree to the MLP's accumulation order and the fast
+ *   sine of gamma. A query plan's autotuner times both and keeps the faster.
  * NIF_ERR_ARG for an unknown knob or a value out of range. */
 #define NIF_KNOB_WAIT_NS 1
 #define NIF_KNOB_SEG_SCRATCH 2

@@ -562,12 +562,18 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
 #pragma unroll
                     for (int q = 0; q < 8; q++) cacc[q] = make_float2(0.f, 0.f);
                 }
+                // corner weights (x fastest, the same products as one at a
+                // time) and both features of a corner in one packed FP32 FMA
+                const float2 wx = make_float2(1.f - cl.wx, cl.wx);
+                const float wy0 = 1.f - cl.wy, wy1 = cl.wy, wz0 = 1.f - cl.wz, wz1 = cl.wz;
+                const float2 wxy0 = __fmul2_rn(wx, make_float2(wy0, wy0));
+                const float2 wxy1 = __fmul2_rn(wx, make_float2(wy1, wy1));
+                const float2 wq[4] = {__fmul2_rn(wxy0, make_float2(wz0, wz0)), __fmul2_rn(wxy1, make_float2(wz0, wz0)),
+                                      __fmul2_rn(wxy0, make_float2(wz1, wz1)), __fmul2_rn(wxy1, make_float2(wz1, wz1))};
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
-                    float w = ((q & 1) ? cl.wx : 1.f - cl.wx) * ((q & 2) ? cl.wy : 1.f - cl.wy) *
-                              ((q & 4) ? cl.wz : 1.f - cl.wz);
-                    cacc[q].x += w * gr.x;
-                    cacc[q].y += w * gr.y;
+                    const float w = (q & 1) ? wq[q >> 1].y : wq[q >> 1].x;
+                    cacc[q] = __ffma2_rn(make_float2(w, w), gr, cacc[q]);
                 }
             }
         }

@@ -451,8 +451,15 @@ constexpr int kGW = 6;
 
 }  // namespace
 
+// Tables above 4 MiB (FP16 copy) miss L1 at every hashed level, and the 24
+// producer warps of a CTA do not hide the L2 latency that the two-kernel
+// path's encoder hides with many more warps and rest-space-sorted points
+// (measured: 64 instances, 32 MiB tables, 112.8 ms fused against 42.4 ms).
+constexpr size_t kFusedTableBytes = (size_t)4 << 20;
+
 bool nif_mlp_enc_fusable(const nif_handle* h) {
     if (!h->tune.query_fused || h->concat || h->Fd != 2) return false;
+    if ((size_t)h->T * h->L * h->Fd * sizeof(__half) > kFusedTableBytes) return false;
     if (h->cfg.precision != NIF_BF16 && h->cfg.precision != NIF_FP16) return false;
     if (h->L != 4 && h->L != 8 && h->L != 16) return false;
     if (h->W != 32 && h->W != 64) return false;

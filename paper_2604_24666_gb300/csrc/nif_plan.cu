@@ -168,6 +168,7 @@ nif_status autotune(nif_query_plan* p, cudaStream_t s) {
         *knob = keep;
         return NIF_OK;
     };
+    if (nif_mlp_enc_fusable(h) && (st = try_knob(&h->tune.query_fused, {0, 1})) != NIF_OK) return st;
     if ((st = try_knob(&h->tune.trav_warps, {2, 4, 8})) != NIF_OK) return st;
     if ((st = try_knob(&h->tune.enc_threads, {128, 256, 512})) != NIF_OK) return st;
     if ((st = try_knob(&h->tune.enc_blocks_per_sm, {4, 8, 16, 32})) != NIF_OK) return st;
