@@ -619,6 +619,14 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   and the MLP as two kernels per chunk with the features in a global
  *   buffer. The outputs agree to the MLP's accumulation order and the fast
  *   sine of gamma. A query plan's autotuner times both and keeps the faster.
+ * NIF_KNOB_STEP_PRIORITY: 1 runs the steps of nif_train_steps and
+ *   nif_train_steps_rays on the handle's streams of the device's greatest
+ *   priority (ordered after the caller's work and before its next), while
+ *   the next batch is built on a stream of the least priority; 0 (default)
+ *   runs them on the caller's stream. A scheduling choice only (measured on
+ *   the 64^3 FP32 step: 3.06-3.09 ms with priorities, 3.04-3.05 ms without:
+ *   a batch that finishes later delays the step that needs it).
+ *   Synchronises the device.
  * NIF_ERR_ARG for an unknown knob or a value out of range. */
 #define NIF_KNOB_WAIT_NS 1
 #define NIF_KNOB_SEG_SCRATCH 2
@@ -626,6 +634,7 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
 #define NIF_KNOB_BATCH_AT 4
 #define NIF_KNOB_FP32_FUSED 5
 #define NIF_KNOB_QUERY_FUSED 6
+#define NIF_KNOB_STEP_PRIORITY 7
 nif_status nif_set_knob(nif_handle* h, int knob, double value);
 
 /* Allocation-free variant of nif_segments (the paper has no counterpart:
@@ -711,6 +720,13 @@ nif_status nif_profile_filter(nif_handle* h, const char* names);
  * the number of stages. i = -1 only reports *n_names. */
 nif_status nif_profile_read(nif_handle* h, int i, char* name, int name_cap, double* ms, long* count,
                             int* n_names);
+/* The timed stages one by one, before nif_profile_read folds them: record i
+ * (in launch order) gives its name and its start and end in milliseconds
+ * after the start of record 0, on the GPU's clock (stages on different
+ * streams overlap). *n_recs (nullable) gets the number of records; i = -1
+ * only reports it. Synchronises the device; NIF_ERR_ARG for i out of range. */
+nif_status nif_profile_timeline(nif_handle* h, int i, char* name, int name_cap, double* t0_ms, double* t1_ms,
+                                int* n_recs);
 
 #ifdef __cplusplus
 }

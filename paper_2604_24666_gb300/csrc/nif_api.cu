@@ -85,6 +85,27 @@ static nif_status prof_fold(nif_handle* h) {
     return NIF_OK;
 }
 
+extern "C" nif_status nif_profile_timeline(nif_handle* h, int i, char* name, int name_cap, double* t0_ms,
+                                           double* t1_ms, int* n_recs) {
+    if (!h) return NIF_ERR_ARG;
+    NIF_CK(h, cudaDeviceSynchronize());
+    if (n_recs) *n_recs = (int)h->prof_recs.size();
+    if (i == -1) return NIF_OK;
+    if (i < 0 || i >= (int)h->prof_recs.size()) return NIF_ERR_ARG;
+    const nif_handle::ProfRec& r0 = h->prof_recs[0];
+    const nif_handle::ProfRec& r = h->prof_recs[i];
+    float a = 0.f, b = 0.f;
+    NIF_CK(h, cudaEventElapsedTime(&a, r0.a, r.a));
+    NIF_CK(h, cudaEventElapsedTime(&b, r0.a, r.b));
+    if (name && name_cap > 0) {
+        std::strncpy(name, r.name, name_cap - 1);
+        name[name_cap - 1] = 0;
+    }
+    if (t0_ms) *t0_ms = a;
+    if (t1_ms) *t1_ms = b;
+    return NIF_OK;
+}
+
 extern "C" nif_status nif_profile_read(nif_handle* h, int i, char* name, int name_cap, double* ms, long* count,
                                        int* n_names) {
     if (!h) return NIF_ERR_ARG;
@@ -491,7 +512,15 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
     CKC(cudaMalloc(&h->d_next, sizeof(uint32_t) * 4));
     CKC(cudaMallocHost(&h->h_pinned, sizeof(int) * 16));
     CKC(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
-    CKC(cudaStreamCreateWithFlags(&h->aux2, cudaStreamNonBlocking));
+    {
+        int least = 0, greatest = 0;
+        CKC(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CKC(cudaStreamCreateWithPriority(&h->aux2, cudaStreamNonBlocking, least));
+        CKC(cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, greatest));
+        CKC(cudaStreamCreateWithPriority(&h->aux_hi, cudaStreamNonBlocking, greatest));
+    }
+    CKC(cudaEventCreateWithFlags(&h->ev_hi_fork, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&h->ev_hi_join, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&h->ev_batch, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&h->ev_step, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
@@ -575,6 +604,10 @@ extern "C" void nif_destroy(nif_handle* h) {
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->aux2) cudaStreamDestroy(h->aux2);
+    if (h->hi) cudaStreamDestroy(h->hi);
+    if (h->aux_hi) cudaStreamDestroy(h->aux_hi);
+    if (h->ev_hi_fork) cudaEventDestroy(h->ev_hi_fork);
+    if (h->ev_hi_join) cudaEventDestroy(h->ev_hi_join);
     if (h->h_loss) cudaFreeHost(h->h_loss);
     if (h->ev_batch) cudaEventDestroy(h->ev_batch);
     if (h->ev_step) cudaEventDestroy(h->ev_step);
@@ -1628,8 +1661,8 @@ static void swap_batch(nif_handle* h) {
 // n_rays is read after build(0) has set it; loss_last (nullable) receives the
 // last step's loss parts.
 template <class Build, class Done>
-static nif_status train_pipeline(nif_handle* h, int n_steps, const int& n_rays, int64_t n_segments, float lr_grid,
-                                 float lr_mlp, double* loss_last, cudaStream_t s, Build build, Done done) {
+static nif_status train_pipeline_on(nif_handle* h, int n_steps, const int& n_rays, int64_t n_segments, float lr_grid,
+                                    float lr_mlp, double* loss_last, cudaStream_t s, Build build, Done done) {
     nif_status st;
     if ((st = build(0, h->d_count + 2, s)) != NIF_OK) return st;
     NIF_CK(h, cudaEventRecord(h->ev_batch, s));
@@ -1661,7 +1694,7 @@ static nif_status train_pipeline(nif_handle* h, int n_steps, const int& n_rays, 
         if ((st = train_compute(h, n_rays, n_segments, h->d_count + 2 + i % 2, lr_grid, lr_mlp,
                                 more ? nullptr : loss_last, s, early ? nullptr : h->ev_step)) != NIF_OK)
             return st;
-        if ((st = done(i)) != NIF_OK) return st;
+        if ((st = done(i, s)) != NIF_OK) return st;
         if (more && !early && (st = next_batch(i)) != NIF_OK) return st;
         if (early) {
             NIF_CK(h, cudaEventRecord(h->ev_step, s));                      // end of step i
@@ -1669,6 +1702,31 @@ static nif_status train_pipeline(nif_handle* h, int n_steps, const int& n_rays, 
         }
     }
     return NIF_OK;
+}
+
+template <class Build, class Done>
+static nif_status train_pipeline(nif_handle* h, int n_steps, const int& n_rays, int64_t n_segments, float lr_grid,
+                                 float lr_mlp, double* loss_last, cudaStream_t caller, Build build, Done done) {
+    nif_status st;
+    // the steps on the high-priority stream (and the weight gradients on its
+    // high-priority partner), after the caller's work and before the caller's
+    // next; the next batch on the least-priority stream fills what they leave
+    const bool prio = h->tune.step_prio != 0;
+    const cudaStream_t s = prio ? h->hi : caller;
+    const cudaStream_t keep_aux = h->aux;
+    if (prio) {
+        NIF_CK(h, cudaEventRecord(h->ev_hi_fork, caller));
+        NIF_CK(h, cudaStreamWaitEvent(s, h->ev_hi_fork, 0));
+        h->aux = h->aux_hi;
+    }
+    st = train_pipeline_on(h, n_steps, n_rays, n_segments, lr_grid, lr_mlp, loss_last, s, build, done);
+    h->aux = keep_aux;
+    if (prio) {
+        // the join also covers the third stream: its last batch is this call's
+        NIF_CK(h, cudaEventRecord(h->ev_hi_join, s));
+        NIF_CK(h, cudaStreamWaitEvent(caller, h->ev_hi_join, 0));
+    }
+    return st;
 }
 
 extern "C" nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segments, int n_poses,
@@ -1690,7 +1748,7 @@ extern "C" nif_status nif_train_steps(nif_handle* h, int n_steps, int64_t n_segm
         return NIF_OK;
     };
     return train_pipeline(h, n_steps, n_rays, n_segments, lr_grid, lr_mlp, loss_host, s, build,
-                          [](int) { return NIF_OK; });
+                          [](int, cudaStream_t) { return NIF_OK; });
 }
 
 extern "C" nif_status nif_train_steps_rays(nif_handle* h, int n_steps, const nif_pose* poses, int n_inst,
@@ -1722,10 +1780,10 @@ extern "C" nif_status nif_train_steps_rays(nif_handle* h, int n_steps, const nif
         return train_batch(h, poses + (size_t)i * n_inst, n_inst, (const nif_ray*)h->b_rays.p, inst_off, n_rays,
                            n_segments, n_hit, bs);
     };
-    auto done = [&](int i) -> nif_status {
+    auto done = [&](int i, cudaStream_t ds) -> nif_status {
         if (loss_host)
             NIF_CK(h, cudaMemcpyAsync(h->h_loss + 6 * (size_t)i, h->d_lossacc + 8, sizeof(double) * 6,
-                                      cudaMemcpyDeviceToHost, s));
+                                      cudaMemcpyDeviceToHost, ds));
         return NIF_OK;
     };
     if ((st = train_pipeline(h, n_steps, n_rays, n_segments, lr_grid, lr_mlp, nullptr, s, build, done)) != NIF_OK)
@@ -1758,6 +1816,11 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
         case NIF_KNOB_FP32_FUSED:
             if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "fused FP32 forward knob must be 0 or 1");
             h->tune.fp32_fused = (int)value;
+            return NIF_OK;
+        case NIF_KNOB_STEP_PRIORITY:
+            if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "step priority knob must be 0 or 1");
+            NIF_CK(h, cudaDeviceSynchronize());
+            h->tune.step_prio = (int)value;
             return NIF_OK;
         case NIF_KNOB_QUERY_FUSED:
             if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "fused query knob must be 0 or 1");

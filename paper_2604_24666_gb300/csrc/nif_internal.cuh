@@ -140,6 +140,12 @@ struct nif_handle {
     // a third stream for nif_train_steps' next batch, and its ordering events
     cudaStream_t aux2 = nullptr;
     cudaEvent_t ev_batch = nullptr, ev_step = nullptr;
+    // nif_train_steps[_rays] run their steps on `hi` (the device's greatest
+    // stream priority; the weight-gradient stream `aux` too), forked from and
+    // joined back into the caller's stream, so that the next batch on `aux2`
+    // (the least priority) takes the SMs the step leaves free
+    cudaStream_t hi = nullptr, aux_hi = nullptr;
+    cudaEvent_t ev_hi_fork = nullptr, ev_hi_join = nullptr;
     double* h_loss = nullptr;           // pinned: per-step loss parts of nif_train_steps_rays
     int h_loss_steps = 0;
 
@@ -203,6 +209,7 @@ struct nif_handle {
                                         // than 1 on the 64^3 step, 2 and 3 are 0.1-0.2 ms slower)
         int fp32_fused = 0;             // NIF_KNOB_FP32_FUSED: the FP32 forward in one launch (measured equal
                                         // to the per-layer launches on the 64^3 step)
+        int step_prio = 0;              // NIF_KNOB_STEP_PRIORITY: pipelined steps on the high-priority streams
         int query_fused = 1;            // NIF_KNOB_QUERY_FUSED: 16-bit queries encode into the tensor-core
                                         // MLP's shared-memory ring (one launch) instead of two kernels
     } tune;

@@ -26,7 +26,7 @@ NIF_FLAG_FIXED_TASK_WEIGHTS, NIF_FLAG_SIGMOID_DISTANCE, NIF_FLAG_MIXED_TRAINING 
 NIF_FLAG_CONCAT_ENCODING = 8
 NIF_FLAG_BILINEAR_FACES = 16
 NIF_KNOB_WAIT_NS, NIF_KNOB_SEG_SCRATCH, NIF_KNOB_QUERY_SEGS, NIF_KNOB_BATCH_AT, NIF_KNOB_FP32_FUSED = 1, 2, 3, 4, 5
-NIF_KNOB_QUERY_FUSED = 6
+NIF_KNOB_QUERY_FUSED, NIF_KNOB_STEP_PRIORITY = 6, 7
 NIF_PROBE_RED8, NIF_PROBE_RED16, NIF_PROBE_LOAD8, NIF_PROBE_LOAD4 = 1, 2, 3, 4
 NIF_PROBE_RED8_WARP, NIF_PROBE_RED16_WARP, NIF_PROBE_LOAD8_WARP, NIF_PROBE_LOAD4_WARP = 5, 6, 7, 8
 
@@ -150,6 +150,8 @@ def lib() -> ctypes.CDLL:
             "nif_kernel_launches": ([], ctypes.c_ulonglong),
             "nif_profile": ([_vp, ctypes.c_int], ctypes.c_int),
             "nif_profile_filter": ([_vp, ctypes.c_char_p], ctypes.c_int),
+            "nif_profile_timeline": ([_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "nif_profile_read": ([_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         }
@@ -645,6 +647,20 @@ def nif_profile_filter(h, names=None):
     """Time only the named stages (an iterable of names, or None for all)."""
     arg = ",".join(names).encode() if names else None
     _check(h, lib().nif_profile_filter(h, arg))
+
+
+def nif_profile_timeline(h):
+    """[(stage, start ms, end ms)] of the timed stages in launch order, relative
+    to the first one's start (read before nif_profile_read folds them)."""
+    n = ctypes.c_int()
+    _check(h, lib().nif_profile_timeline(h, -1, None, 0, None, None, ctypes.byref(n)))
+    out = []
+    for i in range(n.value):
+        name = ctypes.create_string_buffer(64)
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(h, lib().nif_profile_timeline(h, i, name, 64, ctypes.byref(a), ctypes.byref(b), None))
+        out.append((name.value.decode(), a.value, b.value))
+    return out
 
 
 def nif_profile_read(h):

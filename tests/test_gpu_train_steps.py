@@ -198,3 +198,24 @@ def test_profile_filter_times_only_named_stages(nif, torus):
     assert len(nif.nif_profile_read(h.h)) > 5
     nif.nif_profile(h.h, 0)
     h.close()
+
+
+def test_profile_timeline_orders_stages(nif, torus):
+    h = nif.Nif(S.NetConfig(), torus, seed=4)
+    nif.nif_train_steps(h.h, 1, 1 << 14, 4, 21)
+    nif.nif_profile(h.h, 1)
+    nif.nif_train_steps(h.h, 2, 1 << 14, 4, 22)
+    tl = nif.nif_profile_timeline(h.h)
+    prof = nif.nif_profile_read(h.h)
+    nif.nif_profile(h.h, 0)
+    h.close()
+    assert tl[0][1] == 0.0 and all(b >= a for _, a, b in tl)
+    names = [n for n, _, _ in tl]
+    assert names.count("adam") == 2 and names.count("encode_bwd") == 2
+    # the same intervals as the folded sums
+    tot = sum(b - a for n, a, b in tl if n == "encode_bwd")
+    assert abs(tot - prof["encode_bwd"][0]) < 1e-3 * max(1.0, tot)
+    # a step's Adam update follows its encoding backward on the step's stream
+    i_bwd = names.index("encode_bwd")
+    i_adam = names.index("adam")
+    assert tl[i_adam][1] >= tl[i_bwd][2] - 1e-3
