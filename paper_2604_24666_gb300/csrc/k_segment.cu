@@ -847,15 +847,23 @@ __global__ void __launch_bounds__(256) k_seg_scatter(const nif_segment* __restri
 }
 
 // ... and sorts every ray's row by (t0, voxel). A warp takes 32 consecutive
-// rays, whose rows are one contiguous range: it is loaded into shared memory
-// with coalesced 16-byte accesses, each lane sorts its ray's row there, and
-// the range goes back the same way (a range longer than kSortCap segments is
-// sorted in place in global memory).
+// rays, whose rows are one contiguous range of at most kSortCap segments:
+// lane l loads elements l, l + 32, ... of the range (coalesced) into
+// registers and their keys into shared memory. Each element, not each row,
+// then belongs to a lane, which counts the elements of the element's row
+// that precede it (smaller (t0, voxel), ties by position: the stable order
+// an insertion sort gives) and stores the element at that rank. A row of n
+// costs n^2 compares spread over the warp's lanes, instead of n^2/2 serial
+// steps on one lane while the others wait for the longest row. A longer
+// range is sorted in place in global memory.
 constexpr int kSortCap = 256;
+constexpr int kSortPer = kSortCap / 32;
 
 __global__ void __launch_bounds__(256) k_seg_sort(const uint32_t* __restrict__ offsets, int n_rays,
                                                   nif_segment* __restrict__ segs, int64_t cap) {
-    __shared__ nif_segment sh[8][kSortCap];
+    __shared__ float2 s_key[8][kSortCap];           // (t0, voxel bits) of each element
+    __shared__ uint8_t s_row[8][kSortCap];          // the warp-local row (lane) of each element
+    __shared__ uint16_t s_beg[8][33];               // row bounds, relative to the range
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = (blockIdx.x * 8 + warp) * 32;
     if (r0 >= n_rays) return;
@@ -865,16 +873,40 @@ __global__ void __launch_bounds__(256) k_seg_sort(const uint32_t* __restrict__ o
     const int64_t b = clampc(offsets[r0]), e = clampc(offsets[r1]);
     const int64_t mb = r < n_rays ? clampc(offsets[r]) : e;
     const int64_t me = r < n_rays ? clampc(offsets[r + 1]) : e;
-    const int64_t len = e - b;
+    const int len = (int)(e - b);
     if (len > kSortCap) {
         sort_row_inplace(segs, mb, me);
         return;
     }
-    for (int64_t i = lane; i < len; i += 32) sh[warp][i] = segs[b + i];
+    nif_segment el[kSortPer];
+#pragma unroll
+    for (int k = 0; k < kSortPer; k++) {
+        const int i = lane + 32 * k;
+        if (i < len) {
+            el[k] = segs[b + i];
+            s_key[warp][i] = make_float2(el[k].t0, __uint_as_float(el[k].voxel));
+        }
+    }
+    s_beg[warp][lane] = (uint16_t)(mb - b);
+    if (lane == 31) s_beg[warp][32] = (uint16_t)len;
+    for (int i = (int)(mb - b); i < (int)(me - b); i++) s_row[warp][i] = (uint8_t)lane;
     __syncwarp();
-    sort_row_inplace(sh[warp], mb - b, me - b);
-    __syncwarp();
-    for (int64_t i = lane; i < len; i += 32) segs[b + i] = sh[warp][i];
+#pragma unroll
+    for (int k = 0; k < kSortPer; k++) {
+        const int i = lane + 32 * k;
+        if (i >= len) break;
+        const int row = s_row[warp][i];
+        const int j0 = s_beg[warp][row], j1 = s_beg[warp][row + 1];
+        const float t = el[k].t0;
+        const uint32_t v = el[k].voxel;
+        int rank = 0;
+        for (int j = j0; j < j1; j++) {
+            const float2 o = s_key[warp][j];
+            const uint32_t ov = __float_as_uint(o.y);
+            rank += (o.x < t || (o.x == t && (ov < v || (ov == v && j < i)))) ? 1 : 0;
+        }
+        segs[b + j0 + rank] = el[k];
+    }
 }
 
 // ---------------------------------------------------------------------------
