@@ -762,7 +762,13 @@ __global__ void __launch_bounds__(kTravWarps * 32, 32 / kTravWarps) k_seg_traver
                 if (node < tree.n_leaves) {
                     cand = node;
                 } else {
-                    const RayPre& ray = s_ray[warp][lane];
+                    // the slab test's 8 ray values in registers for all
+                    // children (read from shared memory once per node)
+                    const RayPre& rs = s_ray[warp][lane];
+                    RayPre ray;
+                    ray.ox = rs.ox; ray.oy = rs.oy; ray.oz = rs.oz;
+                    ray.ix = rs.ix; ray.iy = rs.iy; ray.iz = rs.iz;
+                    ray.tmin = rs.tmin; ray.tmax = rs.tmax;
                     const float4* A = aabb + (int64_t)s_inst[warp][lane] * tree.n_nodes * 2;
                     const int2 ch = __ldg(tree.child + (node - tree.n_leaves));
                     if (sp + ch.y > kStack) {
