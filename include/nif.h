@@ -627,6 +627,15 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   the 64^3 FP32 step: 3.06-3.09 ms with priorities, 3.04-3.05 ms without:
  *   a batch that finishes later delays the step that needs it).
  *   Synchronises the device.
+ * NIF_KNOB_DEFER_WEIGHTS: 1 (default) lets an FP32 step of nif_train_steps
+ *   / nif_train_steps_rays update the tables on the step's stream right
+ *   after the encoding backward, and the MLP weights and log-variances on
+ *   the handle's second stream after the weight gradients, beside the next
+ *   step's encoding forward (which writes a second feature buffer); the next
+ *   step's MLP forward waits for that update, and every call ends with all
+ *   of it ordered on the caller's stream. 0 updates all parameters in one
+ *   launch after both gradients. The same Adam arithmetic either way.
+ *   Synchronises the device.
  * NIF_ERR_ARG for an unknown knob or a value out of range. */
 #define NIF_KNOB_WAIT_NS 1
 #define NIF_KNOB_SEG_SCRATCH 2
@@ -635,6 +644,7 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
 #define NIF_KNOB_FP32_FUSED 5
 #define NIF_KNOB_QUERY_FUSED 6
 #define NIF_KNOB_STEP_PRIORITY 7
+#define NIF_KNOB_DEFER_WEIGHTS 8
 nif_status nif_set_knob(nif_handle* h, int knob, double value);
 
 /* Allocation-free variant of nif_segments (the paper has no counterpart:

@@ -1,6 +1,8 @@
 // k_train.cu -- ground-truth labels of linearized segments (Sec. 2), task
 // losses with uncertainty weighting (Sec. 2.4), Adam, the segmented-ray
 // reconstruction (Sec. 2.2) and the counter-based sampler of training rays.
+#include <algorithm>
+
 #include "nif_internal.cuh"
 
 namespace {
@@ -543,6 +545,36 @@ nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels
     k_loss_final<<<1, 32, 0, s>>>(h->d_lossacc, n_dev, n_max, n_hit, h->d_params + h->off_s, h->cfg.flags,
                                   want_ds ? h->d_grad + h->off_s : nullptr, h->d_status);
     NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_adam_split_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s_tab, cudaStream_t s_w,
+                              bool* split) {
+    const size_t cut = h->off_layer[0];          // tables [0, cut), weights and log-variances [cut, n_params)
+    *split = cut % 4 == 0 && h->off_tables == 0 && cut < h->n_params;
+    if (!*split) return NIF_OK;
+    h->adam_step++;
+    const double c1 = 1.0 / (1.0 - pow(0.9, (double)h->adam_step));
+    const double c2 = 1.0 / (1.0 - pow(0.99, (double)h->adam_step));
+    const unsigned cap = (unsigned)h->num_sms * 16;
+    {
+        NifProf prof_(h, "adam", s_tab);
+        unsigned g = std::min(nif_blocks((int64_t)cut, 256), cap);
+        // relative to the range: no element of [0, cut) lies in [cut, off_s)
+        k_adam<<<g, 256, 0, s_tab>>>(h->d_params, h->d_grad, h->d_m, h->d_v, cut, cut, cut, lr_grid, lr_mlp,
+                                      (float)c1, (float)c2);
+        NIF_CK_LAUNCH(h);
+    }
+    {
+        NifProf prof_(h, "adam_weights", s_w);
+        const size_t n = h->n_params - cut;
+        unsigned g = std::min(nif_blocks((int64_t)n, 256), cap);
+        k_adam<<<g, 256, 0, s_w>>>(h->d_params + cut, h->d_grad + cut, h->d_m + cut, h->d_v + cut, n, 0,
+                                    h->off_s - cut, lr_grid, lr_mlp, (float)c1, (float)c2);
+        NIF_CK_LAUNCH(h);
+    }
+    h->lowp_dirty = true;
+    h->x3_dirty = true;
     return NIF_OK;
 }
 

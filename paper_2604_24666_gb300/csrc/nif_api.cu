@@ -520,6 +520,9 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
         CKC(cudaStreamCreateWithPriority(&h->aux_hi, cudaStreamNonBlocking, greatest));
     }
     CKC(cudaEventCreateWithFlags(&h->ev_hi_fork, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&h->ev_wupd, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&h->ev_dw[0], cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&h->ev_dw[1], cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&h->ev_hi_join, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&h->ev_batch, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&h->ev_step, cudaEventDisableTiming));
@@ -589,7 +592,7 @@ extern "C" void nif_destroy(nif_handle* h) {
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
                                &h->b_acts, &h->b_dout, &h->b_dx, &h->b_labels, &h->b_scan, &h->b_rays,
                                &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys, &h->b_dup, &h->b_pts,
-                               &h->b_lattice, &h->b_sort, &h->b_lin_t, &h->alt_counts, &h->alt_offsets, &h->alt_temp, &h->alt_segs,
+                               &h->b_lattice, &h->b_sort, &h->b_lin_t, &h->b_feat_alt, &h->alt_counts, &h->alt_offsets, &h->alt_temp, &h->alt_segs,
                                &h->alt_scan, &h->alt_rays, &h->alt_inst, &h->alt_lin, &h->alt_labels,
                                &h->alt_dup, &h->alt_pts, &h->alt_sort};
     for (auto* b : bufs)
@@ -607,6 +610,9 @@ extern "C" void nif_destroy(nif_handle* h) {
     if (h->hi) cudaStreamDestroy(h->hi);
     if (h->aux_hi) cudaStreamDestroy(h->aux_hi);
     if (h->ev_hi_fork) cudaEventDestroy(h->ev_hi_fork);
+    if (h->ev_wupd) cudaEventDestroy(h->ev_wupd);
+    for (cudaEvent_t e : h->ev_dw)
+        if (e) cudaEventDestroy(e);
     if (h->ev_hi_join) cudaEventDestroy(h->ev_hi_join);
     if (h->h_loss) cudaFreeHost(h->h_loss);
     if (h->ev_batch) cudaEventDestroy(h->ev_batch);
@@ -1345,7 +1351,8 @@ static nif_status train_batch(nif_handle* h, const nif_pose* poses, int n_inst, 
 // ev_next (nullable) is recorded on s where the next batch may start beside
 // the step: after the encoding forward (FP32 path only).
 static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, const int* n_hit, float lr_grid,
-                                float lr_mlp, double* loss_host, cudaStream_t s, cudaEvent_t ev_next = nullptr) {
+                                float lr_mlp, double* loss_host, cudaStream_t s, cudaEvent_t ev_next = nullptr,
+                                bool join_weights = true, int set = -1) {
     nif_status st;
     const bool mixed = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
     uint32_t* offs = (uint32_t*)h->b_offsets.p;
@@ -1392,11 +1399,25 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         if ((st = nif_grad_check_run(h, s)) != NIF_OK) return st;
         if ((st = nif_adam_scaled_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
     } else {
+        // With the weight update deferred, the weights' Adam of this step runs
+        // on the second stream after its weight gradients, beside the next
+        // step's encoding forward, which therefore writes the other feature
+        // buffer; the next step's MLP forward waits for that update.
+        const bool defer = h->tune.defer_wupd != 0;
+        if (defer) {
+            if ((st = nif_grow(h, h->b_feat_alt, sizeof(float) * (size_t)h->in_dim * n)) != NIF_OK) return st;
+            if (h->feat_flip) feat = (float*)h->b_feat_alt.p;
+            h->feat_flip ^= 1;
+        }
         // the next batch may start where the handle's placement knob says
         const int at = h->tune.batch_at;
         if (ev_next && at == 0) NIF_CK(h, cudaEventRecord(ev_next, s));
         if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, NIF_FP32, NIF_FP32, s, true)) != NIF_OK) return st;
         if (ev_next && at == 1) NIF_CK(h, cudaEventRecord(ev_next, s));
+        if (h->wupd_pending) {                  // the previous step's weights are updated
+            NIF_CK(h, cudaStreamWaitEvent(s, h->ev_wupd, 0));
+            h->wupd_pending = false;
+        }
         if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
         if (ev_next && at == 2) NIF_CK(h, cudaEventRecord(ev_next, s));
         if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, true, n_hit)) != NIF_OK) return st;
@@ -1405,8 +1426,22 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         if (ev_next && at >= 3) NIF_CK(h, cudaEventRecord(ev_next, s));
         if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s, true)) != NIF_OK)
             return st;
-        NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
-        if ((st = nif_adam_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
+        bool split = false;
+        if (defer && (st = nif_adam_split_run(h, lr_grid, lr_mlp, s, h->aux, &split)) != NIF_OK) return st;
+        if (split) {
+            NIF_CK(h, cudaEventRecord(h->ev_wupd, h->aux));
+            // a later batch built into this step's buffer set (its segment
+            // count is read by the weight gradients) waits for them
+            if (set >= 0) NIF_CK(h, cudaEventRecord(h->ev_dw[set], h->aux));
+            h->wupd_pending = true;
+            if (join_weights) {
+                NIF_CK(h, cudaStreamWaitEvent(s, h->ev_wupd, 0));
+                h->wupd_pending = false;
+            }
+        } else {
+            NIF_CK(h, cudaStreamWaitEvent(s, h->ev_join, 0));
+            if ((st = nif_adam_run(h, lr_grid, lr_mlp, s)) != NIF_OK) return st;
+        }
     }
     if (loss_host) {
         double acc[16];
@@ -1678,6 +1713,7 @@ static nif_status train_pipeline_on(nif_handle* h, int n_steps, const int& n_ray
         swap_batch(h);
         NIF_CK(h, cudaStreamWaitEvent(h->aux2, h->ev_batch, 0));   // batch i built: geometry and cursor free
         NIF_CK(h, cudaStreamWaitEvent(h->aux2, h->ev_step, 0));    // step i - 1 done with this set
+        NIF_CK(h, cudaStreamWaitEvent(h->aux2, h->ev_dw[(i + 1) % 2], 0));   // and its late weight gradients
         nif_status r = build(i + 1, h->d_count + 2 + (i + 1) % 2, h->aux2);
         if (r != NIF_OK) return r;
         NIF_CK(h, cudaEventRecord(h->ev_batch, h->aux2));
@@ -1692,7 +1728,7 @@ static nif_status train_pipeline_on(nif_handle* h, int n_steps, const int& n_ray
             swap_batch(h);                                                  // back to step i's set
         }
         if ((st = train_compute(h, n_rays, n_segments, h->d_count + 2 + i % 2, lr_grid, lr_mlp,
-                                more ? nullptr : loss_last, s, early ? nullptr : h->ev_step)) != NIF_OK)
+                                more ? nullptr : loss_last, s, early ? nullptr : h->ev_step, !more, i % 2)) != NIF_OK)
             return st;
         if ((st = done(i, s)) != NIF_OK) return st;
         if (more && !early && (st = next_batch(i)) != NIF_OK) return st;
@@ -1816,6 +1852,12 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
         case NIF_KNOB_FP32_FUSED:
             if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "fused FP32 forward knob must be 0 or 1");
             h->tune.fp32_fused = (int)value;
+            return NIF_OK;
+        case NIF_KNOB_DEFER_WEIGHTS:
+            if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "deferred weight update knob must be 0 or 1");
+            NIF_CK(h, cudaDeviceSynchronize());
+            h->tune.defer_wupd = (int)value;
+            h->wupd_pending = false;
             return NIF_OK;
         case NIF_KNOB_STEP_PRIORITY:
             if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "step priority knob must be 0 or 1");

@@ -160,7 +160,15 @@ struct nif_handle {
     // grown scratch buffers (query / train)
     struct Buf { void* p = nullptr; size_t bytes = 0; };
     Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
-        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts, b_lattice, b_sort, b_lin_t;
+        b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts, b_lattice, b_sort, b_lin_t,
+        b_feat_alt;                     // the other step's FP32 features while its weight gradients run late
+    // FP32 steps with the weight update deferred (NIF_KNOB_DEFER_WEIGHTS): the
+    // weights' Adam runs on the second stream after the weight gradients and
+    // records ev_wupd; the next step's MLP forward waits for it
+    cudaEvent_t ev_wupd = nullptr;
+    cudaEvent_t ev_dw[2] = {nullptr, nullptr};   // weight gradients of the last step on batch set k done
+    bool wupd_pending = false;
+    int feat_flip = 0;
     // the distinct end points of the last segment encoding (in b_dup, b_pts,
     // b_sort; sorted: in rest-space order), which the backward of the same
     // segments in a training step takes instead of listing them again
@@ -209,6 +217,7 @@ struct nif_handle {
                                         // than 1 on the 64^3 step, 2 and 3 are 0.1-0.2 ms slower)
         int fp32_fused = 0;             // NIF_KNOB_FP32_FUSED: the FP32 forward in one launch (measured equal
                                         // to the per-layer launches on the 64^3 step)
+        int defer_wupd = 1;             // NIF_KNOB_DEFER_WEIGHTS: FP32 steps update the weights beside the next step
         int step_prio = 0;              // NIF_KNOB_STEP_PRIORITY: pipelined steps on the high-priority streams
         int query_fused = 1;            // NIF_KNOB_QUERY_FUSED: 16-bit queries encode into the tensor-core
                                         // MLP's shared-memory ring (one launch) instead of two kernels
@@ -395,6 +404,12 @@ nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels
                         const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max, float* dout,
                         cudaStream_t s, bool want_ds = true, const int* n_hit = nullptr);
 nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s);
+// Adam over the tables (on s_tab) and over the weights and log-variances (on
+// s_w) as two launches of the same step (one step count, the same bias
+// corrections); false from *split when the ranges cannot be split on
+// 16-byte boundaries (then nothing is launched)
+nif_status nif_adam_split_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s_tab, cudaStream_t s_w,
+                              bool* split);
 nif_status nif_reconstruct_run(nif_handle* h, const nif_ray* rays, const int* inst_off, int n_inst,
                                int n_rays, const uint32_t* offsets, const nif_segment* segs,
                                int64_t seg_cap, const nif_linseg* lin, const float* out,

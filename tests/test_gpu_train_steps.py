@@ -219,3 +219,37 @@ def test_profile_timeline_orders_stages(nif, torus):
     i_bwd = names.index("encode_bwd")
     i_adam = names.index("adam")
     assert tl[i_adam][1] >= tl[i_bwd][2] - 1e-3
+
+
+@pytest.mark.parametrize("batch_at", [0, 1])
+def test_deferred_weight_update_trains_alike(nif, torus, batch_at):
+    """FP32 steps whose weights are updated on the second stream beside the
+    next step (NIF_KNOB_DEFER_WEIGHTS) follow the trajectory of steps that
+    update everything at once, and the parameters after the call are final:
+    losses of 12 pipelined steps agree up to the order of float atomics, and
+    the weights read back right after the call equal those of a handle that
+    trained the same steps one call at a time."""
+    net = S.NetConfig(levels=16, log2_table=16, mlp_depth=3, mlp_width=64)
+    a = nif.Nif(net, torus, seed=19)
+    b = nif.Nif(net, torus, seed=19)
+    for h, d in ((a, 1), (b, 0)):
+        nif.nif_set_knob(h.h, nif.NIF_KNOB_DEFER_WEIGHTS, d)
+        nif.nif_set_knob(h.h, nif.NIF_KNOB_BATCH_AT, batch_at)
+    # learning rates 0: the batches alone decide the losses
+    la = nif.nif_train_steps(a.h, 3, 1 << 15, 8, 700, lr_grid=0.0, lr_mlp=0.0, want_loss=True)
+    lb = nif.nif_train_steps(b.h, 3, 1 << 15, 8, 700, lr_grid=0.0, lr_mlp=0.0, want_loss=True)
+    np.testing.assert_allclose(la, lb, rtol=1e-6, atol=1e-9)
+    la = nif.nif_train_steps(a.h, 12, 1 << 15, 8, 800, lr_grid=1e-2, lr_mlp=1e-3, want_loss=True)
+    lb = nif.nif_train_steps(b.h, 12, 1 << 15, 8, 800, lr_grid=1e-2, lr_mlp=1e-3, want_loss=True)
+    np.testing.assert_allclose(la[1:], lb[1:], rtol=2e-2, atol=1e-4)
+    # a single step with lr 0 then reads the updated weights: a stale copy
+    # (the last update still running) would change this loss
+    ta, wa, _ = a.get_params()
+    tb, wb, _ = b.get_params()
+    for x, y in zip(wa, wb):
+        np.testing.assert_allclose(x, y, rtol=5e-2, atol=1e-3)
+    l1 = nif.nif_train_steps(a.h, 1, 1 << 15, 8, 900, lr_grid=0.0, lr_mlp=0.0, want_loss=True)
+    l2, _ = nif.nif_train_step(a.h, 1 << 15, 8, 900, lr_grid=0.0, lr_mlp=0.0, want_loss=True)
+    np.testing.assert_allclose(l1, l2, rtol=1e-6, atol=1e-9)
+    a.close()
+    b.close()
