@@ -11,12 +11,28 @@ namespace {
 // Labels: straight rest segment p0 -> p1 against the voxel's triangles
 // (Moeller-Trumbore, FP32); first hit in [0,1], ties to the smaller id.
 // ---------------------------------------------------------------------------
+// One record per triangle for the labels: A, e1 = B - A, e2 = C - A, each
+// difference the FP32 subtraction the test would do, read as 3 float4 in
+// place of 3 vertex indices and 9 dependent vertex loads.
+__global__ void __launch_bounds__(256) k_tri_geo(const float* __restrict__ verts, const int* __restrict__ tris,
+                                                 int n_tris, float4* __restrict__ geo) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tris; t += gridDim.x * blockDim.x) {
+        const int i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
+        const float Ax = verts[3 * i0], Ay = verts[3 * i0 + 1], Az = verts[3 * i0 + 2];
+        const float e1x = verts[3 * i1] - Ax, e1y = verts[3 * i1 + 1] - Ay, e1z = verts[3 * i1 + 2] - Az;
+        const float e2x = verts[3 * i2] - Ax, e2y = verts[3 * i2 + 1] - Ay, e2z = verts[3 * i2 + 2] - Az;
+        geo[3 * t] = make_float4(Ax, Ay, Az, e1x);
+        geo[3 * t + 1] = make_float4(e1y, e1z, e2x, e2y);
+        geo[3 * t + 2] = make_float4(e2z, 0.f, 0.f, 0.f);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_labels(const nif_segment* __restrict__ segs,
                                                 const nif_linseg* __restrict__ lin,
                                                 const uint32_t* __restrict__ n_dev, int64_t n_max,
                                                 const uint32_t* __restrict__ tri_ptr,
                                                 const int32_t* __restrict__ tri_idx,
-                                                const float* __restrict__ verts, const int* __restrict__ tris,
+                                                const float4* __restrict__ geo,
                                                 const float* __restrict__ alb, const uint8_t* __restrict__ mat,
                                                 nif_label* __restrict__ out, int* __restrict__ n_hit,
                                                 uint32_t nvox) {
@@ -34,10 +50,10 @@ __global__ void __launch_bounds__(256) k_labels(const nif_segment* __restrict__ 
         int bt = -1;
         for (uint32_t q = a; q < b; q++) {
             int t = tri_idx[q];
-            int i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
-            float Ax = verts[3 * i0], Ay = verts[3 * i0 + 1], Az = verts[3 * i0 + 2];
-            float e1x = verts[3 * i1] - Ax, e1y = verts[3 * i1 + 1] - Ay, e1z = verts[3 * i1 + 2] - Az;
-            float e2x = verts[3 * i2] - Ax, e2y = verts[3 * i2 + 1] - Ay, e2z = verts[3 * i2 + 2] - Az;
+            const float4 g0 = __ldg(geo + 3 * t), g1 = __ldg(geo + 3 * t + 1), g2 = __ldg(geo + 3 * t + 2);
+            float Ax = g0.x, Ay = g0.y, Az = g0.z;
+            float e1x = g0.w, e1y = g1.x, e1z = g1.y;
+            float e2x = g1.z, e2y = g1.w, e2z = g2.x;
             float px = dy * e2z - dz * e2y, py = dz * e2x - dx * e2z, pz = dx * e2y - dy * e2x;
             float det = e1x * px + e1y * py + e1z * pz;
             if (det == 0.f) continue;
@@ -60,11 +76,9 @@ __global__ void __launch_bounds__(256) k_labels(const nif_segment* __restrict__ 
             lab.occ = 0;
             lab.material = 0;
         } else {
-            int i0 = tris[3 * bt], i1 = tris[3 * bt + 1], i2 = tris[3 * bt + 2];
-            float e1x = verts[3 * i1] - verts[3 * i0], e1y = verts[3 * i1 + 1] - verts[3 * i0 + 1],
-                  e1z = verts[3 * i1 + 2] - verts[3 * i0 + 2];
-            float e2x = verts[3 * i2] - verts[3 * i0], e2y = verts[3 * i2 + 1] - verts[3 * i0 + 1],
-                  e2z = verts[3 * i2 + 2] - verts[3 * i0 + 2];
+            const float4 g0 = __ldg(geo + 3 * bt), g1 = __ldg(geo + 3 * bt + 1), g2 = __ldg(geo + 3 * bt + 2);
+            float e1x = g0.w, e1y = g1.x, e1z = g1.y;
+            float e2x = g1.z, e2y = g1.w, e2z = g2.x;
             float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
             float il = rsqrtf(nx * nx + ny * ny + nz * nz);
             lab.tpar = best;
@@ -522,8 +536,15 @@ nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_lins
     unsigned g = nif_blocks(n_max, 256);
     unsigned cap = (unsigned)h->num_sms * 8;
     if (g > cap) g = cap;
-    k_labels<<<g, 256, 0, s>>>(segs, lin, n_dev, n_max, h->d_tri_ptr, h->d_tri_idx, h->d_verts, h->d_tris, h->d_alb,
+    k_labels<<<g, 256, 0, s>>>(segs, lin, n_dev, n_max, h->d_tri_ptr, h->d_tri_idx, h->d_tri_geo, h->d_alb,
                                h->d_mat, labels, n_hit, (uint32_t)((int64_t)h->N * h->N * h->N));
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+nif_status nif_tri_geo_run(nif_handle* h, cudaStream_t s) {
+    if (h->n_tris <= 0) return NIF_OK;
+    k_tri_geo<<<nif_blocks(h->n_tris, 256), 256, 0, s>>>(h->d_verts, h->d_tris, h->n_tris, h->d_tri_geo);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

@@ -502,6 +502,9 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
         if (h->n_tris) CKC(cudaMemcpy(h->d_tris, mesh->tris, sizeof(int) * 3 * h->n_tris, cudaMemcpyHostToDevice));
         CKC(cudaMemcpy(h->d_alb, alb.data(), sizeof(float) * alb.size(), cudaMemcpyHostToDevice));
         CKC(cudaMemcpy(h->d_mat, mat.data(), mat.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMalloc(&h->d_tri_geo, sizeof(float4) * 3 * (size_t)std::max(h->n_tris, 1)));
+        if (nif_tri_geo_run(h, nullptr) != NIF_OK) return fail(NIF_ERR_CUDA);
+        CKC(cudaDeviceSynchronize());
     }
     CKC(cudaMalloc(&h->d_status, sizeof(int) * 4));
     CKC(cudaMemset(h->d_status, 0, sizeof(int) * 4));
@@ -582,7 +585,7 @@ extern "C" nif_status nif_create(const nif_config* cfg, const nif_mesh* mesh, ni
 extern "C" void nif_destroy(nif_handle* h) {
     if (!h) return;
     cudaDeviceSynchronize();
-    void* ptrs[] = {h->d_verts, h->d_tris, h->d_alb, h->d_mat, h->d_occ, h->d_tri_ptr, h->d_tri_idx, h->d_child,
+    void* ptrs[] = {h->d_verts, h->d_tris, h->d_tri_geo, h->d_alb, h->d_mat, h->d_occ, h->d_tri_ptr, h->d_tri_idx, h->d_child,
                     h->d_leaf_vox, h->d_leaf_lat, h->d_corners, h->d_aabb, h->d_pose, h->d_params, h->d_grad,
                     h->d_m, h->d_v, h->d_tables_h, h->d_w_bf16, h->d_w_f16, h->d_wt_bf16, h->d_wt_f16, h->d_ls,
                     h->d_w_x3, h->d_vox_leaf, h->d_status, h->d_lossacc, h->d_count,

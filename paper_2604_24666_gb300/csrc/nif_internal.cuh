@@ -71,6 +71,7 @@ struct nif_handle {
     // mesh (device copy)
     float* d_verts = nullptr;
     int* d_tris = nullptr;
+    float4* d_tri_geo = nullptr;        // per triangle A, B - A, C - A in 3 float4 (w of the third unused)
     float* d_alb = nullptr;
     uint8_t* d_mat = nullptr;
     int n_verts = 0, n_tris = 0;
@@ -396,6 +397,8 @@ nif_status nif_adam_scaled_run(nif_handle* h, float lr_grid, float lr_mlp, cudaS
 nif_status nif_labels_count_hits(nif_handle* h, const nif_label* labels, int64_t n, cudaStream_t s);
 // n_hit (device int, default the handle's first counter word): the count of
 // labelled hits, written by nif_labels_run and read by nif_loss_run
+// the labels' per-triangle records (d_tri_geo) from d_verts and d_tris
+nif_status nif_tri_geo_run(nif_handle* h, cudaStream_t s);
 nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin,
                           const uint32_t* n_dev, int64_t n_max, nif_label* labels, cudaStream_t s,
                           int* n_hit = nullptr);
