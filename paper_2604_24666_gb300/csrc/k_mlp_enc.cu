@@ -43,6 +43,7 @@ namespace {
 constexpr int kRows = 128;                          // MMA M, rows per tile
 constexpr uint32_t kStageBytes = kRows * 128;       // one 128 x 64 box of 16-bit features
 constexpr uint32_t kGrpBytes = 768;                 // per group: point list, dup flags, warp sums, decision
+constexpr int kLB = 2;                              // levels whose corner loads a producer issues together
 
 struct EncLayout {
     uint32_t wo_off, w0_off, wh_off, a_off, x_off, grp_off, bar_off, total;
@@ -343,28 +344,36 @@ __global__ void __launch_bounds__((5 + G * GW) * 32, 1)
                 for (int tt = 0; tt < nterm; tt++) {
                     const float3 u = term_u_fast(p, t0 + tt);
                     uint32_t res[L];
+                    // kLB levels at a time: their 8 kLB corner loads in flight together
 #pragma unroll
-                    for (int l = 0; l < L; l++) {
-                        const Cell c = cell_of(u, g.res[l]);
-                        typename RawRow<__half>::T vr[8];
-                        level_gather<__half>(g, tab, l, c, vr);
-                        // corner weights (x fastest), then both features of a
-                        // corner in one packed FP32 FMA
-                        const float2 wx = make_float2(1.f - c.wx, c.wx);
-                        const float wy0 = 1.f - c.wy, wy1 = c.wy, wz0 = 1.f - c.wz, wz1 = c.wz;
-                        const float2 wxy0 = __fmul2_rn(wx, make_float2(wy0, wy0));
-                        const float2 wxy1 = __fmul2_rn(wx, make_float2(wy1, wy1));
-                        const float2 wq[4] = {__fmul2_rn(wxy0, make_float2(wz0, wz0)),
-                                              __fmul2_rn(wxy1, make_float2(wz0, wz0)),
-                                              __fmul2_rn(wxy0, make_float2(wz1, wz1)),
-                                              __fmul2_rn(wxy1, make_float2(wz1, wz1))};
-                        float2 acc = make_float2(0.f, 0.f);
+                    for (int l0 = 0; l0 < L; l0 += kLB) {
+                        Cell c[kLB];
+                        typename RawRow<__half>::T vr[kLB][8];
 #pragma unroll
-                        for (int q = 0; q < 8; q++) {
-                            const float w = (q & 1) ? wq[q >> 1].y : wq[q >> 1].x;
-                            acc = __ffma2_rn(make_float2(w, w), RawRow<__half>::f2(vr[q]), acc);
+                        for (int i = 0; i < kLB; i++) {
+                            c[i] = cell_of(u, g.res[l0 + i]);
+                            level_gather<__half>(g, tab, l0 + i, c[i], vr[i]);
                         }
-                        res[l] = pack2(acc.x, acc.y, fmt);
+#pragma unroll
+                        for (int i = 0; i < kLB; i++) {
+                            // corner weights (x fastest), then both features of a
+                            // corner in one packed FP32 FMA
+                            const float2 wx = make_float2(1.f - c[i].wx, c[i].wx);
+                            const float wy0 = 1.f - c[i].wy, wy1 = c[i].wy, wz0 = 1.f - c[i].wz, wz1 = c[i].wz;
+                            const float2 wxy0 = __fmul2_rn(wx, make_float2(wy0, wy0));
+                            const float2 wxy1 = __fmul2_rn(wx, make_float2(wy1, wy1));
+                            const float2 wq[4] = {__fmul2_rn(wxy0, make_float2(wz0, wz0)),
+                                                  __fmul2_rn(wxy1, make_float2(wz0, wz0)),
+                                                  __fmul2_rn(wxy0, make_float2(wz1, wz1)),
+                                                  __fmul2_rn(wxy1, make_float2(wz1, wz1))};
+                            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                            for (int q = 0; q < 8; q++) {
+                                const float w = (q & 1) ? wq[q >> 1].y : wq[q >> 1].x;
+                                acc = __ffma2_rn(make_float2(w, w), RawRow<__half>::f2(vr[i][q]), acc);
+                            }
+                            res[l0 + i] = pack2(acc.x, acc.y, fmt);
+                        }
                     }
                     // row r's (term, e) columns; an exit point that the next row
                     // repeats also goes to that row's (term, entry) columns
