@@ -253,3 +253,26 @@ def test_deferred_weight_update_trains_alike(nif, torus, batch_at):
     np.testing.assert_allclose(l1, l2, rtol=1e-6, atol=1e-9)
     a.close()
     b.close()
+
+
+def test_high_priority_streams_compute_the_same(nif, torus):
+    """NIF_KNOB_STEP_PRIORITY moves the steps onto the handle's high-priority
+    streams (joined back into the caller's): the same batches and losses."""
+    net = S.NetConfig()
+    a = nif.Nif(net, torus, seed=23)
+    b = nif.Nif(net, torus, seed=23)
+    nif.nif_set_knob(b.h, nif.NIF_KNOB_STEP_PRIORITY, 1)
+    for K in (1, 4):
+        la = nif.nif_train_steps(a.h, K, 1 << 14, 8, 600 + K, lr_grid=0.0, lr_mlp=0.0, want_loss=True)
+        lb = nif.nif_train_steps(b.h, K, 1 << 14, 8, 600 + K, lr_grid=0.0, lr_mlp=0.0, want_loss=True)
+        np.testing.assert_allclose(la, lb, rtol=1e-6, atol=1e-9)
+    # the caller's stream is ordered after the call: parameters read back at once
+    la = nif.nif_train_steps(a.h, 6, 1 << 14, 8, 650, lr_grid=1e-2, lr_mlp=5e-3, want_loss=True)
+    lb = nif.nif_train_steps(b.h, 6, 1 << 14, 8, 650, lr_grid=1e-2, lr_mlp=5e-3, want_loss=True)
+    np.testing.assert_allclose(la[1:], lb[1:], rtol=2e-2, atol=1e-4)
+    _, wa, _ = a.get_params()
+    _, wb, _ = b.get_params()
+    for x, y in zip(wa, wb):
+        np.testing.assert_allclose(x, y, rtol=5e-2, atol=1e-3)
+    a.close()
+    b.close()
