@@ -333,16 +333,24 @@ def run_ours(args):
     clocks = clk.stop() if clk else None
     ms_max = _max_over_ranks(ms, ws)
     value = ws * args.steps * N_SEG / (ms_max / 1e3)
-    # the FP32 forward in one launch (NIF_KNOB_FP32_FUSED) beside the per-layer launches
-    nif.nif_set_knob(h.h, nif.NIF_KNOB_FP32_FUSED, 1)
-    ms_fused, prof_fused = timed_steps(args.steps, seed0 + args.warmup + 2 * args.steps)
+    # the default one-launch FP32 forward on part of the SMs beside the
+    # alternatives: on every SM (NIF_KNOB_STEP_FWD_CTAS = -1) and one launch
+    # per layer (NIF_KNOB_FP32_FUSED = 0)
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_STEP_FWD_CTAS, -1)
+    ms_all_sms, prof_all_sms = timed_steps(args.steps, seed0 + args.warmup + 2 * args.steps)
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_STEP_FWD_CTAS, 0)
     nif.nif_set_knob(h.h, nif.NIF_KNOB_FP32_FUSED, 0)
-    fused_fwd = {"ms_per_step": ms_fused / args.steps,
-                 "mlp_fwd_fp32_ms": prof_fused["mlp_fwd_fp32"][0] / args.steps,
-                 "per_layer": {"ms_per_step": ms_all / args.steps,
-                               "mlp_fwd_fp32_ms": prof["mlp_fwd_fp32"][0] / args.steps},
-                 "note": "both with every stage's events on; the fused launch keeps hidden activations in "
-                         "shared memory and still writes those the backward reads"}
+    ms_layer, prof_layer = timed_steps(args.steps, seed0 + args.warmup + 3 * args.steps)
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_FP32_FUSED, 1)
+    fused_fwd = {"ms_per_step": ms_all / args.steps,
+                 "mlp_fwd_fp32_ms": prof["mlp_fwd_fp32"][0] / args.steps,
+                 "one_launch_every_sm": {"ms_per_step": ms_all_sms / args.steps,
+                                         "mlp_fwd_fp32_ms": prof_all_sms["mlp_fwd_fp32"][0] / args.steps},
+                 "per_layer": {"ms_per_step": ms_layer / args.steps,
+                               "mlp_fwd_fp32_ms": prof_layer["mlp_fwd_fp32"][0] / args.steps},
+                 "note": "all with every stage's events on; the one-launch forward keeps hidden activations in "
+                         "shared memory and still writes those the backward reads; by default it runs on 3/4 of "
+                         "the SMs (tile-balanced) while the next batch is built beside it"}
     loss, _ = nif.nif_train_step(h.h, N_SEG, N_POSES, seed0 + 99999, want_loss=True)
 
     # ---- dominant stage and its roofline -------------------------------

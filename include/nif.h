@@ -607,11 +607,14 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   of nif_train_steps / nif_train_steps_rays: 0 with the step (default),
  *   1 after the encoding forward, 2 after the MLP forward, 3 after the MLP
  *   backward. A scheduling choice only: the steps compute the same.
- * NIF_KNOB_FP32_FUSED: 1 runs every layer of the FP32 MLP forward in one
- *   persistent launch whose hidden activations stay in shared memory (the
- *   activations the backward needs are still written), 0 one launch per
- *   layer (default). Applies to hidden widths 32 and 64 with at least one
- *   hidden layer and in_dim a multiple of 4; the results are the same.
+ * NIF_KNOB_FP32_FUSED: 1 (default) runs every layer of the FP32 MLP forward
+ *   in one persistent launch whose hidden activations stay in shared memory
+ *   (a training step still writes the activations its backward reads; a
+ *   query writes none), 0 one launch per layer, in training steps,
+ *   nif_mlp_forward and queries alike. Applies to hidden widths 32 and 64
+ *   with at least one hidden layer and in_dim a multiple of 4; the results
+ *   are the same. An autotuned query plan of an FP32 handle times both and
+ *   keeps the faster for its queries (the training steps keep the knob's).
  * NIF_KNOB_QUERY_FUSED: 1 (default) computes a BF16/FP16 query's encoding
  *   (Eq. 1) inside the tensor-core MLP's kernel, which keeps each tile's
  *   features in shared memory (handles with L in {4, 8, 16}, F_d = 2, width
@@ -636,6 +639,14 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   of it ordered on the caller's stream. 0 updates all parameters in one
  *   launch after both gradients. The same Adam arithmetic either way.
  *   Synchronises the device.
+ * NIF_KNOB_STEP_FWD_CTAS: persistent CTAs of a training step's MLP forward
+ *   (the one-launch FP32 forward or the 16-bit tensor-core forward) while
+ *   nif_train_steps / nif_train_steps_rays build the next batch beside it.
+ *   0 (default): the FP32 forward takes three quarters of the SMs, then the
+ *   fewest CTAs that give each the same number of 128-row tiles, so that the
+ *   batch's kernels keep the other SMs, and the 16-bit forward one CTA per
+ *   SM; k > 0: k CTAs (at most one per SM); -1: one per SM. A scheduling
+ *   choice only: the steps compute the same.
  * NIF_ERR_ARG for an unknown knob or a value out of range. */
 #define NIF_KNOB_WAIT_NS 1
 #define NIF_KNOB_SEG_SCRATCH 2
@@ -645,6 +656,7 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
 #define NIF_KNOB_QUERY_FUSED 6
 #define NIF_KNOB_STEP_PRIORITY 7
 #define NIF_KNOB_DEFER_WEIGHTS 8
+#define NIF_KNOB_STEP_FWD_CTAS 9
 nif_status nif_set_knob(nif_handle* h, int knob, double value);
 
 /* Allocation-free variant of nif_segments (the paper has no counterpart:

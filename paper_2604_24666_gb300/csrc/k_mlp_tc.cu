@@ -717,7 +717,7 @@ TcLayout make_layout(int W, int K0, int H) {
 
 template <int W>
 nif_status launch_tc(nif_handle* h, const void* x, int dtype, int64_t n, const uint32_t* n_dev, float* out,
-                     uint16_t* acts_out, int64_t acts_rows, int acts_ld, cudaStream_t s) {
+                     uint16_t* acts_out, int64_t acts_rows, int acts_ld, cudaStream_t s, int ctas) {
     TcLayout lay = make_layout(W, h->in_dim, h->H);
     for (int l = 0; l < h->n_layers; l++) {
         lay.woff[l] = (uint32_t)(h->off_layer[l] - h->off_layer[0]);
@@ -736,7 +736,7 @@ nif_status launch_tc(nif_handle* h, const void* x, int dtype, int64_t n, const u
     if (r != CUDA_SUCCESS) return nif_fail(h, NIF_ERR_ARG, "cuTensorMapEncodeTiled failed for the feature matrix");
     NIF_CK(h, cudaFuncSetAttribute(k_mlp_tc<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total));
     int64_t n_tiles = (n + kRows - 1) / kRows;
-    int grid = (int)std::min<int64_t>(n_tiles, h->num_sms);
+    int grid = (int)std::min<int64_t>(n_tiles, ctas > 0 ? std::min(ctas, h->num_sms) : h->num_sms);
     const uint16_t* w = reinterpret_cast<const uint16_t*>(dtype == NIF_BF16 ? (const void*)h->d_w_bf16
                                                                              : (const void*)h->d_w_f16);
     k_mlp_tc<W><<<grid, kThreads, lay.total, s>>>(map, lay, w, h->in_dim, h->H, dtype == NIF_BF16 ? 1 : 0, n, n_dev,
@@ -753,7 +753,8 @@ nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uin
 }
 
 nif_status nif_mlp_fwd_tc_acts_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev, int64_t n_max,
-                                   float* out, uint16_t* acts_out, int64_t acts_rows, int acts_ld, cudaStream_t s) {
+                                   float* out, uint16_t* acts_out, int64_t acts_rows, int acts_ld, cudaStream_t s,
+                                   int ctas) {
     NifProf prof_(h, "mlp_fwd_tc", s);
     if (n_max <= 0) return NIF_OK;
     if (dtype != NIF_BF16 && dtype != NIF_FP16) return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP dtype");
@@ -763,9 +764,9 @@ nif_status nif_mlp_fwd_tc_acts_run(nif_handle* h, const void* x, int dtype, cons
     if (st != NIF_OK) return st;
     if ((st = nif_refresh_lowp(h, s)) != NIF_OK) return st;
     switch (h->W) {
-        case 32: return launch_tc<32>(h, x, dtype, n_max, n_dev, out, acts_out, acts_rows, acts_ld, s);
-        case 64: return launch_tc<64>(h, x, dtype, n_max, n_dev, out, acts_out, acts_rows, acts_ld, s);
-        case 128: return launch_tc<128>(h, x, dtype, n_max, n_dev, out, acts_out, acts_rows, acts_ld, s);
+        case 32: return launch_tc<32>(h, x, dtype, n_max, n_dev, out, acts_out, acts_rows, acts_ld, s, ctas);
+        case 64: return launch_tc<64>(h, x, dtype, n_max, n_dev, out, acts_out, acts_rows, acts_ld, s, ctas);
+        case 128: return launch_tc<128>(h, x, dtype, n_max, n_dev, out, acts_out, acts_rows, acts_ld, s, ctas);
         default: return nif_fail(h, NIF_ERR_ARG, "tensor-core MLP width must be 32, 64 or 128");
     }
 }

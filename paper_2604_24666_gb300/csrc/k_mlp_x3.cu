@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(kX3Threads, 1)
                             *reinterpret_cast<float4*>(ahp + off) = hv;
                             *reinterpret_cast<float4*>(alp + off) = lv;
                         }
-                        x3_store<kX3Relu, 32>(so, stg, v, nullptr, lane, row0, n, c0);
+                        if (a.acts) x3_store<kX3Relu, 32>(so, stg, v, nullptr, lane, row0, n, c0);
                     }
                     fence_async_smem();
                     tc_fence_before();
@@ -1018,10 +1018,11 @@ nif_status dw_x3(nif_handle* h, const float* X, int64_t ldx, int in_l, const flo
     return NIF_OK;
 }
 
-// The whole forward in one launch (W = 32 or 64): acts [H][n_max][W], out [n_max][NIF_OUT].
+// The whole forward in one launch (W = 32 or 64): acts [H][n_max][W] (null:
+// not stored), out [n_max][NIF_OUT]; ctas > 0 caps the persistent CTAs.
 template <int W>
 nif_status mlp_fwd_x3_fused(nif_handle* h, const float* x, int64_t n_max, const uint32_t* n_dev, float* acts,
-                            float* out, cudaStream_t s) {
+                            float* out, cudaStream_t s, int ctas) {
     X3FwdArgs a{};
     a.acts = acts; a.out = out; a.n_max = n_max;
     a.K0 = h->in_dim; a.W = W; a.H = h->H;
@@ -1054,7 +1055,7 @@ nif_status mlp_fwd_x3_fused(nif_handle* h, const float* x, int64_t n_max, const 
     const uint32_t total = a.bar_off + bars + 1024u;
     NIF_CK(h, cudaFuncSetAttribute(k_mlp_x3_fwd<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total));
     const int64_t tiles = (n_max + 127) / 128;
-    const int grid = (int)std::min<int64_t>(tiles, h->num_sms);
+    const int grid = (int)std::min<int64_t>(tiles, ctas > 0 ? std::min(ctas, h->num_sms) : h->num_sms);
     k_mlp_x3_fwd<W><<<grid, kX3Threads, total, s>>>(am, wm, a, n_dev, h->d_status);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
@@ -1103,16 +1104,18 @@ nif_status nif_refresh_x3(nif_handle* h, cudaStream_t s) {
 }
 
 nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max, float* out,
-                                float* acts, cudaStream_t s) {
+                                float* acts, cudaStream_t s, int ctas, bool query) {
     NifProf prof_(h, "mlp_fwd_fp32", s);
     if (n_max <= 0) return NIF_OK;
     nif_status st = get_encoder(h);
     if (st != NIF_OK) return st;
     if ((st = nif_refresh_x3(h, s)) != NIF_OK) return st;
     // hidden widths 32 and 64 on request: every layer in one launch, hidden activations on chip
-    const bool fusable = h->tune.fp32_fused && h->H >= 1 && h->H < NIF_MAX_LAYERS && h->in_dim % 4 == 0;
-    if (fusable && h->W == 64) return mlp_fwd_x3_fused<64>(h, x, n_max, n_dev, acts, out, s);
-    if (fusable && h->W == 32) return mlp_fwd_x3_fused<32>(h, x, n_max, n_dev, acts, out, s);
+    const bool fusable = (query ? h->tune.query_fp32_fused : h->tune.fp32_fused) && h->H >= 1 &&
+                         h->H < NIF_MAX_LAYERS && h->in_dim % 4 == 0;
+    float* kept = query ? nullptr : acts;        // a query needs no hidden activations
+    if (fusable && h->W == 64) return mlp_fwd_x3_fused<64>(h, x, n_max, n_dev, kept, out, s, ctas);
+    if (fusable && h->W == 32) return mlp_fwd_x3_fused<32>(h, x, n_max, n_dev, kept, out, s, ctas);
     const float* in = x;
     int64_t in_ld = h->in_dim;
     for (int l = 0; l < h->n_layers; l++) {

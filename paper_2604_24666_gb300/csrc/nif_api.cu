@@ -1253,7 +1253,7 @@ static nif_status query_encode_mlp(nif_handle* h, const nif_linseg* lin, const u
                 NIF_OK)
                 return st;
             if ((st = nif_mlp_fwd_fp32_run(h, (const float*)h->b_feat.p, cn, len, out + c0 * NIF_OUT,
-                                           (float*)h->b_acts.p, s)) != NIF_OK)
+                                           (float*)h->b_acts.p, s, 0, true)) != NIF_OK)
                 return st;
         } else {
             if ((st = nif_encode_segments_run(h, lin + c0, cn, len, h->b_feat.p, prec, NIF_FP16, s, false, dedup)) !=
@@ -1353,6 +1353,23 @@ static nif_status train_batch(nif_handle* h, const nif_pose* poses, int n_inst, 
 // batch buffers (n_rays rays, at most n_segments segments; hit count *n_hit).
 // ev_next (nullable) is recorded on s where the next batch may start beside
 // the step: after the encoding forward (FP32 path only).
+// CTAs of a training step's persistent MLP forward while the next batch is
+// built beside it (NIF_KNOB_STEP_FWD_CTAS); 0 = one per SM. By default the
+// FP32 forward takes three quarters of the SMs, then the fewest CTAs that give
+// each the same number of 128-row tiles, and the batch's kernels keep the
+// other SMs (measured on the 64^3 FP32 step: 2.97 ms on 103-114 CTAs,
+// 3.01-3.04 ms on 96 or 120-152); the 16-bit forward keeps every SM (its
+// step: 2.390-2.393 ms, against 2.398-2.400 ms on three quarters).
+static int step_fwd_ctas(const nif_handle* h, int64_t n, bool fp32) {
+    const int k = h->tune.step_fwd_ctas;
+    if (k != 0) return k < 0 ? 0 : k;
+    if (!fp32) return 0;
+    const int64_t tiles = std::max<int64_t>((n + 127) / 128, 1);
+    const int64_t c = std::max(1, h->num_sms * 3 / 4);
+    const int64_t per = (tiles + c - 1) / c;
+    return (int)((tiles + per - 1) / per);
+}
+
 static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, const int* n_hit, float lr_grid,
                                 float lr_mlp, double* loss_host, cudaStream_t s, cudaEvent_t ev_next = nullptr,
                                 bool join_weights = true, int set = -1) {
@@ -1388,7 +1405,9 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         uint16_t* acts16 = (uint16_t*)h->b_acts.p;
         uint16_t* dys = (uint16_t*)h->b_dys.p;
         if ((st = nif_encode_segments_run(h, lin, n_dev, n, feat, prec, NIF_FP16, s, true)) != NIF_OK) return st;
-        if ((st = nif_mlp_fwd_tc_acts_run(h, feat, prec, n_dev, n, out, acts16, np, kLd, s)) != NIF_OK) return st;
+        if ((st = nif_mlp_fwd_tc_acts_run(h, feat, prec, n_dev, n, out, acts16, np, kLd, s,
+                                          h->batch_beside ? step_fwd_ctas(h, n, false) : 0)) != NIF_OK)
+            return st;
         if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, true, n_hit)) != NIF_OK) return st;
         if ((st = nif_mlp_bwd_tc_run(h, dout, acts16, n_dev, n, np, kLd, dys, dx, s)) != NIF_OK) return st;
         // weight gradients on the second stream, beside the encoding backward
@@ -1421,7 +1440,9 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
             NIF_CK(h, cudaStreamWaitEvent(s, h->ev_wupd, 0));
             h->wupd_pending = false;
         }
-        if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s)) != NIF_OK) return st;
+        const bool beside = h->batch_beside && at <= 1;   // the next batch starts before this forward
+        if ((st = nif_mlp_fwd_fp32_run(h, feat, n_dev, n, out, acts, s, beside ? step_fwd_ctas(h, n, true) : 0)) != NIF_OK)
+            return st;
         if (ev_next && at == 2) NIF_CK(h, cudaEventRecord(ev_next, s));
         if ((st = nif_loss_run(h, out, lab, lin, n_dev, n, dout, s, true, n_hit)) != NIF_OK) return st;
         // weight gradients on the second stream, beside dX_0 and the encoding backward
@@ -1730,9 +1751,11 @@ static nif_status train_pipeline_on(nif_handle* h, int n_steps, const int& n_ray
             if ((st = next_batch(i)) != NIF_OK) return st;
             swap_batch(h);                                                  // back to step i's set
         }
-        if ((st = train_compute(h, n_rays, n_segments, h->d_count + 2 + i % 2, lr_grid, lr_mlp,
-                                more ? nullptr : loss_last, s, early ? nullptr : h->ev_step, !more, i % 2)) != NIF_OK)
-            return st;
+        h->batch_beside = more;                     // the next batch is built beside this step
+        st = train_compute(h, n_rays, n_segments, h->d_count + 2 + i % 2, lr_grid, lr_mlp, more ? nullptr : loss_last,
+                           s, early ? nullptr : h->ev_step, !more, i % 2);
+        h->batch_beside = false;
+        if (st != NIF_OK) return st;
         if ((st = done(i, s)) != NIF_OK) return st;
         if (more && !early && (st = next_batch(i)) != NIF_OK) return st;
         if (early) {
@@ -1854,7 +1877,12 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
             return NIF_OK;
         case NIF_KNOB_FP32_FUSED:
             if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "fused FP32 forward knob must be 0 or 1");
-            h->tune.fp32_fused = (int)value;
+            h->tune.fp32_fused = h->tune.query_fp32_fused = (int)value;
+            return NIF_OK;
+        case NIF_KNOB_STEP_FWD_CTAS:
+            if (!(value >= -1.0 && value <= 4096.0) || value != std::floor(value))
+                return nif_fail(h, NIF_ERR_ARG, "step forward CTA count must be an integer in [-1, 4096]");
+            h->tune.step_fwd_ctas = (int)value;
             return NIF_OK;
         case NIF_KNOB_DEFER_WEIGHTS:
             if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "deferred weight update knob must be 0 or 1");

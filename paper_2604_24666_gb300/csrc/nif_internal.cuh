@@ -170,6 +170,9 @@ struct nif_handle {
     cudaEvent_t ev_dw[2] = {nullptr, nullptr};   // weight gradients of the last step on batch set k done
     bool wupd_pending = false;
     int feat_flip = 0;
+    // set by the training pipeline while the next batch is built beside a
+    // step: the step's persistent MLP forward then leaves SMs to that batch
+    bool batch_beside = false;
     // the distinct end points of the last segment encoding (in b_dup, b_pts,
     // b_sort; sorted: in rest-space order), which the backward of the same
     // segments in a training step takes instead of listing them again
@@ -216,8 +219,12 @@ struct nif_handle {
                                         // start, 1 after the encoding forward, 2 after the MLP forward, 3 after
                                         // the MLP backward (NIF_KNOB_BATCH_AT; measured: 0 is ~0.01 ms faster
                                         // than 1 on the 64^3 step, 2 and 3 are 0.1-0.2 ms slower)
-        int fp32_fused = 0;             // NIF_KNOB_FP32_FUSED: the FP32 forward in one launch (measured equal
-                                        // to the per-layer launches on the 64^3 step)
+        int fp32_fused = 1;             // NIF_KNOB_FP32_FUSED: the FP32 forward in one launch (training steps,
+                                        // nif_mlp_forward)
+        int query_fp32_fused = 1;       // the same for FP32 queries (set by the knob, timed by plan autotuning)
+        int step_fwd_ctas = 0;          // NIF_KNOB_STEP_FWD_CTAS: the step's MLP forward CTAs beside the next
+                                        // batch (0: FP32 three quarters of the SMs, tile-balanced, 16-bit
+                                        // every SM; -1: every SM)
         int defer_wupd = 1;             // NIF_KNOB_DEFER_WEIGHTS: FP32 steps update the weights beside the next step
         int step_prio = 0;              // NIF_KNOB_STEP_PRIORITY: pipelined steps on the high-priority streams
         int query_fused = 1;            // NIF_KNOB_QUERY_FUSED: 16-bit queries encode into the tensor-core
@@ -355,8 +362,11 @@ nif_status nif_pose_grad_run(nif_handle* h, const nif_segment* segs, const nif_l
                              const uint32_t* n_dev, int64_t n, const int* inst_off, int n_inst, float* dposes,
                              cudaStream_t s);
 // FP32 MLP on the tensor cores (split TF32, k_mlp_x3.cu); acts [H][n_max][W]
+// ctas > 0 caps the one-launch forward's persistent CTAs. query: the hidden
+// activations are not needed (acts is then scratch for the per-layer launches
+// only) and the one-launch choice is tune.query_fp32_fused, not fp32_fused
 nif_status nif_mlp_fwd_fp32_run(nif_handle* h, const float* x, const uint32_t* n_dev, int64_t n_max,
-                                float* out, float* acts, cudaStream_t s);
+                                float* out, float* acts, cudaStream_t s, int ctas = 0, bool query = false);
 // want_dw: add dL/dW into the gradient buffer (off for an input gradient only);
 // with `aux`, the weight gradients run there (forked from s once every dY_l is
 // ready; the caller joins with h->ev_join before reading gradients)
@@ -379,8 +389,10 @@ nif_status nif_mlp_enc_tc_run(nif_handle* h, const nif_linseg* lin, const uint32
 nif_status nif_mlp_fwd_tc_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev,
                               int64_t n_max, float* out, cudaStream_t s);
 // acts_out (nullable): 16-bit hidden activations, layer l row r at (l * acts_rows + r) * acts_ld
+// (ctas > 0 caps its persistent CTAs)
 nif_status nif_mlp_fwd_tc_acts_run(nif_handle* h, const void* x, int dtype, const uint32_t* n_dev, int64_t n_max,
-                                   float* out, uint16_t* acts_out, int64_t acts_rows, int acts_ld, cudaStream_t s);
+                                   float* out, uint16_t* acts_out, int64_t acts_rows, int acts_ld, cudaStream_t s,
+                                   int ctas = 0);
 // 16-bit backward in the handle's precision: dY_l (scaled by the loss scale) into
 // dys [H+1][n_pad][ld], dx [n][in_dim] FP32 (scaled)
 nif_status nif_mlp_bwd_tc_run(nif_handle* h, const float* dout, const uint16_t* acts, const uint32_t* n_dev,

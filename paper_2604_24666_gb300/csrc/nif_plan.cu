@@ -101,7 +101,7 @@ nif_status plan_enqueue(nif_query_plan* p, cudaStream_t s) {
             if ((st = nif_encode_segments_run(h, lin + c0, cn, len, h->b_feat.p, NIF_FP32, NIF_FP32, s)) != NIF_OK)
                 return st;
             if ((st = nif_mlp_fwd_fp32_run(h, (const float*)h->b_feat.p, cn, len, out + c0 * NIF_OUT,
-                                           (float*)h->b_acts.p, s)) != NIF_OK)
+                                           (float*)h->b_acts.p, s, 0, true)) != NIF_OK)
                 return st;
         } else {
             if ((st = nif_encode_segments_run(h, lin + c0, cn, len, h->b_feat.p, prec, NIF_FP16, s)) != NIF_OK)
@@ -169,6 +169,7 @@ nif_status autotune(nif_query_plan* p, cudaStream_t s) {
         return NIF_OK;
     };
     if (nif_mlp_enc_fusable(h) && (st = try_knob(&h->tune.query_fused, {0, 1})) != NIF_OK) return st;
+    if (h->cfg.precision == NIF_FP32 && (st = try_knob(&h->tune.query_fp32_fused, {0, 1})) != NIF_OK) return st;
     if ((st = try_knob(&h->tune.trav_warps, {2, 4, 8})) != NIF_OK) return st;
     if ((st = try_knob(&h->tune.enc_threads, {128, 256, 512})) != NIF_OK) return st;
     if ((st = try_knob(&h->tune.enc_blocks_per_sm, {4, 8, 16, 32})) != NIF_OK) return st;

@@ -353,10 +353,14 @@ def test_loss_matches_oracle(nif, torus, flags):
 # ---------------------------------------------------------------------------
 # Whole query
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("pose", [(0, 0, 0), (0.6, -1.0, 0.4)])
-def test_query_fp32_matches_oracle(nif, torus, pose):
+@pytest.mark.parametrize("pose,fused", [((0, 0, 0), 1), ((0.6, -1.0, 0.4), 1), ((0.6, -1.0, 0.4), 0)])
+def test_query_fp32_matches_oracle(nif, torus, pose, fused):
+    """fused: the MLP forward in one launch, which stores no hidden
+    activations in a query (NIF_KNOB_FP32_FUSED, default), or one launch per
+    layer."""
     net = S.NetConfig()
     h = nif.Nif(net, torus)
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_FP32_FUSED, fused)
     tables = random_tables(net, 101)
     ws, s = occupancy_biased_weights(net, 102)
     h.set_params(tables, ws, s)
