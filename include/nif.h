@@ -647,6 +647,12 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   batch's kernels keep the other SMs, and the 16-bit forward one CTA per
  *   SM; k > 0: k CTAs (at most one per SM); -1: one per SM. A scheduling
  *   choice only: the steps compute the same.
+ * NIF_KNOB_STEP_BWD_CTAS: persistent CTAs of the encoding backward in an
+ *   FP32 training step, which runs beside the weight gradients on the
+ *   handle's second stream. 0 (default): seven eighths of the SMs, leaving
+ *   the rest to the weight gradients; k > 0: k CTAs (at most one per SM);
+ *   -1: one per SM (as in nif_encode_segments_backward and mixed-precision
+ *   steps). A scheduling choice only: the same sums in another order.
  * NIF_ERR_ARG for an unknown knob or a value out of range. */
 #define NIF_KNOB_WAIT_NS 1
 #define NIF_KNOB_SEG_SCRATCH 2
@@ -657,6 +663,7 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
 #define NIF_KNOB_STEP_PRIORITY 7
 #define NIF_KNOB_DEFER_WEIGHTS 8
 #define NIF_KNOB_STEP_FWD_CTAS 9
+#define NIF_KNOB_STEP_BWD_CTAS 10
 nif_status nif_set_knob(nif_handle* h, int knob, double value);
 
 /* Allocation-free variant of nif_segments (the paper has no counterpart:

@@ -1054,7 +1054,8 @@ nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n,
 }
 
 nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
-                                       const float* dfeats, float* dtables, cudaStream_t s, bool reuse_points) {
+                                       const float* dfeats, float* dtables, cudaStream_t s, bool reuse_points,
+                                       int ctas) {
     NifProf prof_(h, "encode_bwd", s);
     if (n_max <= 0) return NIF_OK;
     if (h->concat) {
@@ -1097,10 +1098,10 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
         }
         NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
-        // one 1024-thread block per SM (64 registers a thread fill the register
-        // file); its warps take chunks from the task counter
+        // at most one 1024-thread block per SM (64 registers a thread fill the
+        // register file); its warps take chunks from the task counter
         NIF_CK(h, cudaMemsetAsync(h->d_next + 1, 0, sizeof(uint32_t), s));
-        k_encode_segments_bwd_rl<<<h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables, pts,
+        k_encode_segments_bwd_rl<<<ctas > 0 ? std::min(ctas, h->num_sms) : h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables, pts,
                                                                 n_pts, dupf, h->d_next + 1);
         NIF_CK_LAUNCH(h);
         return NIF_OK;

@@ -1448,7 +1448,13 @@ static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, c
         // weight gradients on the second stream, beside dX_0 and the encoding backward
         if ((st = nif_mlp_bwd_fp32_run(h, feat, n_dev, n, acts, dout, dx, s, true, h->aux)) != NIF_OK) return st;
         if (ev_next && at >= 3) NIF_CK(h, cudaEventRecord(ev_next, s));
-        if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s, true)) != NIF_OK)
+        // the encoding backward leaves some SMs to the weight gradients
+        // (NIF_KNOB_STEP_BWD_CTAS; measured on the 64^3 step: 2.91-2.92 ms on
+        // 128-136 of 152 SMs, 2.97 ms on all, 2.94-2.95 ms on 124 or 144)
+        const int kb = h->tune.step_bwd_ctas;
+        const int bwd_ctas = kb < 0 ? 0 : (kb > 0 ? kb : std::max(1, h->num_sms * 7 / 8));
+        if ((st = nif_encode_segments_bwd_run(h, lin, n_dev, n, dx, h->d_grad + h->off_tables, s, true, bwd_ctas)) !=
+            NIF_OK)
             return st;
         bool split = false;
         if (defer && (st = nif_adam_split_run(h, lr_grid, lr_mlp, s, h->aux, &split)) != NIF_OK) return st;
@@ -1878,6 +1884,11 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
         case NIF_KNOB_FP32_FUSED:
             if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "fused FP32 forward knob must be 0 or 1");
             h->tune.fp32_fused = h->tune.query_fp32_fused = (int)value;
+            return NIF_OK;
+        case NIF_KNOB_STEP_BWD_CTAS:
+            if (!(value >= -1.0 && value <= 4096.0) || value != std::floor(value))
+                return nif_fail(h, NIF_ERR_ARG, "step backward CTA count must be an integer in [-1, 4096]");
+            h->tune.step_bwd_ctas = (int)value;
             return NIF_OK;
         case NIF_KNOB_STEP_FWD_CTAS:
             if (!(value >= -1.0 && value <= 4096.0) || value != std::floor(value))

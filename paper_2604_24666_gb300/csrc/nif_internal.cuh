@@ -213,6 +213,8 @@ struct nif_handle {
         int enc_threads = 256;          // encoding block size
         int enc_blocks_per_sm = 16;     // encoding grid cap per SM (grid-stride beyond)
         int64_t tc_chunk = 1 << 20;     // rows per encode + tensor-core MLP chunk
+        int step_bwd_ctas = 0;          // NIF_KNOB_STEP_BWD_CTAS: the FP32 step's encoding backward CTAs beside
+                                        // the weight gradients (0: seven eighths of the SMs; -1: every SM)
         int bwd_smem_rows = 512;        // encoding backward: dense coarse levels of at most this many rows
                                         // go to shared memory (measured: larger ones reduce faster in L2)
         int batch_at = 0;               // FP32 steps of nif_train_steps: the next batch starts at 0 the step's
@@ -352,10 +354,11 @@ nif_status nif_encode_points_prepare(nif_handle* h, const nif_linseg* lin, const
 nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n, const float* dfeats,
                                      float* dtables, float* dpts, cudaStream_t s);
 // reuse_points: the segment encoding just before, on the same stream, read the
-// same lin / n_dev / n_max; its list of distinct end points is taken as it is
+// same lin / n_dev / n_max; its list of distinct end points is taken as it is.
+// ctas > 0 caps the persistent run-length kernel's CTAs (0: one per SM)
 nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev,
                                        int64_t n_max, const float* dfeats, float* dtables,
-                                       cudaStream_t s, bool reuse_points = false);
+                                       cudaStream_t s, bool reuse_points = false, int ctas = 0);
 nif_status nif_encode_segments_dp_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n,
                                       const float* dfeats, float* dp, cudaStream_t s);
 nif_status nif_pose_grad_run(nif_handle* h, const nif_segment* segs, const nif_linseg* lin, const float* dp,

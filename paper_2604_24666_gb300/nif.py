@@ -28,6 +28,7 @@ NIF_FLAG_BILINEAR_FACES = 16
 NIF_KNOB_WAIT_NS, NIF_KNOB_SEG_SCRATCH, NIF_KNOB_QUERY_SEGS, NIF_KNOB_BATCH_AT, NIF_KNOB_FP32_FUSED = 1, 2, 3, 4, 5
 NIF_KNOB_QUERY_FUSED, NIF_KNOB_STEP_PRIORITY, NIF_KNOB_DEFER_WEIGHTS = 6, 7, 8
 NIF_KNOB_STEP_FWD_CTAS = 9
+NIF_KNOB_STEP_BWD_CTAS = 10
 NIF_PROBE_RED8, NIF_PROBE_RED16, NIF_PROBE_LOAD8, NIF_PROBE_LOAD4 = 1, 2, 3, 4
 NIF_PROBE_RED8_WARP, NIF_PROBE_RED16_WARP, NIF_PROBE_LOAD8_WARP, NIF_PROBE_LOAD4_WARP = 5, 6, 7, 8
 

@@ -158,18 +158,22 @@ def test_train_step_table_gradient_matches_stages(nif, torus, levels, log2T):
     assert agree.all(), (np.count_nonzero(~agree), big.sum())
 
 
-@pytest.mark.parametrize("batch_at,ctas", [(0, 0), (1, 37), (2, -1), (3, 0), (0, 5)])
-def test_train_steps_batch_placement_and_fused_forward(nif, torus, batch_at, ctas):
+@pytest.mark.parametrize("batch_at,ctas,bwd", [(0, 0, 0), (1, 37, -1), (2, -1, 19), (3, 0, 0), (0, 5, 152)])
+def test_train_steps_batch_placement_and_fused_forward(nif, torus, batch_at, ctas, bwd):
     """Where the next batch starts beside a step (NIF_KNOB_BATCH_AT), the
-    one-launch FP32 forward (NIF_KNOB_FP32_FUSED) and its CTA count beside
-    the batch (NIF_KNOB_STEP_FWD_CTAS) change the schedule, not the steps:
-    the losses equal those of one launch per layer."""
+    one-launch FP32 forward (NIF_KNOB_FP32_FUSED), its CTA count beside the
+    batch (NIF_KNOB_STEP_FWD_CTAS) and the encoding backward's CTA count
+    beside the weight gradients (NIF_KNOB_STEP_BWD_CTAS) change the
+    schedule, not the steps: the losses equal those of one launch per layer
+    on every SM."""
     net = S.NetConfig(levels=16, log2_table=19, mlp_depth=3, mlp_width=64)
     a = nif.Nif(net, torus, seed=9)
     b = nif.Nif(net, torus, seed=9)
     nif.nif_set_knob(a.h, nif.NIF_KNOB_FP32_FUSED, 0)
+    nif.nif_set_knob(a.h, nif.NIF_KNOB_STEP_BWD_CTAS, -1)
     nif.nif_set_knob(b.h, nif.NIF_KNOB_BATCH_AT, batch_at)
     nif.nif_set_knob(b.h, nif.NIF_KNOB_STEP_FWD_CTAS, ctas)
+    nif.nif_set_knob(b.h, nif.NIF_KNOB_STEP_BWD_CTAS, bwd)
     # learning rates 0: each step's loss depends only on its batch (a batch
     # built into the buffers of the step still running would show here)
     for K in (1, 3):
