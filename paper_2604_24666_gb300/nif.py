@@ -619,8 +619,12 @@ def nif_encoder_points(h):
 
 
 def nif_set_knob(h, knob, value):
-    """NIF_KNOB_WAIT_NS (bound of the tensor-core kernels' waits, ns; 0 = default) or
-    NIF_KNOB_SEG_SCRATCH (scale in (0, 1] of the single-traversal segment scratch)."""
+    """Set one of the handle's NIF_KNOB_* tuning knobs (include/nif.h gives
+    each one's values). Knobs choose schedules, kernels or scratch sizes,
+    not results. Examples: NIF_KNOB_WAIT_NS bounds the tensor-core kernels'
+    waits (ns; 0 = default), NIF_KNOB_SEG_SCRATCH scales the single-traversal
+    segment scratch, and NIF_KNOB_STEP_FWD_CTAS / NIF_KNOB_STEP_BWD_CTAS set
+    how the FP32 training step shares SMs between concurrent kernels."""
     _check(h, lib().nif_set_knob(h, knob, float(value)))
 
 
