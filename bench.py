@@ -457,6 +457,7 @@ def run_ours(args):
 
     # ---- mixed-precision training, same workload ---------------------------
     mixed = run_train_mixed(args, nif, S, dev, rank, hbm) if not args.no_mixed else None
+    det = run_train_det(args, nif, S, dev, rank) if not args.no_det else None
 
     # ---- inference queries ------------------------------------------------
     query = run_query(args, nif, S, dev, rank) if not args.no_query else None
@@ -492,7 +493,7 @@ def run_ours(args):
             "roofline": roof, "kernels": kernels, "l2_probe": l2, "encoder_points": {"distinct": n_pts, "segments": n_segs_enc},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "loss": list(loss) if loss is not None else None, "train_mixed": mixed,
-            "query": query, "batch": batch, "frame_loop": frame, "traversal": trav, "field": field,
+            "train_deterministic": det, "query": query, "batch": batch, "frame_loop": frame, "traversal": trav, "field": field,
             "precision": precision}
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -543,6 +544,38 @@ def run_train_mixed(args, nif, S, dev, rank, hbm):
                      "loss_scale": scale, "skipped_steps": skipped, "loss": list(loss), "kernels": stages}
         h.close()
     return res
+
+
+def run_train_det(args, nif, S, dev, rank):
+    """The FP32 training step of the same workload with NIF_KNOB_DETERMINISTIC
+    (order-free gradient sums: 64-bit fixed-point table gradient, per-range
+    weight gradients added in order): segments/s, ms per step and the
+    encoding backward's share, over at most 20 steps."""
+    import torch
+    w = S.WORKLOADS[TRAIN_WORKLOAD]
+    h = nif.Nif(w["net"], S.make_mesh(w["shape"]), seed=1234 + rank)
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_DETERMINISTIC, 1)
+    stream = torch.cuda.current_stream()
+    k = max(1, min(args.steps, 20))
+    seed0 = 77 + 1000003 * rank
+    nif.nif_train_steps(h.h, args.warmup, N_SEG, N_POSES, seed0, lr_grid=1e-2, lr_mlp=1e-3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    nif.nif_train_steps(h.h, k, N_SEG, N_POSES, seed0 + args.warmup, lr_grid=1e-2, lr_mlp=1e-3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nif.nif_profile(h.h, 1)
+    nif.nif_profile_filter(h.h, ["encode_bwd"])
+    nif.nif_train_steps(h.h, k, N_SEG, N_POSES, seed0 + args.warmup + k, lr_grid=1e-2, lr_mlp=1e-3)
+    torch.cuda.synchronize()
+    prof = nif.nif_profile_read(h.h)
+    nif.nif_profile(h.h, 0)
+    h.close()
+    bwd = prof.get("encode_bwd", (0.0,))[0] / k
+    return {"value": k * N_SEG / (ms / 1e3), "unit": "segments/s", "ms_per_step": ms / k, "steps": k,
+            "encode_bwd_ms_per_step": bwd}
 
 
 def h_seg_per_ray(h, nif):
@@ -1002,6 +1035,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-instance query measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-output precision study")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision training measurement")
+    ap.add_argument("--no-det", action="store_true", help="skip the deterministic-gradient training measurement")
     ap.add_argument("--no-frame", action="store_true", help="skip the animated frame loop")
     ap.add_argument("--no-traversal", action="store_true", help="skip the enumeration vs exit-face walk comparison")
     ap.add_argument("--no-field", action="store_true", help="skip the learned deformation field measurement")

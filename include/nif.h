@@ -199,12 +199,17 @@ nif_status nif_set_params(nif_handle* h, int group, const void* src_host, size_t
 nif_status nif_reset_optimizer(nif_handle* h);
 
 /* Checkpoint of the trainable state: a 64-byte header (magic "NIFCKPT1",
- * format version, the sizes of the configuration that must match, the Adam
- * step count), then the FP32 parameters, Adam first and second moments, and a
- * CRC-32 (IEEE) of everything before it. nif_checkpoint_bytes gives the size;
- * save writes into host memory, load checks the header, sizes and CRC
+ * format version 2, the sizes of the configuration that must match, the Adam
+ * step count), then the FP32 parameters, Adam first and second moments, the
+ * 40-byte state of the mixed-precision path (loss scale, clean-step and
+ * skipped-step counts, the Adam bias-correction products of the steps taken),
+ * and a CRC-32 (IEEE) of everything before it. nif_checkpoint_bytes gives the
+ * size; save writes into host memory, load checks the header, sizes and CRC
  * (NIF_ERR_ARG on any mismatch, leaving the handle unchanged) and restores
- * parameters, moments and step. Both block the host. */
+ * all of it. Both block the host. Sampling is seeded by the caller (step
+ * seeds), so a checkpoint plus the next seeds determine the run; with
+ * NIF_KNOB_DETERMINISTIC the resumed steps are bit-identical to the
+ * uninterrupted ones. */
 nif_status nif_checkpoint_bytes(const nif_handle* h, size_t* bytes);
 nif_status nif_checkpoint_save(nif_handle* h, void* dst_host, size_t bytes);
 nif_status nif_checkpoint_load(nif_handle* h, const void* src_host, size_t bytes);
@@ -653,6 +658,22 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   the rest to the weight gradients; k > 0: k CTAs (at most one per SM);
  *   -1: one per SM (as in nif_encode_segments_backward and mixed-precision
  *   steps). A scheduling choice only: the same sums in another order.
+ * NIF_KNOB_DETERMINISTIC: 1 makes the gradients of training steps (and of
+ *   nif_encode_segments_backward) independent of the order in which the GPU
+ *   adds them, so that the same calls on the same state give bit-identical
+ *   parameters, losses and checkpoints, across runs and after a checkpoint
+ *   is loaded into another handle; 0 (default) adds them with float
+ *   reductions in L2, whose order varies from run to run. In this mode the
+ *   table gradient is summed as 64-bit fixed point: each contribution is
+ *   rounded once to a multiple of 2^-S, with S chosen per call from the
+ *   largest dL/dfeature so that no sum can overflow, and each sum is
+ *   converted to FP32 at the end (an added absolute error of at most 2^-(S+1)
+ *   per contribution); the MLP weight gradients are summed per row range and
+ *   the ranges added in order; the loss sums are added in block order. The
+ *   paper has no counterpart (it trains with no stated reduction order).
+ *   Slower (measured on the 64^3 FP32 step in the design notes). Handles
+ *   with NIF_FLAG_CONCAT_ENCODING are refused (NIF_ERR_ARG). Synchronises the
+ *   device.
  * NIF_ERR_ARG for an unknown knob or a value out of range. */
 #define NIF_KNOB_WAIT_NS 1
 #define NIF_KNOB_SEG_SCRATCH 2
@@ -664,6 +685,7 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
 #define NIF_KNOB_DEFER_WEIGHTS 8
 #define NIF_KNOB_STEP_FWD_CTAS 9
 #define NIF_KNOB_STEP_BWD_CTAS 10
+#define NIF_KNOB_DETERMINISTIC 11
 nif_status nif_set_knob(nif_handle* h, int knob, double value);
 
 /* Allocation-free variant of nif_segments (the paper has no counterpart:
@@ -697,6 +719,19 @@ nif_status nif_segments_noalloc(nif_handle* h, const nif_pose* poses_host, int n
 /* Number of kernels this library has enqueued since it was loaded (all
  * handles, all threads). */
 unsigned long long nif_kernel_launches(void);
+
+/* Bounds-checked build (the paper has none: a debugging aid). The library
+ * compiled with -DNIF_BOUNDS=1 (libnif_bounds.so) checks the index
+ * computations of its gathers and scatters -- the grid cell of every encoder
+ * gather and scatter (so every table row stays inside its level), the
+ * triangle indices of the labels, the positions of the rest-space point order
+ * and of the per-ray segment rows -- and, when a check fails, counts it in a
+ * device word and redirects or skips the access instead of trapping.
+ * *enabled = 1 in that build (the call then synchronises the device and
+ * returns in *failures the checks that failed since the last call, clearing
+ * the count); *enabled = 0 and *failures = 0 in the normal build, whose checks
+ * compile away. NIF_ERR_ARG for null pointers. */
+nif_status nif_bounds_check(int* enabled, unsigned long long* failures);
 
 /* Measured ceilings of the memory patterns that bound the encoding kernels
  * (the paper has no counterpart): `kind`

@@ -21,6 +21,9 @@ __device__ __forceinline__ Cell cell_of(float3 u, int Nl) {
     c.ix = min((int)floorf(qx), Nl - 1);
     c.iy = min((int)floorf(qy), Nl - 1);
     c.iz = min((int)floorf(qz), Nl - 1);
+    // bounds build: a cell outside the level's grid would put corner rows
+    // past the level's block; it is counted and the cell moved to the origin
+    if (!(NIF_IN(c.ix, Nl) && NIF_IN(c.iy, Nl) && NIF_IN(c.iz, Nl))) c.ix = c.iy = c.iz = 0;
     c.wx = qx - (float)c.ix;
     c.wy = qy - (float)c.iy;
     c.wz = qz - (float)c.iz;

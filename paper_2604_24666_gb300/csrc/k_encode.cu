@@ -723,7 +723,8 @@ __global__ void __launch_bounds__(256) k_point_scatter(const uint32_t* __restric
     const int64_t n = *n_pts_dev;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t key = keys[k];
-        sorted[off[key] + atomicAdd(fill + key, 1u)] = pts[k];
+        const uint32_t at = off[key] + atomicAdd(fill + key, 1u);
+        if (NIF_IN(at, n)) sorted[at] = pts[k];
     }
 }
 
@@ -966,6 +967,135 @@ __global__ void __launch_bounds__(256) k_encode_cat_dp(GridInfo g, const float* 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Deterministic table gradient (NIF_KNOB_DETERMINISTIC). Float reductions in
+// L2 add in whatever order the warps reach them, so two runs of one step can
+// differ in the last bits of the sums. Here each contribution w * dL/dfeature
+// (the same FP32 product as above) is scaled by 2^S, rounded once to a 64-bit
+// integer and added with integer atomics; integer addition is associative,
+// so the sum and the FP32 value it converts to do not depend on the order.
+// S comes from M = max |dL/dfeature| of the call: a table entry of level l
+// takes at most one weighted term per (segment, end point, gamma term), with
+// trilinear weights summing to at most 1 over the cell's corners, so every
+// sum is bounded by 2 n P M; S is the largest integer with 2 n P M 2^S <
+// 2^61, which leaves the rounding (at most 1/2 per contribution) far from
+// overflow. Each contribution's rounding error is at most 2^-(S+1).
+// ---------------------------------------------------------------------------
+constexpr int kFixBad = -100000;         // scale word: a non-finite dL/dfeature was seen
+
+// *bits = max over the first min(*n_dev, n_max) * per floats of x of the bit
+// pattern of |x| (the order of non-negative floats; NaN compares above inf)
+__global__ void __launch_bounds__(256) k_absmax_bits(const float* __restrict__ x, const uint32_t* __restrict__ n_dev,
+                                                     int64_t n_max, int64_t per, uint32_t* __restrict__ bits) {
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    const int64_t cnt = n * per;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t m = 0;
+    if ((reinterpret_cast<uintptr_t>(x) & 15u) == 0 && cnt % 4 == 0) {
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        for (int64_t i = i0; i < cnt / 4; i += stride) {
+            const float4 v = x4[i];
+            m = max(m, max(max(__float_as_uint(v.x) & 0x7fffffffu, __float_as_uint(v.y) & 0x7fffffffu),
+                           max(__float_as_uint(v.z) & 0x7fffffffu, __float_as_uint(v.w) & 0x7fffffffu)));
+        }
+    } else {
+        for (int64_t i = i0; i < cnt; i += stride) m = max(m, __float_as_uint(x[i]) & 0x7fffffffu);
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(bits, m);
+}
+
+// the scale exponent S of the call (see above), or kFixBad
+__global__ void k_fix_scale(const uint32_t* __restrict__ bits, const uint32_t* __restrict__ n_dev, int64_t n_max,
+                            int P, int* __restrict__ S_out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    const uint32_t b = *bits;
+    if (b >= 0x7f800000u) { *S_out = kFixBad; return; }
+    const double B = 2.0 * (double)n * (double)P * (double)__uint_as_float(b);
+    if (B == 0.0) { *S_out = 0; return; }      // every contribution is zero
+    int E = 0;
+    frexp(B, &E);                              // B = m 2^E, 1/2 <= m < 1, so B 2^(61-E) < 2^61
+    *S_out = 61 - E;
+}
+
+// One thread per (segment, end point, gamma term), as k_encode_segments_bwd_sm:
+// the dense coarse levels of cs go to the block's shared-memory copy, the rest
+// to fix, both as 64-bit fixed point.
+__global__ void __launch_bounds__(1024) k_encode_bwd_fixed(GridInfo g, Coarse cs, const nif_linseg* __restrict__ lin,
+                                                           const uint32_t* __restrict__ n_dev, int64_t n_max,
+                                                           const float* __restrict__ dfeats,
+                                                           unsigned long long* __restrict__ fix,
+                                                           const int* __restrict__ S_dev) {
+    extern __shared__ unsigned long long sfix[];
+    const int S = *S_dev;
+    if (S == kFixBad) return;                  // the conversion writes NaN gradients
+    const double scale = ldexp(1.0, S);
+    const int nsh = cs.soff[cs.Lc];
+    for (int i = threadIdx.x; i < nsh; i += blockDim.x) sfix[i] = 0ull;
+    __syncthreads();
+    int64_t n = n_dev ? (int64_t)*n_dev : n_max;
+    if (n > n_max) n = n_max;
+    const int per = 2 * g.P;
+    for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < n * per;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = gid / per;
+        const int r = (int)(gid - s * per);
+        const int e = r >= g.P;
+        const int t = r - e * g.P;
+        const float* L = reinterpret_cast<const float*>(lin + s) + 3 * e;
+        const float3 u = term_u(clamp01(make_float3(L[0], L[1], L[2])), t);
+        const float* df = dfeats + gid * g.L * 2;
+        for (int l = 0; l < g.L; l++) {
+            const int Nl = g.res[l];
+            const bool dense = (g.dense_mask >> l) & 1u;
+            const Cell c = cell_of(u, Nl);
+            const float2 gr = *reinterpret_cast<const float2*>(df + 2 * l);
+            if (gr.x == 0.f && gr.y == 0.f) continue;
+            unsigned long long* dl = l < cs.Lc ? sfix + cs.soff[l] : fix + (int64_t)l * g.T * 2;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint32_t row = grid_row(c.ix + (q & 1), c.iy + ((q >> 1) & 1), c.iz + ((q >> 2) & 1), Nl, dense, g.T);
+                const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) * ((q & 4) ? c.wz : 1.f - c.wz);
+                const long long a = __double2ll_rn((double)(w * gr.x) * scale);
+                const long long b = __double2ll_rn((double)(w * gr.y) * scale);
+                if (a) atomicAdd(dl + 2 * row, (unsigned long long)a);
+                if (b) atomicAdd(dl + 2 * row + 1, (unsigned long long)b);
+            }
+        }
+    }
+    __syncthreads();
+    for (int l = 0; l < cs.Lc; l++) {
+        const int cnt = cs.soff[l + 1] - cs.soff[l];
+        unsigned long long* dst = fix + (int64_t)l * g.T * 2;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const unsigned long long v = sfix[cs.soff[l] + i];
+            if (v) atomicAdd(dst + i, v);
+        }
+    }
+}
+
+// dtab[i] += fix[i] 2^-S, and fix[i] = 0 for the next call; NaN everywhere
+// when the call saw a non-finite dL/dfeature
+__global__ void __launch_bounds__(256) k_fix_to_float(unsigned long long* __restrict__ fix, int64_t cnt,
+                                                      const int* __restrict__ S_dev, float* __restrict__ dtab) {
+    const int S = *S_dev;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long v = fix[i];
+        if (S == kFixBad) {
+            dtab[i] = __int_as_float(0x7fffffff);
+            if (v) fix[i] = 0ull;
+        } else if (v) {
+            dtab[i] += (float)ldexp((double)(long long)v, -S);
+            fix[i] = 0ull;
+        }
+    }
+}
+
 }  // namespace
 
 nif_status nif_encode_points_prepare(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
@@ -1053,11 +1183,57 @@ nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n,
     return NIF_OK;
 }
 
+// Deterministic mode's table gradient (see k_encode_bwd_fixed): the scale from
+// max |dL/dfeature|, the fixed-point sums, their conversion into dtables.
+static nif_status encode_bwd_fixed(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
+                                   const float* dfeats, float* dtables, cudaStream_t s) {
+    const int64_t cnt = (int64_t)h->L * h->T * 2;
+    const size_t bytes = sizeof(unsigned long long) * (size_t)cnt;
+    if (h->b_fix.bytes < bytes + 16) {
+        nif_status st = nif_grow(h, h->b_fix, bytes + 16);
+        if (st != NIF_OK) return st;
+        NIF_CK(h, cudaMemsetAsync(h->b_fix.p, 0, bytes, s));      // zero between calls from here on
+    }
+    unsigned long long* fix = (unsigned long long*)h->b_fix.p;
+    uint32_t* bits = (uint32_t*)((char*)h->b_fix.p + bytes);
+    int* S_dev = (int*)(bits + 1);
+    NIF_CK(h, cudaMemsetAsync(bits, 0, sizeof(uint32_t), s));
+    const int64_t per = 4LL * h->P * h->L;                         // floats of dL/dfeature per segment
+    const unsigned g4 = (unsigned)std::min<int64_t>(nif_blocks(n_max * per / 4, 256), (int64_t)h->num_sms * 8);
+    k_absmax_bits<<<g4, 256, 0, s>>>(dfeats, n_dev, n_max, per, bits);
+    NIF_CK_LAUNCH(h);
+    k_fix_scale<<<1, 32, 0, s>>>(bits, n_dev, n_max, h->P, S_dev);
+    NIF_CK_LAUNCH(h);
+    // dense coarse levels of at most 4096 rows in shared memory (96 KB at most,
+    // two 1024-thread blocks per SM)
+    Coarse cs{};
+    cs.Lc = 0;
+    cs.soff[0] = 0;
+    const int budget = 96 * 1024 / 8;
+    for (int l = 0; l < h->L; l++) {
+        if (!((h->grid.dense_mask >> l) & 1u)) break;
+        const int64_t r = (int64_t)h->grid.res[l] + 1;
+        if (r * r * r > 4096 || cs.soff[l] + 2 * r * r * r > budget) break;
+        cs.soff[l + 1] = cs.soff[l] + (int)(2 * r * r * r);
+        cs.Lc = l + 1;
+    }
+    const size_t smem = sizeof(unsigned long long) * (size_t)cs.soff[cs.Lc];
+    NIF_CK(h, cudaFuncSetAttribute(k_encode_bwd_fixed, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    const unsigned gb = (unsigned)std::min<int64_t>(nif_blocks(n_max * 2 * h->P, 1024), (int64_t)h->num_sms * 2);
+    k_encode_bwd_fixed<<<gb, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, fix, S_dev);
+    NIF_CK_LAUNCH(h);
+    const unsigned gc = (unsigned)std::min<int64_t>(nif_blocks(cnt, 256), (int64_t)h->num_sms * 8);
+    k_fix_to_float<<<gc, 256, 0, s>>>(fix, cnt, S_dev, dtables);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
 nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
                                        const float* dfeats, float* dtables, cudaStream_t s, bool reuse_points,
                                        int ctas) {
     NifProf prof_(h, "encode_bwd", s);
     if (n_max <= 0) return NIF_OK;
+    if (h->det && !h->concat) return encode_bwd_fixed(h, lin, n_dev, n_max, dfeats, dtables, s);
     if (h->concat) {
         const int64_t work = n_max * 2 * h->L;
         k_encode_cat_bwd<<<(unsigned)std::min<int64_t>(nif_blocks(work, 256), (int64_t)h->num_sms * 16), 256, 0, s>>>(

@@ -529,7 +529,8 @@ __device__ __forceinline__ uint32_t idesc_f16_mn(int fmt, int N) {
 __global__ void __launch_bounds__(kDwThreads, 1)
     k_mlp_dw_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap amap,
                 const __grid_constant__ CUtensorMap dmap, DwJobs jobs, int fmt, int64_t n_max, int64_t n_pad,
-                const uint32_t* __restrict__ n_dev, float* __restrict__ grad, int* __restrict__ status) {
+                const uint32_t* __restrict__ n_dev, float* __restrict__ grad, int64_t part_stride,
+                int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint64_t wlim = wait_limit(status);   // bound of the work loop's waits
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -626,13 +627,21 @@ __global__ void __launch_bounds__(kDwThreads, 1)
             tc_fence_after();
             const int i = i0 + warp * 32 + lane;
             const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-            float* g = grad + jobs.goff[l] + i;
+            // part_stride > 0 (deterministic mode): grad holds one copy of the
+            // weight blocks per row range, each range's sum is stored in its own
+            float* g = grad + (int64_t)blockIdx.y * part_stride + jobs.goff[l] + i;
             for (int c0 = 0; c0 < out_l; c0 += 16) {
                 float v[16];
                 tmem_ld16(lane_base + (uint32_t)c0, v);
-                if (i < in_l)
+                if (i < in_l) {
+                    if (part_stride > 0) {
 #pragma unroll
-                    for (int k = 0; k < 16; k++) atomicAdd(g + (int64_t)(c0 + k) * in_l, v[k]);
+                        for (int k = 0; k < 16; k++) g[(int64_t)(c0 + k) * in_l] = v[k];
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 16; k++) atomicAdd(g + (int64_t)(c0 + k) * in_l, v[k]);
+                    }
+                }
             }
         }
     }
@@ -858,9 +867,13 @@ nif_status nif_mlp_dw_tc_run(nif_handle* h, const void* x16, const uint16_t* act
                                            (uint16_t*)acts, h->H, (uint16_t*)dys, h->H + 1, ld);
     NIF_CK_LAUNCH(h);
     DwJobs jobs{};
+    // deterministic mode: offsets within the weights' span [off_layer[0], wend)
+    const int64_t wbase = h->det ? (int64_t)h->off_layer[0] : 0;
+    const int64_t wcnt = (int64_t)h->off_layer[h->n_layers - 1] +
+                         (int64_t)h->lay_out[h->n_layers - 1] * h->lay_in[h->n_layers - 1] - (int64_t)h->off_layer[0];
     for (int l = 0; l < h->n_layers; l++) {
         const int in_l = h->lay_in[l];
-        jobs.goff[l] = (int64_t)h->off_layer[l];
+        jobs.goff[l] = (int64_t)h->off_layer[l] - wbase;
         jobs.in[l] = in_l;
         jobs.out[l] = h->lay_out[l];
         for (int i0 = 0; i0 < in_l; i0 += 128) {
@@ -876,8 +889,16 @@ nif_status nif_mlp_dw_tc_run(nif_handle* h, const void* x16, const uint16_t* act
     const int64_t chunks = (n_max + 127) / 128;
     int splits = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (h->num_sms + jobs.n - 1) / jobs.n));
     dim3 grid(jobs.n, splits);
+    float* part = nullptr;
+    if (h->det) {
+        // each row range's sums kept apart (a range with no live rows leaves zeros)
+        if ((st = nif_grow(h, h->b_parts, sizeof(float) * (size_t)splits * wcnt)) != NIF_OK) return st;
+        part = (float*)h->b_parts.p;
+        NIF_CK(h, cudaMemsetAsync(part, 0, sizeof(float) * (size_t)splits * wcnt, s));
+    }
     k_mlp_dw_tc<<<grid, kDwThreads, smem, s>>>(xm, am, dm, jobs, dtype == NIF_BF16 ? 1 : 0, n_max, n_pad, n_dev,
-                                               h->d_grad, h->d_status);
+                                               part ? part : h->d_grad, part ? wcnt : 0, h->d_status);
     NIF_CK_LAUNCH(h);
+    if (part) return nif_sum_parts_run(h, part, splits, wcnt, h->d_grad + wbase, s);
     return NIF_OK;
 }

@@ -655,6 +655,8 @@ constexpr int kDwConv = 256;                   // converter threads
 
 struct DwX3Args {
     float* grad;                      // [out_l][in_l] block of the gradient buffer
+    float* part;                      // deterministic mode: [gridDim.y][out_l][in_l] sums of each row range
+                                      // (stored, then added in range order); nullptr: added in L2
     int in_l, out_l, MI;              // MI: columns of X_l in one TMA box (<= 128)
     int64_t n_max;
     int raw_stages, op_stages;
@@ -844,9 +846,16 @@ __global__ void __launch_bounds__(kDwX3Threads, 1)
                 for (int c0 = 0; c0 < OUT; c0 += 16) {
                     float v[16];
                     tmem_ld16(tb + (uint32_t)c0, v);
-                    if (i < a.in_l)
+                    if (i < a.in_l) {
+                        if (a.part) {
+                            float* p = a.part + ((int64_t)blockIdx.y * a.out_l + c0) * a.in_l + i;
 #pragma unroll
-                        for (int k = 0; k < 16; k++) atomicAdd(a.grad + (int64_t)(c0 + k) * a.in_l + i, v[k]);
+                            for (int k = 0; k < 16; k++) p[(int64_t)k * a.in_l] = v[k];
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 16; k++) atomicAdd(a.grad + (int64_t)(c0 + k) * a.in_l + i, v[k]);
+                        }
+                    }
                 }
             }
         }
@@ -1002,6 +1011,13 @@ nif_status dw_x3(nif_handle* h, const float* X, int64_t ldx, int in_l, const flo
     const int tiles = (in_l + 127) / 128;
     const int64_t nkb = (n_max + 31) / 32;
     const int gy = (int)std::max<int64_t>(1, std::min<int64_t>(nkb, std::max(1, h->num_sms / tiles)));
+    const int64_t cnt = (int64_t)out_l * in_l;
+    if (h->det) {
+        // each row range's sum kept apart (a range with no live rows leaves zeros)
+        if ((st = nif_grow(h, h->b_parts, sizeof(float) * (size_t)gy * cnt)) != NIF_OK) return st;
+        a.part = (float*)h->b_parts.p;
+        NIF_CK(h, cudaMemsetAsync(a.part, 0, sizeof(float) * (size_t)gy * cnt, s));
+    }
     auto launch = [&](auto kern) -> nif_status {
         NIF_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total));
         kern<<<dim3(tiles, gy), kDwX3Threads, total, s>>>(xm, dm, a, n_dev, h->d_status);
@@ -1015,6 +1031,7 @@ nif_status dw_x3(nif_handle* h, const float* X, int64_t ldx, int in_l, const flo
     }
     if (st != NIF_OK) return st;
     NIF_CK_LAUNCH(h);
+    if (a.part) return nif_sum_parts_run(h, a.part, gy, cnt, grad, s);
     return NIF_OK;
 }
 

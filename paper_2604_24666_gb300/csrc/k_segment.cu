@@ -842,13 +842,14 @@ __global__ void __launch_bounds__(kTravWarps * 32, 32 / kTravWarps) k_seg_traver
 __global__ void __launch_bounds__(256) k_seg_scatter(const nif_segment* __restrict__ temp, const uint32_t* __restrict__ n_temp,
                                                      int64_t temp_cap, const uint32_t* __restrict__ offsets,
                                                      uint32_t* __restrict__ fill, nif_segment* __restrict__ segs,
-                                                     int64_t cap) {
+                                                     int64_t cap, int n_rays) {
     int64_t n = *n_temp;
     if (n > temp_cap) n = temp_cap;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         nif_segment sg = temp[i];
+        if (!NIF_IN(sg.ray, n_rays)) continue;
         int64_t g = (int64_t)offsets[sg.ray] + atomicAdd(fill + sg.ray, 1u);
-        if (g < cap) segs[g] = sg;
+        if (g < cap && NIF_IN(g, (int64_t)offsets[sg.ray + 1])) segs[g] = sg;
     }
 }
 
@@ -1226,7 +1227,7 @@ nif_status nif_seg_scatter_run(nif_handle* h, const nif_segment* temp, const uin
     unsigned g = nif_blocks(std::max<int64_t>(n_temp_max, 1), 256);
     unsigned gcap = (unsigned)h->num_sms * 8;
     if (g > gcap) g = gcap;
-    k_seg_scatter<<<g, 256, 0, s>>>(temp, n_temp, n_temp_max, offsets, fill, segs, cap);
+    k_seg_scatter<<<g, 256, 0, s>>>(temp, n_temp, n_temp_max, offsets, fill, segs, cap, n_rays);
     NIF_CK_LAUNCH(h);
     k_seg_sort<<<nif_blocks(n_rays, 256), 256, 0, s>>>(offsets, n_rays, segs, cap);   // 8 warps x 32 rays
     NIF_CK_LAUNCH(h);

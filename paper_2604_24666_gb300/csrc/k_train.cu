@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) k_labels(const nif_segment* __restrict__ 
                                                 const float4* __restrict__ geo,
                                                 const float* __restrict__ alb, const uint8_t* __restrict__ mat,
                                                 nif_label* __restrict__ out, int* __restrict__ n_hit,
-                                                uint32_t nvox) {
+                                                uint32_t nvox, int n_tris) {
     int64_t n = n_dev ? (int64_t)*n_dev : n_max;
     if (n > n_max) n = n_max;
     int local_hits = 0;
@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(256) k_labels(const nif_segment* __restrict__ 
         int bt = -1;
         for (uint32_t q = a; q < b; q++) {
             int t = tri_idx[q];
+            if (!NIF_IN(t, n_tris)) continue;
             const float4 g0 = __ldg(geo + 3 * t), g1 = __ldg(geo + 3 * t + 1), g2 = __ldg(geo + 3 * t + 2);
             float Ax = g0.x, Ay = g0.y, Az = g0.z;
             float e1x = g0.w, e1y = g1.x, e1z = g1.y;
@@ -107,7 +108,8 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ out, con
                                               const nif_linseg* __restrict__ lin, const uint32_t* __restrict__ n_dev,
                                               int64_t n_max, const int* __restrict__ n_hit,
                                               const float* __restrict__ s_par, int N, int M, unsigned flags,
-                                              float* __restrict__ dout, double* __restrict__ acc) {
+                                              float* __restrict__ dout, double* __restrict__ acc,
+                                              double* __restrict__ parts) {
     int64_t n = n_dev ? (int64_t)*n_dev : n_max;
     if (n > n_max) n = n_max;
     int nh = *n_hit;
@@ -192,15 +194,24 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ out, con
     if (threadIdx.x < 5) {
         double t = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w][threadIdx.x];
-        atomicAdd(acc + threadIdx.x, t);
+        // deterministic mode: each block's sums are kept and added in block order
+        if (parts) parts[5 * blockIdx.x + threadIdx.x] = t;
+        else atomicAdd(acc + threadIdx.x, t);
     }
 }
 
 // parts -> total and dL/ds (added into the gradient buffer)
-__global__ void k_loss_final(double* acc, const uint32_t* __restrict__ n_dev, int64_t n_max,
+__global__ void k_loss_final(double* acc, const double* __restrict__ parts, int n_parts,
+                             const uint32_t* __restrict__ n_dev, int64_t n_max,
                              const int* __restrict__ n_hit, const float* __restrict__ s_par, unsigned flags,
                              float* __restrict__ ds, int* status) {
     if (threadIdx.x != 0) return;
+    if (parts)
+        for (int i = 0; i < 5; i++) {
+            double t = 0;
+            for (int b = 0; b < n_parts; b++) t += parts[5 * b + i];
+            acc[i] = t;
+        }
     int64_t n = n_dev ? (int64_t)*n_dev : n_max;
     if (n > n_max) n = n_max;
     int nh = *n_hit;
@@ -537,7 +548,7 @@ nif_status nif_labels_run(nif_handle* h, const nif_segment* segs, const nif_lins
     unsigned cap = (unsigned)h->num_sms * 8;
     if (g > cap) g = cap;
     k_labels<<<g, 256, 0, s>>>(segs, lin, n_dev, n_max, h->d_tri_ptr, h->d_tri_idx, h->d_tri_geo, h->d_alb,
-                               h->d_mat, labels, n_hit, (uint32_t)((int64_t)h->N * h->N * h->N));
+                               h->d_mat, labels, n_hit, (uint32_t)((int64_t)h->N * h->N * h->N), h->n_tris);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }
@@ -555,16 +566,42 @@ nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels
     NifProf prof_(h, "loss", s);
     if (!n_hit) n_hit = h->d_count;
     NIF_CK(h, cudaMemsetAsync(h->d_lossacc, 0, sizeof(double) * 16, s));
+    double* parts = nullptr;
+    unsigned g = 0;
     if (n_max > 0) {
-        unsigned g = nif_blocks(n_max, 256);
+        g = nif_blocks(n_max, 256);
         unsigned cap = (unsigned)h->num_sms * 8;
         if (g > cap) g = cap;
+        if (h->det) {
+            nif_status st = nif_grow(h, h->b_lparts, sizeof(double) * 5 * (size_t)g);
+            if (st != NIF_OK) return st;
+            parts = (double*)h->b_lparts.p;
+        }
         k_loss<<<g, 256, 0, s>>>(out, labels, lin, n_dev, n_max, n_hit, h->d_params + h->off_s, h->N,
-                                 h->cfg.n_materials, h->cfg.flags, dout, h->d_lossacc);
+                                 h->cfg.n_materials, h->cfg.flags, dout, h->d_lossacc, parts);
         NIF_CK_LAUNCH(h);
     }
-    k_loss_final<<<1, 32, 0, s>>>(h->d_lossacc, n_dev, n_max, n_hit, h->d_params + h->off_s, h->cfg.flags,
-                                  want_ds ? h->d_grad + h->off_s : nullptr, h->d_status);
+    k_loss_final<<<1, 32, 0, s>>>(h->d_lossacc, parts, (int)g, n_dev, n_max, n_hit, h->d_params + h->off_s,
+                                  h->cfg.flags, want_ds ? h->d_grad + h->off_s : nullptr, h->d_status);
+    NIF_CK_LAUNCH(h);
+    return NIF_OK;
+}
+
+// grad[e] += part[0][e] + part[1][e] + ... in row-range order (deterministic
+// mode's weight gradients: each range's sum was stored, not added in L2)
+__global__ void __launch_bounds__(256) k_sum_parts(const float* __restrict__ part, int ny, int64_t cnt,
+                                                   float* __restrict__ grad) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+        float t = 0.f;
+        for (int y = 0; y < ny; y++) t += part[(int64_t)y * cnt + e];
+        grad[e] += t;
+    }
+}
+
+nif_status nif_sum_parts_run(nif_handle* h, const float* part, int ny, int64_t cnt, float* grad, cudaStream_t s) {
+    if (cnt <= 0 || ny <= 0) return NIF_OK;
+    const unsigned g = (unsigned)std::min<int64_t>(nif_blocks(cnt, 256), (int64_t)h->num_sms * 8);
+    k_sum_parts<<<g, 256, 0, s>>>(part, ny, cnt, grad);
     NIF_CK_LAUNCH(h);
     return NIF_OK;
 }

@@ -595,7 +595,7 @@ extern "C" void nif_destroy(nif_handle* h) {
     nif_handle::Buf* bufs[] = {&h->b_counts, &h->b_offsets, &h->b_segs, &h->b_lin, &h->b_feat, &h->b_out,
                                &h->b_acts, &h->b_dout, &h->b_dx, &h->b_labels, &h->b_scan, &h->b_rays,
                                &h->b_inst, &h->b_feat2, &h->b_temp, &h->b_dys, &h->b_dup, &h->b_pts,
-                               &h->b_lattice, &h->b_sort, &h->b_lin_t, &h->b_feat_alt, &h->alt_counts, &h->alt_offsets, &h->alt_temp, &h->alt_segs,
+                               &h->b_lattice, &h->b_sort, &h->b_lin_t, &h->b_feat_alt, &h->b_fix, &h->b_parts, &h->b_lparts, &h->alt_counts, &h->alt_offsets, &h->alt_temp, &h->alt_segs,
                                &h->alt_scan, &h->alt_rays, &h->alt_inst, &h->alt_lin, &h->alt_labels,
                                &h->alt_dup, &h->alt_pts, &h->alt_sort};
     for (auto* b : bufs)
@@ -762,7 +762,7 @@ uint32_t crc32_ieee(const uint8_t* p, size_t n) {
 CkptHeader ckpt_header(const nif_handle* h) {
     CkptHeader hd{};
     std::memcpy(hd.magic, "NIFCKPT1", 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.n_params_lo = (uint32_t)(h->n_params & 0xFFFFFFFFu);
     hd.n_params_hi = (uint32_t)(h->n_params >> 32);
     hd.L = (uint32_t)h->L;
@@ -780,7 +780,7 @@ CkptHeader ckpt_header(const nif_handle* h) {
 
 extern "C" nif_status nif_checkpoint_bytes(const nif_handle* h, size_t* bytes) {
     if (!h || !bytes) return NIF_ERR_ARG;
-    *bytes = sizeof(CkptHeader) + 3 * sizeof(float) * h->n_params + sizeof(uint32_t);
+    *bytes = sizeof(CkptHeader) + 3 * sizeof(float) * h->n_params + sizeof(NifLossScale) + sizeof(uint32_t);
     return NIF_OK;
 }
 
@@ -796,8 +796,10 @@ extern "C" nif_status nif_checkpoint_save(nif_handle* h, void* dst, size_t bytes
     NIF_CK(h, cudaMemcpy(o + sizeof hd, h->d_params, nb, cudaMemcpyDeviceToHost));
     NIF_CK(h, cudaMemcpy(o + sizeof hd + nb, h->d_m, nb, cudaMemcpyDeviceToHost));
     NIF_CK(h, cudaMemcpy(o + sizeof hd + 2 * nb, h->d_v, nb, cudaMemcpyDeviceToHost));
-    uint32_t crc = crc32_ieee(o, sizeof hd + 3 * nb);
-    std::memcpy(o + sizeof hd + 3 * nb, &crc, sizeof crc);
+    NIF_CK(h, cudaMemcpy(o + sizeof hd + 3 * nb, h->d_ls, sizeof(NifLossScale), cudaMemcpyDeviceToHost));
+    const size_t body = sizeof hd + 3 * nb + sizeof(NifLossScale);
+    uint32_t crc = crc32_ieee(o, body);
+    std::memcpy(o + body, &crc, sizeof crc);
     return NIF_OK;
 }
 
@@ -812,13 +814,15 @@ extern "C" nif_status nif_checkpoint_load(nif_handle* h, const void* src, size_t
     mine.adam_step = hd.adam_step;
     if (std::memcmp(&hd, &mine, sizeof hd) != 0) return nif_fail(h, NIF_ERR_ARG, "checkpoint header mismatch");
     size_t nb = sizeof(float) * h->n_params;
+    const size_t body = sizeof hd + 3 * nb + sizeof(NifLossScale);
     uint32_t crc = 0;
-    std::memcpy(&crc, in + sizeof hd + 3 * nb, sizeof crc);
-    if (crc != crc32_ieee(in, sizeof hd + 3 * nb)) return nif_fail(h, NIF_ERR_ARG, "checkpoint CRC mismatch");
+    std::memcpy(&crc, in + body, sizeof crc);
+    if (crc != crc32_ieee(in, body)) return nif_fail(h, NIF_ERR_ARG, "checkpoint CRC mismatch");
     NIF_CK(h, cudaDeviceSynchronize());
     NIF_CK(h, cudaMemcpy(h->d_params, in + sizeof hd, nb, cudaMemcpyHostToDevice));
     NIF_CK(h, cudaMemcpy(h->d_m, in + sizeof hd + nb, nb, cudaMemcpyHostToDevice));
     NIF_CK(h, cudaMemcpy(h->d_v, in + sizeof hd + 2 * nb, nb, cudaMemcpyHostToDevice));
+    NIF_CK(h, cudaMemcpy(h->d_ls, in + sizeof hd + 3 * nb, sizeof(NifLossScale), cudaMemcpyHostToDevice));
     NIF_CK(h, cudaMemset(h->d_grad, 0, nb));
     h->adam_step = hd.adam_step;
     h->lowp_dirty = true;
@@ -1863,6 +1867,35 @@ extern "C" nif_status nif_train_steps_rays(nif_handle* h, int n_steps, const nif
 }
 
 // ---------------------------------------------------------------------------
+// Bounds build: each translation unit registers the reader of its device word
+// ---------------------------------------------------------------------------
+static std::vector<unsigned long long (*)()>& bounds_takers() {
+    static std::vector<unsigned long long (*)()> v;
+    return v;
+}
+
+int nif_bounds_register(unsigned long long (*take)()) {
+    bounds_takers().push_back(take);
+    return 1;
+}
+
+extern "C" nif_status nif_bounds_check(int* enabled, unsigned long long* failures) {
+    if (!enabled || !failures) return NIF_ERR_ARG;
+    *failures = 0;
+#if defined(NIF_BOUNDS) && NIF_BOUNDS
+    *enabled = 1;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return NIF_ERR_CUDA;
+    }
+    for (auto take : bounds_takers()) *failures += take();
+#else
+    *enabled = 0;
+#endif
+    return NIF_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Knobs
 // ---------------------------------------------------------------------------
 extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
@@ -1915,6 +1948,13 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
             h->q_init = value;
             h->q_hint = 0.0;
             h->q_pending = false;
+            return NIF_OK;
+        case NIF_KNOB_DETERMINISTIC:
+            if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "deterministic knob must be 0 or 1");
+            if (value == 1.0 && h->concat)
+                return nif_fail(h, NIF_ERR_ARG, "deterministic gradients cover the composed reading of Eq. 1 only");
+            NIF_CK(h, cudaDeviceSynchronize());
+            h->det = value == 1.0;
             return NIF_OK;
         case NIF_KNOB_SEG_SCRATCH:
             if (!(value > 0.0 && value <= 1.0)) return nif_fail(h, NIF_ERR_ARG, "segment scratch scale must be in (0, 1]");

@@ -19,6 +19,41 @@
 #define NIF_EPS_DIST 1e-2f    // log-distance epsilon (voxel units)
 
 // ---------------------------------------------------------------------------
+// Bounds build. Compiled with -DNIF_BOUNDS=1, NIF_IN(i, n) checks 0 <= i < n
+// at the index computations that use it (the grid cell of every encoder
+// gather and scatter, label triangles, the rest-space point order, the
+// per-ray segment rows); a failed check adds one to this translation unit's
+// device word and the caller redirects or skips the access, so nothing
+// traps. nif_bounds_check() (include/nif.h) sums and clears the words of
+// every translation unit. In the normal build NIF_IN is the constant true
+// and compiles away.
+// ---------------------------------------------------------------------------
+#if defined(NIF_BOUNDS) && NIF_BOUNDS
+int nif_bounds_register(unsigned long long (*take)());
+namespace {
+__device__ unsigned long long nif_bounds_word;
+__device__ __forceinline__ bool nif_in_bounds(long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicAdd(&nif_bounds_word, 1ull);
+    return false;
+}
+unsigned long long nif_bounds_take() {
+    unsigned long long v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, nif_bounds_word, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaMemcpyToSymbol(nif_bounds_word, &z, sizeof z);
+    return v;
+}
+const int nif_bounds_registered = nif_bounds_register(&nif_bounds_take);
+}  // namespace
+#define NIF_IN(i, n) nif_in_bounds((long long)(i), (long long)(n))
+#else
+#define NIF_IN(i, n) true
+#endif
+
+// ---------------------------------------------------------------------------
 // Encoding constants passed by value to kernels.
 // ---------------------------------------------------------------------------
 struct GridInfo {
@@ -163,6 +198,13 @@ struct nif_handle {
     Buf b_counts, b_offsets, b_segs, b_lin, b_feat, b_out, b_acts, b_dout, b_dx, b_labels,
         b_scan, b_rays, b_inst, b_feat2, b_temp, b_dys, b_dup, b_pts, b_lattice, b_sort, b_lin_t,
         b_feat_alt;                     // the other step's FP32 features while its weight gradients run late
+    // NIF_KNOB_DETERMINISTIC: gradients summed in an order-free way. b_fix holds
+    // the table gradient as 64-bit fixed point ([L][T][F_d] words, zero between
+    // calls) followed by two 32-bit words (max |dL/dfeature| bits, scale exponent);
+    // b_parts the weight-gradient partial sums of each row range; b_lparts the
+    // loss partial sums of each block
+    bool det = false;
+    Buf b_fix, b_parts, b_lparts;
     // FP32 steps with the weight update deferred (NIF_KNOB_DEFER_WEIGHTS): the
     // weights' Adam runs on the second stream after the weight gradients and
     // records ev_wupd; the next step's MLP forward waits for it
@@ -422,6 +464,9 @@ nif_status nif_loss_run(nif_handle* h, const float* out, const nif_label* labels
                         const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max, float* dout,
                         cudaStream_t s, bool want_ds = true, const int* n_hit = nullptr);
 nif_status nif_adam_run(nif_handle* h, float lr_grid, float lr_mlp, cudaStream_t s);
+// grad[e] += sum over y = 0 .. ny-1, in that order, of part[y * cnt + e]
+// (the order-fixed reduction of per-range partial sums in deterministic mode)
+nif_status nif_sum_parts_run(nif_handle* h, const float* part, int ny, int64_t cnt, float* grad, cudaStream_t s);
 // Adam over the tables (on s_tab) and over the weights and log-variances (on
 // s_w) as two launches of the same step (one step count, the same bias
 // corrections); false from *split when the ranges cannot be split on

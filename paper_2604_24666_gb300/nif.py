@@ -15,7 +15,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libnif.so")
+# NIF_BOUNDS_BUILD=1 loads the bounds-checked build of the same sources
+# (build(bounds=True): index checks that count failures instead of trapping)
+LIB_PATH = os.path.join(_HERE, "libnif_bounds.so" if os.environ.get("NIF_BOUNDS_BUILD") == "1" else "libnif.so")
 
 NIF_OK, NIF_ERR_ARG, NIF_ERR_CUDA, NIF_ERR_OOM, NIF_ERR_CAPACITY, NIF_ERR_TIMEOUT, NIF_ERR_NAN, NIF_ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7
@@ -29,6 +31,7 @@ NIF_KNOB_WAIT_NS, NIF_KNOB_SEG_SCRATCH, NIF_KNOB_QUERY_SEGS, NIF_KNOB_BATCH_AT, 
 NIF_KNOB_QUERY_FUSED, NIF_KNOB_STEP_PRIORITY, NIF_KNOB_DEFER_WEIGHTS = 6, 7, 8
 NIF_KNOB_STEP_FWD_CTAS = 9
 NIF_KNOB_STEP_BWD_CTAS = 10
+NIF_KNOB_DETERMINISTIC = 11
 NIF_PROBE_RED8, NIF_PROBE_RED16, NIF_PROBE_LOAD8, NIF_PROBE_LOAD4 = 1, 2, 3, 4
 NIF_PROBE_RED8_WARP, NIF_PROBE_RED16_WARP, NIF_PROBE_LOAD8_WARP, NIF_PROBE_LOAD4_WARP = 5, 6, 7, 8
 
@@ -78,7 +81,8 @@ def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError(f"libnif.so is not built ({LIB_PATH}); run paper_2604_24666_gb300.build.build()")
+            raise ImportError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); "
+                              "run paper_2604_24666_gb300.build.build()")
         L = ctypes.CDLL(LIB_PATH)
         sig = {
             "nif_create": ([ctypes.POINTER(nif_config), ctypes.POINTER(nif_mesh), ctypes.POINTER(_vp)], ctypes.c_int),
@@ -150,6 +154,7 @@ def lib() -> ctypes.CDLL:
             "nif_checkpoint_save": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
             "nif_checkpoint_load": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
             "nif_kernel_launches": ([], ctypes.c_ulonglong),
+            "nif_bounds_check": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_ulonglong)], ctypes.c_int),
             "nif_profile": ([_vp, ctypes.c_int], ctypes.c_int),
             "nif_profile_filter": ([_vp, ctypes.c_char_p], ctypes.c_int),
             "nif_profile_timeline": ([_vp, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -624,7 +629,10 @@ def nif_set_knob(h, knob, value):
     not results. Examples: NIF_KNOB_WAIT_NS bounds the tensor-core kernels'
     waits (ns; 0 = default), NIF_KNOB_SEG_SCRATCH scales the single-traversal
     segment scratch, and NIF_KNOB_STEP_FWD_CTAS / NIF_KNOB_STEP_BWD_CTAS set
-    how the FP32 training step shares SMs between concurrent kernels."""
+    how the FP32 training step shares SMs between concurrent kernels.
+    NIF_KNOB_DETERMINISTIC = 1 is the one knob that changes results (in
+    their last bits): gradients are then summed in an order-free way, so
+    that repeated runs and resumed checkpoints give bit-identical states."""
     _check(h, lib().nif_set_knob(h, knob, float(value)))
 
 
@@ -639,6 +647,16 @@ def nif_checkpoint_save(h) -> bytes:
 def nif_checkpoint_load(h, blob: bytes):
     buf = (ctypes.c_uint8 * len(blob)).from_buffer_copy(blob)
     _check(h, lib().nif_checkpoint_load(h, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
+
+
+def nif_bounds_check():
+    """(enabled, failures): whether this is the bounds-checked build, and the
+    index checks that failed since the last call (then cleared)."""
+    en, n = ctypes.c_int(), ctypes.c_ulonglong()
+    st = lib().nif_bounds_check(ctypes.byref(en), ctypes.byref(n))
+    if st != NIF_OK:
+        raise NifError(st, "nif_bounds_check failed")
+    return bool(en.value), int(n.value)
 
 
 def nif_kernel_launches() -> int:

@@ -31,6 +31,8 @@ of a typical sincosf difference), which passes 1e-4 at the finest levels
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 import oracle as O
@@ -105,7 +107,20 @@ def loss_grad_bound(net, out, lab, s, l_rest, out_err, flags=0):
     return err
 
 
-def table_grad_bound(net, tables, p, dfeat, dfeat_err=0.0):
+def fixed_scale(n_segments, P, dfeat):
+    """Scale exponent S of the deterministic table gradient for a call on
+    n_segments segments with gradients dfeat (float32, as the GPU holds
+    them): every sum is bounded by B = 2 n P max|dfeat|, and S is the largest
+    integer with B 2^S < 2^61 (0 when B = 0). Computed in the same double
+    arithmetic and order as the library, so both sides get the same S."""
+    m = float(np.abs(np.asarray(dfeat, np.float32)).max()) if np.size(dfeat) else 0.0
+    b = 2.0 * float(n_segments) * float(P) * m
+    if b == 0.0:
+        return 0
+    return 61 - math.frexp(b)[1]
+
+
+def table_grad_bound(net, tables, p, dfeat, dfeat_err=0.0, fix_S=None):
     """[L, T, F_d] bound on the FP32 table gradient of sum(dfeat * psi(p))
     against the oracle's (same cells). Entry e with contributions w_i d_i,
     i = 1..k_e:
@@ -113,7 +128,8 @@ def table_grad_bound(net, tables, p, dfeat, dfeat_err=0.0):
       + 3 N_l DU sum_{i sin/cos} |d_i|     sin/cos weights
       + sum w_i dfeat_err_i                error of the given gradients
     dfeat_err is a scalar or per element of dfeat. Several (p, dfeat) pairs
-    are summed by calling this on the stacked arrays."""
+    are summed by calling this on the stacked arrays. fix_S (deterministic
+    mode) adds k_e 2^-(S+1): each contribution rounded to a multiple of 2^-S."""
     tables = np.asarray(tables, np.float64)
     _, u = _terms(net, p)
     n, P = u.shape[0], u.shape[1]
@@ -137,7 +153,8 @@ def table_grad_bound(net, tables, p, dfeat, dfeat_err=0.0):
                 if t > 0:
                     np.add.at(B[l], idx, d[:, t, l, :])
     res_col = np.asarray(res, np.float64)[:, None, None]
-    return (K[..., None] + 6) * U32 * A + 3 * res_col * DU * B + E
+    fix = 0.0 if fix_S is None else K[..., None] * 2.0 ** -(fix_S + 1)
+    return (K[..., None] + 6) * U32 * A + 3 * res_col * DU * B + E + fix
 
 
 def point_grad_bound(net, tables, p, dfeat, dfeat_err=0.0):

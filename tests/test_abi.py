@@ -78,3 +78,11 @@ def test_product_code_never_touches_the_oracle():
                 if re.search(r"^\s*(import|from)\s+oracle\b|nif_oracle|oracle/", src, flags=re.M):
                     offenders.append(f)
     assert not offenders, offenders
+
+
+def test_bounds_check_reports_the_normal_build_without_device():
+    """The normal build's index checks compile away: nif_bounds_check says so
+    without touching the device; null arguments fail validation."""
+    from paper_2604_24666_gb300 import nif
+    assert nif.nif_bounds_check() == (False, 0)
+    assert nif.lib().nif_bounds_check(None, None) == nif.NIF_ERR_ARG

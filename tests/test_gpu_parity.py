@@ -418,13 +418,17 @@ def _abs_mat(ws, lo, hi):
     return m
 
 
-def test_train_gradients_match_oracle(nif, torus):
+@pytest.mark.parametrize("det", [0, 1], ids=["l2-reductions", "deterministic"])
+def test_train_gradients_match_oracle(nif, torus, det):
     """The whole backward of a training batch (loss -> MLP backward ->
     encoding backward -> parameter gradients) on identical inputs: linearized
     segments from the seeded generator, ground-truth labels from the oracle
     (fed to both sides), so that every gradient can be compared element by
     element. Bounds: loss output gradient 1e-5 of its largest entry (FP32
-    loss), carried back through |W| (tests/bounds.py for the encoding)."""
+    loss), carried back through |W| (tests/bounds.py for the encoding). With
+    NIF_KNOB_DETERMINISTIC the table gradient's bound adds the fixed-point
+    rounding, 2^-(S+1) per contribution, and a second backward on the same
+    inputs must give the same gradients bit for bit."""
     net = S.NetConfig()
     N = net.voxel_res
     occ, ptr, idx = O.voxelize(N, torus)
@@ -444,6 +448,8 @@ def test_train_gradients_match_oracle(nif, torus):
     assert n > 1500 and rlab["occ"].sum() > 300, (n, rlab["occ"].sum())
 
     h = nif.Nif(net, torus)
+    if det:
+        nif.nif_set_knob(h.h, nif.NIF_KNOB_DETERMINISTIC, 1)
     h.set_params(tables, ws, s)
     lab = np.zeros(n, dtype=nif.LABEL_DTYPE)
     for k in ("tpar", "normal", "albedo", "occ", "material"):
@@ -460,6 +466,19 @@ def test_train_gradients_match_oracle(nif, torus):
     nif.nif_encode_segments_backward(h.h, lint, dx, dtab)
     torch.cuda.synchronize()
     _, gws, gs = h.get_grads()
+    if det:
+        # the same backward again: every gradient repeats bit for bit
+        nif.nif_zero_grad(h.h)
+        parts2, dout2 = nif.nif_loss(h.h, out, labt, lint)
+        dx2 = nif.nif_mlp_backward(h.h, feat, acts, dout2)
+        dtab2 = torch.zeros_like(dtab)
+        nif.nif_encode_segments_backward(h.h, lint, dx2, dtab2)
+        torch.cuda.synchronize()
+        _, gws2, gs2 = h.get_grads()
+        assert np.array_equal(parts2, parts)
+        assert torch.equal(dx2, dx) and torch.equal(dtab2, dtab)
+        assert all(np.array_equal(a, b) for a, b in zip(gws2, gws)) and np.array_equal(gs2, gs)
+    fix_S = B.fixed_scale(n, net.n_terms, dx.cpu().numpy()) if det else None
     dout, dx, g = dout.cpu().numpy(), dx.cpu().numpy(), dtab.cpu().numpy()
 
     o, racts = O.mlp_forward(ws, x)
@@ -487,7 +506,7 @@ def test_train_gradients_match_oracle(nif, torus):
         tol = 2e-5 * np.abs(rdw[i]).max() + ey.T @ np.abs(racts[i])
         assert np.all(np.abs(gws[i] - rdw[i]) <= tol), (i, (np.abs(gws[i] - rdw[i]) / tol).max())
     bt = B.table_grad_bound(net, tables, np.concatenate([p0, p1]), np.concatenate([rdx[:, :half], rdx[:, half:]]),
-                            dfeat_err=np.concatenate([tol_dx[:, :half], tol_dx[:, half:]]))
+                            dfeat_err=np.concatenate([tol_dx[:, :half], tol_dx[:, half:]]), fix_S=fix_S)
     assert np.all(np.abs(g - rt) <= bt), (np.abs(g - rt) / np.maximum(bt, 1e-300)).max()
     h.close()
 

@@ -103,21 +103,33 @@ def test_encode_forward_fp16_tables_matches_oracle(nif, handle, batch, out):
     assert np.all(err <= tol), (err / tol).max()
 
 
-def test_encode_backward_sorted_matches_oracle(nif, handle, batch):
+@pytest.mark.parametrize("det", [0, 1], ids=["l2-reductions", "deterministic"])
+def test_encode_backward_sorted_matches_oracle(nif, handle, batch, det):
+    """The table gradient at the training sizes; with NIF_KNOB_DETERMINISTIC
+    the 64-bit fixed-point sums instead, whose bound adds 2^-(S+1) per
+    contribution and whose second run must repeat the first bit for bit."""
     lin, tables = batch
     net = NET
     handle.set_params(tables, S.init_params(net)[1])
     n = len(lin)
     df = np.random.default_rng(203).normal(size=(n, net.in_dim)).astype(np.float32)
+    lint, dft = torch.from_numpy(lin).to(_dev()), torch.from_numpy(df).to(_dev())
     dtab = torch.zeros((net.levels, 1 << net.log2_table, net.feats), dtype=torch.float32, device=_dev())
-    nif.nif_encode_segments_backward(handle.h, torch.from_numpy(lin).to(_dev()), torch.from_numpy(df).to(_dev()),
-                                     dtab)
+    nif.nif_set_knob(handle.h, nif.NIF_KNOB_DETERMINISTIC, det)
+    try:
+        nif.nif_encode_segments_backward(handle.h, lint, dft, dtab)
+        if det:
+            again = torch.zeros_like(dtab)
+            nif.nif_encode_segments_backward(handle.h, lint, dft, again)
+            assert torch.equal(again, dtab)
+    finally:
+        nif.nif_set_knob(handle.h, nif.NIF_KNOB_DETERMINISTIC, 0)
     g = dtab.cpu().numpy()
     half = net.in_dim // 2
     p = np.concatenate([lin[:, 0:3], lin[:, 3:6]]).astype(np.float64)
     d = np.concatenate([df[:, :half], df[:, half:]]).astype(np.float64)
     ref, _ = O.encode_points_backward(net, tables, p, d)
-    bnd = B.table_grad_bound(net, tables, p, d)
+    bnd = B.table_grad_bound(net, tables, p, d, fix_S=B.fixed_scale(n, net.n_terms, df) if det else None)
     err = np.abs(g - ref)
     assert np.all(err <= bnd), ((err / np.maximum(bnd, 1e-300)).max(), int((err > bnd).sum()))
     # untouched rows stay exactly zero
@@ -170,6 +182,28 @@ def test_mlp_split_tf32_full_batch_matches_oracle(nif, handle):
         sabs = np.abs(g).T @ np.abs(racts[i])
         tol = (2.0 ** -21 + 2.0 ** -17) * sabs + 1e-6 * np.abs(rdw[i]).max()
         err = np.abs(gws[i] - rdw[i])
+        assert np.all(err <= tol), (i, (err / tol).max())
+        g = g @ np.asarray(ws[i], np.float64)
+        if i > 0:
+            g = g * (racts[i] > 0)
+    # deterministic mode: each row range's sum stored and the ranges added in
+    # order; the same bound, and a second run repeats the first bit for bit
+    nif.nif_set_knob(handle.h, nif.NIF_KNOB_DETERMINISTIC, 1)
+    try:
+        runs = []
+        for _ in range(2):
+            nif.nif_zero_grad(handle.h)
+            nif.nif_mlp_backward(handle.h, xt, acts, torch.from_numpy(dout).to(_dev()), want_dx=False)
+            torch.cuda.synchronize()
+            runs.append(handle.get_grads()[1])
+    finally:
+        nif.nif_set_knob(handle.h, nif.NIF_KNOB_DETERMINISTIC, 0)
+    assert all(np.array_equal(a, b) for a, b in zip(runs[0], runs[1]))
+    g = dout.astype(np.float64)
+    for i in range(len(ws) - 1, -1, -1):
+        sabs = np.abs(g).T @ np.abs(racts[i])
+        tol = (2.0 ** -21 + 2.0 ** -17) * sabs + 1e-6 * np.abs(rdw[i]).max()
+        err = np.abs(runs[0][i] - rdw[i])
         assert np.all(err <= tol), (i, (err / tol).max())
         g = g @ np.asarray(ws[i], np.float64)
         if i > 0:
