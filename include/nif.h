@@ -674,6 +674,11 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   Slower (measured on the 64^3 FP32 step in the design notes). Handles
  *   with NIF_FLAG_CONCAT_ENCODING are refused (NIF_ERR_ARG). Synchronises the
  *   device.
+ * NIF_KNOB_ORDER_BITS: b in [4, 8] (default 7): the encoders of tables over
+ *   4 MiB visit the distinct end points sorted by the Morton code of their
+ *   cell in a 2^b-per-axis grid over the rest cube (a counting sort over
+ *   2^(3b) cells), so that a warp's points share corner rows. A scheduling
+ *   choice only: the features are the same. Synchronises the device.
  * NIF_ERR_ARG for an unknown knob or a value out of range. */
 #define NIF_KNOB_WAIT_NS 1
 #define NIF_KNOB_SEG_SCRATCH 2
@@ -686,6 +691,7 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
 #define NIF_KNOB_STEP_FWD_CTAS 9
 #define NIF_KNOB_STEP_BWD_CTAS 10
 #define NIF_KNOB_DETERMINISTIC 11
+#define NIF_KNOB_ORDER_BITS 12
 nif_status nif_set_knob(nif_handle* h, int knob, double value);
 
 /* Allocation-free variant of nif_segments (the paper has no counterpart:

@@ -437,6 +437,7 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_sm(GridInfo g, Coa
 // takes more of them (with a fixed stride a block's warps waited at its final
 // barrier for the slowest one).
 constexpr int kRun = 32;
+constexpr int kFixBad = -100000;         // deterministic mode's scale word: a non-finite dL/dfeature was seen
 
 __device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
@@ -445,6 +446,21 @@ __device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
                  : "memory");
+}
+
+// deterministic mode's flush: each corner sum (an FP32 value fixed by the
+// chunk's points and their order) rounded to 64-bit fixed point, scale 2^S,
+// and added with integer atomics, whose result does not depend on the order
+__device__ __forceinline__ void flush_cell_fixed(unsigned long long* dl, int ix, int iy, int iz, int Nl, bool dense,
+                                                 uint32_t T, const float2* acc, double scale) {
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const uint32_t r = grid_row(ix + (q & 1), iy + ((q >> 1) & 1), iz + ((q >> 2) & 1), Nl, dense, T);
+        const long long a = __double2ll_rn((double)acc[q].x * scale);
+        const long long b = __double2ll_rn((double)acc[q].y * scale);
+        if (a) atomicAdd(dl + 2 * r, (unsigned long long)a);
+        if (b) atomicAdd(dl + 2 * r + 1, (unsigned long long)b);
+    }
 }
 
 __device__ __forceinline__ void flush_cell(float* dl, bool in_sh, int ix, int iy, int iz, int Nl, bool dense,
@@ -468,6 +484,10 @@ __device__ __forceinline__ void flush_cell(float* dl, bool in_sh, int ix, int iy
     }
 }
 
+// FIX (deterministic mode): the shared-memory levels and the table gradient
+// are 64-bit fixed point (sfix, fix), flushed by flush_cell_fixed; the scale
+// exponent comes from S_dev (k_fix_scale), and dtab is not touched.
+template <bool FIX>
 __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coarse cs,
                                                                  const nif_linseg* __restrict__ lin,
                                                                  const uint32_t* __restrict__ n_dev, int64_t n_max,
@@ -476,10 +496,22 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
                                                                  const uint32_t* __restrict__ pts,
                                                                  const uint32_t* __restrict__ n_pts_dev,
                                                                  const uint32_t* __restrict__ dupf,
-                                                                 uint32_t* __restrict__ next) {
+                                                                 uint32_t* __restrict__ next,
+                                                                 unsigned long long* __restrict__ fix,
+                                                                 const int* __restrict__ S_dev) {
     extern __shared__ float sacc[];
+    unsigned long long* sfix = reinterpret_cast<unsigned long long*>(sacc);
+    double scale = 0.0;
+    if (FIX) {
+        const int S = *S_dev;
+        if (S == kFixBad) return;                 // the conversion writes NaN gradients
+        scale = ldexp(1.0, S);
+    }
     const int nsh = cs.soff[cs.Lc];
-    for (int i = threadIdx.x; i < nsh; i += blockDim.x) sacc[i] = 0.f;
+    for (int i = threadIdx.x; i < nsh; i += blockDim.x) {
+        if (FIX) sfix[i] = 0ull;
+        else sacc[i] = 0.f;
+    }
     __syncthreads();
     int64_t n = n_dev ? (int64_t)*n_dev : n_max;
     if (n > n_max) n = n_max;
@@ -492,6 +524,7 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
     const bool dense = (g.dense_mask >> l) & 1u;
     const bool in_sh = l < cs.Lc;
     float* dl = in_sh ? sacc + cs.soff[l] : dtab + (int64_t)l * g.T * 2;
+    unsigned long long* dlf = FIX ? (in_sh ? sfix + cs.soff[l] : fix + (int64_t)l * g.T * 2) : nullptr;
     // the distinct end points in order (a repeated entry point adds its
     // feature gradient to the exit point it repeats), 2 kRun per chunk
     const int64_t n_points = *n_pts_dev;
@@ -555,7 +588,10 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
                     gr.y += g2.y;
                 }
                 if (cl.ix != cx || cl.iy != cy || cl.iz != cz) {
-                    if (cx >= 0) flush_cell(dl, in_sh, cx, cy, cz, Nl, dense, g.T, cacc);
+                    if (cx >= 0) {
+                        if (FIX) flush_cell_fixed(dlf, cx, cy, cz, Nl, dense, g.T, cacc, scale);
+                        else flush_cell(dl, in_sh, cx, cy, cz, Nl, dense, g.T, cacc);
+                    }
                     cx = cl.ix;
                     cy = cl.iy;
                     cz = cl.iz;
@@ -577,15 +613,22 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
                 }
             }
         }
-        if (cx >= 0) flush_cell(dl, in_sh, cx, cy, cz, Nl, dense, g.T, cacc);
+        if (cx >= 0) {
+            if (FIX) flush_cell_fixed(dlf, cx, cy, cz, Nl, dense, g.T, cacc, scale);
+            else flush_cell(dl, in_sh, cx, cy, cz, Nl, dense, g.T, cacc);
+        }
     }
     __syncthreads();
     for (int lv = 0; lv < cs.Lc; lv++) {
         int cnt = cs.soff[lv + 1] - cs.soff[lv];
-        float* dst = dtab + (int64_t)lv * g.T * 2;
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-            float v = sacc[cs.soff[lv] + i];
-            if (v != 0.f) atomicAdd(dst + i, v);
+            if (FIX) {
+                const unsigned long long v = sfix[cs.soff[lv] + i];
+                if (v) atomicAdd(fix + (int64_t)lv * g.T * 2 + i, v);
+            } else {
+                float v = sacc[cs.soff[lv] + i];
+                if (v != 0.f) atomicAdd(dtab + (int64_t)lv * g.T * 2 + i, v);
+            }
         }
     }
 }
@@ -680,35 +723,36 @@ nif_status distinct_points(nif_handle* h, const nif_linseg* lin, const uint32_t*
 }
 
 // The distinct points in rest-space order: a counting sort by the Morton
-// code of each point's cell in a 64^3 grid over the cube. A warp of the
-// encoder then takes 32 points of one small region, whose corner rows at the
-// coarse levels (and the low bands of gamma) coincide, so their loads merge
-// into far fewer L1 wavefronts than points taken along rays; the gather is
-// bound by L1 wavefronts. The order within a cell is arbitrary and does not
-// matter: every point's features go to its own rows.
-constexpr int kOrderBits = 6;
-constexpr uint32_t kOrderCells = 1u << (3 * kOrderBits);
-
-__device__ __forceinline__ uint32_t spread3(uint32_t v) {
-    v &= 0x3Fu;
-    v = (v | (v << 8)) & 0x0000F00Fu;
-    v = (v | (v << 4)) & 0x000C30C3u;
-    v = (v | (v << 2)) & 0x00249249u;
+// code of each point's cell in a 2^b x 2^b x 2^b grid over the cube
+// (b = NIF_KNOB_ORDER_BITS, default 7: a finer grid keeps the backward's
+// cell cache on one cell longer at the middle levels). A warp of the encoder then takes 32
+// points of one small region, whose corner rows at the coarse levels (and
+// the low bands of gamma) coincide, so their loads merge into far fewer L1
+// wavefronts than points taken along rays; the gather is bound by L1
+// wavefronts. The order within a cell is arbitrary and does not matter:
+// every point's features go to its own rows.
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {     // bits 0..9 of v to bits 0, 3, 6, ...
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
     return v;
 }
 
 __global__ void __launch_bounds__(256) k_point_keys(const nif_linseg* __restrict__ lin, const uint32_t* __restrict__ pts,
-                                                    const uint32_t* __restrict__ n_pts_dev, uint32_t* __restrict__ keys,
-                                                    uint32_t* __restrict__ hist) {
+                                                    const uint32_t* __restrict__ n_pts_dev, int bits,
+                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
     const int64_t n = *n_pts_dev;
-    const float cells = (float)(1 << kOrderBits);
+    const float cells = (float)(1 << bits);
+    const uint32_t top = (1u << bits) - 1u;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t pt = pts[k];
         const float* L = reinterpret_cast<const float*>(lin + (pt >> 1)) + 3 * (pt & 1u);
         const float3 p = clamp01(make_float3(L[0], L[1], L[2]));
-        const uint32_t ix = min((uint32_t)(p.x * cells), (1u << kOrderBits) - 1u);
-        const uint32_t iy = min((uint32_t)(p.y * cells), (1u << kOrderBits) - 1u);
-        const uint32_t iz = min((uint32_t)(p.z * cells), (1u << kOrderBits) - 1u);
+        const uint32_t ix = min((uint32_t)(p.x * cells), top);
+        const uint32_t iy = min((uint32_t)(p.y * cells), top);
+        const uint32_t iz = min((uint32_t)(p.z * cells), top);
         const uint32_t key = spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
         keys[k] = key;
         atomicAdd(hist + key, 1u);
@@ -728,26 +772,53 @@ __global__ void __launch_bounds__(256) k_point_scatter(const uint32_t* __restric
     }
 }
 
+// Deterministic mode: the scatter above leaves a cell's points in the order
+// the atomics gave them; each cell's run is put in ascending point order (one
+// thread a cell, insertion sort: cells hold a few points each), so the order,
+// and with it every float sum the backward forms along it, is fixed.
+__global__ void __launch_bounds__(256) k_point_cell_sort(const uint32_t* __restrict__ off, int64_t cells,
+                                                         uint32_t* __restrict__ sorted) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = off[c], b = off[c + 1];
+        for (uint32_t i = a + 1; i < b; i++) {
+            const uint32_t v = sorted[i];
+            uint32_t j = i;
+            while (j > a && sorted[j - 1] > v) {
+                sorted[j] = sorted[j - 1];
+                j--;
+            }
+            sorted[j] = v;
+        }
+    }
+}
+
 // sorted (out): the *n_pts_dev points of pts in rest-space order
 nif_status spatial_order(nif_handle* h, const nif_linseg* lin, const uint32_t* pts, const uint32_t* n_pts_dev,
                          int64_t n_max, const uint32_t** sorted_out, cudaStream_t s) {
     const size_t np = 2 * (size_t)n_max;
-    const size_t nbs = kOrderCells / 1024 + 2;
-    nif_status st = nif_grow(h, h->b_sort, sizeof(uint32_t) * (2 * np + 2 * (size_t)kOrderCells + 1 + nbs));
+    const int bits = h->tune.order_bits;
+    const size_t cells = (size_t)1 << (3 * bits);
+    const size_t nbs = cells / 1024 + 2;
+    nif_status st = nif_grow(h, h->b_sort, sizeof(uint32_t) * (2 * np + 2 * cells + 1 + nbs));
     if (st != NIF_OK) return st;
     uint32_t* keys = (uint32_t*)h->b_sort.p;
     uint32_t* sorted = keys + np;
     uint32_t* hist = sorted + np;
-    uint32_t* off = hist + kOrderCells;
-    uint32_t* bsum = off + kOrderCells + 1;
+    uint32_t* off = hist + cells;
+    uint32_t* bsum = off + cells + 1;
     const unsigned g = std::min<unsigned>(nif_blocks((int64_t)np, 256), (unsigned)h->num_sms * 8);
-    NIF_CK(h, cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kOrderCells, s));
-    k_point_keys<<<g, 256, 0, s>>>(lin, pts, n_pts_dev, keys, hist);
+    NIF_CK(h, cudaMemsetAsync(hist, 0, sizeof(uint32_t) * cells, s));
+    k_point_keys<<<g, 256, 0, s>>>(lin, pts, n_pts_dev, bits, keys, hist);
     NIF_CK_LAUNCH(h);
-    if ((st = nif_scan_run_with(h, hist, off, (int)kOrderCells, bsum, s)) != NIF_OK) return st;
-    NIF_CK(h, cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kOrderCells, s));
+    if ((st = nif_scan_run_with(h, hist, off, (int)cells, bsum, s)) != NIF_OK) return st;
+    NIF_CK(h, cudaMemsetAsync(hist, 0, sizeof(uint32_t) * cells, s));
     k_point_scatter<<<g, 256, 0, s>>>(pts, n_pts_dev, keys, off, hist, sorted);
     NIF_CK_LAUNCH(h);
+    if (h->det) {
+        k_point_cell_sort<<<(unsigned)std::min<int64_t>(nif_blocks((int64_t)cells, 256), (int64_t)h->num_sms * 8), 256,
+                            0, s>>>(off, (int64_t)cells, sorted);
+        NIF_CK_LAUNCH(h);
+    }
     *sorted_out = sorted;
     return NIF_OK;
 }
@@ -982,7 +1053,6 @@ __global__ void __launch_bounds__(256) k_encode_cat_dp(GridInfo g, const float* 
 // 2^61, which leaves the rounding (at most 1/2 per contribution) far from
 // overflow. Each contribution's rounding error is at most 2^-(S+1).
 // ---------------------------------------------------------------------------
-constexpr int kFixBad = -100000;         // scale word: a non-finite dL/dfeature was seen
 
 // *bits = max over the first min(*n_dev, n_max) * per floats of x of the bit
 // pattern of |x| (the order of non-negative floats; NaN compares above inf)
@@ -1185,8 +1255,51 @@ nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n,
 
 // Deterministic mode's table gradient (see k_encode_bwd_fixed): the scale from
 // max |dL/dfeature|, the fixed-point sums, their conversion into dtables.
+// The distinct end points the backward walks: the forward's list when it is
+// of these segments (a training step), else listed (and ordered) here.
+static nif_status bwd_points(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
+                             bool reuse_points, const uint32_t** pts, const uint32_t** n_pts, const uint32_t** dupf,
+                             cudaStream_t s) {
+    // rest-space order: a lane's run of points stays in one small region,
+    // so its cell cache flushes less at the middle levels
+    const bool sorted = (size_t)h->T * h->L * h->Fd * sizeof(float) > ((size_t)4 << 20);
+    const nif_handle::PointList& pl = h->enc_points;
+    if (reuse_points && pl.pts && pl.lin == lin && pl.n_dev == n_dev && pl.n_max == n_max && pl.sorted == sorted) {
+        *pts = pl.pts;                                    // as the forward of this step left them
+        *n_pts = pl.n_pts;
+        *dupf = pl.dupf;
+        return NIF_OK;
+    }
+    nif_status st = distinct_points(h, lin, n_dev, n_max, pts, n_pts, dupf, s);
+    if (st != NIF_OK) return st;
+    if (sorted && (st = spatial_order(h, lin, *pts, *n_pts, n_max, pts, s)) != NIF_OK) return st;
+    return NIF_OK;
+}
+
+// Dense prefix of levels of at most max_rows rows each that fits `budget`
+// elements of shared memory (two per row).
+static Coarse coarse_levels(const nif_handle* h, int64_t max_rows, int budget) {
+    Coarse cs{};
+    cs.Lc = 0;
+    cs.soff[0] = 0;
+    for (int l = 0; l < h->L; l++) {
+        if (!((h->grid.dense_mask >> l) & 1u)) break;
+        const int64_t r = (int64_t)h->grid.res[l] + 1;
+        if (r * r * r > max_rows || cs.soff[l] + 2 * r * r * r > budget) break;
+        cs.soff[l + 1] = cs.soff[l] + (int)(2 * r * r * r);
+        cs.Lc = l + 1;
+    }
+    return cs;
+}
+
+// Deterministic mode's table gradient: the scale from max |dL/dfeature|
+// (k_absmax_bits, k_fix_scale), the fixed-point sums -- by the run-length
+// walk over the distinct points in their fixed order where the default path
+// takes it (its per-cell FP32 sums depend only on the chunk's points and
+// order, which are fixed, and are rounded once each), else one thread per
+// (segment, end point, gamma term) -- and their conversion into dtables.
 static nif_status encode_bwd_fixed(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
-                                   const float* dfeats, float* dtables, cudaStream_t s) {
+                                   const float* dfeats, float* dtables, cudaStream_t s, bool reuse_points, int ctas) {
     const int64_t cnt = (int64_t)h->L * h->T * 2;
     const size_t bytes = sizeof(unsigned long long) * (size_t)cnt;
     if (h->b_fix.bytes < bytes + 16) {
@@ -1204,24 +1317,28 @@ static nif_status encode_bwd_fixed(nif_handle* h, const nif_linseg* lin, const u
     NIF_CK_LAUNCH(h);
     k_fix_scale<<<1, 32, 0, s>>>(bits, n_dev, n_max, h->P, S_dev);
     NIF_CK_LAUNCH(h);
-    // dense coarse levels of at most 4096 rows in shared memory (96 KB at most,
-    // two 1024-thread blocks per SM)
-    Coarse cs{};
-    cs.Lc = 0;
-    cs.soff[0] = 0;
-    const int budget = 96 * 1024 / 8;
-    for (int l = 0; l < h->L; l++) {
-        if (!((h->grid.dense_mask >> l) & 1u)) break;
-        const int64_t r = (int64_t)h->grid.res[l] + 1;
-        if (r * r * r > 4096 || cs.soff[l] + 2 * r * r * r > budget) break;
-        cs.soff[l + 1] = cs.soff[l] + (int)(2 * r * r * r);
-        cs.Lc = l + 1;
+    if (32 % h->L == 0 && h->L >= 4) {
+        const uint32_t *pts, *n_pts, *dupf;
+        nif_status st = bwd_points(h, lin, n_dev, n_max, reuse_points, &pts, &n_pts, &dupf, s);
+        if (st != NIF_OK) return st;
+        const Coarse cs = coarse_levels(h, h->tune.bwd_smem_rows, 200 * 1024 / 8);
+        const size_t smem = sizeof(unsigned long long) * (size_t)cs.soff[cs.Lc];
+        NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+        NIF_CK(h, cudaMemsetAsync(h->d_next + 1, 0, sizeof(uint32_t), s));
+        k_encode_segments_bwd_rl<true><<<ctas > 0 ? std::min(ctas, h->num_sms) : h->num_sms, 1024, smem, s>>>(
+            h->grid, cs, lin, n_dev, n_max, dfeats, dtables, pts, n_pts, dupf, h->d_next + 1, fix, S_dev);
+        NIF_CK_LAUNCH(h);
+    } else {
+        // dense coarse levels of at most 4096 rows in shared memory (96 KB at
+        // most, two 1024-thread blocks per SM)
+        const Coarse cs = coarse_levels(h, 4096, 96 * 1024 / 8);
+        const size_t smem = sizeof(unsigned long long) * (size_t)cs.soff[cs.Lc];
+        NIF_CK(h, cudaFuncSetAttribute(k_encode_bwd_fixed, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        const unsigned gb = (unsigned)std::min<int64_t>(nif_blocks(n_max * 2 * h->P, 1024), (int64_t)h->num_sms * 2);
+        k_encode_bwd_fixed<<<gb, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, fix, S_dev);
+        NIF_CK_LAUNCH(h);
     }
-    const size_t smem = sizeof(unsigned long long) * (size_t)cs.soff[cs.Lc];
-    NIF_CK(h, cudaFuncSetAttribute(k_encode_bwd_fixed, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-    const unsigned gb = (unsigned)std::min<int64_t>(nif_blocks(n_max * 2 * h->P, 1024), (int64_t)h->num_sms * 2);
-    k_encode_bwd_fixed<<<gb, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, fix, S_dev);
-    NIF_CK_LAUNCH(h);
     const unsigned gc = (unsigned)std::min<int64_t>(nif_blocks(cnt, 256), (int64_t)h->num_sms * 8);
     k_fix_to_float<<<gc, 256, 0, s>>>(fix, cnt, S_dev, dtables);
     NIF_CK_LAUNCH(h);
@@ -1233,7 +1350,7 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
                                        int ctas) {
     NifProf prof_(h, "encode_bwd", s);
     if (n_max <= 0) return NIF_OK;
-    if (h->det && !h->concat) return encode_bwd_fixed(h, lin, n_dev, n_max, dfeats, dtables, s);
+    if (h->det && !h->concat) return encode_bwd_fixed(h, lin, n_dev, n_max, dfeats, dtables, s, reuse_points, ctas);
     if (h->concat) {
         const int64_t work = n_max * 2 * h->L;
         k_encode_cat_bwd<<<(unsigned)std::min<int64_t>(nif_blocks(work, 256), (int64_t)h->num_sms * 16), 256, 0, s>>>(
@@ -1242,43 +1359,19 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
         return NIF_OK;
     }
     // dense prefix of levels that fits the shared-memory budget
-    const int budget = 200 * 1024 / 4;
-    Coarse cs{};
-    cs.Lc = 0;
-    cs.soff[0] = 0;
-    for (int l = 0; l < h->L; l++) {
-        if (!((h->grid.dense_mask >> l) & 1u)) break;
-        int64_t r = (int64_t)h->grid.res[l] + 1;
-        if (r * r * r > h->tune.bwd_smem_rows) break;
-        int64_t need = r * r * r * 2;
-        if (cs.soff[l] + need > budget) break;
-        cs.soff[l + 1] = cs.soff[l] + (int)need;
-        cs.Lc = l + 1;
-    }
+    const Coarse cs = coarse_levels(h, h->tune.bwd_smem_rows, 200 * 1024 / 4);
     size_t smem = sizeof(float) * (size_t)cs.soff[cs.Lc];
     if (32 % h->L == 0 && h->L >= 4) {      // a level group holds the 3 lanes that evaluate u
         const uint32_t *pts, *n_pts, *dupf;
-        // rest-space order: a lane's run of points stays in one small region,
-        // so its cell cache flushes less at the middle levels
-        const bool sorted = (size_t)h->T * h->L * h->Fd * sizeof(float) > ((size_t)4 << 20);
-        const nif_handle::PointList& pl = h->enc_points;
-        if (reuse_points && pl.pts && pl.lin == lin && pl.n_dev == n_dev && pl.n_max == n_max &&
-            pl.sorted == sorted) {
-            pts = pl.pts;                                 // as the forward of this step left them
-            n_pts = pl.n_pts;
-            dupf = pl.dupf;
-        } else {
-            nif_status st = distinct_points(h, lin, n_dev, n_max, &pts, &n_pts, &dupf, s);
-            if (st != NIF_OK) return st;
-            if (sorted && (st = spatial_order(h, lin, pts, n_pts, n_max, &pts, s)) != NIF_OK) return st;
-        }
-        NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        nif_status st = bwd_points(h, lin, n_dev, n_max, reuse_points, &pts, &n_pts, &dupf, s);
+        if (st != NIF_OK) return st;
+        NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
         // at most one 1024-thread block per SM (64 registers a thread fill the
         // register file); its warps take chunks from the task counter
         NIF_CK(h, cudaMemsetAsync(h->d_next + 1, 0, sizeof(uint32_t), s));
-        k_encode_segments_bwd_rl<<<ctas > 0 ? std::min(ctas, h->num_sms) : h->num_sms, 1024, smem, s>>>(h->grid, cs, lin, n_dev, n_max, dfeats, dtables, pts,
-                                                                n_pts, dupf, h->d_next + 1);
+        k_encode_segments_bwd_rl<false><<<ctas > 0 ? std::min(ctas, h->num_sms) : h->num_sms, 1024, smem, s>>>(
+            h->grid, cs, lin, n_dev, n_max, dfeats, dtables, pts, n_pts, dupf, h->d_next + 1, nullptr, nullptr);
         NIF_CK_LAUNCH(h);
         return NIF_OK;
     }

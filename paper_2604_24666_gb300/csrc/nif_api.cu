@@ -1949,12 +1949,22 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
             h->q_hint = 0.0;
             h->q_pending = false;
             return NIF_OK;
+        case NIF_KNOB_ORDER_BITS:
+            if (!(value >= 4.0 && value <= 8.0) || value != std::floor(value))
+                return nif_fail(h, NIF_ERR_ARG, "point-order grid bits must be an integer in [4, 8]");
+            NIF_CK(h, cudaDeviceSynchronize());
+            h->tune.order_bits = (int)value;
+            h->enc_points = nif_handle::PointList{};     // a listed order of the old grid is not reused
+            h->alt_enc_points = nif_handle::PointList{};
+            return NIF_OK;
         case NIF_KNOB_DETERMINISTIC:
             if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "deterministic knob must be 0 or 1");
             if (value == 1.0 && h->concat)
                 return nif_fail(h, NIF_ERR_ARG, "deterministic gradients cover the composed reading of Eq. 1 only");
             NIF_CK(h, cudaDeviceSynchronize());
             h->det = value == 1.0;
+            h->enc_points = nif_handle::PointList{};     // a listed order is re-made in the mode's own way
+            h->alt_enc_points = nif_handle::PointList{};
             return NIF_OK;
         case NIF_KNOB_SEG_SCRATCH:
             if (!(value > 0.0 && value <= 1.0)) return nif_fail(h, NIF_ERR_ARG, "segment scratch scale must be in (0, 1]");
