@@ -438,6 +438,13 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_sm(GridInfo g, Coa
 // barrier for the slowest one).
 constexpr int kRun = 32;
 constexpr int kFixBad = -100000;         // deterministic mode's scale word: a non-finite dL/dfeature was seen
+constexpr int kFixMinS = -60, kFixMaxS = 100;
+
+// 2^S as an FP32 value (exact: S in [kFixMinS, kFixMaxS]). A FP32 value times
+// 2^S is exact wherever the rounding to an integer can matter (results of at
+// least 1/2 are far above FP32's normal range limit), so the rounding gives
+// what the exact product would.
+__device__ __forceinline__ float fix_scale_f(int S) { return __int_as_float((S + 127) << 23); }
 
 __device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
@@ -452,12 +459,12 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
 // chunk's points and their order) rounded to 64-bit fixed point, scale 2^S,
 // and added with integer atomics, whose result does not depend on the order
 __device__ __forceinline__ void flush_cell_fixed(unsigned long long* dl, int ix, int iy, int iz, int Nl, bool dense,
-                                                 uint32_t T, const float2* acc, double scale) {
+                                                 uint32_t T, const float2* acc, float scale) {
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         const uint32_t r = grid_row(ix + (q & 1), iy + ((q >> 1) & 1), iz + ((q >> 2) & 1), Nl, dense, T);
-        const long long a = __double2ll_rn((double)acc[q].x * scale);
-        const long long b = __double2ll_rn((double)acc[q].y * scale);
+        const long long a = __float2ll_rn(acc[q].x * scale);
+        const long long b = __float2ll_rn(acc[q].y * scale);
         if (a) atomicAdd(dl + 2 * r, (unsigned long long)a);
         if (b) atomicAdd(dl + 2 * r + 1, (unsigned long long)b);
     }
@@ -501,11 +508,11 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
                                                                  const int* __restrict__ S_dev) {
     extern __shared__ float sacc[];
     unsigned long long* sfix = reinterpret_cast<unsigned long long*>(sacc);
-    double scale = 0.0;
+    float scale = 0.f;
     if (FIX) {
         const int S = *S_dev;
         if (S == kFixBad) return;                 // the conversion writes NaN gradients
-        scale = ldexp(1.0, S);
+        scale = fix_scale_f(S);
     }
     const int nsh = cs.soff[cs.Lc];
     for (int i = threadIdx.x; i < nsh; i += blockDim.x) {
@@ -1090,7 +1097,9 @@ __global__ void k_fix_scale(const uint32_t* __restrict__ bits, const uint32_t* _
     if (B == 0.0) { *S_out = 0; return; }      // every contribution is zero
     int E = 0;
     frexp(B, &E);                              // B = m 2^E, 1/2 <= m < 1, so B 2^(61-E) < 2^61
-    *S_out = 61 - E;
+    // a smaller S only coarsens the rounding; an S below the lowest would mean
+    // gradients near FP32's range limit, treated as non-finite
+    *S_out = 61 - E < kFixMinS ? kFixBad : min(61 - E, kFixMaxS);
 }
 
 // One thread per (segment, end point, gamma term), as k_encode_segments_bwd_sm:
@@ -1104,7 +1113,7 @@ __global__ void __launch_bounds__(1024) k_encode_bwd_fixed(GridInfo g, Coarse cs
     extern __shared__ unsigned long long sfix[];
     const int S = *S_dev;
     if (S == kFixBad) return;                  // the conversion writes NaN gradients
-    const double scale = ldexp(1.0, S);
+    const float scale = fix_scale_f(S);
     const int nsh = cs.soff[cs.Lc];
     for (int i = threadIdx.x; i < nsh; i += blockDim.x) sfix[i] = 0ull;
     __syncthreads();
@@ -1131,8 +1140,8 @@ __global__ void __launch_bounds__(1024) k_encode_bwd_fixed(GridInfo g, Coarse cs
             for (int q = 0; q < 8; q++) {
                 const uint32_t row = grid_row(c.ix + (q & 1), c.iy + ((q >> 1) & 1), c.iz + ((q >> 2) & 1), Nl, dense, g.T);
                 const float w = ((q & 1) ? c.wx : 1.f - c.wx) * ((q & 2) ? c.wy : 1.f - c.wy) * ((q & 4) ? c.wz : 1.f - c.wz);
-                const long long a = __double2ll_rn((double)(w * gr.x) * scale);
-                const long long b = __double2ll_rn((double)(w * gr.y) * scale);
+                const long long a = __float2ll_rn((w * gr.x) * scale);
+                const long long b = __float2ll_rn((w * gr.y) * scale);
                 if (a) atomicAdd(dl + 2 * row, (unsigned long long)a);
                 if (b) atomicAdd(dl + 2 * row + 1, (unsigned long long)b);
             }

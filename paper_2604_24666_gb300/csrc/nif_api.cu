@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nif_internal.cuh"
 
 #include <atomic>
@@ -31,7 +33,11 @@ static bool prof_selected(const std::string& filter, const char* name) {
     return false;
 }
 
+// Every stage is also an NVTX range on the calling host thread (header-only
+// NVTX 3: a no-op unless a tool such as ncu --nvtx is attached), so a
+// profiler can select one stage's launches by name.
 NifProf::NifProf(nif_handle* h_, const char* name, cudaStream_t s_) : h(h_), s(s_) {
+    nvtxRangePushA(name);
     if (!h || !h->prof || !prof_selected(h->prof_filter, name)) return;
     if (h->prof_used + 2 > h->prof_pool.size()) {
         for (int i = 0; i < 64; i++) {
@@ -49,6 +55,7 @@ NifProf::NifProf(nif_handle* h_, const char* name, cudaStream_t s_) : h(h_), s(s
 
 NifProf::~NifProf() {
     if (rec != (size_t)-1) cudaEventRecord(h->prof_recs[rec].b, s);
+    nvtxRangePop();
 }
 
 extern "C" nif_status nif_profile(nif_handle* h, int enable) {

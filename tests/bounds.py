@@ -111,13 +111,15 @@ def fixed_scale(n_segments, P, dfeat):
     """Scale exponent S of the deterministic table gradient for a call on
     n_segments segments with gradients dfeat (float32, as the GPU holds
     them): every sum is bounded by B = 2 n P max|dfeat|, and S is the largest
-    integer with B 2^S < 2^61 (0 when B = 0). Computed in the same double
+    integer with B 2^S < 2^61, at most 100 (0 when B = 0). Computed in the same double
     arithmetic and order as the library, so both sides get the same S."""
     m = float(np.abs(np.asarray(dfeat, np.float32)).max()) if np.size(dfeat) else 0.0
     b = 2.0 * float(n_segments) * float(P) * m
     if b == 0.0:
         return 0
-    return 61 - math.frexp(b)[1]
+    s = 61 - math.frexp(b)[1]
+    assert s >= -60, "gradients this large are reported as non-finite"
+    return min(s, 100)
 
 
 def table_grad_bound(net, tables, p, dfeat, dfeat_err=0.0, fix_S=None):
