@@ -679,6 +679,14 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   cell in a 2^b-per-axis grid over the rest cube (a counting sort over
  *   2^(3b) cells), so that a warp's points share corner rows. A scheduling
  *   choice only: the features are the same. Synchronises the device.
+ * NIF_KNOB_FAIL_ALLOC: n >= 1 makes the n-th allocation of scratch memory
+ *   from now on (a buffer the handle grows on demand) fail as an
+ *   out-of-memory cudaMalloc would: the call that needs it returns
+ *   NIF_ERR_OOM and the buffer is left unallocated, to be allocated again
+ *   by a later call. 0 (default) disables it. Host-side fault injection for
+ *   testing recovery; nothing fails on the device. A training call that
+ *   fails before its parameter update clears the gradients it had added,
+ *   so the trainable state is the one before the call.
  * NIF_ERR_ARG for an unknown knob or a value out of range. */
 #define NIF_KNOB_WAIT_NS 1
 #define NIF_KNOB_SEG_SCRATCH 2
@@ -692,6 +700,7 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
 #define NIF_KNOB_STEP_BWD_CTAS 10
 #define NIF_KNOB_DETERMINISTIC 11
 #define NIF_KNOB_ORDER_BITS 12
+#define NIF_KNOB_FAIL_ALLOC 13
 nif_status nif_set_knob(nif_handle* h, int knob, double value);
 
 /* Allocation-free variant of nif_segments (the paper has no counterpart:

@@ -162,6 +162,8 @@ nif_status nif_grow(nif_handle* h, nif_handle::Buf& b, size_t bytes) {
         b.bytes = 0;
     }
     size_t want = bytes + bytes / 4 + 256;
+    if (h->fail_alloc > 0 && --h->fail_alloc == 0)
+        return nif_fail(h, NIF_ERR_OOM, "cudaMalloc(scratch): injected failure (NIF_KNOB_FAIL_ALLOC)");
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1381,9 +1383,30 @@ static int step_fwd_ctas(const nif_handle* h, int64_t n, bool fp32) {
     return (int)((tiles + per - 1) / per);
 }
 
+static nif_status train_compute_on(nif_handle* h, int n_rays, int64_t n_segments, const int* n_hit, float lr_grid,
+                                   float lr_mlp, double* loss_host, cudaStream_t s, cudaEvent_t ev_next,
+                                   bool join_weights, int set);
+
+// One step's forward, losses, backward and update. A step that fails before
+// its update (an allocation, an argument of a stage) may have added part of
+// its gradients: they are cleared, after the device has finished what was
+// enqueued, so that the trainable state is the one before the step.
 static nif_status train_compute(nif_handle* h, int n_rays, int64_t n_segments, const int* n_hit, float lr_grid,
                                 float lr_mlp, double* loss_host, cudaStream_t s, cudaEvent_t ev_next = nullptr,
                                 bool join_weights = true, int set = -1) {
+    const nif_status st =
+        train_compute_on(h, n_rays, n_segments, n_hit, lr_grid, lr_mlp, loss_host, s, ev_next, join_weights, set);
+    if (st == NIF_OK || st == NIF_ERR_NAN || st == NIF_ERR_TIMEOUT || st == NIF_ERR_CAPACITY) return st;
+    if (cudaDeviceSynchronize() == cudaSuccess && cudaMemset(h->d_grad, 0, sizeof(float) * h->n_params) == cudaSuccess)
+        h->wupd_pending = false;
+    else
+        cudaGetLastError();
+    return st;
+}
+
+static nif_status train_compute_on(nif_handle* h, int n_rays, int64_t n_segments, const int* n_hit, float lr_grid,
+                                   float lr_mlp, double* loss_host, cudaStream_t s, cudaEvent_t ev_next,
+                                   bool join_weights, int set) {
     nif_status st;
     const bool mixed = (h->cfg.flags & NIF_FLAG_MIXED_TRAINING) != 0;
     uint32_t* offs = (uint32_t*)h->b_offsets.p;
@@ -1963,6 +1986,11 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
             h->tune.order_bits = (int)value;
             h->enc_points = nif_handle::PointList{};     // a listed order of the old grid is not reused
             h->alt_enc_points = nif_handle::PointList{};
+            return NIF_OK;
+        case NIF_KNOB_FAIL_ALLOC:
+            if (!(value >= 0.0 && value <= 1.0e6) || value != std::floor(value))
+                return nif_fail(h, NIF_ERR_ARG, "allocation-failure countdown must be an integer in [0, 1e6]");
+            h->fail_alloc = (int)value;
             return NIF_OK;
         case NIF_KNOB_DETERMINISTIC:
             if (value != 0.0 && value != 1.0) return nif_fail(h, NIF_ERR_ARG, "deterministic knob must be 0 or 1");

@@ -205,6 +205,9 @@ struct nif_handle {
     // loss partial sums of each block
     bool det = false;
     Buf b_fix, b_parts, b_lparts;
+    // NIF_KNOB_FAIL_ALLOC: the n-th scratch allocation from the knob's setting
+    // fails as an out-of-memory cudaMalloc would (host-side fault injection)
+    int fail_alloc = 0;
     // FP32 steps with the weight update deferred (NIF_KNOB_DEFER_WEIGHTS): the
     // weights' Adam runs on the second stream after the weight gradients and
     // records ev_wupd; the next step's MLP forward waits for it

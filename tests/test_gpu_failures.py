@@ -11,6 +11,11 @@ address is bad, and every wait that a test makes run out is bounded.
 * A segment capacity that is too small returns (or, in a query plan,
   latches) NIF_ERR_CAPACITY and writes nothing past it.
 * A non-finite parameter makes a training step report NIF_ERR_NAN.
+* An allocation made to fail on the host (NIF_KNOB_FAIL_ALLOC) returns
+  NIF_ERR_OOM; the handle recovers with the results, and the training state,
+  of a handle that never failed.
+* A loss scale far too large makes FP16 steps overflow one after another:
+  each is skipped and halves the scale until steps are taken again.
 """
 import ctypes
 
@@ -158,4 +163,116 @@ def test_non_finite_parameter_reports_nan(nif, torus):
     nif.nif_reset_optimizer(h.h)
     loss, _ = nif.nif_train_step(h.h, 1 << 13, 4, 342)
     assert np.all(np.isfinite(loss))
+    h.close()
+
+
+def test_injected_allocation_failure_query_recovers(nif, torus):
+    """Each of a fresh handle's first scratch allocations fails in turn
+    (NIF_KNOB_FAIL_ALLOC, an out-of-memory cudaMalloc made on the host): the
+    query returns NIF_ERR_OOM, and the same query on the same handle then
+    gives bit for bit the hits of a handle that never failed."""
+    net = S.NetConfig()
+    tables, ws, s = S.init_params(net, seed=351)
+    rays = torch.from_numpy(S.sphere_rays(4096, seed=352)).to(_dev())
+    pose = [(0.3, -0.5, 0.2)]
+    ref_h = nif.Nif(net, torus)
+    ref_h.set_params(tables, ws, s)
+    ref = nif.nif_query(ref_h.h, pose, rays).clone()
+    torch.cuda.synchronize()
+    failed = []
+    for k in range(1, 9):
+        h = nif.Nif(net, torus)
+        h.set_params(tables, ws, s)
+        nif.nif_set_knob(h.h, nif.NIF_KNOB_FAIL_ALLOC, k)
+        try:
+            nif.nif_query(h.h, pose, rays)
+            torch.cuda.synchronize()
+        except nif.NifError as e:
+            assert e.status == nif.NIF_ERR_OOM, e
+            failed.append(k)
+        nif.nif_set_knob(h.h, nif.NIF_KNOB_FAIL_ALLOC, 0)
+        got = nif.nif_query(h.h, pose, rays)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref), k
+        h.close()
+    assert failed and failed[0] == 1, failed
+    ref_h.close()
+
+
+def _grads_zero(h):
+    t, w, s = h.get_grads()
+    return not np.any(t) and all(not np.any(x) for x in w) and not np.any(s)
+
+
+@pytest.mark.parametrize("mixed", [False, True], ids=["fp32", "bf16-mixed"])
+def test_injected_allocation_failure_training_recovers(nif, torus, mixed):
+    """A training step whose k-th scratch allocation fails returns
+    NIF_ERR_OOM and leaves parameters, Adam state and gradients as they were
+    (gradients it had added are cleared). With deterministic gradients the
+    steps that follow are then bit for bit those of a handle that never
+    failed."""
+    net = S.NetConfig(levels=8, log2_table=12)
+    kw = dict(precision=nif.NIF_BF16, flags=nif.NIF_FLAG_MIXED_TRAINING) if mixed else {}
+
+    def fresh():
+        x = nif.Nif(net, torus, seed=3, **kw)
+        nif.nif_set_knob(x.h, nif.NIF_KNOB_DETERMINISTIC, 1)
+        return x
+
+    ref = fresh()
+    for i in range(2):
+        nif.nif_train_step(ref.h, 1 << 13, 4, 400 + i)
+    want = nif.nif_checkpoint_save(ref.h)
+    ref.close()
+    failed = []
+    for k in (1, 2, 3, 4, 6, 8, 11, 14, 18, 23):
+        h = fresh()
+        blob0 = nif.nif_checkpoint_save(h.h)
+        nif.nif_set_knob(h.h, nif.NIF_KNOB_FAIL_ALLOC, k)
+        try:
+            nif.nif_train_step(h.h, 1 << 13, 4, 400)
+            redo = False
+        except nif.NifError as e:
+            assert e.status == nif.NIF_ERR_OOM, e
+            failed.append(k)
+            assert nif.nif_checkpoint_save(h.h) == blob0
+            assert _grads_zero(h)
+            redo = True
+        nif.nif_set_knob(h.h, nif.NIF_KNOB_FAIL_ALLOC, 0)
+        if redo:
+            nif.nif_train_step(h.h, 1 << 13, 4, 400)
+        nif.nif_train_step(h.h, 1 << 13, 4, 401)
+        assert nif.nif_checkpoint_save(h.h) == want, k
+        h.close()
+    assert len(failed) >= 3, failed
+
+
+def test_loss_scale_overflow_storm(nif, torus):
+    """FP16 steps with a loss scale far too large overflow one after another:
+    each is skipped (parameters unchanged, the skip counted) and halves the
+    scale, until the scale fits and steps are taken again with finite
+    parameters."""
+    net = S.NetConfig()
+    h = nif.Nif(net, torus, precision=nif.NIF_FP16, seed=7, flags=nif.NIF_FLAG_MIXED_TRAINING)
+    nif.nif_set_loss_scale(h.h, 2.0 ** 40)
+    scale, skipped = nif.nif_loss_scale(h.h)
+    assert scale == 2.0 ** 40 and skipped == 0
+    taken = None
+    for i in range(60):
+        before = h.get_params()
+        nif.nif_train_step(h.h, 1 << 13, 4, 500 + i, want_loss=False)
+        sc, sk = nif.nif_loss_scale(h.h)
+        after = h.get_params()
+        if sk == skipped + 1:
+            assert sc == scale / 2
+            assert np.array_equal(after[0], before[0]) and all(np.array_equal(a, b) for a, b in zip(after[1], before[1]))
+        else:
+            assert sk == skipped and sc == scale
+            assert not np.array_equal(after[0], before[0])
+            taken = i
+            break
+        scale, skipped = sc, sk
+    assert taken is not None and taken >= 3, (taken, scale)
+    t, w, s = h.get_params()
+    assert np.isfinite(t).all() and all(np.isfinite(x).all() for x in w) and np.isfinite(s).all()
     h.close()
