@@ -494,7 +494,7 @@ __device__ __forceinline__ void flush_cell(float* dl, bool in_sh, int ix, int iy
 // FIX (deterministic mode): the shared-memory levels and the table gradient
 // are 64-bit fixed point (sfix, fix), flushed by flush_cell_fixed; the scale
 // exponent comes from S_dev (k_fix_scale), and dtab is not touched.
-template <bool FIX>
+template <bool FIX, int KS>
 __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coarse cs,
                                                                  const nif_linseg* __restrict__ lin,
                                                                  const uint32_t* __restrict__ n_dev, int64_t n_max,
@@ -506,6 +506,7 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
                                                                  uint32_t* __restrict__ next,
                                                                  unsigned long long* __restrict__ fix,
                                                                  const int* __restrict__ S_dev) {
+    constexpr int ksplit = KS;
     extern __shared__ float sacc[];
     unsigned long long* sfix = reinterpret_cast<unsigned long long*>(sacc);
     float scale = 0.f;
@@ -523,27 +524,33 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
     int64_t n = n_dev ? (int64_t)*n_dev : n_max;
     if (n > n_max) n = n_max;
     const int lane = threadIdx.x & 31;
-    const int tpw = 32 / g.L;                          // gamma terms per warp
+    // ksplit = 2: a task holds half of the levels (lane = level in the half +
+    // L/2 * term), so a warp's fine (hashed) levels, which flush on almost
+    // every point, fill all 32 lanes instead of idling beside the coarse ones
+    const int LK = g.L / ksplit;                       // levels of a lane group
+    const int tpw = 32 / LK;                           // gamma terms per warp
     const int groups = (g.P + tpw - 1) / tpw;
-    const int l = lane % g.L;
-    const int term_in_warp = lane / g.L;
-    const int Nl = g.res[l];
-    const bool dense = (g.dense_mask >> l) & 1u;
-    const bool in_sh = l < cs.Lc;
-    float* dl = in_sh ? sacc + cs.soff[l] : dtab + (int64_t)l * g.T * 2;
-    unsigned long long* dlf = FIX ? (in_sh ? sfix + cs.soff[l] : fix + (int64_t)l * g.T * 2) : nullptr;
+    const int lh = lane % LK;
+    const int term_in_warp = lane / LK;
     // the distinct end points in order (a repeated entry point adds its
     // feature gradient to the exit point it repeats), 2 kRun per chunk
     const int64_t n_points = *n_pts_dev;
     const int64_t chunks = (n_points + 2 * kRun - 1) / (2 * kRun);
-    const int64_t tasks = chunks * groups;
+    const int64_t tasks = chunks * groups * ksplit;
     for (;;) {
         uint32_t tk = 0;
         if (lane == 0) tk = atomicAdd(next, 1u);
         const int64_t task = (int64_t)__shfl_sync(0xffffffffu, tk, 0);
         if (task >= tasks) break;
-        const int64_t c = task / groups;
-        const int grp = (int)(task - c * groups);
+        const int64_t c = task / (groups * ksplit);
+        const int rem = (int)(task - c * groups * ksplit);
+        const int grp = rem / ksplit;
+        const int l = (rem - grp * ksplit) * LK + lh;      // this lane's level
+        const int Nl = g.res[l];
+        const bool dense = (g.dense_mask >> l) & 1u;
+        const bool in_sh = l < cs.Lc;
+        float* dl = in_sh ? sacc + cs.soff[l] : dtab + (int64_t)l * g.T * 2;
+        unsigned long long* dlf = FIX ? (in_sh ? sfix + cs.soff[l] : fix + (int64_t)l * g.T * 2) : nullptr;
         // a group with fewer terms than level groups (the last one when tpw
         // does not divide P) gives each term nr of them, each walking its own
         // part of the chunk, instead of leaving them idle
@@ -561,7 +568,7 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
         const int part = (span + nr - 1) / nr;
         const int kb = sub < nr ? sub * part : span;      // this part's points: k0 + [kb, ke)
         const int ke = min(kb + part, span);
-        const int base = term_in_warp * g.L;              // first lane of this term's level group
+        const int base = term_in_warp * LK;               // first lane of this term's level group
         for (int i = 0; i < part; i++) {                  // warp-uniform trip count (shuffles below)
             const bool active = kb + i < ke;
             {
@@ -571,7 +578,7 @@ __global__ void __launch_bounds__(1024) k_encode_segments_bwd_rl(GridInfo g, Coa
                 // the term's u is the same for all L levels: lanes base..base+2
                 // evaluate one coordinate each and the group shares them
                 const float* Lp = reinterpret_cast<const float*>(lin + s) + 3 * e;
-                const int cc = l < 3 ? l : 0;
+                const int cc = lh < 3 ? lh : 0;
                 const float pc = fminf(fmaxf(Lp[cc], 0.f), 1.f);
                 float uc;
                 if (tc == 0) {
@@ -1264,6 +1271,13 @@ nif_status nif_encode_points_bwd_run(nif_handle* h, const float* pts, int64_t n,
 
 // Deterministic mode's table gradient (see k_encode_bwd_fixed): the scale from
 // max |dL/dfeature|, the fixed-point sums, their conversion into dtables.
+// Level halves per task of the run-length backward (NIF_KNOB_BWD_SPLIT), where
+// each half still holds the 3 lanes that evaluate a term's u.
+static int bwd_split(const nif_handle* h) {
+    const int k = h->tune.bwd_split;
+    return (k == 2 && h->L % 2 == 0 && 32 % (h->L / 2) == 0 && h->L / 2 >= 4) ? 2 : 1;
+}
+
 // The distinct end points the backward walks: the forward's list when it is
 // of these segments (a training step), else listed (and ordered) here.
 static nif_status bwd_points(nif_handle* h, const nif_linseg* lin, const uint32_t* n_dev, int64_t n_max,
@@ -1332,10 +1346,10 @@ static nif_status encode_bwd_fixed(nif_handle* h, const nif_linseg* lin, const u
         if (st != NIF_OK) return st;
         const Coarse cs = coarse_levels(h, h->tune.bwd_smem_rows, 200 * 1024 / 8);
         const size_t smem = sizeof(unsigned long long) * (size_t)cs.soff[cs.Lc];
-        NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024));
+        auto kern = bwd_split(h) == 2 ? k_encode_segments_bwd_rl<true, 2> : k_encode_segments_bwd_rl<true, 1>;
+        NIF_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         NIF_CK(h, cudaMemsetAsync(h->d_next + 1, 0, sizeof(uint32_t), s));
-        k_encode_segments_bwd_rl<true><<<ctas > 0 ? std::min(ctas, h->num_sms) : h->num_sms, 1024, smem, s>>>(
+        kern<<<ctas > 0 ? std::min(ctas, h->num_sms) : h->num_sms, 1024, smem, s>>>(
             h->grid, cs, lin, n_dev, n_max, dfeats, dtables, pts, n_pts, dupf, h->d_next + 1, fix, S_dev);
         NIF_CK_LAUNCH(h);
     } else {
@@ -1374,12 +1388,12 @@ nif_status nif_encode_segments_bwd_run(nif_handle* h, const nif_linseg* lin, con
         const uint32_t *pts, *n_pts, *dupf;
         nif_status st = bwd_points(h, lin, n_dev, n_max, reuse_points, &pts, &n_pts, &dupf, s);
         if (st != NIF_OK) return st;
-        NIF_CK(h, cudaFuncSetAttribute(k_encode_segments_bwd_rl<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024));
+        auto kern = bwd_split(h) == 2 ? k_encode_segments_bwd_rl<false, 2> : k_encode_segments_bwd_rl<false, 1>;
+        NIF_CK(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         // at most one 1024-thread block per SM (64 registers a thread fill the
         // register file); its warps take chunks from the task counter
         NIF_CK(h, cudaMemsetAsync(h->d_next + 1, 0, sizeof(uint32_t), s));
-        k_encode_segments_bwd_rl<false><<<ctas > 0 ? std::min(ctas, h->num_sms) : h->num_sms, 1024, smem, s>>>(
+        kern<<<ctas > 0 ? std::min(ctas, h->num_sms) : h->num_sms, 1024, smem, s>>>(
             h->grid, cs, lin, n_dev, n_max, dfeats, dtables, pts, n_pts, dupf, h->d_next + 1, nullptr, nullptr);
         NIF_CK_LAUNCH(h);
         return NIF_OK;

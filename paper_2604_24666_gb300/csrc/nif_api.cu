@@ -1987,6 +1987,10 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
             h->enc_points = nif_handle::PointList{};     // a listed order of the old grid is not reused
             h->alt_enc_points = nif_handle::PointList{};
             return NIF_OK;
+        case NIF_KNOB_BWD_SPLIT:
+            if (value != 1.0 && value != 2.0) return nif_fail(h, NIF_ERR_ARG, "backward level split must be 1 or 2");
+            h->tune.bwd_split = (int)value;
+            return NIF_OK;
         case NIF_KNOB_FAIL_ALLOC:
             if (!(value >= 0.0 && value <= 1.0e6) || value != std::floor(value))
                 return nif_fail(h, NIF_ERR_ARG, "allocation-failure countdown must be an integer in [0, 1e6]");

@@ -34,6 +34,7 @@ NIF_KNOB_STEP_BWD_CTAS = 10
 NIF_KNOB_DETERMINISTIC = 11
 NIF_KNOB_ORDER_BITS = 12
 NIF_KNOB_FAIL_ALLOC = 13
+NIF_KNOB_BWD_SPLIT = 14
 NIF_PROBE_RED8, NIF_PROBE_RED16, NIF_PROBE_LOAD8, NIF_PROBE_LOAD4 = 1, 2, 3, 4
 NIF_PROBE_RED8_WARP, NIF_PROBE_RED16_WARP, NIF_PROBE_LOAD8_WARP, NIF_PROBE_LOAD4_WARP = 5, 6, 7, 8
 

@@ -90,15 +90,19 @@ def test_checkpoint_resume_is_bit_identical(nif, torus, mixed):
     b.close()
 
 
-def test_pipelined_steps_equal_single_steps_bit_for_bit(nif):
+@pytest.mark.parametrize("split", [1, 2], ids=["levels-together", "level-halves"])
+def test_pipelined_steps_equal_single_steps_bit_for_bit(nif, split):
     """Three steps of the training workload (64^3 ellipsoid union, L = 16,
     T = 2^19, 2^18 segments, 16 poses) through one nif_train_steps call and
-    through three nif_train_step calls."""
+    through three nif_train_step calls (the encoding backward's walk with
+    its levels together or in halves, NIF_KNOB_BWD_SPLIT)."""
     wl = S.WORKLOADS["ellipsoids64_train"]
     net = wl["net"]
     mesh = S.ellipsoid_union_mesh()
     a = _det_handle(nif, net, mesh, 5, False)
     b = _det_handle(nif, net, mesh, 5, False)
+    for x in (a, b):
+        nif.nif_set_knob(x.h, nif.NIF_KNOB_BWD_SPLIT, split)
     n_seg, n_poses, seed = 1 << 18, 16, 900
     la = nif.nif_train_steps(a.h, 3, n_seg, n_poses, seed, lr_grid=1e-2, lr_mlp=1e-3, want_loss=True)
     lb = None

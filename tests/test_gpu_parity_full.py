@@ -103,11 +103,17 @@ def test_encode_forward_fp16_tables_matches_oracle(nif, handle, batch, out):
     assert np.all(err <= tol), (err / tol).max()
 
 
+_REF = {}
+
+
+@pytest.mark.parametrize("split", [1, 2], ids=["levels-together", "level-halves"])
 @pytest.mark.parametrize("det", [0, 1], ids=["l2-reductions", "deterministic"])
-def test_encode_backward_sorted_matches_oracle(nif, handle, batch, det):
+def test_encode_backward_sorted_matches_oracle(nif, handle, batch, det, split):
     """The table gradient at the training sizes; with NIF_KNOB_DETERMINISTIC
     the 64-bit fixed-point sums instead, whose bound adds 2^-(S+1) per
-    contribution and whose second run must repeat the first bit for bit."""
+    contribution and whose second run must repeat the first bit for bit;
+    with NIF_KNOB_BWD_SPLIT = 2 each task of the walk holds half of the
+    levels."""
     lin, tables = batch
     net = NET
     handle.set_params(tables, S.init_params(net)[1])
@@ -116,6 +122,7 @@ def test_encode_backward_sorted_matches_oracle(nif, handle, batch, det):
     lint, dft = torch.from_numpy(lin).to(_dev()), torch.from_numpy(df).to(_dev())
     dtab = torch.zeros((net.levels, 1 << net.log2_table, net.feats), dtype=torch.float32, device=_dev())
     nif.nif_set_knob(handle.h, nif.NIF_KNOB_DETERMINISTIC, det)
+    nif.nif_set_knob(handle.h, nif.NIF_KNOB_BWD_SPLIT, split)
     try:
         nif.nif_encode_segments_backward(handle.h, lint, dft, dtab)
         if det:
@@ -124,12 +131,18 @@ def test_encode_backward_sorted_matches_oracle(nif, handle, batch, det):
             assert torch.equal(again, dtab)
     finally:
         nif.nif_set_knob(handle.h, nif.NIF_KNOB_DETERMINISTIC, 0)
+        nif.nif_set_knob(handle.h, nif.NIF_KNOB_BWD_SPLIT, 1)
     g = dtab.cpu().numpy()
     half = net.in_dim // 2
     p = np.concatenate([lin[:, 0:3], lin[:, 3:6]]).astype(np.float64)
     d = np.concatenate([df[:, :half], df[:, half:]]).astype(np.float64)
-    ref, _ = O.encode_points_backward(net, tables, p, d)
-    bnd = B.table_grad_bound(net, tables, p, d, fix_S=B.fixed_scale(n, net.n_terms, df) if det else None)
+    if "ref" not in _REF:
+        _REF["ref"] = O.encode_points_backward(net, tables, p, d)[0]
+    ref = _REF["ref"]
+    key = ("bnd", det)
+    if key not in _REF:
+        _REF[key] = B.table_grad_bound(net, tables, p, d, fix_S=B.fixed_scale(n, net.n_terms, df) if det else None)
+    bnd = _REF[key]
     err = np.abs(g - ref)
     assert np.all(err <= bnd), ((err / np.maximum(bnd, 1e-300)).max(), int((err > bnd).sum()))
     # untouched rows stay exactly zero
