@@ -679,11 +679,11 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   cell in a 2^b-per-axis grid over the rest cube (a counting sort over
  *   2^(3b) cells), so that a warp's points share corner rows. A scheduling
  *   choice only: the features are the same. Synchronises the device.
- * NIF_KNOB_BWD_SPLIT: 1 (default) or 2: how many tasks share a gamma term's
- *   levels in the run-length encoding backward (2: one task per half of the
- *   levels, so that a warp's 32 lanes hold the fine levels of 4 terms; for
- *   L with L/2 >= 4 dividing 32, else 1). A scheduling choice only: the same
- *   sums in another order.
+ * NIF_KNOB_BWD_SPLIT: 1 or 2: how many tasks share a gamma term's levels in
+ *   the run-length encoding backward (2: one task per half of the levels, so
+ *   that a warp's 32 lanes hold the fine levels of 4 terms; for L with
+ *   L/2 >= 4 dividing 32, else 1); 0 (default): 2 when L >= 16, else 1. A
+ *   scheduling choice only: the same sums in another order.
  * NIF_KNOB_FAIL_ALLOC: n >= 1 makes the n-th allocation of scratch memory
  *   from now on (a buffer the handle grows on demand) fail as an
  *   out-of-memory cudaMalloc would: the call that needs it returns

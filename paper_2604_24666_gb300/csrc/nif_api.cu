@@ -1988,7 +1988,8 @@ extern "C" nif_status nif_set_knob(nif_handle* h, int knob, double value) {
             h->alt_enc_points = nif_handle::PointList{};
             return NIF_OK;
         case NIF_KNOB_BWD_SPLIT:
-            if (value != 1.0 && value != 2.0) return nif_fail(h, NIF_ERR_ARG, "backward level split must be 1 or 2");
+            if (value != 0.0 && value != 1.0 && value != 2.0)
+                return nif_fail(h, NIF_ERR_ARG, "backward level split must be 0, 1 or 2");
             h->tune.bwd_split = (int)value;
             return NIF_OK;
         case NIF_KNOB_FAIL_ALLOC:

@@ -276,7 +276,8 @@ struct nif_handle {
         int step_prio = 0;              // NIF_KNOB_STEP_PRIORITY: pipelined steps on the high-priority streams
         int query_fused = 1;            // NIF_KNOB_QUERY_FUSED: 16-bit queries encode into the tensor-core
                                         // MLP's shared-memory ring (one launch) instead of two kernels
-        int bwd_split = 1;              // NIF_KNOB_BWD_SPLIT: level halves per task of the run-length backward
+        int bwd_split = 0;              // NIF_KNOB_BWD_SPLIT: level halves per task of the run-length backward
+                                        // (0: 2 when L >= 16, else 1)
         int order_bits = 7;             // NIF_KNOB_ORDER_BITS: the rest-space point order sorts by the Morton
                                         // code of a 2^b-per-axis grid (measured on the 64^3 steps: FP32 2.90 ms
                                         // at 6, 2.79 at 7, 2.85 at 8; BF16 mixed 2.35, 2.22, 2.28; the

@@ -131,7 +131,7 @@ def test_encode_backward_sorted_matches_oracle(nif, handle, batch, det, split):
             assert torch.equal(again, dtab)
     finally:
         nif.nif_set_knob(handle.h, nif.NIF_KNOB_DETERMINISTIC, 0)
-        nif.nif_set_knob(handle.h, nif.NIF_KNOB_BWD_SPLIT, 1)
+        nif.nif_set_knob(handle.h, nif.NIF_KNOB_BWD_SPLIT, 0)
     g = dtab.cpu().numpy()
     half = net.in_dim // 2
     p = np.concatenate([lin[:, 0:3], lin[:, 3:6]]).astype(np.float64)
