@@ -39,11 +39,10 @@ QUERY_WORKLOAD = "torus128_query"
 N_SEG = 1 << 18
 N_POSES = 16
 # DRAM bytes (read + write) per launch from one ncu capture (--set full) of
-# the current kernel of a stage on this workload; a stage missing here
-# reports traffic null. The encoding backward's last capture (679.7 MB) was
-# of its one-task-per-term layout; the default for L = 16 now splits the
-# levels over two tasks, so its traffic is null until captured again.
-NCU_TRAFFIC = {}
+# the current kernel of a stage on this workload (the encoding backward with
+# a term's levels split over two tasks); a stage missing here reports
+# traffic null.
+NCU_TRAFFIC = {"encode_bwd": 701.4e6}
 # stages the library runs beside the main stream's work (weight gradients and
 # the weights' update on its second stream, the next step's batch on its
 # third): their event intervals include the overlap, so they are not the
