@@ -199,14 +199,20 @@ nif_status nif_set_params(nif_handle* h, int group, const void* src_host, size_t
 nif_status nif_reset_optimizer(nif_handle* h);
 
 /* Checkpoint of the trainable state: a 64-byte header (magic "NIFCKPT1",
- * format version 2, the sizes of the configuration that must match, the Adam
+ * format version 3, the sizes of the configuration that must match, the Adam
  * step count), then the FP32 parameters, Adam first and second moments, the
  * 40-byte state of the mixed-precision path (loss scale, clean-step and
  * skipped-step counts, the Adam bias-correction products of the steps taken),
- * and a CRC-32 (IEEE) of everything before it. nif_checkpoint_bytes gives the
- * size; save writes into host memory, load checks the header, sizes and CRC
- * (NIF_ERR_ARG on any mismatch, leaving the handle unchanged) and restores
- * all of it. Both block the host. Sampling is seeded by the caller (step
+ * the learned deformation field's section (a 16-byte header: int32
+ * instances, int32 nodes per axis G, int64 Adam step count; then its
+ * displacements, first and second moments, [n][G^3] x (x, y, z, 0) FP32
+ * each; n = G = 0 without a field), and a CRC-32 (IEEE) of everything before
+ * it. nif_checkpoint_bytes gives the size of the handle's current state;
+ * save writes into host memory; load checks the header, sizes and CRC
+ * (NIF_ERR_ARG on any mismatch, leaving the handle unchanged; NIF_ERR_STATE
+ * when the field's shape would change while query plans exist) and restores
+ * all of it, adding, resizing or removing the handle's field to match. Both
+ * block the host. Sampling is seeded by the caller (step
  * seeds), so a checkpoint plus the next seeds determine the run; with
  * NIF_KNOB_DETERMINISTIC the resumed steps are bit-identical to the
  * uninterrupted ones. */

@@ -771,7 +771,7 @@ uint32_t crc32_ieee(const uint8_t* p, size_t n) {
 CkptHeader ckpt_header(const nif_handle* h) {
     CkptHeader hd{};
     std::memcpy(hd.magic, "NIFCKPT1", 8);
-    hd.version = 2;
+    hd.version = 3;
     hd.n_params_lo = (uint32_t)(h->n_params & 0xFFFFFFFFu);
     hd.n_params_hi = (uint32_t)(h->n_params >> 32);
     hd.L = (uint32_t)h->L;
@@ -787,9 +787,22 @@ CkptHeader ckpt_header(const nif_handle* h) {
 
 }  // namespace
 
+// After the mixed path's state: the learned deformation field's section, a
+// 16-byte header (instances, nodes per axis, Adam step count) and its values,
+// first and second moments, [n][G^3] float4 each (empty without a field).
+struct CkptField {
+    int32_t n, G;
+    int64_t step;
+};
+static_assert(sizeof(CkptField) == 16, "checkpoint field header is 16 bytes");
+static_assert(sizeof(NifLossScale) == 40, "checkpoint mixed-precision state is 40 bytes");
+
+static size_t ckpt_field_bytes(int64_t n, int64_t G) { return 3 * sizeof(float4) * (size_t)(n * G * G * G); }
+
 extern "C" nif_status nif_checkpoint_bytes(const nif_handle* h, size_t* bytes) {
     if (!h || !bytes) return NIF_ERR_ARG;
-    *bytes = sizeof(CkptHeader) + 3 * sizeof(float) * h->n_params + sizeof(NifLossScale) + sizeof(uint32_t);
+    *bytes = sizeof(CkptHeader) + 3 * sizeof(float) * h->n_params + sizeof(NifLossScale) + sizeof(CkptField) +
+             ckpt_field_bytes(h->field_n, h->field_G) + sizeof(uint32_t);
     return NIF_OK;
 }
 
@@ -806,27 +819,61 @@ extern "C" nif_status nif_checkpoint_save(nif_handle* h, void* dst, size_t bytes
     NIF_CK(h, cudaMemcpy(o + sizeof hd + nb, h->d_m, nb, cudaMemcpyDeviceToHost));
     NIF_CK(h, cudaMemcpy(o + sizeof hd + 2 * nb, h->d_v, nb, cudaMemcpyDeviceToHost));
     NIF_CK(h, cudaMemcpy(o + sizeof hd + 3 * nb, h->d_ls, sizeof(NifLossScale), cudaMemcpyDeviceToHost));
-    const size_t body = sizeof hd + 3 * nb + sizeof(NifLossScale);
+    uint8_t* f = o + sizeof hd + 3 * nb + sizeof(NifLossScale);
+    const CkptField fh{h->field_n, h->field_G, (int64_t)h->field_step};
+    std::memcpy(f, &fh, sizeof fh);
+    const size_t fb = ckpt_field_bytes(h->field_n, h->field_G) / 3;
+    if (fb) {
+        NIF_CK(h, cudaMemcpy(f + sizeof fh, h->d_field, fb, cudaMemcpyDeviceToHost));
+        NIF_CK(h, cudaMemcpy(f + sizeof fh + fb, h->d_field_m, fb, cudaMemcpyDeviceToHost));
+        NIF_CK(h, cudaMemcpy(f + sizeof fh + 2 * fb, h->d_field_v, fb, cudaMemcpyDeviceToHost));
+    }
+    const size_t body = need - sizeof(uint32_t);
     uint32_t crc = crc32_ieee(o, body);
     std::memcpy(o + body, &crc, sizeof crc);
     return NIF_OK;
 }
 
 extern "C" nif_status nif_checkpoint_load(nif_handle* h, const void* src, size_t bytes) {
-    size_t need = 0;
-    if (nif_checkpoint_bytes(h, &need) != NIF_OK || !src) return NIF_ERR_ARG;
-    if (bytes != need) return nif_fail(h, NIF_ERR_ARG, "checkpoint size does not match this configuration");
+    if (!h || !src) return NIF_ERR_ARG;
+    const size_t nb = sizeof(float) * h->n_params;
+    const size_t fpos = sizeof(CkptHeader) + 3 * nb + sizeof(NifLossScale);     // the field section
+    if (bytes < fpos + sizeof(CkptField) + sizeof(uint32_t))
+        return nif_fail(h, NIF_ERR_ARG, "checkpoint size does not match this configuration");
     const uint8_t* in = static_cast<const uint8_t*>(src);
     CkptHeader hd;
     std::memcpy(&hd, in, sizeof hd);
     CkptHeader mine = ckpt_header(h);
     mine.adam_step = hd.adam_step;
     if (std::memcmp(&hd, &mine, sizeof hd) != 0) return nif_fail(h, NIF_ERR_ARG, "checkpoint header mismatch");
-    size_t nb = sizeof(float) * h->n_params;
-    const size_t body = sizeof hd + 3 * nb + sizeof(NifLossScale);
+    CkptField fh;
+    std::memcpy(&fh, in + fpos, sizeof fh);
+    if (!(fh.n == 0 && fh.G == 0) && !(fh.n > 0 && fh.G >= 2 && fh.G <= NIF_FIELD_MAX_G))
+        return nif_fail(h, NIF_ERR_ARG, "checkpoint field section malformed");
+    const size_t fb = ckpt_field_bytes(fh.n, fh.G) / 3;
+    const size_t body = fpos + sizeof fh + 3 * fb;
+    if (bytes != body + sizeof(uint32_t))
+        return nif_fail(h, NIF_ERR_ARG, "checkpoint size does not match this configuration");
     uint32_t crc = 0;
     std::memcpy(&crc, in + body, sizeof crc);
     if (crc != crc32_ieee(in, body)) return nif_fail(h, NIF_ERR_ARG, "checkpoint CRC mismatch");
+    // a query plan's graph holds the field as captured (see nif_set_field)
+    if ((fh.n != h->field_n || fh.G != h->field_G) && h->n_plans > 0)
+        return nif_fail(h, NIF_ERR_STATE, "destroy the query plans before loading a checkpoint with another field");
+    if (fh.n > 0) {
+        // allocate (or keep) a field of the checkpoint's shape, then overwrite it
+        std::vector<float> zero((size_t)fh.n * fh.G * fh.G * fh.G * 3, 0.f);
+        nif_status st = nif_set_field(h, fh.n, fh.G, zero.data());
+        if (st != NIF_OK) return st;
+        const uint8_t* f = in + fpos + sizeof fh;
+        NIF_CK(h, cudaMemcpy(h->d_field, f, fb, cudaMemcpyHostToDevice));
+        NIF_CK(h, cudaMemcpy(h->d_field_m, f + fb, fb, cudaMemcpyHostToDevice));
+        NIF_CK(h, cudaMemcpy(h->d_field_v, f + 2 * fb, fb, cudaMemcpyHostToDevice));
+        h->field_step = (long)fh.step;
+    } else if (h->field_n > 0) {
+        nif_status st = nif_set_field(h, 0, 0, nullptr);
+        if (st != NIF_OK) return st;
+    }
     NIF_CK(h, cudaDeviceSynchronize());
     NIF_CK(h, cudaMemcpy(h->d_params, in + sizeof hd, nb, cudaMemcpyHostToDevice));
     NIF_CK(h, cudaMemcpy(h->d_m, in + sizeof hd + nb, nb, cudaMemcpyHostToDevice));

@@ -273,3 +273,34 @@ def test_field_fitting_moves_towards_the_target(nif, torus):
     f = nif.nif_get_field(h.h)[0].astype(np.float64)
     assert O.field_lipschitz(f) <= 0.9 + 1e-5
     h.close()
+
+
+def test_checkpoint_carries_the_field(nif, torus):
+    """A checkpoint holds the learned field (displacements, Adam moments and
+    step count): loaded into a fresh handle it gives the same field and
+    saves to the same bytes, and the next field step of both handles moves
+    the field alike; a checkpoint taken without a field removes one."""
+    net = S.NetConfig()
+    a = nif.Nif(net, torus, seed=7)
+    bare = nif.nif_checkpoint_save(a.h)
+    nif.nif_set_field(a.h, _field(5, 451, lip=0.2)[None])
+    pose = np.array([[0.0, 0.7, 0.0]], np.float32)
+    target = np.array([[0.0, 1.0, 0.0]], np.float32)
+    for step in range(3):
+        rays = torch.from_numpy(S.sphere_rays(6000, seed=452 + step)).to(_dev())
+        nif.nif_field_step(a.h, pose, rays, 1 << 13, target, lr_field=2e-3, want_loss=False)
+    blob = nif.nif_checkpoint_save(a.h)
+    assert len(blob) == len(bare) + 3 * 16 * 5 ** 3
+    b = nif.Nif(net, torus, seed=99)
+    nif.nif_checkpoint_load(b.h, blob)
+    assert nif.nif_checkpoint_save(b.h) == blob
+    assert np.array_equal(nif.nif_get_field(b.h), nif.nif_get_field(a.h))
+    rays = torch.from_numpy(S.sphere_rays(6000, seed=460)).to(_dev())
+    for x in (a, b):
+        nif.nif_field_step(x.h, pose, rays, 1 << 13, target, lr_field=2e-3, want_loss=False)
+    # field gradients are summed with float atomics: the same step to rounding
+    np.testing.assert_allclose(nif.nif_get_field(b.h), nif.nif_get_field(a.h), atol=1e-6)
+    nif.nif_checkpoint_load(b.h, bare)
+    assert nif.nif_get_field(b.h) is None
+    for x in (a, b):
+        x.close()
