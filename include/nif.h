@@ -677,8 +677,11 @@ nif_status nif_sync_status(nif_handle* h, void* stream);
  *   per contribution); the MLP weight gradients are summed per row range and
  *   the ranges added in order; the loss sums are added in block order. The
  *   paper has no counterpart (it trains with no stated reduction order).
- *   Slower (measured on the 64^3 FP32 step in the design notes). Handles
- *   with NIF_FLAG_CONCAT_ENCODING are refused (NIF_ERR_ARG). Synchronises the
+ *   Slower (measured on the 64^3 FP32 step in the design notes). The
+ *   gradients with respect to poses and to a learned field (nif_pose_step,
+ *   nif_pose_gradient, nif_field_gradient and the field part of
+ *   nif_field_step) keep their float reductions. Handles with
+ *   NIF_FLAG_CONCAT_ENCODING are refused (NIF_ERR_ARG). Synchronises the
  *   device.
  * NIF_KNOB_ORDER_BITS: b in [4, 8] (default 7): the encoders of tables over
  *   4 MiB visit the distinct end points sorted by the Morton code of their
