@@ -248,6 +248,43 @@ def test_encode_points_backward(nif, torus):
     h.close()
 
 
+@pytest.mark.parametrize("levels", [12, 6])
+def test_deterministic_table_gradient_other_level_counts(nif, torus, levels):
+    """NIF_KNOB_DETERMINISTIC on handles whose level count does not divide
+    32 (one thread per segment end point and gamma term, every contribution
+    rounded to 64-bit fixed point alone): the table gradient of the segment
+    encoding repeats bit for bit and meets the oracle's bound plus 2^-(S+1)
+    per contribution, entry by entry."""
+    net = S.NetConfig(levels=levels, log2_table=12)
+    h = nif.Nif(net, torus)
+    tables = random_tables(net, 71)
+    h.set_params(tables, S.init_params(net)[1])
+    lin, _ = S.chained_segments(3000, seed=72, voxel_res=net.voxel_res, gap=0.1)
+    keep = B.certain_cells(net, lin[:, 0:3]) & B.certain_cells(net, lin[:, 3:6])
+    lin = lin[keep][:2000]
+    n = len(lin)
+    assert n == 2000
+    df = np.random.default_rng(73).normal(size=(n, net.in_dim)).astype(np.float32)
+    lint, dft = torch.from_numpy(lin).to(_dev()), torch.from_numpy(df).to(_dev())
+    nif.nif_set_knob(h.h, nif.NIF_KNOB_DETERMINISTIC, 1)
+    runs = []
+    for _ in range(2):
+        d = torch.zeros((net.levels, 1 << net.log2_table, 2), dtype=torch.float32, device=_dev())
+        nif.nif_encode_segments_backward(h.h, lint, dft, d)
+        runs.append(d)
+    torch.cuda.synchronize()
+    assert torch.equal(runs[0], runs[1])
+    g = runs[0].cpu().numpy()
+    half = net.in_dim // 2
+    p = np.concatenate([lin[:, 0:3], lin[:, 3:6]]).astype(np.float64)
+    d = np.concatenate([df[:, :half], df[:, half:]]).astype(np.float64)
+    ref, _ = O.encode_points_backward(net, tables, p, d)
+    bnd = B.table_grad_bound(net, tables, p, d, fix_S=B.fixed_scale(n, net.n_terms, df))
+    err = np.abs(g - ref)
+    assert np.all(err <= bnd), ((err / np.maximum(bnd, 1e-300)).max(), int((err > bnd).sum()))
+    h.close()
+
+
 # ---------------------------------------------------------------------------
 # MLP (FP32)
 # ---------------------------------------------------------------------------
