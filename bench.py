@@ -51,6 +51,16 @@ OVERLAPPED = {"mlp_dw_fp32", "mlp_dw_tc", "adam_weights", "sample_rays", "refit"
               "seg_scatter", "seg_emit", "linearize", "labels"}
 
 
+def _emit(line, args):
+    """Prints the run's JSON line and, with --log, appends it to a JSON-lines
+    file (one record per run, kept beside the profiles of the same build)."""
+    text = json.dumps(line)
+    print(text, flush=True)
+    if getattr(args, "log", None):
+        with open(args.log, "a") as f:
+            f.write(text + "\n")
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -200,7 +210,7 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": "segments/s", "cores": thr, "kind": "oracle",
                              "sample": f"{args.steps} steps x {n_rays} rays (~{segs // max(args.steps, 1)} segments/step)"},
             "e2e": {"value": v, "unit": "segments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    _emit(line, args)
     return 0
 
 
@@ -496,7 +506,7 @@ def run_ours(args):
             "clocks": clocks, "loss": list(loss) if loss is not None else None, "train_mixed": mixed,
             "train_deterministic": det, "query": query, "batch": batch, "frame_loop": frame, "traversal": trav, "field": field,
             "precision": precision}
-    print(json.dumps(line), flush=True)
+    _emit(line, args)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -1043,6 +1053,7 @@ def main():
     ap.add_argument("--only-field", action="store_true", help="measure only the learned deformation field (profiling aid)")
     ap.add_argument("--only-batch", action="store_true", help="measure only the batched query (profiling aid)")
     ap.add_argument("--only-traversal", action="store_true", help="measure only the traversal comparison (profiling aid)")
+    ap.add_argument("--log", default="", help="also append the JSON line to this JSON-lines file")
     ap.add_argument("--frames", type=int, default=120, help="frames of the animated frame loop")
     ap.add_argument("--frame-pretrain", type=int, default=20000, help="training steps before the frame loop")
     args = ap.parse_args()

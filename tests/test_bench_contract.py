@@ -1,6 +1,6 @@
-"""bench.py's reference arm (the FP64 oracle on the host cores, as the
-round's driver runs it) prints one JSON line in the contract's form; it
-needs no GPU, so it runs here on a bounded sample."""
+"""bench.py's reference arm (the FP64 oracle on the host cores) prints one
+JSON line in the benchmark's form, and --log appends the same record to a
+JSON-lines file; it needs no GPU, so it runs here on a bounded sample."""
 import json
 import os
 import subprocess
@@ -9,13 +9,15 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_reference_arm_prints_one_contract_line():
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
-                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+def test_reference_arm_prints_one_contract_line(tmp_path):
+    log = tmp_path / "runs.jsonl"
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3",
+                        "--log", str(log)], cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1, r.stdout[-2000:]
     d = json.loads(lines[0])
+    assert log.read_text().splitlines() == lines         # --log appends the same record
     assert d["impl"] == "reference" and d["unit"] == "segments/s" and d["higher_is_better"] is True
     assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] >= 3 and d["value"] > 0
     assert d["config"]["workload"] == "ellipsoids64_train" and d["dtype"] == "f64"
